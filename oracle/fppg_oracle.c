@@ -1,0 +1,1655 @@
+/*
+ * FP64 CPU oracle for the FPPG relaxation hot path (arXiv 2501.03056).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA library is checked against.  Only the test-suite, the smoke check and
+ * the CPU-baseline leg of the benchmark load it; the product path never does.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Every step follows the paper in its own order and notation:
+ *   Sec. 3.1.1  uniform background grid, cell = particle spacing dx
+ *   Sec. 3.1.2  triangle-box overlap (separating axes) marks surface cells,
+ *               ray parity (Fig. 6) classifies points as inside / outside
+ *   Sec. 3.1.3  cell keys (row-major here; Eq. 9 Morton as an alternative),
+ *               cell lists sorted by key, C_compact begin/length
+ *   Sec. 3.2.1  projection onto the nearest triangle whose foot is inside
+ *               (cross-product test of Fig. 8)
+ *   Sec. 3.2.2  edge-face map, dihedral feature rule, singular points,
+ *               feature lines by colouring walk, even spacing L/ceil(L/dx)
+ *   Sec. 3.3.1  pairwise pressure force, Eq. 15, Wendland C2 kernel Eq. 16/17
+ *   Sec. 3.3.2  velocity reset and Euler update, Eqs. 22-23, tangential
+ *               displacement, Eqs. 24-25
+ *   Sec. 3.3.3  surface re-projection over the 27 neighbouring cells, revert
+ *               when no triangle is projectable; Algorithm 1
+ *   Sec. 3.3.4  volume particles feel volume, surface and innermost ones
+ *
+ * Readings where the paper is silent or garbled (all shared with the CUDA
+ * side by documentation only):
+ *   - alpha_3 = 21 / (16 pi h^3): the printed 21/(6 pi h^3) does not
+ *     integrate to one over the support 2h; q = r / h.
+ *   - the time step follows the acceleration criterion dt = 0.25 sqrt(h/amax)
+ *     of the cited feature-aware SPH work; with v reset to 0 the move is
+ *     a dt^2, so the fastest particle moves exactly h/16.
+ *   - Eqs. 24-25 are read as removing the normal component of the
+ *     displacement (the printed form projects the position itself).
+ *   - force constants m = 1, p0 / rho_t^2 terms folded into K = 1; the step
+ *     is invariant to K because dt normalises by amax.
+ *   - interaction mask: S <- {S, F, P}; V <- {S, V, F, I, P}; F <- {F, P};
+ *     I and P (singular feature points) never move.
+ *   - one Jacobi update per iteration over all mobile classes with a single
+ *     amax per body.
+ *   - volume particles are kept inside by the sign of the angle-weighted
+ *     pseudonormal of the closest triangle feature (Baerentzen and Aanaes
+ *     2005); a volume particle with no triangle within the 27 cells is
+ *     accepted.
+ *   - decisions that turn floating point into an integer (cell keys, the
+ *     neighbour test r^2 < (2h)^2, which triangle / segment is chosen, inside
+ *     or outside) are taken in FP32 like the kernels; every continuous
+ *     quantity (forces, displacements, feet, energies) is FP64.
+ *
+ * Parity status per function is listed in the tests that pin it; the
+ * end-state quality versus the paper's own figures is unpinned (the paper
+ * publishes no particle data).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_S 0
+#define OR_V 1
+#define OR_F 2
+#define OR_I 3
+#define OR_P 4
+
+typedef struct {
+    uint32_t key;
+    uint32_t id;
+} or_kv;
+
+typedef struct {
+    /* mesh (Sec. 3.1) */
+    int64_t nv, nt;
+    double *V;      /* [nv*3] vertices (FP64 copy of the FP32 input)        */
+    float *Vf;      /* [nv*3] vertices as given                             */
+    int32_t *T;     /* [nt*3]                                              */
+    double *Nrm;    /* [nt*3] cross(b - a, c - a), not normalised          */
+    double *Nu;     /* [nt*3] unit normals                                  */
+    float *Nuf;     /* [nt*3] unit normals rounded to FP32                  */
+    float *EPf;     /* [nt*9] edge pseudonormals, edge k = (v_k, v_k+1)     */
+    float *VPf;     /* [nv*3] angle-weighted vertex pseudonormals           */
+    float dx, h;
+    /* triangle grid, cell = dx (Sec. 3.1.1) */
+    float tg_o[3];
+    float tg_inv;
+    int32_t tg_n[3];
+    int64_t npairs;
+    int64_t *pair_key; /* sorted (cell key, triangle) pairs = C_compact   */
+    int32_t *pair_tri;
+    /* neighbour grid, cell = 2h (1 + 2^-8) */
+    float ng_o[3];
+    float ng_inv;
+    float ng_cell;
+    int32_t ng_n[3];
+    float R2;
+    /* features (Sec. 3.2.2) */
+    double feat_deg;
+    int64_t nfe;
+    int32_t *fe;        /* [nfe*2] feature edges (v1 < v2), sorted           */
+    int64_t nsing;
+    int32_t *sing;      /* singular vertices, ascending                      */
+    int64_t nlines;
+    int64_t *line_first;  /* first segment of each line                     */
+    int64_t *line_nseg;
+    int32_t *line_closed;
+    int64_t nseg;
+    int32_t *seg_v;       /* [nseg*2] vertex ids of each segment            */
+    int32_t *seg_line;
+    /* particles */
+    int64_t n;
+    double *X;
+    int32_t *cls;
+    int32_t *cons;
+    int fixed_features;
+    double last_maxdisp;
+    double last_amax;
+    int64_t last_reverts;
+} or_ctx;
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                     */
+/* ------------------------------------------------------------------------ */
+static void sub3(const double *a, const double *b, double *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void subf(const float *a, const float *b, float *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static float dotf(const float *a, const float *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void crossf(const float *a, const float *b, float *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wendland C2 kernel, Eqs. 16-17 (3-D, support 2h)                          */
+/* ------------------------------------------------------------------------ */
+double oracle_alpha3(double h) { return 21.0 / (16.0 * M_PI * h * h * h); }
+
+double oracle_W(double r, double h)
+{
+    double q = r / h;
+    if (q > 2.0) return 0.0;
+    double t = 1.0 - 0.5 * q;
+    return oracle_alpha3(h) * t * t * t * t * (2.0 * q + 1.0);
+}
+
+/* dW/dr = alpha/h * d/dq[(1 - q/2)^4 (2q + 1)] = -5 alpha q (1 - q/2)^3 / h */
+double oracle_dW(double r, double h)
+{
+    double q = r / h;
+    if (q > 2.0) return 0.0;
+    double t = 1.0 - 0.5 * q;
+    return -5.0 * oracle_alpha3(h) * q * t * t * t / h;
+}
+
+/* Lattice sum of W over a cubic (dim 3), square (dim 2) or linear (dim 1)
+ * lattice of spacing dx, origin included: the ideal kernel sum W0 of a
+ * perfectly uniform distribution of the class. */
+double oracle_lattice_sum(double dx, double h, int dim)
+{
+    int m = (int)ceil(2.0 * h / dx) + 1;
+    double s = 0.0;
+    for (int i = -m; i <= m; i++)
+        for (int j = (dim >= 2 ? -m : 0); j <= (dim >= 2 ? m : 0); j++)
+            for (int k = (dim >= 3 ? -m : 0); k <= (dim >= 3 ? m : 0); k++) {
+                double r = dx * sqrt((double)(i * i + j * j + k * k));
+                s += oracle_W(r, h);
+            }
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* grids: FP32 cell coordinate rule (Sec. 3.1.1 / 3.1.3)                     */
+/* ------------------------------------------------------------------------ */
+/* origin = bbmin - margin * cell (FP64, rounded to FP32); inv = 1 / cell in
+ * FP64 rounded to FP32; n = ceil((bbmax - origin) / cell) + margin. */
+static void grid_setup(const float *bbmin, const float *bbmax, float cell, int margin,
+                       float *o, float *inv, int32_t *n)
+{
+    for (int a = 0; a < 3; a++) {
+        o[a] = (float)((double)bbmin[a] - (double)margin * (double)cell);
+        n[a] = (int32_t)ceil(((double)bbmax[a] - (double)o[a]) / (double)cell) + margin;
+    }
+    *inv = (float)(1.0 / (double)cell);
+}
+
+/* cell coordinate of a point along one axis: clamp((x - o) * inv, 0, n - 1),
+ * evaluated in FP32 without contraction, truncated to an integer. */
+static int32_t cell_coord(float x, float o, float inv, int32_t n)
+{
+    float t = x - o;
+    t = t * inv;
+    t = fmaxf(t, 0.0f);
+    t = fminf(t, (float)(n - 1));
+    return (int32_t)t;
+}
+
+/* Eq. 9: interleave the bits of (x, y, z) into a Morton code (x lowest). */
+uint64_t oracle_morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    uint64_t code = 0;
+    for (int b = 0; b < 21; b++) {
+        code |= (uint64_t)((x >> b) & 1u) << (3 * b);
+        code |= (uint64_t)((y >> b) & 1u) << (3 * b + 1);
+        code |= (uint64_t)((z >> b) & 1u) << (3 * b + 2);
+    }
+    return code;
+}
+
+/* ------------------------------------------------------------------------ */
+/* mesh preprocessing                                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t v1, v2, tri, k;
+} or_edge;
+
+static int edge_cmp(const void *pa, const void *pb)
+{
+    const or_edge *a = pa, *b = pb;
+    if (a->v1 != b->v1) return a->v1 < b->v1 ? -1 : 1;
+    if (a->v2 != b->v2) return a->v2 < b->v2 ? -1 : 1;
+    if (a->tri != b->tri) return a->tri < b->tri ? -1 : 1;
+    return a->k < b->k ? -1 : (a->k > b->k);
+}
+
+/* Edge-face map of Sec. 3.2.2: every triangle edge as (v1 < v2, face). */
+static or_edge *edge_face_map(const or_ctx *c)
+{
+    or_edge *E = malloc(sizeof(or_edge) * 3 * (size_t)c->nt);
+    for (int64_t t = 0; t < c->nt; t++)
+        for (int k = 0; k < 3; k++) {
+            int32_t a = c->T[3 * t + k], b = c->T[3 * t + (k + 1) % 3];
+            or_edge *e = &E[3 * t + k];
+            e->v1 = a < b ? a : b;
+            e->v2 = a < b ? b : a;
+            e->tri = (int32_t)t;
+            e->k = k;
+        }
+    qsort(E, 3 * (size_t)c->nt, sizeof(or_edge), edge_cmp);
+    return E;
+}
+
+static void mesh_prepare(or_ctx *c)
+{
+    int64_t nt = c->nt, nv = c->nv;
+    c->Nrm = malloc(sizeof(double) * 3 * nt);
+    c->Nu = malloc(sizeof(double) * 3 * nt);
+    c->Nuf = malloc(sizeof(float) * 3 * nt);
+    c->EPf = malloc(sizeof(float) * 9 * nt);
+    c->VPf = malloc(sizeof(float) * 3 * nv);
+    for (int64_t t = 0; t < nt; t++) {
+        const double *a = c->V + 3 * c->T[3 * t], *b = c->V + 3 * c->T[3 * t + 1], *cc = c->V + 3 * c->T[3 * t + 2];
+        double e1[3], e2[3], n[3];
+        sub3(b, a, e1);
+        sub3(cc, a, e2);
+        cross3(e1, e2, n);
+        double len = sqrt(dot3(n, n));
+        for (int k = 0; k < 3; k++) {
+            c->Nrm[3 * t + k] = n[k];
+            c->Nu[3 * t + k] = len > 0 ? n[k] / len : 0.0;
+            c->Nuf[3 * t + k] = (float)c->Nu[3 * t + k];
+        }
+    }
+    /* edge pseudonormal: normalised sum of the unit normals of all faces on
+     * the edge (two for a closed manifold) */
+    or_edge *E = edge_face_map(c);
+    int64_t m = 3 * nt;
+    for (int64_t s = 0; s < m;) {
+        int64_t e = s;
+        while (e < m && E[e].v1 == E[s].v1 && E[e].v2 == E[s].v2) e++;
+        double sum[3] = {0, 0, 0};
+        for (int64_t q = s; q < e; q++)
+            for (int k = 0; k < 3; k++) sum[k] += c->Nu[3 * E[q].tri + k];
+        double len = sqrt(dot3(sum, sum));
+        for (int64_t q = s; q < e; q++)
+            for (int k = 0; k < 3; k++)
+                c->EPf[9 * E[q].tri + 3 * E[q].k + k] = (float)(len > 0 ? sum[k] / len : 0.0);
+        s = e;
+    }
+    free(E);
+    /* vertex pseudonormal: sum of incident unit normals weighted by the
+     * triangle's angle at the vertex */
+    double *acc = calloc(3 * (size_t)nv, sizeof(double));
+    for (int64_t t = 0; t < nt; t++)
+        for (int k = 0; k < 3; k++) {
+            int32_t vi = c->T[3 * t + k];
+            const double *p = c->V + 3 * vi;
+            const double *q1 = c->V + 3 * c->T[3 * t + (k + 1) % 3];
+            const double *q2 = c->V + 3 * c->T[3 * t + (k + 2) % 3];
+            double u[3], w[3];
+            sub3(q1, p, u);
+            sub3(q2, p, w);
+            double lu = sqrt(dot3(u, u)), lw = sqrt(dot3(w, w));
+            double cosang = (lu > 0 && lw > 0) ? dot3(u, w) / (lu * lw) : 1.0;
+            if (cosang > 1.0) cosang = 1.0;
+            if (cosang < -1.0) cosang = -1.0;
+            double ang = acos(cosang);
+            for (int j = 0; j < 3; j++) acc[3 * vi + j] += ang * c->Nu[3 * t + j];
+        }
+    for (int64_t v = 0; v < nv; v++) {
+        double len = sqrt(dot3(acc + 3 * v, acc + 3 * v));
+        for (int j = 0; j < 3; j++) c->VPf[3 * v + j] = (float)(len > 0 ? acc[3 * v + j] / len : 0.0);
+    }
+    free(acc);
+}
+
+/* ------------------------------------------------------------------------ */
+/* triangle-box overlap by separating axes (Sec. 3.1.2)                       */
+/* ------------------------------------------------------------------------ */
+/* Box given by its centre and half size; the box is inflated by 1e-6 dx so
+ * that a triangle lying exactly on a cell face counts in both cells. */
+static int axis_separates(const double *ax, const double *v0, const double *v1, const double *v2, double hs)
+{
+    double p0 = dot3(ax, v0), p1 = dot3(ax, v1), p2 = dot3(ax, v2);
+    double mn = fmin(p0, fmin(p1, p2)), mx = fmax(p0, fmax(p1, p2));
+    double r = hs * (fabs(ax[0]) + fabs(ax[1]) + fabs(ax[2]));
+    return mn > r || mx < -r;
+}
+
+static int tri_box_overlap(const double *ctr, double hs, const double *a, const double *b, const double *c)
+{
+    double v0[3], v1[3], v2[3], f[3][3];
+    sub3(a, ctr, v0);
+    sub3(b, ctr, v1);
+    sub3(c, ctr, v2);
+    sub3(v1, v0, f[0]);
+    sub3(v2, v1, f[1]);
+    sub3(v0, v2, f[2]);
+    /* box face normals */
+    for (int k = 0; k < 3; k++) {
+        double mn = fmin(v0[k], fmin(v1[k], v2[k])), mx = fmax(v0[k], fmax(v1[k], v2[k]));
+        if (mn > hs || mx < -hs) return 0;
+    }
+    /* triangle normal */
+    double n[3];
+    cross3(f[0], f[1], n);
+    if (fabs(dot3(n, v0)) > hs * (fabs(n[0]) + fabs(n[1]) + fabs(n[2]))) return 0;
+    /* nine edge cross products */
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double e[3] = {0, 0, 0}, ax[3];
+            e[i] = 1.0;
+            cross3(e, f[j], ax);
+            if (axis_separates(ax, v0, v1, v2, hs)) return 0;
+        }
+    return 1;
+}
+
+typedef struct {
+    int64_t key;
+    int32_t tri;
+} or_pair;
+
+static int pair_cmp(const void *pa, const void *pb)
+{
+    const or_pair *a = pa, *b = pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->tri < b->tri ? -1 : (a->tri > b->tri);
+}
+
+static void bin_triangles(or_ctx *c)
+{
+    double cell = (double)c->dx, hs = 0.5 * cell + 1e-6 * cell;
+    int64_t cap = 1024, np = 0;
+    or_pair *P = malloc(sizeof(or_pair) * cap);
+    for (int64_t t = 0; t < c->nt; t++) {
+        const double *a = c->V + 3 * c->T[3 * t], *b = c->V + 3 * c->T[3 * t + 1], *cc = c->V + 3 * c->T[3 * t + 2];
+        int32_t lo[3], hi[3];
+        for (int k = 0; k < 3; k++) {
+            double mn = fmin(a[k], fmin(b[k], cc[k])), mx = fmax(a[k], fmax(b[k], cc[k]));
+            lo[k] = (int32_t)floor((mn - (double)c->tg_o[k]) / cell) - 1;
+            hi[k] = (int32_t)floor((mx - (double)c->tg_o[k]) / cell) + 1;
+            if (lo[k] < 0) lo[k] = 0;
+            if (hi[k] > c->tg_n[k] - 1) hi[k] = c->tg_n[k] - 1;
+        }
+        for (int32_t z = lo[2]; z <= hi[2]; z++)
+            for (int32_t y = lo[1]; y <= hi[1]; y++)
+                for (int32_t x = lo[0]; x <= hi[0]; x++) {
+                    double ctr[3] = {(double)c->tg_o[0] + (x + 0.5) * cell, (double)c->tg_o[1] + (y + 0.5) * cell,
+                                     (double)c->tg_o[2] + (z + 0.5) * cell};
+                    if (!tri_box_overlap(ctr, hs, a, b, cc)) continue;
+                    if (np == cap) {
+                        cap *= 2;
+                        P = realloc(P, sizeof(or_pair) * cap);
+                    }
+                    P[np].key = (int64_t)x + (int64_t)c->tg_n[0] * ((int64_t)y + (int64_t)c->tg_n[1] * z);
+                    P[np].tri = (int32_t)t;
+                    np++;
+                }
+    }
+    qsort(P, (size_t)np, sizeof(or_pair), pair_cmp);
+    c->npairs = np;
+    c->pair_key = malloc(sizeof(int64_t) * (np ? np : 1));
+    c->pair_tri = malloc(sizeof(int32_t) * (np ? np : 1));
+    for (int64_t i = 0; i < np; i++) {
+        c->pair_key[i] = P[i].key;
+        c->pair_tri[i] = P[i].tri;
+    }
+    free(P);
+}
+
+static int64_t lower_bound_i64(const int64_t *a, int64_t n, int64_t key)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------------------------ */
+/* context                                                                  */
+/* ------------------------------------------------------------------------ */
+or_ctx *oracle_create(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, float dx, float h)
+{
+    if (nv <= 0 || nt <= 0 || !(dx > 0) || !(h > 0)) return NULL;
+    for (int64_t i = 0; i < 3 * nt; i++)
+        if (tris[i] < 0 || tris[i] >= nv) return NULL;
+    or_ctx *c = calloc(1, sizeof(or_ctx));
+    c->nv = nv;
+    c->nt = nt;
+    c->dx = dx;
+    c->h = h;
+    c->V = malloc(sizeof(double) * 3 * nv);
+    c->Vf = malloc(sizeof(float) * 3 * nv);
+    c->T = malloc(sizeof(int32_t) * 3 * nt);
+    memcpy(c->Vf, verts, sizeof(float) * 3 * nv);
+    memcpy(c->T, tris, sizeof(int32_t) * 3 * nt);
+    float bbmin[3] = {INFINITY, INFINITY, INFINITY}, bbmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nv; i++)
+        for (int k = 0; k < 3; k++) {
+            c->V[3 * i + k] = (double)verts[3 * i + k];
+            bbmin[k] = fminf(bbmin[k], verts[3 * i + k]);
+            bbmax[k] = fmaxf(bbmax[k], verts[3 * i + k]);
+        }
+    mesh_prepare(c);
+    grid_setup(bbmin, bbmax, dx, 2, c->tg_o, &c->tg_inv, c->tg_n);
+    bin_triangles(c);
+    float R = 2.0f * h;
+    c->R2 = (float)((double)R * (double)R);
+    c->ng_cell = (float)((double)R * (1.0 + 1.0 / 256.0));
+    grid_setup(bbmin, bbmax, c->ng_cell, 1, c->ng_o, &c->ng_inv, c->ng_n);
+    c->feat_deg = -1.0;
+    return c;
+}
+
+static void free_features(or_ctx *c)
+{
+    free(c->fe);
+    free(c->sing);
+    free(c->line_first);
+    free(c->line_nseg);
+    free(c->line_closed);
+    free(c->seg_v);
+    free(c->seg_line);
+    c->fe = c->sing = c->line_closed = c->seg_v = c->seg_line = NULL;
+    c->line_first = c->line_nseg = NULL;
+    c->nfe = c->nsing = c->nlines = c->nseg = 0;
+}
+
+void oracle_destroy(or_ctx *c)
+{
+    if (!c) return;
+    free(c->V);
+    free(c->Vf);
+    free(c->T);
+    free(c->Nrm);
+    free(c->Nu);
+    free(c->Nuf);
+    free(c->EPf);
+    free(c->VPf);
+    free(c->pair_key);
+    free(c->pair_tri);
+    free_features(c);
+    free(c->X);
+    free(c->cls);
+    free(c->cons);
+    free(c);
+}
+
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int oracle_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_fixed_features(or_ctx *c, int fixed) { c->fixed_features = fixed; }
+
+void oracle_tri_grid(const or_ctx *c, float *o, float *inv, int32_t *n)
+{
+    for (int k = 0; k < 3; k++) {
+        o[k] = c->tg_o[k];
+        n[k] = c->tg_n[k];
+    }
+    *inv = c->tg_inv;
+}
+
+void oracle_nbr_grid(const or_ctx *c, float *o, float *inv, float *cell, int32_t *n, float *R2)
+{
+    for (int k = 0; k < 3; k++) {
+        o[k] = c->ng_o[k];
+        n[k] = c->ng_n[k];
+    }
+    *inv = c->ng_inv;
+    *cell = c->ng_cell;
+    *R2 = c->R2;
+}
+
+/* C_compact content: sorted (cell key, triangle) pairs.  Returns the count;
+ * copies at most cap pairs. */
+int64_t oracle_tri_bins(const or_ctx *c, int64_t *keys, int32_t *tris, int64_t cap)
+{
+    for (int64_t i = 0; i < c->npairs && i < cap; i++) {
+        keys[i] = c->pair_key[i];
+        tris[i] = c->pair_tri[i];
+    }
+    return c->npairs;
+}
+
+void oracle_pseudonormals(const or_ctx *c, float *face, float *edge, float *vert)
+{
+    if (face) memcpy(face, c->Nuf, sizeof(float) * 3 * c->nt);
+    if (edge) memcpy(edge, c->EPf, sizeof(float) * 9 * c->nt);
+    if (vert) memcpy(vert, c->VPf, sizeof(float) * 3 * c->nv);
+}
+
+/* ------------------------------------------------------------------------ */
+/* features (Sec. 3.2.2)                                                     */
+/* ------------------------------------------------------------------------ */
+static int32_t other_end(const int32_t *fe, int64_t e, int32_t v) { return fe[2 * e] == v ? fe[2 * e + 1] : fe[2 * e]; }
+
+int64_t oracle_extract_features(or_ctx *c, double dihedral_deg)
+{
+    free_features(c);
+    c->feat_deg = dihedral_deg;
+    double cthr = cos(dihedral_deg * M_PI / 180.0);
+    or_edge *E = edge_face_map(c);
+    int64_t m = 3 * c->nt, nfe = 0;
+    int32_t *fe = malloc(sizeof(int32_t) * 2 * (m ? m : 1));
+    for (int64_t s = 0; s < m;) {
+        int64_t e = s;
+        while (e < m && E[e].v1 == E[s].v1 && E[e].v2 == E[s].v2) e++;
+        int feature;
+        if (e - s != 2) {
+            feature = 1; /* boundary or non-manifold edge */
+        } else {
+            /* angle between the two face normals above the threshold */
+            double d = dot3(c->Nu + 3 * E[s].tri, c->Nu + 3 * E[s + 1].tri);
+            feature = d < cthr;
+        }
+        if (feature) {
+            fe[2 * nfe] = E[s].v1;
+            fe[2 * nfe + 1] = E[s].v2;
+            nfe++;
+        }
+        s = e;
+    }
+    free(E);
+    c->nfe = nfe;
+    c->fe = fe;
+    /* vertex degrees and incidence lists (edges in ascending id) */
+    int32_t *deg = calloc((size_t)c->nv, sizeof(int32_t));
+    for (int64_t e = 0; e < nfe; e++) {
+        deg[fe[2 * e]]++;
+        deg[fe[2 * e + 1]]++;
+    }
+    int64_t *start = malloc(sizeof(int64_t) * (c->nv + 1));
+    start[0] = 0;
+    for (int64_t v = 0; v < c->nv; v++) start[v + 1] = start[v] + deg[v];
+    int64_t *fill = malloc(sizeof(int64_t) * (c->nv ? c->nv : 1));
+    for (int64_t v = 0; v < c->nv; v++) fill[v] = start[v];
+    int64_t *inc = malloc(sizeof(int64_t) * (2 * nfe + 1));
+    for (int64_t e = 0; e < nfe; e++) {
+        inc[fill[fe[2 * e]]++] = e;
+        inc[fill[fe[2 * e + 1]]++] = e;
+    }
+    /* singular points: feature degree 1 or above 2 */
+    c->sing = malloc(sizeof(int32_t) * (c->nv ? c->nv : 1));
+    c->nsing = 0;
+    for (int64_t v = 0; v < c->nv; v++)
+        if (deg[v] == 1 || deg[v] > 2) c->sing[c->nsing++] = (int32_t)v;
+    /* feature lines: walks from singular points, then loops; colouring */
+    char *col = calloc((size_t)nfe + 1, 1);
+    int64_t lcap = 16, scap = 64;
+    c->line_first = malloc(sizeof(int64_t) * lcap);
+    c->line_nseg = malloc(sizeof(int64_t) * lcap);
+    c->line_closed = malloc(sizeof(int32_t) * lcap);
+    c->seg_v = malloc(sizeof(int32_t) * 2 * scap);
+    c->seg_line = malloc(sizeof(int32_t) * scap);
+#define PUSH_SEG(a, b)                                                  \
+    do {                                                                \
+        if (c->nseg == scap) {                                          \
+            scap *= 2;                                                  \
+            c->seg_v = realloc(c->seg_v, sizeof(int32_t) * 2 * scap);   \
+            c->seg_line = realloc(c->seg_line, sizeof(int32_t) * scap); \
+        }                                                               \
+        c->seg_v[2 * c->nseg] = (a);                                    \
+        c->seg_v[2 * c->nseg + 1] = (b);                                \
+        c->seg_line[c->nseg] = (int32_t)c->nlines;                      \
+        c->nseg++;                                                      \
+    } while (0)
+#define PUSH_LINE(first, closed)                                                  \
+    do {                                                                          \
+        if (c->nlines == lcap) {                                                  \
+            lcap *= 2;                                                            \
+            c->line_first = realloc(c->line_first, sizeof(int64_t) * lcap);       \
+            c->line_nseg = realloc(c->line_nseg, sizeof(int64_t) * lcap);         \
+            c->line_closed = realloc(c->line_closed, sizeof(int32_t) * lcap);     \
+        }                                                                         \
+        c->line_first[c->nlines] = (first);                                       \
+        c->line_nseg[c->nlines] = c->nseg - (first);                              \
+        c->line_closed[c->nlines] = (closed);                                     \
+        c->nlines++;                                                              \
+    } while (0)
+    for (int64_t si = 0; si < c->nsing; si++) {
+        int32_t s = c->sing[si];
+        for (int64_t q = start[s]; q < start[s + 1]; q++) {
+            int64_t e = inc[q];
+            if (col[e]) continue;
+            int64_t first = c->nseg;
+            int32_t cur = s;
+            for (;;) {
+                col[e] = 1;
+                int32_t nxt = other_end(fe, e, cur);
+                PUSH_SEG(cur, nxt);
+                if (deg[nxt] != 2) break;
+                int64_t e2 = inc[start[nxt]] == e ? inc[start[nxt] + 1] : inc[start[nxt]];
+                if (col[e2]) break;
+                e = e2;
+                cur = nxt;
+            }
+            PUSH_LINE(first, 0);
+        }
+    }
+    for (int64_t e0 = 0; e0 < nfe; e0++) {
+        if (col[e0]) continue;
+        int64_t first = c->nseg, e = e0;
+        int32_t v0 = fe[2 * e0], cur = v0;
+        int closed = 0;
+        for (;;) {
+            col[e] = 1;
+            int32_t nxt = other_end(fe, e, cur);
+            PUSH_SEG(cur, nxt);
+            if (nxt == v0) {
+                closed = 1;
+                break;
+            }
+            int64_t e2 = inc[start[nxt]] == e ? inc[start[nxt] + 1] : inc[start[nxt]];
+            if (col[e2]) break;
+            e = e2;
+            cur = nxt;
+        }
+        PUSH_LINE(first, closed);
+    }
+#undef PUSH_SEG
+#undef PUSH_LINE
+    free(col);
+    free(inc);
+    free(fill);
+    free(start);
+    free(deg);
+    return nfe;
+}
+
+int64_t oracle_feature_edges(const or_ctx *c, int32_t *out, int64_t cap)
+{
+    for (int64_t i = 0; i < c->nfe && i < cap; i++) {
+        out[2 * i] = c->fe[2 * i];
+        out[2 * i + 1] = c->fe[2 * i + 1];
+    }
+    return c->nfe;
+}
+
+int64_t oracle_singular_points(const or_ctx *c, int32_t *out, int64_t cap)
+{
+    for (int64_t i = 0; i < c->nsing && i < cap; i++) out[i] = c->sing[i];
+    return c->nsing;
+}
+
+/* Lines as (first segment, segment count, closed) triples; segments as
+ * vertex pairs.  Returns the number of lines. */
+int64_t oracle_feature_lines(const or_ctx *c, int64_t *first, int64_t *nseg, int32_t *closed, int32_t *seg_v,
+                             int64_t *nseg_total)
+{
+    for (int64_t l = 0; l < c->nlines; l++) {
+        if (first) first[l] = c->line_first[l];
+        if (nseg) nseg[l] = c->line_nseg[l];
+        if (closed) closed[l] = c->line_closed[l];
+    }
+    if (seg_v) memcpy(seg_v, c->seg_v, sizeof(int32_t) * 2 * c->nseg);
+    if (nseg_total) *nseg_total = c->nseg;
+    return c->nlines;
+}
+
+static double seg_len(const or_ctx *c, int64_t s)
+{
+    double d[3];
+    sub3(c->V + 3 * c->seg_v[2 * s + 1], c->V + 3 * c->seg_v[2 * s], d);
+    return sqrt(dot3(d, d));
+}
+
+/* Feature particles: along each line n = ceil(L / dx) equal pieces of
+ * length L / n (slightly below dx); open lines carry both end points, which
+ * are singular points (class P, emitted once each); loops carry n points.
+ * Writes up to cap points; returns the total count. */
+int64_t oracle_feature_particles(const or_ctx *c, double dx, double *xyz, int32_t *cls, int64_t cap)
+{
+    int64_t cnt = 0;
+    char *done = calloc((size_t)c->nv, 1);
+#define EMIT(px, py, pz, cl)             \
+    do {                                 \
+        if (cnt < cap) {                 \
+            xyz[3 * cnt] = (px);         \
+            xyz[3 * cnt + 1] = (py);     \
+            xyz[3 * cnt + 2] = (pz);     \
+            cls[cnt] = (cl);             \
+        }                                \
+        cnt++;                           \
+    } while (0)
+    for (int64_t l = 0; l < c->nlines; l++) {
+        int64_t f = c->line_first[l], ns = c->line_nseg[l];
+        double L = 0.0;
+        for (int64_t s = f; s < f + ns; s++) L += seg_len(c, s);
+        int64_t npc = (int64_t)ceil(L / dx);
+        if (npc < 1) npc = 1;
+        double sp = L / (double)npc;
+        int closed = c->line_closed[l];
+        if (!closed) {
+            int32_t va = c->seg_v[2 * f], vb = c->seg_v[2 * (f + ns - 1) + 1];
+            if (!done[va]) {
+                done[va] = 1;
+                EMIT(c->V[3 * va], c->V[3 * va + 1], c->V[3 * va + 2], OR_P);
+            }
+            if (!done[vb]) {
+                done[vb] = 1;
+                EMIT(c->V[3 * vb], c->V[3 * vb + 1], c->V[3 * vb + 2], OR_P);
+            }
+        }
+        int64_t k0 = closed ? 0 : 1, k1 = closed ? npc - 1 : npc - 1;
+        int64_t s = f;
+        double cum = 0.0;
+        for (int64_t k = k0; k <= k1; k++) {
+            double target = sp * (double)k;
+            while (s < f + ns - 1 && cum + seg_len(c, s) <= target) {
+                cum += seg_len(c, s);
+                s++;
+            }
+            double len = seg_len(c, s), t = len > 0 ? (target - cum) / len : 0.0;
+            const double *a = c->V + 3 * c->seg_v[2 * s], *b = c->V + 3 * c->seg_v[2 * s + 1];
+            EMIT(a[0] + t * (b[0] - a[0]), a[1] + t * (b[1] - a[1]), a[2] + t * (b[2] - a[2]), OR_F);
+        }
+    }
+#undef EMIT
+    free(done);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* particles                                                                */
+/* ------------------------------------------------------------------------ */
+int oracle_set_particles(or_ctx *c, const float *xyz, const int32_t *cls, int64_t n)
+{
+    for (int64_t i = 0; i < n; i++)
+        if (cls[i] < 0 || cls[i] > 4) return -1;
+    free(c->X);
+    free(c->cls);
+    free(c->cons);
+    c->n = n;
+    c->X = malloc(sizeof(double) * 3 * (n ? n : 1));
+    c->cls = malloc(sizeof(int32_t) * (n ? n : 1));
+    c->cons = malloc(sizeof(int32_t) * (n ? n : 1));
+    for (int64_t i = 0; i < n; i++) {
+        for (int k = 0; k < 3; k++) c->X[3 * i + k] = (double)xyz[3 * i + k];
+        c->cls[i] = cls[i];
+        c->cons[i] = -1;
+    }
+    c->last_maxdisp = 0.0;
+    return 0;
+}
+
+/* Overwrite positions (FP64) and constraint ids, e.g. to start the oracle
+ * from a given state. */
+void oracle_set_state(or_ctx *c, const double *xyz, const int32_t *cons)
+{
+    if (xyz) memcpy(c->X, xyz, sizeof(double) * 3 * c->n);
+    if (cons) memcpy(c->cons, cons, sizeof(int32_t) * c->n);
+}
+
+void oracle_get_particles(const or_ctx *c, double *xyz, int32_t *cls, int32_t *cons)
+{
+    if (xyz) memcpy(xyz, c->X, sizeof(double) * 3 * c->n);
+    if (cls) memcpy(cls, c->cls, sizeof(int32_t) * c->n);
+    if (cons) memcpy(cons, c->cons, sizeof(int32_t) * c->n);
+}
+
+static int is_mobile(const or_ctx *c, int32_t cl)
+{
+    if (cl == OR_S || cl == OR_V) return 1;
+    if (cl == OR_F) return !c->fixed_features;
+    return 0;
+}
+
+/* does a particle of class cj act on one of class ci (interaction rules of
+ * Sec. 3.3.3 and Sec. 3.3.4) */
+static int acts_on(int32_t ci, int32_t cj)
+{
+    switch (ci) {
+    case OR_S: return cj == OR_S || cj == OR_F || cj == OR_P;
+    case OR_V: return 1;
+    case OR_F: return cj == OR_F || cj == OR_P;
+    default: return 0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* neighbour grid: keys, stable sort, cell ranges (Sec. 3.1.3)               */
+/* ------------------------------------------------------------------------ */
+static void cell_of(const or_ctx *c, const double *x, int32_t *ci)
+{
+    for (int k = 0; k < 3; k++) ci[k] = cell_coord((float)x[k], c->ng_o[k], c->ng_inv, c->ng_n[k]);
+}
+
+static uint32_t key_of(const or_ctx *c, const int32_t *ci)
+{
+    return (uint32_t)ci[0] + (uint32_t)c->ng_n[0] * ((uint32_t)ci[1] + (uint32_t)c->ng_n[1] * (uint32_t)ci[2]);
+}
+
+static int kv_cmp(const void *pa, const void *pb)
+{
+    const or_kv *a = pa, *b = pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->id < b->id ? -1 : (a->id > b->id);
+}
+
+/* sorted (key, id) list for positions X; ties by id = a stable sort of the
+ * id-ordered keys */
+static or_kv *build_cells(const or_ctx *c, const double *X, int64_t n)
+{
+    or_kv *L = malloc(sizeof(or_kv) * (n ? n : 1));
+    for (int64_t i = 0; i < n; i++) {
+        int32_t ci[3];
+        cell_of(c, X + 3 * i, ci);
+        L[i].key = key_of(c, ci);
+        L[i].id = (uint32_t)i;
+    }
+    qsort(L, (size_t)n, sizeof(or_kv), kv_cmp);
+    return L;
+}
+
+static int64_t lower_bound_kv(const or_kv *L, int64_t n, uint32_t key)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (L[mid].key < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+/* Keys of the current state in id order and the permutation that sorts them
+ * stably (perm[k] = id of the k-th particle in key order). */
+void oracle_keys(const or_ctx *c, uint32_t *key, uint32_t *perm)
+{
+    or_kv *L = build_cells(c, c->X, c->n);
+    for (int64_t k = 0; k < c->n; k++) {
+        key[L[k].id] = L[k].key;
+        perm[k] = L[k].id;
+    }
+    free(L);
+}
+
+/* Occupied cells with their [start, end) ranges in sorted order (C_compact
+ * begin / length). Returns the count. */
+int64_t oracle_cell_ranges(const or_ctx *c, uint32_t *cell, uint32_t *start, uint32_t *end, int64_t cap)
+{
+    or_kv *L = build_cells(c, c->X, c->n);
+    int64_t m = 0;
+    for (int64_t k = 0; k < c->n;) {
+        int64_t e = k;
+        while (e < c->n && L[e].key == L[k].key) e++;
+        if (m < cap) {
+            cell[m] = L[k].key;
+            start[m] = (uint32_t)k;
+            end[m] = (uint32_t)e;
+        }
+        m++;
+        k = e;
+    }
+    free(L);
+    return m;
+}
+
+/* FP32 neighbour test: r^2 = (dx dx + dy dy) + dz dz < (2h)^2 */
+static int within(const or_ctx *c, const double *xi, const double *xj)
+{
+    float dx = (float)xi[0] - (float)xj[0];
+    float dy = (float)xi[1] - (float)xj[1];
+    float dz = (float)xi[2] - (float)xj[2];
+    float r2 = dx * dx + dy * dy;
+    r2 = r2 + dz * dz;
+    return r2 < c->R2;
+}
+
+typedef void (*pair_fn)(void *user, int64_t i, int64_t j);
+
+/* visit the neighbours j of particle i (27 cells, FP32 test, class mask
+ * unless unmasked) in stencil order */
+static void for_neighbours(const or_ctx *c, const double *X, const int32_t *cls, const or_kv *L, int64_t n,
+                           int64_t i, int masked, pair_fn fn, void *user)
+{
+    int32_t ci[3];
+    cell_of(c, X + 3 * i, ci);
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int32_t cc[3] = {ci[0] + dx, ci[1] + dy, ci[2] + dz};
+                if (cc[0] < 0 || cc[1] < 0 || cc[2] < 0 || cc[0] >= c->ng_n[0] || cc[1] >= c->ng_n[1] ||
+                    cc[2] >= c->ng_n[2])
+                    continue;
+                uint32_t key = key_of(c, cc);
+                for (int64_t k = lower_bound_kv(L, n, key); k < n && L[k].key == key; k++) {
+                    int64_t j = L[k].id;
+                    if (j == i) continue;
+                    if (masked && !acts_on(cls[i], cls[j])) continue;
+                    if (!within(c, X + 3 * i, X + 3 * j)) continue;
+                    fn(user, i, j);
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* pressure force, Eq. 15 with K = 1                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const or_ctx *c;
+    const double *X;
+    double a[3];
+    int64_t cnt;
+} force_acc;
+
+static void force_pair(void *user, int64_t i, int64_t j)
+{
+    force_acc *fa = user;
+    double d[3];
+    sub3(fa->X + 3 * i, fa->X + 3 * j, d);
+    double r = sqrt(dot3(d, d));
+    fa->cnt++;
+    if (r > 0.0) {
+        double w = oracle_dW(r, (double)fa->c->h);
+        for (int k = 0; k < 3; k++) fa->a[k] -= w * d[k] / r;   /* -dW/dr e_ij */
+    }
+}
+
+/* acc [n*3] and the masked neighbour count of every particle; fixed
+ * particles get zero acceleration but still report their count.  Returns
+ * amax over mobile particles. */
+static double compute_forces(const or_ctx *c, const double *X, double *acc, int32_t *count)
+{
+    or_kv *L = build_cells(c, X, c->n);
+    double amax = 0.0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(max : amax)
+    for (int64_t i = 0; i < c->n; i++) {
+        force_acc fa = {c, X, {0, 0, 0}, 0};
+        for_neighbours(c, X, c->cls, L, c->n, i, 1, force_pair, &fa);
+        int mob = is_mobile(c, c->cls[i]);
+        for (int k = 0; k < 3; k++) acc[3 * i + k] = mob ? fa.a[k] : 0.0;
+        if (count) count[i] = (int32_t)fa.cnt;
+        if (mob) {
+            double m = sqrt(dot3(fa.a, fa.a));
+            if (m > amax) amax = m;
+        }
+    }
+    free(L);
+    return amax;
+}
+
+double oracle_forces(const or_ctx *c, double *acc, int32_t *count)
+{
+    return compute_forces(c, c->X, acc, count);
+}
+
+/* brute-force O(N^2) masked neighbour counts (validator) */
+void oracle_brute_neighbours(const or_ctx *c, int32_t *count)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < c->n; i++) {
+        int32_t m = 0;
+        for (int64_t j = 0; j < c->n; j++) {
+            if (j == i || !acts_on(c->cls[i], c->cls[j])) continue;
+            if (within(c, c->X + 3 * i, c->X + 3 * j)) m++;
+        }
+        count[i] = m;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* projection (Sec. 3.2.1, 3.3.3, 3.3.4)                                     */
+/* ------------------------------------------------------------------------ */
+static void tri_cell_of(const or_ctx *c, const float *yf, int32_t *ci)
+{
+    for (int k = 0; k < 3; k++) ci[k] = cell_coord(yf[k], c->tg_o[k], c->tg_inv, c->tg_n[k]);
+}
+
+/* z-component of the cross product of edge (p -> q) and (p -> f), measured
+ * along n: non-negative when f is on the inner side of the edge (Fig. 8) */
+static float edge_side(const float *p, const float *q, const float *f, const float *n)
+{
+    float e[3], w[3], cr[3];
+    subf(q, p, e);
+    subf(f, p, w);
+    crossf(e, w, cr);
+    return dotf(cr, n);
+}
+
+/* FP32 decision for one triangle: is the orthogonal foot of y inside, and
+ * at what distance. */
+static int surface_candidate(const or_ctx *c, int64_t t, const float *y, float *dist)
+{
+    const float *a = c->Vf + 3 * c->T[3 * t], *b = c->Vf + 3 * c->T[3 * t + 1], *cc = c->Vf + 3 * c->T[3 * t + 2];
+    const float *n = c->Nuf + 3 * t;
+    float ya[3], f[3];
+    subf(y, a, ya);
+    float d = dotf(ya, n);
+    for (int k = 0; k < 3; k++) f[k] = y[k] - d * n[k];
+    if (edge_side(a, b, f, n) < 0.0f) return 0;
+    if (edge_side(b, cc, f, n) < 0.0f) return 0;
+    if (edge_side(cc, a, f, n) < 0.0f) return 0;
+    *dist = fabsf(d);
+    return 1;
+}
+
+/* foot of y on the plane of triangle t, FP64 */
+static void plane_foot(const or_ctx *c, int64_t t, const double *y, double *x)
+{
+    const double *a = c->V + 3 * c->T[3 * t], *n = c->Nu + 3 * t;
+    double ya[3];
+    sub3(y, a, ya);
+    double s = dot3(ya, n);
+    for (int k = 0; k < 3; k++) x[k] = y[k] - s * n[k];
+}
+
+/* Closest projectable triangle among those binned into the 3x3x3 cells
+ * around y: smallest |plane distance|, ties to the lower triangle index.
+ * Returns the triangle or -1 when none is projectable. */
+static int64_t choose_surface_triangle(const or_ctx *c, const double *y)
+{
+    float yf[3] = {(float)y[0], (float)y[1], (float)y[2]};
+    int32_t ci[3];
+    tri_cell_of(c, yf, ci);
+    float best = INFINITY;
+    int64_t bt = -1;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int32_t cc[3] = {ci[0] + dx, ci[1] + dy, ci[2] + dz};
+                if (cc[0] < 0 || cc[1] < 0 || cc[2] < 0 || cc[0] >= c->tg_n[0] || cc[1] >= c->tg_n[1] ||
+                    cc[2] >= c->tg_n[2])
+                    continue;
+                int64_t key = (int64_t)cc[0] + (int64_t)c->tg_n[0] * ((int64_t)cc[1] + (int64_t)c->tg_n[1] * cc[2]);
+                for (int64_t p = lower_bound_i64(c->pair_key, c->npairs, key); p < c->npairs && c->pair_key[p] == key;
+                     p++) {
+                    int64_t t = c->pair_tri[p];
+                    float d;
+                    if (!surface_candidate(c, t, yf, &d)) continue;
+                    if (d < best || (d == best && t < bt)) {
+                        best = d;
+                        bt = t;
+                    }
+                }
+            }
+    return bt;
+}
+
+/* FP32 closest point on triangle t to y; region 0 = face, 1 + k = edge k,
+ * 4 + k = vertex k.  Returns the squared distance. */
+static float closest_on_triangle(const or_ctx *c, int64_t t, const float *y, float *cp, int *region)
+{
+    const float *v[3] = {c->Vf + 3 * c->T[3 * t], c->Vf + 3 * c->T[3 * t + 1], c->Vf + 3 * c->T[3 * t + 2]};
+    const float *n = c->Nuf + 3 * t;
+    float ya[3], f[3];
+    subf(y, v[0], ya);
+    float d = dotf(ya, n);
+    for (int k = 0; k < 3; k++) f[k] = y[k] - d * n[k];
+    if (edge_side(v[0], v[1], f, n) >= 0.0f && edge_side(v[1], v[2], f, n) >= 0.0f &&
+        edge_side(v[2], v[0], f, n) >= 0.0f) {
+        memcpy(cp, f, sizeof(float) * 3);
+        *region = 0;
+        float w[3];
+        subf(y, f, w);
+        return dotf(w, w);
+    }
+    float best = INFINITY;
+    for (int k = 0; k < 3; k++) {
+        const float *p = v[k], *q = v[(k + 1) % 3];
+        float e[3], w[3];
+        subf(q, p, e);
+        subf(y, p, w);
+        float ee = dotf(e, e);
+        float s = ee > 0.0f ? dotf(w, e) / ee : 0.0f;
+        if (s < 0.0f) s = 0.0f;
+        if (s > 1.0f) s = 1.0f;
+        float pt[3] = {p[0] + s * e[0], p[1] + s * e[1], p[2] + s * e[2]}, u[3];
+        subf(y, pt, u);
+        float dd = dotf(u, u);
+        if (dd < best) {
+            best = dd;
+            memcpy(cp, pt, sizeof(float) * 3);
+            *region = s <= 0.0f ? 4 + k : (s >= 1.0f ? 4 + (k + 1) % 3 : 1 + k);
+        }
+    }
+    return best;
+}
+
+/* Inside test of a volume particle: closest triangle among the 27 cells
+ * (smallest distance, ties to the lower index) and the sign of (y - c) . psi
+ * with psi the pseudonormal of the closest feature.  Returns 1 inside (or no
+ * triangle near), 0 outside. */
+static int volume_inside_f(const or_ctx *c, const float *yf)
+{
+    int32_t ci[3];
+    tri_cell_of(c, yf, ci);
+    float best = INFINITY, bcp[3] = {0, 0, 0};
+    int64_t bt = -1;
+    int breg = 0;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                int32_t cc[3] = {ci[0] + dx, ci[1] + dy, ci[2] + dz};
+                if (cc[0] < 0 || cc[1] < 0 || cc[2] < 0 || cc[0] >= c->tg_n[0] || cc[1] >= c->tg_n[1] ||
+                    cc[2] >= c->tg_n[2])
+                    continue;
+                int64_t key = (int64_t)cc[0] + (int64_t)c->tg_n[0] * ((int64_t)cc[1] + (int64_t)c->tg_n[1] * cc[2]);
+                for (int64_t p = lower_bound_i64(c->pair_key, c->npairs, key); p < c->npairs && c->pair_key[p] == key;
+                     p++) {
+                    int64_t t = c->pair_tri[p];
+                    float cp[3];
+                    int reg;
+                    float dd = closest_on_triangle(c, t, yf, cp, &reg);
+                    if (dd < best || (dd == best && t < bt)) {
+                        best = dd;
+                        bt = t;
+                        breg = reg;
+                        memcpy(bcp, cp, sizeof(bcp));
+                    }
+                }
+            }
+    if (bt < 0) return 1;
+    const float *psi;
+    if (breg == 0) psi = c->Nuf + 3 * bt;
+    else if (breg <= 3) psi = c->EPf + 9 * bt + 3 * (breg - 1);
+    else psi = c->VPf + 3 * c->T[3 * bt + (breg - 4)];
+    float w[3];
+    subf(yf, bcp, w);
+    return dotf(w, psi) <= 0.0f;
+}
+
+/* closest point on the own feature line (all lines when cons < 0): FP32
+ * choice of the segment (smallest squared distance, ties to the lower
+ * segment), FP64 point.  Returns the segment or -1. */
+static int64_t project_feature(const or_ctx *c, const double *y, int32_t cons, double *x)
+{
+    if (c->nseg == 0) return -1;
+    int64_t s0 = 0, s1 = c->nseg;
+    if (cons >= 0 && cons < c->nseg) {
+        int32_t l = c->seg_line[cons];
+        s0 = c->line_first[l];
+        s1 = s0 + c->line_nseg[l];
+    }
+    float yf[3] = {(float)y[0], (float)y[1], (float)y[2]};
+    float best = INFINITY;
+    int64_t bs = -1;
+    for (int64_t s = s0; s < s1; s++) {
+        const float *a = c->Vf + 3 * c->seg_v[2 * s], *b = c->Vf + 3 * c->seg_v[2 * s + 1];
+        float e[3], w[3];
+        subf(b, a, e);
+        subf(yf, a, w);
+        float ee = dotf(e, e);
+        float t = ee > 0.0f ? dotf(w, e) / ee : 0.0f;
+        if (t < 0.0f) t = 0.0f;
+        if (t > 1.0f) t = 1.0f;
+        float q[3] = {a[0] + t * e[0], a[1] + t * e[1], a[2] + t * e[2]}, u[3];
+        subf(yf, q, u);
+        float dd = dotf(u, u);
+        if (dd < best) {
+            best = dd;
+            bs = s;
+        }
+    }
+    const double *a = c->V + 3 * c->seg_v[2 * bs], *b = c->V + 3 * c->seg_v[2 * bs + 1];
+    double e[3], w[3];
+    sub3(b, a, e);
+    sub3(y, a, w);
+    double ee = dot3(e, e);
+    double t = ee > 0.0 ? dot3(w, e) / ee : 0.0;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    for (int k = 0; k < 3; k++) x[k] = a[k] + t * e[k];
+    return bs;
+}
+
+/* Project one trial point according to its class.  Writes the new position
+ * and constraint; returns 1 on success, 0 when the particle must revert. */
+static int project_point(const or_ctx *c, int32_t cl, const double *y, int32_t cons_in, double *x, int32_t *cons_out)
+{
+    *cons_out = cons_in;
+    if (cl == OR_S) {
+        int64_t t = choose_surface_triangle(c, y);
+        if (t < 0) return 0;
+        plane_foot(c, t, y, x);
+        *cons_out = (int32_t)t;
+        return 1;
+    }
+    if (cl == OR_V) {
+        float yf[3] = {(float)y[0], (float)y[1], (float)y[2]};
+        if (!volume_inside_f(c, yf)) return 0;
+        memcpy(x, y, sizeof(double) * 3);
+        return 1;
+    }
+    if (cl == OR_F) {
+        int64_t s = project_feature(c, y, cons_in, x);
+        if (s < 0) return 0;
+        *cons_out = (int32_t)s;
+        return 1;
+    }
+    memcpy(x, y, sizeof(double) * 3);
+    return 1;
+}
+
+/* Projection of given FP32 points (the standalone form of the constraint
+ * step).  ok[i] = 0 marks "not projectable" (x[i] then equals y[i]). */
+void oracle_project_points(const or_ctx *c, const float *y, const int32_t *cls, const int32_t *cons_in, int64_t n,
+                           double *x, int32_t *cons_out, int32_t *ok)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; i++) {
+        double yd[3] = {(double)y[3 * i], (double)y[3 * i + 1], (double)y[3 * i + 2]};
+        int r = project_point(c, cls[i], yd, cons_in ? cons_in[i] : -1, x + 3 * i, cons_out + i);
+        if (!r) memcpy(x + 3 * i, yd, sizeof(yd));
+        ok[i] = r;
+    }
+}
+
+/* Brute force over all triangles: the closest projectable triangle (same
+ * FP32 decision, no grid).  Validates the binned search. */
+void oracle_brute_surface(const or_ctx *c, const float *y, int64_t n, int32_t *tri, float *dist)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        float best = INFINITY;
+        int64_t bt = -1;
+        for (int64_t t = 0; t < c->nt; t++) {
+            float d;
+            if (!surface_candidate(c, t, y + 3 * i, &d)) continue;
+            if (d < best || (d == best && t < bt)) {
+                best = d;
+                bt = t;
+            }
+        }
+        tri[i] = (int32_t)bt;
+        dist[i] = best;
+    }
+}
+
+/* Pseudonormal inside test on given points (1 inside or far, 0 outside). */
+void oracle_volume_inside(const or_ctx *c, const float *y, int64_t n, int32_t *inside)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; i++) inside[i] = volume_inside_f(c, y + 3 * i);
+}
+
+/* Ray parity of Fig. 6: count crossings of the +z ray from p with the
+ * triangles (FP64, half-open edge rule).  1 = inside. */
+void oracle_ray_parity(const or_ctx *c, const double *p, int64_t n, int32_t *inside)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        const double *q = p + 3 * i;
+        int64_t cross = 0;
+        for (int64_t t = 0; t < c->nt; t++) {
+            const double *a = c->V + 3 * c->T[3 * t], *b = c->V + 3 * c->T[3 * t + 1], *cc = c->V + 3 * c->T[3 * t + 2];
+            /* 2-D point-in-triangle in the xy plane, barycentric with a
+             * consistent tie rule, then the crossing height */
+            double d = (b[0] - a[0]) * (cc[1] - a[1]) - (cc[0] - a[0]) * (b[1] - a[1]);
+            if (d == 0.0) continue;
+            double l1 = ((b[0] - q[0]) * (cc[1] - q[1]) - (cc[0] - q[0]) * (b[1] - q[1])) / d;
+            double l2 = ((cc[0] - q[0]) * (a[1] - q[1]) - (a[0] - q[0]) * (cc[1] - q[1])) / d;
+            double l3 = 1.0 - l1 - l2;
+            if (l1 < 0 || l2 < 0 || l3 < 0) continue;
+            double z = l1 * a[2] + l2 * b[2] + l3 * cc[2];
+            if (z > q[2]) cross++;
+        }
+        inside[i] = (int32_t)(cross & 1);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* one relaxation iteration (Algorithm 1, Eqs. 22-25, Sec. 3.3.3-3.3.4)      */
+/* ------------------------------------------------------------------------ */
+/* Apply the step to every mobile particle from accelerations acc and the
+ * body's amax: dt = 0.25 sqrt(h / amax); v_{n+1} = 0 + a dt (velocity
+ * reset); dr = v_{n+1} dt (Eq. 23); tangential part only for surface
+ * (triangle normal) and feature (segment direction) particles; then the
+ * projection of the trial point, or revert. */
+static void apply_step(or_ctx *c, const double *acc, double amax)
+{
+    double dt = amax > 0.0 ? 0.25 * sqrt((double)c->h / amax) : 0.0;
+    double *Xn = malloc(sizeof(double) * 3 * (c->n ? c->n : 1));
+    int32_t *Cn = malloc(sizeof(int32_t) * (c->n ? c->n : 1));
+    double maxdisp = 0.0;
+    int64_t reverts = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(max : maxdisp) reduction(+ : reverts)
+    for (int64_t i = 0; i < c->n; i++) {
+        const double *x = c->X + 3 * i;
+        int32_t cl = c->cls[i];
+        Cn[i] = c->cons[i];
+        memcpy(Xn + 3 * i, x, sizeof(double) * 3);
+        if (!is_mobile(c, cl)) continue;
+        double v[3], dr[3], y[3];
+        for (int k = 0; k < 3; k++) {
+            v[k] = acc[3 * i + k] * dt;   /* Eq. 22 with v_n = 0 */
+            dr[k] = v[k] * dt;            /* Eq. 23 */
+        }
+        int32_t cs = c->cons[i];
+        if (cl == OR_S && cs >= 0) {      /* Eqs. 24-25: drop the normal part */
+            const double *n = c->Nrm + 3 * cs;
+            double s = dot3(dr, n) / dot3(n, n);
+            for (int k = 0; k < 3; k++) dr[k] -= s * n[k];
+        } else if (cl == OR_F && cs >= 0) { /* along the segment only */
+            double tau[3];
+            sub3(c->V + 3 * c->seg_v[2 * cs + 1], c->V + 3 * c->seg_v[2 * cs], tau);
+            double s = dot3(dr, tau) / dot3(tau, tau);
+            for (int k = 0; k < 3; k++) dr[k] = s * tau[k];
+        }
+        for (int k = 0; k < 3; k++) y[k] = x[k] + dr[k];
+        double xn[3];
+        int32_t cn;
+        if (project_point(c, cl, y, cs, xn, &cn)) {
+            memcpy(Xn + 3 * i, xn, sizeof(xn));
+            Cn[i] = cn;
+        } else {
+            reverts++;
+        }
+        double d[3];
+        sub3(Xn + 3 * i, x, d);
+        double m = sqrt(dot3(d, d));
+        if (m > maxdisp) maxdisp = m;
+    }
+    memcpy(c->X, Xn, sizeof(double) * 3 * c->n);
+    memcpy(c->cons, Cn, sizeof(int32_t) * c->n);
+    free(Xn);
+    free(Cn);
+    c->last_maxdisp = maxdisp;
+    c->last_reverts = reverts;
+}
+
+int oracle_relax(or_ctx *c, int32_t n_iter)
+{
+    double *acc = malloc(sizeof(double) * 3 * (c->n ? c->n : 1));
+    for (int32_t it = 0; it < n_iter; it++) {
+        double amax = compute_forces(c, c->X, acc, NULL);
+        c->last_amax = amax;
+        apply_step(c, acc, amax);
+    }
+    free(acc);
+    return 0;
+}
+
+void oracle_last_iteration(const or_ctx *c, double *amax, double *maxdisp, int64_t *reverts)
+{
+    if (amax) *amax = c->last_amax;
+    if (maxdisp) *maxdisp = c->last_maxdisp;
+    if (reverts) *reverts = c->last_reverts;
+}
+
+/* ------------------------------------------------------------------------ */
+/* uniformity energy and its gradient                                        */
+/* ------------------------------------------------------------------------ */
+/* W0 per class: planar lattice for S, cubic for V, linear for F (3-D kernel
+ * throughout). */
+static double class_w0(const or_ctx *c, int32_t cl)
+{
+    int dim = cl == OR_S ? 2 : (cl == OR_F ? 1 : 3);
+    return oracle_lattice_sum((double)c->dx, (double)c->h, dim);
+}
+
+void oracle_w0(const or_ctx *c, double *w0)
+{
+    for (int cl = 0; cl < 5; cl++) w0[cl] = class_w0(c, cl);
+}
+
+typedef struct {
+    const or_ctx *c;
+    const double *X;
+    double rho;
+} dens_acc;
+
+static void dens_pair(void *user, int64_t i, int64_t j)
+{
+    dens_acc *da = user;
+    double d[3];
+    sub3(da->X + 3 * i, da->X + 3 * j, d);
+    da->rho += oracle_W(sqrt(dot3(d, d)), (double)da->c->h);
+}
+
+/* kernel sum rho_i = W(0) + sum over masked neighbours of W(r_ij) */
+static void densities(const or_ctx *c, const double *X, const or_kv *L, double *rho)
+{
+    double w00 = oracle_W(0.0, (double)c->h);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < c->n; i++) {
+        dens_acc da = {c, X, w00};
+        for_neighbours(c, X, c->cls, L, c->n, i, 1, dens_pair, &da);
+        rho[i] = da.rho;
+    }
+}
+
+void oracle_density(const or_ctx *c, double *rho)
+{
+    or_kv *L = build_cells(c, c->X, c->n);
+    densities(c, c->X, L, rho);
+    free(L);
+}
+
+typedef struct {
+    const or_ctx *c;
+    const double *X;
+    const double *rho;
+    const double *w0;
+    double g[3];
+} grad_acc;
+
+/* pair (k, j) visited without a mask: the term of rho_k (if j acts on k and
+ * k is counted) and the term of rho_j (if k acts on j and j is counted) */
+static void grad_pair(void *user, int64_t k, int64_t j)
+{
+    grad_acc *ga = user;
+    const or_ctx *c = ga->c;
+    double coef = 0.0;
+    int32_t ck = c->cls[k], cj = c->cls[j];
+    if (is_mobile(c, ck) && acts_on(ck, cj)) coef += 2.0 * (ga->rho[k] - ga->w0[ck]);
+    if (is_mobile(c, cj) && acts_on(cj, ck)) coef += 2.0 * (ga->rho[j] - ga->w0[cj]);
+    if (coef == 0.0) return;
+    double d[3];
+    sub3(ga->X + 3 * k, ga->X + 3 * j, d);
+    double r = sqrt(dot3(d, d));
+    if (r <= 0.0) return;
+    double w = oracle_dW(r, (double)c->h);
+    for (int q = 0; q < 3; q++) ga->g[q] += coef * w * d[q] / r;
+}
+
+/* E = sum over mobile i of (rho_i - W0_{class i})^2 at positions X, and
+ * dE/dX [n*3] (nullable). */
+static double energy_at(const or_ctx *c, const double *X, double *gX)
+{
+    or_kv *L = build_cells(c, X, c->n);
+    double *rho = malloc(sizeof(double) * (c->n ? c->n : 1));
+    densities(c, X, L, rho);
+    double w0[5];
+    oracle_w0(c, w0);
+    double E = 0.0;
+    for (int64_t i = 0; i < c->n; i++)
+        if (is_mobile(c, c->cls[i])) {
+            double e = rho[i] - w0[c->cls[i]];
+            E += e * e;
+        }
+    if (gX) {
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t k = 0; k < c->n; k++) {
+            grad_acc ga = {c, X, rho, w0, {0, 0, 0}};
+            for_neighbours(c, X, c->cls, L, c->n, k, 0, grad_pair, &ga);
+            for (int q = 0; q < 3; q++) gX[3 * k + q] = ga.g[q];
+        }
+    }
+    free(rho);
+    free(L);
+    return E;
+}
+
+double oracle_energy(const or_ctx *c, double *grad)
+{
+    return energy_at(c, c->X, grad);
+}
+
+/* Energy through the surface projection.  Surface particles with a
+ * triangle are x = y - ((y - v_a) . n) n with n the unit normal of the
+ * frozen triangle built from verts (the mesh when verts is NULL); every
+ * other particle has x = y.  Returns E and the gradients w.r.t. y [n*3] and
+ * w.r.t. the vertices [nv*3] (both nullable). */
+double oracle_energy_projected(const or_ctx *c, const double *y, const double *verts, double *gy, double *gV)
+{
+    const double *Vv = verts ? verts : c->V;
+    int64_t n = c->n;
+    double *X = malloc(sizeof(double) * 3 * (n ? n : 1));
+    for (int64_t i = 0; i < n; i++) {
+        const double *yi = y + 3 * i;
+        int32_t t = c->cons[i];
+        if (c->cls[i] == OR_S && t >= 0) {
+            const double *a = Vv + 3 * c->T[3 * t], *b = Vv + 3 * c->T[3 * t + 1], *cc = Vv + 3 * c->T[3 * t + 2];
+            double e1[3], e2[3], m[3], ya[3];
+            sub3(b, a, e1);
+            sub3(cc, a, e2);
+            cross3(e1, e2, m);
+            double ml = sqrt(dot3(m, m)), nh[3] = {m[0] / ml, m[1] / ml, m[2] / ml};
+            sub3(yi, a, ya);
+            double s = dot3(ya, nh);
+            for (int k = 0; k < 3; k++) X[3 * i + k] = yi[k] - s * nh[k];
+        } else {
+            memcpy(X + 3 * i, yi, sizeof(double) * 3);
+        }
+    }
+    double *gX = (gy || gV) ? malloc(sizeof(double) * 3 * (n ? n : 1)) : NULL;
+    double E = energy_at(c, X, gX);
+    if (gV) memset(gV, 0, sizeof(double) * 3 * c->nv);
+    if (gX) {
+        for (int64_t i = 0; i < n; i++) {
+            const double *g = gX + 3 * i, *yi = y + 3 * i;
+            int32_t t = c->cons[i];
+            if (!(c->cls[i] == OR_S && t >= 0)) {
+                if (gy) memcpy(gy + 3 * i, g, sizeof(double) * 3);
+                continue;
+            }
+            int32_t ia = c->T[3 * t], ib = c->T[3 * t + 1], ic = c->T[3 * t + 2];
+            const double *a = Vv + 3 * ia, *b = Vv + 3 * ib, *cc = Vv + 3 * ic;
+            double e1[3], e2[3], m[3], ya[3];
+            sub3(b, a, e1);
+            sub3(cc, a, e2);
+            cross3(e1, e2, m);
+            double ml = sqrt(dot3(m, m)), nh[3] = {m[0] / ml, m[1] / ml, m[2] / ml};
+            sub3(yi, a, ya);
+            double s = dot3(ya, nh), gn = dot3(g, nh);
+            /* dx = dy - ds n - s dn with ds = (dy - da) . n + (y - a) . dn */
+            if (gy)
+                for (int k = 0; k < 3; k++) gy[3 * i + k] = g[k] - gn * nh[k];
+            if (gV) {
+                /* u . dn with u = -(gn (y - a) + s g); dn = (I - n n^T) dm / |m| */
+                double u[3], ut[3];
+                for (int k = 0; k < 3; k++) u[k] = -(gn * ya[k] + s * g[k]);
+                double un = dot3(u, nh);
+                for (int k = 0; k < 3; k++) ut[k] = (u[k] - un * nh[k]) / ml;
+                double gb[3], gc[3];
+                cross3(e2, ut, gb); /* d/d e1 of ut . (e1 x e2) */
+                cross3(ut, e1, gc); /* d/d e2 */
+                for (int k = 0; k < 3; k++) {
+                    gV[3 * ib + k] += gb[k];
+                    gV[3 * ic + k] += gc[k];
+                    gV[3 * ia + k] += -gb[k] - gc[k] + gn * nh[k];
+                }
+            }
+        }
+        free(gX);
+    }
+    free(X);
+    return E;
+}
+
+/* Energy-descent relaxation: the same limited step and projection as the
+ * force form, with a = -dE/dx in place of the pressure force. */
+int oracle_relax_energy(or_ctx *c, int32_t n_iter)
+{
+    double *g = malloc(sizeof(double) * 3 * (c->n ? c->n : 1));
+    for (int32_t it = 0; it < n_iter; it++) {
+        energy_at(c, c->X, g);
+        double amax = 0.0;
+        for (int64_t i = 0; i < c->n; i++) {
+            for (int k = 0; k < 3; k++) g[3 * i + k] = is_mobile(c, c->cls[i]) ? -g[3 * i + k] : 0.0;
+            double m = sqrt(dot3(g + 3 * i, g + 3 * i));
+            if (m > amax) amax = m;
+        }
+        c->last_amax = amax;
+        apply_step(c, g, amax);
+    }
+    free(g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* uniformity statistics                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const double *X;
+    double rmin;
+} min_acc;
+
+static void min_pair(void *user, int64_t i, int64_t j)
+{
+    min_acc *ma = user;
+    double d[3];
+    sub3(ma->X + 3 * i, ma->X + 3 * j, d);
+    double r = sqrt(dot3(d, d));
+    if (r < ma->rmin) ma->rmin = r;
+}
+
+/* out[0..2]  mean kernel sum of S, V, F particles
+ * out[3..5]  standard deviation of the kernel sum of S, V, F
+ * out[6]     minimum masked pair distance over mobile particles / dx
+ * out[7]     largest displacement of the last iteration / dx
+ * out[8..10] number of S, V, F particles */
+void oracle_stats(const or_ctx *c, double *out)
+{
+    double *rho = malloc(sizeof(double) * (c->n ? c->n : 1));
+    or_kv *L = build_cells(c, c->X, c->n);
+    densities(c, c->X, L, rho);
+    double s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0}, cnt[3] = {0, 0, 0}, rmin = INFINITY;
+    for (int64_t i = 0; i < c->n; i++) {
+        int32_t cl = c->cls[i];
+        if (cl > OR_F) continue;
+        s1[cl] += rho[i];
+        cnt[cl] += 1.0;
+    }
+    for (int k = 0; k < 3; k++) s1[k] = cnt[k] > 0 ? s1[k] / cnt[k] : 0.0;
+    for (int64_t i = 0; i < c->n; i++) {
+        int32_t cl = c->cls[i];
+        if (cl > OR_F) continue;
+        s2[cl] += (rho[i] - s1[cl]) * (rho[i] - s1[cl]);
+    }
+#pragma omp parallel for schedule(dynamic, 256) reduction(min : rmin)
+    for (int64_t i = 0; i < c->n; i++) {
+        if (!is_mobile(c, c->cls[i])) continue;
+        min_acc ma = {c->X, INFINITY};
+        for_neighbours(c, c->X, c->cls, L, c->n, i, 1, min_pair, &ma);
+        if (ma.rmin < rmin) rmin = ma.rmin;
+    }
+    for (int k = 0; k < 3; k++) {
+        out[k] = s1[k];
+        out[3 + k] = cnt[k] > 0 ? sqrt(s2[k] / cnt[k]) : 0.0;
+        out[8 + k] = cnt[k];
+    }
+    out[6] = rmin / (double)c->dx;
+    out[7] = c->last_maxdisp / (double)c->dx;
+    free(L);
+    free(rho);
+}

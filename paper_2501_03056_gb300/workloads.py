@@ -1,0 +1,398 @@
+"""Seeded synthetic inputs for the FPPG relaxation path.
+
+This module only *makes inputs*: triangle meshes (cube, icosphere, torus,
+cylinder, spur gear) and the initial particle sets that sit on or inside them
+(lattices plus a counter-based jitter).  It holds none of the relaxation
+arithmetic -- no kernel, no force, no projection onto triangles, no feature
+extraction.  Both the CUDA library and the FP64 oracle consume exactly the
+arrays produced here, so the two sides always see identical data.
+
+Particle classes (shared vocabulary of the whole package, Sec. 3.3 and
+Sec. 3.3.4 of the paper):
+
+* ``S`` = 0  surface particle (mapped to the closest projectable triangle)
+* ``V`` = 1  volume particle that relaxes (the "intermediate" layer)
+* ``F`` = 2  feature-line particle (moves along its polyline)
+* ``I`` = 3  innermost volume particle (fixed)
+* ``P`` = 4  singular feature point (fixed)
+
+Jitter is a counter-based stream: splitmix64 (Steele, Lea and Flood, 2014) of
+the 64-bit counter ``seed * 2**32 + 4 * id + axis``; the top 53 bits give a
+uniform number in [0, 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+CLS_S, CLS_V, CLS_F, CLS_I, CLS_P = 0, 1, 2, 3, 4
+CLASS_NAMES = {CLS_S: "S", CLS_V: "V", CLS_F: "F", CLS_I: "I", CLS_P: "P"}
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+# --------------------------------------------------------------------------
+# counter-based random numbers
+# --------------------------------------------------------------------------
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser applied element-wise to uint64 counters."""
+    x = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, ids: np.ndarray, axis: int) -> np.ndarray:
+    """U[0,1) for each particle id on one axis (0, 1, 2), counter-based."""
+    ids = np.asarray(ids, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        ctr = np.uint64(seed) * np.uint64(1 << 32) + ids * np.uint64(4) + np.uint64(axis)
+    z = splitmix64(ctr)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def jitter(seed: int, ids: np.ndarray, axis: int, amp: float) -> np.ndarray:
+    """Uniform offsets in [-amp, amp)."""
+    return (2.0 * uniform01(seed, ids, axis) - 1.0) * amp
+
+
+# --------------------------------------------------------------------------
+# meshes (outward-facing, counter-clockwise seen from outside)
+# --------------------------------------------------------------------------
+def _orient_outward(verts: np.ndarray, tris: np.ndarray, inside_point) -> np.ndarray:
+    """Flip triangles whose winding points towards ``inside_point``."""
+    v = verts.astype(np.float64)
+    a, b, c = v[tris[:, 0]], v[tris[:, 1]], v[tris[:, 2]]
+    nrm = np.cross(b - a, c - a)
+    cen = (a + b + c) / 3.0
+    flip = np.einsum("ij,ij->i", nrm, cen - np.asarray(inside_point, dtype=np.float64)) < 0
+    out = tris.copy()
+    out[flip, 1], out[flip, 2] = tris[flip, 2], tris[flip, 1]
+    return out
+
+
+def cube_mesh(half: float = 0.5):
+    """Axis-aligned cube [-half, half]^3 as 12 triangles."""
+    verts = np.array([[(i & 1) * 2 - 1, ((i >> 1) & 1) * 2 - 1, ((i >> 2) & 1) * 2 - 1]
+                      for i in range(8)], dtype=np.float64) * half
+    tris = []
+    for axis in range(3):
+        for sgn in (0, 1):
+            quad = [i for i in range(8) if ((i >> axis) & 1) == sgn]
+            o1, o2 = [ax for ax in range(3) if ax != axis]
+            # order the four corners around the face
+            ang = [math.atan2(verts[i, o2], verts[i, o1]) for i in quad]
+            quad = [q for _, q in sorted(zip(ang, quad))]
+            tris.append([quad[0], quad[1], quad[2]])
+            tris.append([quad[0], quad[2], quad[3]])
+    tris = np.array(tris, dtype=np.int32)
+    tris = _orient_outward(verts, tris, (0.0, 0.0, 0.0))
+    return verts.astype(np.float32), tris.astype(np.int32)
+
+
+def icosphere_mesh(level: int, radius: float = 1.0):
+    """Icosahedron refined ``level`` times by edge midpoints pushed to the sphere."""
+    phi = (1.0 + 5.0 ** 0.5) / 2.0
+    base = []
+    for s1 in (-1.0, 1.0):
+        for s2 in (-1.0, 1.0):
+            base += [(0.0, s1, s2 * phi), (s1, s2 * phi, 0.0), (s2 * phi, 0.0, s1)]
+    v = np.array(base, dtype=np.float64)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    # faces: triples of mutually adjacent vertices (edge = shortest distance)
+    d = np.linalg.norm(v[:, None, :] - v[None, :, :], axis=2)
+    emin = np.min(d[d > 1e-9])
+    adj = np.abs(d - emin) < 1e-6
+    faces = []
+    for i in range(12):
+        for j in range(i + 1, 12):
+            if not adj[i, j]:
+                continue
+            for k in range(j + 1, 12):
+                if adj[i, k] and adj[j, k]:
+                    faces.append([i, j, k])
+    tris = _orient_outward(v, np.array(faces, dtype=np.int64), (0.0, 0.0, 0.0))
+    verts = [tuple(p) for p in v]
+    for _ in range(level):
+        cache = {}
+
+        def mid(a, b):
+            key = (a, b) if a < b else (b, a)
+            if key not in cache:
+                p = (np.asarray(verts[a]) + np.asarray(verts[b])) * 0.5
+                p /= np.linalg.norm(p)
+                cache[key] = len(verts)
+                verts.append(tuple(p))
+            return cache[key]
+
+        new = []
+        for a, b, c in tris:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            new += [[a, ab, ca], [b, bc, ab], [c, ca, bc], [ab, bc, ca]]
+        tris = np.array(new, dtype=np.int64)
+    verts = np.array(verts, dtype=np.float64) * radius
+    return verts.astype(np.float32), tris.astype(np.int32)
+
+
+def torus_mesh(R: float = 1.0, r: float = 0.3, nu: int = 256, nv: int = 64):
+    """Torus around the z axis from an nu x nv grid of (u, v) quads."""
+    u = 2.0 * np.pi * np.arange(nu) / nu
+    v = 2.0 * np.pi * np.arange(nv) / nv
+    uu, vv = np.meshgrid(u, v, indexing="ij")
+    rho = R + r * np.cos(vv)
+    verts = np.stack([rho * np.cos(uu), rho * np.sin(uu), r * np.sin(vv)], axis=-1).reshape(-1, 3)
+    idx = lambda i, j: (i % nu) * nv + (j % nv)  # noqa: E731
+    tris = []
+    for i in range(nu):
+        for j in range(nv):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            tris += [[a, b, c], [a, c, d]]
+    return verts.astype(np.float32), np.array(tris, dtype=np.int32)
+
+
+def cylinder_mesh(radius: float = 0.5, height: float = 1.0, n: int = 64, nz: int = 8):
+    """Closed cylinder along z with capped ends (fan around the cap centres)."""
+    ang = 2.0 * np.pi * np.arange(n) / n
+    zs = np.linspace(-height / 2, height / 2, nz + 1)
+    verts = [(radius * math.cos(a), radius * math.sin(a), z) for z in zs for a in ang]
+    tris = []
+    for k in range(nz):
+        for i in range(n):
+            a, b = k * n + i, k * n + (i + 1) % n
+            c, d = (k + 1) * n + (i + 1) % n, (k + 1) * n + i
+            tris += [[a, b, c], [a, c, d]]
+    bot = len(verts)
+    verts.append((0.0, 0.0, -height / 2))
+    top = len(verts)
+    verts.append((0.0, 0.0, height / 2))
+    for i in range(n):
+        tris.append([bot, (i + 1) % n, i])
+        tris.append([top, nz * n + i, nz * n + (i + 1) % n])
+    verts = np.array(verts, dtype=np.float64)
+    tris = _orient_outward(verts, np.array(tris, dtype=np.int64), (0.0, 0.0, 0.0))
+    return verts.astype(np.float32), tris.astype(np.int32)
+
+
+def gear_profile(teeth: int = 40, r_out: float = 1.0, r_root: float = 0.9,
+                 pts_per_tooth: int = 4):
+    """Closed 2-D outline of a spur gear with trapezoidal teeth.
+
+    Each tooth pitch is split into root land, rising flank, tip land and
+    falling flank (equal angular quarters); returns (x, y) vertices in
+    counter-clockwise order."""
+    pitch = 2.0 * np.pi / teeth
+    out = []
+    for t in range(teeth):
+        a0 = t * pitch
+        # root land: quarter pitch; flank; tip land; flank
+        for k in range(pts_per_tooth):
+            out.append((r_root, a0 + 0.25 * pitch * k / pts_per_tooth))
+        out.append((r_root, a0 + 0.25 * pitch))
+        for k in range(pts_per_tooth):
+            out.append((r_out, a0 + 0.5 * pitch + 0.25 * pitch * k / pts_per_tooth))
+        out.append((r_out, a0 + 0.75 * pitch))
+    xy = np.array([(r * math.cos(a), r * math.sin(a)) for r, a in out], dtype=np.float64)
+    return xy
+
+
+# --------------------------------------------------------------------------
+# particle sets
+# --------------------------------------------------------------------------
+@dataclass
+class Assembly:
+    """One body: its mesh, spacing and initial particles."""
+    name: str
+    verts: np.ndarray          # float32 [nv, 3]
+    tris: np.ndarray           # int32 [nt, 3]
+    dx: float
+    h: float
+    xyz: np.ndarray            # float32 [n, 3]
+    cls: np.ndarray            # int32 [n]
+    dihedral_deg: float | None = None   # feature threshold; None = no features
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+def smoothing_length(dx: float, factor: float = 1.3) -> float:
+    """h = 1.3 dx rounded to FP32 (the value both sides receive)."""
+    return float(np.float32(factor * dx))
+
+
+def cube_particles(dx: float = 0.05, seed: int = 0, half: float = 0.5):
+    """Face lattices (S), edge points (F), corners (P) and a volume lattice (V).
+
+    S: n x n per face at (k + 1/2) dx with in-plane jitter; F: the n - 1
+    interior edge points at k dx with jitter along the edge; P: the 8 corners;
+    V: the n^3 lattice at (k + 1/2) dx with 3-D jitter; jitter +-0.25 dx."""
+    n = int(round(2 * half / dx))
+    amp = 0.25 * dx
+    xyz, cls = [], []
+    # S
+    k = (np.arange(n) + 0.5) * dx - half
+    g1, g2 = np.meshgrid(k, k, indexing="ij")
+    g1, g2 = g1.ravel(), g2.ravel()
+    for axis in range(3):
+        for sgn in (-1.0, 1.0):
+            o1, o2 = [ax for ax in range(3) if ax != axis]
+            p = np.zeros((g1.size, 3))
+            p[:, axis] = sgn * half
+            p[:, o1] = g1
+            p[:, o2] = g2
+            xyz.append(p)
+            cls.append(np.full(g1.size, CLS_S))
+    # F (interior points of the 12 edges)
+    t = np.arange(1, n) * dx - half
+    for axis in range(3):
+        o1, o2 = [ax for ax in range(3) if ax != axis]
+        for s1 in (-1.0, 1.0):
+            for s2 in (-1.0, 1.0):
+                p = np.zeros((t.size, 3))
+                p[:, axis] = t
+                p[:, o1] = s1 * half
+                p[:, o2] = s2 * half
+                xyz.append(p)
+                cls.append(np.full(t.size, CLS_F))
+    # P (corners)
+    corners = np.array([[(i & 1) * 2 - 1, ((i >> 1) & 1) * 2 - 1, ((i >> 2) & 1) * 2 - 1]
+                        for i in range(8)], dtype=np.float64) * half
+    xyz.append(corners)
+    cls.append(np.full(8, CLS_P))
+    # V
+    gx, gy, gz = np.meshgrid(k, k, k, indexing="ij")
+    xyz.append(np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1))
+    cls.append(np.full(gx.size, CLS_V))
+
+    xyz = np.concatenate(xyz).astype(np.float64)
+    cls = np.concatenate(cls).astype(np.int32)
+    ids = np.arange(xyz.shape[0])
+    jit = np.stack([jitter(seed, ids, a, amp) for a in range(3)], axis=1)
+    # S: in-plane jitter only; F: along-edge jitter only; P: none; V: 3-D.
+    on_face = np.abs(np.abs(xyz) - half) < 1e-12
+    mask = np.ones_like(xyz)
+    mask[cls == CLS_P] = 0.0
+    sel = (cls == CLS_S) | (cls == CLS_F)
+    mask[sel] = (~on_face[sel]).astype(np.float64)
+    xyz = xyz + jit * mask
+    return xyz.astype(np.float32), cls
+
+
+def _tangent_frame(p: np.ndarray):
+    """Two unit tangents orthogonal to the unit radial direction of p."""
+    nrm = p / np.linalg.norm(p, axis=1, keepdims=True)
+    ref = np.where(np.abs(nrm[:, 2:3]) < 0.9, np.array([[0.0, 0.0, 1.0]]), np.array([[1.0, 0.0, 0.0]]))
+    e1 = np.cross(ref, nrm)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(nrm, e1)
+    return e1, e2
+
+
+def _lattice_box(lo, hi, dx):
+    ax = [np.arange(math.floor(lo[i] / dx), math.ceil(hi[i] / dx) + 1) * dx for i in range(3)]
+    g = np.meshgrid(*ax, indexing="ij")
+    return np.stack([c.ravel() for c in g], axis=1)
+
+
+def sphere_particles(dx: float = 0.02, seed: int = 1, radius: float = 1.0,
+                     band: float | None = None):
+    """Fibonacci points on the sphere (S) plus a cubic volume lattice (V/I).
+
+    Volume points keep at least dx/2 from the analytic surface.  With
+    ``band`` set, points deeper than ``band`` below the surface are class I
+    (fixed innermost layer); otherwise every volume point is V."""
+    amp = 0.25 * dx
+    ns = int(round(4.0 * np.pi * radius * radius / (dx * dx)))
+    k = np.arange(ns, dtype=np.float64)
+    z = 1.0 - (2.0 * k + 1.0) / ns
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    ga = np.pi * (3.0 - 5.0 ** 0.5)
+    phi = k * ga
+    s = np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1) * radius
+    ids = np.arange(ns)
+    e1, e2 = _tangent_frame(s)
+    s = s + e1 * jitter(seed, ids, 0, amp)[:, None] + e2 * jitter(seed, ids, 1, amp)[:, None]
+    s *= radius / np.linalg.norm(s, axis=1, keepdims=True)
+
+    v = _lattice_box((-radius,) * 3, (radius,) * 3, dx)
+    depth = radius - np.linalg.norm(v, axis=1)
+    keep = depth >= 0.5 * dx
+    v, depth = v[keep], depth[keep]
+    ids = np.arange(ns, ns + v.shape[0])
+    v = v + np.stack([jitter(seed, ids, a, amp) for a in range(3)], axis=1)
+    vcls = np.full(v.shape[0], CLS_V, dtype=np.int32)
+    if band is not None:
+        vcls[depth >= band] = CLS_I
+    xyz = np.concatenate([s, v]).astype(np.float32)
+    cls = np.concatenate([np.full(ns, CLS_S, dtype=np.int32), vcls])
+    return xyz, cls
+
+
+def torus_particles(dx: float = 0.02, seed: int = 2, R: float = 1.0, r: float = 0.3,
+                    band: float | None = None):
+    """Rings of surface points of equal spacing (S) plus a volume lattice (V/I)."""
+    amp = 0.25 * dx
+    nv = int(round(2.0 * np.pi * r / dx))
+    pts = []
+    for j in range(nv):
+        v = 2.0 * np.pi * (j + 0.5) / nv
+        rho = R + r * math.cos(v)
+        nu = max(3, int(round(2.0 * np.pi * rho / dx)))
+        u = 2.0 * np.pi * (np.arange(nu) + 0.5 * (j % 2)) / nu
+        pts.append(np.stack([u, np.full(nu, v)], axis=1))
+    uv = np.concatenate(pts)
+    ns = uv.shape[0]
+    ids = np.arange(ns)
+    u, v = uv[:, 0], uv[:, 1]
+    rho = R + r * np.cos(v)
+    u = u + jitter(seed, ids, 0, amp) / rho
+    v = v + jitter(seed, ids, 1, amp) / r
+    rho = R + r * np.cos(v)
+    s = np.stack([rho * np.cos(u), rho * np.sin(u), r * np.sin(v)], axis=1)
+
+    vol = _lattice_box((-(R + r), -(R + r), -r), (R + r, R + r, r), dx)
+    tube = np.sqrt((np.sqrt(vol[:, 0] ** 2 + vol[:, 1] ** 2) - R) ** 2 + vol[:, 2] ** 2)
+    depth = r - tube
+    keep = depth >= 0.5 * dx
+    vol, depth = vol[keep], depth[keep]
+    ids = np.arange(ns, ns + vol.shape[0])
+    vol = vol + np.stack([jitter(seed, ids, a, amp) for a in range(3)], axis=1)
+    vcls = np.full(vol.shape[0], CLS_V, dtype=np.int32)
+    if band is not None:
+        vcls[depth >= band] = CLS_I
+    xyz = np.concatenate([s, vol]).astype(np.float32)
+    cls = np.concatenate([np.full(ns, CLS_S, dtype=np.int32), vcls])
+    return xyz, cls
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+def cube_workload(seed: int = 0, dx: float = 0.05) -> list[Assembly]:
+    """Unit cube, 12 triangles, dx = 0.05, h = 1.3 dx, 100 iterations.
+
+    ~2,400 surface, 228 edge, 8 corner and 8,000 volume particles with
+    +-0.25 dx jitter; features at a 30 degree threshold (the 12 cube edges)."""
+    v, t = cube_mesh()
+    xyz, cls = cube_particles(dx, seed)
+    return [Assembly("cube", v, t, float(np.float32(dx)), smoothing_length(dx), xyz, cls,
+                     dihedral_deg=30.0, meta={"n_iter": 100})]
+
+
+def sphere_torus_workload(seed: int = 1, dx: float = 0.02, level: int = 5,
+                          torus_nu: int = 256, torus_nv: int = 64) -> list[Assembly]:
+    """Icosphere r = 1 (level 5, 20,480 triangles) and torus R = 1, r = 0.3
+    (256 x 64 quads, 32,768 triangles) at dx = 0.02, relaxed for 500 iterations."""
+    sv, st = icosphere_mesh(level)
+    sx, sc = sphere_particles(dx, seed)
+    tv, tt = torus_mesh(1.0, 0.3, torus_nu, torus_nv)
+    tx, tc = torus_particles(dx, seed + 100)
+    dxf = float(np.float32(dx))
+    return [Assembly("icosphere", sv, st, dxf, smoothing_length(dx), sx, sc, None, {"n_iter": 500}),
+            Assembly("torus", tv, tt, dxf, smoothing_length(dx), tx, tc, None, {"n_iter": 500})]
