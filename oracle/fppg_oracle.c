@@ -1037,8 +1037,15 @@ static float edge_side(const float *p, const float *q, const float *f, const flo
 
 /* FP32 decision for one triangle: is the orthogonal foot of y inside, and
  * at what distance. */
+static int is_degenerate(const or_ctx *c, int64_t t)
+{
+    const double *n = c->Nu + 3 * t;
+    return n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0;
+}
+
 static int surface_candidate(const or_ctx *c, int64_t t, const float *y, float *dist)
 {
+    if (is_degenerate(c, t)) return 0; /* a zero-area triangle has no foot */
     const float *a = c->Vf + 3 * c->T[3 * t], *b = c->Vf + 3 * c->T[3 * t + 1], *cc = c->Vf + 3 * c->T[3 * t + 2];
     const float *n = c->Nuf + 3 * t;
     float ya[3], f[3];
@@ -1156,6 +1163,7 @@ static int volume_inside_f(const or_ctx *c, const float *yf)
                 for (int64_t p = lower_bound_i64(c->pair_key, c->npairs, key); p < c->npairs && c->pair_key[p] == key;
                      p++) {
                     int64_t t = c->pair_tri[p];
+                    if (is_degenerate(c, t)) continue;
                     float cp[3];
                     int reg;
                     float dd = closest_on_triangle(c, t, yf, cp, &reg);

@@ -195,3 +195,20 @@ def test_feature_projection_on_cube_edges():
     np.testing.assert_allclose(x[:, 2], -0.5, atol=1e-15)
     np.testing.assert_allclose(x[:, 0], y[:, 0].astype(np.float32), atol=1e-7)
     assert len(np.unique(seg)) == 1
+
+
+def test_zero_area_triangles_are_never_projection_targets():
+    # a cube whose top face carries an extra zero-area sliver
+    v, t = W.cube_mesh()
+    v = np.vstack([v, [[0.0, 0.0, 0.5]]]).astype(np.float32)
+    top = [i for i in range(len(t)) if np.all(v[t[i], 2] == 0.5)][0]
+    a, b = t[top, 0], t[top, 1]
+    t = np.vstack([t, [[a, b, a]]]).astype(np.int32)       # degenerate (repeated vertex)
+    o = O.Oracle(v, t, 0.05, 0.065)
+    rng = np.random.default_rng(0)
+    y = np.stack([rng.uniform(-0.45, 0.45, 500), rng.uniform(-0.45, 0.45, 500),
+                  np.full(500, 0.51)], 1).astype(np.float32)
+    x, tri, ok = o.project_points(y, np.zeros(500, np.int32))
+    assert ok.all() and np.all(tri != len(t) - 1)
+    np.testing.assert_allclose(x[:, 2], 0.5, atol=1e-15)
+    assert o.volume_inside(y - np.array([0, 0, 0.02], np.float32)).all()
