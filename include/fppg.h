@@ -1,0 +1,210 @@
+/*
+ * fppg.h -- C ABI of the GB300 (sm_103a) relaxation library for
+ * Feature-Preserving Particle Generation (FPPG, arXiv 2501.03056).
+ *
+ * The library relaxes surface, feature-line and volume particles of a body
+ * given as an explicit triangle mesh (Sec. 3.1): every iteration rebuilds a
+ * cell-key + radix-sort neighbour grid (Sec. 3.1.3), sums the pairwise
+ * Wendland C2 kernel-gradient repulsion (Eq. 15 with Eqs. 16-17), takes the
+ * limited step (Eqs. 22-25) and projects each particle back to its
+ * constraint (Sec. 3.3.3, Sec. 3.3.4).  Everything runs in hand-written CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every call:
+ *  - Return value: FPPG_OK (0) or one of the FPPG_ERR_* codes.  A failing
+ *    call leaves a message in fppg_last_error(ctx).  No C++ exception crosses
+ *    the ABI.
+ *  - Pointers named *_host are host memory; pointers named *_dev are device
+ *    memory of the current CUDA device.  Inputs are copied: the caller keeps
+ *    ownership of every buffer it passes.  Outputs go to caller-allocated
+ *    buffers whose capacity is passed explicitly.
+ *  - Handles (fppg_ctx, fppg_batch) are owned by the library until the
+ *    matching destroy call.
+ *  - Work is enqueued on the stream given by fppg_set_stream (default: the
+ *    legacy default stream).  Calls that return host data synchronise that
+ *    stream before returning; fppg_relax and fppg_batch_relax do not.
+ *  - Arrays of points are packed xyz triples (row-major [n][3]).
+ *  - Particle classes: FPPG_S surface, FPPG_V volume (relaxes),
+ *    FPPG_F feature line, FPPG_I innermost volume (fixed), FPPG_P singular
+ *    feature point (fixed).
+ */
+#ifndef FPPG_H
+#define FPPG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FPPG_OK = 0,
+    FPPG_ERR_ARG = 1,      /* invalid argument (null, size, index, NaN)      */
+    FPPG_ERR_STATE = 2,    /* call out of order (e.g. relax before particles) */
+    FPPG_ERR_OOM = 3,      /* device or host allocation failed               */
+    FPPG_ERR_CUDA = 4,     /* a CUDA runtime call failed                     */
+    FPPG_ERR_TIMEOUT = 5,  /* a device-side wait ran out of its budget       */
+    FPPG_ERR_INTERNAL = 6  /* a device-side consistency check failed         */
+};
+
+enum { FPPG_S = 0, FPPG_V = 1, FPPG_F = 2, FPPG_I = 3, FPPG_P = 4 };
+
+typedef struct fppg_ctx fppg_ctx;
+typedef struct fppg_batch fppg_batch;
+
+/* Uniformity statistics (fppg_stats). */
+typedef struct {
+    double mean_rho[3];      /* mean kernel sum of S, V, F particles           */
+    double std_rho[3];       /* its standard deviation per class               */
+    double min_pair_over_dx; /* smallest masked pair distance / dx (mobile)    */
+    double max_disp_over_dx; /* largest move of the last iteration / dx        */
+    int64_t count[3];        /* number of S, V, F particles                    */
+} fppg_stats_t;
+
+/* ---- body ----------------------------------------------------------------
+ * fppg_create: upload a closed, outward-oriented triangle mesh (Sec. 3.1:
+ * explicit STL-like geometry) and build its device structures:
+ *   - per-triangle unit normals, in-plane edge normals, edge and
+ *     angle-weighted vertex pseudonormals (FP64, stored FP32);
+ *   - the triangle grid with cell size dx (Sec. 3.1.1), triangles binned to
+ *     cells by the separating-axis triangle-box test (Sec. 3.1.2) on cells
+ *     inflated by 1e-6 dx;
+ *   - the compact cell list C_compact and the hash H of Eq. 10 with
+ *     H_begin / H_length (Sec. 3.1.3);
+ *   - the neighbour grid: cell 2h (1 + 2^-8), one cell of margin around the
+ *     mesh bounding box.
+ * verts_host: [nv][3] float; tris_host: [nt][3] int32 vertex indices in
+ * [0, nv); dx: particle spacing; h: smoothing length (Wendland support 2h;
+ * the paper uses h = 1.3 dx).  Errors: FPPG_ERR_ARG for empty meshes,
+ * out-of-range indices, non-finite vertices or dx, h <= 0; FPPG_ERR_OOM. */
+int fppg_create(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,
+                fppg_ctx **out);
+int fppg_destroy(fppg_ctx *ctx);
+/* Last error message of ctx ("" when none); ctx may be NULL for errors of
+ * fppg_create.  The string lives until the next call on ctx. */
+const char *fppg_last_error(const fppg_ctx *ctx);
+/* Stream (a cudaStream_t) on which all later work of ctx is enqueued. */
+int fppg_set_stream(fppg_ctx *ctx, void *stream);
+/* Feature particles never move when fixed != 0 (paper-literal boundary
+ * role of feature lines, Sec. 2.2); by default they slide along their line. */
+int fppg_set_fixed_features(fppg_ctx *ctx, int32_t fixed);
+
+/* ---- features (Sec. 3.2.2) -------------------------------------------------
+ * fppg_extract_features: edge-face map with v1 < v2 keys; an edge is a
+ * feature when it has other than two faces or when the angle between the
+ * two unit face normals exceeds dihedral_deg (dot < cos(dihedral_deg)),
+ * both in FP64.  Singular points: feature degree 1 or more than 2.  Feature
+ * lines: walks from singular points (ascending vertex id, incident edges in
+ * ascending edge id), then closed loops from the lowest uncoloured edge.
+ * Writes the feature-edge count to *n_edges (nullable). */
+int fppg_extract_features(fppg_ctx *ctx, float dihedral_deg, int64_t *n_edges);
+/* Feature edges as [n][2] vertex ids (v1 < v2), ascending (v1, v2) order.
+ * Copies min(cap, n) edges; *n receives the total. */
+int fppg_get_feature_edges(fppg_ctx *ctx, int32_t *edges_host, int64_t cap, int64_t *n);
+/* Feature lines: line_nseg_host[l] segments each, closed flag per line,
+ * seg_v_host [n_seg][2] vertex pairs in walk order.  Capacities in lines and
+ * segments; totals through *n_lines and *n_seg. */
+int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *closed_host, int64_t cap_lines,
+                           int32_t *seg_v_host, int64_t cap_seg, int64_t *n_lines, int64_t *n_seg);
+
+/* ---- particles --------------------------------------------------------------
+ * fppg_set_particles: copy n particles (xyz_host [n][3] float, cls_host [n]
+ * class codes) to the device; constraint ids start at -1 (the first
+ * iteration then searches all triangles / feature segments of the body).
+ * Errors: FPPG_ERR_ARG for a class outside 0..4 or non-finite coordinates. */
+int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_host, int64_t n);
+/* Positions, classes and constraint ids (triangle for S, feature segment for
+ * F, -1 otherwise) into caller buffers of capacity cap (each nullable);
+ * *n_out receives the particle count.  Synchronises the stream. */
+int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_t *cons_host, int64_t cap,
+                       int64_t *n_out);
+
+/* ---- relaxation (Algorithm 1) ----------------------------------------------
+ * fppg_relax: n_iter Jacobi iterations of
+ *   A1 cell keys  A2 stable radix sort  A3 gather + cell ranges
+ *   A4 force a_i = -sum_j dW/dr(r_ij) e_ij over the masked neighbours
+ *      (S <- S,F,P; V <- all; F <- F,P) and amax over mobile particles
+ *   A5 step dr = a dt^2 with dt = 0.25 sqrt(h / amax) (largest move h/16),
+ *      normal part removed for S (current triangle), tangential only for F
+ *   A6 projection: S to the closest projectable triangle in the 3x3x3 cells
+ *      around the trial point, else revert; F to the closest point of its
+ *      line; V reverted when the pseudonormal sign says outside.
+ * Enqueued on the stream; does not synchronise.  Errors: FPPG_ERR_STATE
+ * without particles; FPPG_ERR_ARG for n_iter < 0. */
+int fppg_relax(fppg_ctx *ctx, int32_t n_iter);
+/* Same iteration with the acceleration a = -dE/dx of the uniformity energy
+ * (energy-descent relaxation). */
+int fppg_relax_energy(fppg_ctx *ctx, int32_t n_iter);
+/* Statistics of the current state; synchronises. */
+int fppg_stats(fppg_ctx *ctx, fppg_stats_t *out);
+
+/* ---- single steps of the path (parity and diagnostics) ---------------------
+ * fppg_debug_grid: A1-A3 on the current state.  key_host [n]: cell key per
+ * particle in id order; perm_host [n]: stable sort permutation (id of the
+ * k-th particle in key order); cells/start/end: occupied cells ascending
+ * with their [start, end) slot ranges (capacity cap_cells, count through
+ * *n_cells).  Any output may be NULL. */
+int fppg_debug_grid(fppg_ctx *ctx, uint32_t *key_host, uint32_t *perm_host, uint32_t *cells_host,
+                    uint32_t *start_host, uint32_t *end_host, int64_t cap_cells, int64_t *n_cells);
+/* A4 on the current state: acc_host [n][3] (id order, zero for fixed
+ * particles), count_host [n] masked neighbour counts, *amax.  Nullable. */
+int fppg_debug_forces(fppg_ctx *ctx, float *acc_host, int32_t *count_host, float *amax_host);
+/* A6 alone on n given trial points y_host [n][3] with classes cls_host and
+ * incoming constraints cons_host (nullable = all -1): writes x_host [n][3],
+ * cons_out_host [n] and ok_host [n] (0 = not projectable / outside; x then
+ * equals y). */
+int fppg_project_points(fppg_ctx *ctx, const float *y_host, const int32_t *cls_host, const int32_t *cons_host,
+                        int64_t n, float *x_host, int32_t *cons_out_host, int32_t *ok_host);
+
+/* Work of one force pass (A4) on the current state, summed over mobile
+ * particles: candidates = particles in the 27 neighbour cells tested by the
+ * FP32 distance rule, pairs = masked neighbours within 2h.  Synchronises. */
+int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs);
+
+/* ---- uniformity energy and its backward -------------------------------------
+ * E = sum over mobile i of (rho_i - W0_{c_i})^2, rho_i = W(0) + sum over the
+ * masked neighbours of W(r_ij); W0 the kernel sum of a perfect lattice of
+ * the class (cubic for V, square for S, line for F).  Positions are
+ * x = y - ((y - v_a) . n) n for S particles with a triangle (frozen
+ * triangle, unit normal n from verts_dev) and x = y otherwise.
+ * y_dev [n][3] float, verts_dev [nv][3] float (NULL = the body's mesh).
+ * Writes *E_host; gy_dev [n][3] and gV_dev [nv][3] receive dE/dy and
+ * dE/dverts when non-NULL (gV_dev is overwritten, not accumulated).
+ * Synchronises the stream. */
+int fppg_energy(fppg_ctx *ctx, const float *y_dev, const float *verts_dev, double *E_host, float *gy_dev,
+                float *gV_dev);
+/* Current positions [n][3] into a device buffer (for the energy). */
+int fppg_copy_positions_dev(fppg_ctx *ctx, float *xyz_dev);
+
+/* ---- batched form -------------------------------------------------------------
+ * fppg_batch_create: one group over n bodies (each with particles set):
+ * their particles are concatenated and every phase of an iteration runs as
+ * one launch over all bodies, each keeping its own grids, mesh and amax.
+ * The batch copies the bodies' state; fppg_batch_store writes it back. */
+int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out);
+int fppg_batch_destroy(fppg_batch *b);
+int fppg_batch_set_stream(fppg_batch *b, void *stream);
+/* n_iter iterations; use_graph != 0 captures graph_iters iterations into
+ * one CUDA graph (built on first use) and replays it. */
+int fppg_batch_relax(fppg_batch *b, int32_t n_iter, int32_t use_graph);
+int fppg_batch_set_graph_iters(fppg_batch *b, int32_t graph_iters);
+/* Copy the batch state back into its bodies, or reload it from them (after
+ * fppg_set_particles on the bodies with unchanged particle counts). */
+int fppg_batch_store(fppg_batch *b);
+int fppg_batch_load(fppg_batch *b);
+/* Kernel launches of one iteration of the batch (A1-A6, all bodies). */
+int32_t fppg_batch_kernels_per_iter(const fppg_batch *b);
+/* Particle count and the last error of the batch. */
+int64_t fppg_batch_size(const fppg_batch *b);
+const char *fppg_batch_last_error(const fppg_batch *b);
+/* Per-launch device time of the force kernel (A4) averaged over the
+ * iterations of the last call of fppg_batch_relax when timing was enabled
+ * with fppg_batch_time_force(b, 1); ms through *ms. */
+int fppg_batch_time_force(fppg_batch *b, int32_t enable);
+int fppg_batch_force_ms(fppg_batch *b, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FPPG_H */

@@ -1,0 +1,335 @@
+"""GB300-native relaxation path of Feature-Preserving Particle Generation.
+
+Thin ctypes binding of the C ABI in ``include/fppg.h`` (the CUDA library
+``_lib/libfppg.so``).  It only marshals arguments; every step of the path
+runs in the library's CUDA kernels.  Importing works without a GPU; any call
+that needs the library raises ``FPPGError`` when it has not been built
+(``__graft_entry__.build()``) -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (seeded synthetic inputs)
+
+__all__ = ["Body", "Batch", "FPPGError", "lib", "library_path", "workloads", "S", "V", "F", "I", "P"]
+
+S, V, F, I, P = 0, 1, 2, 3, 4
+OK, ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL = range(7)
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "_lib", "libfppg.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class FPPGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fppg error {code}: {msg}")
+        self.code = code
+
+
+class _Stats(C.Structure):
+    _fields_ = [("mean_rho", C.c_double * 3), ("std_rho", C.c_double * 3), ("min_pair_over_dx", C.c_double),
+                ("max_disp_over_dx", C.c_double), ("count", C.c_int64 * 3)]
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def lib():
+    """The loaded CUDA library (raises FPPGError when it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIBPATH):
+                raise FPPGError(-1, f"{_LIBPATH} is missing: build it with __graft_entry__.build()")
+            L = C.CDLL(_LIBPATH)
+            vp, i32, i64, f32, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_double
+            P_ = C.POINTER
+            sig = {
+                "fppg_create": [P_(f32), i64, P_(i32), i64, f32, f32, P_(vp)],
+                "fppg_destroy": [vp],
+                "fppg_set_stream": [vp, vp],
+                "fppg_set_fixed_features": [vp, i32],
+                "fppg_extract_features": [vp, f32, P_(i64)],
+                "fppg_get_feature_edges": [vp, P_(i32), i64, P_(i64)],
+                "fppg_get_feature_lines": [vp, P_(i64), P_(i32), i64, P_(i32), i64, P_(i64), P_(i64)],
+                "fppg_set_particles": [vp, P_(f32), P_(i32), i64],
+                "fppg_get_particles": [vp, P_(f32), P_(i32), P_(i32), i64, P_(i64)],
+                "fppg_relax": [vp, i32],
+                "fppg_relax_energy": [vp, i32],
+                "fppg_stats": [vp, P_(_Stats)],
+                "fppg_debug_grid": [vp, P_(C.c_uint32), P_(C.c_uint32), P_(C.c_uint32), P_(C.c_uint32),
+                                    P_(C.c_uint32), i64, P_(i64)],
+                "fppg_debug_forces": [vp, P_(f32), P_(i32), P_(f32)],
+                "fppg_project_points": [vp, P_(f32), P_(i32), P_(i32), i64, P_(f32), P_(i32), P_(i32)],
+                "fppg_energy": [vp, vp, vp, P_(f64), vp, vp],
+                "fppg_work_counts": [vp, P_(i64), P_(i64)],
+                "fppg_batch_load": [vp],
+                "fppg_copy_positions_dev": [vp, vp],
+                "fppg_batch_create": [P_(vp), i32, P_(vp)],
+                "fppg_batch_destroy": [vp],
+                "fppg_batch_set_stream": [vp, vp],
+                "fppg_batch_relax": [vp, i32, i32],
+                "fppg_batch_set_graph_iters": [vp, i32],
+                "fppg_batch_store": [vp],
+                "fppg_batch_time_force": [vp, i32],
+                "fppg_batch_force_ms": [vp, P_(f64)],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            L.fppg_last_error.argtypes = [vp]
+            L.fppg_last_error.restype = C.c_char_p
+            L.fppg_batch_last_error.argtypes = [vp]
+            L.fppg_batch_last_error.restype = C.c_char_p
+            L.fppg_batch_kernels_per_iter.argtypes = [vp]
+            L.fppg_batch_kernels_per_iter.restype = C.c_int32
+            L.fppg_batch_size.argtypes = [vp]
+            L.fppg_batch_size.restype = C.c_int64
+            _lib = L
+    return _lib
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ct))
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Body:
+    """One body: ``fppg_create`` on its mesh (the handle lives until close())."""
+
+    def __init__(self, verts, tris, dx, h, stream=None):
+        L = lib()
+        self.verts = _f32(verts, (-1, 3))
+        self.tris = _i32(tris).reshape(-1, 3)
+        self.dx, self.h = float(np.float32(dx)), float(np.float32(h))
+        h_ = C.c_void_p()
+        r = L.fppg_create(_ptr(self.verts, C.c_float), self.verts.shape[0], _ptr(self.tris, C.c_int32),
+                          self.tris.shape[0], C.c_float(dx), C.c_float(h), C.byref(h_))
+        if r != OK:
+            raise FPPGError(r, L.fppg_last_error(None).decode())
+        self._h = h_
+        self.n = 0
+        if stream is not None:
+            self.set_stream(stream)
+
+    @classmethod
+    def from_assembly(cls, a, features=True, stream=None):
+        b = cls(a.verts, a.tris, a.dx, a.h, stream=stream)
+        if features and a.dihedral_deg is not None:
+            b.extract_features(a.dihedral_deg)
+        b.set_particles(a.xyz, a.cls)
+        return b
+
+    def _chk(self, r):
+        if r != OK:
+            raise FPPGError(r, lib().fppg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fppg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        self._chk(lib().fppg_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_fixed_features(self, fixed: bool):
+        self._chk(lib().fppg_set_fixed_features(self._h, int(bool(fixed))))
+
+    def extract_features(self, dihedral_deg) -> int:
+        n = C.c_int64()
+        self._chk(lib().fppg_extract_features(self._h, C.c_float(dihedral_deg), C.byref(n)))
+        return n.value
+
+    def feature_edges(self):
+        n = C.c_int64()
+        self._chk(lib().fppg_get_feature_edges(self._h, None, 0, C.byref(n)))
+        out = np.zeros((max(n.value, 1), 2), np.int32)
+        self._chk(lib().fppg_get_feature_edges(self._h, _ptr(out, C.c_int32), n.value, C.byref(n)))
+        return out[:n.value]
+
+    def feature_lines(self):
+        nl, ns = C.c_int64(), C.c_int64()
+        self._chk(lib().fppg_get_feature_lines(self._h, None, None, 0, None, 0, C.byref(nl), C.byref(ns)))
+        nseg = np.zeros(max(nl.value, 1), np.int64)
+        closed = np.zeros(max(nl.value, 1), np.int32)
+        segv = np.zeros((max(ns.value, 1), 2), np.int32)
+        self._chk(lib().fppg_get_feature_lines(self._h, _ptr(nseg, C.c_int64), _ptr(closed, C.c_int32), nl.value,
+                                               _ptr(segv, C.c_int32), ns.value, C.byref(nl), C.byref(ns)))
+        return nseg[:nl.value], closed[:nl.value], segv[:ns.value]
+
+    def set_particles(self, xyz, cls):
+        xyz = _f32(xyz, (-1, 3))
+        cls = _i32(cls)
+        self._chk(lib().fppg_set_particles(self._h, _ptr(xyz, C.c_float), _ptr(cls, C.c_int32), xyz.shape[0]))
+        self.n = xyz.shape[0]
+
+    def get_particles(self):
+        xyz = np.zeros((max(self.n, 1), 3), np.float32)
+        cls = np.zeros(max(self.n, 1), np.int32)
+        cons = np.zeros(max(self.n, 1), np.int32)
+        n = C.c_int64()
+        self._chk(lib().fppg_get_particles(self._h, _ptr(xyz, C.c_float), _ptr(cls, C.c_int32),
+                                           _ptr(cons, C.c_int32), self.n, C.byref(n)))
+        return xyz[:self.n], cls[:self.n], cons[:self.n]
+
+    def get_positions_into(self, xyz_out: np.ndarray):
+        """Positions into a caller buffer (e.g. pinned host memory)."""
+        n = C.c_int64()
+        self._chk(lib().fppg_get_particles(self._h, _ptr(xyz_out, C.c_float), None, None, self.n, C.byref(n)))
+
+    def relax(self, n_iter: int):
+        self._chk(lib().fppg_relax(self._h, int(n_iter)))
+
+    def relax_energy(self, n_iter: int):
+        self._chk(lib().fppg_relax_energy(self._h, int(n_iter)))
+
+    def stats(self) -> dict:
+        s = _Stats()
+        self._chk(lib().fppg_stats(self._h, C.byref(s)))
+        return {"mean_S": s.mean_rho[0], "mean_V": s.mean_rho[1], "mean_F": s.mean_rho[2],
+                "std_S": s.std_rho[0], "std_V": s.std_rho[1], "std_F": s.std_rho[2],
+                "min_pair_over_dx": s.min_pair_over_dx, "max_disp_over_dx": s.max_disp_over_dx,
+                "n_S": s.count[0], "n_V": s.count[1], "n_F": s.count[2]}
+
+    def debug_grid(self):
+        n = self.n
+        key, perm = np.zeros(max(n, 1), np.uint32), np.zeros(max(n, 1), np.uint32)
+        nc = C.c_int64()
+        self._chk(lib().fppg_debug_grid(self._h, None, None, None, None, None, 0, C.byref(nc)))
+        cells, st, en = (np.zeros(max(nc.value, 1), np.uint32) for _ in range(3))
+        self._chk(lib().fppg_debug_grid(self._h, _ptr(key, C.c_uint32), _ptr(perm, C.c_uint32),
+                                        _ptr(cells, C.c_uint32), _ptr(st, C.c_uint32), _ptr(en, C.c_uint32),
+                                        nc.value, C.byref(nc)))
+        m = nc.value
+        return key[:n], perm[:n], cells[:m], st[:m], en[:m]
+
+    def debug_forces(self):
+        n = self.n
+        acc, cnt = np.zeros((max(n, 1), 3), np.float32), np.zeros(max(n, 1), np.int32)
+        amax = np.zeros(1, np.float32)
+        self._chk(lib().fppg_debug_forces(self._h, _ptr(acc, C.c_float), _ptr(cnt, C.c_int32),
+                                          _ptr(amax, C.c_float)))
+        return acc[:n], cnt[:n], float(amax[0])
+
+    def project_points(self, y, cls, cons=None):
+        y = _f32(y, (-1, 3))
+        cls = _i32(cls)
+        m = y.shape[0]
+        cons = None if cons is None else _i32(cons)
+        x, co, ok = np.zeros((max(m, 1), 3), np.float32), np.zeros(max(m, 1), np.int32), np.zeros(max(m, 1), np.int32)
+        self._chk(lib().fppg_project_points(self._h, _ptr(y, C.c_float), _ptr(cls, C.c_int32),
+                                            _ptr(cons, C.c_int32), m, _ptr(x, C.c_float), _ptr(co, C.c_int32),
+                                            _ptr(ok, C.c_int32)))
+        return x[:m], co[:m], ok[:m].astype(bool)
+
+    def work_counts(self):
+        """(candidates, pairs) of one force pass on the current state."""
+        c, p = C.c_int64(), C.c_int64()
+        self._chk(lib().fppg_work_counts(self._h, C.byref(c), C.byref(p)))
+        return c.value, p.value
+
+    def energy_ptr(self, y_ptr: int, verts_ptr: int = 0, gy_ptr: int = 0, gv_ptr: int = 0) -> float:
+        """Energy (and gradients into device buffers) from device pointers."""
+        E = C.c_double()
+        self._chk(lib().fppg_energy(self._h, C.c_void_p(y_ptr), C.c_void_p(verts_ptr or None), C.byref(E),
+                                    C.c_void_p(gy_ptr or None), C.c_void_p(gv_ptr or None)))
+        return E.value
+
+    def copy_positions_dev(self, ptr: int):
+        self._chk(lib().fppg_copy_positions_dev(self._h, C.c_void_p(ptr)))
+
+
+class Batch:
+    """Many bodies relaxed by one launch per phase (``fppg_batch_*``)."""
+
+    def __init__(self, bodies, stream=None):
+        L = lib()
+        self.bodies = list(bodies)
+        arr = (C.c_void_p * len(self.bodies))(*[b.handle for b in self.bodies])
+        h_ = C.c_void_p()
+        r = L.fppg_batch_create(arr, len(self.bodies), C.byref(h_))
+        if r != OK:
+            raise FPPGError(r, L.fppg_batch_last_error(None).decode())
+        self._h = h_
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _chk(self, r):
+        if r != OK:
+            raise FPPGError(r, lib().fppg_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fppg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n(self) -> int:
+        return int(lib().fppg_batch_size(self._h))
+
+    @property
+    def kernels_per_iter(self) -> int:
+        return int(lib().fppg_batch_kernels_per_iter(self._h))
+
+    def set_stream(self, stream):
+        self._chk(lib().fppg_batch_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_graph_iters(self, k: int):
+        self._chk(lib().fppg_batch_set_graph_iters(self._h, int(k)))
+
+    def relax(self, n_iter: int, use_graph: bool = True):
+        self._chk(lib().fppg_batch_relax(self._h, int(n_iter), int(bool(use_graph))))
+
+    def store(self):
+        self._chk(lib().fppg_batch_store(self._h))
+
+    def load(self):
+        self._chk(lib().fppg_batch_load(self._h))
+
+    def time_force(self, enable: bool = True):
+        self._chk(lib().fppg_batch_time_force(self._h, int(bool(enable))))
+
+    def force_ms(self) -> float:
+        ms = C.c_double()
+        self._chk(lib().fppg_batch_force_ms(self._h, C.byref(ms)))
+        return ms.value

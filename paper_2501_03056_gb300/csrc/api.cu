@@ -1,0 +1,613 @@
+// extern "C" entry points of the relaxation library (include/fppg.h).
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "../../include/fppg.h"
+#include "body.h"
+
+using namespace fppg;
+
+struct fppg_ctx {
+    Body body;
+    Group group;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t n = 0;
+    bool has_particles = false;
+    int fixed_features = 0;
+    std::vector<int32_t> cls_host;
+};
+
+struct fppg_batch {
+    Group group;
+    std::vector<fppg_ctx *> ctxs;
+    std::vector<int64_t> off;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(std::string &dst, int code, const std::string &msg) {
+    dst = msg;
+    return code;
+}
+
+#define CUDA_OR(dst, x)                                                                 \
+    do {                                                                                \
+        cudaError_t e_ = (x);                                                           \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(dst, e_ == cudaErrorMemoryAllocation ? FPPG_ERR_OOM : FPPG_ERR_CUDA, \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+__global__ void k_pack(const float *__restrict__ xyz, const int32_t *__restrict__ cls, int64_t n, int body,
+                       float4 *__restrict__ pos, int32_t *__restrict__ cons) {
+    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    pos[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2],
+                         __uint_as_float((uint32_t)cls[i] | ((uint32_t)body << 8)));
+    cons[i] = -1;
+}
+
+__global__ void k_unpack(const float4 *__restrict__ pos, int64_t n, float *__restrict__ xyz) {
+    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    float4 p = pos[i];
+    xyz[3 * i] = p.x;
+    xyz[3 * i + 1] = p.y;
+    xyz[3 * i + 2] = p.z;
+}
+
+__global__ void k_set_body(float4 *__restrict__ pos, int64_t n, int body) {
+    int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    float4 p = pos[i];
+    p.w = __uint_as_float((__float_as_uint(p.w) & 0xffu) | ((uint32_t)body << 8));
+    pos[i] = p;
+}
+
+inline unsigned nb(int64_t n) { return (unsigned)std::max<int64_t>((n + 255) / 256, 1); }
+
+MeshView view_of(const Body &b) {
+    return MeshView{b.geo, b.vx, b.pn, b.hrng, b.compact, b.tlist, b.seg, b.lines};
+}
+
+// (re)build the single-body group of a context
+int ctx_group(fppg_ctx *c) {
+    Group &g = c->group;
+    g.d.B = 1;
+    g.d.total_cells = (int64_t)c->body.ng_n[0] * c->body.ng_n[1] * c->body.ng_n[2];
+    g.hp.assign(1, make_params(c->body, 0u, 0, (int)c->n, c->fixed_features));
+    g.mesh = view_of(c->body);
+    return g.upload_params(c->stream, c->err) ? FPPG_ERR_CUDA : FPPG_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int fppg_create(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,
+                fppg_ctx **out) {
+    g_create_err.clear();
+    if (!out) return fail(g_create_err, FPPG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!verts_host || !tris_host || nv < 3 || nt < 1 || nv > (1 << 30) || nt > (1 << 29))
+        return fail(g_create_err, FPPG_ERR_ARG, "empty or oversized mesh");
+    if (!(dx > 0.f) || !(h > 0.f) || !std::isfinite(dx) || !std::isfinite(h))
+        return fail(g_create_err, FPPG_ERR_ARG, "dx and h must be finite and positive");
+    for (int64_t i = 0; i < 3 * nv; i++)
+        if (!std::isfinite(verts_host[i])) return fail(g_create_err, FPPG_ERR_ARG, "non-finite vertex");
+    for (int64_t i = 0; i < 3 * nt; i++)
+        if (tris_host[i] < 0 || tris_host[i] >= nv)
+            return fail(g_create_err, FPPG_ERR_ARG, "triangle index out of range");
+    fppg_ctx *c = new (std::nothrow) fppg_ctx();
+    if (!c) return fail(g_create_err, FPPG_ERR_OOM, "host allocation failed");
+    c->body.verts_host.assign(verts_host, verts_host + 3 * nv);
+    int r = c->body.build_mesh(verts_host, nv, tris_host, nt, dx, h, c->stream, c->err);
+    if (r == 0) r = ctx_group(c);
+    if (r != 0) {
+        g_create_err = c->err;
+        delete c;
+        return r == 1 ? FPPG_ERR_ARG : r;
+    }
+    *out = c;
+    return FPPG_OK;
+}
+
+int fppg_destroy(fppg_ctx *ctx) {
+    if (!ctx) return FPPG_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return FPPG_OK;
+}
+
+const char *fppg_last_error(const fppg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+int fppg_set_stream(fppg_ctx *ctx, void *stream) {
+    if (!ctx) return FPPG_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return FPPG_OK;
+}
+
+int fppg_set_fixed_features(fppg_ctx *ctx, int32_t fixed) {
+    if (!ctx) return FPPG_ERR_ARG;
+    ctx->fixed_features = fixed ? 1 : 0;
+    return ctx_group(ctx);
+}
+
+int fppg_extract_features(fppg_ctx *ctx, float dihedral_deg, int64_t *n_edges) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (!std::isfinite(dihedral_deg)) return fail(ctx->err, FPPG_ERR_ARG, "dihedral_deg must be finite");
+    int r = ctx->body.extract_features(dihedral_deg, ctx->stream, ctx->err);
+    if (r) return r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA;
+    if (n_edges) *n_edges = (int64_t)ctx->body.fe.size() / 2;
+    return ctx_group(ctx);
+}
+
+int fppg_get_feature_edges(fppg_ctx *ctx, int32_t *edges_host, int64_t cap, int64_t *n) {
+    if (!ctx) return FPPG_ERR_ARG;
+    const int64_t m = (int64_t)ctx->body.fe.size() / 2;
+    if (n) *n = m;
+    if (edges_host) std::copy(ctx->body.fe.begin(), ctx->body.fe.begin() + 2 * std::min(cap, m), edges_host);
+    return FPPG_OK;
+}
+
+int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *closed_host, int64_t cap_lines,
+                           int32_t *seg_v_host, int64_t cap_seg, int64_t *n_lines, int64_t *n_seg) {
+    if (!ctx) return FPPG_ERR_ARG;
+    const Body &b = ctx->body;
+    if (n_lines) *n_lines = b.nlines;
+    if (n_seg) *n_seg = b.nseg;
+    for (int64_t l = 0; l < std::min<int64_t>(cap_lines, b.nlines); l++) {
+        if (line_nseg_host) line_nseg_host[l] = b.line_nseg[l];
+        if (closed_host) closed_host[l] = b.line_closed[l];
+    }
+    if (seg_v_host) std::copy(b.seg_v.begin(), b.seg_v.begin() + 2 * std::min<int64_t>(cap_seg, b.nseg), seg_v_host);
+    return FPPG_OK;
+}
+
+int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_host, int64_t n) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (n < 0 || n > (int64_t)1 << 31) return fail(ctx->err, FPPG_ERR_ARG, "particle count out of range");
+    if (n > 0 && (!xyz_host || !cls_host)) return fail(ctx->err, FPPG_ERR_ARG, "NULL particle buffer");
+    for (int64_t i = 0; i < n; i++)
+        if (cls_host[i] < 0 || cls_host[i] > 4) return fail(ctx->err, FPPG_ERR_ARG, "class outside 0..4");
+    for (int64_t i = 0; i < 3 * n; i++)
+        if (!std::isfinite(xyz_host[i])) return fail(ctx->err, FPPG_ERR_ARG, "non-finite coordinate");
+    Group &g = ctx->group;
+    if (n != g.d.N || !g.d.pos) {
+        int r = g.alloc_particles(n, ctx->err);
+        if (r) return r;
+    }
+    ctx->n = n;
+    ctx->cls_host.assign(cls_host, cls_host + n);
+    float *dx = nullptr;
+    int32_t *dc = nullptr;
+    CUDA_OR(ctx->err, cudaMalloc(&dx, sizeof(float) * 3 * (size_t)std::max<int64_t>(n, 1)));
+    CUDA_OR(ctx->err, cudaMalloc(&dc, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
+    if (n > 0) {
+        CUDA_OR(ctx->err, cudaMemcpyAsync(dx, xyz_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_OR(ctx->err, cudaMemcpyAsync(dc, cls_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        k_pack<<<nb(n), 256, 0, ctx->stream>>>(dx, dc, n, 0, g.d.pos, g.d.cons);
+    }
+    CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    cudaFree(dx);
+    cudaFree(dc);
+    ctx->has_particles = true;
+    return ctx_group(ctx);
+}
+
+int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_t *cons_host, int64_t cap,
+                       int64_t *n_out) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (n_out) *n_out = ctx->n;
+    const int64_t m = std::min(cap, ctx->n);
+    if (m <= 0) return FPPG_OK;
+    if (xyz_host) {
+        float *dx = nullptr;
+        CUDA_OR(ctx->err, cudaMalloc(&dx, sizeof(float) * 3 * (size_t)ctx->n));
+        k_unpack<<<nb(ctx->n), 256, 0, ctx->stream>>>(ctx->group.d.pos, ctx->n, dx);
+        CUDA_OR(ctx->err, cudaMemcpyAsync(xyz_host, dx, sizeof(float) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+        cudaFree(dx);
+    }
+    if (cons_host)
+        CUDA_OR(ctx->err, cudaMemcpyAsync(cons_host, ctx->group.d.cons, sizeof(int32_t) * m, cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+    if (cls_host) std::copy(ctx->cls_host.begin(), ctx->cls_host.begin() + m, cls_host);
+    CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    return FPPG_OK;
+}
+
+static int relax_impl(fppg_ctx *ctx, int32_t n_iter, bool energy_mode) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (n_iter < 0) return fail(ctx->err, FPPG_ERR_ARG, "n_iter < 0");
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    for (int32_t it = 0; it < n_iter; it++) iterate(ctx->group, ctx->stream, energy_mode);
+    CUDA_OR(ctx->err, cudaGetLastError());
+    return FPPG_OK;
+}
+
+int fppg_relax(fppg_ctx *ctx, int32_t n_iter) { return relax_impl(ctx, n_iter, false); }
+
+int fppg_relax_energy(fppg_ctx *ctx, int32_t n_iter) { return relax_impl(ctx, n_iter, true); }
+
+int fppg_stats(fppg_ctx *ctx, fppg_stats_t *out) {
+    if (!ctx || !out) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    int r = stats(ctx->group, ctx->stream, out->mean_rho, out->std_rho, &out->min_pair_over_dx,
+                  &out->max_disp_over_dx, out->count, ctx->err);
+    return r == 0 ? FPPG_OK : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
+}
+
+int fppg_debug_grid(fppg_ctx *ctx, uint32_t *key_host, uint32_t *perm_host, uint32_t *cells_host,
+                    uint32_t *start_host, uint32_t *end_host, int64_t cap_cells, int64_t *n_cells) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    Group &g = ctx->group;
+    const int64_t n = ctx->n;
+    if (n == 0) {
+        if (n_cells) *n_cells = 0;
+        return FPPG_OK;
+    }
+    int buf = build_grid(g, ctx->stream);
+    std::vector<uint32_t> ks(n), perm(n);
+    CUDA_OR(ctx->err, cudaMemcpyAsync(ks.data(), g.d.key[buf], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR(ctx->err, cudaMemcpyAsync(perm.data(), g.d.id[buf], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<uint4> table((size_t)g.d.total_cells);
+    uint32_t ep = 0;
+    CUDA_OR(ctx->err, cudaMemcpyAsync(table.data(), g.d.cells, sizeof(uint4) * table.size(), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    CUDA_OR(ctx->err, cudaMemcpyAsync(&ep, g.d.epoch, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    if (key_host)
+        for (int64_t k = 0; k < n; k++) key_host[perm[k]] = ks[k];
+    if (perm_host) std::copy(perm.begin(), perm.end(), perm_host);
+    int64_t m = 0;
+    for (int64_t c = 0; c < (int64_t)table.size(); c++) {
+        if (table[c].z != ep) continue;
+        if (m < cap_cells) {
+            if (cells_host) cells_host[m] = (uint32_t)c;
+            if (start_host) start_host[m] = table[c].x;
+            if (end_host) end_host[m] = table[c].y;
+        }
+        m++;
+    }
+    if (n_cells) *n_cells = m;
+    return FPPG_OK;
+}
+
+int fppg_debug_forces(fppg_ctx *ctx, float *acc_host, int32_t *count_host, float *amax_host) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    Group &g = ctx->group;
+    const int64_t n = ctx->n;
+    if (n == 0) return FPPG_OK;
+    float *dacc = nullptr;
+    int32_t *dcnt_s = nullptr, *dcnt = nullptr;
+    CUDA_OR(ctx->err, cudaMalloc(&dacc, sizeof(float) * 3 * n));
+    CUDA_OR(ctx->err, cudaMalloc(&dcnt_s, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, cudaMalloc(&dcnt, sizeof(int32_t) * n));
+    int buf = build_grid(g, ctx->stream);
+    forces(g, ctx->stream, dcnt_s);
+    unpermute(g, buf, ctx->stream, dacc, dcnt_s, dcnt);
+    uint32_t am = 0;
+    if (acc_host) CUDA_OR(ctx->err, cudaMemcpyAsync(acc_host, dacc, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (count_host)
+        CUDA_OR(ctx->err, cudaMemcpyAsync(count_host, dcnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR(ctx->err, cudaMemcpyAsync(&am, g.d.amax, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    if (amax_host) memcpy(amax_host, &am, 4);
+    cudaFree(dacc);
+    cudaFree(dcnt_s);
+    cudaFree(dcnt);
+    return FPPG_OK;
+}
+
+int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    Group &g = ctx->group;
+    const int64_t n = ctx->n;
+    int64_t c = 0, p = 0;
+    if (n > 0) {
+        int32_t *dcnt = nullptr, *dcand = nullptr;
+        CUDA_OR(ctx->err, cudaMalloc(&dcnt, sizeof(int32_t) * n));
+        CUDA_OR(ctx->err, cudaMalloc(&dcand, sizeof(int32_t) * n));
+        build_grid(g, ctx->stream);
+        forces(g, ctx->stream, dcnt, dcand);
+        std::vector<int32_t> hc(n), hp(n);
+        CUDA_OR(ctx->err, cudaMemcpyAsync(hc.data(), dcand, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_OR(ctx->err, cudaMemcpyAsync(hp.data(), dcnt, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+        cudaFree(dcnt);
+        cudaFree(dcand);
+        for (int64_t k = 0; k < n; k++) {
+            c += hc[k];
+            if (hc[k] > 0) p += hp[k];
+        }
+    }
+    if (candidates) *candidates = c;
+    if (pairs) *pairs = p;
+    return FPPG_OK;
+}
+
+int fppg_project_points(fppg_ctx *ctx, const float *y_host, const int32_t *cls_host, const int32_t *cons_host,
+                        int64_t n, float *x_host, int32_t *cons_out_host, int32_t *ok_host) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (n < 0 || (n > 0 && (!y_host || !cls_host || !x_host || !cons_out_host || !ok_host)))
+        return fail(ctx->err, FPPG_ERR_ARG, "bad projection buffers");
+    if (n == 0) return FPPG_OK;
+    for (int64_t i = 0; i < n; i++)
+        if (cls_host[i] < 0 || cls_host[i] > 4) return fail(ctx->err, FPPG_ERR_ARG, "class outside 0..4");
+    float *dy = nullptr, *dxo = nullptr;
+    int32_t *dcls = nullptr, *dcin = nullptr, *dcout = nullptr, *dok = nullptr;
+    CUDA_OR(ctx->err, cudaMalloc(&dy, sizeof(float) * 3 * n));
+    CUDA_OR(ctx->err, cudaMalloc(&dxo, sizeof(float) * 3 * n));
+    CUDA_OR(ctx->err, cudaMalloc(&dcls, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, cudaMalloc(&dcout, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, cudaMalloc(&dok, sizeof(int32_t) * n));
+    if (cons_host) CUDA_OR(ctx->err, cudaMalloc(&dcin, sizeof(int32_t) * n));
+    cudaStream_t s = ctx->stream;
+    CUDA_OR(ctx->err, cudaMemcpyAsync(dy, y_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    CUDA_OR(ctx->err, cudaMemcpyAsync(dcls, cls_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    if (cons_host) CUDA_OR(ctx->err, cudaMemcpyAsync(dcin, cons_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    project_points(ctx->group, dy, dcls, dcin, n, dxo, dcout, dok, s);
+    CUDA_OR(ctx->err, cudaMemcpyAsync(x_host, dxo, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+    CUDA_OR(ctx->err, cudaMemcpyAsync(cons_out_host, dcout, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_OR(ctx->err, cudaMemcpyAsync(ok_host, dok, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_OR(ctx->err, cudaStreamSynchronize(s));
+    void *p[] = {dy, dxo, dcls, dcin, dcout, dok};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    return FPPG_OK;
+}
+
+int fppg_energy(fppg_ctx *ctx, const float *y_dev, const float *verts_dev, double *E_host, float *gy_dev,
+                float *gV_dev) {
+    if (!ctx || !y_dev || !E_host) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    if (ctx->n == 0) {
+        *E_host = 0.0;
+        return FPPG_OK;
+    }
+    int r = energy(ctx->group, ctx->body, y_dev, verts_dev, E_host, gy_dev, gV_dev, ctx->stream, ctx->err);
+    return r == 0 ? FPPG_OK : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
+}
+
+int fppg_copy_positions_dev(fppg_ctx *ctx, float *xyz_dev) {
+    if (!ctx || !xyz_dev) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    if (ctx->n) k_unpack<<<nb(ctx->n), 256, 0, ctx->stream>>>(ctx->group.d.pos, ctx->n, xyz_dev);
+    CUDA_OR(ctx->err, cudaGetLastError());
+    return FPPG_OK;
+}
+
+// ---- batches ------------------------------------------------------------------
+int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
+    if (!out) return FPPG_ERR_ARG;
+    *out = nullptr;
+    if (!ctxs || n <= 0 || n > (1 << 20)) return fail(g_create_err, FPPG_ERR_ARG, "bad body list");
+    for (int32_t i = 0; i < n; i++)
+        if (!ctxs[i] || !ctxs[i]->has_particles)
+            return fail(g_create_err, FPPG_ERR_STATE, "every body needs particles before batching");
+    fppg_batch *b = new (std::nothrow) fppg_batch();
+    if (!b) return fail(g_create_err, FPPG_ERR_OOM, "host allocation failed");
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->stream = ctxs[0]->stream;
+    Group &g = b->group;
+    g.owns_mesh = true;
+    DevGroup &d = g.d;
+    d.B = n;
+    int64_t N = 0, cells = 0, nt = 0, nv = 0, hs = 0, nc = 0, np = 0, ns = 0, nl = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const fppg_ctx *c = ctxs[i];
+        const Body &bd = c->body;
+        AsmParams A = make_params(bd, (uint32_t)cells, (int)N, (int)(N + c->n), c->fixed_features);
+        A.tri_off = (int)nt;
+        A.vert_off = (int)nv;
+        A.hash_off = (uint32_t)hs;
+        A.compact_off = (uint32_t)nc;
+        A.tlist_off = (uint32_t)np;
+        A.seg_off = (int)ns;
+        A.line_off = (int)nl;
+        g.hp.push_back(A);
+        b->off.push_back(N);
+        N += c->n;
+        cells += (int64_t)bd.ng_n[0] * bd.ng_n[1] * bd.ng_n[2];
+        nt += bd.nt;
+        nv += bd.nv;
+        hs += bd.hash_size;
+        nc += bd.ncompact;
+        np += bd.npairs;
+        ns += bd.nseg;
+        nl += bd.nlines;
+    }
+    b->off.push_back(N);
+    if (cells >= 0xffffffffLL || N > ((int64_t)1 << 31)) {
+        delete b;
+        return fail(g_create_err, FPPG_ERR_ARG, "batch too large for 32-bit keys");
+    }
+    d.total_cells = cells;
+    std::string &err = b->err;
+    int r = g.alloc_particles(N, err);
+    auto A = [&](void **p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
+    if (!r && (A((void **)&d.geo, sizeof(float4) * 5 * nt) || A((void **)&d.vx, sizeof(float4) * 3 * nt) ||
+               A((void **)&d.pn, sizeof(float4) * 6 * nt) || A((void **)&d.hrng, sizeof(uint2) * hs) ||
+               A((void **)&d.compact, sizeof(uint4) * nc) || A((void **)&d.tlist, sizeof(int32_t) * np) ||
+               A((void **)&d.seg, sizeof(float4) * 3 * ns) || A((void **)&d.lines, sizeof(int2) * nl)))
+        r = FPPG_ERR_OOM;
+    cudaStream_t s = b->stream;
+    for (int32_t i = 0; i < n && !r; i++) {
+        const Body &bd = ctxs[i]->body;
+        const AsmParams &P = g.hp[i];
+        auto cp = [&](void *dst, const void *src, size_t bytes) {
+            if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+        };
+        cp(d.geo + 5 * (size_t)P.tri_off, bd.geo, sizeof(float4) * 5 * bd.nt);
+        cp(d.vx + 3 * (size_t)P.tri_off, bd.vx, sizeof(float4) * 3 * bd.nt);
+        cp(d.pn + 6 * (size_t)P.tri_off, bd.pn, sizeof(float4) * 6 * bd.nt);
+        cp(d.hrng + P.hash_off, bd.hrng, sizeof(uint2) * bd.hash_size);
+        cp(d.compact + P.compact_off, bd.compact, sizeof(uint4) * bd.ncompact);
+        cp(d.tlist + P.tlist_off, bd.tlist, sizeof(int32_t) * bd.npairs);
+        if (bd.nseg) cp(d.seg + 3 * (size_t)P.seg_off, bd.seg, sizeof(float4) * 3 * bd.nseg);
+        if (bd.nlines) cp(d.lines + P.line_off, bd.lines, sizeof(int2) * bd.nlines);
+        const int64_t cn = ctxs[i]->n;
+        cp(d.pos + b->off[i], ctxs[i]->group.d.pos, sizeof(float4) * cn);
+        cp(d.cons + b->off[i], ctxs[i]->group.d.cons, sizeof(int32_t) * cn);
+        if (cn) k_set_body<<<nb(cn), 256, 0, s>>>(d.pos + b->off[i], cn, i);
+    }
+    g.mesh = MeshView{d.geo, d.vx, d.pn, d.hrng, d.compact, d.tlist, d.seg, d.lines};
+    if (!r) r = g.upload_params(s, err);
+    if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = FPPG_ERR_CUDA;
+    if (r) {
+        g_create_err = err.empty() ? "batch allocation failed" : err;
+        delete b;
+        return r;
+    }
+    *out = b;
+    return FPPG_OK;
+}
+
+int fppg_batch_destroy(fppg_batch *b) {
+    if (!b) return FPPG_ERR_ARG;
+    cudaStreamSynchronize(b->stream);
+    delete b;
+    return FPPG_OK;
+}
+
+int fppg_batch_set_stream(fppg_batch *b, void *stream) {
+    if (!b) return FPPG_ERR_ARG;
+    b->stream = (cudaStream_t)stream;
+    return FPPG_OK;
+}
+
+int fppg_batch_set_graph_iters(fppg_batch *b, int32_t graph_iters) {
+    if (!b || graph_iters <= 0 || graph_iters > 100000) return FPPG_ERR_ARG;
+    if (b->group.graph && b->group.graph_iters != graph_iters) {
+        cudaGraphExecDestroy(b->group.graph);
+        b->group.graph = nullptr;
+    }
+    b->group.graph_iters = graph_iters;
+    return FPPG_OK;
+}
+
+int fppg_batch_time_force(fppg_batch *b, int32_t enable) {
+    if (!b) return FPPG_ERR_ARG;
+    if (b->group.time_force != (enable != 0) && b->group.graph) {
+        cudaGraphExecDestroy(b->group.graph);
+        b->group.graph = nullptr;
+    }
+    b->group.time_force = enable != 0;
+    return FPPG_OK;
+}
+
+static int build_graph(fppg_batch *b) {
+    Group &g = b->group;
+    if (g.graph_iters <= 0) g.graph_iters = 50;
+    if (!g.graph_stream) CUDA_OR(b->err, cudaStreamCreateWithFlags(&g.graph_stream, cudaStreamNonBlocking));
+    if (g.time_force) {
+        while ((int)g.ev.size() < 2 * g.graph_iters) {
+            cudaEvent_t e;
+            CUDA_OR(b->err, cudaEventCreate(&e));
+            g.ev.push_back(e);
+        }
+    }
+    g.ev_used = 0;
+    cudaGraph_t graph;
+    CUDA_OR(b->err, cudaStreamBeginCapture(g.graph_stream, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < g.graph_iters; it++) iterate(g, g.graph_stream, false);
+    CUDA_OR(b->err, cudaStreamEndCapture(g.graph_stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g.graph, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_OR(b->err, e);
+    return FPPG_OK;
+}
+
+int fppg_batch_relax(fppg_batch *b, int32_t n_iter, int32_t use_graph) {
+    if (!b) return FPPG_ERR_ARG;
+    if (n_iter < 0) return fail(b->err, FPPG_ERR_ARG, "n_iter < 0");
+    Group &g = b->group;
+    int32_t done = 0;
+    if (use_graph) {
+        if (!g.graph) {
+            int r = build_graph(b);
+            if (r) return r;
+        }
+        for (; done + g.graph_iters <= n_iter; done += g.graph_iters)
+            CUDA_OR(b->err, cudaGraphLaunch(g.graph, b->stream));
+    }
+    const bool t = g.time_force;
+    g.time_force = false;   // eager iterations are not timed
+    for (; done < n_iter; done++) iterate(g, b->stream, false);
+    g.time_force = t;
+    CUDA_OR(b->err, cudaGetLastError());
+    return FPPG_OK;
+}
+
+int fppg_batch_force_ms(fppg_batch *b, double *ms) {
+    if (!b || !ms) return FPPG_ERR_ARG;
+    Group &g = b->group;
+    if (!g.time_force || !g.graph || g.ev.size() < 2) return fail(b->err, FPPG_ERR_STATE, "force timing not active");
+    CUDA_OR(b->err, cudaStreamSynchronize(b->stream));
+    double tot = 0.0;
+    for (int i = 0; i + 1 < 2 * g.graph_iters; i += 2) {
+        float t = 0.f;
+        CUDA_OR(b->err, cudaEventElapsedTime(&t, g.ev[i], g.ev[i + 1]));
+        tot += t;
+    }
+    *ms = tot / g.graph_iters;
+    return FPPG_OK;
+}
+
+int fppg_batch_store(fppg_batch *b) {
+    if (!b) return FPPG_ERR_ARG;
+    cudaStream_t s = b->stream;
+    DevGroup &d = b->group.d;
+    for (size_t i = 0; i < b->ctxs.size(); i++) {
+        fppg_ctx *c = b->ctxs[i];
+        const int64_t cn = c->n;
+        if (!cn) continue;
+        CUDA_OR(b->err, cudaMemcpyAsync(c->group.d.pos, d.pos + b->off[i], sizeof(float4) * cn,
+                                        cudaMemcpyDeviceToDevice, s));
+        CUDA_OR(b->err, cudaMemcpyAsync(c->group.d.cons, d.cons + b->off[i], sizeof(int32_t) * cn,
+                                        cudaMemcpyDeviceToDevice, s));
+        k_set_body<<<nb(cn), 256, 0, s>>>(c->group.d.pos, cn, 0);
+    }
+    CUDA_OR(b->err, cudaStreamSynchronize(s));
+    return FPPG_OK;
+}
+
+int fppg_batch_load(fppg_batch *b) {
+    if (!b) return FPPG_ERR_ARG;
+    cudaStream_t s = b->stream;
+    DevGroup &d = b->group.d;
+    for (size_t i = 0; i < b->ctxs.size(); i++) {
+        fppg_ctx *c = b->ctxs[i];
+        const int64_t cn = c->n;
+        if (cn != b->off[i + 1] - b->off[i]) return fail(b->err, FPPG_ERR_STATE, "a body changed its particle count");
+        if (!cn) continue;
+        CUDA_OR(b->err, cudaMemcpyAsync(d.pos + b->off[i], c->group.d.pos, sizeof(float4) * cn,
+                                        cudaMemcpyDeviceToDevice, s));
+        CUDA_OR(b->err, cudaMemcpyAsync(d.cons + b->off[i], c->group.d.cons, sizeof(int32_t) * cn,
+                                        cudaMemcpyDeviceToDevice, s));
+        k_set_body<<<nb(cn), 256, 0, s>>>(d.pos + b->off[i], cn, (int)i);
+    }
+    CUDA_OR(b->err, cudaGetLastError());
+    return FPPG_OK;
+}
+
+int32_t fppg_batch_kernels_per_iter(const fppg_batch *b) {
+    // keys, 3 per radix pass, gather + ranges, force, step + projection
+    return b ? 4 + 3 * b->group.d.passes : -1;
+}
+
+int64_t fppg_batch_size(const fppg_batch *b) { return b ? b->group.d.N : -1; }
+
+const char *fppg_batch_last_error(const fppg_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+} // extern "C"

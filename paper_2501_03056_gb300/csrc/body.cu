@@ -1,0 +1,266 @@
+// Host side of a body (feature lines) and of a group (allocation, params).
+#include <algorithm>
+#include <cmath>
+
+#include "body.h"
+
+namespace fppg {
+
+namespace {
+int bits_for(uint64_t maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) b++;
+    return b;
+}
+} // namespace
+
+// Feature lines from the sorted feature-edge list (Sec. 3.2.2): walks that
+// start at singular vertices (feature degree 1 or > 2) in ascending vertex
+// order, each incident uncoloured edge in ascending edge order, continuing
+// through degree-2 vertices; then closed loops from the lowest uncoloured
+// edge.  Edges are coloured as they are walked.
+void Body::build_lines() {
+    const int64_t m = (int64_t)fe.size() / 2;
+    std::vector<int32_t> deg(nv, 0);
+    for (int64_t e = 0; e < m; e++) {
+        deg[fe[2 * e]]++;
+        deg[fe[2 * e + 1]]++;
+    }
+    std::vector<int64_t> first(nv + 1, 0);
+    for (int v = 0; v < nv; v++) first[v + 1] = first[v] + deg[v];
+    std::vector<int64_t> incident(2 * m), fill(first.begin(), first.end() - 1);
+    for (int64_t e = 0; e < m; e++) {
+        incident[fill[fe[2 * e]]++] = e;
+        incident[fill[fe[2 * e + 1]]++] = e;
+    }
+    sing.clear();
+    for (int v = 0; v < nv; v++)
+        if (deg[v] == 1 || deg[v] > 2) sing.push_back(v);
+    std::vector<char> used(m, 0);
+    line_first.clear();
+    line_nseg.clear();
+    line_closed.clear();
+    seg_v.clear();
+    auto other = [&](int64_t e, int32_t v) { return fe[2 * e] == v ? fe[2 * e + 1] : fe[2 * e]; };
+    auto next_edge = [&](int32_t v, int64_t from) {
+        return incident[first[v]] == from ? incident[first[v] + 1] : incident[first[v]];
+    };
+    for (int32_t s : sing) {
+        for (int64_t q = first[s]; q < first[s + 1]; q++) {
+            int64_t e = incident[q];
+            if (used[e]) continue;
+            const int64_t start = (int64_t)seg_v.size() / 2;
+            int32_t cur = s;
+            while (true) {
+                used[e] = 1;
+                const int32_t nxt = other(e, cur);
+                seg_v.push_back(cur);
+                seg_v.push_back(nxt);
+                if (deg[nxt] != 2) break;
+                const int64_t e2 = next_edge(nxt, e);
+                if (used[e2]) break;
+                e = e2;
+                cur = nxt;
+            }
+            line_first.push_back(start);
+            line_nseg.push_back((int64_t)seg_v.size() / 2 - start);
+            line_closed.push_back(0);
+        }
+    }
+    for (int64_t e0 = 0; e0 < m; e0++) {
+        if (used[e0]) continue;
+        const int64_t start = (int64_t)seg_v.size() / 2;
+        const int32_t v0 = fe[2 * e0];
+        int32_t cur = v0;
+        int64_t e = e0;
+        int closed = 0;
+        while (true) {
+            used[e] = 1;
+            const int32_t nxt = other(e, cur);
+            seg_v.push_back(cur);
+            seg_v.push_back(nxt);
+            if (nxt == v0) {
+                closed = 1;
+                break;
+            }
+            const int64_t e2 = next_edge(nxt, e);
+            if (used[e2]) break;
+            e = e2;
+            cur = nxt;
+        }
+        line_first.push_back(start);
+        line_nseg.push_back((int64_t)seg_v.size() / 2 - start);
+        line_closed.push_back(closed);
+    }
+    nseg = (int)(seg_v.size() / 2);
+    nlines = (int)line_first.size();
+    has_features = true;
+}
+
+int Body::upload_lines(cudaStream_t s, std::string &err) {
+    if (seg) cudaFree(seg);
+    if (lines) cudaFree(lines);
+    seg = nullptr;
+    lines = nullptr;
+    std::vector<float4> hs(3 * (size_t)std::max(nseg, 1));
+    std::vector<int2> hl((size_t)std::max(nlines, 1));
+    for (int l = 0; l < nlines; l++) {
+        hl[l] = make_int2((int)line_first[l], (int)line_nseg[l]);
+        for (int64_t q = line_first[l]; q < line_first[l] + line_nseg[l]; q++) {
+            const float *a = &verts_host[3 * (size_t)seg_v[2 * q]];
+            const float *b = &verts_host[3 * (size_t)seg_v[2 * q + 1]];
+            double e[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+            double len = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            float lb;
+            int li = l;
+            memcpy(&lb, &li, 4);
+            hs[3 * q] = make_float4(a[0], a[1], a[2], lb);
+            hs[3 * q + 1] = make_float4(b[0], b[1], b[2], 0.f);
+            hs[3 * q + 2] = len > 0 ? make_float4((float)(e[0] / len), (float)(e[1] / len), (float)(e[2] / len),
+                                                  (float)len)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    if (cudaMalloc(&seg, sizeof(float4) * hs.size()) != cudaSuccess ||
+        cudaMalloc(&lines, sizeof(int2) * hl.size()) != cudaSuccess) {
+        err = "feature lines: out of device memory";
+        return 3;
+    }
+    cudaMemcpyAsync(seg, hs.data(), sizeof(float4) * hs.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(lines, hl.data(), sizeof(int2) * hl.size(), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        err = std::string("feature lines: ") + cudaGetErrorString(e);
+        return 4;
+    }
+    return 0;
+}
+
+static double host_alpha3(double h) { return 21.0 / (16.0 * M_PI * h * h * h); }
+
+static double host_W(double r, double h) {
+    double q = r / h;
+    if (q > 2.0) return 0.0;
+    double t = 1.0 - 0.5 * q;
+    return host_alpha3(h) * t * t * t * t * (2.0 * q + 1.0);
+}
+
+// ideal kernel sum of a perfect lattice of spacing dx in dim dimensions
+static double lattice_w0(double dx, double h, int dim) {
+    int m = (int)std::ceil(2.0 * h / dx) + 1;
+    double s = 0.0;
+    for (int i = -m; i <= m; i++)
+        for (int j = (dim >= 2 ? -m : 0); j <= (dim >= 2 ? m : 0); j++)
+            for (int k = (dim >= 3 ? -m : 0); k <= (dim >= 3 ? m : 0); k++)
+                s += host_W(dx * std::sqrt((double)(i * i + j * j + k * k)), h);
+    return s;
+}
+
+AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, int fixed_features) {
+    AsmParams A;
+    memset(&A, 0, sizeof(A));
+    for (int k = 0; k < 3; k++) {
+        A.ng_o[k] = b.ng_o[k];
+        A.ng_n[k] = b.ng_n[k];
+        A.tg_o[k] = b.tg_o[k];
+        A.tg_n[k] = b.tg_n[k];
+    }
+    A.ng_inv = b.ng_inv;
+    A.tg_inv = b.tg_inv;
+    A.key_base = key_base;
+    A.hash_mask = (uint32_t)(b.hash_size - 1);
+    A.nt = b.nt;
+    A.nv = b.nv;
+    A.nseg = b.nseg;
+    A.nlines = b.nlines;
+    A.fixed_features = fixed_features;
+    const double h = (double)b.h;
+    A.h = b.h;
+    A.R2 = b.R2;
+    A.half_inv_h = (float)(1.0 / (2.0 * h));
+    A.alpha = (float)host_alpha3(h);
+    A.w_zero = A.alpha;
+    A.force_scale = (float)(5.0 * host_alpha3(h) / (h * h));
+    A.step_h = (float)(h / 16.0);
+    A.dx = b.dx;
+    A.w0[0] = (float)lattice_w0((double)b.dx, h, 2);
+    A.w0[1] = (float)lattice_w0((double)b.dx, h, 3);
+    A.w0[2] = (float)lattice_w0((double)b.dx, h, 1);
+    A.p_begin = p_begin;
+    A.p_end = p_end;
+    return A;
+}
+
+#define CKA(x)                                                                  \
+    do {                                                                        \
+        cudaError_t e_ = (x);                                                   \
+        if (e_ != cudaSuccess) {                                                \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_);              \
+            return e_ == cudaErrorMemoryAllocation ? 3 : 4;                     \
+        }                                                                       \
+    } while (0)
+
+int Group::alloc_particles(int64_t N, std::string &err) {
+    DevGroup &g = d;
+    void *old[] = {g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.hist, g.rho_s};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    g.N = N;
+    const size_t n1 = (size_t)std::max<int64_t>(N, 1);
+    g.n_tiles = (int)std::max<int64_t>(radix_tiles(N), 1);
+    g.key_bits = bits_for((uint64_t)std::max<int64_t>(g.total_cells - 1, 1));
+    g.passes = (g.key_bits + 7) / 8;
+    CKA(cudaMalloc(&g.pos, sizeof(float4) * n1));
+    CKA(cudaMalloc(&g.cons, sizeof(int32_t) * n1));
+    for (int k = 0; k < 2; k++) {
+        CKA(cudaMalloc(&g.key[k], sizeof(uint32_t) * n1));
+        CKA(cudaMalloc(&g.id[k], sizeof(uint32_t) * n1));
+    }
+    CKA(cudaMalloc(&g.pos_s, sizeof(float4) * n1));
+    CKA(cudaMalloc(&g.acc_s, sizeof(float4) * n1));
+    CKA(cudaMalloc(&g.rho_s, sizeof(float) * n1));
+    CKA(cudaMalloc(&g.hist, sizeof(uint32_t) * 256 * (size_t)g.n_tiles));
+    if (!g.totals) CKA(cudaMalloc(&g.totals, sizeof(uint32_t) * 256));
+    if (!g.cells) {
+        CKA(cudaMalloc(&g.cells, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));
+        CKA(cudaMemset(g.cells, 0, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));
+        CKA(cudaMalloc(&g.epoch, sizeof(uint32_t)));
+        CKA(cudaMemset(g.epoch, 0, sizeof(uint32_t)));
+    }
+    if (!g.amax) {
+        CKA(cudaMalloc(&g.amax, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
+        CKA(cudaMalloc(&g.maxdisp, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
+        CKA(cudaMemset(g.amax, 0, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
+        CKA(cudaMemset(g.maxdisp, 0, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
+    }
+    return 0;
+}
+
+int Group::upload_params(cudaStream_t s, std::string &err) {
+    if (!d.params) CKA(cudaMalloc(&d.params, sizeof(AsmParams) * (size_t)std::max<int>(d.B, 1)));
+    CKA(cudaMemcpyAsync(d.params, hp.data(), sizeof(AsmParams) * hp.size(), cudaMemcpyHostToDevice, s));
+    CKA(cudaStreamSynchronize(s));
+    return 0;
+}
+
+void Group::free_all() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    if (graph_stream) cudaStreamDestroy(graph_stream);
+    graph_stream = nullptr;
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    DevGroup &g = d;
+    void *ptrs[] = {g.params, g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.cells,
+                    g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (owns_mesh) {
+        void *m[] = {g.geo, g.vx, g.pn, g.hrng, g.compact, g.tlist, g.seg, g.lines};
+        for (void *p : m)
+            if (p) cudaFree(p);
+    }
+    d = DevGroup();
+}
+
+} // namespace fppg

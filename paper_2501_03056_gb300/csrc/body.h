@@ -1,0 +1,99 @@
+// One body (mesh + grids + feature lines) and the group runtime that relaxes
+// one or many bodies with the same launches.
+#pragma once
+
+#include "fppg_internal.cuh"
+
+namespace fppg {
+
+void grid_setup(const float *bbmin, const float *bbmax, float cell, int margin, float *o, float *inv, int *n);
+
+struct Body {
+    int nv = 0, nt = 0;
+    float dx = 0, h = 0;
+    // triangle grid (cell dx, 2 cells of margin)
+    float tg_o[3] = {0, 0, 0};
+    float tg_inv = 0;
+    int tg_n[3] = {0, 0, 0};
+    // neighbour grid (cell 2h (1 + 2^-8), 1 cell of margin)
+    float ng_o[3] = {0, 0, 0};
+    float ng_inv = 0, ng_cell = 0, R2 = 0;
+    int ng_n[3] = {0, 0, 0};
+    // device mesh
+    float *d_verts = nullptr;
+    int32_t *d_tris = nullptr;
+    float4 *geo = nullptr, *vx = nullptr, *pn = nullptr;
+    double *nu = nullptr;        // FP64 unit normals (set-up only)
+    uint64_t *ekey = nullptr;    // sorted edge keys v1 * nv + v2
+    uint32_t *eval = nullptr;    // 3 t + k of each sorted edge entry
+    uint2 *hrng = nullptr;
+    int64_t hash_size = 0;
+    uint4 *compact = nullptr;
+    int64_t ncompact = 0;
+    int32_t *tlist = nullptr;
+    int64_t npairs = 0;
+    // feature lines (host copies + device segments)
+    bool has_features = false;
+    std::vector<int32_t> fe;           // [nfe][2] sorted
+    std::vector<int32_t> sing;         // singular vertices
+    std::vector<int64_t> line_first, line_nseg;
+    std::vector<int32_t> line_closed;
+    std::vector<int32_t> seg_v;        // [nseg][2]
+    std::vector<float> verts_host;     // FP32 copy of the mesh vertices
+    float4 *seg = nullptr;
+    int2 *lines = nullptr;
+    int nseg = 0, nlines = 0;
+
+    int build_mesh(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,
+                   cudaStream_t s, std::string &err);
+    int extract_features(float deg, cudaStream_t s, std::string &err);
+    void build_lines();
+    int upload_lines(cudaStream_t s, std::string &err);
+    void free_mesh();
+    ~Body() { free_mesh(); }
+};
+
+// Host description of one body inside a group.
+AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, int fixed_features);
+
+struct Group {
+    DevGroup d;
+    std::vector<AsmParams> hp;    // host copy of the per-body parameters
+    MeshView mesh{};
+    bool owns_mesh = false;       // batches own concatenated copies
+    // timing of the force kernel inside a relaxation (optional)
+    bool time_force = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    // CUDA graph of graph_iters iterations
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    cudaStream_t graph_stream = nullptr;
+
+    int alloc_particles(int64_t N, std::string &err);
+    int upload_params(cudaStream_t s, std::string &err);
+    void free_all();
+    ~Group() { free_all(); }
+};
+
+// one relaxation iteration of every body of the group (A1-A6)
+void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg = nullptr);
+// A1-A3 only (keys, sort, gather + cell ranges); returns the buffer index
+// holding the sorted keys / ids
+int build_grid(Group &g, cudaStream_t s);
+// A4 into acc_s (and counts when non-null)
+void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s = nullptr);
+// energy-descent acceleration -dE/dx into acc_s
+void energy_accel(Group &g, cudaStream_t s);
+// debug helpers
+void unpermute(Group &g, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s, int32_t *count_out);
+void project_points(Group &g, const float *y, const int32_t *cls, const int32_t *cons_in, int64_t n, float *x,
+                    int32_t *cons_out, int32_t *ok, cudaStream_t s);
+// uniformity statistics into host doubles (see fppg_stats_t)
+int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, double *maxdisp, int64_t *cnt,
+          std::string &err);
+// energy and gradients (positions y, vertex coordinates verts of body 0)
+int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
+           cudaStream_t s, std::string &err);
+
+} // namespace fppg

@@ -1,0 +1,467 @@
+// Set-up of a body's device geometry (Sec. 3.1, Sec. 3.2.2).
+//
+// Compiled with -fmad=false: every FP64 expression here is evaluated
+// operation by operation in the order written, so the unit normals and the
+// dihedral test decide exactly like any other IEEE implementation of the
+// same formulas.
+//   k_tri_prep      unit normals, in-plane edge normals, vertex copies,
+//                   edge keys v1 * nv + v2 (v1 < v2) and corner keys
+//   k_edge_runs     per edge (sorted keys): edge pseudonormal = normalised
+//                   sum of the unit normals of its faces
+//   k_vertex_runs   per vertex: angle-weighted pseudonormal
+//   k_bin_*         triangle-box overlap by separating axes (Sec. 3.1.2)
+//                   on cells inflated by 1e-6 dx, emitted as (cell, tri)
+//   compact + hash  C_compact and the Eq. 10 hash with H_begin/H_length
+//   k_feature_flags dihedral rule on the sorted edge list
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "body.h"
+
+namespace fppg {
+
+namespace {
+
+struct d3 {
+    double x, y, z;
+};
+__device__ inline d3 mk(double x, double y, double z) { return {x, y, z}; }
+__device__ inline d3 sub(d3 a, d3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ inline double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ inline d3 cross(d3 a, d3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ inline d3 vload(const float *v, int i) { return {(double)v[3 * i], (double)v[3 * i + 1], (double)v[3 * i + 2]}; }
+__device__ inline float4 f4(d3 a, float w) { return make_float4((float)a.x, (float)a.y, (float)a.z, w); }
+
+__global__ void k_tri_prep(const float *__restrict__ verts, const int32_t *__restrict__ tris, int nt, int nv,
+                           float4 *__restrict__ geo, float4 *__restrict__ vx, double *__restrict__ nu,
+                           uint64_t *__restrict__ ekey, uint32_t *__restrict__ ckey) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int id[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+    d3 v[3] = {vload(verts, id[0]), vload(verts, id[1]), vload(verts, id[2])};
+    d3 e1 = sub(v[1], v[0]), e2 = sub(v[2], v[0]);
+    d3 n = cross(e1, e2);
+    double len = sqrt(dot(n, n));
+    d3 u = len > 0.0 ? mk(n.x / len, n.y / len, n.z / len) : mk(0.0, 0.0, 0.0);
+    nu[3 * t] = u.x;
+    nu[3 * t + 1] = u.y;
+    nu[3 * t + 2] = u.z;
+    geo[5 * t + 0] = f4(v[0], 0.0f);
+    geo[5 * t + 1] = f4(u, 0.0f);
+    for (int k = 0; k < 3; k++) {
+        d3 e = sub(v[(k + 1) % 3], v[k]);
+        d3 m = cross(u, e);
+        double ml = sqrt(dot(m, m));
+        m = ml > 0.0 ? mk(m.x / ml, m.y / ml, m.z / ml) : mk(0.0, 0.0, 0.0);
+        double ck = dot(sub(v[k], v[0]), m);
+        // a degenerate triangle is never projectable: its first edge test
+        // can never pass
+        float w = (float)ck;
+        if (len <= 0.0 && k == 1) w = INFINITY;
+        geo[5 * t + 2 + k] = f4(m, k == 0 ? 0.0f : w);
+        vx[3 * t + k] = f4(v[k], __int_as_float(id[k]));
+        int a = id[k], b = id[(k + 1) % 3];
+        uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
+        ekey[3 * t + k] = lo * (uint64_t)nv + hi;
+        ckey[3 * t + k] = (uint32_t)id[k];
+    }
+}
+
+__global__ void k_edge_runs(const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, int64_t m,
+                            const double *__restrict__ nu, float4 *__restrict__ pn) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || (i > 0 && key[i] == key[i - 1])) return;
+    d3 s = mk(0.0, 0.0, 0.0);
+    int64_t j = i;
+    for (; j < m && key[j] == key[i]; j++) {
+        uint32_t t = val[j] / 3;
+        s = mk(s.x + nu[3 * t], s.y + nu[3 * t + 1], s.z + nu[3 * t + 2]);
+    }
+    double len = sqrt(dot(s, s));
+    d3 e = len > 0.0 ? mk(s.x / len, s.y / len, s.z / len) : mk(0.0, 0.0, 0.0);
+    for (int64_t q = i; q < j; q++) {
+        uint32_t t = val[q] / 3, k = val[q] % 3;
+        pn[6 * t + k] = f4(e, 0.0f);
+    }
+}
+
+__global__ void k_vertex_runs(const uint32_t *__restrict__ key, const uint32_t *__restrict__ val, int64_t m,
+                              const float *__restrict__ verts, const int32_t *__restrict__ tris,
+                              const double *__restrict__ nu, float4 *__restrict__ vpn) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || (i > 0 && key[i] == key[i - 1])) return;
+    d3 s = mk(0.0, 0.0, 0.0);
+    for (int64_t j = i; j < m && key[j] == key[i]; j++) {
+        uint32_t t = val[j] / 3, k = val[j] % 3;
+        d3 p = vload(verts, tris[3 * t + k]);
+        d3 u = sub(vload(verts, tris[3 * t + (k + 1) % 3]), p);
+        d3 w = sub(vload(verts, tris[3 * t + (k + 2) % 3]), p);
+        double lu = sqrt(dot(u, u)), lw = sqrt(dot(w, w));
+        double c = (lu > 0.0 && lw > 0.0) ? dot(u, w) / (lu * lw) : 1.0;
+        c = fmin(1.0, fmax(-1.0, c));
+        double ang = acos(c);
+        s = mk(s.x + ang * nu[3 * t], s.y + ang * nu[3 * t + 1], s.z + ang * nu[3 * t + 2]);
+    }
+    double len = sqrt(dot(s, s));
+    d3 e = len > 0.0 ? mk(s.x / len, s.y / len, s.z / len) : mk(0.0, 0.0, 0.0);
+    vpn[key[i]] = f4(e, 0.0f);
+}
+
+__global__ void k_fill_vertex_pn(const int32_t *__restrict__ tris, int nt, const float4 *__restrict__ vpn,
+                                 float4 *__restrict__ pn) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    for (int k = 0; k < 3; k++) pn[6 * t + 3 + k] = vpn[tris[3 * t + k]];
+}
+
+// ---- triangle-box overlap (separating axes) ---------------------------------
+__device__ inline bool axis_separates(d3 ax, d3 v0, d3 v1, d3 v2, double hs) {
+    double p0 = dot(ax, v0), p1 = dot(ax, v1), p2 = dot(ax, v2);
+    double mn = fmin(p0, fmin(p1, p2)), mx = fmax(p0, fmax(p1, p2));
+    double r = hs * (fabs(ax.x) + fabs(ax.y) + fabs(ax.z));
+    return mn > r || mx < -r;
+}
+
+__device__ bool tri_box_overlap(d3 ctr, double hs, d3 a, d3 b, d3 c) {
+    d3 v0 = sub(a, ctr), v1 = sub(b, ctr), v2 = sub(c, ctr);
+    d3 f[3] = {sub(v1, v0), sub(v2, v1), sub(v0, v2)};
+    double vk[3][3] = {{v0.x, v1.x, v2.x}, {v0.y, v1.y, v2.y}, {v0.z, v1.z, v2.z}};
+    for (int k = 0; k < 3; k++) {
+        double mn = fmin(vk[k][0], fmin(vk[k][1], vk[k][2])), mx = fmax(vk[k][0], fmax(vk[k][1], vk[k][2]));
+        if (mn > hs || mx < -hs) return false;
+    }
+    d3 n = cross(f[0], f[1]);
+    if (fabs(dot(n, v0)) > hs * (fabs(n.x) + fabs(n.y) + fabs(n.z))) return false;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            d3 e = mk(i == 0 ? 1.0 : 0.0, i == 1 ? 1.0 : 0.0, i == 2 ? 1.0 : 0.0);
+            if (axis_separates(cross(e, f[j]), v0, v1, v2, hs)) return false;
+        }
+    return true;
+}
+
+struct TriGrid {
+    float o[3];
+    int n[3];
+    double cell;
+};
+
+template <bool EMIT>
+__global__ void k_bin(const float *__restrict__ verts, const int32_t *__restrict__ tris, int nt, TriGrid g,
+                      uint32_t *__restrict__ count, const uint32_t *__restrict__ offs, uint32_t *__restrict__ pkey,
+                      uint32_t *__restrict__ ptri) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    d3 a = vload(verts, tris[3 * t]), b = vload(verts, tris[3 * t + 1]), c = vload(verts, tris[3 * t + 2]);
+    double av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, cv[3] = {c.x, c.y, c.z};
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; k++) {
+        double mn = fmin(av[k], fmin(bv[k], cv[k])), mx = fmax(av[k], fmax(bv[k], cv[k]));
+        lo[k] = (int)floor((mn - (double)g.o[k]) / g.cell) - 1;
+        hi[k] = (int)floor((mx - (double)g.o[k]) / g.cell) + 1;
+        lo[k] = max(lo[k], 0);
+        hi[k] = min(hi[k], g.n[k] - 1);
+    }
+    double hs = 0.5 * g.cell + 1e-6 * g.cell;
+    uint32_t m = 0, o = EMIT ? offs[t] : 0u;
+    for (int z = lo[2]; z <= hi[2]; z++)
+        for (int y = lo[1]; y <= hi[1]; y++)
+            for (int x = lo[0]; x <= hi[0]; x++) {
+                d3 ctr = mk((double)g.o[0] + (x + 0.5) * g.cell, (double)g.o[1] + (y + 0.5) * g.cell,
+                            (double)g.o[2] + (z + 0.5) * g.cell);
+                if (!tri_box_overlap(ctr, hs, a, b, c)) continue;
+                if (EMIT) {
+                    pkey[o + m] = (uint32_t)x + (uint32_t)g.n[0] * ((uint32_t)y + (uint32_t)g.n[1] * (uint32_t)z);
+                    ptri[o + m] = (uint32_t)t;
+                }
+                m++;
+            }
+    if (!EMIT) count[t] = m;
+}
+
+__global__ void k_run_flags(const uint32_t *__restrict__ key, int64_t m, uint32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+}
+
+// occupied cell -> compact entry {cell key, tlist begin, length, hash}
+__global__ void k_compact(const uint32_t *__restrict__ key, int64_t m, const uint32_t *__restrict__ flag,
+                          const uint32_t *__restrict__ pos, TriGrid g, uint32_t hmask, uint4 *__restrict__ compact,
+                          uint32_t *__restrict__ hkey) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !flag[i]) return;
+    int64_t j = i;
+    while (j < m && key[j] == key[i]) j++;
+    uint32_t c = key[i];
+    uint32_t x = c % (uint32_t)g.n[0], yz = c / (uint32_t)g.n[0];
+    uint32_t y = yz % (uint32_t)g.n[1], z = yz / (uint32_t)g.n[1];
+    uint32_t h = (kHashP1 * x + kHashP2 * y + kHashP3 * z) & hmask;   // Eq. 10
+    compact[pos[i]] = make_uint4(c, (uint32_t)i, (uint32_t)(j - i), h);
+    hkey[pos[i]] = h;
+}
+
+__global__ void k_gather_compact(const uint4 *__restrict__ in, const uint32_t *__restrict__ perm, int64_t m,
+                                 uint4 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) {
+        uint4 e = in[perm[i]];
+        e.w = 0;
+        out[i] = e;
+    }
+}
+
+__global__ void k_hash_ranges(const uint32_t *__restrict__ hsorted, int64_t m, uint2 *__restrict__ hrng) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || (i > 0 && hsorted[i] == hsorted[i - 1])) return;
+    int64_t j = i;
+    while (j < m && hsorted[j] == hsorted[i]) j++;
+    hrng[hsorted[i]] = make_uint2((uint32_t)i, (uint32_t)(j - i));
+}
+
+__global__ void k_feature_flags(const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, int64_t m,
+                                const double *__restrict__ nu, double cthr, uint32_t *__restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t f = 0;
+    if (i == 0 || key[i] != key[i - 1]) {
+        int64_t j = i;
+        while (j < m && key[j] == key[i]) j++;
+        if (j - i != 2) {
+            f = 1; // boundary or non-manifold edge
+        } else {
+            uint32_t t1 = val[i] / 3, t2 = val[i + 1] / 3;
+            double d = nu[3 * t1] * nu[3 * t2] + nu[3 * t1 + 1] * nu[3 * t2 + 1] + nu[3 * t1 + 2] * nu[3 * t2 + 2];
+            f = d < cthr ? 1u : 0u;
+        }
+    }
+    flag[i] = f;
+}
+
+__global__ void k_feature_emit(const uint64_t *__restrict__ key, int64_t m, const uint32_t *__restrict__ flag,
+                               const uint32_t *__restrict__ pos, int nv, int32_t *__restrict__ fe) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !flag[i]) return;
+    uint64_t k = key[i];
+    fe[2 * pos[i]] = (int32_t)(k / (uint64_t)nv);
+    fe[2 * pos[i] + 1] = (int32_t)(k % (uint64_t)nv);
+}
+
+inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+int bits_for(uint64_t maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) b++;
+    return b;
+}
+
+} // namespace
+
+// Grid rule shared with every other implementation of the method:
+// origin = bbmin - margin * cell (FP64, rounded to FP32), inv = 1 / cell
+// (FP64, rounded), n = ceil((bbmax - origin) / cell) + margin.
+void grid_setup(const float *bbmin, const float *bbmax, float cell, int margin, float *o, float *inv, int *n) {
+    for (int a = 0; a < 3; a++) {
+        o[a] = (float)((double)bbmin[a] - (double)margin * (double)cell);
+        n[a] = (int)std::ceil(((double)bbmax[a] - (double)o[a]) / (double)cell) + margin;
+    }
+    *inv = (float)(1.0 / (double)cell);
+}
+
+#define CK(x)                                                                          \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) {                                                       \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_);                     \
+            return e_ == cudaErrorMemoryAllocation ? 3 : 4;                            \
+        }                                                                              \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T **p, int64_t n) {
+    return cudaMalloc((void **)p, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+}
+
+void Body::free_mesh() {
+    void *ptrs[] = {d_verts, d_tris, geo, vx, pn, hrng, compact, tlist, nu, ekey, eval, seg, lines};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    d_verts = nullptr;
+    d_tris = nullptr;
+    geo = vx = pn = nullptr;
+    hrng = nullptr;
+    compact = nullptr;
+    tlist = nullptr;
+    nu = nullptr;
+    ekey = nullptr;
+    eval = nullptr;
+    seg = nullptr;
+    lines = nullptr;
+}
+
+int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_host, int64_t nt_, float dx_,
+                     float h_, cudaStream_t s, std::string &err) {
+    nv = (int)nv_;
+    nt = (int)nt_;
+    dx = dx_;
+    h = h_;
+    float bbmin[3] = {INFINITY, INFINITY, INFINITY}, bbmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nv_; i++)
+        for (int k = 0; k < 3; k++) {
+            bbmin[k] = std::min(bbmin[k], verts_host[3 * i + k]);
+            bbmax[k] = std::max(bbmax[k], verts_host[3 * i + k]);
+        }
+    grid_setup(bbmin, bbmax, dx, 2, tg_o, &tg_inv, tg_n);
+    float R = 2.0f * h;
+    R2 = (float)((double)R * (double)R);
+    ng_cell = (float)((double)R * (1.0 + 1.0 / 256.0));
+    grid_setup(bbmin, bbmax, ng_cell, 1, ng_o, &ng_inv, ng_n);
+    if ((double)tg_n[0] * tg_n[1] * tg_n[2] >= 4294967295.0 || (double)ng_n[0] * ng_n[1] * ng_n[2] >= 2147483647.0) {
+        err = "grid too large for 32-bit cell keys (dx too small for the mesh extent)";
+        return 1;
+    }
+    CK(dalloc(&d_verts, 3 * (int64_t)nv));
+    CK(dalloc(&d_tris, 3 * (int64_t)nt));
+    CK(cudaMemcpyAsync(d_verts, verts_host, sizeof(float) * 3 * nv, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_tris, tris_host, sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice, s));
+    CK(dalloc(&geo, 5 * (int64_t)nt));
+    CK(dalloc(&vx, 3 * (int64_t)nt));
+    CK(dalloc(&pn, 6 * (int64_t)nt));
+    CK(dalloc(&nu, 3 * (int64_t)nt));
+    const int64_t m = 3 * (int64_t)nt;
+    uint64_t *ek[2] = {nullptr, nullptr};
+    uint32_t *ev[2] = {nullptr, nullptr}, *ck[2] = {nullptr, nullptr}, *cv[2] = {nullptr, nullptr};
+    uint32_t *hist = nullptr, *tot = nullptr;
+    float4 *vpn = nullptr;
+    CK(dalloc(&ek[0], m));
+    CK(dalloc(&ek[1], m));
+    CK(dalloc(&ev[0], m));
+    CK(dalloc(&ev[1], m));
+    CK(dalloc(&ck[0], m));
+    CK(dalloc(&ck[1], m));
+    CK(dalloc(&cv[0], m));
+    CK(dalloc(&cv[1], m));
+    CK(dalloc(&vpn, nv));
+    int64_t tiles = radix_tiles(m);
+    CK(dalloc(&hist, 256 * std::max<int64_t>(tiles, 1)));
+    CK(dalloc(&tot, 256));
+    k_tri_prep<<<blocks(nt), 256, 0, s>>>(d_verts, d_tris, nt, nv, geo, vx, nu, ek[0], ck[0]);
+    int eb = radix_sort_u64(ek, ev, true, m, bits_for((uint64_t)nv * (uint64_t)nv), hist, tot, s);
+    k_edge_runs<<<blocks(m), 256, 0, s>>>(ek[eb], ev[eb], m, nu, pn);
+    int cb = radix_sort_u32(ck, cv, true, m, bits_for((uint64_t)nv), hist, tot, s);
+    k_vertex_runs<<<blocks(m), 256, 0, s>>>(ck[cb], cv[cb], m, d_verts, d_tris, nu, vpn);
+    k_fill_vertex_pn<<<blocks(nt), 256, 0, s>>>(d_tris, nt, vpn, pn);
+    // keep the sorted edge list for feature extraction
+    ekey = ek[eb];
+    eval = ev[eb];
+    cudaFree(ek[eb ^ 1]);
+    cudaFree(ev[eb ^ 1]);
+    cudaFree(ck[0]);
+    cudaFree(ck[1]);
+    cudaFree(cv[0]);
+    cudaFree(cv[1]);
+
+    // ---- triangle binning, C_compact and the hash -------------------------
+    TriGrid g;
+    for (int k = 0; k < 3; k++) {
+        g.o[k] = tg_o[k];
+        g.n[k] = tg_n[k];
+    }
+    g.cell = (double)dx;
+    uint32_t *cnt = nullptr, *off = nullptr, *total = nullptr, *scratch = nullptr;
+    int64_t sc = scan_tmp_elems(std::max<int64_t>(nt, 1) * 64);
+    CK(dalloc(&cnt, nt));
+    CK(dalloc(&off, nt));
+    CK(dalloc(&total, 1));
+    CK(dalloc(&scratch, sc));
+    k_bin<false><<<blocks(nt, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, cnt, nullptr, nullptr, nullptr);
+    exclusive_scan_u32(cnt, off, nt, total, scratch, sc, s);
+    uint32_t npairs_h = 0;
+    CK(cudaMemcpyAsync(&npairs_h, total, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    npairs = npairs_h;
+    uint32_t *pk[2] = {nullptr, nullptr}, *pt[2] = {nullptr, nullptr}, *flag = nullptr, *pos = nullptr;
+    CK(dalloc(&pk[0], npairs));
+    CK(dalloc(&pk[1], npairs));
+    CK(dalloc(&pt[0], npairs));
+    CK(dalloc(&pt[1], npairs));
+    CK(dalloc(&flag, npairs));
+    CK(dalloc(&pos, npairs));
+    k_bin<true><<<blocks(nt, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, nullptr, off, pk[0], pt[0]);
+    int64_t pt_tiles = radix_tiles(npairs);
+    cudaFree(hist);
+    CK(dalloc(&hist, 256 * std::max<int64_t>(std::max(pt_tiles, tiles), 1)));
+    int pb = radix_sort_u32(pk, pt, false, npairs, bits_for((uint64_t)tg_n[0] * tg_n[1] * tg_n[2]), hist, tot, s);
+    CK(dalloc(&tlist, npairs));
+    CK(cudaMemcpyAsync(tlist, pt[pb], sizeof(uint32_t) * npairs, cudaMemcpyDeviceToDevice, s));
+    k_run_flags<<<blocks(npairs), 256, 0, s>>>(pk[pb], npairs, flag);
+    int64_t sc2 = scan_tmp_elems(std::max<int64_t>(npairs, 1));
+    if (sc2 > sc) {
+        cudaFree(scratch);
+        CK(dalloc(&scratch, sc2));
+        sc = sc2;
+    }
+    exclusive_scan_u32(flag, pos, npairs, total, scratch, sc, s);
+    uint32_t nocc = 0;
+    CK(cudaMemcpyAsync(&nocc, total, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ncompact = nocc;
+    hash_size = 1;
+    while (hash_size < 2 * std::max<int64_t>(ncompact, 1)) hash_size <<= 1;
+    uint4 *cmp_unsorted = nullptr;
+    uint32_t *hk[2] = {nullptr, nullptr}, *hv[2] = {nullptr, nullptr};
+    CK(dalloc(&cmp_unsorted, ncompact));
+    CK(dalloc(&compact, ncompact));
+    CK(dalloc(&hk[0], ncompact));
+    CK(dalloc(&hk[1], ncompact));
+    CK(dalloc(&hv[0], ncompact));
+    CK(dalloc(&hv[1], ncompact));
+    CK(dalloc(&hrng, hash_size));
+    CK(cudaMemsetAsync(hrng, 0, sizeof(uint2) * hash_size, s));
+    k_compact<<<blocks(npairs), 256, 0, s>>>(pk[pb], npairs, flag, pos, g, (uint32_t)(hash_size - 1), cmp_unsorted,
+                                              hk[0]);
+    int hb = radix_sort_u32(hk, hv, true, ncompact, bits_for((uint64_t)hash_size - 1), hist, tot, s);
+    k_gather_compact<<<blocks(ncompact), 256, 0, s>>>(cmp_unsorted, hv[hb], ncompact, compact);
+    k_hash_ranges<<<blocks(ncompact), 256, 0, s>>>(hk[hb], ncompact, hrng);
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    void *tmp[] = {cnt, off, total, scratch, pk[0], pk[1], pt[0], pt[1], flag, pos, cmp_unsorted,
+                   hk[0], hk[1], hv[0], hv[1], hist, tot, vpn};
+    for (void *p : tmp) cudaFree(p);
+    return 0;
+}
+
+// Feature edges on the device (sorted (v1, v2)), lines by a colouring walk on
+// the host (a few thousand edges at most), segments back to the device.
+int Body::extract_features(float deg, cudaStream_t s, std::string &err) {
+    const int64_t m = 3 * (int64_t)nt;
+    double cthr = std::cos((double)deg * M_PI / 180.0);
+    uint32_t *flag = nullptr, *pos = nullptr, *total = nullptr, *scratch = nullptr;
+    int32_t *dfe = nullptr;
+    int64_t sc = scan_tmp_elems(m);
+    CK(dalloc(&flag, m));
+    CK(dalloc(&pos, m));
+    CK(dalloc(&total, 1));
+    CK(dalloc(&scratch, sc));
+    k_feature_flags<<<blocks(m), 256, 0, s>>>(ekey, eval, m, nu, cthr, flag);
+    exclusive_scan_u32(flag, pos, m, total, scratch, sc, s);
+    uint32_t nfe = 0;
+    CK(cudaMemcpyAsync(&nfe, total, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(dalloc(&dfe, 2 * (int64_t)nfe));
+    k_feature_emit<<<blocks(m), 256, 0, s>>>(ekey, m, flag, pos, nv, dfe);
+    fe.assign(2 * (size_t)nfe, 0);
+    if (nfe) CK(cudaMemcpyAsync(fe.data(), dfe, sizeof(int32_t) * 2 * nfe, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(flag);
+    cudaFree(pos);
+    cudaFree(total);
+    cudaFree(scratch);
+    cudaFree(dfe);
+    build_lines();
+    return upload_lines(s, err);
+}
+
+} // namespace fppg

