@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--iters-per-step", type=int, default=50)
     p.add_argument("--dx", type=float, default=0.02)
     p.add_argument("--no-extras", action="store_true", help="skip plain / e2e / CPU legs")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default kernel configuration")
     return p.parse_args()
 
 
@@ -207,6 +208,7 @@ def main():
 
     # ---- batched form, CUDA graph of G iterations --------------------------
     batch = pkg.Batch(bodies, stream=stream)
+    tuned = None if args.no_autotune else batch.autotune(5)
     batch.set_graph_iters(G)
     batch.time_force(True)
     clocks = Clocks(local)
@@ -281,6 +283,7 @@ def main():
         "hbm": {"useful_bytes_per_particle_iteration": 56, "useful_GBps": useful_gbs,
                 "frac_of_measured": useful_gbs / hbm},
         "gpu_launches": kpi * G * K,
+        "autotune": tuned,
         "clocks": clk,
     }
     line.update(extras)

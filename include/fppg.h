@@ -113,6 +113,11 @@ int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *clos
  * iteration then searches all triangles / feature segments of the body).
  * Errors: FPPG_ERR_ARG for a class outside 0..4 or non-finite coordinates. */
 int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_host, int64_t n);
+/* Constraint ids per particle (cons_host [n]: local triangle for S, local
+ * feature segment for F, -1 for none), e.g. to resume a saved state.
+ * Errors: FPPG_ERR_STATE without particles, FPPG_ERR_ARG for n other than
+ * the particle count or an id out of range for the particle's class. */
+int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n);
 /* Positions, classes and constraint ids (triangle for S, feature segment for
  * F, -1 otherwise) into caller buffers of capacity cap (each nullable);
  * *n_out receives the particle count.  Synchronises the stream. */
@@ -192,6 +197,16 @@ int fppg_batch_set_graph_iters(fppg_batch *b, int32_t graph_iters);
  * fppg_set_particles on the bodies with unchanged particle counts). */
 int fppg_batch_store(fppg_batch *b);
 int fppg_batch_load(fppg_batch *b);
+/* Autotuner: times `iters` iterations of the batch for every combination
+ * of force-kernel block size (128, 256), force-kernel variant (per-lane rows
+ * or shared-row union) and persistent search grid (4, 8 or 16 CTAs per SM),
+ * keeps the fastest and restores the particle state afterwards.  The choice
+ * is cached per (particle-count bucket, volume-particle share, GPU name) for
+ * the life of the process; a cached choice is applied without timing.
+ * Outputs (nullable): chosen variant, block size, search CTAs and the
+ * measured ms per iteration (0 when taken from the cache). */
+int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
+                        double *ms_per_iter);
 /* Kernel launches of one iteration of the batch (A1-A6, all bodies). */
 int32_t fppg_batch_kernels_per_iter(const fppg_batch *b);
 /* Particle count and the last error of the batch. */

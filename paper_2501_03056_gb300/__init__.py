@@ -61,6 +61,7 @@ def lib():
                 "fppg_get_feature_lines": [vp, P_(i64), P_(i32), i64, P_(i32), i64, P_(i64), P_(i64)],
                 "fppg_set_particles": [vp, P_(f32), P_(i32), i64],
                 "fppg_get_particles": [vp, P_(f32), P_(i32), P_(i32), i64, P_(i64)],
+                "fppg_set_constraints": [vp, P_(i32), i64],
                 "fppg_relax": [vp, i32],
                 "fppg_relax_energy": [vp, i32],
                 "fppg_stats": [vp, P_(_Stats)],
@@ -80,6 +81,7 @@ def lib():
                 "fppg_batch_store": [vp],
                 "fppg_batch_time_force": [vp, i32],
                 "fppg_batch_force_ms": [vp, P_(f64)],
+                "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(f64)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -196,6 +198,10 @@ class Body:
         cls = _i32(cls)
         self._chk(lib().fppg_set_particles(self._h, _ptr(xyz, C.c_float), _ptr(cls, C.c_int32), xyz.shape[0]))
         self.n = xyz.shape[0]
+
+    def set_constraints(self, cons):
+        cons = _i32(cons)
+        self._chk(lib().fppg_set_constraints(self._h, _ptr(cons, C.c_int32), cons.shape[0]))
 
     def get_particles(self):
         xyz = np.zeros((max(self.n, 1), 3), np.float32)
@@ -328,6 +334,14 @@ class Batch:
 
     def time_force(self, enable: bool = True):
         self._chk(lib().fppg_batch_time_force(self._h, int(bool(enable))))
+
+    def autotune(self, iters: int = 5) -> dict:
+        """Pick force variant, block size and search grid by timing; the state
+        is restored afterwards."""
+        v, tb, sc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        self._chk(lib().fppg_batch_autotune(self._h, int(iters), C.byref(v), C.byref(tb), C.byref(sc), C.byref(ms)))
+        return {"force_variant": v.value, "force_block": tb.value, "search_ctas_per_sm": sc.value,
+                "ms_per_iter": ms.value}
 
     def force_ms(self) -> float:
         ms = C.c_double()

@@ -1,7 +1,10 @@
 // extern "C" entry points of the relaxation library (include/fppg.h).
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "../../include/fppg.h"
 #include "body.h"
@@ -49,7 +52,7 @@ __global__ void k_pack(const float *__restrict__ xyz, const int32_t *__restrict_
     int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     pos[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2],
-                         __uint_as_float((uint32_t)cls[i] | ((uint32_t)body << 8)));
+                         __uint_as_float(class_bit(cls[i]) | ((uint32_t)body << 8)));
     cons[i] = -1;
 }
 
@@ -73,7 +76,7 @@ __global__ void k_set_body(float4 *__restrict__ pos, int64_t n, int body) {
 inline unsigned nb(int64_t n) { return (unsigned)std::max<int64_t>((n + 255) / 256, 1); }
 
 MeshView view_of(const Body &b) {
-    return MeshView{b.geo, b.vx, b.pn, b.hrng, b.compact, b.tlist, b.seg, b.lines};
+    return MeshView{b.geo, b.vx, b.pn, b.hrng, b.compact, b.tlist, b.seg, b.lines, b.occ};
 }
 
 // (re)build the single-body group of a context
@@ -199,6 +202,22 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
     cudaFree(dc);
     ctx->has_particles = true;
     return ctx_group(ctx);
+}
+
+int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    if (n != ctx->n || (n > 0 && !cons_host)) return fail(ctx->err, FPPG_ERR_ARG, "constraint count mismatch");
+    for (int64_t i = 0; i < n; i++) {
+        const int32_t c = cons_host[i], cl = ctx->cls_host[i];
+        const int64_t lim = cl == FPPG_S ? ctx->body.nt : cl == FPPG_F ? ctx->body.nseg : 0;
+        if (c < -1 || c >= lim) return fail(ctx->err, FPPG_ERR_ARG, "constraint id out of range for its class");
+    }
+    if (n > 0)
+        CUDA_OR(ctx->err, cudaMemcpyAsync(ctx->group.d.cons, cons_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+    CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    return FPPG_OK;
 }
 
 int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_t *cons_host, int64_t cap,
@@ -403,7 +422,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     g.owns_mesh = true;
     DevGroup &d = g.d;
     d.B = n;
-    int64_t N = 0, cells = 0, nt = 0, nv = 0, hs = 0, nc = 0, np = 0, ns = 0, nl = 0;
+    int64_t N = 0, cells = 0, nt = 0, nv = 0, hs = 0, nc = 0, np = 0, ns = 0, nl = 0, ow = 0;
     for (int32_t i = 0; i < n; i++) {
         const fppg_ctx *c = ctxs[i];
         const Body &bd = c->body;
@@ -415,6 +434,8 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         A.tlist_off = (uint32_t)np;
         A.seg_off = (int)ns;
         A.line_off = (int)nl;
+        A.occ_off = (uint32_t)ow;
+        A.dil_off = (uint32_t)(ow + bd.occ_words);
         g.hp.push_back(A);
         b->off.push_back(N);
         N += c->n;
@@ -426,9 +447,10 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         np += bd.npairs;
         ns += bd.nseg;
         nl += bd.nlines;
+        ow += 2 * bd.occ_words;
     }
     b->off.push_back(N);
-    if (cells >= 0xffffffffLL || N > ((int64_t)1 << 31)) {
+    if (cells >= 0xffffffffLL || N > ((int64_t)1 << 31) || ow >= 0xffffffffLL) {
         delete b;
         return fail(g_create_err, FPPG_ERR_ARG, "batch too large for 32-bit keys");
     }
@@ -439,7 +461,8 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     if (!r && (A((void **)&d.geo, sizeof(float4) * 5 * nt) || A((void **)&d.vx, sizeof(float4) * 3 * nt) ||
                A((void **)&d.pn, sizeof(float4) * 6 * nt) || A((void **)&d.hrng, sizeof(uint2) * hs) ||
                A((void **)&d.compact, sizeof(uint4) * nc) || A((void **)&d.tlist, sizeof(int32_t) * np) ||
-               A((void **)&d.seg, sizeof(float4) * 3 * ns) || A((void **)&d.lines, sizeof(int2) * nl)))
+               A((void **)&d.seg, sizeof(float4) * 3 * ns) || A((void **)&d.lines, sizeof(int2) * nl) ||
+               A((void **)&d.occ, sizeof(uint32_t) * ow)))
         r = FPPG_ERR_OOM;
     cudaStream_t s = b->stream;
     for (int32_t i = 0; i < n && !r; i++) {
@@ -456,12 +479,13 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         cp(d.tlist + P.tlist_off, bd.tlist, sizeof(int32_t) * bd.npairs);
         if (bd.nseg) cp(d.seg + 3 * (size_t)P.seg_off, bd.seg, sizeof(float4) * 3 * bd.nseg);
         if (bd.nlines) cp(d.lines + P.line_off, bd.lines, sizeof(int2) * bd.nlines);
+        cp(d.occ + P.occ_off, bd.occ, sizeof(uint32_t) * 2 * bd.occ_words);
         const int64_t cn = ctxs[i]->n;
         cp(d.pos + b->off[i], ctxs[i]->group.d.pos, sizeof(float4) * cn);
         cp(d.cons + b->off[i], ctxs[i]->group.d.cons, sizeof(int32_t) * cn);
         if (cn) k_set_body<<<nb(cn), 256, 0, s>>>(d.pos + b->off[i], cn, i);
     }
-    g.mesh = MeshView{d.geo, d.vx, d.pn, d.hrng, d.compact, d.tlist, d.seg, d.lines};
+    g.mesh = MeshView{d.geo, d.vx, d.pn, d.hrng, d.compact, d.tlist, d.seg, d.lines, d.occ};
     if (!r) r = g.upload_params(s, err);
     if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = FPPG_ERR_CUDA;
     if (r) {
@@ -601,9 +625,110 @@ int fppg_batch_load(fppg_batch *b) {
     return FPPG_OK;
 }
 
+namespace {
+struct TuneKey {
+    int n_bucket, v_share;
+    std::string gpu;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(n_bucket, v_share, gpu) < std::tie(o.n_bucket, o.v_share, o.gpu);
+    }
+};
+struct TuneVal {
+    int variant, block, search_ctas;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+} // namespace
+
+int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
+                        double *ms_per_iter) {
+    if (!b || iters <= 0 || iters > 10000) return FPPG_ERR_ARG;
+    Group &g = b->group;
+    DevGroup &d = g.d;
+    cudaStream_t s = b->stream;
+    int dev = 0, sms = 152;
+    cudaDeviceProp prop;
+    CUDA_OR(b->err, cudaGetDevice(&dev));
+    CUDA_OR(b->err, cudaGetDeviceProperties(&prop, dev));
+    sms = prop.multiProcessorCount;
+    int64_t nv = 0;
+    for (const fppg_ctx *c : b->ctxs)
+        for (int32_t cl : c->cls_host) nv += cl == FPPG_V;
+    int nb = 0;
+    while ((int64_t)1 << (nb + 1) <= std::max<int64_t>(d.N, 1)) nb++;
+    const TuneKey key{nb, d.N ? (int)(10 * nv / d.N) : 0, prop.name};
+    TuneVal best{g.force_variant, g.force_block, g.search_blocks / std::max(sms, 1)};
+    double best_ms = 0.0;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        float4 *pos0 = nullptr;
+        int32_t *cons0 = nullptr;
+        CUDA_OR(b->err, cudaMalloc(&pos0, sizeof(float4) * std::max<int64_t>(d.N, 1)));
+        CUDA_OR(b->err, cudaMalloc(&cons0, sizeof(int32_t) * std::max<int64_t>(d.N, 1)));
+        CUDA_OR(b->err, cudaMemcpyAsync(pos0, d.pos, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
+        CUDA_OR(b->err, cudaMemcpyAsync(cons0, d.cons, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
+        cudaEvent_t e0, e1;
+        CUDA_OR(b->err, cudaEventCreate(&e0));
+        CUDA_OR(b->err, cudaEventCreate(&e1));
+        const bool tf = g.time_force;
+        g.time_force = false;
+        best_ms = 1e30;
+        for (int v = 0; v < 2; v++)
+            for (int tb : {128, 256})
+                for (int sc : {4, 8, 16}) {
+                    g.force_variant = v;
+                    g.force_block = tb;
+                    g.search_blocks = sc * sms;
+                    CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
+                    CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
+                    iterate(g, s, false);
+                    CUDA_OR(b->err, cudaEventRecord(e0, s));
+                    for (int it = 0; it < iters; it++) iterate(g, s, false);
+                    CUDA_OR(b->err, cudaEventRecord(e1, s));
+                    CUDA_OR(b->err, cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CUDA_OR(b->err, cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms / iters < best_ms) {
+                        best_ms = ms / iters;
+                        best = TuneVal{v, tb, sc};
+                    }
+                }
+        g.time_force = tf;
+        CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
+        CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
+        CUDA_OR(b->err, cudaStreamSynchronize(s));
+        cudaFree(pos0);
+        cudaFree(cons0);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    g.force_variant = best.variant;
+    g.force_block = best.block;
+    g.search_blocks = best.search_ctas * sms;
+    if (g.graph) {
+        cudaGraphExecDestroy(g.graph);
+        g.graph = nullptr;
+    }
+    if (variant) *variant = best.variant;
+    if (block) *block = best.block;
+    if (search_ctas) *search_ctas = best.search_ctas;
+    if (ms_per_iter) *ms_per_iter = cached ? 0.0 : best_ms;
+    return FPPG_OK;
+}
+
 int32_t fppg_batch_kernels_per_iter(const fppg_batch *b) {
-    // keys, 3 per radix pass, gather + ranges, force, step + projection
-    return b ? 4 + 3 * b->group.d.passes : -1;
+    // keys, 3 per radix pass, gather + ranges, force, step, search
+    return b ? 5 + 3 * b->group.d.passes : -1;
 }
 
 int64_t fppg_batch_size(const fppg_batch *b) { return b ? b->group.d.N : -1; }

@@ -169,6 +169,8 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.tg_inv = b.tg_inv;
     A.key_base = key_base;
     A.hash_mask = (uint32_t)(b.hash_size - 1);
+    A.occ_off = 0;
+    A.dil_off = (uint32_t)b.occ_words;
     A.nt = b.nt;
     A.nv = b.nv;
     A.nseg = b.nseg;
@@ -202,7 +204,7 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
 
 int Group::alloc_particles(int64_t N, std::string &err) {
     DevGroup &g = d;
-    void *old[] = {g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.hist, g.rho_s};
+    void *old[] = {g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.hist, g.rho_s, g.work};
     for (void *p : old)
         if (p) cudaFree(p);
     g.N = N;
@@ -219,6 +221,11 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     CKA(cudaMalloc(&g.pos_s, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.acc_s, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.rho_s, sizeof(float) * n1));
+    CKA(cudaMalloc(&g.work, sizeof(int4) * n1));
+    if (!g.work_count) {
+        CKA(cudaMalloc(&g.work_count, sizeof(uint32_t)));
+        CKA(cudaMemset(g.work_count, 0, sizeof(uint32_t)));
+    }
     CKA(cudaMalloc(&g.hist, sizeof(uint32_t) * 256 * (size_t)g.n_tiles));
     if (!g.totals) CKA(cudaMalloc(&g.totals, sizeof(uint32_t) * 256));
     if (!g.cells) {
@@ -252,11 +259,11 @@ void Group::free_all() {
     ev.clear();
     DevGroup &g = d;
     void *ptrs[] = {g.params, g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.cells,
-                    g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s};
+                    g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s, g.work, g.work_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (owns_mesh) {
-        void *m[] = {g.geo, g.vx, g.pn, g.hrng, g.compact, g.tlist, g.seg, g.lines};
+        void *m[] = {g.geo, g.vx, g.pn, g.hrng, g.compact, g.tlist, g.seg, g.lines, g.occ};
         for (void *p : m)
             if (p) cudaFree(p);
     }

@@ -32,6 +32,8 @@ struct Body {
     int64_t ncompact = 0;
     int32_t *tlist = nullptr;
     int64_t npairs = 0;
+    uint32_t *occ = nullptr;     // occupancy bitmap, then its 27-cell dilation
+    int64_t occ_words = 0;       // words of one bitmap
     // feature lines (host copies + device segments)
     bool has_features = false;
     std::vector<int32_t> fe;           // [nfe][2] sorted
@@ -66,6 +68,9 @@ struct Group {
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
     // CUDA graph of graph_iters iterations
+    int search_blocks = 152 * 8;  // persistent grid of the warp-per-particle search
+    int force_block = 256;        // threads per block of the force kernel (multiple of 32, <= 256)
+    int force_variant = 0;        // 0 per-lane rows, 1 shared-row union
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     cudaStream_t graph_stream = nullptr;

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, i
             const float4 q = pos_s[j];
             const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
             const float r2 = dist2_rn(dx, dy, dz);
-            if (r2 < A.R2 && (int64_t)j != k && ((mbits >> cls_of(q.w)) & 1u)) {
+            if (r2 < A.R2 && (int64_t)j != k && (mbits & __float_as_uint(q.w)) != 0u) {
                 const float qh = sqrtf(r2) * A.half_inv_h;
                 const float t = 1.f - qh;
                 rho += t * t * t * t * (4.f * qh + 1.f);
@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, 
             if (!(r2 < A.R2) || (int64_t)j == k) return;
             const int cj = cls_of(q.w);
             float coef = 0.f;
-            if (mk && ((bk >> cj) & 1u)) coef += ek;
-            if (is_mobile(cj, A) && ((acts_on_bits(cj) >> ck) & 1u)) coef += 2.f * (rho_s[j] - w0_of(A, cj));
+            if (mk && (bk & class_bit(cj)) != 0u) coef += ek;
+            if (is_mobile(cj, A) && (acts_on_bits(cj) & class_bit(ck)) != 0u) coef += 2.f * (rho_s[j] - w0_of(A, cj));
             if (coef == 0.f) return;
             const float t = 1.f - sqrtf(r2) * A.half_inv_h;
             const float w = -A.force_scale * t * t * t * coef;   // dW/dr / r * coef

@@ -1,7 +1,7 @@
 // Internal declarations of the FPPG relaxation library (GB300, sm_103a).
 //
 // Data layout in HBM (one "group" = one or more bodies relaxed together):
-//   particles   pos   float4[N]  x, y, z, w = bits(class | body << 8)
+//   particles   pos   float4[N]  x, y, z, w = bits((1 << class) | body << 8)
 //               cons  int32[N]   triangle (S) / feature segment (F) / -1
 //               key, id  u32[N] x 2 (radix ping-pong), pos_s / acc_s float4[N]
 //               in key order
@@ -13,6 +13,8 @@
 //   hash        hrng  uint2[sum hash sizes]   {begin, length} in compact
 //               compact uint4[occupied cells] {cell key, list begin, length, 0}
 //               tlist int32[pairs]            triangle ids grouped by cell
+//               occ   u32 bitmaps   occupied triangle cells, then the same
+//                                   dilated by one cell (any of the 27)
 //   features    seg   float4[3 nseg]  a (w = line bits), b, unit tangent
 //               lines int2[nlines]    {first segment, count}
 #pragma once
@@ -52,6 +54,8 @@ struct AsmParams {
     uint32_t hash_mask;
     uint32_t compact_off;  // offset of its C_compact entries
     uint32_t tlist_off;    // offset of its triangle list
+    uint32_t occ_off;      // word offset of its triangle-cell occupancy bitmap
+    uint32_t dil_off;      // word offset of the dilated bitmap (any of 27 cells)
     int tri_off;           // offset of its triangles (ids are local)
     int nt;
     int vert_off;
@@ -84,6 +88,7 @@ struct MeshView {
     const int32_t *tlist;
     const float4 *seg;
     const int2 *lines;
+    const uint32_t *occ;
 };
 
 // Device arrays of one group.
@@ -107,6 +112,8 @@ struct DevGroup {
     uint32_t *epoch = nullptr;
     uint32_t *amax = nullptr;
     uint32_t *maxdisp = nullptr;
+    int4 *work = nullptr;          // search queue {key slot, trial point}
+    uint32_t *work_count = nullptr;
     uint32_t *hist = nullptr;  // 256 * n_tiles
     uint32_t *totals = nullptr; // 256
     // mesh
@@ -116,20 +123,17 @@ struct DevGroup {
     int32_t *tlist = nullptr;
     float4 *seg = nullptr;
     int2 *lines = nullptr;
+    uint32_t *occ = nullptr;
     // energy scratch
     float *rho_s = nullptr;
 };
 
 // ---- small device helpers ------------------------------------------------
-__host__ __device__ inline int cls_of(float w) {
-#ifdef __CUDA_ARCH__
-    return (int)(__float_as_uint(w) & 7u);
-#else
-    uint32_t u;
-    memcpy(&u, &w, 4);
-    return (int)(u & 7u);
-#endif
-}
+// the class is stored one-hot in the low byte of w, so "does class c act on
+// me" is (acts_on_bits(me) & bits(w)) != 0
+__device__ inline int cls_of(float w) { return __ffs(__float_as_uint(w) & 0xffu) - 1; }
+
+__host__ __device__ constexpr uint32_t class_bit(int c) { return 1u << c; }
 
 __device__ inline int body_of(float w) { return (int)(__float_as_uint(w) >> 8); }
 

@@ -221,6 +221,24 @@ __global__ void k_hash_ranges(const uint32_t *__restrict__ hsorted, int64_t m, u
     hrng[hsorted[i]] = make_uint2((uint32_t)i, (uint32_t)(j - i));
 }
 
+// occupied cell c: its bit in the occupancy map and the bits of its 27
+// neighbours in the dilated map
+__global__ void k_mark_occupancy(const uint4 *__restrict__ compact, int64_t m, TriGrid g, int64_t words,
+                                 uint32_t *__restrict__ occ) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    uint32_t c = compact[i].x;
+    atomicOr(occ + (c >> 5), 1u << (c & 31u));
+    int x = (int)(c % (uint32_t)g.n[0]), yz = (int)(c / (uint32_t)g.n[0]);
+    int y = yz % g.n[1], z = yz / g.n[1];
+    for (int zz = max(z - 1, 0); zz <= min(z + 1, g.n[2] - 1); zz++)
+        for (int yy = max(y - 1, 0); yy <= min(y + 1, g.n[1] - 1); yy++)
+            for (int xx = max(x - 1, 0); xx <= min(x + 1, g.n[0] - 1); xx++) {
+                uint32_t d = (uint32_t)xx + (uint32_t)g.n[0] * ((uint32_t)yy + (uint32_t)g.n[1] * (uint32_t)zz);
+                atomicOr(occ + words + (d >> 5), 1u << (d & 31u));
+            }
+}
+
 __global__ void k_feature_flags(const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, int64_t m,
                                 const double *__restrict__ nu, double cthr, uint32_t *__restrict__ flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -285,7 +303,7 @@ static cudaError_t dalloc(T **p, int64_t n) {
 }
 
 void Body::free_mesh() {
-    void *ptrs[] = {d_verts, d_tris, geo, vx, pn, hrng, compact, tlist, nu, ekey, eval, seg, lines};
+    void *ptrs[] = {d_verts, d_tris, geo, vx, pn, hrng, compact, tlist, nu, ekey, eval, seg, lines, occ};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d_verts = nullptr;
@@ -299,6 +317,7 @@ void Body::free_mesh() {
     eval = nullptr;
     seg = nullptr;
     lines = nullptr;
+    occ = nullptr;
 }
 
 int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_host, int64_t nt_, float dx_,
@@ -425,6 +444,10 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     int hb = radix_sort_u32(hk, hv, true, ncompact, bits_for((uint64_t)hash_size - 1), hist, tot, s);
     k_gather_compact<<<blocks(ncompact), 256, 0, s>>>(cmp_unsorted, hv[hb], ncompact, compact);
     k_hash_ranges<<<blocks(ncompact), 256, 0, s>>>(hk[hb], ncompact, hrng);
+    occ_words = ((int64_t)tg_n[0] * tg_n[1] * tg_n[2] + 31) / 32;
+    CK(dalloc(&occ, 2 * occ_words));
+    CK(cudaMemsetAsync(occ, 0, sizeof(uint32_t) * 2 * occ_words, s));
+    k_mark_occupancy<<<blocks(ncompact), 256, 0, s>>>(compact, ncompact, g, occ_words, occ);
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     void *tmp[] = {cnt, off, total, scratch, pk[0], pk[1], pt[0], pt[1], flag, pos, cmp_unsorted,

@@ -10,8 +10,12 @@
 //   k_force         A4  Eq. 15 over the 3 x 3 rows of 3 cells around the
 //                       particle (each row is one contiguous slot range),
 //                       amax per body by a labelled warp max + atomicMax
-//   k_step_project  A5 + A6  limited step, tangential part, projection or
-//                       revert; writes positions back in id order
+//   k_step          A5  limited step and tangential part; feature particles,
+//                       and particles with no triangle within reach, finish
+//                       here; the others are queued
+//   k_search        A6  one warp per queued particle, its lanes over the 27
+//                       triangle cells: projection or revert; positions are
+//                       written back in id order
 #include <cfloat>
 
 #include "body.h"
@@ -30,6 +34,12 @@ __device__ inline float3 operator+(float3 a, float3 b) { return make_float3(a.x 
 __device__ inline float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 __device__ inline float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+__device__ inline uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
 // max of v over the lanes that share `label`, added to dst[label] by one lane
 __device__ inline void labelled_max(uint32_t *dst, int label, float v) {
     uint32_t peers = __match_any_sync(0xffffffffu, label);
@@ -41,13 +51,17 @@ __device__ inline void labelled_max(uint32_t *dst, int label, float v) {
 __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, int64_t N,
                                               const AsmParams *__restrict__ P, uint32_t *__restrict__ key,
                                               uint32_t *__restrict__ epoch, uint32_t *__restrict__ amax,
-                                              uint32_t *__restrict__ maxdisp, int B) {
+                                              uint32_t *__restrict__ maxdisp, int B,
+                                              uint32_t *__restrict__ work_count) {
     int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (i < B) {
         amax[i] = 0u;
         maxdisp[i] = 0u;
     }
-    if (i == 0) epoch[0] += 1u;
+    if (i == 0) {
+        epoch[0] += 1u;
+        *work_count = 0u;
+    }
     if (i >= N) return;
     float4 p = pos[i];
     const AsmParams &A = P[body_of(p.w)];
@@ -76,77 +90,153 @@ __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restric
 
 // ---- A4 ----------------------------------------------------------------------
 // a_i = -sum_j dW/dr(r_ij) e_ij = force_scale * sum_j (1 - r_ij / 2h)^3 (x_i - x_j)
-template <bool COUNT>
+//
+// Each lane owns one particle (key order) and scans the 9 rows of 3 cells
+// around it; each row is one contiguous slot range.  Candidates are taken
+// two at a time with packed FP32x2 arithmetic (per component identical to
+// the scalar round-to-nearest operations, so the neighbour test
+// r^2 = (dx dx + dy dy) + dz dz < (2h)^2 decides exactly as the scalar
+// rule) and accumulated without branches into two partial sums.
+//
+// Variant 1 (shared row): when every moving lane of a warp lies in the same
+// grid row of the same body, the lanes' ranges for one row offset lie in a
+// single grid row and the warp walks their union in lockstep (broadcast
+// loads, no divergence).  A candidate outside a lane's own 3 cells is at
+// least one full cell (> 2h) away and fails the test, so each lane accepts
+// exactly its own neighbours, in the same order.  The particle itself adds
+// (1 - 0)^3 * 0 = 0, so no self test is needed.
+// Slots are paired by absolute parity (even -> .x, odd -> .y) with the range
+// [s, e) applied as a mask, so every accepted neighbour lands in the same
+// partial sum, in the same order, whichever range (own or union) is walked.
+template <bool ALL>
+__device__ inline void force_range2(const float4 *__restrict__ pos_s, const float4 p, uint32_t mbits, float R2,
+                                    float hih, uint32_t s, uint32_t e, float2 &ax, float2 &ay, float2 &az) {
+    const float2 px = make_float2(p.x, p.x), py = make_float2(p.y, p.y), pz = make_float2(p.z, p.z);
+    const float2 nh = make_float2(-hih, -hih), one = make_float2(1.f, 1.f);
+    for (uint32_t j = s & ~1u; j < e; j += 2) {
+        const bool has0 = j >= s, has1 = j + 1 < e;
+        const float4 q0 = pos_s[has0 ? j : j + 1];
+        const float4 q1 = pos_s[has1 ? j + 1 : j];
+        const float2 dx = __fadd2_rn(px, make_float2(-q0.x, -q1.x));
+        const float2 dy = __fadd2_rn(py, make_float2(-q0.y, -q1.y));
+        const float2 dz = __fadd2_rn(pz, make_float2(-q0.z, -q1.z));
+        const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+        bool t0 = has0 && r2.x < R2, t1 = has1 && r2.y < R2;
+        if (!ALL) {
+            t0 = t0 && (mbits & __float_as_uint(q0.w)) != 0u;
+            t1 = t1 && (mbits & __float_as_uint(q1.w)) != 0u;
+        }
+        const float2 r = __fmul2_rn(r2, make_float2(rsqrtf(r2.x + 1e-30f), rsqrtf(r2.y + 1e-30f)));
+        const float2 t = __ffma2_rn(r, nh, one);                     // 1 - r / 2h
+        float2 w = __fmul2_rn(__fmul2_rn(t, t), t);
+        w.x = t0 ? w.x : 0.f;
+        w.y = t1 ? w.y : 0.f;
+        ax = __ffma2_rn(w, dx, ax);
+        ay = __ffma2_rn(w, dy, ay);
+        az = __ffma2_rn(w, dz, az);
+    }
+}
+
+template <int VARIANT>
 __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s, int64_t N,
                                                const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
                                                const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s,
-                                               uint32_t *__restrict__ amax, int32_t *__restrict__ count_s,
-                                               int32_t *__restrict__ cand_s) {
-    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+                                               uint32_t *__restrict__ amax) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int cls = cls_of(p.w);
+    const int cls = active ? cls_of(p.w) : kClsI;
     const int b = active ? body_of(p.w) : 0;
     const AsmParams &A = P[b];
     const bool mob = active && is_mobile(cls, A);
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    int cnt = 0, cand = 0;
-    if (mob || (COUNT && active)) {
-        const uint32_t mbits = acts_on_bits(cls);
-        const uint32_t ep = *epoch;
-        const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
-        const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
-        const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
-        const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, nz);
-        const float R2 = A.R2, hih = A.half_inv_h;
-        const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
-        if (mbits) {
-            for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
-                for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
-                    const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-                    uint32_t s = 0xffffffffu, e = 0u;
-                    for (int x = x0; x <= x1; x++) {
-                        uint4 c = cells[row + (uint32_t)x];
-                        if (c.z == ep) {
-                            s = min(s, c.x);
-                            e = max(e, c.y);
-                        }
-                    }
-                    if (COUNT && e > s) cand += (int)(e - s);
-                    for (uint32_t j = s; j < e; j++) {
-                        const float4 q = pos_s[j];
-                        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-                        const float r2 = dist2_rn(dx, dy, dz);
-                        if (r2 < R2 && (int64_t)j != k && ((mbits >> cls_of(q.w)) & 1u)) {
-                            if (COUNT) cnt++;
-                            const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
-                            const float t = 1.f - r * hih;
-                            const float w = t * t * t;
-                            ax += w * dx;
-                            ay += w * dy;
-                            az += w * dz;
-                        }
+    const uint32_t mbits = mob ? acts_on_bits(cls) : 0u;
+    const uint32_t ep = *epoch;
+    const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
+    const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
+    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
+    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, nz);
+    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
+    const float R2 = A.R2, hih = A.half_inv_h;
+    // every class acts on every moving lane (volume targets): no mask test
+    const bool all_cls = __all_sync(0xffffffffu, mbits == 0u || mbits == 0x1Fu);
+    bool shared_row = false;
+    if (VARIANT == 1) {
+        const uint32_t mover = __ballot_sync(0xffffffffu, mbits != 0u);
+        const int leader = mover ? __ffs(mover) - 1 : 0;
+        const uint32_t rowkey = A.key_base + (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
+        const uint32_t lead_row = __shfl_sync(0xffffffffu, rowkey, leader);
+        shared_row = __all_sync(0xffffffffu, mbits == 0u || rowkey == lead_row);
+    }
+    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+    for (int dz = -1; dz <= 1; dz++)
+        for (int dy = -1; dy <= 1; dy++) {
+            const int z = cz + dz, y = cy + dy;
+            uint32_t s = 0xffffffffu, e = 0u;
+            if (mbits && z >= 0 && z < nz && y >= 0 && y < ny) {
+                const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+                for (int x = x0; x <= x1; x++) {
+                    const uint4 c = cells[row + (uint32_t)x];
+                    if (c.z == ep) {
+                        s = min(s, c.x);
+                        e = max(e, c.y);
                     }
                 }
+            }
+            if (VARIANT == 1 && shared_row) {
+                s = __reduce_min_sync(0xffffffffu, s);
+                e = __reduce_max_sync(0xffffffffu, e);
+            }
+            if (all_cls) force_range2<true>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az);
+            else force_range2<false>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az);
         }
-    }
-    float mag = 0.f;
+    float fx = 0.f, fy = 0.f, fz = 0.f, mag = 0.f;
     if (mob) {
-        ax *= A.force_scale;
-        ay *= A.force_scale;
-        az *= A.force_scale;
-        mag = sqrtf(ax * ax + ay * ay + az * az);
-    } else {
-        ax = ay = az = 0.f;
+        fx = (ax.x + ax.y) * A.force_scale;
+        fy = (ay.x + ay.y) * A.force_scale;
+        fz = (az.x + az.y) * A.force_scale;
+        mag = sqrtf(fx * fx + fy * fy + fz * fz);
     }
-    if (active) {
-        acc_s[k] = make_float4(ax, ay, az, mag);
-        if (COUNT) {
-            count_s[k] = cnt;
-            if (cand_s) cand_s[k] = mob ? cand : 0;
-        }
-    }
+    if (active) acc_s[k] = make_float4(fx, fy, fz, mag);
     labelled_max(amax, b, mag);
+}
+
+// Masked neighbour count (self excluded) and the number of candidates in the
+// particle's own 27 cells, per particle in key order (diagnostics).
+__global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s, int64_t N,
+                                               const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
+                                               const uint32_t *__restrict__ epoch, int32_t *__restrict__ count_s,
+                                               int32_t *__restrict__ cand_s) {
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k >= N) return;
+    const float4 p = pos_s[k];
+    const int cls = cls_of(p.w);
+    const AsmParams &A = P[body_of(p.w)];
+    const uint32_t mbits = acts_on_bits(cls), ep = *epoch;
+    const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
+    const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
+    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
+    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, nz);
+    int cnt = 0, cand = 0;
+    for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
+        for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
+            const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+            uint32_t s = 0xffffffffu, e = 0u;
+            for (int x = max(cx - 1, 0); x <= min(cx + 1, nx - 1); x++) {
+                const uint4 c = cells[row + (uint32_t)x];
+                if (c.z == ep) {
+                    s = min(s, c.x);
+                    e = max(e, c.y);
+                }
+            }
+            if (e > s) cand += (int)(e - s);
+            for (uint32_t j = s; j < e; j++) {
+                const float4 q = pos_s[j];
+                const float r2 = dist2_rn(p.x - q.x, p.y - q.y, p.z - q.z);
+                if (r2 < A.R2 && (int64_t)j != k && (mbits & __float_as_uint(q.w)) != 0u) cnt++;
+            }
+        }
+    count_s[k] = cnt;
+    if (cand_s) cand_s[k] = is_mobile(cls, A) ? cand : 0;
 }
 
 // ---- A6 helpers -------------------------------------------------------------
@@ -166,43 +256,12 @@ __device__ inline bool tri_cell(const MeshView &M, const AsmParams &A, int x, in
     return false;
 }
 
-// closest projectable triangle (smallest |plane distance| among triangles
-// whose foot is inside, ties to the lower index) over the 27 cells around y
-__device__ bool project_surface(const MeshView &M, const AsmParams &A, float3 y, float3 &x, int &tri) {
-    const int cx = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]);
-    const int cy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]);
-    const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
-    float best = FLT_MAX, bd = 0.f;
-    int bt = -1;
-    for (int z = max(cz - 1, 0); z <= min(cz + 1, A.tg_n[2] - 1); z++)
-        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, A.tg_n[1] - 1); yy++)
-            for (int xx = max(cx - 1, 0); xx <= min(cx + 1, A.tg_n[0] - 1); xx++) {
-                uint32_t beg, len;
-                if (!tri_cell(M, A, xx, yy, z, beg, len)) continue;
-                for (uint32_t e = beg; e < beg + len; e++) {
-                    const int t = M.tlist[e];
-                    const float4 *g = M.geo + 5 * (size_t)(A.tri_off + t);
-                    const float3 u = y - f3(g[0]);
-                    const float4 m0 = g[2];
-                    if (dot3(u, f3(m0)) < 0.f) continue;
-                    const float4 m1 = g[3];
-                    if (dot3(u, f3(m1)) - m1.w < 0.f) continue;
-                    const float4 m2 = g[4];
-                    if (dot3(u, f3(m2)) - m2.w < 0.f) continue;
-                    const float d = dot3(u, f3(g[1]));
-                    const float ad = fabsf(d);
-                    if (ad < best || (ad == best && t < bt)) {
-                        best = ad;
-                        bd = d;
-                        bt = t;
-                    }
-                }
-            }
-    if (bt < 0) return false;
-    const float3 n = f3(M.geo[5 * (size_t)(A.tri_off + bt) + 1]);
-    x = y - bd * n;
-    tri = bt;
-    return true;
+__device__ inline bool test_bit(const uint32_t *m, uint32_t off, uint32_t c) {
+    return (m[off + (c >> 5)] >> (c & 31u)) & 1u;
+}
+
+__device__ inline uint32_t tri_key(const AsmParams &A, int x, int y, int z) {
+    return (uint32_t)x + (uint32_t)A.tg_n[0] * ((uint32_t)y + (uint32_t)A.tg_n[1] * (uint32_t)z);
 }
 
 // closest point on a triangle by barycentric regions (Ericson, Real-Time
@@ -247,43 +306,144 @@ __device__ inline float3 closest_on_triangle(float3 p, float3 a, float3 b, float
     return a + (vb * den) * ab + (vc * den) * ac;
 }
 
-// inside test of a volume particle: sign of (y - c) . psi for the closest
-// point c over the 27 cells and the pseudonormal psi of its region; no
-// triangle near = inside
-__device__ bool volume_inside(const MeshView &M, const AsmParams &A, float3 y) {
-    const int cx = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]);
-    const int cy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]);
-    const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
+// Warp-cooperative search of the 27 triangle cells around y (every lane
+// holds the same y).  Lane c < 27 owns cell c of the block: its occupancy
+// bit, its hash lookup (Eq. 10) and its triangles; the warp then reduces to
+// the overall best with ties to the lower triangle index, so the choice is
+// the same as a serial scan of the 27 cells.
+//   surface: smallest |plane distance| among triangles whose foot is inside
+//            (edge functions >= 0); returns the triangle or -1
+//   volume:  closest triangle; returns inside (sign of (y - c) . psi <= 0)
+//            or true when no triangle is near
+struct CellRange {
+    uint32_t beg, len;
+};
+
+__device__ inline CellRange lane_cell(const MeshView &M, const AsmParams &A, float3 y, int lane) {
+    CellRange r{0u, 0u};
+    if (lane >= 27) return r;
+    const int x = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]) + lane % 3 - 1;
+    const int yy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]) + (lane / 3) % 3 - 1;
+    const int z = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]) + lane / 9 - 1;
+    if (x < 0 || yy < 0 || z < 0 || x >= A.tg_n[0] || yy >= A.tg_n[1] || z >= A.tg_n[2]) return r;
+    if (!test_bit(M.occ, A.occ_off, tri_key(A, x, yy, z))) return r;
+    tri_cell(M, A, x, yy, z, r.beg, r.len);
+    return r;
+}
+
+// lexicographic (value, index) minimum over the warp; every lane gets it
+__device__ inline void warp_argmin(float &v, int &t) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int ot = __shfl_xor_sync(0xffffffffu, t, o);
+        if (ov < v || (ov == v && ot < t)) {
+            v = ov;
+            t = ot;
+        }
+    }
+}
+
+// The candidate triangles of the 27 cells are gathered into a per-warp list
+// in shared memory (an exclusive scan of the cells' list lengths gives each
+// cell its place), then all 32 lanes test the list together.  A list longer
+// than the buffer is tested by the lanes cell by cell instead.
+constexpr int kSearchBuf = 160;   // triangle ids per warp
+
+__device__ inline int gather_candidates(const MeshView &M, const CellRange r, int32_t *buf) {
+    const int lane = threadIdx.x & 31;
+    uint32_t off = r.len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, off, 31);
+    off -= r.len;
+    if (total <= (uint32_t)kSearchBuf)
+        for (uint32_t q = 0; q < r.len; q++) buf[off + q] = M.tlist[r.beg + q];
+    __syncwarp();
+    return (int)total;
+}
+
+template <typename Test>
+__device__ inline void for_candidates(const MeshView &M, const CellRange r, int32_t *buf, Test &&test) {
+    const int lane = threadIdx.x & 31;
+    const int total = gather_candidates(M, r, buf);
+    if (total <= kSearchBuf) {
+        for (int q = lane; q < total; q += 32) test(buf[q]);
+    } else {
+        for (uint32_t e = r.beg; e < r.beg + r.len; e++) test(M.tlist[e]);
+    }
+    __syncwarp();
+}
+
+__device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist, int32_t *buf) {
+    const int lane = threadIdx.x & 31;
+    const CellRange r = lane_cell(M, A, y, lane);
     float best = FLT_MAX;
-    int bt = -1, breg = 0;
+    int bt = 0x7fffffff;
+    float bd = 0.f;
+    for_candidates(M, r, buf, [&](int t) {
+        const float4 *g = M.geo + 5 * (size_t)(A.tri_off + t);
+        const float3 u = y - f3(g[0]);
+        const float4 m0 = g[2];
+        if (dot3(u, f3(m0)) < 0.f) return;
+        const float4 m1 = g[3];
+        if (dot3(u, f3(m1)) - m1.w < 0.f) return;
+        const float4 m2 = g[4];
+        if (dot3(u, f3(m2)) - m2.w < 0.f) return;
+        const float d = dot3(u, f3(g[1]));
+        const float ad = fabsf(d);
+        if (ad < best || (ad == best && t < bt)) {
+            best = ad;
+            bt = t;
+            bd = d;
+        }
+    });
+    float v = best;
+    int t = bt;
+    warp_argmin(v, t);
+    // the signed distance of the winner, from a lane that holds it
+    const uint32_t own = __ballot_sync(0xffffffffu, bt == t && best == v);
+    dist = __shfl_sync(0xffffffffu, bd, own ? __ffs(own) - 1 : 0);
+    return t == 0x7fffffff ? -1 : t;
+}
+
+__device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf) {
+    const int lane = threadIdx.x & 31;
+    const CellRange r = lane_cell(M, A, y, lane);
+    float best = FLT_MAX;
+    int bt = 0x7fffffff, breg = 0;
     float3 bcp = make_float3(0.f, 0.f, 0.f);
-    for (int z = max(cz - 1, 0); z <= min(cz + 1, A.tg_n[2] - 1); z++)
-        for (int yy = max(cy - 1, 0); yy <= min(cy + 1, A.tg_n[1] - 1); yy++)
-            for (int xx = max(cx - 1, 0); xx <= min(cx + 1, A.tg_n[0] - 1); xx++) {
-                uint32_t beg, len;
-                if (!tri_cell(M, A, xx, yy, z, beg, len)) continue;
-                for (uint32_t e = beg; e < beg + len; e++) {
-                    const int t = M.tlist[e];
-                    const size_t g = (size_t)(A.tri_off + t);
-                    const float3 n = f3(M.geo[5 * g + 1]);
-                    if (n.x == 0.f && n.y == 0.f && n.z == 0.f) continue;   // degenerate
-                    int reg;
-                    const float3 cp =
-                        closest_on_triangle(y, f3(M.vx[3 * g]), f3(M.vx[3 * g + 1]), f3(M.vx[3 * g + 2]), reg);
-                    const float3 w = y - cp;
-                    const float dd = dot3(w, w);
-                    if (dd < best || (dd == best && t < bt)) {
-                        best = dd;
-                        bt = t;
-                        breg = reg;
-                        bcp = cp;
-                    }
-                }
-            }
-    if (bt < 0) return true;
-    const size_t g = (size_t)(A.tri_off + bt);
-    const float3 psi = breg == 0 ? f3(M.geo[5 * g + 1]) : f3(M.pn[6 * g + (breg <= 3 ? breg - 1 : breg - 1)]);
-    return dot3(y - bcp, psi) <= 0.f;
+    for_candidates(M, r, buf, [&](int t) {
+        const size_t g = (size_t)(A.tri_off + t);
+        const float3 n = f3(M.geo[5 * g + 1]);
+        if (n.x == 0.f && n.y == 0.f && n.z == 0.f) return;   // degenerate
+        int reg;
+        const float3 cp = closest_on_triangle(y, f3(M.vx[3 * g]), f3(M.vx[3 * g + 1]), f3(M.vx[3 * g + 2]), reg);
+        const float3 w = y - cp;
+        const float dd = dot3(w, w);
+        if (dd < best || (dd == best && t < bt)) {
+            best = dd;
+            bt = t;
+            breg = reg;
+            bcp = cp;
+        }
+    });
+    float v = best;
+    int t = bt;
+    warp_argmin(v, t);
+    if (t == 0x7fffffff) return true;
+    const uint32_t own = __ballot_sync(0xffffffffu, bt == t && best == v);
+    const int src = __ffs(own) - 1;
+    int inside = 0;
+    if (lane == src) {
+        const size_t g = (size_t)(A.tri_off + bt);
+        const float3 psi = breg == 0 ? f3(M.geo[5 * g + 1]) : f3(M.pn[6 * g + breg - 1]);
+        inside = dot3(y - bcp, psi) <= 0.f;
+    }
+    return __shfl_sync(0xffffffffu, inside, src) != 0;
 }
 
 // closest point of the particle's feature line (all lines of the body when
@@ -321,20 +481,26 @@ __device__ bool project_feature(const MeshView &M, const AsmParams &A, float3 y,
 }
 
 // ---- A5 + A6 -------------------------------------------------------------------
-__global__ void __launch_bounds__(TPB) k_step_project(const float4 *__restrict__ pos_s,
-                                                      const float4 *__restrict__ acc_s,
-                                                      const uint32_t *__restrict__ id_s, int64_t N,
-                                                      const AsmParams *__restrict__ P,
-                                                      const uint32_t *__restrict__ amax, float4 *__restrict__ pos,
-                                                      int32_t *__restrict__ cons, MeshView M,
-                                                      uint32_t *__restrict__ maxdisp) {
+// k_step: one thread per particle (key order): the limited step and its
+// tangential part, then the cases that need no triangle search -- feature
+// particles (their own line), volume particles with no triangle in the 27
+// cells (accepted), surface particles with none (reverted).  Every other
+// particle is queued with its trial point for k_search.
+__global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, const float4 *__restrict__ acc_s,
+                                              const uint32_t *__restrict__ id_s, int64_t N,
+                                              const AsmParams *__restrict__ P, const uint32_t *__restrict__ amax,
+                                              float4 *__restrict__ pos, int32_t *__restrict__ cons, MeshView M,
+                                              uint32_t *__restrict__ maxdisp, int4 *__restrict__ work,
+                                              uint32_t *__restrict__ work_count) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int cls = cls_of(p.w);
+    const int cls = active ? cls_of(p.w) : kClsI;
     const int b = active ? body_of(p.w) : 0;
     const AsmParams &A = P[b];
     float disp = 0.f;
+    bool queue = false;
+    float3 y = f3(p);
     if (active && is_mobile(cls, A)) {
         const uint32_t i = id_s[k];
         const float am = __uint_as_float(amax[b]);
@@ -350,21 +516,81 @@ __global__ void __launch_bounds__(TPB) k_step_project(const float4 *__restrict__
             dr = dot3(dr, tau) * tau;
         }
         const float3 p3 = f3(p);
-        const float3 y = p3 + dr;
-        float3 x = y;
-        int cn = c;
-        bool ok;
-        if (cls == kClsS) ok = project_surface(M, A, y, x, cn);
-        else if (cls == kClsV) ok = volume_inside(M, A, y);
-        else ok = project_feature(M, A, y, c, x, cn);
-        if (ok) {
-            pos[i] = make_float4(x.x, x.y, x.z, p.w);
-            cons[i] = cn;
-            const float3 w = x - p3;
-            disp = sqrtf(dot3(w, w));
+        y = p3 + dr;
+        if (cls == kClsF) {
+            float3 x;
+            int cn;
+            if (project_feature(M, A, y, c, x, cn)) {
+                pos[i] = make_float4(x.x, x.y, x.z, p.w);
+                cons[i] = cn;
+                const float3 w = x - p3;
+                disp = sqrtf(dot3(w, w));
+            }
+        } else {
+            const int cx = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]);
+            const int cy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]);
+            const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
+            if (test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
+                queue = true;
+            } else if (cls == kClsV) {       // nothing near: inside, accept
+                pos[i] = make_float4(y.x, y.y, y.z, p.w);
+                disp = sqrtf(dot3(dr, dr));
+            }                                // S with nothing near: revert
         }
     }
+    // warp-aggregated append to the search queue
+    const uint32_t m = __ballot_sync(0xffffffffu, queue);
+    if (m) {
+        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(work_count, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (queue)
+            work[base + __popc(m & lanemask_lt())] =
+                make_int4((int)k, __float_as_int(y.x), __float_as_int(y.y), __float_as_int(y.z));
+    }
     labelled_max(maxdisp, b, disp);
+}
+
+// k_search: one warp per queued particle (grid-stride over the queue):
+// surface particles go to the closest projectable triangle or revert,
+// volume particles are accepted when the pseudonormal sign says inside.
+__global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s,
+                                                const uint32_t *__restrict__ id_s,
+                                                const AsmParams *__restrict__ P, float4 *__restrict__ pos,
+                                                int32_t *__restrict__ cons, MeshView M,
+                                                uint32_t *__restrict__ maxdisp, const int4 *__restrict__ work,
+                                                const uint32_t *__restrict__ work_count) {
+    __shared__ int32_t sbuf[TPB / 32][kSearchBuf];
+    int32_t *buf = sbuf[threadIdx.x / 32];
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (TPB / 32);
+    const uint32_t n = *work_count;
+    for (uint32_t e = (blockIdx.x * TPB + threadIdx.x) / 32; e < n; e += warps) {
+        const int4 it = work[e];
+        const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
+        const float4 p = pos_s[it.x];
+        const int cls = cls_of(p.w), b = body_of(p.w);
+        const AsmParams &A = P[b];
+        float3 x = y;
+        int tri = -2;
+        bool ok;
+        if (cls == kClsS) {
+            float d;
+            tri = warp_project_surface(M, A, y, d, buf);
+            ok = tri >= 0;
+            if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
+        } else {
+            ok = warp_volume_inside(M, A, y, buf);
+        }
+        if (ok && lane == 0) {
+            const uint32_t i = id_s[it.x];
+            pos[i] = make_float4(x.x, x.y, x.z, p.w);
+            if (tri >= 0) cons[i] = tri;
+            const float3 w = x - f3(p);
+            atomicMax(maxdisp + b, __float_as_uint(sqrtf(dot3(w, w))));
+        }
+    }
 }
 
 // ---- diagnostics --------------------------------------------------------------
@@ -386,25 +612,42 @@ __global__ void k_project_points(const float *__restrict__ y, const int32_t *__r
                                   const int32_t *__restrict__ cons_in, int64_t n, const AsmParams *__restrict__ P,
                                   MeshView M, float *__restrict__ x, int32_t *__restrict__ cons_out,
                                   int32_t *__restrict__ ok) {
-    int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (i >= n) return;
+    __shared__ int32_t sbuf[TPB / 32][kSearchBuf];
+    int32_t *buf = sbuf[threadIdx.x / 32];
+    const int64_t i = ((int64_t)blockIdx.x * TPB + threadIdx.x) / 32;   // one warp per point
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;                                                    // whole warp
     const AsmParams &A = P[0];
-    float3 yy = make_float3(y[3 * i], y[3 * i + 1], y[3 * i + 2]), xx = yy;
-    int c = cons_in ? cons_in[i] : -1, cn = c;
+    const float3 yy = make_float3(y[3 * i], y[3 * i + 1], y[3 * i + 2]);
+    float3 xx = yy;
+    const int c = cons_in ? cons_in[i] : -1;
+    int cn = c;
     bool r = true;
-    int cl = cls[i];
-    if (cl == kClsS) r = project_surface(M, A, yy, xx, cn);
-    else if (cl == kClsV) r = volume_inside(M, A, yy);
-    else if (cl == kClsF) r = project_feature(M, A, yy, c, xx, cn);
+    const int cl = cls[i];
+    if (cl == kClsS) {
+        float d;
+        const int t = warp_project_surface(M, A, yy, d, buf);
+        r = t >= 0;
+        if (r) {
+            xx = yy - d * f3(M.geo[5 * (size_t)(A.tri_off + t) + 1]);
+            cn = t;
+        }
+    } else if (cl == kClsV) {
+        r = warp_volume_inside(M, A, yy, buf);
+    } else if (cl == kClsF) {
+        r = project_feature(M, A, yy, c, xx, cn);
+    }
     if (!r) {
         xx = yy;
         cn = c;
     }
-    x[3 * i] = xx.x;
-    x[3 * i + 1] = xx.y;
-    x[3 * i + 2] = xx.z;
-    cons_out[i] = cn;
-    ok[i] = r ? 1 : 0;
+    if (lane == 0) {
+        x[3 * i] = xx.x;
+        x[3 * i + 1] = xx.y;
+        x[3 * i + 2] = xx.z;
+        cons_out[i] = cn;
+        ok[i] = r ? 1 : 0;
+    }
 }
 
 // ---- statistics -------------------------------------------------------------------
@@ -441,7 +684,7 @@ __global__ void __launch_bounds__(TPB) k_density(const float4 *__restrict__ pos_
                 const float4 q = pos_s[j];
                 const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
                 const float r2 = dist2_rn(dx, dy, dz);
-                if (r2 < A.R2 && (int64_t)j != k && ((mbits >> cls_of(q.w)) & 1u)) {
+                if (r2 < A.R2 && (int64_t)j != k && (mbits & __float_as_uint(q.w)) != 0u) {
                     const float r = sqrtf(r2);
                     const float qh = r * A.half_inv_h;   // q / 2
                     const float t = 1.f - qh;
@@ -477,7 +720,7 @@ __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__re
 int build_grid(Group &g, cudaStream_t s) {
     DevGroup &d = g.d;
     k_keys<<<nblocks(std::max<int64_t>(d.N, d.B)), TPB, 0, s>>>(d.pos, d.N, d.params, d.key[0], d.epoch, d.amax,
-                                                                 d.maxdisp, d.B);
+                                                                 d.maxdisp, d.B, d.work_count);
     int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
     k_gather_ranges<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s,
                                                   reinterpret_cast<uint32_t *>(d.cells), d.epoch);
@@ -486,12 +729,14 @@ int build_grid(Group &g, cudaStream_t s) {
 
 void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s) {
     DevGroup &d = g.d;
-    if (count_s)
-        k_force<true><<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax,
-                                                   count_s, cand_s);
+    const int tb = g.force_block;
+    const unsigned nbk = (unsigned)std::max<int64_t>((d.N + tb - 1) / tb, 1);
+    if (g.force_variant == 1)
+        k_force<1><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax);
     else
-        k_force<false><<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax,
-                                                    nullptr, nullptr);
+        k_force<0><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax);
+    if (count_s)
+        k_count<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, count_s, cand_s);
 }
 
 void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
@@ -499,15 +744,22 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     if (d.N == 0) return;
     int buf = build_grid(g, s);
     const bool timed = g.time_force && g.ev_used + 2 <= (int)g.ev.size();
-    if (timed) cudaEventRecord(g.ev[g.ev_used], s);
+    // inside a stream capture the records must be external so that they
+    // become event-record nodes whose timestamps can be read after a replay
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (timed) cudaStreamIsCapturing(s, &cap);
+    const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used], s, flags);
     if (energy_mode) energy_accel(g, s);
     else forces(g, s, count_dbg);
     if (timed) {
-        cudaEventRecord(g.ev[g.ev_used + 1], s);
+        cudaEventRecordWithFlags(g.ev[g.ev_used + 1], s, flags);
         g.ev_used += 2;
     }
-    k_step_project<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons,
-                                                 g.mesh, d.maxdisp);
+    k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
+                                         d.maxdisp, d.work, d.work_count);
+    k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp, d.work,
+                                             d.work_count);
 }
 
 void unpermute(Group &g, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s, int32_t *count_out) {
@@ -516,7 +768,7 @@ void unpermute(Group &g, int buf, cudaStream_t s, float *acc_out, const int32_t 
 
 void project_points(Group &g, const float *y, const int32_t *cls, const int32_t *cons_in, int64_t n, float *x,
                     int32_t *cons_out, int32_t *ok, cudaStream_t s) {
-    k_project_points<<<nblocks(n), TPB, 0, s>>>(y, cls, cons_in, n, g.d.params, g.mesh, x, cons_out, ok);
+    k_project_points<<<nblocks(32 * n), TPB, 0, s>>>(y, cls, cons_in, n, g.d.params, g.mesh, x, cons_out, ok);
 }
 
 int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, double *maxdisp, int64_t *cnt,

@@ -1,0 +1,83 @@
+"""Uniformity energy and its hand-written backward on the GPU against the
+FP64 oracle (whose gradients are pinned by central differences), the
+torch.autograd.Function wrapper, and the energy-descent relaxation."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2501_03056_gb300 as pkg
+from paper_2501_03056_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2501_03056_gb300 import _build
+    _build.build()
+
+
+def shared_state(seed=0, iters=3):
+    """Oracle state after a few iterations, loaded bit-for-bit on both sides."""
+    a = W.cube_workload(seed=seed)[0]
+    o = O.from_assembly(a)
+    o.relax(iters)
+    x, cls, cons = o.get_particles()
+    x32 = x.astype(np.float32)
+    o.set_state(x32.astype(np.float64), cons)
+    b = pkg.Body(a.verts, a.tris, a.dx, a.h)
+    b.extract_features(a.dihedral_deg)
+    b.set_particles(x32, cls)
+    b.set_constraints(cons)
+    return a, b, o, x32, cls, cons
+
+
+def test_energy_and_gradients_match_the_oracle():
+    import torch
+    a, b, o, x32, cls, cons = shared_state()
+    rng = np.random.default_rng(2)
+    y = x32.copy()
+    s = cls == W.CLS_S
+    y[s] += (rng.normal(size=(s.sum(), 3)) * 0.01 * a.dx).astype(np.float32)
+    yd = torch.from_numpy(y).cuda()
+    vd = torch.from_numpy(a.verts).cuda()
+    gy = torch.empty_like(yd)
+    gV = torch.empty_like(vd)
+    E = b.energy_ptr(yd.data_ptr(), vd.data_ptr(), gy.data_ptr(), gV.data_ptr())
+    torch.cuda.synchronize()
+    Eo, gyo, gVo = o.energy_projected(y.astype(np.float64))
+    assert E == pytest.approx(Eo, rel=1e-5)
+    gy, gV = gy.cpu().numpy().astype(np.float64), gV.cpu().numpy().astype(np.float64)
+    assert np.abs(gy - gyo).max() <= 1e-4 * np.abs(gyo).max()
+    assert np.abs(gV - gVo).max() <= 1e-4 * np.abs(gVo).max()
+
+
+def test_autograd_function():
+    import torch
+    from paper_2501_03056_gb300.autograd import uniformity_energy
+    a, b, o, x32, cls, cons = shared_state(1)
+    y = torch.from_numpy(x32).cuda().requires_grad_(True)
+    v = torch.from_numpy(a.verts).cuda().requires_grad_(True)
+    E = uniformity_energy(y, v, b)
+    (2.0 * E).backward()
+    Eo, gyo, gVo = o.energy_projected(x32.astype(np.float64))
+    assert float(E) == pytest.approx(Eo, rel=1e-5)
+    g = y.grad.cpu().numpy().astype(np.float64)
+    assert np.abs(g - 2.0 * gyo).max() <= 2e-4 * np.abs(gyo).max()
+    gv = v.grad.cpu().numpy().astype(np.float64)
+    assert np.abs(gv - 2.0 * gVo).max() <= 2e-4 * np.abs(gVo).max()
+
+
+def test_energy_descent_relaxation_matches_the_oracle():
+    a, b, o, x32, cls, cons = shared_state(2)
+    e0 = o.energy()
+    b.relax_energy(5)
+    o.relax_energy(5)
+    x, _, _ = b.get_particles()
+    ox, _, _ = o.get_particles()
+    err = np.abs(x.astype(np.float64) - ox).max(axis=1) / a.dx
+    assert np.quantile(err, 0.999) < 1e-4, err.max()
+    assert o.energy() < e0
