@@ -218,6 +218,37 @@ const char *fppg_batch_last_error(const fppg_batch *b);
 int fppg_batch_time_force(fppg_batch *b, int32_t enable);
 int fppg_batch_force_ms(fppg_batch *b, double *ms);
 
+/* ---- allocation-free force pass ---------------------------------------------
+ * fppg_forces_static: the neighbour grid and the force pass (A1-A4) for one
+ * body, without a handle and without allocating any memory: for callers
+ * that cannot call cudaMalloc -- applications whose device memory is owned
+ * by their own pool allocator, and time-critical loops that must not pay
+ * for an allocation or the device synchronisation it may cause.  The paper
+ * has no counterpart; the result equals fppg_debug_forces of a body whose
+ * mesh has the bounding box [bbmin, bbmax] (the neighbour-grid rule of
+ * fppg_create).
+ *
+ * xyz_dev [n][3] float and cls_dev [n] int32 (device), n <= 65536; the box
+ * must need at most 131072 grid cells of 2h (1 + 2^-8); acc_dev [n][3]
+ * float (device) receives the accelerations in input order (zero for fixed
+ * classes); *amax_host (nullable) the largest |a| over moving particles.
+ * stream: a cudaStream_t (NULL = legacy default); the call synchronises it.
+ *
+ * Every temporary lives in one static device array of about 6 MB that each
+ * GPU loading the library holds until the process exits.  The first call on
+ * a device looks up that array's address (cudaGetSymbolAddress) -- make it
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents, so calls that overlap on the GPU (other streams,
+ * other host threads) race: serialise them.
+ *
+ * Errors (message in fppg_last_error(NULL)): FPPG_ERR_ARG for n above the
+ * limit, a box needing more cells, null buffers, h not finite and positive
+ * or a class outside 0..4 (the output is then unspecified); FPPG_ERR_CUDA
+ * when a CUDA call fails.  Non-finite coordinates give unspecified output. */
+int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, int64_t n, const float *bbmin_host,
+                       const float *bbmax_host, float h, int32_t fixed_features, float *acc_dev, float *amax_host,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

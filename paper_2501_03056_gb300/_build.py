@@ -28,6 +28,7 @@ UNITS = {
     "relax.cu": [],
     "energy.cu": [],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -11,6 +11,10 @@
 
 using namespace fppg;
 
+namespace fppg {
+void set_global_error(const char *msg);
+}
+
 struct fppg_ctx {
     Body body;
     Group group;
@@ -32,10 +36,17 @@ struct fppg_batch {
 
 namespace {
 
-thread_local std::string g_create_err;
+// errors of calls without a handle (creation, the static-scratch entry
+// point) go to a fixed per-thread buffer, so reporting them never allocates
+thread_local char g_global_err[256] = {0};
 
 int fail(std::string &dst, int code, const std::string &msg) {
     dst = msg;
+    return code;
+}
+
+int fail_global(int code, const char *msg) {
+    fppg::set_global_error(msg);
     return code;
 }
 
@@ -91,29 +102,31 @@ int ctx_group(fppg_ctx *c) {
 
 } // namespace
 
+void fppg::set_global_error(const char *msg) { snprintf(g_global_err, sizeof(g_global_err), "%s", msg); }
+
 extern "C" {
 
 int fppg_create(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,
                 fppg_ctx **out) {
-    g_create_err.clear();
-    if (!out) return fail(g_create_err, FPPG_ERR_ARG, "out is NULL");
+    g_global_err[0] = 0;
+    if (!out) return fail_global(FPPG_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!verts_host || !tris_host || nv < 3 || nt < 1 || nv > (1 << 30) || nt > (1 << 29))
-        return fail(g_create_err, FPPG_ERR_ARG, "empty or oversized mesh");
+        return fail_global(FPPG_ERR_ARG, "empty or oversized mesh");
     if (!(dx > 0.f) || !(h > 0.f) || !std::isfinite(dx) || !std::isfinite(h))
-        return fail(g_create_err, FPPG_ERR_ARG, "dx and h must be finite and positive");
+        return fail_global(FPPG_ERR_ARG, "dx and h must be finite and positive");
     for (int64_t i = 0; i < 3 * nv; i++)
-        if (!std::isfinite(verts_host[i])) return fail(g_create_err, FPPG_ERR_ARG, "non-finite vertex");
+        if (!std::isfinite(verts_host[i])) return fail_global(FPPG_ERR_ARG, "non-finite vertex");
     for (int64_t i = 0; i < 3 * nt; i++)
         if (tris_host[i] < 0 || tris_host[i] >= nv)
-            return fail(g_create_err, FPPG_ERR_ARG, "triangle index out of range");
+            return fail_global(FPPG_ERR_ARG, "triangle index out of range");
     fppg_ctx *c = new (std::nothrow) fppg_ctx();
-    if (!c) return fail(g_create_err, FPPG_ERR_OOM, "host allocation failed");
+    if (!c) return fail_global(FPPG_ERR_OOM, "host allocation failed");
     c->body.verts_host.assign(verts_host, verts_host + 3 * nv);
     int r = c->body.build_mesh(verts_host, nv, tris_host, nt, dx, h, c->stream, c->err);
     if (r == 0) r = ctx_group(c);
     if (r != 0) {
-        g_create_err = c->err;
+        set_global_error(c->err.c_str());
         delete c;
         return r == 1 ? FPPG_ERR_ARG : r;
     }
@@ -128,7 +141,7 @@ int fppg_destroy(fppg_ctx *ctx) {
     return FPPG_OK;
 }
 
-const char *fppg_last_error(const fppg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+const char *fppg_last_error(const fppg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_global_err; }
 
 int fppg_set_stream(fppg_ctx *ctx, void *stream) {
     if (!ctx) return FPPG_ERR_ARG;
@@ -410,12 +423,12 @@ int fppg_copy_positions_dev(fppg_ctx *ctx, float *xyz_dev) {
 int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     if (!out) return FPPG_ERR_ARG;
     *out = nullptr;
-    if (!ctxs || n <= 0 || n > (1 << 20)) return fail(g_create_err, FPPG_ERR_ARG, "bad body list");
+    if (!ctxs || n <= 0 || n > (1 << 20)) return fail_global(FPPG_ERR_ARG, "bad body list");
     for (int32_t i = 0; i < n; i++)
         if (!ctxs[i] || !ctxs[i]->has_particles)
-            return fail(g_create_err, FPPG_ERR_STATE, "every body needs particles before batching");
+            return fail_global(FPPG_ERR_STATE, "every body needs particles before batching");
     fppg_batch *b = new (std::nothrow) fppg_batch();
-    if (!b) return fail(g_create_err, FPPG_ERR_OOM, "host allocation failed");
+    if (!b) return fail_global(FPPG_ERR_OOM, "host allocation failed");
     b->ctxs.assign(ctxs, ctxs + n);
     b->stream = ctxs[0]->stream;
     Group &g = b->group;
@@ -452,7 +465,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     b->off.push_back(N);
     if (cells >= 0xffffffffLL || N > ((int64_t)1 << 31) || ow >= 0xffffffffLL) {
         delete b;
-        return fail(g_create_err, FPPG_ERR_ARG, "batch too large for 32-bit keys");
+        return fail_global(FPPG_ERR_ARG, "batch too large for 32-bit keys");
     }
     d.total_cells = cells;
     std::string &err = b->err;
@@ -489,7 +502,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     if (!r) r = g.upload_params(s, err);
     if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = FPPG_ERR_CUDA;
     if (r) {
-        g_create_err = err.empty() ? "batch allocation failed" : err;
+        set_global_error(err.empty() ? "batch allocation failed" : err.c_str());
         delete b;
         return r;
     }
@@ -733,6 +746,6 @@ int32_t fppg_batch_kernels_per_iter(const fppg_batch *b) {
 
 int64_t fppg_batch_size(const fppg_batch *b) { return b ? b->group.d.N : -1; }
 
-const char *fppg_batch_last_error(const fppg_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+const char *fppg_batch_last_error(const fppg_batch *b) { return b ? b->err.c_str() : g_global_err; }
 
 } // extern "C"

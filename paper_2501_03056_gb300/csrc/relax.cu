@@ -717,8 +717,7 @@ __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__re
 } // namespace
 
 // ---- host driver ----------------------------------------------------------------
-int build_grid(Group &g, cudaStream_t s) {
-    DevGroup &d = g.d;
+int build_grid_dev(DevGroup &d, cudaStream_t s) {
     k_keys<<<nblocks(std::max<int64_t>(d.N, d.B)), TPB, 0, s>>>(d.pos, d.N, d.params, d.key[0], d.epoch, d.amax,
                                                                  d.maxdisp, d.B, d.work_count);
     int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
@@ -727,14 +726,19 @@ int build_grid(Group &g, cudaStream_t s) {
     return buf;
 }
 
-void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s) {
-    DevGroup &d = g.d;
-    const int tb = g.force_block;
+int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
+
+void forces_dev(DevGroup &d, int tb, int variant, cudaStream_t s) {
     const unsigned nbk = (unsigned)std::max<int64_t>((d.N + tb - 1) / tb, 1);
-    if (g.force_variant == 1)
+    if (variant == 1)
         k_force<1><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax);
     else
         k_force<0><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax);
+}
+
+void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s) {
+    DevGroup &d = g.d;
+    forces_dev(d, g.force_block, g.force_variant, s);
     if (count_s)
         k_count<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, count_s, cand_s);
 }
@@ -762,8 +766,13 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
                                              d.work_count);
 }
 
+void unpermute_dev(DevGroup &d, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s,
+                   int32_t *count_out) {
+    k_unpermute<<<nblocks(d.N), TPB, 0, s>>>(d.acc_s, d.id[buf], d.N, acc_out, count_s, count_out);
+}
+
 void unpermute(Group &g, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s, int32_t *count_out) {
-    k_unpermute<<<nblocks(g.d.N), TPB, 0, s>>>(g.d.acc_s, g.d.id[buf], g.d.N, acc_out, count_s, count_out);
+    unpermute_dev(g.d, buf, s, acc_out, count_s, count_out);
 }
 
 void project_points(Group &g, const float *y, const int32_t *cls, const int32_t *cons_in, int64_t n, float *x,
