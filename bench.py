@@ -34,6 +34,10 @@ if ROOT not in sys.path:
 
 L2_FLUSH_BYTES = 256 << 20
 SMS, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
+# DRAM bytes (read + write) of one k_force launch on the default workload
+# (dx = 0.02), from the ncu capture summarised in
+# profiles/k_force_icosphere_torus_dx002.md; None for other workloads.
+K_FORCE_DRAM_BYTES = {0.02: 13661952}
 
 
 def parse():
@@ -112,6 +116,19 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(value: float) -> float:
+    """Largest value over the ranks of the default process group (itself
+    when not distributed); CUDA tensors under NCCL, CPU tensors under gloo."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def cpu_oracle(asm, iters=1):
@@ -216,11 +233,7 @@ def main():
     ms = timed_steps(lambda: batch.relax(G, use_graph=True), batch.load)
     clk = clocks.stop()
     force_ms = batch.force_ms()
-    tot_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(ms))
     value = n * world * G * K / (tot_ms / 1e3)
     kpi = batch.kernels_per_iter
 
@@ -277,7 +290,8 @@ def main():
         "config": {"workload": f"icosphere_l5+torus_256x64 dx={args.dx}", "bodies": len(asm), "particles": n,
                    "iterations_per_step": G, "l2": "flushed between steps (256 MiB write), working set < L2"},
         "roofline": {"bound": "alu", "kernel": "k_force", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": K_FORCE_DRAM_BYTES.get(round(args.dx, 6)),
                      "peak_kind": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz ({peak_kind} clock)",
                      "flops_per_launch": flops, "candidates": cand, "pairs": pairs, "force_ms": force_ms},
         "hbm": {"useful_bytes_per_particle_iteration": 56, "useful_GBps": useful_gbs,

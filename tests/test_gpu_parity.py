@@ -281,3 +281,32 @@ def test_edge_cases():
     o = O.Oracle(v, t, 0.05, 0.065)
     o.set_particles(far, np.full(3, W.CLS_V, np.int32))
     assert np.array_equal(b.debug_grid()[0], o.keys()[0])
+
+
+# ---- full size, in the benchmark's launch configuration ---------------------------------
+def test_full_size_icosphere_torus_in_the_bench_configuration():
+    asm = W.sphere_torus_workload()                      # 777,215 particles, dx = 0.02
+    bodies = [pkg.Body.from_assembly(a) for a in asm]
+    oracles = [O.from_assembly(a) for a in asm]
+    for a, b, o in zip(asm, bodies, oracles):
+        key, perm, *_ = b.debug_grid()
+        okey, operm = o.keys()
+        assert np.array_equal(key, okey) and np.array_equal(perm, operm)
+        _, cnt, amax = b.debug_forces()
+        _, ocnt, oamax = o.forces()
+        assert np.array_equal(cnt, ocnt)
+        assert amax == pytest.approx(oamax, rel=1e-5)
+    batch = pkg.Batch(bodies)
+    batch.autotune(2)
+    batch.set_graph_iters(5)
+    batch.relax(10, use_graph=True)
+    batch.store()
+    for a, b, o in zip(asm, bodies, oracles):
+        o.relax(10)
+        x, _, _ = b.get_particles()
+        ox, _, _ = o.get_particles()
+        err = np.abs(x.astype(np.float64) - ox).max(axis=1) / a.dx
+        assert err.max() < 1e-4, (a.name, err.max())
+        s, so = b.stats(), o.stats()
+        for k in ("mean_S", "mean_V", "std_S", "std_V", "min_pair_over_dx"):
+            assert s[k] == pytest.approx(so[k], rel=1e-2), (a.name, k)
