@@ -107,6 +107,33 @@ int fppg_get_feature_edges(fppg_ctx *ctx, int32_t *edges_host, int64_t cap, int6
 int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *closed_host, int64_t cap_lines,
                            int32_t *seg_v_host, int64_t cap_seg, int64_t *n_lines, int64_t *n_seg);
 
+/* ---- particle generation (Sec. 3.2) ------------------------------------------
+ * fppg_map_particles: replace the body's particles by the initial set of
+ * Sec. 3.2, built on the triangle grid (cell dx):
+ *   features   particles along the feature lines of fppg_extract_features,
+ *              n = ceil(L / dx) pieces of length L / n, singular end points
+ *              once (class P), the others F (Sec. 3.2.2);
+ *   surface    every cell holding triangles maps its centre to the nearest
+ *              triangle of that cell whose orthogonal foot is inside (class S,
+ *              constraint = that triangle); a centre with none is discarded
+ *              (Sec. 3.2.1, Figs. 8-9);
+ *   volume     every cell without triangles whose centre is inside by ray
+ *              parity along +z (Fig. 6; the ray starts at the centre displaced
+ *              by (1.234567e-6, 2.345678e-6) dx so it meets no edge or vertex
+ *              exactly) gives a particle at its centre: class V, or I when
+ *              band_cells > 0 and no cell with triangles lies within
+ *              band_cells cells (Chebyshev) -- the three layers of Sec. 3.3.4.
+ * Order: feature, surface (cell key order), volume (cell key order).
+ * *n_out (nullable) receives the count.  Errors: FPPG_ERR_INTERNAL when a
+ * grid column meets more than 256 triangle entries (ray buffer). */
+typedef struct {
+    int32_t surface;
+    int32_t volume;
+    int32_t features;
+    int32_t band_cells;
+} fppg_map_opts;
+int fppg_map_particles(fppg_ctx *ctx, const fppg_map_opts *opts, int64_t *n_out);
+
 /* ---- particles --------------------------------------------------------------
  * fppg_set_particles: copy n particles (xyz_host [n][3] float, cls_host [n]
  * class codes) to the device; constraint ids start at -1 (the first

@@ -84,6 +84,7 @@ def lib():
                 "oracle_energy": (f64, [vp, P(f64)]),
                 "oracle_energy_projected": (f64, [vp, P(f64), P(f64), P(f64), P(f64)]),
                 "oracle_stats": (None, [vp, P(f64)]),
+                "oracle_map_particles": (i64, [vp, C.c_int, C.c_int, C.c_int, C.c_int, P(f64), P(i32), P(i32), i64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -201,6 +202,14 @@ class Oracle:
         xyz, cls = np.zeros((max(m, 1), 3)), np.zeros(max(m, 1), np.int32)
         lib().oracle_feature_particles(self._c, float(dx), _p(xyz, C.c_double), _p(cls, C.c_int32), m)
         return xyz[:m], cls[:m]
+
+    def map_particles(self, surface=True, volume=True, features=True, band_cells=0):
+        """Initial particles of Sec. 3.2 (feature, surface-cell, interior-cell)."""
+        args = (int(surface), int(volume), int(features), int(band_cells))
+        m = lib().oracle_map_particles(self._c, *args, None, None, None, 0)
+        xyz, cls, cons = np.zeros((max(m, 1), 3)), np.zeros(max(m, 1), np.int32), np.zeros(max(m, 1), np.int32)
+        lib().oracle_map_particles(self._c, *args, _p(xyz, C.c_double), _p(cls, C.c_int32), _p(cons, C.c_int32), m)
+        return xyz[:m], cls[:m], cons[:m]
 
     def set_fixed_features(self, fixed: bool):
         lib().oracle_set_fixed_features(self._c, int(bool(fixed)))

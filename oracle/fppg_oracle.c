@@ -82,6 +82,7 @@ typedef struct {
     float *EPf;     /* [nt*9] edge pseudonormals, edge k = (v_k, v_k+1)     */
     float *VPf;     /* [nv*3] angle-weighted vertex pseudonormals           */
     float dx, h;
+    float edge_tol;  /* a foot this close outside an edge still counts as inside */
     /* triangle grid, cell = dx (Sec. 3.1.1) */
     float tg_o[3];
     float tg_inv;
@@ -180,13 +181,16 @@ double oracle_lattice_sum(double dx, double h, int dim)
 /* ------------------------------------------------------------------------ */
 /* grids: FP32 cell coordinate rule (Sec. 3.1.1 / 3.1.3)                     */
 /* ------------------------------------------------------------------------ */
-/* origin = bbmin - margin * cell (FP64, rounded to FP32); inv = 1 / cell in
- * FP64 rounded to FP32; n = ceil((bbmax - origin) / cell) + margin. */
-static void grid_setup(const float *bbmin, const float *bbmax, float cell, int margin,
+/* origin = bbmin - shift * cell (FP64, rounded to FP32); inv = 1 / cell in
+ * FP64 rounded to FP32; n = ceil((bbmax - origin) / cell) + margin.  The
+ * triangle grid uses shift 2.5 (half a cell more than its margin of 2), so a
+ * face lying on the bounding box passes through cell centres, not between
+ * two layers of cells; the neighbour grid uses shift = margin = 1. */
+static void grid_setup(const float *bbmin, const float *bbmax, float cell, double shift, int margin,
                        float *o, float *inv, int32_t *n)
 {
     for (int a = 0; a < 3; a++) {
-        o[a] = (float)((double)bbmin[a] - (double)margin * (double)cell);
+        o[a] = (float)((double)bbmin[a] - shift * (double)cell);
         n[a] = (int32_t)ceil(((double)bbmax[a] - (double)o[a]) / (double)cell) + margin;
     }
     *inv = (float)(1.0 / (double)cell);
@@ -444,12 +448,17 @@ or_ctx *oracle_create(const float *verts, int64_t nv, const int32_t *tris, int64
             bbmax[k] = fmaxf(bbmax[k], verts[3 * i + k]);
         }
     mesh_prepare(c);
-    grid_setup(bbmin, bbmax, dx, 2, c->tg_o, &c->tg_inv, c->tg_n);
+    {
+        double ext = 0.0;
+        for (int k = 0; k < 3; k++) ext = fmax(ext, (double)bbmax[k] - (double)bbmin[k]);
+        c->edge_tol = (float)ldexp(ext, -20);
+    }
+    grid_setup(bbmin, bbmax, dx, 2.5, 2, c->tg_o, &c->tg_inv, c->tg_n);
     bin_triangles(c);
     float R = 2.0f * h;
     c->R2 = (float)((double)R * (double)R);
     c->ng_cell = (float)((double)R * (1.0 + 1.0 / 256.0));
-    grid_setup(bbmin, bbmax, c->ng_cell, 1, c->ng_o, &c->ng_inv, c->ng_n);
+    grid_setup(bbmin, bbmax, c->ng_cell, 1.0, 1, c->ng_o, &c->ng_inv, c->ng_n);
     c->feat_deg = -1.0;
     return c;
 }
@@ -1024,8 +1033,8 @@ static void tri_cell_of(const or_ctx *c, const float *yf, int32_t *ci)
     for (int k = 0; k < 3; k++) ci[k] = cell_coord(yf[k], c->tg_o[k], c->tg_inv, c->tg_n[k]);
 }
 
-/* z-component of the cross product of edge (p -> q) and (p -> f), measured
- * along n: non-negative when f is on the inner side of the edge (Fig. 8) */
+/* component along n of the cross product of edge (p -> q) and (p -> f):
+ * non-negative when f is on the inner side of the edge (Fig. 8) */
 static float edge_side(const float *p, const float *q, const float *f, const float *n)
 {
     float e[3], w[3], cr[3];
@@ -1033,6 +1042,16 @@ static float edge_side(const float *p, const float *q, const float *f, const flo
     subf(f, p, w);
     crossf(e, w, cr);
     return dotf(cr, n);
+}
+
+/* the cross-product test with a tolerance: f counts as inside the edge when
+ * it lies at most tol outside it (signed distance = edge_side / |q - p|), so
+ * that a foot on an edge shared by two triangles belongs to both */
+static int edge_inside(const float *p, const float *q, const float *f, const float *n, float tol)
+{
+    float e[3];
+    subf(q, p, e);
+    return edge_side(p, q, f, n) >= -tol * sqrtf(dotf(e, e));
 }
 
 /* FP32 decision for one triangle: is the orthogonal foot of y inside, and
@@ -1052,9 +1071,9 @@ static int surface_candidate(const or_ctx *c, int64_t t, const float *y, float *
     subf(y, a, ya);
     float d = dotf(ya, n);
     for (int k = 0; k < 3; k++) f[k] = y[k] - d * n[k];
-    if (edge_side(a, b, f, n) < 0.0f) return 0;
-    if (edge_side(b, cc, f, n) < 0.0f) return 0;
-    if (edge_side(cc, a, f, n) < 0.0f) return 0;
+    if (!edge_inside(a, b, f, n, c->edge_tol)) return 0;
+    if (!edge_inside(b, cc, f, n, c->edge_tol)) return 0;
+    if (!edge_inside(cc, a, f, n, c->edge_tol)) return 0;
     *dist = fabsf(d);
     return 1;
 }
@@ -1660,4 +1679,136 @@ void oracle_stats(const or_ctx *c, double *out)
     out[7] = c->last_maxdisp / (double)c->dx;
     free(L);
     free(rho);
+}
+
+/* ------------------------------------------------------------------------ */
+/* particle generation (Sec. 3.2)                                            */
+/* ------------------------------------------------------------------------ */
+/* centre of triangle cell (i, j, k), FP64 rounded to FP32 */
+static void cell_centre(const or_ctx *c, int32_t i, int32_t j, int32_t k, float *out)
+{
+    int32_t idx[3] = {i, j, k};
+    for (int a = 0; a < 3; a++) out[a] = (float)((double)c->tg_o[a] + ((double)idx[a] + 0.5) * (double)c->dx);
+}
+
+/* Ray parity of Fig. 6 for a cell centre: the +z ray starts at the centre
+ * displaced by (1.234567e-6, 2.345678e-6) dx in x and y so that it never
+ * meets a mesh edge or vertex exactly; crossings above the start are
+ * counted with the FP64 barycentric test. */
+static int centre_inside(const or_ctx *c, const float *p)
+{
+    double q[3] = {(double)p[0] + 1.234567e-6 * (double)c->dx, (double)p[1] + 2.345678e-6 * (double)c->dx,
+                   (double)p[2]};
+    int64_t cross = 0;
+    for (int64_t t = 0; t < c->nt; t++) {
+        const double *a = c->V + 3 * c->T[3 * t], *b = c->V + 3 * c->T[3 * t + 1], *cc = c->V + 3 * c->T[3 * t + 2];
+        double d = (b[0] - a[0]) * (cc[1] - a[1]) - (cc[0] - a[0]) * (b[1] - a[1]);
+        if (d == 0.0) continue;
+        double l1 = ((b[0] - q[0]) * (cc[1] - q[1]) - (cc[0] - q[0]) * (b[1] - q[1])) / d;
+        double l2 = ((cc[0] - q[0]) * (a[1] - q[1]) - (a[0] - q[0]) * (cc[1] - q[1])) / d;
+        double l3 = 1.0 - l1 - l2;
+        if (l1 < 0 || l2 < 0 || l3 < 0) continue;
+        if (l1 * a[2] + l2 * b[2] + l3 * cc[2] > q[2]) cross++;
+    }
+    return (int)(cross & 1);
+}
+
+static int occupied_cell(const or_ctx *c, int64_t key)
+{
+    int64_t p = lower_bound_i64(c->pair_key, c->npairs, key);
+    return p < c->npairs && c->pair_key[p] == key;
+}
+
+/* Initial particles (Sec. 3.2, Fig. 9):
+ *   features: the feature-line particles (F, and P at singular points);
+ *   surface:  every triangle cell holding triangles contributes its centre
+ *             mapped to the nearest triangle of that cell whose foot is
+ *             inside (smallest |plane distance|, ties to the lower index);
+ *             a centre with no such triangle is discarded (S, constraint =
+ *             the triangle);
+ *   volume:   every cell without triangles whose centre is inside by ray
+ *             parity (Fig. 6) contributes its centre: class V when band_cells
+ *             <= 0 or when a cell with triangles lies within band_cells cells
+ *             (Chebyshev), else I.
+ * Order: features, then surface cells by key, then volume cells by key.
+ * Writes at most cap particles; returns the total count. */
+int64_t oracle_map_particles(const or_ctx *c, int surface, int volume, int features, int band_cells, double *xyz,
+                             int32_t *cls, int32_t *cons, int64_t cap)
+{
+    int64_t cnt = 0;
+    if (features) {
+        int64_t nf = oracle_feature_particles(c, (double)c->dx, NULL, NULL, 0);
+        double *fx = malloc(sizeof(double) * 3 * (nf ? nf : 1));
+        int32_t *fc = malloc(sizeof(int32_t) * (nf ? nf : 1));
+        oracle_feature_particles(c, (double)c->dx, fx, fc, nf);
+        for (int64_t i = 0; i < nf; i++, cnt++)
+            if (cnt < cap) {
+                memcpy(xyz + 3 * cnt, fx + 3 * i, sizeof(double) * 3);
+                cls[cnt] = fc[i];
+                cons[cnt] = -1;
+            }
+        free(fx);
+        free(fc);
+    }
+    const int32_t *n = c->tg_n;
+    if (surface) {
+        for (int64_t q = 0; q < c->npairs;) {
+            int64_t key = c->pair_key[q], e = q;
+            while (e < c->npairs && c->pair_key[e] == key) e++;
+            int32_t i = (int32_t)(key % n[0]), j = (int32_t)((key / n[0]) % n[1]), k = (int32_t)(key / ((int64_t)n[0] * n[1]));
+            float ctr[3];
+            cell_centre(c, i, j, k, ctr);
+            float best = INFINITY;
+            int64_t bt = -1;
+            for (int64_t p = q; p < e; p++) {
+                float d;
+                int64_t t = c->pair_tri[p];
+                if (!surface_candidate(c, t, ctr, &d)) continue;
+                if (d < best || (d == best && t < bt)) {
+                    best = d;
+                    bt = t;
+                }
+            }
+            if (bt >= 0) {
+                if (cnt < cap) {
+                    double y[3] = {ctr[0], ctr[1], ctr[2]};
+                    plane_foot(c, bt, y, xyz + 3 * cnt);
+                    cls[cnt] = OR_S;
+                    cons[cnt] = (int32_t)bt;
+                }
+                cnt++;
+            }
+            q = e;
+        }
+    }
+    if (volume) {
+        for (int32_t k = 0; k < n[2]; k++)
+            for (int32_t j = 0; j < n[1]; j++)
+                for (int32_t i = 0; i < n[0]; i++) {
+                    int64_t key = (int64_t)i + (int64_t)n[0] * ((int64_t)j + (int64_t)n[1] * k);
+                    if (occupied_cell(c, key)) continue;
+                    float ctr[3];
+                    cell_centre(c, i, j, k, ctr);
+                    if (!centre_inside(c, ctr)) continue;
+                    int32_t cl = OR_V;
+                    if (band_cells > 0) {
+                        int near = 0;
+                        for (int32_t dz = -band_cells; dz <= band_cells && !near; dz++)
+                            for (int32_t dy = -band_cells; dy <= band_cells && !near; dy++)
+                                for (int32_t dx = -band_cells; dx <= band_cells && !near; dx++) {
+                                    int32_t a = i + dx, b = j + dy, d = k + dz;
+                                    if (a < 0 || b < 0 || d < 0 || a >= n[0] || b >= n[1] || d >= n[2]) continue;
+                                    near = occupied_cell(c, (int64_t)a + (int64_t)n[0] * ((int64_t)b + (int64_t)n[1] * d));
+                                }
+                        if (!near) cl = OR_I;
+                    }
+                    if (cnt < cap) {
+                        for (int a = 0; a < 3; a++) xyz[3 * cnt + a] = (double)ctr[a];
+                        cls[cnt] = cl;
+                        cons[cnt] = -1;
+                    }
+                    cnt++;
+                }
+    }
+    return cnt;
 }

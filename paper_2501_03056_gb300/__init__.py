@@ -32,6 +32,10 @@ class FPPGError(RuntimeError):
         self.code = code
 
 
+class _MapOpts(C.Structure):
+    _fields_ = [("surface", C.c_int32), ("volume", C.c_int32), ("features", C.c_int32), ("band_cells", C.c_int32)]
+
+
 class _Stats(C.Structure):
     _fields_ = [("mean_rho", C.c_double * 3), ("std_rho", C.c_double * 3), ("min_pair_over_dx", C.c_double),
                 ("max_disp_over_dx", C.c_double), ("count", C.c_int64 * 3)]
@@ -62,6 +66,7 @@ def lib():
                 "fppg_set_particles": [vp, P_(f32), P_(i32), i64],
                 "fppg_get_particles": [vp, P_(f32), P_(i32), P_(i32), i64, P_(i64)],
                 "fppg_set_constraints": [vp, P_(i32), i64],
+                "fppg_map_particles": [vp, P_(_MapOpts), P_(i64)],
                 "fppg_relax": [vp, i32],
                 "fppg_relax_energy": [vp, i32],
                 "fppg_stats": [vp, P_(_Stats)],
@@ -192,6 +197,14 @@ class Body:
         self._chk(lib().fppg_get_feature_lines(self._h, _ptr(nseg, C.c_int64), _ptr(closed, C.c_int32), nl.value,
                                                _ptr(segv, C.c_int32), ns.value, C.byref(nl), C.byref(ns)))
         return nseg[:nl.value], closed[:nl.value], segv[:ns.value]
+
+    def map_particles(self, surface=True, volume=True, features=True, band_cells=0) -> int:
+        """Replace the particles by the initial set of Sec. 3.2 (on the GPU)."""
+        o = _MapOpts(int(surface), int(volume), int(features), int(band_cells))
+        n = C.c_int64()
+        self._chk(lib().fppg_map_particles(self._h, C.byref(o), C.byref(n)))
+        self.n = n.value
+        return self.n
 
     def set_particles(self, xyz, cls):
         xyz = _f32(xyz, (-1, 3))

@@ -29,6 +29,7 @@ UNITS = {
     "energy.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
+    "mapping.cu": ["-fmad=false"],
 }
 
 

@@ -185,6 +185,7 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.force_scale = (float)(5.0 * host_alpha3(h) / (h * h));
     A.step_h = (float)(h / 16.0);
     A.dx = b.dx;
+    A.edge_tol = b.edge_tol;
     A.w0[0] = (float)lattice_w0((double)b.dx, h, 2);
     A.w0[1] = (float)lattice_w0((double)b.dx, h, 3);
     A.w0[2] = (float)lattice_w0((double)b.dx, h, 1);

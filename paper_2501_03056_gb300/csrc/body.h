@@ -6,18 +6,20 @@
 
 namespace fppg {
 
-void grid_setup(const float *bbmin, const float *bbmax, float cell, int margin, float *o, float *inv, int *n);
+void grid_setup(const float *bbmin, const float *bbmax, float cell, double shift, int margin, float *o, float *inv,
+                int *n);
 
 struct Body {
     int nv = 0, nt = 0;
     float dx = 0, h = 0;
-    // triangle grid (cell dx, 2 cells of margin)
+    // triangle grid (cell dx, origin 2.5 cells below the box, 2 cells of margin)
     float tg_o[3] = {0, 0, 0};
     float tg_inv = 0;
     int tg_n[3] = {0, 0, 0};
     // neighbour grid (cell 2h (1 + 2^-8), 1 cell of margin)
     float ng_o[3] = {0, 0, 0};
     float ng_inv = 0, ng_cell = 0, R2 = 0;
+    float edge_tol = 0;  // 2^-20 of the largest bounding-box extent
     int ng_n[3] = {0, 0, 0};
     // device mesh
     float *d_verts = nullptr;
@@ -46,6 +48,7 @@ struct Body {
     int2 *lines = nullptr;
     int nseg = 0, nlines = 0;
 
+    void feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls) const;
     int build_mesh(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,
                    cudaStream_t s, std::string &err);
     int extract_features(float deg, cudaStream_t s, std::string &err);
@@ -101,6 +104,9 @@ void project_points(Group &g, const float *y, const int32_t *cls, const int32_t 
 // uniformity statistics into host doubles (see fppg_stats_t)
 int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, double *maxdisp, int64_t *cnt,
           std::string &err);
+// initial particles of Sec. 3.2 into the group (features, surface, volume)
+int map_particles(Group &g, Body &b, int surface, int volume, int features, int band_cells, cudaStream_t s,
+                  int64_t *n_out, std::vector<int32_t> &cls_host, std::string &err);
 // energy and gradients (positions y, vertex coordinates verts of body 0)
 int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
            cudaStream_t s, std::string &err);

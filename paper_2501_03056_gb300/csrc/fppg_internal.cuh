@@ -75,6 +75,7 @@ struct AsmParams {
     float w0[3];       // ideal kernel sums of S, V, F
     float w_zero;      // W(0) = alpha_3
     float alpha;       // alpha_3
+    float edge_tol;    // a foot this close outside a triangle edge still counts as inside
     int p_begin, p_end;
 };
 

@@ -278,11 +278,14 @@ int bits_for(uint64_t maxval) {
 } // namespace
 
 // Grid rule shared with every other implementation of the method:
-// origin = bbmin - margin * cell (FP64, rounded to FP32), inv = 1 / cell
-// (FP64, rounded), n = ceil((bbmax - origin) / cell) + margin.
-void grid_setup(const float *bbmin, const float *bbmax, float cell, int margin, float *o, float *inv, int *n) {
+// origin = bbmin - shift * cell (FP64, rounded to FP32), inv = 1 / cell
+// (FP64, rounded), n = ceil((bbmax - origin) / cell) + margin.  The triangle
+// grid uses shift 2.5 with margin 2 (a face on the bounding box passes
+// through cell centres), the neighbour grid shift 1 with margin 1.
+void grid_setup(const float *bbmin, const float *bbmax, float cell, double shift, int margin, float *o, float *inv,
+                int *n) {
     for (int a = 0; a < 3; a++) {
-        o[a] = (float)((double)bbmin[a] - (double)margin * (double)cell);
+        o[a] = (float)((double)bbmin[a] - shift * (double)cell);
         n[a] = (int)std::ceil(((double)bbmax[a] - (double)o[a]) / (double)cell) + margin;
     }
     *inv = (float)(1.0 / (double)cell);
@@ -332,11 +335,16 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
             bbmin[k] = std::min(bbmin[k], verts_host[3 * i + k]);
             bbmax[k] = std::max(bbmax[k], verts_host[3 * i + k]);
         }
-    grid_setup(bbmin, bbmax, dx, 2, tg_o, &tg_inv, tg_n);
+    {
+        double ext = 0.0;
+        for (int k = 0; k < 3; k++) ext = std::max(ext, (double)bbmax[k] - (double)bbmin[k]);
+        edge_tol = (float)std::ldexp(ext, -20);
+    }
+    grid_setup(bbmin, bbmax, dx, 2.5, 2, tg_o, &tg_inv, tg_n);
     float R = 2.0f * h;
     R2 = (float)((double)R * (double)R);
     ng_cell = (float)((double)R * (1.0 + 1.0 / 256.0));
-    grid_setup(bbmin, bbmax, ng_cell, 1, ng_o, &ng_inv, ng_n);
+    grid_setup(bbmin, bbmax, ng_cell, 1.0, 1, ng_o, &ng_inv, ng_n);
     if ((double)tg_n[0] * tg_n[1] * tg_n[2] >= 4294967295.0 || (double)ng_n[0] * ng_n[1] * ng_n[2] >= 2147483647.0) {
         err = "grid too large for 32-bit cell keys (dx too small for the mesh extent)";
         return 1;

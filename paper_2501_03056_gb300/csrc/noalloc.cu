@@ -102,7 +102,7 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     memset(&A, 0, sizeof(A));
     const float R = 2.0f * h;
     const float cell = (float)((double)R * (1.0 + 1.0 / 256.0));
-    grid_setup(bbmin_host, bbmax_host, cell, 1, A.ng_o, &A.ng_inv, A.ng_n);
+    grid_setup(bbmin_host, bbmax_host, cell, 1.0, 1, A.ng_o, &A.ng_inv, A.ng_n);
     const int64_t cells = (int64_t)A.ng_n[0] * A.ng_n[1] * A.ng_n[2];
     if (cells > kStaticMaxCells) {
         set_global_error("fppg_forces_static: the box needs more than 131072 grid cells of 2h (static scratch limit)");

@@ -387,12 +387,15 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
     for_candidates(M, r, buf, [&](int t) {
         const float4 *g = M.geo + 5 * (size_t)(A.tri_off + t);
         const float3 u = y - f3(g[0]);
+        // inside: every in-plane edge distance >= -edge_tol (Fig. 8 with a
+        // tolerance, so a foot on a shared edge belongs to both triangles)
+        const float tol = -A.edge_tol;
         const float4 m0 = g[2];
-        if (dot3(u, f3(m0)) < 0.f) return;
+        if (dot3(u, f3(m0)) < tol) return;
         const float4 m1 = g[3];
-        if (dot3(u, f3(m1)) - m1.w < 0.f) return;
+        if (dot3(u, f3(m1)) - m1.w < tol) return;
         const float4 m2 = g[4];
-        if (dot3(u, f3(m2)) - m2.w < 0.f) return;
+        if (dot3(u, f3(m2)) - m2.w < tol) return;
         const float d = dot3(u, f3(g[1]));
         const float ad = fabsf(d);
         if (ad < best || (ad == best && t < bt)) {
