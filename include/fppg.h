@@ -122,7 +122,9 @@ int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *clos
  *              by (1.234567e-6, 2.345678e-6) dx so it meets no edge or vertex
  *              exactly) gives a particle at its centre: class V, or I when
  *              band_cells > 0 and no cell with triangles lies within
- *              band_cells cells (Chebyshev) -- the three layers of Sec. 3.3.4.
+ *              band_cells cells (Chebyshev) -- the three layers of Sec. 3.3.4;
+ *              with inner_cells > 0 the innermost layer is inner_cells thick
+ *              and deeper cells give no particle.
  * Order: feature, surface (cell key order), volume (cell key order).
  * *n_out (nullable) receives the count.  Errors: FPPG_ERR_INTERNAL when a
  * grid column meets more than 256 triangle entries (ray buffer). */
@@ -131,6 +133,7 @@ typedef struct {
     int32_t volume;
     int32_t features;
     int32_t band_cells;
+    int32_t inner_cells;
 } fppg_map_opts;
 int fppg_map_particles(fppg_ctx *ctx, const fppg_map_opts *opts, int64_t *n_out);
 

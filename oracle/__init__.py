@@ -84,7 +84,8 @@ def lib():
                 "oracle_energy": (f64, [vp, P(f64)]),
                 "oracle_energy_projected": (f64, [vp, P(f64), P(f64), P(f64), P(f64)]),
                 "oracle_stats": (None, [vp, P(f64)]),
-                "oracle_map_particles": (i64, [vp, C.c_int, C.c_int, C.c_int, C.c_int, P(f64), P(i32), P(i32), i64]),
+                "oracle_map_particles": (i64, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(f64), P(i32), P(i32),
+                                                i64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -203,9 +204,9 @@ class Oracle:
         lib().oracle_feature_particles(self._c, float(dx), _p(xyz, C.c_double), _p(cls, C.c_int32), m)
         return xyz[:m], cls[:m]
 
-    def map_particles(self, surface=True, volume=True, features=True, band_cells=0):
+    def map_particles(self, surface=True, volume=True, features=True, band_cells=0, inner_cells=0):
         """Initial particles of Sec. 3.2 (feature, surface-cell, interior-cell)."""
-        args = (int(surface), int(volume), int(features), int(band_cells))
+        args = (int(surface), int(volume), int(features), int(band_cells), int(inner_cells))
         m = lib().oracle_map_particles(self._c, *args, None, None, None, 0)
         xyz, cls, cons = np.zeros((max(m, 1), 3)), np.zeros(max(m, 1), np.int32), np.zeros(max(m, 1), np.int32)
         lib().oracle_map_particles(self._c, *args, _p(xyz, C.c_double), _p(cls, C.c_int32), _p(cons, C.c_int32), m)
@@ -326,9 +327,16 @@ class Oracle:
 
 
 def from_assembly(a, features=True) -> Oracle:
-    """Oracle body for a workloads.Assembly, features extracted, particles set."""
+    """Oracle body for a workloads.Assembly, features extracted, particles set
+    (generated by the oracle's own Sec. 3.2 generation when it carries none;
+    the constraints of the generated surface particles are kept)."""
     o = Oracle(a.verts, a.tris, a.dx, a.h)
     if features and a.dihedral_deg is not None:
         o.extract_features(a.dihedral_deg)
-    o.set_particles(a.xyz, a.cls)
+    if a.xyz is None:
+        x, c, cons = o.map_particles(**a.meta.get("generate", {}))
+        o.set_particles(x.astype(np.float32), c)
+        o.set_state(x.astype(np.float32).astype(np.float64), cons)
+    else:
+        o.set_particles(a.xyz, a.cls)
     return o

@@ -1691,32 +1691,64 @@ static void cell_centre(const or_ctx *c, int32_t i, int32_t j, int32_t k, float 
     for (int a = 0; a < 3; a++) out[a] = (float)((double)c->tg_o[a] + ((double)idx[a] + 0.5) * (double)c->dx);
 }
 
-/* Ray parity of Fig. 6 for a cell centre: the +z ray starts at the centre
- * displaced by (1.234567e-6, 2.345678e-6) dx in x and y so that it never
- * meets a mesh edge or vertex exactly; crossings above the start are
- * counted with the FP64 barycentric test. */
-static int centre_inside(const or_ctx *c, const float *p)
+/* Ray parity of Fig. 6 for the cell centres of one grid column (i, j): the
+ * +z ray starts at each centre displaced by (1.234567e-6, 2.345678e-6) dx in
+ * x and y so that it never meets a mesh edge or vertex exactly.  Every
+ * triangle the vertical line crosses is binned into some cell of the
+ * column, so the column's triangles (each counted once) give all crossing
+ * heights; a centre is inside when an odd number of them lie above it. */
+static int cmp_i32(const void *a, const void *b)
 {
-    double q[3] = {(double)p[0] + 1.234567e-6 * (double)c->dx, (double)p[1] + 2.345678e-6 * (double)c->dx,
-                   (double)p[2]};
-    int64_t cross = 0;
-    for (int64_t t = 0; t < c->nt; t++) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return x < y ? -1 : (x > y);
+}
+
+static void column_inside(const or_ctx *c, int32_t i, int32_t j, unsigned char *inside_col)
+{
+    const int32_t *n = c->tg_n;
+    float p0[3];
+    cell_centre(c, i, j, 0, p0);
+    double qx = (double)p0[0] + 1.234567e-6 * (double)c->dx, qy = (double)p0[1] + 2.345678e-6 * (double)c->dx;
+    /* triangles binned into the column's cells, each once */
+    int64_t cap = 64, m = 0;
+    int32_t *tri = malloc(sizeof(int32_t) * cap);
+    for (int32_t k = 0; k < n[2]; k++) {
+        int64_t key = (int64_t)i + (int64_t)n[0] * ((int64_t)j + (int64_t)n[1] * k);
+        for (int64_t p = lower_bound_i64(c->pair_key, c->npairs, key); p < c->npairs && c->pair_key[p] == key; p++) {
+            if (m == cap) {
+                cap *= 2;
+                tri = realloc(tri, sizeof(int32_t) * cap);
+            }
+            tri[m++] = c->pair_tri[p];
+        }
+    }
+    qsort(tri, (size_t)m, sizeof(int32_t), cmp_i32);
+    int64_t u = 0;
+    for (int64_t q = 0; q < m; q++)
+        if (q == 0 || tri[q] != tri[q - 1]) tri[u++] = tri[q];
+    double *zc = malloc(sizeof(double) * (u ? u : 1));
+    int64_t nz = 0;
+    for (int64_t q = 0; q < u; q++) {
+        int64_t t = tri[q];
         const double *a = c->V + 3 * c->T[3 * t], *b = c->V + 3 * c->T[3 * t + 1], *cc = c->V + 3 * c->T[3 * t + 2];
         double d = (b[0] - a[0]) * (cc[1] - a[1]) - (cc[0] - a[0]) * (b[1] - a[1]);
         if (d == 0.0) continue;
-        double l1 = ((b[0] - q[0]) * (cc[1] - q[1]) - (cc[0] - q[0]) * (b[1] - q[1])) / d;
-        double l2 = ((cc[0] - q[0]) * (a[1] - q[1]) - (a[0] - q[0]) * (cc[1] - q[1])) / d;
+        double l1 = ((b[0] - qx) * (cc[1] - qy) - (cc[0] - qx) * (b[1] - qy)) / d;
+        double l2 = ((cc[0] - qx) * (a[1] - qy) - (a[0] - qx) * (cc[1] - qy)) / d;
         double l3 = 1.0 - l1 - l2;
         if (l1 < 0 || l2 < 0 || l3 < 0) continue;
-        if (l1 * a[2] + l2 * b[2] + l3 * cc[2] > q[2]) cross++;
+        zc[nz++] = l1 * a[2] + l2 * b[2] + l3 * cc[2];
     }
-    return (int)(cross & 1);
-}
-
-static int occupied_cell(const or_ctx *c, int64_t key)
-{
-    int64_t p = lower_bound_i64(c->pair_key, c->npairs, key);
-    return p < c->npairs && c->pair_key[p] == key;
+    for (int32_t k = 0; k < n[2]; k++) {
+        float p[3];
+        cell_centre(c, i, j, k, p);
+        int64_t cross = 0;
+        for (int64_t q = 0; q < nz; q++)
+            if (zc[q] > (double)p[2]) cross++;
+        inside_col[k] = (unsigned char)(cross & 1);
+    }
+    free(zc);
+    free(tri);
 }
 
 /* Initial particles (Sec. 3.2, Fig. 9):
@@ -1729,11 +1761,12 @@ static int occupied_cell(const or_ctx *c, int64_t key)
  *   volume:   every cell without triangles whose centre is inside by ray
  *             parity (Fig. 6) contributes its centre: class V when band_cells
  *             <= 0 or when a cell with triangles lies within band_cells cells
- *             (Chebyshev), else I.
+ *             (Chebyshev), else I -- or nothing when inner_cells > 0 and no
+ *             cell with triangles lies within band_cells + inner_cells.
  * Order: features, then surface cells by key, then volume cells by key.
  * Writes at most cap particles; returns the total count. */
-int64_t oracle_map_particles(const or_ctx *c, int surface, int volume, int features, int band_cells, double *xyz,
-                             int32_t *cls, int32_t *cons, int64_t cap)
+int64_t oracle_map_particles(const or_ctx *c, int surface, int volume, int features, int band_cells, int inner_cells,
+                             double *xyz, int32_t *cls, int32_t *cons, int64_t cap)
 {
     int64_t cnt = 0;
     if (features) {
@@ -1782,33 +1815,50 @@ int64_t oracle_map_particles(const or_ctx *c, int surface, int volume, int featu
         }
     }
     if (volume) {
+        const int64_t cells = (int64_t)n[0] * n[1] * n[2];
+        unsigned char *occ = calloc((size_t)cells, 1), *ins = calloc((size_t)cells, 1);
+        for (int64_t p = 0; p < c->npairs; p++) occ[c->pair_key[p]] = 1;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t col = 0; col < (int64_t)n[0] * n[1]; col++) {
+            int32_t i = (int32_t)(col % n[0]), j = (int32_t)(col / n[0]);
+            unsigned char *buf = malloc((size_t)n[2]);
+            column_inside(c, i, j, buf);
+            for (int32_t k = 0; k < n[2]; k++) ins[(int64_t)i + (int64_t)n[0] * ((int64_t)j + (int64_t)n[1] * k)] = buf[k];
+            free(buf);
+        }
         for (int32_t k = 0; k < n[2]; k++)
             for (int32_t j = 0; j < n[1]; j++)
                 for (int32_t i = 0; i < n[0]; i++) {
                     int64_t key = (int64_t)i + (int64_t)n[0] * ((int64_t)j + (int64_t)n[1] * k);
-                    if (occupied_cell(c, key)) continue;
-                    float ctr[3];
-                    cell_centre(c, i, j, k, ctr);
-                    if (!centre_inside(c, ctr)) continue;
+                    if (occ[key] || !ins[key]) continue;
                     int32_t cl = OR_V;
                     if (band_cells > 0) {
-                        int near = 0;
-                        for (int32_t dz = -band_cells; dz <= band_cells && !near; dz++)
-                            for (int32_t dy = -band_cells; dy <= band_cells && !near; dy++)
-                                for (int32_t dx = -band_cells; dx <= band_cells && !near; dx++) {
+                        /* Chebyshev distance (in cells) to the nearest cell with triangles */
+                        int32_t reach = inner_cells > 0 ? band_cells + inner_cells : band_cells, dmin = reach + 1;
+                        for (int32_t dz = -reach; dz <= reach; dz++)
+                            for (int32_t dy = -reach; dy <= reach; dy++)
+                                for (int32_t dx = -reach; dx <= reach; dx++) {
                                     int32_t a = i + dx, b = j + dy, d = k + dz;
                                     if (a < 0 || b < 0 || d < 0 || a >= n[0] || b >= n[1] || d >= n[2]) continue;
-                                    near = occupied_cell(c, (int64_t)a + (int64_t)n[0] * ((int64_t)b + (int64_t)n[1] * d));
+                                    if (!occ[(int64_t)a + (int64_t)n[0] * ((int64_t)b + (int64_t)n[1] * d)]) continue;
+                                    int32_t cd = abs(dx) > abs(dy) ? abs(dx) : abs(dy);
+                                    if (abs(dz) > cd) cd = abs(dz);
+                                    if (cd < dmin) dmin = cd;
                                 }
-                        if (!near) cl = OR_I;
+                        if (dmin > band_cells) cl = OR_I;
+                        if (inner_cells > 0 && dmin > band_cells + inner_cells) continue;
                     }
                     if (cnt < cap) {
+                        float ctr[3];
+                        cell_centre(c, i, j, k, ctr);
                         for (int a = 0; a < 3; a++) xyz[3 * cnt + a] = (double)ctr[a];
                         cls[cnt] = cl;
                         cons[cnt] = -1;
                     }
                     cnt++;
                 }
+        free(occ);
+        free(ins);
     }
     return cnt;
 }

@@ -33,7 +33,8 @@ class FPPGError(RuntimeError):
 
 
 class _MapOpts(C.Structure):
-    _fields_ = [("surface", C.c_int32), ("volume", C.c_int32), ("features", C.c_int32), ("band_cells", C.c_int32)]
+    _fields_ = [("surface", C.c_int32), ("volume", C.c_int32), ("features", C.c_int32), ("band_cells", C.c_int32),
+                ("inner_cells", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -145,10 +146,15 @@ class Body:
 
     @classmethod
     def from_assembly(cls, a, features=True, stream=None):
+        """Body of a workloads.Assembly: its mesh, its features, and its given
+        particles -- or, when it carries none, the generation of Sec. 3.2."""
         b = cls(a.verts, a.tris, a.dx, a.h, stream=stream)
         if features and a.dihedral_deg is not None:
             b.extract_features(a.dihedral_deg)
-        b.set_particles(a.xyz, a.cls)
+        if a.xyz is None:
+            b.map_particles(**a.meta.get("generate", {}))
+        else:
+            b.set_particles(a.xyz, a.cls)
         return b
 
     def _chk(self, r):
@@ -198,9 +204,9 @@ class Body:
                                                _ptr(segv, C.c_int32), ns.value, C.byref(nl), C.byref(ns)))
         return nseg[:nl.value], closed[:nl.value], segv[:ns.value]
 
-    def map_particles(self, surface=True, volume=True, features=True, band_cells=0) -> int:
+    def map_particles(self, surface=True, volume=True, features=True, band_cells=0, inner_cells=0) -> int:
         """Replace the particles by the initial set of Sec. 3.2 (on the GPU)."""
-        o = _MapOpts(int(surface), int(volume), int(features), int(band_cells))
+        o = _MapOpts(int(surface), int(volume), int(features), int(band_cells), int(inner_cells))
         n = C.c_int64()
         self._chk(lib().fppg_map_particles(self._h, C.byref(o), C.byref(n)))
         self.n = n.value

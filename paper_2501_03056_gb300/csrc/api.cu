@@ -188,11 +188,12 @@ int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *clos
 
 int fppg_map_particles(fppg_ctx *ctx, const fppg_map_opts *opts, int64_t *n_out) {
     if (!ctx || !opts) return FPPG_ERR_ARG;
-    if (opts->band_cells < 0 || opts->band_cells > 64) return fail(ctx->err, FPPG_ERR_ARG, "band_cells outside 0..64");
+    if (opts->band_cells < 0 || opts->band_cells > 64 || opts->inner_cells < 0 || opts->inner_cells > 64)
+        return fail(ctx->err, FPPG_ERR_ARG, "band_cells or inner_cells outside 0..64");
     int64_t n = 0;
     std::vector<int32_t> cls;
     int r = map_particles(ctx->group, ctx->body, opts->surface, opts->volume, opts->features, opts->band_cells,
-                          ctx->stream, &n, cls, ctx->err);
+                          opts->band_cells > 0 ? opts->inner_cells : 0, ctx->stream, &n, cls, ctx->err);
     if (r) return r == 1 ? FPPG_ERR_ARG : (r == 3 ? FPPG_ERR_OOM : (r == 6 ? FPPG_ERR_INTERNAL : FPPG_ERR_CUDA));
     ctx->n = n;
     ctx->cls_host.swap(cls);

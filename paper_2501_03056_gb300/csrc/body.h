@@ -105,8 +105,8 @@ void project_points(Group &g, const float *y, const int32_t *cls, const int32_t 
 int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, double *maxdisp, int64_t *cnt,
           std::string &err);
 // initial particles of Sec. 3.2 into the group (features, surface, volume)
-int map_particles(Group &g, Body &b, int surface, int volume, int features, int band_cells, cudaStream_t s,
-                  int64_t *n_out, std::vector<int32_t> &cls_host, std::string &err);
+int map_particles(Group &g, Body &b, int surface, int volume, int features, int band_cells, int inner_cells,
+                  cudaStream_t s, int64_t *n_out, std::vector<int32_t> &cls_host, std::string &err);
 // energy and gradients (positions y, vertex coordinates verts of body 0)
 int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
            cudaStream_t s, std::string &err);

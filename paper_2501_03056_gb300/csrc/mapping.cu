@@ -177,7 +177,8 @@ template <bool EMIT>
 __global__ void k_map_cells(const float4 *__restrict__ geo, const uint2 *__restrict__ hrng,
                             const uint4 *__restrict__ compact, const int32_t *__restrict__ tlist,
                             const uint32_t *__restrict__ occ, const uint8_t *__restrict__ inside,
-                            const uint8_t *__restrict__ band, MapGrid g, int surface, int volume,
+                            const uint8_t *__restrict__ band, const uint8_t *__restrict__ inner, MapGrid g,
+                            int surface, int volume,
                             uint32_t *__restrict__ sflag, uint32_t *__restrict__ vflag,
                             const uint32_t *__restrict__ soff, const uint32_t *__restrict__ voff, int64_t base_s,
                             int64_t base_v, float4 *__restrict__ pos, int32_t *__restrict__ cons,
@@ -204,7 +205,7 @@ __global__ void k_map_cells(const float4 *__restrict__ geo, const uint2 *__restr
                 }
             }
         }
-    } else if (volume && inside[c]) {
+    } else if (volume && inside[c] && (inner == nullptr || inner[c])) {
         fv = 1;
         if (EMIT) {
             const int cl = (band == nullptr || band[c]) ? kClsV : kClsI;
@@ -280,8 +281,8 @@ void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls)
         }                                                                            \
     } while (0)
 
-int map_particles(Group &g, Body &b, int surface, int volume, int features, int band_cells, cudaStream_t s,
-                  int64_t *n_out, std::vector<int32_t> &cls_host, std::string &err) {
+int map_particles(Group &g, Body &b, int surface, int volume, int features, int band_cells, int inner_cells,
+                  cudaStream_t s, int64_t *n_out, std::vector<int32_t> &cls_host, std::string &err) {
     MapGrid mg;
     for (int k = 0; k < 3; k++) {
         mg.o[k] = b.tg_o[k];
@@ -300,11 +301,11 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
     if (features && b.has_features) b.feature_particles(fxyz, fcls);
     const int64_t nf = (int64_t)fcls.size();
 
-    uint8_t *inside = nullptr, *band = nullptr, *tmp = nullptr;
+    uint8_t *inside = nullptr, *band = nullptr, *tmp = nullptr, *inner = nullptr;
     uint32_t *sflag = nullptr, *vflag = nullptr, *soff = nullptr, *voff = nullptr, *tot = nullptr, *scr = nullptr,
              *error = nullptr;
     auto cleanup = [&]() {
-        void *p[] = {inside, band, tmp, sflag, vflag, soff, voff, tot, scr, error};
+        void *p[] = {inside, band, tmp, inner, sflag, vflag, soff, voff, tot, scr, error};
         for (void *q : p)
             if (q) cudaFree(q);
     };
@@ -332,8 +333,21 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
             k_dilate_axis<<<nblk(cells), 256, 0, s>>>(band, tmp, mg, axis, band_cells);
             std::swap(band, tmp);
         }
+        if (inner_cells > 0) {
+            if (cudaMalloc(&inner, cells)) {
+                cleanup();
+                err = "map_particles: out of device memory";
+                return 3;
+            }
+            k_occ_bytes<<<nblk(cells), 256, 0, s>>>(b.occ, cells, inner);
+            for (int axis = 0; axis < 3; axis++) {
+                k_dilate_axis<<<nblk(cells), 256, 0, s>>>(inner, tmp, mg, axis, band_cells + inner_cells);
+                std::swap(inner, tmp);
+            }
+        }
     }
-    k_map_cells<false><<<nblk(cells), 256, 0, s>>>(b.geo, b.hrng, b.compact, b.tlist, b.occ, inside, band, mg, surface,
+    k_map_cells<false><<<nblk(cells), 256, 0, s>>>(b.geo, b.hrng, b.compact, b.tlist, b.occ, inside, band, inner, mg,
+                                                   surface,
                                                    volume, sflag, vflag, nullptr, nullptr, 0, 0, nullptr, nullptr,
                                                    nullptr);
     exclusive_scan_u32(sflag, soff, cells, tot, scr, sc, s);
@@ -373,7 +387,8 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
         CKM(cudaMemcpyAsync(dcls, fcls.data(), sizeof(int32_t) * nf, cudaMemcpyHostToDevice, s));
         CKM(cudaStreamSynchronize(s));
     }
-    k_map_cells<true><<<nblk(cells), 256, 0, s>>>(b.geo, b.hrng, b.compact, b.tlist, b.occ, inside, band, mg, surface,
+    k_map_cells<true><<<nblk(cells), 256, 0, s>>>(b.geo, b.hrng, b.compact, b.tlist, b.occ, inside, band, inner, mg,
+                                                  surface,
                                                   volume, nullptr, nullptr, soff, voff, nf, nf + ns, g.d.pos,
                                                   g.d.cons, dcls);
     cls_host.assign(N, 0);

@@ -200,25 +200,100 @@ def gear_profile(teeth: int = 40, r_out: float = 1.0, r_root: float = 0.9,
     return xy
 
 
+def _zipper(inner, outer, ai, ao):
+    """Triangles between two closed rings whose angles increase from 0 to
+    2 pi (star-shaped about the axis): walk both rings in angle order."""
+    ni, no = len(inner), len(outer)
+    ti = np.r_[ai, ai[0] + 2 * np.pi]
+    to = np.r_[ao, ao[0] + 2 * np.pi]
+    i = j = 0
+    tris = []
+    while i < ni or j < no:
+        if j >= no or (i < ni and ti[i + 1] <= to[j + 1]):
+            tris.append([inner[i % ni], outer[j % no], inner[(i + 1) % ni]])
+            i += 1
+        else:
+            tris.append([inner[i % ni], outer[j % no], outer[(j + 1) % no]])
+            j += 1
+    return tris
+
+
+def gear_mesh(teeth: int = 40, r_out: float = 1.0, r_root: float = 0.9, r_bore: float = 0.3,
+              height: float = 0.3, pts_per_tooth: int = 6, rings: int = 20, nz: int = 12,
+              bore_points: int = 240):
+    """Closed spur gear: trapezoidal teeth extruded along z, with a bore.
+
+    Top and bottom faces are rings of points (bore circle, intermediate
+    circles, tooth outline) joined by a zipper; the outer wall and the bore
+    wall are nz layers of quads.  Outward orientation by construction."""
+    outline = gear_profile(teeth, r_out, r_root, pts_per_tooth)
+    ang_o = np.mod(np.arctan2(outline[:, 1], outline[:, 0]), 2 * np.pi)
+    ring_xy, ring_ang = [], []
+    radii = np.linspace(r_bore, 0.98 * r_root, rings)
+    for k, r in enumerate(radii):
+        n = int(round(bore_points + (len(outline) - bore_points) * k / max(rings - 1, 1)))
+        a = 2.0 * np.pi * np.arange(n) / n
+        ring_xy.append(np.stack([r * np.cos(a), r * np.sin(a)], 1))
+        ring_ang.append(a)
+    ring_xy.append(outline)
+    ring_ang.append(ang_o)
+    verts, tris = [], []
+    zs = np.linspace(-height / 2, height / 2, nz + 1)
+    # face rings at the two ends
+    face_ids = {}
+    for side, z in ((0, zs[0]), (1, zs[-1])):
+        ids = []
+        for xy in ring_xy:
+            start = len(verts)
+            verts.extend([(x, y, z) for x, y in xy])
+            ids.append(np.arange(start, start + len(xy)))
+        face_ids[side] = ids
+        for k in range(len(ring_xy) - 1):
+            t = _zipper(ids[k], ids[k + 1], ring_ang[k], ring_ang[k + 1])
+            # zipper triangles are counter-clockwise seen from +z
+            tris.extend(t if side == 1 else [[a, c, b] for a, b, c in t])
+    # walls: interior layers get new vertices, the end layers reuse the rings
+    def wall(ring, outward):
+        m = len(ring_xy[ring])
+        layers = [face_ids[0][ring]]
+        for z in zs[1:-1]:
+            start = len(verts)
+            verts.extend([(x, y, z) for x, y in ring_xy[ring]])
+            layers.append(np.arange(start, start + m))
+        layers.append(face_ids[1][ring])
+        for k in range(nz):
+            lo, hi = layers[k], layers[k + 1]
+            for i in range(m):
+                a, b, c, d = lo[i], lo[(i + 1) % m], hi[(i + 1) % m], hi[i]
+                tris.extend([[a, b, c], [a, c, d]] if outward else [[a, c, b], [a, d, c]])
+    wall(len(ring_xy) - 1, True)      # tooth outline: counter-clockwise ring, outward
+    wall(0, False)                    # bore: the solid lies outside the circle
+    return np.array(verts, dtype=np.float32), np.array(tris, dtype=np.int32)
+
+
 # --------------------------------------------------------------------------
 # particle sets
 # --------------------------------------------------------------------------
 @dataclass
 class Assembly:
-    """One body: its mesh, spacing and initial particles."""
+    """One body: its mesh, spacing and initial particles.
+
+    ``xyz``/``cls`` are None for bodies whose initial particles come from
+    the method's own generation (Sec. 3.2); ``meta["generate"]`` then holds
+    its options (band_cells, inner_cells)."""
     name: str
     verts: np.ndarray          # float32 [nv, 3]
     tris: np.ndarray           # int32 [nt, 3]
     dx: float
     h: float
-    xyz: np.ndarray            # float32 [n, 3]
-    cls: np.ndarray            # int32 [n]
+    xyz: np.ndarray | None     # float32 [n, 3]
+    cls: np.ndarray | None     # int32 [n]
     dihedral_deg: float | None = None   # feature threshold; None = no features
     meta: dict = field(default_factory=dict)
 
     @property
     def n(self) -> int:
-        return int(self.xyz.shape[0])
+        return 0 if self.xyz is None else int(self.xyz.shape[0])
 
 
 def smoothing_length(dx: float, factor: float = 1.3) -> float:
@@ -396,3 +471,37 @@ def sphere_torus_workload(seed: int = 1, dx: float = 0.02, level: int = 5,
     dxf = float(np.float32(dx))
     return [Assembly("icosphere", sv, st, dxf, smoothing_length(dx), sx, sc, None, {"n_iter": 500}),
             Assembly("torus", tv, tt, dxf, smoothing_length(dx), tx, tc, None, {"n_iter": 500})]
+
+
+def gear_workload(dx: float = 0.004) -> list[Assembly]:
+    """Spur gear: 40 trapezoidal teeth, outer r = 1, root r = 0.9, bore
+    r = 0.3, height 0.3 (51,840 triangles), 30 degree features, dx = 0.004;
+    particles from the generation of Sec. 3.2 with a band of 2 cells of
+    relaxing volume particles and 1 cell of fixed innermost ones (~2.4 M)."""
+    v, t = gear_mesh()
+    dxf = float(np.float32(dx))
+    return [Assembly("gear", v, t, dxf, smoothing_length(dx), None, None, 30.0,
+                     {"n_iter": 500, "generate": {"band_cells": 2, "inner_cells": 1}})]
+
+
+def batch_workload(seed: int = 3, bodies: int = 64, dx: float = 0.008) -> list[Assembly]:
+    """Batch of bodies of uneven size: cubes, cylinders, icospheres and gears
+    at seeded scales 0.1-1 (uniform), one spacing dx; particles from the
+    generation of Sec. 3.2 with a 3-cell relaxing band and a 1-cell fixed
+    innermost layer (a few thousand to ~470 k particles per body)."""
+    shapes = ("cube", "cylinder", "sphere", "gear")
+    u = uniform01(seed, np.arange(bodies), 0)
+    kind = (uniform01(seed, np.arange(bodies), 1) * len(shapes)).astype(int)
+    dxf = float(np.float32(dx))
+    meshes = {"cube": cube_mesh(0.5), "cylinder": cylinder_mesh(0.5, 1.0, 64, 8), "sphere": icosphere_mesh(4, 0.5),
+              "gear": gear_mesh(teeth=24, r_out=0.5, r_root=0.45, r_bore=0.15, height=0.2, pts_per_tooth=4,
+                                rings=8, nz=6, bore_points=96)}
+    out = []
+    for b in range(bodies):
+        scale = 0.1 + 0.9 * float(u[b])
+        name = shapes[kind[b]]
+        v, t = meshes[name]
+        out.append(Assembly(f"{name}{b}", (v.astype(np.float64) * scale).astype(np.float32), t, dxf,
+                            smoothing_length(dx), None, None, 30.0,
+                            {"n_iter": 50, "scale": scale, "generate": {"band_cells": 3, "inner_cells": 1}}))
+    return out

@@ -1,0 +1,153 @@
+"""Parity at the full sizes of the procedural gear (~2.4 M particles) and
+the 64-body batch (~8.1 M particles), in the launch configuration the
+benchmark uses (autotuned batch, CUDA graph), plus the energy backward
+on a 5 k-particle crop of the gear against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2501_03056_gb300 as pkg
+from paper_2501_03056_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2501_03056_gb300 import _build
+    _build.build()
+
+
+@pytest.fixture(scope="module")
+def gear():
+    a = W.gear_workload()[0]
+    o = O.from_assembly(a)            # the oracle's own generation
+    x, c, cons = o.get_particles()
+    return a, o, x.astype(np.float32), c, cons
+
+
+def test_gear_generation_at_full_size(gear):
+    a, o, x, c, cons = gear
+    b = pkg.Body.from_assembly(a)     # generation on the GPU
+    gx, gc, gcons = b.get_particles()
+    assert len(gx) == len(x) and np.array_equal(gc, c)
+    s = c == W.CLS_S
+    assert (gcons[s] == cons[s]).mean() > 0.999
+    assert np.abs(gx.astype(np.float64) - x).max() < 2e-6
+
+
+def test_gear_relaxation_at_full_size(gear):
+    a, o, x, c, cons = gear
+    b = pkg.Body(a.verts, a.tris, a.dx, a.h)
+    b.extract_features(a.dihedral_deg)
+    b.set_particles(x, c)
+    b.set_constraints(cons)
+    key, perm, *_ = b.debug_grid()
+    okey, operm = o.keys()
+    assert np.array_equal(key, okey) and np.array_equal(perm, operm)
+    _, cnt, amax = b.debug_forces()
+    _, ocnt, oamax = o.forces()
+    assert np.array_equal(cnt, ocnt) and amax == pytest.approx(oamax, rel=1e-5)
+    batch = pkg.Batch([b])
+    batch.autotune(1)
+    batch.set_graph_iters(2)
+    batch.relax(2, use_graph=True)
+    batch.store()
+    o.relax(2)
+    err = np.abs(b.get_particles()[0].astype(np.float64) - o.get_particles()[0]).max(axis=1) / a.dx
+    assert (err < 1e-4).mean() > 0.9999 and err.max() < 1.3 / 16.0
+    s, so = b.stats(), o.stats()
+    for k in ("mean_S", "mean_V", "mean_F", "std_S", "std_V"):
+        assert s[k] == pytest.approx(so[k], rel=1e-2), k
+    # generated surface particles on sharp edges nearly coincide with feature
+    # particles (~5e-5 dx apart, i.e. ~2e-7 in coordinates): that distance is
+    # at FP32 coordinate rounding (ulp(1) / dx ~ 3e-5 dx here), so it is
+    # compared to that floor
+    assert s["min_pair_over_dx"] == pytest.approx(so["min_pair_over_dx"], rel=1e-2, abs=1e-4)
+
+
+def test_gear_energy_backward_on_a_5k_crop(gear):
+    import torch
+    a, o_full, x, c, cons = gear
+    # particles near one tooth (the crop keeps its triangles frozen)
+    sel = np.where((np.abs(x[:, 1]) < 0.05) & (x[:, 0] > 0.85))[0][:5000]
+    assert len(sel) >= 2000
+    xc, cc, consc = x[sel], c[sel], cons[sel]
+    o = O.Oracle(a.verts, a.tris, a.dx, a.h)
+    o.set_particles(xc, cc)
+    o.set_state(xc.astype(np.float64), consc)
+    b = pkg.Body(a.verts, a.tris, a.dx, a.h)
+    b.set_particles(xc, cc)
+    b.set_constraints(consc)
+    rng = np.random.default_rng(8)
+    y = xc.astype(np.float64) + rng.normal(size=xc.shape) * 0.01 * a.dx * (cc == W.CLS_S)[:, None]
+    y32 = y.astype(np.float32)
+    E, gy, gV = o.energy_projected(y32.astype(np.float64))
+    # FP64 central differences on the oracle (positions and vertices)
+    eps = 1e-6 * a.dx
+    yd = y32.astype(np.float64)
+    for i in rng.choice(np.where(cc == W.CLS_S)[0], 6, replace=False):
+        for k in range(3):
+            yp, ym = yd.copy(), yd.copy()
+            yp[i, k] += eps
+            ym[i, k] -= eps
+            fd = (o.energy_projected(yp, grad=False) - o.energy_projected(ym, grad=False)) / (2 * eps)
+            assert gy[i, k] == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(gy).max())
+    V0 = a.verts.astype(np.float64)
+    used = np.unique(a.tris[consc[cc == W.CLS_S]])
+    for vi in rng.choice(used, 6, replace=False):
+        for k in range(3):
+            vp, vm = V0.copy(), V0.copy()
+            vp[vi, k] += eps
+            vm[vi, k] -= eps
+            fd = (o.energy_projected(yd, vp, grad=False) - o.energy_projected(yd, vm, grad=False)) / (2 * eps)
+            assert gV[vi, k] == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(gV).max())
+    # the GPU backward against the oracle's gradients
+    yt = torch.from_numpy(y32).cuda()
+    vt = torch.from_numpy(a.verts).cuda()
+    gyt, gvt = torch.empty_like(yt), torch.empty_like(vt)
+    Eg = b.energy_ptr(yt.data_ptr(), vt.data_ptr(), gyt.data_ptr(), gvt.data_ptr())
+    torch.cuda.synchronize()
+    assert Eg == pytest.approx(E, rel=1e-5)
+    assert np.abs(gyt.cpu().numpy() - gy).max() <= 1e-4 * np.abs(gy).max()
+    assert np.abs(gvt.cpu().numpy() - gV).max() <= 1e-4 * np.abs(gV).max()
+
+
+def test_batch_of_64_bodies_batched_equals_plain_at_full_size():
+    asm = W.batch_workload()
+    plain = [pkg.Body.from_assembly(a) for a in asm]
+    batched = [pkg.Body.from_assembly(a) for a in asm]
+    n = sum(p.n for p in plain)
+    assert 7.5e6 < n < 8.5e6 and min(p.n for p in plain) >= 1000 and max(p.n for p in plain) <= 500000
+    bt = pkg.Batch(batched)
+    bt.autotune(1)
+    bt.set_graph_iters(4)
+    bt.relax(8, use_graph=True)
+    bt.store()
+    for p in plain:
+        p.relax(8)
+    for p, q in zip(plain, batched):
+        x, _, c = p.get_particles()
+        y, _, d = q.get_particles()
+        assert np.array_equal(x, y) and np.array_equal(c, d)
+
+
+def test_batch_bodies_match_the_oracle():
+    asm = W.batch_workload()
+    order = np.argsort([a.meta["scale"] for a in asm])
+    for i in list(order[:3]) + [order[len(order) // 2]]:      # three small bodies and a middle one
+        a = asm[i]
+        o = O.from_assembly(a)
+        x, c, cons = o.get_particles()
+        b = pkg.Body.from_assembly(a)
+        gx, gc, _ = b.get_particles()
+        assert np.array_equal(gc, c) and np.abs(gx.astype(np.float64) - x).max() < 2e-6
+        b.set_particles(x.astype(np.float32), c)
+        b.set_constraints(cons)
+        b.relax(3)
+        o.relax(3)
+        err = np.abs(b.get_particles()[0].astype(np.float64) - o.get_particles()[0]).max(axis=1) / a.dx
+        assert (err < 1e-4).mean() > 0.999 and err.max() < 1.3 / 16.0, (a.name, err.max())
