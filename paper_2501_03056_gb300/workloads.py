@@ -505,3 +505,158 @@ def batch_workload(seed: int = 3, bodies: int = 64, dx: float = 0.008) -> list[A
                             smoothing_length(dx), None, None, 30.0,
                             {"n_iter": 50, "scale": scale, "generate": {"band_cells": 3, "inner_cells": 1}}))
     return out
+
+
+# --------------------------------------------------------------------------
+# vehicle-like shell (union of rounded boxes and wheels)
+# --------------------------------------------------------------------------
+def _sd_round_box(p, centre, half, radius):
+    q = np.abs(p - np.asarray(centre)) - (np.asarray(half) - radius)
+    outside = np.linalg.norm(np.maximum(q, 0.0), axis=-1)
+    inside = np.minimum(np.max(q, axis=-1), 0.0)
+    return outside + inside - radius
+
+
+def _sd_cylinder_y(p, centre, radius, half_width):
+    d = p - np.asarray(centre)
+    r = np.sqrt(d[..., 0] ** 2 + d[..., 2] ** 2) - radius
+    w = np.abs(d[..., 1]) - half_width
+    return np.minimum(np.maximum(r, w), 0.0) + np.sqrt(np.maximum(r, 0.0) ** 2 + np.maximum(w, 0.0) ** 2)
+
+
+def vehicle_sdf(p):
+    """Signed distance (approximate inside the union) of a car-like body:
+    chassis and cabin as rounded boxes, four wheels as cylinders along y."""
+    d = _sd_round_box(p, (0.0, 0.0, 0.55), (2.0, 0.9, 0.3), 0.15)
+    d = np.minimum(d, _sd_round_box(p, (-0.2, 0.0, 1.05), (1.1, 0.75, 0.25), 0.2))
+    for x in (-1.3, 1.3):
+        for y in (-0.85, 0.85):
+            d = np.minimum(d, _sd_cylinder_y(p, (x, y, 0.38), 0.36, 0.16))
+    return d
+
+
+def surface_nets(sdf, lo, hi, spacing):
+    """Closed triangle mesh of {sdf = 0} by surface nets: one vertex per grid
+    cell whose corners change sign (mean of the edge crossings), one quad
+    (two triangles) per grid edge that changes sign, wound so that the
+    normal points from negative (inside) to positive values."""
+    axes = [np.arange(lo[a], hi[a] + spacing, spacing) for a in range(3)]
+    n = [len(x) for x in axes]
+    G = np.stack(np.meshgrid(*axes, indexing="ij"), -1)
+    f = sdf(G)
+    f[f == 0.0] = 1e-12
+    inside = f < 0
+    # cells with a sign change
+    cs = np.zeros((n[0] - 1, n[1] - 1, n[2] - 1), dtype=np.int8)
+    corners = [(i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+    for (i, j, k) in corners:
+        cs += inside[i:n[0] - 1 + i, j:n[1] - 1 + j, k:n[2] - 1 + k]
+    active = (cs > 0) & (cs < 8)
+    idx = -np.ones(active.shape, dtype=np.int64)
+    cells = np.argwhere(active)
+    idx[active] = np.arange(len(cells))
+    # vertex = mean of the crossings on the 12 cell edges
+    acc = np.zeros((len(cells), 3))
+    cnt = np.zeros(len(cells))
+    ci, cj, ck = cells[:, 0], cells[:, 1], cells[:, 2]
+    for (a, b) in [((0, 0, 0), (1, 0, 0)), ((0, 1, 0), (1, 1, 0)), ((0, 0, 1), (1, 0, 1)), ((0, 1, 1), (1, 1, 1)),
+                   ((0, 0, 0), (0, 1, 0)), ((1, 0, 0), (1, 1, 0)), ((0, 0, 1), (0, 1, 1)), ((1, 0, 1), (1, 1, 1)),
+                   ((0, 0, 0), (0, 0, 1)), ((1, 0, 0), (1, 0, 1)), ((0, 1, 0), (0, 1, 1)), ((1, 1, 0), (1, 1, 1))]:
+        fa = f[ci + a[0], cj + a[1], ck + a[2]]
+        fb = f[ci + b[0], cj + b[1], ck + b[2]]
+        ch = (fa < 0) != (fb < 0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = np.where(ch, fa / np.where(ch, fa - fb, 1.0), 0.0)
+        pa = G[ci + a[0], cj + a[1], ck + a[2]]
+        pb = G[ci + b[0], cj + b[1], ck + b[2]]
+        acc[ch] += (pa + t[:, None] * (pb - pa))[ch]
+        cnt[ch] += 1
+    verts = acc / cnt[:, None]
+    tris = []
+    # a grid edge along axis a between points p and p + e_a is shared by the
+    # four cells around it; those cells' vertices form the quad
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        sl0 = [slice(None)] * 3
+        sl1 = [slice(None)] * 3
+        sl0[a] = slice(0, n[a] - 1)
+        sl1[a] = slice(1, n[a])
+        ch = inside[tuple(sl0)] != inside[tuple(sl1)]
+        e = np.argwhere(ch)
+        # the four cells: offsets 0/-1 along b and c
+        ok = (e[:, b] >= 1) & (e[:, b] <= n[b] - 2) & (e[:, c] >= 1) & (e[:, c] <= n[c] - 2)
+        e = e[ok]
+        flip = inside[tuple(e.T)]          # inside at the lower end: normal along +a
+        def cell(db, dc):
+            q = e.copy()
+            q[:, b] -= db
+            q[:, c] -= dc
+            return idx[q[:, 0], q[:, 1], q[:, 2]]
+        v00, v10, v11, v01 = cell(1, 1), cell(0, 1), cell(0, 0), cell(1, 0)
+        q1 = np.stack([v00, v10, v11], 1)
+        q2 = np.stack([v00, v11, v01], 1)
+        r1 = np.stack([v00, v11, v10], 1)
+        r2 = np.stack([v00, v01, v11], 1)
+        tris.append(np.where(flip[:, None], q1, r1))
+        tris.append(np.where(flip[:, None], q2, r2))
+    return verts, np.concatenate(tris).astype(np.int64)
+
+
+def loop_subdivide(verts, tris):
+    """One step of Loop subdivision (Loop, 1987): edge points 3/8 (a + b) +
+    1/8 (c + d), vertex points (1 - n beta) v + beta sum(neighbours) with
+    beta = (5/8 - (3/8 + cos(2 pi / n) / 4)^2) / n; each triangle -> 4."""
+    v = np.asarray(verts, dtype=np.float64)
+    t = np.asarray(tris, dtype=np.int64)
+    nv = len(v)
+    e = np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]])
+    opp = np.concatenate([t[:, 2], t[:, 0], t[:, 1]])
+    key = np.minimum(e[:, 0], e[:, 1]) * nv + np.maximum(e[:, 0], e[:, 1])
+    uk, inv = np.unique(key, return_inverse=True)
+    ne = len(uk)
+    a, b = uk // nv, uk % nv
+    osum = np.zeros((ne, 3))
+    ocnt = np.zeros(ne)
+    np.add.at(osum, inv, v[opp])
+    np.add.at(ocnt, inv, 1)
+    ep = np.where((ocnt == 2)[:, None], 0.375 * (v[a] + v[b]) + 0.125 * osum, 0.5 * (v[a] + v[b]))
+    nsum = np.zeros((nv, 3))
+    deg = np.zeros(nv)
+    np.add.at(nsum, a, v[b])
+    np.add.at(nsum, b, v[a])
+    np.add.at(deg, a, 1)
+    np.add.at(deg, b, 1)
+    beta = (0.625 - (0.375 + 0.25 * np.cos(2 * np.pi / np.maximum(deg, 3))) ** 2) / np.maximum(deg, 1)
+    vp = (1 - deg * beta)[:, None] * v + beta[:, None] * nsum
+    mid = nv + inv.reshape(3, -1).T             # edge point ids of (ab, bc, ca)
+    ab, bc, ca = mid[:, 0], mid[:, 1], mid[:, 2]
+    new = np.concatenate([np.stack([t[:, 0], ab, ca], 1), np.stack([t[:, 1], bc, ab], 1),
+                          np.stack([t[:, 2], ca, bc], 1), np.stack([ab, bc, ca], 1)])
+    return np.vstack([vp, ep]), new
+
+
+def vehicle_mesh(spacing: float = 0.021, noise: float = 1e-3, seed: int = 5, subdivide: int = 2):
+    """Closed vehicle-like shell: surface nets of vehicle_sdf, Loop
+    subdivision, then seeded vertex noise of amplitude `noise` along the
+    vertex normals (counter-based jitter)."""
+    v, t = surface_nets(vehicle_sdf, (-2.4, -1.2, -0.2), (2.4, 1.2, 1.6), spacing)
+    for _ in range(subdivide):
+        v, t = loop_subdivide(v, t)
+    nrm = np.zeros_like(v)
+    fn = np.cross(v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]])
+    for k in range(3):
+        np.add.at(nrm, t[:, k], fn)
+    nrm /= np.maximum(np.linalg.norm(nrm, axis=1, keepdims=True), 1e-30)
+    v = v + nrm * jitter(seed, np.arange(len(v)), 0, noise)[:, None]
+    return v.astype(np.float32), t.astype(np.int32)
+
+
+def vehicle_workload(dx: float = 0.0068, spacing: float = 0.021) -> list[Assembly]:
+    """Vehicle-like closed shell (~2 M triangles after two Loop steps, 1e-3
+    vertex noise, 30 degree features) at a spacing giving ~20 M surface and
+    volume particles from the generation of Sec. 3.2 (every interior cell
+    relaxes)."""
+    v, t = vehicle_mesh(spacing)
+    dxf = float(np.float32(dx))
+    return [Assembly("vehicle", v, t, dxf, smoothing_length(dx), None, None, 30.0,
+                     {"n_iter": 1000, "generate": {"band_cells": 0, "inner_cells": 0}})]
