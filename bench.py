@@ -36,8 +36,9 @@ L2_FLUSH_BYTES = 256 << 20
 SMS, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 # DRAM bytes (read + write) of one k_force launch on the default workload
 # (dx = 0.02), from the ncu capture summarised in
-# profiles/k_force_icosphere_torus_dx002.md; None for other workloads.
-K_FORCE_DRAM_BYTES = {0.02: 13661952}
+# profiles/k_force_icosphere_torus_dx002.md; None for other workloads and
+# until the current kernel has been captured.
+K_FORCE_DRAM_BYTES = {}
 
 
 def parse():
@@ -196,11 +197,12 @@ def main():
     n = sum(a.n for a in asm)
     stream = torch.cuda.current_stream()
     bodies = [pkg.Body.from_assembly(a, stream=stream) for a in asm]
-    cand = pairs = 0
+    cand = pairs = tested = 0
     for b in bodies:
-        c, p = b.work_counts()
+        c, p, t = b.work_counts()
         cand += c
         pairs += p
+        tested += t
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -325,6 +327,7 @@ def main():
     fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12     # TFLOP/s, FMA = 2
     flops = 8.0 * cand + 12.0 * pairs                           # per force launch (all bodies)
     achieved = flops / (force_ms / 1e3) / 1e12
+    executed = (8.0 * tested + 12.0 * pairs) / (force_ms / 1e3) / 1e12
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     useful_gbs = 56.0 * value / world / 1e9
     line = {
@@ -338,7 +341,8 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": K_FORCE_DRAM_BYTES.get(round(args.dx, 6)),
                      "peak_kind": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz ({peak_kind} clock)",
-                     "flops_per_launch": flops, "candidates": cand, "pairs": pairs, "force_ms": force_ms},
+                     "flops_per_launch": flops, "candidates": cand, "pairs": pairs, "force_ms": force_ms,
+                     "tested": tested, "executed_TFLOPs": executed, "executed_frac": executed / fp32_peak},
         "hbm": {"useful_bytes_per_particle_iteration": 56, "useful_GBps": useful_gbs,
                 "frac_of_measured": useful_gbs / hbm},
         "gpu_launches": kpi * G * K,

@@ -192,9 +192,12 @@ int fppg_project_points(fppg_ctx *ctx, const float *y_host, const int32_t *cls_h
                         int64_t n, float *x_host, int32_t *cons_out_host, int32_t *ok_host);
 
 /* Work of one force pass (A4) on the current state, summed over mobile
- * particles: candidates = particles in the 27 neighbour cells tested by the
- * FP32 distance rule, pairs = masked neighbours within 2h.  Synchronises. */
-int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs);
+ * particles: candidates = particles in the 27 neighbour cells around each
+ * particle (the search set of the cell grid, Sec. 3.1.3), pairs = masked
+ * neighbours within 2h (Eq. 15), tested = candidates the force kernel
+ * actually tests after cutting each grid row to the x-slabs within reach.
+ * Any output may be NULL.  Synchronises. */
+int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs, int64_t *tested);
 
 /* ---- uniformity energy and its backward -------------------------------------
  * E = sum over mobile i of (rho_i - W0_{c_i})^2, rho_i = W(0) + sum over the

@@ -851,9 +851,35 @@ static void cell_of(const or_ctx *c, const double *x, int32_t *ci)
     for (int k = 0; k < 3; k++) ci[k] = cell_coord((float)x[k], c->ng_o[k], c->ng_inv, c->ng_n[k]);
 }
 
-static uint32_t key_of(const or_ctx *c, const int32_t *ci)
+/* Sort key of a particle: its cell refined by one of 8 slabs along x.  The
+ * paper sorts particles by cell (Sec. 3.1.3) and leaves their order inside
+ * a cell open; this order takes, inside each cell, the fine x coordinate
+ * clamp(floor(8 t), 0, 8 n - 1), t = (x - o) * inv in FP32, whose top bits
+ * are the cell's x (8 t is exact).  key = 8 * cell index + slab, so every
+ * cell owns the 8 consecutive keys [8 cell, 8 cell + 8). */
+#define OR_SLABS 8
+
+static int32_t fine_coord(float x, float o, float inv, int32_t n)
+{
+    float t = x - o;
+    t = t * inv;
+    t = t * (float)OR_SLABS;
+    t = fmaxf(t, 0.0f);
+    t = fminf(t, (float)(OR_SLABS * n - 1));
+    return (int32_t)t;
+}
+
+static uint32_t cell_index(const or_ctx *c, const int32_t *ci)
 {
     return (uint32_t)ci[0] + (uint32_t)c->ng_n[0] * ((uint32_t)ci[1] + (uint32_t)c->ng_n[1] * (uint32_t)ci[2]);
+}
+
+static uint32_t key_of(const or_ctx *c, const double *x)
+{
+    int32_t ci[3];
+    cell_of(c, x, ci);
+    int32_t fx = fine_coord((float)x[0], c->ng_o[0], c->ng_inv, c->ng_n[0]);
+    return OR_SLABS * cell_index(c, ci) + (uint32_t)(fx % OR_SLABS);
 }
 
 static int kv_cmp(const void *pa, const void *pb)
@@ -869,9 +895,7 @@ static or_kv *build_cells(const or_ctx *c, const double *X, int64_t n)
 {
     or_kv *L = malloc(sizeof(or_kv) * (n ? n : 1));
     for (int64_t i = 0; i < n; i++) {
-        int32_t ci[3];
-        cell_of(c, X + 3 * i, ci);
-        L[i].key = key_of(c, ci);
+        L[i].key = key_of(c, X + 3 * i);
         L[i].id = (uint32_t)i;
     }
     qsort(L, (size_t)n, sizeof(or_kv), kv_cmp);
@@ -901,17 +925,17 @@ void oracle_keys(const or_ctx *c, uint32_t *key, uint32_t *perm)
     free(L);
 }
 
-/* Occupied cells with their [start, end) ranges in sorted order (C_compact
- * begin / length). Returns the count. */
+/* Occupied cells (cell index = key / 8) with their [start, end) ranges in
+ * sorted order (C_compact begin / length). Returns the count. */
 int64_t oracle_cell_ranges(const or_ctx *c, uint32_t *cell, uint32_t *start, uint32_t *end, int64_t cap)
 {
     or_kv *L = build_cells(c, c->X, c->n);
     int64_t m = 0;
     for (int64_t k = 0; k < c->n;) {
         int64_t e = k;
-        while (e < c->n && L[e].key == L[k].key) e++;
+        while (e < c->n && L[e].key / OR_SLABS == L[k].key / OR_SLABS) e++;
         if (m < cap) {
-            cell[m] = L[k].key;
+            cell[m] = L[k].key / OR_SLABS;
             start[m] = (uint32_t)k;
             end[m] = (uint32_t)e;
         }
@@ -949,8 +973,8 @@ static void for_neighbours(const or_ctx *c, const double *X, const int32_t *cls,
                 if (cc[0] < 0 || cc[1] < 0 || cc[2] < 0 || cc[0] >= c->ng_n[0] || cc[1] >= c->ng_n[1] ||
                     cc[2] >= c->ng_n[2])
                     continue;
-                uint32_t key = key_of(c, cc);
-                for (int64_t k = lower_bound_kv(L, n, key); k < n && L[k].key == key; k++) {
+                uint32_t key = OR_SLABS * cell_index(c, cc);
+                for (int64_t k = lower_bound_kv(L, n, key); k < n && L[k].key < key + OR_SLABS; k++) {
                     int64_t j = L[k].id;
                     if (j == i) continue;
                     if (masked && !acts_on(cls[i], cls[j])) continue;

@@ -76,7 +76,7 @@ def lib():
                 "fppg_debug_forces": [vp, P_(f32), P_(i32), P_(f32)],
                 "fppg_project_points": [vp, P_(f32), P_(i32), P_(i32), i64, P_(f32), P_(i32), P_(i32)],
                 "fppg_energy": [vp, vp, vp, P_(f64), vp, vp],
-                "fppg_work_counts": [vp, P_(i64), P_(i64)],
+                "fppg_work_counts": [vp, P_(i64), P_(i64), P_(i64)],
                 "fppg_batch_load": [vp],
                 "fppg_copy_positions_dev": [vp, vp],
                 "fppg_batch_create": [P_(vp), i32, P_(vp)],
@@ -282,10 +282,11 @@ class Body:
         return x[:m], co[:m], ok[:m].astype(bool)
 
     def work_counts(self):
-        """(candidates, pairs) of one force pass on the current state."""
-        c, p = C.c_int64(), C.c_int64()
-        self._chk(lib().fppg_work_counts(self._h, C.byref(c), C.byref(p)))
-        return c.value, p.value
+        """(candidates in the 27 cells, pairs within 2h, candidates actually
+        tested by the force kernel) of one force pass on the current state."""
+        c, p, t = C.c_int64(), C.c_int64(), C.c_int64()
+        self._chk(lib().fppg_work_counts(self._h, C.byref(c), C.byref(p), C.byref(t)))
+        return c.value, p.value, t.value
 
     def energy_ptr(self, y_ptr: int, verts_ptr: int = 0, gy_ptr: int = 0, gv_ptr: int = 0) -> float:
         """Energy (and gradients into device buffers) from device pointers."""

@@ -356,31 +356,36 @@ int fppg_debug_forces(fppg_ctx *ctx, float *acc_host, int32_t *count_host, float
     return FPPG_OK;
 }
 
-int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs) {
+int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs, int64_t *tested) {
     if (!ctx) return FPPG_ERR_ARG;
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
     Group &g = ctx->group;
     const int64_t n = ctx->n;
-    int64_t c = 0, p = 0;
+    int64_t c = 0, p = 0, t = 0;
     if (n > 0) {
-        int32_t *dcnt = nullptr, *dcand = nullptr;
+        int32_t *dcnt = nullptr, *dcand = nullptr, *dtest = nullptr;
         CUDA_OR(ctx->err, cudaMalloc(&dcnt, sizeof(int32_t) * n));
         CUDA_OR(ctx->err, cudaMalloc(&dcand, sizeof(int32_t) * n));
+        CUDA_OR(ctx->err, cudaMalloc(&dtest, sizeof(int32_t) * n));
         build_grid(g, ctx->stream);
-        forces(g, ctx->stream, dcnt, dcand);
-        std::vector<int32_t> hc(n), hp(n);
+        forces(g, ctx->stream, dcnt, dcand, dtest);
+        std::vector<int32_t> hc(n), hp(n), ht(n);
         CUDA_OR(ctx->err, cudaMemcpyAsync(hc.data(), dcand, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_OR(ctx->err, cudaMemcpyAsync(hp.data(), dcnt, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_OR(ctx->err, cudaMemcpyAsync(ht.data(), dtest, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
         cudaFree(dcnt);
         cudaFree(dcand);
+        cudaFree(dtest);
         for (int64_t k = 0; k < n; k++) {
             c += hc[k];
+            t += ht[k];
             if (hc[k] > 0) p += hp[k];
         }
     }
     if (candidates) *candidates = c;
     if (pairs) *pairs = p;
+    if (tested) *tested = t;
     return FPPG_OK;
 }
 
@@ -479,7 +484,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         ow += 2 * bd.occ_words;
     }
     b->off.push_back(N);
-    if (cells >= 0xffffffffLL || N > ((int64_t)1 << 31) || ow >= 0xffffffffLL) {
+    if (cells >= ((int64_t)1 << 29) || N > ((int64_t)1 << 31) || ow >= 0xffffffffLL) {
         delete b;
         return fail_global(FPPG_ERR_ARG, "batch too large for 32-bit keys");
     }

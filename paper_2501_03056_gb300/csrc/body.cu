@@ -6,13 +6,6 @@
 
 namespace fppg {
 
-namespace {
-int bits_for(uint64_t maxval) {
-    int b = 0;
-    while (b < 64 && (maxval >> b) != 0) b++;
-    return b;
-}
-} // namespace
 
 // Feature lines from the sorted feature-edge list (Sec. 3.2.2): walks that
 // start at singular vertices (feature degree 1 or > 2) in ascending vertex
@@ -166,6 +159,7 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
         A.tg_n[k] = b.tg_n[k];
     }
     A.ng_inv = b.ng_inv;
+    A.slab_r2 = slab_reach2(b.R2, b.ng_inv);
     A.tg_inv = b.tg_inv;
     A.key_base = key_base;
     A.hash_mask = (uint32_t)(b.hash_size - 1);
@@ -211,7 +205,7 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     g.N = N;
     const size_t n1 = (size_t)std::max<int64_t>(N, 1);
     g.n_tiles = (int)std::max<int64_t>(radix_tiles(N), 1);
-    g.key_bits = bits_for((uint64_t)std::max<int64_t>(g.total_cells - 1, 1));
+    g.key_bits = fine_key_bits(g.total_cells);
     g.passes = (g.key_bits + 7) / 8;
     CKA(cudaMalloc(&g.pos, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.cons, sizeof(int32_t) * n1));
@@ -232,6 +226,7 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     if (!g.cells) {
         CKA(cudaMalloc(&g.cells, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));
         CKA(cudaMemset(g.cells, 0, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));
+        CKA(cudaMalloc(&g.slab, sizeof(uint2) * (size_t)std::max<int64_t>(g.total_cells, 1)));
         CKA(cudaMalloc(&g.epoch, sizeof(uint32_t)));
         CKA(cudaMemset(g.epoch, 0, sizeof(uint32_t)));
     }
@@ -260,7 +255,7 @@ void Group::free_all() {
     ev.clear();
     DevGroup &g = d;
     void *ptrs[] = {g.params, g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.cells,
-                    g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s, g.work, g.work_count};
+                    g.slab, g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s, g.work, g.work_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (owns_mesh) {

@@ -30,30 +30,29 @@ __device__ inline float3 cross(float3 a, float3 b) {
 
 __device__ inline float w0_of(const AsmParams &A, int c) { return c == kClsS ? A.w0[0] : c == kClsV ? A.w0[1] : A.w0[2]; }
 
+// every slot j of the 3 x 3 grid rows around p that the reach cut keeps (a
+// superset of the particles within 2h of p), row by row, slots ascending
 template <typename F>
-__device__ inline void for_rows(const float4 &p, const AsmParams &A, const uint4 *cells, uint32_t ep, F &&f) {
-    const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
-    const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
-    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
-    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, nz);
-    for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
+__device__ inline void for_rows(const float4 &p, const AsmParams &A, const uint4 *cells, const uint2 *slab,
+                                uint32_t ep, F &&f) {
+    const int ny = A.ng_n[1], nz = A.ng_n[2];
+    const GridPoint g = grid_point(A, p.x, p.y, p.z);
+    const int cy = g.c[1], cz = g.c[2];
+    for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++) {
+        const float gz = row_gap(g.t[2], cz, z - cz, g.slack);
         for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
-            const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-            uint32_t s = 0xffffffffu, e = 0u;
-            for (int x = max(cx - 1, 0); x <= min(cx + 1, nx - 1); x++) {
-                uint4 c = cells[row + (uint32_t)x];
-                if (c.z == ep) {
-                    s = min(s, c.x);
-                    e = max(e, c.y);
-                }
-            }
+            const uint32_t row = A.key_base + (uint32_t)A.ng_n[0] * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+            uint32_t s, e;
+            row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, y - cy, g.slack), gz, row, s, e);
             for (uint32_t j = s; j < e; j++) f(j);
         }
+    }
 }
 
 __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, int64_t N,
                                              const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                             const uint32_t *__restrict__ epoch, float *__restrict__ rho_s,
+                                             const uint2 *__restrict__ slab, const uint32_t *__restrict__ epoch,
+                                             float *__restrict__ rho_s,
                                              double *__restrict__ E) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     double e = 0.0;
@@ -63,7 +62,7 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, i
         const AsmParams &A = P[body_of(p.w)];
         const uint32_t mbits = acts_on_bits(cls);
         float rho = 0.f;
-        for_rows(p, A, cells, *epoch, [&](uint32_t j) {
+        for_rows(p, A, cells, slab, *epoch, [&](uint32_t j) {
             const float4 q = pos_s[j];
             const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
             const float r2 = dist2_rn(dx, dy, dz);
@@ -90,7 +89,8 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, i
 // |out| per body over mobile particles
 __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, int64_t N,
                                               const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                              const uint32_t *__restrict__ epoch, const float *__restrict__ rho_s,
+                                              const uint2 *__restrict__ slab, const uint32_t *__restrict__ epoch,
+                                              const float *__restrict__ rho_s,
                                               float sign, float4 *__restrict__ out_s, uint32_t *__restrict__ amax) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, 
         const bool mk = is_mobile(ck, A);
         const float ek = mk ? 2.f * (rho_s[k] - w0_of(A, ck)) : 0.f;
         const uint32_t bk = acts_on_bits(ck);
-        for_rows(p, A, cells, *epoch, [&](uint32_t j) {
+        for_rows(p, A, cells, slab, *epoch, [&](uint32_t j) {
             const float4 q = pos_s[j];
             const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
             const float r2 = dist2_rn(dx, dy, dz);
@@ -210,8 +210,9 @@ __global__ void k_vjp(const float4 *__restrict__ gx_s, const uint32_t *__restric
 
 void energy_accel(Group &g, cudaStream_t s) {
     DevGroup &d = g.d;
-    k_rho<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.rho_s, nullptr);
-    k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.rho_s, -1.f, d.acc_s, d.amax);
+    k_rho<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, nullptr);
+    k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, -1.f, d.acc_s,
+                                        d.amax);
 }
 
 int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
@@ -232,10 +233,10 @@ int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, 
     d.pos = xs;
     int buf = build_grid(g, s);
     d.pos = saved;
-    k_rho<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.rho_s, dE);
+    k_rho<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, dE);
     if (gy || gV) {
         if (gV) cudaMemsetAsync(gV, 0, sizeof(float) * 3 * (size_t)b.nv, s);
-        k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.rho_s, 1.f, d.acc_s,
+        k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, 1.f, d.acc_s,
                                              nullptr);
         k_vjp<<<nblocks(d.N), TPB, 0, s>>>(d.acc_s, d.id[buf], d.N, y_dev, d.pos, d.cons, V, b.d_tris, gy, gV);
     }

@@ -4,9 +4,11 @@
 //   particles   pos   float4[N]  x, y, z, w = bits((1 << class) | body << 8)
 //               cons  int32[N]   triangle (S) / feature segment (F) / -1
 //               key, id  u32[N] x 2 (radix ping-pong), pos_s / acc_s float4[N]
-//               in key order
+//               in key order; key = 8 (key_base + cell) + x-slab of the cell
 //   grid        cells uint4[total cells] {start, end, epoch, 0}: dense over
 //               every body's neighbour grid, validated by epoch (never cleared)
+//               slab  uint2[total cells]  low bytes of the first slot of
+//               x-slabs 1..7 of the cell (valid with the cell's epoch)
 //   triangles   geo   float4[5 nt]  v0, n, m0, m1 (w = c1), m2 (w = c2)
 //               vx    float4[3 nt]  v0, v1, v2 (w = vertex id bits)
 //               pn    float4[6 nt]  edge pseudonormals 0..2, vertex ones 0..2
@@ -45,7 +47,8 @@ struct AsmParams {
     float ng_o[3];
     float ng_inv;
     int ng_n[3];
-    uint32_t key_base;
+    uint32_t key_base;     // in cells; fine keys start at 8 key_base
+    float slab_r2;         // (2h / cell)^2 (1 + 2^-12): reach in cell units, squared
     // triangle grid (cell dx)
     float tg_o[3];
     float tg_inv;
@@ -110,6 +113,7 @@ struct DevGroup {
     float4 *pos_s = nullptr;
     float4 *acc_s = nullptr;
     uint4 *cells = nullptr;
+    uint2 *slab = nullptr;
     uint32_t *epoch = nullptr;
     uint32_t *amax = nullptr;
     uint32_t *maxdisp = nullptr;
@@ -145,6 +149,109 @@ __device__ inline int cell_coord(float x, float o, float inv, int n) {
     t = fmaxf(t, 0.0f);
     t = fminf(t, (float)(n - 1));
     return (int)t;
+}
+
+// ---- neighbour grid rows --------------------------------------------------
+// Keys are refined by 8 slabs along x inside each cell: key = 8 (key_base +
+// cell) + slab, the slab being the fine coordinate clamp(floor(8 t), 0,
+// 8 n - 1) with t = (x - o) * inv.  Since 8 t is exact, fine >> 3 is
+// cell_coord(x).  A grid row (fixed y, z) is then one contiguous key range
+// ordered by x in steps of 1/8 cell, so a particle walks, per row, only the
+// slabs that can hold a point within 2h of it.
+constexpr int kSlabBits = 3;
+constexpr int kSlabs = 1 << kSlabBits;
+
+__device__ inline int fine_coord(float x, float o, float inv, int n) {
+    float t = __fsub_rn(x, o);
+    t = __fmul_rn(t, inv);
+    t = __fmul_rn(t, (float)kSlabs);
+    t = fmaxf(t, 0.0f);
+    t = fminf(t, (float)(kSlabs * n - 1));
+    return (int)t;
+}
+
+// bits of the largest fine key of a grid of `cells` cells
+inline int fine_key_bits(int64_t cells) {
+    const uint64_t m = (uint64_t)(cells > 0 ? cells : 1) * kSlabs - 1;
+    int b = 0;
+    while (b < 64 && (m >> b) != 0) b++;
+    return b;
+}
+
+// (2h / cell)^2 with a relative margin of 2^-12, so that the row reach
+// below never cuts off a pair that the FP32 test r^2 < (2h)^2 accepts
+inline float slab_reach2(float R2, float inv) {
+    return (float)((double)R2 * (double)inv * (double)inv * (1.0 + 1.0 / 4096.0));
+}
+
+// A particle's place in the grid: unclamped cell coordinates t, clamped
+// cells c and the slack (cell units) that covers the FP32 rounding of t and
+// of the reach arithmetic (relative errors of a few 2^-24 of |t|).
+struct GridPoint {
+    float t[3];
+    int c[3];
+    float slack;
+};
+
+__device__ inline GridPoint grid_point(const AsmParams &A, float x, float y, float z) {
+    GridPoint g;
+    const float v[3] = {x, y, z};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        g.t[k] = __fmul_rn(__fsub_rn(v[k], A.ng_o[k]), A.ng_inv);
+        g.c[k] = (int)fminf(fmaxf(g.t[k], 0.0f), (float)(A.ng_n[k] - 1));
+    }
+    g.slack = 0x1p-12f + (fabsf(g.t[0]) + fabsf(g.t[1]) + fabsf(g.t[2]) + 4.0f) * 0x1p-19f;
+    return g;
+}
+
+// Lower bound (cell units) of the distance from the particle to any point
+// keyed into grid row offset d (-1, 0, +1) along a y or z axis: a point of
+// row c + 1 has t >= c + 1, one of row c - 1 has t < c.
+__device__ inline float row_gap(float t, int c, int d, float slack) {
+    if (d == 0) return 0.0f;
+    const float g = d < 0 ? t - (float)c : (float)(c + 1) - t;
+    return fmaxf(g - slack, 0.0f);
+}
+
+// Slot range [s, e) of the particles of grid row `row` (index of its x = 0
+// cell) whose fine x lies within reach of the particle, given the row's
+// y / z gaps.  Empty (s = ~0, e = 0) when no point of the row can be within
+// 2h.  The range covers every cell x0..x1 of the 3 x 3 x 3 stencil that the
+// reach touches; in the end cells it starts / stops at a slab boundary
+// unless the cell holds more than 255 particles (then the whole cell).
+__device__ inline void row_slots(const AsmParams &A, const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
+                                 uint32_t ep, const GridPoint &g, float gy, float gz, uint32_t row, uint32_t &s,
+                                 uint32_t &e) {
+    s = 0xffffffffu;
+    e = 0u;
+    const float w2 = A.slab_r2 - gy * gy - gz * gz;
+    if (!(w2 > 0.0f)) return;
+    const float w = sqrtf(w2) + g.slack;
+    // fine coordinates of t -/+ w under the key's own clamp to [0, 8 n - 1]
+    // (monotone, so every point within reach has its fine x in [flo, fhi]),
+    // cut to the stencil cells x0..x1; the particle's own slab is inside
+    const int x0 = max(g.c[0] - 1, 0), x1 = min(g.c[0] + 1, A.ng_n[0] - 1);
+    const float flo = fmaxf(fminf(floorf((g.t[0] - w) * (float)kSlabs), (float)(kSlabs * A.ng_n[0] - 1)),
+                            (float)(kSlabs * x0));
+    const float fhi = fminf(fmaxf(floorf((g.t[0] + w) * (float)kSlabs), 0.0f), (float)(kSlabs * x1 + kSlabs - 1));
+    if (!(flo <= fhi)) return;   // only for non-finite coordinates
+    const int lo = (int)flo, hi = (int)fhi;
+    const int xl = lo >> kSlabBits, xh = hi >> kSlabBits, sl = lo & (kSlabs - 1), sh = hi & (kSlabs - 1);
+    for (int x = xl; x <= xh; x++) {
+        const uint4 c = cells[row + (uint32_t)x];
+        if (c.z != ep) continue;
+        uint32_t cs = c.x, ce = c.y;
+        const bool cut_lo = x == xl && sl > 0, cut_hi = x == xh && sh < kSlabs - 1;
+        if ((cut_lo || cut_hi) && ce - cs <= 255u) {
+            const uint2 b = slab[row + (uint32_t)x];
+            const uint64_t v = ((uint64_t)b.y << 32) | b.x;
+            if (cut_lo) cs = c.x + (((uint32_t)(v >> (8 * (sl - 1))) - c.x) & 0xffu);
+            if (cut_hi) ce = c.x + (((uint32_t)(v >> (8 * sh)) - c.x) & 0xffu);
+        }
+        s = min(s, cs);
+        e = max(e, ce);
+    }
 }
 
 // FP32 squared distance (dx dx + dy dy) + dz dz without contraction

@@ -345,7 +345,8 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     R2 = (float)((double)R * (double)R);
     ng_cell = (float)((double)R * (1.0 + 1.0 / 256.0));
     grid_setup(bbmin, bbmax, ng_cell, 1.0, 1, ng_o, &ng_inv, ng_n);
-    if ((double)tg_n[0] * tg_n[1] * tg_n[2] >= 4294967295.0 || (double)ng_n[0] * ng_n[1] * ng_n[2] >= 2147483647.0) {
+    if ((double)tg_n[0] * tg_n[1] * tg_n[2] >= 4294967295.0 || (double)ng_n[0] * ng_n[1] * ng_n[2] >= 536870912.0) {
+        // neighbour keys carry 3 slab bits below the cell index
         err = "grid too large for 32-bit cell keys (dx too small for the mesh extent)";
         return 1;
     }

@@ -44,7 +44,8 @@ constexpr size_t kOffId1 = kOffId0 + align256(4 * kStaticMaxN);
 constexpr size_t kOffPosS = kOffId1 + align256(4 * kStaticMaxN);
 constexpr size_t kOffAccS = kOffPosS + align256(16 * kStaticMaxN);
 constexpr size_t kOffCells = kOffAccS + align256(16 * kStaticMaxN);
-constexpr size_t kScratchBytes = kOffCells + align256(16 * kStaticMaxCells);
+constexpr size_t kOffSlab = kOffCells + align256(16 * kStaticMaxCells);
+constexpr size_t kScratchBytes = kOffSlab + align256(8 * kStaticMaxCells);
 
 __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
@@ -63,12 +64,6 @@ __global__ void k_pack_static(const float *__restrict__ xyz, const int32_t *__re
         c = kClsI;
     }
     pos[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], __uint_as_float(class_bit(c)));
-}
-
-int bits_for(uint64_t v) {
-    int b = 0;
-    while (b < 64 && (v >> b) != 0) b++;
-    return b;
 }
 
 } // namespace
@@ -111,6 +106,7 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     const double hd = (double)h;
     A.h = h;
     A.R2 = (float)((double)R * (double)R);
+    A.slab_r2 = slab_reach2(A.R2, A.ng_inv);
     A.half_inv_h = (float)(1.0 / (2.0 * hd));
     A.force_scale = (float)(5.0 * (21.0 / (16.0 * M_PI * hd * hd * hd)) / (hd * hd));
     A.step_h = (float)(hd / 16.0);
@@ -144,7 +140,7 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     d.B = 1;
     d.N = n;
     d.total_cells = cells;
-    d.key_bits = bits_for((uint64_t)std::max<int64_t>(cells - 1, 1));
+    d.key_bits = fine_key_bits(cells);
     d.passes = (d.key_bits + 7) / 8;
     d.n_tiles = (int)std::max<int64_t>(radix_tiles(n), 1);
     d.params = (AsmParams *)(base + kOffParams);
@@ -156,6 +152,7 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     d.pos_s = (float4 *)(base + kOffPosS);
     d.acc_s = (float4 *)(base + kOffAccS);
     d.cells = (uint4 *)(base + kOffCells);
+    d.slab = (uint2 *)(base + kOffSlab);
     d.epoch = flags + 0;
     d.amax = flags + 1;
     d.maxdisp = flags + 2;

@@ -65,52 +65,74 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
     if (i >= N) return;
     float4 p = pos[i];
     const AsmParams &A = P[body_of(p.w)];
-    int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
-    int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
-    int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
-    key[i] = A.key_base + (uint32_t)cx + (uint32_t)A.ng_n[0] * ((uint32_t)cy + (uint32_t)A.ng_n[1] * (uint32_t)cz);
+    const int fx = fine_coord(p.x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
+    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
+    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
+    key[i] = kSlabs * A.key_base + (uint32_t)fx +
+             kSlabs * (uint32_t)A.ng_n[0] * ((uint32_t)cy + (uint32_t)A.ng_n[1] * (uint32_t)cz);
 }
 
 // ---- A3 ----------------------------------------------------------------------
+// Positions in key order, and per occupied cell its slot range [start, end)
+// with the epoch, plus the first slot of each x-slab 1..7 (low byte, so a
+// reader rebuilds it as start + ((byte - start) & 255) when the cell holds
+// at most 255 particles).  Boundary b of a cell is written by the slot that
+// starts the first fine-key run with slab >= b, or by the cell's last slot
+// (value end) when no slab >= b is present: exactly one writer per byte.
 __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restrict__ key_s,
                                                        const uint32_t *__restrict__ id_s,
                                                        const float4 *__restrict__ pos, int64_t N,
                                                        float4 *__restrict__ pos_s, uint32_t *__restrict__ cells,
-                                                       const uint32_t *__restrict__ epoch) {
+                                                       uint8_t *__restrict__ slab, const uint32_t *__restrict__ epoch) {
     int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (k >= N) return;
-    uint32_t c = key_s[k];
+    const uint32_t f = key_s[k], c = f >> kSlabBits, sk = f & (kSlabs - 1);
     pos_s[k] = pos[id_s[k]];
-    if (k == 0 || key_s[k - 1] != c) {
+    const bool first = k == 0 || (key_s[k - 1] >> kSlabBits) != c;
+    const bool last = k == N - 1 || (key_s[k + 1] >> kSlabBits) != c;
+    uint8_t *b = slab + 8 * (size_t)c;
+    if (first) {
         cells[4 * (size_t)c + 0] = (uint32_t)k;
         cells[4 * (size_t)c + 2] = *epoch;
+        for (uint32_t q = 1; q <= sk; q++) b[q - 1] = (uint8_t)k;
+    } else {
+        const uint32_t sp = key_s[k - 1] & (kSlabs - 1);
+        for (uint32_t q = sp + 1; q <= sk; q++) b[q - 1] = (uint8_t)k;
     }
-    if (k == N - 1 || key_s[k + 1] != c) cells[4 * (size_t)c + 1] = (uint32_t)(k + 1);
+    if (last) {
+        cells[4 * (size_t)c + 1] = (uint32_t)(k + 1);
+        for (uint32_t q = sk + 1; q < (uint32_t)kSlabs; q++) b[q - 1] = (uint8_t)(k + 1);
+    }
 }
 
 // ---- A4 ----------------------------------------------------------------------
 // a_i = -sum_j dW/dr(r_ij) e_ij = force_scale * sum_j (1 - r_ij / 2h)^3 (x_i - x_j)
 //
-// Each lane owns one particle (key order) and scans the 9 rows of 3 cells
-// around it; each row is one contiguous slot range.  Candidates are taken
-// two at a time with packed FP32x2 arithmetic (per component identical to
-// the scalar round-to-nearest operations, so the neighbour test
+// Each lane owns one particle (key order) and scans the 3 x 3 grid rows
+// around it; per row it walks one contiguous slot range: the x-slabs of the
+// row's stencil cells that lie within the reach sqrt((2h)^2 - gap_y^2 -
+// gap_z^2) of it (rows out of reach are skipped).  Candidates are taken two
+// at a time with packed FP32x2 arithmetic (per component identical to the
+// scalar round-to-nearest operations, so the neighbour test
 // r^2 = (dx dx + dy dy) + dz dz < (2h)^2 decides exactly as the scalar
 // rule) and accumulated without branches into two partial sums.
 //
 // Variant 1 (shared row): when every moving lane of a warp lies in the same
 // grid row of the same body, the lanes' ranges for one row offset lie in a
 // single grid row and the warp walks their union in lockstep (broadcast
-// loads, no divergence).  A candidate outside a lane's own 3 cells is at
-// least one full cell (> 2h) away and fails the test, so each lane accepts
-// exactly its own neighbours, in the same order.  The particle itself adds
+// loads, no divergence).  A candidate outside a lane's own range is out of
+// its reach and fails the test, so each lane accepts exactly its own
+// neighbours, in the same order.  The particle itself adds
 // (1 - 0)^3 * 0 = 0, so no self test is needed.
 // Slots are paired by absolute parity (even -> .x, odd -> .y) with the range
 // [s, e) applied as a mask, so every accepted neighbour lands in the same
 // partial sum, in the same order, whichever range (own or union) is walked.
-template <bool ALL>
+// COUNT adds, per particle, the accepted neighbours (self excluded) and the
+// slots of its own ranges (candidates tested).
+template <bool ALL, bool COUNT>
 __device__ inline void force_range2(const float4 *__restrict__ pos_s, const float4 p, uint32_t mbits, float R2,
-                                    float hih, uint32_t s, uint32_t e, float2 &ax, float2 &ay, float2 &az) {
+                                    float hih, uint32_t s, uint32_t e, float2 &ax, float2 &ay, float2 &az,
+                                    int &cnt, uint32_t self) {
     const float2 px = make_float2(p.x, p.x), py = make_float2(p.y, p.y), pz = make_float2(p.z, p.z);
     const float2 nh = make_float2(-hih, -hih), one = make_float2(1.f, 1.f);
     for (uint32_t j = s & ~1u; j < e; j += 2) {
@@ -126,6 +148,7 @@ __device__ inline void force_range2(const float4 *__restrict__ pos_s, const floa
             t0 = t0 && (mbits & __float_as_uint(q0.w)) != 0u;
             t1 = t1 && (mbits & __float_as_uint(q1.w)) != 0u;
         }
+        if (COUNT) cnt += (int)(t0 && j != self) + (int)(t1 && j + 1 != self);
         const float2 r = __fmul2_rn(r2, make_float2(rsqrtf(r2.x + 1e-30f), rsqrtf(r2.y + 1e-30f)));
         const float2 t = __ffma2_rn(r, nh, one);                     // 1 - r / 2h
         float2 w = __fmul2_rn(__fmul2_rn(t, t), t);
@@ -137,11 +160,12 @@ __device__ inline void force_range2(const float4 *__restrict__ pos_s, const floa
     }
 }
 
-template <int VARIANT>
+template <int VARIANT, bool COUNT>
 __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s, int64_t N,
                                                const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                               const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s,
-                                               uint32_t *__restrict__ amax) {
+                                               const uint2 *__restrict__ slab, const uint32_t *__restrict__ epoch,
+                                               float4 *__restrict__ acc_s, uint32_t *__restrict__ amax,
+                                               int32_t *__restrict__ count_s, int32_t *__restrict__ tested_s) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -149,13 +173,12 @@ __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s,
     const int b = active ? body_of(p.w) : 0;
     const AsmParams &A = P[b];
     const bool mob = active && is_mobile(cls, A);
-    const uint32_t mbits = mob ? acts_on_bits(cls) : 0u;
+    // the counting form also counts the neighbours of fixed particles
+    const uint32_t mbits = (mob || (COUNT && active)) ? acts_on_bits(cls) : 0u;
     const uint32_t ep = *epoch;
     const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
-    const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
-    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
-    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, nz);
-    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, nx - 1);
+    const GridPoint g = grid_point(A, p.x, p.y, p.z);
+    const int cy = g.c[1], cz = g.c[2];
     const float R2 = A.R2, hih = A.half_inv_h;
     // every class acts on every moving lane (volume targets): no mask test
     const bool all_cls = __all_sync(0xffffffffu, mbits == 0u || mbits == 0x1Fu);
@@ -168,27 +191,26 @@ __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s,
         shared_row = __all_sync(0xffffffffu, mbits == 0u || rowkey == lead_row);
     }
     float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
-    for (int dz = -1; dz <= 1; dz++)
+    int cnt = 0, tested = 0;
+    for (int dz = -1; dz <= 1; dz++) {
+        const int z = cz + dz;
+        const float gz = row_gap(g.t[2], cz, dz, g.slack);
         for (int dy = -1; dy <= 1; dy++) {
-            const int z = cz + dz, y = cy + dy;
+            const int y = cy + dy;
             uint32_t s = 0xffffffffu, e = 0u;
             if (mbits && z >= 0 && z < nz && y >= 0 && y < ny) {
                 const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-                for (int x = x0; x <= x1; x++) {
-                    const uint4 c = cells[row + (uint32_t)x];
-                    if (c.z == ep) {
-                        s = min(s, c.x);
-                        e = max(e, c.y);
-                    }
-                }
+                row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
             }
+            if (COUNT && e > s) tested += (int)(e - s);
             if (VARIANT == 1 && shared_row) {
                 s = __reduce_min_sync(0xffffffffu, s);
                 e = __reduce_max_sync(0xffffffffu, e);
             }
-            if (all_cls) force_range2<true>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az);
-            else force_range2<false>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az);
+            if (all_cls) force_range2<true, COUNT>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az, cnt, (uint32_t)k);
+            else force_range2<false, COUNT>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az, cnt, (uint32_t)k);
         }
+    }
     float fx = 0.f, fy = 0.f, fz = 0.f, mag = 0.f;
     if (mob) {
         fx = (ax.x + ax.y) * A.force_scale;
@@ -197,11 +219,16 @@ __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s,
         mag = sqrtf(fx * fx + fy * fy + fz * fz);
     }
     if (active) acc_s[k] = make_float4(fx, fy, fz, mag);
+    if (COUNT && active) {
+        count_s[k] = cnt;
+        if (tested_s) tested_s[k] = mob ? tested : 0;
+    }
     labelled_max(amax, b, mag);
 }
 
 // Masked neighbour count (self excluded) and the number of candidates in the
-// particle's own 27 cells, per particle in key order (diagnostics).
+// particle's own 27 cells (the full stencil, no reach cut), per particle in
+// key order (diagnostics).
 __global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s, int64_t N,
                                                const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
                                                const uint32_t *__restrict__ epoch, int32_t *__restrict__ count_s,
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s,
                 if (r2 < A.R2 && (int64_t)j != k && (mbits & __float_as_uint(q.w)) != 0u) cnt++;
             }
         }
-    count_s[k] = cnt;
+    if (count_s) count_s[k] = cnt;
     if (cand_s) cand_s[k] = is_mobile(cls, A) ? cand : 0;
 }
 
@@ -725,25 +752,33 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
                                                                  d.maxdisp, d.B, d.work_count);
     int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
     k_gather_ranges<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s,
-                                                  reinterpret_cast<uint32_t *>(d.cells), d.epoch);
+                                                  reinterpret_cast<uint32_t *>(d.cells),
+                                                  reinterpret_cast<uint8_t *>(d.slab), d.epoch);
     return buf;
 }
 
 int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
 
-void forces_dev(DevGroup &d, int tb, int variant, cudaStream_t s) {
+void forces_dev(DevGroup &d, int tb, int variant, cudaStream_t s, int32_t *count_s, int32_t *tested_s) {
     const unsigned nbk = (unsigned)std::max<int64_t>((d.N + tb - 1) / tb, 1);
-    if (variant == 1)
-        k_force<1><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax);
-    else
-        k_force<0><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, d.acc_s, d.amax);
+#define FPPG_FORCE(V, C)                                                                                      \
+    k_force<V, C><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.acc_s, d.amax, count_s, \
+                                     tested_s)
+    if (count_s) {
+        if (variant == 1) FPPG_FORCE(1, true);
+        else FPPG_FORCE(0, true);
+    } else {
+        if (variant == 1) FPPG_FORCE(1, false);
+        else FPPG_FORCE(0, false);
+    }
+#undef FPPG_FORCE
 }
 
-void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s) {
+void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s, int32_t *tested_s) {
     DevGroup &d = g.d;
-    forces_dev(d, g.force_block, g.force_variant, s);
-    if (count_s)
-        k_count<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, count_s, cand_s);
+    forces_dev(d, g.force_block, g.force_variant, s, count_s, tested_s);
+    if (cand_s)
+        k_count<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, nullptr, cand_s);
 }
 
 void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {

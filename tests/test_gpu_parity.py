@@ -68,6 +68,47 @@ def test_forces_of_fixed_particles_are_zero():
     assert fixed.sum() == 8 and np.all(acc[fixed] == 0) and np.all(cnt[fixed] == 0)
 
 
+def _cloud(case, rng, org, cell):
+    """Particle sets that stress the x-slab reach cut of the force kernel."""
+    if case == "uniform":
+        xyz = rng.uniform(-0.3, 0.3, (8000, 3))
+    elif case == "dense":                    # > 255 particles per cell: whole-cell ranges
+        xyz = np.concatenate([rng.uniform(0.0, 0.05, (2500, 3)), rng.uniform(-0.3, 0.3, (3000, 3))])
+    elif case == "outside":                  # clamped into the boundary cells of the grid
+        xyz = np.concatenate([rng.uniform(-0.3, 0.3, (3000, 3)), rng.uniform(-1.6, -0.9, (2000, 3)),
+                              rng.uniform(0.95, 3.0, (2000, 3))])
+    else:                                    # exactly on slab boundaries in x, y and z
+        k = rng.integers(0, 8 * 8, (6000, 3))
+        xyz = org[None, :].astype(np.float64) + 6 * cell + k * (cell / 8)
+    return xyz.astype(np.float32)
+
+
+@pytest.mark.parametrize("case", ["uniform", "dense", "outside", "slab_planes"])
+def test_reach_cut_keeps_every_neighbour(case):
+    # The force kernel walks, per grid row, only the x-slabs within reach of
+    # each particle; the neighbours it accepts (its own count, self excluded)
+    # equal the oracle's brute-force O(N^2) sets for every class pair.
+    v, t = W.cube_mesh(1.0)
+    dx, h = 0.02, 0.026
+    o = O.Oracle(v, t, dx, h)
+    org, _, cell, _, _ = o.nbr_grid()
+    rng = np.random.default_rng(11)
+    xyz = _cloud(case, rng, org, cell)
+    cls = rng.integers(0, 5, len(xyz)).astype(np.int32)
+    o.set_particles(xyz, cls)
+    b = pkg.Body(v, t, dx, h)
+    b.set_particles(xyz, cls)
+    acc, cnt, amax = b.debug_forces()
+    assert np.array_equal(cnt, o.brute_neighbours())
+    assert cnt.max() > 10
+    oacc, _, oamax = o.forces()
+    assert np.abs(acc.astype(np.float64) - oacc).max() <= 2e-5 * oamax
+    cand, pairs, tested = b.work_counts()
+    assert pairs <= tested <= cand
+    if case == "uniform":
+        assert tested < 0.7 * cand
+
+
 # ---- A6 -------------------------------------------------------------------------
 def _near_surface_points(v, t, n, spread, seed):
     rng = np.random.default_rng(seed)

@@ -26,14 +26,35 @@ def test_keys_follow_the_row_major_cell_rule():
     org, inv, cell, n, r2 = o.nbr_grid()
     assert cell >= 2 * 0.065 and cell == pytest.approx(2 * np.float32(0.065) * (1 + 1 / 256), rel=1e-6)
     assert r2 == np.float32((2 * np.float32(0.065)) ** 2)
-    # particles at cell centres
+    # particles at 0.55 of their cell along each axis: x-slab floor(8 * 0.55) = 4
     idx = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [3, 7, 2], [n[0] - 1, n[1] - 1, n[2] - 1]])
-    xyz = (org[None, :].astype(np.float64) + (idx + 0.5) * cell).astype(np.float32)
+    xyz = (org[None, :].astype(np.float64) + (idx + 0.55) * cell).astype(np.float32)
     o.set_particles(xyz, np.full(len(idx), W.CLS_V, np.int32))
     key, perm = o.keys()
-    expect = idx[:, 0] + n[0] * (idx[:, 1] + n[1] * idx[:, 2])
+    expect = 8 * (idx[:, 0] + n[0] * (idx[:, 1] + n[1] * idx[:, 2])) + 4
     assert np.array_equal(key, expect.astype(np.uint32))
     assert np.array_equal(perm, np.argsort(expect, kind="stable").astype(np.uint32))
+
+
+def test_keys_order_a_cell_by_x_slab():
+    # inside one cell the key's low 3 bits are floor(8 * fractional x); y and
+    # z fractions do not enter; fractions kept away from slab boundaries
+    v, t = big_box(1.0)
+    o = O.Oracle(v, t, 0.05, 0.065)
+    org, inv, cell, n, r2 = o.nbr_grid()
+    frac = np.array([0.99, 0.01, 0.51, 0.13, 0.9, 0.3, 0.49, 0.6])
+    base = np.array([5, 3, 4])
+    xyz = org[None, :].astype(np.float64) + (base[None, :] + 0.5) * cell + np.zeros((len(frac), 3))
+    xyz[:, 0] = org[0] + (base[0] + frac) * cell
+    xyz[:, 1] += (frac - 0.5) * 0.8 * cell                 # moves inside the cell along y
+    o.set_particles(xyz.astype(np.float32), np.full(len(frac), W.CLS_V, np.int32))
+    key, perm = o.keys()
+    c = base[0] + n[0] * (base[1] + n[1] * base[2])
+    assert np.array_equal(key, (8 * c + np.floor(8 * frac)).astype(np.uint32))
+    # stable: equal slabs (0.9 and 0.99) keep id order
+    assert np.array_equal(perm, np.argsort(np.floor(8 * frac), kind="stable").astype(np.uint32))
+    cells, s, e = o.cell_ranges()
+    assert list(cells) == [c] and s[0] == 0 and e[0] == len(frac)
 
 
 def test_points_outside_the_grid_are_clamped():
@@ -43,7 +64,7 @@ def test_points_outside_the_grid_are_clamped():
     xyz = np.array([[-50, -50, -50], [50, 50, 50]], np.float32)
     o.set_particles(xyz, np.full(2, W.CLS_V, np.int32))
     key, _ = o.keys()
-    assert key[0] == 0 and key[1] == n[0] * n[1] * n[2] - 1
+    assert key[0] == 0 and key[1] == 8 * n[0] * n[1] * n[2] - 1
 
 
 def test_stable_permutation_and_cell_ranges():
@@ -56,7 +77,7 @@ def test_stable_permutation_and_cell_ranges():
     assert np.all(np.diff(cells.astype(np.int64)) > 0)
     assert s[0] == 0 and e[-1] == a.n and np.array_equal(s[1:], e[:-1])
     for c, b, f in zip(cells[::37], s[::37], e[::37]):
-        assert np.all(ks[b:f] == c)
+        assert np.all(ks[b:f] // 8 == c)
 
 
 @pytest.mark.parametrize("seed", [0, 1])
