@@ -191,6 +191,15 @@ int fppg_debug_forces(fppg_ctx *ctx, float *acc_host, int32_t *count_host, float
 int fppg_project_points(fppg_ctx *ctx, const float *y_host, const int32_t *cls_host, const int32_t *cons_host,
                         int64_t n, float *x_host, int32_t *cons_out_host, int32_t *ok_host);
 
+/* A6 bookkeeping: *queued = particles of the last iteration that went to
+ * the triangle search (the others finished in the step: features, nothing
+ * within reach, or a volume particle inside its inside certificate, i.e. a
+ * ball that an earlier search found free of surface and inside a closed
+ * mesh); *closed = 1 when every mesh edge has two faces of opposite
+ * direction and no face is degenerate (certificates apply), else 0.
+ * Either output may be NULL.  Synchronises. */
+int fppg_debug_search(fppg_ctx *ctx, int64_t *queued, int32_t *closed);
+
 /* Work of one force pass (A4) on the current state, summed over mobile
  * particles: candidates = particles in the 27 neighbour cells around each
  * particle (the search set of the cell grid, Sec. 3.1.3), pairs = masked
@@ -231,8 +240,9 @@ int fppg_batch_set_graph_iters(fppg_batch *b, int32_t graph_iters);
 int fppg_batch_store(fppg_batch *b);
 int fppg_batch_load(fppg_batch *b);
 /* Autotuner: times `iters` iterations of the batch for every combination
- * of force-kernel block size (128, 256), force-kernel variant (per-lane rows
- * or shared-row union) and persistent search grid (4, 8 or 16 CTAs per SM),
+ * of force-kernel block size (128, 256), force-kernel variant (0 per-lane
+ * rows, 1 shared-row union, 2 per-lane rows walked back to back) and
+ * persistent search grid (4, 8 or 16 CTAs per SM),
  * keeps the fastest and restores the particle state afterwards.  The choice
  * is cached per (particle-count bucket, volume-particle share, GPU name) for
  * the life of the process; a cached choice is applied without timing.
@@ -240,6 +250,10 @@ int fppg_batch_load(fppg_batch *b);
  * measured ms per iteration (0 when taken from the cache). */
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
                         double *ms_per_iter);
+/* The same choice made by hand: force variant 0..2, force block 128 or 256,
+ * search CTAs per SM 1..64 (FPPG_ERR_ARG otherwise).  Every choice gives the
+ * same bits; only the speed differs.  Drops a captured graph. */
+int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t search_ctas);
 /* Kernel launches of one iteration of the batch (A1-A6, all bodies). */
 int32_t fppg_batch_kernels_per_iter(const fppg_batch *b);
 /* Particle count and the last error of the batch. */

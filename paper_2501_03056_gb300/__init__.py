@@ -77,6 +77,7 @@ def lib():
                 "fppg_project_points": [vp, P_(f32), P_(i32), P_(i32), i64, P_(f32), P_(i32), P_(i32)],
                 "fppg_energy": [vp, vp, vp, P_(f64), vp, vp],
                 "fppg_work_counts": [vp, P_(i64), P_(i64), P_(i64)],
+                "fppg_debug_search": [vp, P_(i64), P_(i32)],
                 "fppg_batch_load": [vp],
                 "fppg_copy_positions_dev": [vp, vp],
                 "fppg_batch_create": [P_(vp), i32, P_(vp)],
@@ -88,6 +89,7 @@ def lib():
                 "fppg_batch_time_force": [vp, i32],
                 "fppg_batch_force_ms": [vp, P_(f64)],
                 "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(f64)],
+                "fppg_batch_configure": [vp, i32, i32, i32],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -281,6 +283,13 @@ class Body:
                                             _ptr(ok, C.c_int32)))
         return x[:m], co[:m], ok[:m].astype(bool)
 
+    def debug_search(self):
+        """(particles sent to the triangle search in the last iteration,
+        whether the mesh is closed so that inside certificates apply)."""
+        q, c = C.c_int64(), C.c_int32()
+        self._chk(lib().fppg_debug_search(self._h, C.byref(q), C.byref(c)))
+        return q.value, bool(c.value)
+
     def work_counts(self):
         """(candidates in the 27 cells, pairs within 2h, candidates actually
         tested by the force kernel) of one force pass on the current state."""
@@ -362,6 +371,10 @@ class Batch:
         self._chk(lib().fppg_batch_autotune(self._h, int(iters), C.byref(v), C.byref(tb), C.byref(sc), C.byref(ms)))
         return {"force_variant": v.value, "force_block": tb.value, "search_ctas_per_sm": sc.value,
                 "ms_per_iter": ms.value}
+
+    def configure(self, force_variant: int = 0, force_block: int = 256, search_ctas_per_sm: int = 16):
+        """Set the kernel configuration by hand (the autotuner's choices)."""
+        self._chk(lib().fppg_batch_configure(self._h, int(force_variant), int(force_block), int(search_ctas_per_sm)))
 
     def force_ms(self) -> float:
         ms = C.c_double()

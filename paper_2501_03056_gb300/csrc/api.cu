@@ -356,6 +356,18 @@ int fppg_debug_forces(fppg_ctx *ctx, float *acc_host, int32_t *count_host, float
     return FPPG_OK;
 }
 
+int fppg_debug_search(fppg_ctx *ctx, int64_t *queued, int32_t *closed) {
+    if (!ctx) return FPPG_ERR_ARG;
+    uint32_t q = 0;
+    if (ctx->group.d.work_count) {
+        CUDA_OR(ctx->err, cudaMemcpyAsync(&q, ctx->group.d.work_count, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    }
+    if (queued) *queued = q;
+    if (closed) *closed = ctx->body.closed ? 1 : 0;
+    return FPPG_OK;
+}
+
 int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs, int64_t *tested) {
     if (!ctx) return FPPG_ERR_ARG;
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
@@ -715,7 +727,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
         const bool tf = g.time_force;
         g.time_force = false;
         best_ms = 1e30;
-        for (int v = 0; v < 2; v++)
+        for (int v = 0; v < 3; v++)
             for (int tb : {128, 256})
                 for (int sc : {4, 8, 16}) {
                     g.force_variant = v;
@@ -757,6 +769,24 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     if (block) *block = best.block;
     if (search_ctas) *search_ctas = best.search_ctas;
     if (ms_per_iter) *ms_per_iter = cached ? 0.0 : best_ms;
+    return FPPG_OK;
+}
+
+int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t search_ctas) {
+    if (!b || variant < 0 || variant > 2 || (block != 128 && block != 256) || search_ctas < 1 || search_ctas > 64)
+        return FPPG_ERR_ARG;
+    Group &g = b->group;
+    int dev = 0;
+    cudaDeviceProp prop;
+    CUDA_OR(b->err, cudaGetDevice(&dev));
+    CUDA_OR(b->err, cudaGetDeviceProperties(&prop, dev));
+    g.force_variant = variant;
+    g.force_block = block;
+    g.search_blocks = search_ctas * prop.multiProcessorCount;
+    if (g.graph) {
+        cudaGraphExecDestroy(g.graph);
+        g.graph = nullptr;
+    }
     return FPPG_OK;
 }
 

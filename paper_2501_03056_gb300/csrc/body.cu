@@ -180,6 +180,7 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.step_h = (float)(h / 16.0);
     A.dx = b.dx;
     A.edge_tol = b.edge_tol;
+    A.closed = b.closed ? 1 : 0;
     A.w0[0] = (float)lattice_w0((double)b.dx, h, 2);
     A.w0[1] = (float)lattice_w0((double)b.dx, h, 3);
     A.w0[2] = (float)lattice_w0((double)b.dx, h, 1);
@@ -199,7 +200,8 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
 
 int Group::alloc_particles(int64_t N, std::string &err) {
     DevGroup &g = d;
-    void *old[] = {g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.hist, g.rho_s, g.work};
+    void *old[] = {g.pos,   g.cons,  g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s,
+                   g.pos_p, g.cert,  g.acc_s,  g.hist,   g.rho_s, g.work};
     for (void *p : old)
         if (p) cudaFree(p);
     g.N = N;
@@ -214,6 +216,9 @@ int Group::alloc_particles(int64_t N, std::string &err) {
         CKA(cudaMalloc(&g.id[k], sizeof(uint32_t) * n1));
     }
     CKA(cudaMalloc(&g.pos_s, sizeof(float4) * n1));
+    CKA(cudaMalloc(&g.pos_p, sizeof(float4) * (n1 + 1)));
+    CKA(cudaMalloc(&g.cert, sizeof(float4) * n1));
+    CKA(cudaMemset(g.cert, 0, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.acc_s, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.rho_s, sizeof(float) * n1));
     CKA(cudaMalloc(&g.work, sizeof(int4) * n1));
@@ -254,8 +259,8 @@ void Group::free_all() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     ev.clear();
     DevGroup &g = d;
-    void *ptrs[] = {g.params, g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.acc_s, g.cells,
-                    g.slab, g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s, g.work, g.work_count};
+    void *ptrs[] = {g.params, g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
+                    g.acc_s, g.cells, g.slab, g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s, g.work, g.work_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (owns_mesh) {

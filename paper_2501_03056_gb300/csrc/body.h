@@ -20,6 +20,7 @@ struct Body {
     float ng_o[3] = {0, 0, 0};
     float ng_inv = 0, ng_cell = 0, R2 = 0;
     float edge_tol = 0;  // 2^-20 of the largest bounding-box extent
+    bool closed = false; // every edge has two faces of opposite direction, none degenerate
     int ng_n[3] = {0, 0, 0};
     // device mesh
     float *d_verts = nullptr;

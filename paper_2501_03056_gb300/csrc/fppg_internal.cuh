@@ -4,7 +4,9 @@
 //   particles   pos   float4[N]  x, y, z, w = bits((1 << class) | body << 8)
 //               cons  int32[N]   triangle (S) / feature segment (F) / -1
 //               key, id  u32[N] x 2 (radix ping-pong), pos_s / acc_s float4[N]
-//               in key order; key = 8 (key_base + cell) + x-slab of the cell
+//               in key order, pos_p float4[N + 1] pos_s as slot pairs;
+//               cert  float4[N]  {x, y, z, r}: a ball of radius r around x
+//               that is free of surface and inside the body (r = 0: none) key = 8 (key_base + cell) + x-slab of the cell
 //   grid        cells uint4[total cells] {start, end, epoch, 0}: dense over
 //               every body's neighbour grid, validated by epoch (never cleared)
 //               slab  uint2[total cells]  low bytes of the first slot of
@@ -79,6 +81,7 @@ struct AsmParams {
     float w_zero;      // W(0) = alpha_3
     float alpha;       // alpha_3
     float edge_tol;    // a foot this close outside a triangle edge still counts as inside
+    int closed;        // closed, consistently oriented mesh: inside certificates apply
     int p_begin, p_end;
 };
 
@@ -111,6 +114,8 @@ struct DevGroup {
     uint32_t *key[2] = {nullptr, nullptr};
     uint32_t *id[2] = {nullptr, nullptr};
     float4 *pos_s = nullptr;
+    float4 *pos_p = nullptr;   // pos_s as slot pairs: [2m] {x, x', y, y'}, [2m + 1] {z, z', w, w'}
+    float4 *cert = nullptr;    // id order: inside certificate {centre, radius} of a volume particle
     float4 *acc_s = nullptr;
     uint4 *cells = nullptr;
     uint2 *slab = nullptr;

@@ -239,6 +239,29 @@ __global__ void k_mark_occupancy(const uint4 *__restrict__ compact, int64_t m, T
             }
 }
 
+// A closed, consistently oriented surface: every edge has exactly two faces
+// that traverse it in opposite directions, and no face is degenerate.  Any
+// violation sets *open.
+__global__ void k_closed_check(const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, int64_t m,
+                               const int32_t *__restrict__ tris, const double *__restrict__ nu,
+                               uint32_t *__restrict__ open) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t t = val[i] / 3;
+    if (nu[3 * t] == 0.0 && nu[3 * t + 1] == 0.0 && nu[3 * t + 2] == 0.0) atomicOr(open, 1u);
+    if (i > 0 && key[i] == key[i - 1]) return;
+    int64_t j = i;
+    while (j < m && key[j] == key[i]) j++;
+    if (j - i != 2) {
+        atomicOr(open, 1u);
+        return;
+    }
+    const uint32_t t1 = val[i] / 3, k1 = val[i] % 3, t2 = val[i + 1] / 3, k2 = val[i + 1] % 3;
+    const int32_t a1 = tris[3 * t1 + k1], b1 = tris[3 * t1 + (k1 + 1) % 3];
+    const int32_t a2 = tris[3 * t2 + k2], b2 = tris[3 * t2 + (k2 + 1) % 3];
+    if (!(a1 == b2 && b1 == a2)) atomicOr(open, 1u);
+}
+
 __global__ void k_feature_flags(const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, int64_t m,
                                 const double *__restrict__ nu, double cthr, uint32_t *__restrict__ flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -378,6 +401,10 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     k_tri_prep<<<blocks(nt), 256, 0, s>>>(d_verts, d_tris, nt, nv, geo, vx, nu, ek[0], ck[0]);
     int eb = radix_sort_u64(ek, ev, true, m, bits_for((uint64_t)nv * (uint64_t)nv), hist, tot, s);
     k_edge_runs<<<blocks(m), 256, 0, s>>>(ek[eb], ev[eb], m, nu, pn);
+    uint32_t *open = nullptr;
+    CK(dalloc(&open, 1));
+    CK(cudaMemsetAsync(open, 0, sizeof(uint32_t), s));
+    k_closed_check<<<blocks(m), 256, 0, s>>>(ek[eb], ev[eb], m, d_tris, nu, open);
     int cb = radix_sort_u32(ck, cv, true, m, bits_for((uint64_t)nv), hist, tot, s);
     k_vertex_runs<<<blocks(m), 256, 0, s>>>(ck[cb], cv[cb], m, d_verts, d_tris, nu, vpn);
     k_fill_vertex_pn<<<blocks(nt), 256, 0, s>>>(d_tris, nt, vpn, pn);
@@ -406,10 +433,13 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     CK(dalloc(&scratch, sc));
     k_bin<false><<<blocks(nt, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, cnt, nullptr, nullptr, nullptr);
     exclusive_scan_u32(cnt, off, nt, total, scratch, sc, s);
-    uint32_t npairs_h = 0;
+    uint32_t npairs_h = 0, open_h = 1;
     CK(cudaMemcpyAsync(&npairs_h, total, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&open_h, open, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     npairs = npairs_h;
+    closed = nt > 0 && open_h == 0;
+    cudaFree(open);
     uint32_t *pk[2] = {nullptr, nullptr}, *pt[2] = {nullptr, nullptr}, *flag = nullptr, *pos = nullptr;
     CK(dalloc(&pk[0], npairs));
     CK(dalloc(&pk[1], npairs));

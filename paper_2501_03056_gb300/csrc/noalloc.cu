@@ -42,7 +42,8 @@ constexpr size_t kOffKey1 = kOffKey0 + align256(4 * kStaticMaxN);
 constexpr size_t kOffId0 = kOffKey1 + align256(4 * kStaticMaxN);
 constexpr size_t kOffId1 = kOffId0 + align256(4 * kStaticMaxN);
 constexpr size_t kOffPosS = kOffId1 + align256(4 * kStaticMaxN);
-constexpr size_t kOffAccS = kOffPosS + align256(16 * kStaticMaxN);
+constexpr size_t kOffPosP = kOffPosS + align256(16 * kStaticMaxN);
+constexpr size_t kOffAccS = kOffPosP + align256(16 * (kStaticMaxN + 1));
 constexpr size_t kOffCells = kOffAccS + align256(16 * kStaticMaxN);
 constexpr size_t kOffSlab = kOffCells + align256(16 * kStaticMaxCells);
 constexpr size_t kScratchBytes = kOffSlab + align256(8 * kStaticMaxCells);
@@ -150,6 +151,7 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     d.id[0] = (uint32_t *)(base + kOffId0);
     d.id[1] = (uint32_t *)(base + kOffId1);
     d.pos_s = (float4 *)(base + kOffPosS);
+    d.pos_p = (float4 *)(base + kOffPosP);
     d.acc_s = (float4 *)(base + kOffAccS);
     d.cells = (uint4 *)(base + kOffCells);
     d.slab = (uint2 *)(base + kOffSlab);

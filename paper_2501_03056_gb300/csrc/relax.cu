@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
 }
 
 // ---- A3 ----------------------------------------------------------------------
-// Positions in key order, and per occupied cell its slot range [start, end)
+// Positions in key order (also as slot pairs), and per occupied cell its
+// slot range [start, end)
 // with the epoch, plus the first slot of each x-slab 1..7 (low byte, so a
 // reader rebuilds it as start + ((byte - start) & 255) when the cell holds
 // at most 255 particles).  Boundary b of a cell is written by the slot that
@@ -82,12 +83,22 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
 __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restrict__ key_s,
                                                        const uint32_t *__restrict__ id_s,
                                                        const float4 *__restrict__ pos, int64_t N,
-                                                       float4 *__restrict__ pos_s, uint32_t *__restrict__ cells,
-                                                       uint8_t *__restrict__ slab, const uint32_t *__restrict__ epoch) {
+                                                       float4 *__restrict__ pos_s, float *__restrict__ pos_p,
+                                                       uint32_t *__restrict__ cells, uint8_t *__restrict__ slab,
+                                                       const uint32_t *__restrict__ epoch) {
     int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (k >= N) return;
     const uint32_t f = key_s[k], c = f >> kSlabBits, sk = f & (kSlabs - 1);
-    pos_s[k] = pos[id_s[k]];
+    const float4 q = pos[id_s[k]];
+    pos_s[k] = q;
+    // slot-pair copy {x0, x1, y0, y1, z0, z1, w0, w1}; an odd count pads the
+    // last pair with a finite point of no class
+    float *pp = pos_p + 8 * (k >> 1) + (k & 1);
+    pp[0] = q.x;
+    pp[2] = q.y;
+    pp[4] = q.z;
+    pp[6] = q.w;
+    if (k == N - 1 && (k & 1) == 0) pp[1] = pp[3] = pp[5] = pp[7] = 0.f;
     const bool first = k == 0 || (key_s[k - 1] >> kSlabBits) != c;
     const bool last = k == N - 1 || (key_s[k + 1] >> kSlabBits) != c;
     uint8_t *b = slab + 8 * (size_t)c;
@@ -111,61 +122,96 @@ __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restric
 // Each lane owns one particle (key order) and scans the 3 x 3 grid rows
 // around it; per row it walks one contiguous slot range: the x-slabs of the
 // row's stencil cells that lie within the reach sqrt((2h)^2 - gap_y^2 -
-// gap_z^2) of it (rows out of reach are skipped).  Candidates are taken two
-// at a time with packed FP32x2 arithmetic (per component identical to the
-// scalar round-to-nearest operations, so the neighbour test
-// r^2 = (dx dx + dy dy) + dz dz < (2h)^2 decides exactly as the scalar
-// rule) and accumulated without branches into two partial sums.
+// gap_z^2) of it (rows out of reach are skipped).  Candidates come two at a
+// time from the slot-pair copy pos_p ({x0, x1, y0, y1}, {z0, z1, w0, w1}),
+// so one float4 load gives the packed FP32x2 operands; each packed
+// operation is per component identical to the scalar round-to-nearest one,
+// so the neighbour test r^2 = (dx dx + dy dy) + dz dz < (2h)^2 decides
+// exactly as the scalar rule.  The loop works on q - p (the exact negation
+// of p - q) and accumulates without branches into two partial sums.
 //
-// Variant 1 (shared row): when every moving lane of a warp lies in the same
-// grid row of the same body, the lanes' ranges for one row offset lie in a
-// single grid row and the warp walks their union in lockstep (broadcast
-// loads, no divergence).  A candidate outside a lane's own range is out of
-// its reach and fails the test, so each lane accepts exactly its own
-// neighbours, in the same order.  The particle itself adds
-// (1 - 0)^3 * 0 = 0, so no self test is needed.
+// Variant 0 walks the rows one by one.  Variant 1 (shared row): when every
+// moving lane of a warp lies in the same grid row of the same body, the
+// lanes' ranges for one row offset lie in a single grid row and the warp
+// walks their union in lockstep (broadcast loads); a candidate outside a
+// lane's own range is out of its reach and fails the test.  Variant 2
+// (flattened): the lane's non-empty ranges are parked in shared memory and
+// walked back to back, so a warp runs as long as its longest lane's total
+// rather than the sum over rows of the longest range.
+// The particle itself adds (1 - 0)^3 * 0 = 0, so no self test is needed.
 // Slots are paired by absolute parity (even -> .x, odd -> .y) with the range
 // [s, e) applied as a mask, so every accepted neighbour lands in the same
-// partial sum, in the same order, whichever range (own or union) is walked.
+// partial sum, in the same order, in every variant.
 // COUNT adds, per particle, the accepted neighbours (self excluded) and the
 // slots of its own ranges (candidates tested).
+struct PairAcc {
+    float2 ax, ay, az;
+    int cnt;
+};
+
 template <bool ALL, bool COUNT>
-__device__ inline void force_range2(const float4 *__restrict__ pos_s, const float4 p, uint32_t mbits, float R2,
-                                    float hih, uint32_t s, uint32_t e, float2 &ax, float2 &ay, float2 &az,
-                                    int &cnt, uint32_t self) {
-    const float2 px = make_float2(p.x, p.x), py = make_float2(p.y, p.y), pz = make_float2(p.z, p.z);
-    const float2 nh = make_float2(-hih, -hih), one = make_float2(1.f, 1.f);
-    for (uint32_t j = s & ~1u; j < e; j += 2) {
-        const bool has0 = j >= s, has1 = j + 1 < e;
-        const float4 q0 = pos_s[has0 ? j : j + 1];
-        const float4 q1 = pos_s[has1 ? j + 1 : j];
-        const float2 dx = __fadd2_rn(px, make_float2(-q0.x, -q1.x));
-        const float2 dy = __fadd2_rn(py, make_float2(-q0.y, -q1.y));
-        const float2 dz = __fadd2_rn(pz, make_float2(-q0.z, -q1.z));
-        const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
-        bool t0 = has0 && r2.x < R2, t1 = has1 && r2.y < R2;
-        if (!ALL) {
-            t0 = t0 && (mbits & __float_as_uint(q0.w)) != 0u;
-            t1 = t1 && (mbits & __float_as_uint(q1.w)) != 0u;
+__device__ inline void pair_step(const float4 *__restrict__ pos_p, uint32_t m, uint32_t s, uint32_t e,
+                                 const float2 npx, const float2 npy, const float2 npz, uint32_t mbits, float R2,
+                                 float hih, PairAcc &acc, uint32_t self) {
+    const uint32_t j = 2 * m;
+    const bool has0 = j >= s, has1 = j + 1 < e;
+    const float4 A = pos_p[2 * (size_t)m], B = pos_p[2 * (size_t)m + 1];
+    const float2 dx = __fadd2_rn(make_float2(A.x, A.y), npx);     // q - p
+    const float2 dy = __fadd2_rn(make_float2(A.z, A.w), npy);
+    const float2 dz = __fadd2_rn(make_float2(B.x, B.y), npz);
+    const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+    bool t0 = has0 && r2.x < R2, t1 = has1 && r2.y < R2;
+    if (!ALL) {
+        t0 = t0 && (mbits & __float_as_uint(B.z)) != 0u;
+        t1 = t1 && (mbits & __float_as_uint(B.w)) != 0u;
+    }
+    if (COUNT) acc.cnt += (int)(t0 && j != self) + (int)(t1 && j + 1 != self);
+    const float2 r = __fmul2_rn(r2, make_float2(rsqrtf(r2.x + 1e-30f), rsqrtf(r2.y + 1e-30f)));
+    const float2 t = __ffma2_rn(r, make_float2(-hih, -hih), make_float2(1.f, 1.f));   // 1 - r / 2h
+    float2 w = __fmul2_rn(__fmul2_rn(t, t), t);
+    w.x = t0 ? w.x : 0.f;
+    w.y = t1 ? w.y : 0.f;
+    acc.ax = __ffma2_rn(w, dx, acc.ax);
+    acc.ay = __ffma2_rn(w, dy, acc.ay);
+    acc.az = __ffma2_rn(w, dz, acc.az);
+}
+
+template <bool ALL, bool COUNT>
+__device__ inline void force_range2(const float4 *__restrict__ pos_p, const float2 npx, const float2 npy,
+                                    const float2 npz, uint32_t mbits, float R2, float hih, uint32_t s, uint32_t e,
+                                    PairAcc &acc, uint32_t self) {
+    for (uint32_t m = s >> 1; 2 * m < e; m++)
+        pair_step<ALL, COUNT>(pos_p, m, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
+}
+
+// the nr ranges rows[0], rows[stride], ... back to back
+template <bool ALL, bool COUNT>
+__device__ inline void force_rows(const float4 *__restrict__ pos_p, const uint2 *rows, int stride, int nr,
+                                  const float2 npx, const float2 npy, const float2 npz, uint32_t mbits, float R2,
+                                  float hih, PairAcc &acc, uint32_t self) {
+    if (nr <= 0) return;
+    int r = 0;
+    uint2 se = rows[0];
+    uint32_t m = se.x >> 1;
+    while (true) {
+        pair_step<ALL, COUNT>(pos_p, m, se.x, se.y, npx, npy, npz, mbits, R2, hih, acc, self);
+        m++;
+        if (2 * m >= se.y) {
+            if (++r >= nr) break;
+            se = rows[r * stride];
+            m = se.x >> 1;
         }
-        if (COUNT) cnt += (int)(t0 && j != self) + (int)(t1 && j + 1 != self);
-        const float2 r = __fmul2_rn(r2, make_float2(rsqrtf(r2.x + 1e-30f), rsqrtf(r2.y + 1e-30f)));
-        const float2 t = __ffma2_rn(r, nh, one);                     // 1 - r / 2h
-        float2 w = __fmul2_rn(__fmul2_rn(t, t), t);
-        w.x = t0 ? w.x : 0.f;
-        w.y = t1 ? w.y : 0.f;
-        ax = __ffma2_rn(w, dx, ax);
-        ay = __ffma2_rn(w, dy, ay);
-        az = __ffma2_rn(w, dz, az);
     }
 }
 
 template <int VARIANT, bool COUNT>
-__global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s, int64_t N,
-                                               const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                               const uint2 *__restrict__ slab, const uint32_t *__restrict__ epoch,
-                                               float4 *__restrict__ acc_s, uint32_t *__restrict__ amax,
-                                               int32_t *__restrict__ count_s, int32_t *__restrict__ tested_s) {
+__global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
+                                               int64_t N, const AsmParams *__restrict__ P,
+                                               const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
+                                               const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s,
+                                               uint32_t *__restrict__ amax, int32_t *__restrict__ count_s,
+                                               int32_t *__restrict__ tested_s) {
+    __shared__ uint2 rows_sm[VARIANT == 2 ? 9 * TPB : 1];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -180,6 +226,7 @@ __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s,
     const GridPoint g = grid_point(A, p.x, p.y, p.z);
     const int cy = g.c[1], cz = g.c[2];
     const float R2 = A.R2, hih = A.half_inv_h;
+    const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y), npz = make_float2(-p.z, -p.z);
     // every class acts on every moving lane (volume targets): no mask test
     const bool all_cls = __all_sync(0xffffffffu, mbits == 0u || mbits == 0x1Fu);
     bool shared_row = false;
@@ -190,8 +237,8 @@ __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s,
         const uint32_t lead_row = __shfl_sync(0xffffffffu, rowkey, leader);
         shared_row = __all_sync(0xffffffffu, mbits == 0u || rowkey == lead_row);
     }
-    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
-    int cnt = 0, tested = 0;
+    PairAcc acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0};
+    int tested = 0, nr = 0;
     for (int dz = -1; dz <= 1; dz++) {
         const int z = cz + dz;
         const float gz = row_gap(g.t[2], cz, dz, g.slack);
@@ -203,24 +250,34 @@ __global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s,
                 row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
             }
             if (COUNT && e > s) tested += (int)(e - s);
+            if (VARIANT == 2) {
+                if (e > s) rows_sm[nr++ * blockDim.x + threadIdx.x] = make_uint2(s, e);
+                continue;
+            }
             if (VARIANT == 1 && shared_row) {
                 s = __reduce_min_sync(0xffffffffu, s);
                 e = __reduce_max_sync(0xffffffffu, e);
             }
-            if (all_cls) force_range2<true, COUNT>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az, cnt, (uint32_t)k);
-            else force_range2<false, COUNT>(pos_s, p, mbits, R2, hih, s, e, ax, ay, az, cnt, (uint32_t)k);
+            if (all_cls) force_range2<true, COUNT>(pos_p, npx, npy, npz, mbits, R2, hih, s, e, acc, (uint32_t)k);
+            else force_range2<false, COUNT>(pos_p, npx, npy, npz, mbits, R2, hih, s, e, acc, (uint32_t)k);
         }
+    }
+    if (VARIANT == 2) {
+        const uint2 *rows = rows_sm + threadIdx.x;
+        if (all_cls) force_rows<true, COUNT>(pos_p, rows, blockDim.x, nr, npx, npy, npz, mbits, R2, hih, acc, (uint32_t)k);
+        else force_rows<false, COUNT>(pos_p, rows, blockDim.x, nr, npx, npy, npz, mbits, R2, hih, acc, (uint32_t)k);
     }
     float fx = 0.f, fy = 0.f, fz = 0.f, mag = 0.f;
     if (mob) {
-        fx = (ax.x + ax.y) * A.force_scale;
-        fy = (ay.x + ay.y) * A.force_scale;
-        fz = (az.x + az.y) * A.force_scale;
+        // the sums hold q - p: negate
+        fx = -(acc.ax.x + acc.ax.y) * A.force_scale;
+        fy = -(acc.ay.x + acc.ay.y) * A.force_scale;
+        fz = -(acc.az.x + acc.az.y) * A.force_scale;
         mag = sqrtf(fx * fx + fy * fy + fz * fz);
     }
     if (active) acc_s[k] = make_float4(fx, fy, fz, mag);
     if (COUNT && active) {
-        count_s[k] = cnt;
+        count_s[k] = acc.cnt;
         if (tested_s) tested_s[k] = mob ? tested : 0;
     }
     labelled_max(amax, b, mag);
@@ -440,7 +497,25 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
     return t == 0x7fffffff ? -1 : t;
 }
 
-__device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf) {
+// distance from y to the faces of the 3 x 3 x 3 triangle-cell block around
+// its cell (0 when y lies outside the grid): no triangle outside the block
+// comes closer than this
+__device__ inline float block_margin(const AsmParams &A, float3 y) {
+    const float v[3] = {y.x, y.y, y.z};
+    float m = FLT_MAX;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float t = __fmul_rn(__fsub_rn(v[k], A.tg_o[k]), A.tg_inv);
+        const float c = (float)cell_coord(v[k], A.tg_o[k], A.tg_inv, A.tg_n[k]);
+        m = fminf(m, fminf(t - (c - 1.f), (c + 2.f) - t));
+    }
+    return fmaxf(m, 0.f) / A.tg_inv;
+}
+
+// Volume test (reading: closest point over the 27 triangle cells, sign of
+// the angle-weighted pseudonormal; none in range: accept).  *clear gets a
+// lower bound of the distance from y to the surface, valid when inside.
+__device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear) {
     const int lane = threadIdx.x & 31;
     const CellRange r = lane_cell(M, A, y, lane);
     float best = FLT_MAX;
@@ -464,6 +539,8 @@ __device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3
     float v = best;
     int t = bt;
     warp_argmin(v, t);
+    const float blk = block_margin(A, y);
+    clear = fmaxf(fminf(t == 0x7fffffff ? FLT_MAX : sqrtf(v), blk) * (1.f - 0x1p-10f) - A.dx * 0x1p-16f, 0.f);
     if (t == 0x7fffffff) return true;
     const uint32_t own = __ballot_sync(0xffffffffu, bt == t && best == v);
     const int src = __ffs(own) - 1;
@@ -521,7 +598,7 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
                                               const AsmParams *__restrict__ P, const uint32_t *__restrict__ amax,
                                               float4 *__restrict__ pos, int32_t *__restrict__ cons, MeshView M,
                                               uint32_t *__restrict__ maxdisp, int4 *__restrict__ work,
-                                              uint32_t *__restrict__ work_count) {
+                                              uint32_t *__restrict__ work_count, const float4 *__restrict__ cert) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -560,7 +637,18 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             const int cx = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]);
             const int cy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]);
             const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
-            if (test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
+            bool certified = false;
+            if (cls == kClsV && A.closed) {
+                // inside a ball that an earlier search found free of surface
+                // and inside the body: the volume test would accept
+                const float4 cc = cert[i];
+                const float3 w = y - f3(cc);
+                certified = cc.w > 0.f && sqrtf(dot3(w, w)) + cc.w * 0x1p-6f + A.dx * 0x1p-10f < cc.w;
+            }
+            if (certified) {
+                pos[i] = make_float4(y.x, y.y, y.z, p.w);
+                disp = sqrtf(dot3(dr, dr));
+            } else if (test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
                 queue = true;
             } else if (cls == kClsV) {       // nothing near: inside, accept
                 pos[i] = make_float4(y.x, y.y, y.z, p.w);
@@ -590,7 +678,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
                                                 const AsmParams *__restrict__ P, float4 *__restrict__ pos,
                                                 int32_t *__restrict__ cons, MeshView M,
                                                 uint32_t *__restrict__ maxdisp, const int4 *__restrict__ work,
-                                                const uint32_t *__restrict__ work_count) {
+                                                const uint32_t *__restrict__ work_count, float4 *__restrict__ cert) {
     __shared__ int32_t sbuf[TPB / 32][kSearchBuf];
     int32_t *buf = sbuf[threadIdx.x / 32];
     const int lane = threadIdx.x & 31;
@@ -604,6 +692,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
         const AsmParams &A = P[b];
         float3 x = y;
         int tri = -2;
+        float clear = 0.f;
         bool ok;
         if (cls == kClsS) {
             float d;
@@ -611,12 +700,13 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             ok = tri >= 0;
             if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
         } else {
-            ok = warp_volume_inside(M, A, y, buf);
+            ok = warp_volume_inside(M, A, y, buf, clear);
         }
         if (ok && lane == 0) {
             const uint32_t i = id_s[it.x];
             pos[i] = make_float4(x.x, x.y, x.z, p.w);
             if (tri >= 0) cons[i] = tri;
+            if (cls == kClsV && A.closed) cert[i] = make_float4(y.x, y.y, y.z, clear);
             const float3 w = x - f3(p);
             atomicMax(maxdisp + b, __float_as_uint(sqrtf(dot3(w, w))));
         }
@@ -663,7 +753,8 @@ __global__ void k_project_points(const float *__restrict__ y, const int32_t *__r
             cn = t;
         }
     } else if (cl == kClsV) {
-        r = warp_volume_inside(M, A, yy, buf);
+        float clear;
+        r = warp_volume_inside(M, A, yy, buf, clear);
     } else if (cl == kClsF) {
         r = project_feature(M, A, yy, c, xx, cn);
     }
@@ -752,6 +843,7 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
                                                                  d.maxdisp, d.B, d.work_count);
     int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
     k_gather_ranges<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s,
+                                                  reinterpret_cast<float *>(d.pos_p),
                                                   reinterpret_cast<uint32_t *>(d.cells),
                                                   reinterpret_cast<uint8_t *>(d.slab), d.epoch);
     return buf;
@@ -761,14 +853,16 @@ int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
 
 void forces_dev(DevGroup &d, int tb, int variant, cudaStream_t s, int32_t *count_s, int32_t *tested_s) {
     const unsigned nbk = (unsigned)std::max<int64_t>((d.N + tb - 1) / tb, 1);
-#define FPPG_FORCE(V, C)                                                                                      \
-    k_force<V, C><<<nbk, tb, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.acc_s, d.amax, count_s, \
-                                     tested_s)
+#define FPPG_FORCE(V, C)                                                                                       \
+    k_force<V, C><<<nbk, tb, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.acc_s, d.amax,  \
+                                     count_s, tested_s)
     if (count_s) {
         if (variant == 1) FPPG_FORCE(1, true);
+        else if (variant == 2) FPPG_FORCE(2, true);
         else FPPG_FORCE(0, true);
     } else {
         if (variant == 1) FPPG_FORCE(1, false);
+        else if (variant == 2) FPPG_FORCE(2, false);
         else FPPG_FORCE(0, false);
     }
 #undef FPPG_FORCE
@@ -799,9 +893,9 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
         g.ev_used += 2;
     }
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
-                                         d.maxdisp, d.work, d.work_count);
+                                         d.maxdisp, d.work, d.work_count, d.cert);
     k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp, d.work,
-                                             d.work_count);
+                                             d.work_count, d.cert);
 }
 
 void unpermute_dev(DevGroup &d, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s,
