@@ -38,7 +38,7 @@ SMS, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 # (dx = 0.02), from the ncu capture summarised in
 # profiles/k_force_icosphere_torus_dx002.md; None for other workloads and
 # until the current kernel has been captured.
-K_FORCE_DRAM_BYTES = {}
+K_FORCE_DRAM_BYTES = {0.02: 26607360 + 8960}
 
 
 def parse():
@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--dx", type=float, default=0.02)
     p.add_argument("--no-extras", action="store_true", help="skip plain / e2e / CPU legs")
     p.add_argument("--no-autotune", action="store_true", help="keep the default kernel configuration")
+    p.add_argument("--config", default=None,
+                   help="force variant,block,search CTAs per SM (e.g. 0,128,4) instead of the autotuner")
     return p.parse_args()
 
 
@@ -227,7 +229,12 @@ def main():
 
     # ---- batched form, CUDA graph of G iterations --------------------------
     batch = pkg.Batch(bodies, stream=stream)
-    tuned = None if args.no_autotune else batch.autotune(5)
+    if args.config:
+        v, tb, sc = (int(x) for x in args.config.split(","))
+        batch.configure(v, tb, sc)
+        tuned = {"force_variant": v, "force_block": tb, "search_ctas_per_sm": sc, "fixed": True}
+    else:
+        tuned = None if args.no_autotune else batch.autotune(5)
     batch.set_graph_iters(G)
     batch.time_force(True)
     clocks = Clocks(local)

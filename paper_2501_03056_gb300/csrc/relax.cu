@@ -144,6 +144,14 @@ __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restric
 // partial sum, in the same order, in every variant.
 // COUNT adds, per particle, the accepted neighbours (self excluded) and the
 // slots of its own ranges (candidates tested).
+// r = sqrt(r^2) by the approximate square-root instruction (relative error
+// of a few 2^-23; exactly 0 at 0, so the particle itself needs no guard)
+__device__ inline float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct PairAcc {
     float2 ax, ay, az;
     int cnt;
@@ -166,7 +174,7 @@ __device__ inline void pair_step(const float4 *__restrict__ pos_p, uint32_t m, u
         t1 = t1 && (mbits & __float_as_uint(B.w)) != 0u;
     }
     if (COUNT) acc.cnt += (int)(t0 && j != self) + (int)(t1 && j + 1 != self);
-    const float2 r = __fmul2_rn(r2, make_float2(rsqrtf(r2.x + 1e-30f), rsqrtf(r2.y + 1e-30f)));
+    const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
     const float2 t = __ffma2_rn(r, make_float2(-hih, -hih), make_float2(1.f, 1.f));   // 1 - r / 2h
     float2 w = __fmul2_rn(__fmul2_rn(t, t), t);
     w.x = t0 ? w.x : 0.f;
@@ -205,7 +213,7 @@ __device__ inline void force_rows(const float4 *__restrict__ pos_p, const uint2 
 }
 
 template <int VARIANT, bool COUNT>
-__global__ void __launch_bounds__(TPB) k_force(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
+__global__ void __launch_bounds__(TPB, 5) k_force(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
                                                int64_t N, const AsmParams *__restrict__ P,
                                                const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
                                                const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s,
