@@ -236,12 +236,18 @@ def main():
     else:
         tuned = None if args.no_autotune else batch.autotune(5)
     batch.set_graph_iters(G)
-    batch.time_force(True)
     clocks = Clocks(local)
     clocks.start()
     ms = timed_steps(lambda: batch.relax(G, use_graph=True), batch.load)
     clk = clocks.stop()
-    force_ms = batch.force_ms()
+    # one more replay, with CUDA event records around the phases of every
+    # iteration captured into the graph: live per-phase device times
+    batch.time_force(True)
+    batch.load()
+    batch.relax(G, use_graph=True)
+    phases = batch.phase_ms()
+    force_ms = phases["force"]
+    batch.time_force(False)
     tot_ms = max_over_ranks(sum(ms))
     value = n * world * G * K / (tot_ms / 1e3)
     kpi = batch.kernels_per_iter
@@ -352,6 +358,7 @@ def main():
                      "tested": tested, "executed_TFLOPs": executed, "executed_frac": executed / fp32_peak},
         "hbm": {"useful_bytes_per_particle_iteration": 56, "useful_GBps": useful_gbs,
                 "frac_of_measured": useful_gbs / hbm},
+        "phase_ms_per_iteration": {**phases, "note": "one extra replay with event records in the graph"},
         "gpu_launches": kpi * G * K,
         "autotune": tuned,
         "clocks": clk,

@@ -241,7 +241,7 @@ int fppg_batch_store(fppg_batch *b);
 int fppg_batch_load(fppg_batch *b);
 /* Autotuner: times `iters` iterations of the batch for every combination
  * of force-kernel block size (128, 256), force-kernel variant (0 per-lane
- * rows, 1 shared-row union, 2 per-lane rows walked back to back) and
+ * rows, 1 shared-row union) and
  * persistent search grid (4, 8 or 16 CTAs per SM),
  * keeps the fastest and restores the particle state afterwards.  The choice
  * is cached per (particle-count bucket, volume-particle share, GPU name) for
@@ -250,7 +250,7 @@ int fppg_batch_load(fppg_batch *b);
  * measured ms per iteration (0 when taken from the cache). */
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
                         double *ms_per_iter);
-/* The same choice made by hand: force variant 0..2, force block 128 or 256,
+/* The same choice made by hand: force variant 0 or 1, force block 128 or 256,
  * search CTAs per SM 1..64 (FPPG_ERR_ARG otherwise).  Every choice gives the
  * same bits; only the speed differs.  Drops a captured graph. */
 int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t search_ctas);
@@ -259,11 +259,17 @@ int32_t fppg_batch_kernels_per_iter(const fppg_batch *b);
 /* Particle count and the last error of the batch. */
 int64_t fppg_batch_size(const fppg_batch *b);
 const char *fppg_batch_last_error(const fppg_batch *b);
-/* Per-launch device time of the force kernel (A4) averaged over the
- * iterations of the last call of fppg_batch_relax when timing was enabled
- * with fppg_batch_time_force(b, 1); ms through *ms. */
+/* Phase timing of the graph form: fppg_batch_time_force(b, 1) puts CUDA
+ * event records into the captured graph (dropping a graph captured
+ * without them) around each iteration's grid build (A1-A3), force pass
+ * (A4) and step + projection (A5-A6).  After a graph replay of
+ * fppg_batch_relax, fppg_batch_phase_ms gives the device time of each
+ * phase averaged over the graph's iterations (outputs nullable) and
+ * fppg_batch_force_ms the force pass alone; FPPG_ERR_STATE when timing is
+ * off or no graph has been captured.  Both synchronise the batch stream. */
 int fppg_batch_time_force(fppg_batch *b, int32_t enable);
 int fppg_batch_force_ms(fppg_batch *b, double *ms);
+int fppg_batch_phase_ms(fppg_batch *b, double *grid_ms, double *force_ms, double *project_ms);
 
 /* ---- allocation-free force pass ---------------------------------------------
  * fppg_forces_static: the neighbour grid and the force pass (A1-A4) for one

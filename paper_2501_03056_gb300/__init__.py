@@ -90,6 +90,7 @@ def lib():
                 "fppg_batch_force_ms": [vp, P_(f64)],
                 "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(f64)],
                 "fppg_batch_configure": [vp, i32, i32, i32],
+                "fppg_batch_phase_ms": [vp, P_(f64), P_(f64), P_(f64)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -375,6 +376,13 @@ class Batch:
     def configure(self, force_variant: int = 0, force_block: int = 256, search_ctas_per_sm: int = 16):
         """Set the kernel configuration by hand (the autotuner's choices)."""
         self._chk(lib().fppg_batch_configure(self._h, int(force_variant), int(force_block), int(search_ctas_per_sm)))
+
+    def phase_ms(self) -> dict:
+        """Device ms per iteration of grid build, force pass and step +
+        projection, from the last graph replay with timing enabled."""
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self._chk(lib().fppg_batch_phase_ms(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"grid": a.value, "force": b.value, "project": c.value}
 
     def force_ms(self) -> float:
         ms = C.c_double()

@@ -581,7 +581,7 @@ static int build_graph(fppg_batch *b) {
     if (g.graph_iters <= 0) g.graph_iters = 50;
     if (!g.graph_stream) CUDA_OR(b->err, cudaStreamCreateWithFlags(&g.graph_stream, cudaStreamNonBlocking));
     if (g.time_force) {
-        while ((int)g.ev.size() < 2 * g.graph_iters) {
+        while ((int)g.ev.size() < 4 * g.graph_iters) {
             cudaEvent_t e;
             CUDA_OR(b->err, cudaEventCreate(&e));
             g.ev.push_back(e);
@@ -619,19 +619,28 @@ int fppg_batch_relax(fppg_batch *b, int32_t n_iter, int32_t use_graph) {
     return FPPG_OK;
 }
 
+int fppg_batch_phase_ms(fppg_batch *b, double *grid_ms, double *force_ms, double *project_ms) {
+    if (!b) return FPPG_ERR_ARG;
+    Group &g = b->group;
+    if (!g.time_force || !g.graph || (int)g.ev.size() < 4 * g.graph_iters)
+        return fail(b->err, FPPG_ERR_STATE, "phase timing not active");
+    CUDA_OR(b->err, cudaStreamSynchronize(b->stream));
+    double tot[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < g.graph_iters; i++)
+        for (int k = 0; k < 3; k++) {
+            float t = 0.f;
+            CUDA_OR(b->err, cudaEventElapsedTime(&t, g.ev[4 * i + k], g.ev[4 * i + k + 1]));
+            tot[k] += t;
+        }
+    if (grid_ms) *grid_ms = tot[0] / g.graph_iters;
+    if (force_ms) *force_ms = tot[1] / g.graph_iters;
+    if (project_ms) *project_ms = tot[2] / g.graph_iters;
+    return FPPG_OK;
+}
+
 int fppg_batch_force_ms(fppg_batch *b, double *ms) {
     if (!b || !ms) return FPPG_ERR_ARG;
-    Group &g = b->group;
-    if (!g.time_force || !g.graph || g.ev.size() < 2) return fail(b->err, FPPG_ERR_STATE, "force timing not active");
-    CUDA_OR(b->err, cudaStreamSynchronize(b->stream));
-    double tot = 0.0;
-    for (int i = 0; i + 1 < 2 * g.graph_iters; i += 2) {
-        float t = 0.f;
-        CUDA_OR(b->err, cudaEventElapsedTime(&t, g.ev[i], g.ev[i + 1]));
-        tot += t;
-    }
-    *ms = tot / g.graph_iters;
-    return FPPG_OK;
+    return fppg_batch_phase_ms(b, nullptr, ms, nullptr);
 }
 
 int fppg_batch_store(fppg_batch *b) {
@@ -727,7 +736,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
         const bool tf = g.time_force;
         g.time_force = false;
         best_ms = 1e30;
-        for (int v = 0; v < 3; v++)
+        for (int v = 0; v < 2; v++)
             for (int tb : {128, 256})
                 for (int sc : {4, 8, 16}) {
                     g.force_variant = v;
@@ -773,7 +782,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
 }
 
 int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t search_ctas) {
-    if (!b || variant < 0 || variant > 2 || (block != 128 && block != 256) || search_ctas < 1 || search_ctas > 64)
+    if (!b || variant < 0 || variant > 1 || (block != 128 && block != 256) || search_ctas < 1 || search_ctas > 64)
         return FPPG_ERR_ARG;
     Group &g = b->group;
     int dev = 0;

@@ -27,7 +27,7 @@ namespace {
 
 constexpr int64_t kStaticMaxN = 65536;       // particles per call
 constexpr int64_t kStaticMaxCells = 131072;  // neighbour-grid cells
-constexpr int64_t kStaticMaxTiles = (kStaticMaxN + 4095) / 4096;
+constexpr int64_t kStaticMaxTiles = (kStaticMaxN + 1023) / 1024;  // tiles of the smallest radix tile
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 

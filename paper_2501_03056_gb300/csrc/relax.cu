@@ -130,14 +130,11 @@ __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restric
 // exactly as the scalar rule.  The loop works on q - p (the exact negation
 // of p - q) and accumulates without branches into two partial sums.
 //
-// Variant 0 walks the rows one by one.  Variant 1 (shared row): when every
-// moving lane of a warp lies in the same grid row of the same body, the
-// lanes' ranges for one row offset lie in a single grid row and the warp
-// walks their union in lockstep (broadcast loads); a candidate outside a
-// lane's own range is out of its reach and fails the test.  Variant 2
-// (flattened): the lane's non-empty ranges are parked in shared memory and
-// walked back to back, so a warp runs as long as its longest lane's total
-// rather than the sum over rows of the longest range.
+// Variant 0 walks each lane's own ranges.  Variant 1 (shared row): when
+// every moving lane of a warp lies in the same grid row of the same body,
+// the lanes' ranges for one row offset lie in a single grid row and the
+// warp walks their union in lockstep (broadcast loads); a candidate outside
+// a lane's own range is out of its reach and fails the test.
 // The particle itself adds (1 - 0)^3 * 0 = 0, so no self test is needed.
 // Slots are paired by absolute parity (even -> .x, odd -> .y) with the range
 // [s, e) applied as a mask, so every accepted neighbour lands in the same
@@ -192,34 +189,13 @@ __device__ inline void force_range2(const float4 *__restrict__ pos_p, const floa
         pair_step<ALL, COUNT>(pos_p, m, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
 }
 
-// the nr ranges rows[0], rows[stride], ... back to back
-template <bool ALL, bool COUNT>
-__device__ inline void force_rows(const float4 *__restrict__ pos_p, const uint2 *rows, int stride, int nr,
-                                  const float2 npx, const float2 npy, const float2 npz, uint32_t mbits, float R2,
-                                  float hih, PairAcc &acc, uint32_t self) {
-    if (nr <= 0) return;
-    int r = 0;
-    uint2 se = rows[0];
-    uint32_t m = se.x >> 1;
-    while (true) {
-        pair_step<ALL, COUNT>(pos_p, m, se.x, se.y, npx, npy, npz, mbits, R2, hih, acc, self);
-        m++;
-        if (2 * m >= se.y) {
-            if (++r >= nr) break;
-            se = rows[r * stride];
-            m = se.x >> 1;
-        }
-    }
-}
-
 template <int VARIANT, bool COUNT>
-__global__ void __launch_bounds__(TPB, 5) k_force(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
-                                               int64_t N, const AsmParams *__restrict__ P,
-                                               const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
-                                               const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s,
-                                               uint32_t *__restrict__ amax, int32_t *__restrict__ count_s,
-                                               int32_t *__restrict__ tested_s) {
-    __shared__ uint2 rows_sm[VARIANT == 2 ? 9 * TPB : 1];
+// (at most 48 registers: five 256-thread blocks per SM)
+__global__ void __launch_bounds__(TPB, 5)
+    k_force(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p, int64_t N,
+            const AsmParams *__restrict__ P, const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
+            const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s, uint32_t *__restrict__ amax,
+            int32_t *__restrict__ count_s, int32_t *__restrict__ tested_s) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -246,7 +222,7 @@ __global__ void __launch_bounds__(TPB, 5) k_force(const float4 *__restrict__ pos
         shared_row = __all_sync(0xffffffffu, mbits == 0u || rowkey == lead_row);
     }
     PairAcc acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0};
-    int tested = 0, nr = 0;
+    int tested = 0;
     for (int dz = -1; dz <= 1; dz++) {
         const int z = cz + dz;
         const float gz = row_gap(g.t[2], cz, dz, g.slack);
@@ -258,10 +234,6 @@ __global__ void __launch_bounds__(TPB, 5) k_force(const float4 *__restrict__ pos
                 row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
             }
             if (COUNT && e > s) tested += (int)(e - s);
-            if (VARIANT == 2) {
-                if (e > s) rows_sm[nr++ * blockDim.x + threadIdx.x] = make_uint2(s, e);
-                continue;
-            }
             if (VARIANT == 1 && shared_row) {
                 s = __reduce_min_sync(0xffffffffu, s);
                 e = __reduce_max_sync(0xffffffffu, e);
@@ -269,11 +241,6 @@ __global__ void __launch_bounds__(TPB, 5) k_force(const float4 *__restrict__ pos
             if (all_cls) force_range2<true, COUNT>(pos_p, npx, npy, npz, mbits, R2, hih, s, e, acc, (uint32_t)k);
             else force_range2<false, COUNT>(pos_p, npx, npy, npz, mbits, R2, hih, s, e, acc, (uint32_t)k);
         }
-    }
-    if (VARIANT == 2) {
-        const uint2 *rows = rows_sm + threadIdx.x;
-        if (all_cls) force_rows<true, COUNT>(pos_p, rows, blockDim.x, nr, npx, npy, npz, mbits, R2, hih, acc, (uint32_t)k);
-        else force_rows<false, COUNT>(pos_p, rows, blockDim.x, nr, npx, npy, npz, mbits, R2, hih, acc, (uint32_t)k);
     }
     float fx = 0.f, fy = 0.f, fz = 0.f, mag = 0.f;
     if (mob) {
@@ -866,11 +833,9 @@ void forces_dev(DevGroup &d, int tb, int variant, cudaStream_t s, int32_t *count
                                      count_s, tested_s)
     if (count_s) {
         if (variant == 1) FPPG_FORCE(1, true);
-        else if (variant == 2) FPPG_FORCE(2, true);
         else FPPG_FORCE(0, true);
     } else {
         if (variant == 1) FPPG_FORCE(1, false);
-        else if (variant == 2) FPPG_FORCE(2, false);
         else FPPG_FORCE(0, false);
     }
 #undef FPPG_FORCE
@@ -886,24 +851,27 @@ void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s, int32_t
 void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     DevGroup &d = g.d;
     if (d.N == 0) return;
-    int buf = build_grid(g, s);
-    const bool timed = g.time_force && g.ev_used + 2 <= (int)g.ev.size();
+    // phase timing: events before A1, after A3, after A4 and after A6
+    const bool timed = g.time_force && g.ev_used + 4 <= (int)g.ev.size();
     // inside a stream capture the records must be external so that they
     // become event-record nodes whose timestamps can be read after a replay
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (timed) cudaStreamIsCapturing(s, &cap);
     const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used], s, flags);
+    int buf = build_grid(g, s);
+    if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 1], s, flags);
     if (energy_mode) energy_accel(g, s);
     else forces(g, s, count_dbg);
-    if (timed) {
-        cudaEventRecordWithFlags(g.ev[g.ev_used + 1], s, flags);
-        g.ev_used += 2;
-    }
+    if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 2], s, flags);
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
                                          d.maxdisp, d.work, d.work_count, d.cert);
     k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp, d.work,
                                              d.work_count, d.cert);
+    if (timed) {
+        cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
+        g.ev_used += 4;
+    }
 }
 
 void unpermute_dev(DevGroup &d, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s,

@@ -18,8 +18,9 @@ namespace {
 
 constexpr int RT = 256;               // threads per CTA
 constexpr int RW = RT / 32;           // warps per CTA
-constexpr int RC = 16;                // 32-item chunks per warp
-constexpr int TILE = RW * RC * 32;    // 4096 items per tile
+// RC 32-item chunks per warp, a tile of RW * RC * 32 items per CTA: 4096,
+// 2048 or 1024, the largest that still gives every SM four tiles
+constexpr int kMinTile = RW * 4 * 32;
 
 __device__ inline uint32_t lanemask_lt() {
     uint32_t m;
@@ -53,9 +54,10 @@ __device__ inline uint32_t block_incl_scan(uint32_t v, uint32_t *wsum, uint32_t 
     return r;
 }
 
-template <typename K>
+template <typename K, int RC>
 __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int64_t n, int shift,
                                                 uint32_t *__restrict__ hist, int n_tiles) {
+    constexpr int TILE = RW * RC * 32;
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -89,11 +91,12 @@ __global__ void __launch_bounds__(RT) k_digit_scan(uint32_t *__restrict__ hist, 
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-template <typename K, bool IOTA>
+template <typename K, bool IOTA, int RC>
 __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                   K *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
                                                   int shift, const uint32_t *__restrict__ hist,
                                                   const uint32_t *__restrict__ totals, int n_tiles) {
+    constexpr int TILE = RW * RC * 32;
     extern __shared__ __align__(16) unsigned char smem[];
     K *skey = reinterpret_cast<K *>(smem);
     uint32_t *sval = reinterpret_cast<uint32_t *>(smem + sizeof(K) * TILE);
@@ -163,39 +166,62 @@ __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, con
     }
 }
 
-template <typename K>
+template <typename K, int RC>
 size_t downsweep_smem() {
-    return (sizeof(K) + 4) * TILE + RW * 256 * 4 + 2 * 256 * 4 + RW * 4;
+    return (sizeof(K) + 4) * (size_t)(RW * RC * 32) + RW * 256 * 4 + 2 * 256 * 4 + RW * 4;
+}
+
+template <typename K, int RC>
+void set_smem_attr() {
+    cudaFuncSetAttribute(k_downsweep<K, true, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)downsweep_smem<K, RC>());
+    cudaFuncSetAttribute(k_downsweep<K, false, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)downsweep_smem<K, RC>());
+}
+
+template <typename K, int RC>
+int radix_passes(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int passes, uint32_t *hist,
+                 uint32_t *totals, cudaStream_t s) {
+    constexpr int TILE = RW * RC * 32;
+    const int n_tiles = (int)((n + TILE - 1) / TILE);
+    int cur = 0;
+    for (int p = 0; p < passes; p++) {
+        const int shift = 8 * p;
+        k_upsweep<K, RC><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles);
+        k_digit_scan<<<256, RT, 0, s>>>(hist, n_tiles, totals);
+        if (p == 0 && iota_vals)
+            k_downsweep<K, true, RC><<<n_tiles, RT, downsweep_smem<K, RC>(), s>>>(
+                keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
+        else
+            k_downsweep<K, false, RC><<<n_tiles, RT, downsweep_smem<K, RC>(), s>>>(
+                keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
+        cur ^= 1;
+    }
+    return cur;
 }
 
 template <typename K>
 int radix_sort_impl(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                     uint32_t *totals, cudaStream_t s) {
     if (n <= 0) return 0;
-    const int n_tiles = (int)((n + TILE - 1) / TILE);
     const int passes = bits <= 0 ? 0 : (bits + 7) / 8;
     static bool attr_done = false;
+    static int sms = 0;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_downsweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)downsweep_smem<K>());
-        cudaFuncSetAttribute(k_downsweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)downsweep_smem<K>());
+        set_smem_attr<K, 4>();
+        set_smem_attr<K, 8>();
+        set_smem_attr<K, 16>();
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
         attr_done = true;
     }
-    int cur = 0;
-    for (int p = 0; p < passes; p++) {
-        const int shift = 8 * p;
-        k_upsweep<K><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles);
-        k_digit_scan<<<256, RT, 0, s>>>(hist, n_tiles, totals);
-        if (p == 0 && iota_vals)
-            k_downsweep<K, true><<<n_tiles, RT, downsweep_smem<K>(), s>>>(
-                keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
-        else
-            k_downsweep<K, false><<<n_tiles, RT, downsweep_smem<K>(), s>>>(
-                keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
-        cur ^= 1;
-    }
-    return cur;
+    // the largest tile that still gives every SM four tiles (latency hiding)
+    const int64_t want = 4 * (int64_t)sms;
+    if ((n + 4095) / 4096 >= want) return radix_passes<K, 16>(keys, vals, iota_vals, n, passes, hist, totals, s);
+    if ((n + 2047) / 2048 >= want) return radix_passes<K, 8>(keys, vals, iota_vals, n, passes, hist, totals, s);
+    return radix_passes<K, 4>(keys, vals, iota_vals, n, passes, hist, totals, s);
 }
 
 // ---- exclusive scan (set-up work) -----------------------------------------
@@ -236,7 +262,8 @@ __global__ void k_scan_total(const uint32_t *in, const uint32_t *out, int64_t n,
 
 } // namespace
 
-int64_t radix_tiles(int64_t n) { return (n + TILE - 1) / TILE; }
+// tiles of the smallest tile size: room for the histogram of any choice
+int64_t radix_tiles(int64_t n) { return (n + kMinTile - 1) / kMinTile; }
 
 int radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                    uint32_t *totals, cudaStream_t s) {
