@@ -77,6 +77,8 @@ def lib():
                 "oracle_volume_inside": (None, [vp, P(f32), i64, P(i32)]),
                 "oracle_ray_parity": (None, [vp, P(f64), i64, P(i32)]),
                 "oracle_relax": (C.c_int, [vp, i32]),
+                "oracle_union_keep": (None, [vp, vp, C.c_int, P(i32)]),
+                "oracle_union_relax": (C.c_int, [vp, vp, i32]),
                 "oracle_relax_energy": (C.c_int, [vp, i32]),
                 "oracle_last_iteration": (None, [vp, P(f64), P(f64), P(i64)]),
                 "oracle_w0": (None, [vp, P(f64)]),
@@ -287,6 +289,14 @@ class Oracle:
     def relax(self, n_iter):
         lib().oracle_relax(self._c, int(n_iter))
 
+    def union_keep(self, other: "Oracle", volume_stays: bool) -> np.ndarray:
+        """Which of this body's particles stay in its Boolean union with
+        `other` (dropped: inside `other` by ray parity, unless volume_stays
+        and the particle is a volume or innermost one)."""
+        keep = np.zeros(max(self.n, 1), np.int32)
+        lib().oracle_union_keep(self._c, other._c, int(bool(volume_stays)), _p(keep, C.c_int32))
+        return keep[:self.n].astype(bool)
+
     def relax_energy(self, n_iter):
         lib().oracle_relax_energy(self._c, int(n_iter))
 
@@ -324,6 +334,21 @@ class Oracle:
         out = np.zeros(len(STATS_KEYS))
         lib().oracle_stats(self._c, _p(out, C.c_double))
         return dict(zip(STATS_KEYS, out.tolist()))
+
+
+def union_relax(a: Oracle, b: Oracle, n_iter: int):
+    """Relax the Boolean union of bodies a and b as one assembly (shared
+    forces and time step; surface and feature particles kept out of the
+    partner)."""
+    if lib().oracle_union_relax(a._c, b._c, int(n_iter)) != 0:
+        raise ValueError("union members need the same dx, h and feature setting")
+
+
+def keep_rows(o: Oracle, keep: np.ndarray):
+    """Keep only the particles (and their constraints) marked in `keep`."""
+    x, c, cons = o.get_particles()
+    o.set_particles(x[keep].astype(np.float32), c[keep])
+    o.set_state(x[keep], cons[keep])
 
 
 def from_assembly(a, features=True) -> Oracle:

@@ -1188,7 +1188,17 @@ static float closest_on_triangle(const or_ctx *c, int64_t t, const float *y, flo
  * (smallest distance, ties to the lower index) and the sign of (y - c) . psi
  * with psi the pseudonormal of the closest feature.  Returns 1 inside (or no
  * triangle near), 0 outside. */
+static int closest_sign_inside(const or_ctx *c, const float *yf);
+
 static int volume_inside_f(const or_ctx *c, const float *yf)
+{
+    int r = closest_sign_inside(c, yf);
+    return r < 0 ? 1 : r;
+}
+
+/* The closest-feature sign test alone: 1 inside, 0 outside, -1 when no
+ * triangle lies in the 27 cells around yf. */
+static int closest_sign_inside(const or_ctx *c, const float *yf)
 {
     int32_t ci[3];
     tri_cell_of(c, yf, ci);
@@ -1218,7 +1228,7 @@ static int volume_inside_f(const or_ctx *c, const float *yf)
                     }
                 }
             }
-    if (bt < 0) return 1;
+    if (bt < 0) return -1;
     const float *psi;
     if (breg == 0) psi = c->Nuf + 3 * bt;
     else if (breg <= 3) psi = c->EPf + 9 * bt + 3 * (breg - 1);
@@ -1375,7 +1385,16 @@ void oracle_ray_parity(const or_ctx *c, const double *p, int64_t n, int32_t *ins
  * reset); dr = v_{n+1} dt (Eq. 23); tangential part only for surface
  * (triangle normal) and feature (segment direction) particles; then the
  * projection of the trial point, or revert. */
-static void apply_step(or_ctx *c, const double *acc, double amax)
+static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner);
+
+static void apply_step(or_ctx *c, const double *acc, double amax) { apply_step_partner(c, acc, amax, NULL); }
+
+/* With a union partner (see oracle_union_relax), a surface or feature
+ * particle whose projected position lies inside the partner reverts: a
+ * partner triangle within the 27 cells and the closest-feature sign inside
+ * (no partner triangle near: outside, as the particle started outside the
+ * partner and moves less than a cell per iteration). */
+static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner)
 {
     double dt = amax > 0.0 ? 0.25 * sqrt((double)c->h / amax) : 0.0;
     double *Xn = malloc(sizeof(double) * 3 * (c->n ? c->n : 1));
@@ -1408,7 +1427,12 @@ static void apply_step(or_ctx *c, const double *acc, double amax)
         for (int k = 0; k < 3; k++) y[k] = x[k] + dr[k];
         double xn[3];
         int32_t cn;
-        if (project_point(c, cl, y, cs, xn, &cn)) {
+        int ok = project_point(c, cl, y, cs, xn, &cn);
+        if (ok && partner && (cl == OR_S || cl == OR_F)) {
+            float xf[3] = {(float)xn[0], (float)xn[1], (float)xn[2]};
+            if (closest_sign_inside(partner, xf) == 1) ok = 0;
+        }
+        if (ok) {
             memcpy(Xn + 3 * i, xn, sizeof(xn));
             Cn[i] = cn;
         } else {
@@ -1436,6 +1460,68 @@ int oracle_relax(or_ctx *c, int32_t n_iter)
         apply_step(c, acc, amax);
     }
     free(acc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Boolean union of two bodies (Sec. 3.2.3, Fig. 10)                         */
+/* ------------------------------------------------------------------------ */
+/* The paper unites two bodies through their cell sets: a cell interior to
+ * either is interior to the union.  Reading, on particles: the particles of
+ * one body that lie inside the other (ray parity of Fig. 6 against the
+ * other's mesh) are dropped, except that the volume and innermost particles
+ * of the second body stay, so that the overlap keeps one copy of its
+ * volume particles.  keep[i] = 1 for the particles of `self` that stay;
+ * volume_stays = 0 for the first body, 1 for the second. */
+void oracle_union_keep(const or_ctx *self, const or_ctx *other, int volume_stays, int32_t *keep)
+{
+    int32_t *inside = malloc(sizeof(int32_t) * (self->n ? self->n : 1));
+    oracle_ray_parity(other, self->X, self->n, inside);
+    for (int64_t i = 0; i < self->n; i++) {
+        int vol = self->cls[i] == OR_V || self->cls[i] == OR_I;
+        keep[i] = !inside[i] || (volume_stays && vol);
+    }
+    free(inside);
+}
+
+/* Relaxation of a union of two bodies (same dx and h) as one assembly: the
+ * forces of Eq. 15 over the particles of both (one neighbour grid over both
+ * meshes' boxes), one amax and so one dt, then each particle's own
+ * projection, a surface or feature particle reverting when it would enter
+ * the partner (apply_step_partner). */
+int oracle_union_relax(or_ctx *a, or_ctx *b, int32_t n_iter)
+{
+    if (a->h != b->h || a->dx != b->dx || a->fixed_features != b->fixed_features) return -1;
+    const int64_t n = a->n + b->n;
+    double *X = malloc(sizeof(double) * 3 * (n ? n : 1));
+    double *acc = malloc(sizeof(double) * 3 * (n ? n : 1));
+    int32_t *cls = malloc(sizeof(int32_t) * (n ? n : 1));
+    or_ctx g = *a;   /* a's parameters, the union's neighbour grid and particles */
+    float bbmin[3] = {INFINITY, INFINITY, INFINITY}, bbmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const or_ctx *m[2] = {a, b};
+    for (int q = 0; q < 2; q++)
+        for (int64_t i = 0; i < m[q]->nv; i++)
+            for (int k = 0; k < 3; k++) {
+                bbmin[k] = fminf(bbmin[k], m[q]->Vf[3 * i + k]);
+                bbmax[k] = fmaxf(bbmax[k], m[q]->Vf[3 * i + k]);
+            }
+    grid_setup(bbmin, bbmax, a->ng_cell, 1.0, 1, g.ng_o, &g.ng_inv, g.ng_n);
+    for (int32_t it = 0; it < n_iter; it++) {
+        memcpy(X, a->X, sizeof(double) * 3 * a->n);
+        memcpy(X + 3 * a->n, b->X, sizeof(double) * 3 * b->n);
+        memcpy(cls, a->cls, sizeof(int32_t) * a->n);
+        memcpy(cls + a->n, b->cls, sizeof(int32_t) * b->n);
+        g.X = X;
+        g.cls = cls;
+        g.n = n;
+        double amax = compute_forces(&g, X, acc, NULL);
+        a->last_amax = b->last_amax = amax;
+        apply_step_partner(a, acc, amax, b);
+        apply_step_partner(b, acc + 3 * a->n, amax, a);
+    }
+    free(X);
+    free(acc);
+    free(cls);
     return 0;
 }
 

@@ -507,6 +507,48 @@ def batch_workload(seed: int = 3, bodies: int = 64, dx: float = 0.008) -> list[A
     return out
 
 
+def union_pair_workload(seed: int = 5, dx: float = 0.05) -> list[Assembly]:
+    """Two overlapping bodies for the Boolean union (Sec. 3.2.3): the unit
+    cube [-0.5, 0.5]^3 (lattice particles as config 1, 30 degree features)
+    and an icosphere of level 3, r = 0.35, centred at (0.45, 0.05, -0.03)
+    (Fibonacci surface points and a volume lattice), so that the sphere pokes
+    out of the cube's +x face.  meta["union_with"] names the partner."""
+    dxf = float(np.float32(dx))
+    cv, ct = cube_mesh()
+    cx, cc = cube_particles(dx, seed)
+    sv, st = icosphere_mesh(3, 0.35)
+    sx, sc = sphere_particles(dx, seed + 1, radius=0.35)
+    centre = np.array([0.45, 0.05, -0.03])
+    sv = (sv.astype(np.float64) + centre).astype(np.float32)
+    sx = (sx.astype(np.float64) + centre).astype(np.float32)
+    return [Assembly("cube", cv, ct, dxf, smoothing_length(dx), cx, cc, 30.0, {"n_iter": 100, "union_with": 1}),
+            Assembly("sphere", sv, st, dxf, smoothing_length(dx), sx, sc, None, {"n_iter": 100, "union_with": 0})]
+
+
+def batch_union_workload(seed: int = 3, bodies: int = 64, dx: float = 0.008) -> list[Assembly]:
+    """Config 4 with its Boolean unions: the 64 bodies of batch_workload,
+    except that the body after each gear becomes a shaft through that gear
+    (a cylinder of radius 0.2 and height 0.5 at the gear's scale, through the
+    bore of radius 0.15, so it overlaps the hub and sticks out on both
+    sides); each gear-shaft pair is one union (meta["union_with"])."""
+    out = batch_workload(seed, bodies, dx)
+    shaft_v, shaft_t = cylinder_mesh(0.2, 0.5, 48, 6)
+    b = 0
+    while b < len(out) - 1:
+        a = out[b]
+        if a.name.startswith("gear"):
+            scale = a.meta["scale"]
+            out[b + 1] = Assembly(f"shaft{b + 1}", (shaft_v.astype(np.float64) * scale).astype(np.float32), shaft_t,
+                                  a.dx, a.h, None, None, 30.0,
+                                  {"n_iter": 50, "scale": scale, "union_with": b,
+                                   "generate": dict(a.meta["generate"])})
+            a.meta["union_with"] = b + 1
+            b += 2
+        else:
+            b += 1
+    return out
+
+
 # --------------------------------------------------------------------------
 # vehicle-like shell (union of rounded boxes and wheels)
 # --------------------------------------------------------------------------
