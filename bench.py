@@ -327,10 +327,16 @@ def main():
             reset_bodies()
         vb = nb * G * kb / (sum(ms_bb[1:]) / 1e3)
         vp = nb * G * kb / (sum(ms_bp[1:]) / 1e3)
+        bb.time_force(True)
+        bb.load()
+        bb.relax(G, use_graph=True)
+        bphases = bb.phase_ms()
+        bb.time_force(False)
         extras["batch64"] = {"workload": "64 bodies (cubes, cylinders, icospheres, gears; scales 0.1-1), dx=0.008",
                              "particles": nb, "iterations_per_step": G, "steps": kb, "warmup": 1,
                              "batched_graph": vb, "plain": vp, "batched_over_plain": vb / vp,
                              "unit": "particle-iterations/s", "autotune": btuned,
+                             "phase_ms_per_iteration": bphases,
                              "launches_per_iteration": {"batched": bb.kernels_per_iter,
                                                         "plain": bb.kernels_per_iter * len(bbodies)}}
         bb.close()

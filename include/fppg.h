@@ -148,6 +148,26 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
  * Errors: FPPG_ERR_STATE without particles, FPPG_ERR_ARG for n other than
  * the particle count or an id out of range for the particle's class. */
 int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n);
+/* Boolean union of two bodies (Sec. 3.2.3 and Fig. 10: bodies united
+ * through their cell sets, a cell interior to either being interior to the
+ * union).  Reading on particles: every particle of a that lies inside b,
+ * and every surface, feature or singular particle of b that lies inside a,
+ * is dropped (the volume and innermost particles of b stay, so the overlap
+ * keeps one copy of its volume particles); "inside" is the ray parity of
+ * Fig. 6 against the other mesh (+z ray, FP64, from the particle displaced
+ * by (1.234567e-6, 2.345678e-6) dx in x, y so that it meets no edge).  The two bodies become
+ * partners: they relax only inside one batch (fppg_batch_create with both),
+ * as one assembly — one neighbour grid over both boxes, so their particles
+ * repel each other, and one time step — and a surface or feature particle
+ * whose projection would lie inside its partner (closest-feature sign of
+ * the partner's triangles within the 27 triangle cells) reverts.  The
+ * intersection curve gets no feature particles.  *n_a, *n_b (nullable)
+ * receive the particle counts left.  Errors: FPPG_ERR_ARG for the same
+ * handle twice, different dx / h / feature setting, or a mesh that is not
+ * closed and consistently oriented; FPPG_ERR_STATE without particles or
+ * when a body is already in a union.  fppg_relax on a partner afterwards
+ * returns FPPG_ERR_STATE. */
+int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b);
 /* Positions, classes and constraint ids (triangle for S, feature segment for
  * F, -1 otherwise) into caller buffers of capacity cap (each nullable);
  * *n_out receives the particle count.  Synchronises the stream. */
@@ -262,14 +282,15 @@ const char *fppg_batch_last_error(const fppg_batch *b);
 /* Phase timing of the graph form: fppg_batch_time_force(b, 1) puts CUDA
  * event records into the captured graph (dropping a graph captured
  * without them) around each iteration's grid build (A1-A3), force pass
- * (A4) and step + projection (A5-A6).  After a graph replay of
- * fppg_batch_relax, fppg_batch_phase_ms gives the device time of each
- * phase averaged over the graph's iterations (outputs nullable) and
+ * (A4), step (A5, with the projections that need no search) and triangle
+ * search (A6).  After a graph replay of fppg_batch_relax,
+ * fppg_batch_phase_ms writes the device ms of the four phases, averaged
+ * over the graph's iterations, into ms4[4] (in that order) and
  * fppg_batch_force_ms the force pass alone; FPPG_ERR_STATE when timing is
  * off or no graph has been captured.  Both synchronise the batch stream. */
 int fppg_batch_time_force(fppg_batch *b, int32_t enable);
 int fppg_batch_force_ms(fppg_batch *b, double *ms);
-int fppg_batch_phase_ms(fppg_batch *b, double *grid_ms, double *force_ms, double *project_ms);
+int fppg_batch_phase_ms(fppg_batch *b, double *ms4);
 
 /* ---- allocation-free force pass ---------------------------------------------
  * fppg_forces_static: the neighbour grid and the force pass (A1-A4) for one

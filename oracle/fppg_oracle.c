@@ -1475,8 +1475,18 @@ int oracle_relax(or_ctx *c, int32_t n_iter)
  * volume_stays = 0 for the first body, 1 for the second. */
 void oracle_union_keep(const or_ctx *self, const or_ctx *other, int volume_stays, int32_t *keep)
 {
+    /* the ray starts at the particle displaced by (1.234567e-6, 2.345678e-6) dx
+     * in x, y (as in the generation), so that it meets no edge or vertex of
+     * the other mesh exactly (a ray through an edge would cross both faces) */
     int32_t *inside = malloc(sizeof(int32_t) * (self->n ? self->n : 1));
-    oracle_ray_parity(other, self->X, self->n, inside);
+    double *q = malloc(sizeof(double) * 3 * (self->n ? self->n : 1));
+    for (int64_t i = 0; i < self->n; i++) {
+        q[3 * i] = self->X[3 * i] + 1.234567e-6 * (double)other->dx;
+        q[3 * i + 1] = self->X[3 * i + 1] + 2.345678e-6 * (double)other->dx;
+        q[3 * i + 2] = self->X[3 * i + 2];
+    }
+    oracle_ray_parity(other, q, self->n, inside);
+    free(q);
     for (int64_t i = 0; i < self->n; i++) {
         int vol = self->cls[i] == OR_V || self->cls[i] == OR_I;
         keep[i] = !inside[i] || (volume_stays && vol);

@@ -90,7 +90,8 @@ def lib():
                 "fppg_batch_force_ms": [vp, P_(f64)],
                 "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(f64)],
                 "fppg_batch_configure": [vp, i32, i32, i32],
-                "fppg_batch_phase_ms": [vp, P_(f64), P_(f64), P_(f64)],
+                "fppg_union": [vp, vp, P_(i64), P_(i64)],
+                "fppg_batch_phase_ms": [vp, P_(f64)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -309,6 +310,19 @@ class Body:
         self._chk(lib().fppg_copy_positions_dev(self._h, C.c_void_p(ptr)))
 
 
+def union(a: "Body", b: "Body") -> tuple[int, int]:
+    """Boolean union of bodies a and b (fppg_union): drops the particles of
+    a inside b and the surface / feature / singular particles of b inside a;
+    the two then relax together in one Batch.  Returns the counts left."""
+    na, nb_ = C.c_int64(), C.c_int64()
+    r = lib().fppg_union(a.handle, b.handle, C.byref(na), C.byref(nb_))
+    if r != OK:
+        msg = lib().fppg_last_error(a.handle) or lib().fppg_last_error(None)
+        raise FPPGError(r, msg.decode() if isinstance(msg, bytes) else str(msg))
+    a.n, b.n = na.value, nb_.value
+    return na.value, nb_.value
+
+
 class Batch:
     """Many bodies relaxed by one launch per phase (``fppg_batch_*``)."""
 
@@ -378,11 +392,11 @@ class Batch:
         self._chk(lib().fppg_batch_configure(self._h, int(force_variant), int(force_block), int(search_ctas_per_sm)))
 
     def phase_ms(self) -> dict:
-        """Device ms per iteration of grid build, force pass and step +
-        projection, from the last graph replay with timing enabled."""
-        a, b, c = C.c_double(), C.c_double(), C.c_double()
-        self._chk(lib().fppg_batch_phase_ms(self._h, C.byref(a), C.byref(b), C.byref(c)))
-        return {"grid": a.value, "force": b.value, "project": c.value}
+        """Device ms per iteration of grid build, force pass, step and
+        triangle search, from the last graph replay with timing enabled."""
+        ms = np.zeros(4, np.float64)
+        self._chk(lib().fppg_batch_phase_ms(self._h, ms.ctypes.data_as(C.POINTER(C.c_double))))
+        return {"grid": float(ms[0]), "force": float(ms[1]), "step": float(ms[2]), "search": float(ms[3])}
 
     def force_ms(self) -> float:
         ms = C.c_double()

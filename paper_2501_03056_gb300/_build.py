@@ -30,6 +30,7 @@ UNITS = {
     "api.cu": [],
     "noalloc.cu": [],
     "mapping.cu": ["-fmad=false"],
+    "union.cu": ["-fmad=false"],
 }
 
 

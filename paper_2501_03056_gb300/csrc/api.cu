@@ -24,6 +24,7 @@ struct fppg_ctx {
     bool has_particles = false;
     int fixed_features = 0;
     std::vector<int32_t> cls_host;
+    fppg_ctx *partner = nullptr;   // Boolean-union partner (fppg_union)
 };
 
 struct fppg_batch {
@@ -137,6 +138,7 @@ int fppg_create(const float *verts_host, int64_t nv, const int32_t *tris_host, i
 int fppg_destroy(fppg_ctx *ctx) {
     if (!ctx) return FPPG_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->partner) ctx->partner->partner = nullptr;
     delete ctx;
     return FPPG_OK;
 }
@@ -249,6 +251,57 @@ int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n) {
     return FPPG_OK;
 }
 
+int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
+    if (!a || !b || a == b) return fail_global(FPPG_ERR_ARG, "fppg_union needs two different bodies");
+    if (!a->has_particles || !b->has_particles) return fail(a->err, FPPG_ERR_STATE, "no particles set");
+    if (a->partner || b->partner) return fail(a->err, FPPG_ERR_STATE, "a body is already in a union");
+    if (a->body.dx != b->body.dx || a->body.h != b->body.h || a->fixed_features != b->fixed_features)
+        return fail(a->err, FPPG_ERR_ARG, "union members need the same dx, h and feature setting");
+    if (!a->body.closed || !b->body.closed)
+        return fail(a->err, FPPG_ERR_ARG, "union members need closed, consistently oriented meshes");
+    cudaStream_t s = a->stream;
+    CUDA_OR(a->err, cudaStreamSynchronize(b->stream));
+    int32_t *in = nullptr;
+    const int64_t na = a->n, nbp = b->n;
+    CUDA_OR(a->err, cudaMalloc(&in, sizeof(int32_t) * (size_t)std::max<int64_t>(na + nbp, 1)));
+    ray_parity(b->group, a->group.d.pos, na, in, s);
+    ray_parity(a->group, b->group.d.pos, nbp, in + na, s);
+    std::vector<int32_t> inside((size_t)(na + nbp));
+    if (na + nbp > 0)
+        CUDA_OR(a->err, cudaMemcpyAsync(inside.data(), in, sizeof(int32_t) * (na + nbp), cudaMemcpyDeviceToHost, s));
+    CUDA_OR(a->err, cudaStreamSynchronize(s));
+    cudaFree(in);
+    // keep rule: every particle of a inside b goes; of b inside a, the
+    // surface, feature and singular ones go, the volume and innermost ones
+    // stay (the overlap keeps one copy of its volume particles)
+    fppg_ctx *m[2] = {a, b};
+    for (int q = 0; q < 2; q++) {
+        fppg_ctx *c = m[q];
+        const int64_t n = c->n, base = q == 0 ? 0 : na;
+        std::vector<float> xyz(3 * (size_t)std::max<int64_t>(n, 1));
+        std::vector<int32_t> cls((size_t)std::max<int64_t>(n, 1)), cons((size_t)std::max<int64_t>(n, 1));
+        int r = fppg_get_particles(c, xyz.data(), cls.data(), cons.data(), n, nullptr);
+        if (r) return r;
+        std::vector<float> kx;
+        std::vector<int32_t> kc, kk;
+        for (int64_t i = 0; i < n; i++) {
+            const bool vol = cls[i] == FPPG_V || cls[i] == FPPG_I;
+            if (inside[base + i] && !(q == 1 && vol)) continue;
+            kx.insert(kx.end(), &xyz[3 * i], &xyz[3 * i] + 3);
+            kc.push_back(cls[i]);
+            kk.push_back(cons[i]);
+        }
+        r = fppg_set_particles(c, kx.data(), kc.data(), (int64_t)kc.size());
+        if (!r) r = fppg_set_constraints(c, kk.data(), (int64_t)kk.size());
+        if (r) return r;
+    }
+    a->partner = b;
+    b->partner = a;
+    if (n_a) *n_a = a->n;
+    if (n_b) *n_b = b->n;
+    return FPPG_OK;
+}
+
 int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_t *cons_host, int64_t cap,
                        int64_t *n_out) {
     if (!ctx) return FPPG_ERR_ARG;
@@ -275,6 +328,8 @@ static int relax_impl(fppg_ctx *ctx, int32_t n_iter, bool energy_mode) {
     if (!ctx) return FPPG_ERR_ARG;
     if (n_iter < 0) return fail(ctx->err, FPPG_ERR_ARG, "n_iter < 0");
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    if (ctx->partner)
+        return fail(ctx->err, FPPG_ERR_STATE, "a union member relaxes in a batch together with its partner");
     for (int32_t it = 0; it < n_iter; it++) iterate(ctx->group, ctx->stream, energy_mode);
     CUDA_OR(ctx->err, cudaGetLastError());
     return FPPG_OK;
@@ -468,11 +523,50 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     g.owns_mesh = true;
     DevGroup &d = g.d;
     d.B = n;
+    // Boolean-union partners share one neighbour grid over both boxes and
+    // one time step
+    std::vector<int> partner(n, -1);
+    for (int32_t i = 0; i < n; i++) {
+        if (!ctxs[i]->partner) continue;
+        for (int32_t j = 0; j < n; j++)
+            if (ctxs[j] == ctxs[i]->partner) partner[i] = j;
+        if (partner[i] < 0) {
+            delete b;
+            return fail_global(FPPG_ERR_STATE, "a union member needs its partner in the same batch");
+        }
+    }
     int64_t N = 0, cells = 0, nt = 0, nv = 0, hs = 0, nc = 0, np = 0, ns = 0, nl = 0, ow = 0;
     for (int32_t i = 0; i < n; i++) {
         const fppg_ctx *c = ctxs[i];
         const Body &bd = c->body;
         AsmParams A = make_params(bd, (uint32_t)cells, (int)N, (int)(N + c->n), c->fixed_features);
+        A.amax_slot = i;
+        const int j = partner[i];
+        int64_t grid_cells = (int64_t)bd.ng_n[0] * bd.ng_n[1] * bd.ng_n[2];
+        if (j >= 0 && j < i) {
+            const AsmParams &Q = g.hp[j];
+            for (int k = 0; k < 3; k++) {
+                A.ng_o[k] = Q.ng_o[k];
+                A.ng_n[k] = Q.ng_n[k];
+            }
+            A.ng_inv = Q.ng_inv;
+            A.key_base = Q.key_base;
+            grid_cells = 0;
+        } else if (j > i) {
+            const Body &pb = ctxs[j]->body;
+            float lo[3], hi[3];
+            for (int k = 0; k < 3; k++) {
+                lo[k] = std::min(bd.bbmin[k], pb.bbmin[k]);
+                hi[k] = std::max(bd.bbmax[k], pb.bbmax[k]);
+            }
+            grid_setup(lo, hi, bd.ng_cell, 1.0, 1, A.ng_o, &A.ng_inv, A.ng_n);
+            grid_cells = (int64_t)A.ng_n[0] * A.ng_n[1] * A.ng_n[2];
+        }
+        if (j >= 0) {
+            A.partner = j;
+            A.amax_slot = std::min(i, j);
+            A.slab_r2 = slab_reach2(A.R2, A.ng_inv);
+        }
         A.tri_off = (int)nt;
         A.vert_off = (int)nv;
         A.hash_off = (uint32_t)hs;
@@ -485,7 +579,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         g.hp.push_back(A);
         b->off.push_back(N);
         N += c->n;
-        cells += (int64_t)bd.ng_n[0] * bd.ng_n[1] * bd.ng_n[2];
+        cells += grid_cells;
         nt += bd.nt;
         nv += bd.nv;
         hs += bd.hash_size;
@@ -581,7 +675,7 @@ static int build_graph(fppg_batch *b) {
     if (g.graph_iters <= 0) g.graph_iters = 50;
     if (!g.graph_stream) CUDA_OR(b->err, cudaStreamCreateWithFlags(&g.graph_stream, cudaStreamNonBlocking));
     if (g.time_force) {
-        while ((int)g.ev.size() < 4 * g.graph_iters) {
+        while ((int)g.ev.size() < kPhaseEvents * g.graph_iters) {
             cudaEvent_t e;
             CUDA_OR(b->err, cudaEventCreate(&e));
             g.ev.push_back(e);
@@ -619,28 +713,29 @@ int fppg_batch_relax(fppg_batch *b, int32_t n_iter, int32_t use_graph) {
     return FPPG_OK;
 }
 
-int fppg_batch_phase_ms(fppg_batch *b, double *grid_ms, double *force_ms, double *project_ms) {
-    if (!b) return FPPG_ERR_ARG;
+int fppg_batch_phase_ms(fppg_batch *b, double *ms4) {
+    if (!b || !ms4) return FPPG_ERR_ARG;
     Group &g = b->group;
-    if (!g.time_force || !g.graph || (int)g.ev.size() < 4 * g.graph_iters)
+    if (!g.time_force || !g.graph || (int)g.ev.size() < kPhaseEvents * g.graph_iters)
         return fail(b->err, FPPG_ERR_STATE, "phase timing not active");
     CUDA_OR(b->err, cudaStreamSynchronize(b->stream));
-    double tot[3] = {0.0, 0.0, 0.0};
+    double tot[kPhaseEvents - 1] = {};
     for (int i = 0; i < g.graph_iters; i++)
-        for (int k = 0; k < 3; k++) {
+        for (int k = 0; k + 1 < kPhaseEvents; k++) {
             float t = 0.f;
-            CUDA_OR(b->err, cudaEventElapsedTime(&t, g.ev[4 * i + k], g.ev[4 * i + k + 1]));
+            CUDA_OR(b->err, cudaEventElapsedTime(&t, g.ev[kPhaseEvents * i + k], g.ev[kPhaseEvents * i + k + 1]));
             tot[k] += t;
         }
-    if (grid_ms) *grid_ms = tot[0] / g.graph_iters;
-    if (force_ms) *force_ms = tot[1] / g.graph_iters;
-    if (project_ms) *project_ms = tot[2] / g.graph_iters;
+    for (int k = 0; k + 1 < kPhaseEvents; k++) ms4[k] = tot[k] / g.graph_iters;
     return FPPG_OK;
 }
 
 int fppg_batch_force_ms(fppg_batch *b, double *ms) {
     if (!b || !ms) return FPPG_ERR_ARG;
-    return fppg_batch_phase_ms(b, nullptr, ms, nullptr);
+    double ph[kPhaseEvents - 1];
+    const int r = fppg_batch_phase_ms(b, ph);
+    if (r == FPPG_OK) *ms = ph[1];
+    return r;
 }
 
 int fppg_batch_store(fppg_batch *b) {

@@ -181,6 +181,8 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.dx = b.dx;
     A.edge_tol = b.edge_tol;
     A.closed = b.closed ? 1 : 0;
+    A.partner = -1;
+    A.amax_slot = 0;
     A.w0[0] = (float)lattice_w0((double)b.dx, h, 2);
     A.w0[1] = (float)lattice_w0((double)b.dx, h, 3);
     A.w0[2] = (float)lattice_w0((double)b.dx, h, 1);

@@ -21,6 +21,7 @@ struct Body {
     float ng_inv = 0, ng_cell = 0, R2 = 0;
     float edge_tol = 0;  // 2^-20 of the largest bounding-box extent
     bool closed = false; // every edge has two faces of opposite direction, none degenerate
+    float bbmin[3] = {0, 0, 0}, bbmax[3] = {0, 0, 0};   // bounding box of the vertices
     int ng_n[3] = {0, 0, 0};
     // device mesh
     float *d_verts = nullptr;
@@ -85,6 +86,8 @@ struct Group {
     ~Group() { free_all(); }
 };
 
+// event records per timed iteration: before A1, after A3, A4, A5 and A6
+constexpr int kPhaseEvents = 5;
 // one relaxation iteration of every body of the group (A1-A6)
 void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg = nullptr);
 // A1-A3 only (keys, sort, gather + cell ranges); returns the buffer index
@@ -109,6 +112,9 @@ int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, d
 // initial particles of Sec. 3.2 into the group (features, surface, volume)
 int map_particles(Group &g, Body &b, int surface, int volume, int features, int band_cells, int inner_cells,
                   cudaStream_t s, int64_t *n_out, std::vector<int32_t> &cls_host, std::string &err);
+// Boolean union: inside[i] (device) = ray parity (Fig. 6, FP64) of point i
+// against body 0 of group `other`
+void ray_parity(const Group &other, const float4 *pos, int64_t n, int32_t *inside, cudaStream_t s);
 // energy and gradients (positions y, vertex coordinates verts of body 0)
 int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
            cudaStream_t s, std::string &err);

@@ -130,9 +130,10 @@ __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, 
         out_s[k] = make_float4(gx, gy, gz, mag);
     }
     if (amax) {
-        uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const int slot = A.amax_slot;
+        uint32_t peers = __match_any_sync(0xffffffffu, slot);
         uint32_t m = __reduce_max_sync(peers, __float_as_uint(mag));
-        if ((uint32_t)(__ffs(peers) - 1) == (threadIdx.x & 31u)) atomicMax(amax + b, m);
+        if ((uint32_t)(__ffs(peers) - 1) == (threadIdx.x & 31u)) atomicMax(amax + slot, m);
     }
 }
 

@@ -82,6 +82,8 @@ struct AsmParams {
     float alpha;       // alpha_3
     float edge_tol;    // a foot this close outside a triangle edge still counts as inside
     int closed;        // closed, consistently oriented mesh: inside certificates apply
+    int partner;       // Boolean-union partner (body index in the group) or -1
+    int amax_slot;     // body whose amax / time step this body shares (itself, or its union partner)
     int p_begin, p_end;
 };
 
@@ -257,6 +259,33 @@ __device__ inline void row_slots(const AsmParams &A, const uint4 *__restrict__ c
         s = min(s, cs);
         e = max(e, ce);
     }
+}
+
+// ---- triangle grid -------------------------------------------------------
+// C_compact entry of triangle cell (x, y, z) through the Eq. 10 hash:
+// [beg, beg + len) in the triangle list; false for a cell without triangles
+__device__ inline bool tri_cell(const MeshView &M, const AsmParams &A, int x, int y, int z, uint32_t &beg,
+                                uint32_t &len) {
+    const uint32_t h = (kHashP1 * (uint32_t)x + kHashP2 * (uint32_t)y + kHashP3 * (uint32_t)z) & A.hash_mask;
+    const uint2 r = M.hrng[A.hash_off + h];
+    const uint32_t key = (uint32_t)x + (uint32_t)A.tg_n[0] * ((uint32_t)y + (uint32_t)A.tg_n[1] * (uint32_t)z);
+    for (uint32_t e = r.x; e < r.x + r.y; e++) {
+        const uint4 c = M.compact[A.compact_off + e];
+        if (c.x == key) {
+            beg = A.tlist_off + c.y;
+            len = c.z;
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ inline bool test_bit(const uint32_t *m, uint32_t off, uint32_t c) {
+    return (m[off + (c >> 5)] >> (c & 31u)) & 1u;
+}
+
+__device__ inline uint32_t tri_key(const AsmParams &A, int x, int y, int z) {
+    return (uint32_t)x + (uint32_t)A.tg_n[0] * ((uint32_t)y + (uint32_t)A.tg_n[1] * (uint32_t)z);
 }
 
 // FP32 squared distance (dx dx + dy dy) + dz dz without contraction

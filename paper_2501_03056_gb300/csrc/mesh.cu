@@ -363,6 +363,10 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
         for (int k = 0; k < 3; k++) ext = std::max(ext, (double)bbmax[k] - (double)bbmin[k]);
         edge_tol = (float)std::ldexp(ext, -20);
     }
+    for (int k = 0; k < 3; k++) {
+        this->bbmin[k] = bbmin[k];
+        this->bbmax[k] = bbmax[k];
+    }
     grid_setup(bbmin, bbmax, dx, 2.5, 2, tg_o, &tg_inv, tg_n);
     float R = 2.0f * h;
     R2 = (float)((double)R * (double)R);

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(TPB, 5)
         count_s[k] = acc.cnt;
         if (tested_s) tested_s[k] = mob ? tested : 0;
     }
-    labelled_max(amax, b, mag);
+    labelled_max(amax, A.amax_slot, mag);
 }
 
 // Masked neighbour count (self excluded) and the number of candidates in the
@@ -299,29 +299,6 @@ __global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s,
 }
 
 // ---- A6 helpers -------------------------------------------------------------
-__device__ inline bool tri_cell(const MeshView &M, const AsmParams &A, int x, int y, int z, uint32_t &beg,
-                                uint32_t &len) {
-    const uint32_t h = (kHashP1 * (uint32_t)x + kHashP2 * (uint32_t)y + kHashP3 * (uint32_t)z) & A.hash_mask;
-    const uint2 r = M.hrng[A.hash_off + h];
-    const uint32_t key = (uint32_t)x + (uint32_t)A.tg_n[0] * ((uint32_t)y + (uint32_t)A.tg_n[1] * (uint32_t)z);
-    for (uint32_t e = r.x; e < r.x + r.y; e++) {
-        const uint4 c = M.compact[A.compact_off + e];
-        if (c.x == key) {
-            beg = A.tlist_off + c.y;
-            len = c.z;
-            return true;
-        }
-    }
-    return false;
-}
-
-__device__ inline bool test_bit(const uint32_t *m, uint32_t off, uint32_t c) {
-    return (m[off + (c >> 5)] >> (c & 31u)) & 1u;
-}
-
-__device__ inline uint32_t tri_key(const AsmParams &A, int x, int y, int z) {
-    return (uint32_t)x + (uint32_t)A.tg_n[0] * ((uint32_t)y + (uint32_t)A.tg_n[1] * (uint32_t)z);
-}
 
 // closest point on a triangle by barycentric regions (Ericson, Real-Time
 // Collision Detection, 2005); region 0 face, 1 + k edge (v_k, v_k+1),
@@ -488,9 +465,12 @@ __device__ inline float block_margin(const AsmParams &A, float3 y) {
 }
 
 // Volume test (reading: closest point over the 27 triangle cells, sign of
-// the angle-weighted pseudonormal; none in range: accept).  *clear gets a
-// lower bound of the distance from y to the surface, valid when inside.
-__device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear) {
+// the angle-weighted pseudonormal; none in range: `none_inside`, true for a
+// volume particle of the body, false for the test against a union
+// partner).  *clear gets a lower bound of the distance from y to the
+// surface, valid when inside.
+__device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear,
+                                   bool none_inside) {
     const int lane = threadIdx.x & 31;
     const CellRange r = lane_cell(M, A, y, lane);
     float best = FLT_MAX;
@@ -516,7 +496,7 @@ __device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3
     warp_argmin(v, t);
     const float blk = block_margin(A, y);
     clear = fmaxf(fminf(t == 0x7fffffff ? FLT_MAX : sqrtf(v), blk) * (1.f - 0x1p-10f) - A.dx * 0x1p-16f, 0.f);
-    if (t == 0x7fffffff) return true;
+    if (t == 0x7fffffff) return none_inside;
     const uint32_t own = __ballot_sync(0xffffffffu, bt == t && best == v);
     const int src = __ffs(own) - 1;
     int inside = 0;
@@ -585,7 +565,7 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
     float3 y = f3(p);
     if (active && is_mobile(cls, A)) {
         const uint32_t i = id_s[k];
-        const float am = __uint_as_float(amax[b]);
+        const float am = __uint_as_float(amax[A.amax_slot]);
         const float sc = am > 0.f ? A.step_h / am : 0.f;     // dt^2 with dt = 0.25 sqrt(h / amax)
         const float4 a = acc_s[k];
         float3 dr = make_float3(a.x * sc, a.y * sc, a.z * sc);
@@ -603,10 +583,24 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             float3 x;
             int cn;
             if (project_feature(M, A, y, c, x, cn)) {
-                pos[i] = make_float4(x.x, x.y, x.z, p.w);
-                cons[i] = cn;
-                const float3 w = x - p3;
-                disp = sqrtf(dot3(w, w));
+                bool near_partner = false;
+                if (A.partner >= 0) {
+                    // the partner's triangles within reach: the search tests
+                    // whether the projection entered the partner
+                    const AsmParams &Q = P[A.partner];
+                    near_partner = test_bit(M.occ, Q.dil_off,
+                                            tri_key(Q, cell_coord(x.x, Q.tg_o[0], Q.tg_inv, Q.tg_n[0]),
+                                                    cell_coord(x.y, Q.tg_o[1], Q.tg_inv, Q.tg_n[1]),
+                                                    cell_coord(x.z, Q.tg_o[2], Q.tg_inv, Q.tg_n[2])));
+                }
+                if (near_partner) {
+                    queue = true;
+                } else {
+                    pos[i] = make_float4(x.x, x.y, x.z, p.w);
+                    cons[i] = cn;
+                    const float3 w = x - p3;
+                    disp = sqrtf(dot3(w, w));
+                }
             }
         } else {
             const int cx = cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]);
@@ -674,8 +668,23 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             tri = warp_project_surface(M, A, y, d, buf);
             ok = tri >= 0;
             if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
+        } else if (cls == kClsF) {
+            // a feature particle of a union member near the partner: its
+            // projection again, then the partner test below
+            int cn = -1, okf = 0;
+            if (lane == 0) okf = project_feature(M, A, y, cons[id_s[it.x]], x, cn) ? 1 : 0;
+            okf = __shfl_sync(0xffffffffu, okf, 0);
+            x = make_float3(__shfl_sync(0xffffffffu, x.x, 0), __shfl_sync(0xffffffffu, x.y, 0),
+                            __shfl_sync(0xffffffffu, x.z, 0));
+            tri = __shfl_sync(0xffffffffu, cn, 0);
+            ok = okf != 0;
         } else {
-            ok = warp_volume_inside(M, A, y, buf, clear);
+            ok = warp_volume_inside(M, A, y, buf, clear, true);
+        }
+        // Boolean union: a surface or feature particle does not enter its partner
+        if (ok && A.partner >= 0 && (cls == kClsS || cls == kClsF)) {
+            float unused;
+            ok = !warp_volume_inside(M, P[A.partner], x, buf, unused, false);
         }
         if (ok && lane == 0) {
             const uint32_t i = id_s[it.x];
@@ -729,7 +738,7 @@ __global__ void k_project_points(const float *__restrict__ y, const int32_t *__r
         }
     } else if (cl == kClsV) {
         float clear;
-        r = warp_volume_inside(M, A, yy, buf, clear);
+        r = warp_volume_inside(M, A, yy, buf, clear, true);
     } else if (cl == kClsF) {
         r = project_feature(M, A, yy, c, xx, cn);
     }
@@ -851,8 +860,8 @@ void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s, int32_t
 void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     DevGroup &d = g.d;
     if (d.N == 0) return;
-    // phase timing: events before A1, after A3, after A4 and after A6
-    const bool timed = g.time_force && g.ev_used + 4 <= (int)g.ev.size();
+    // phase timing: events before A1, after A3, after A4, after A5 and after A6
+    const bool timed = g.time_force && g.ev_used + kPhaseEvents <= (int)g.ev.size();
     // inside a stream capture the records must be external so that they
     // become event-record nodes whose timestamps can be read after a replay
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -866,11 +875,12 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 2], s, flags);
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
                                          d.maxdisp, d.work, d.work_count, d.cert);
+    if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
     k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp, d.work,
                                              d.work_count, d.cert);
     if (timed) {
-        cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
-        g.ev_used += 4;
+        cudaEventRecordWithFlags(g.ev[g.ev_used + 4], s, flags);
+        g.ev_used += kPhaseEvents;
     }
 }
 

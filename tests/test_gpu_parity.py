@@ -335,7 +335,7 @@ def test_phase_timing_of_the_graph_form():
     bt.time_force(True)
     bt.relax(8, use_graph=True)
     ph = bt.phase_ms()
-    assert all(v > 0 for v in (ph["grid"], ph["force"], ph["project"])), ph
+    assert all(v > 0 for v in (ph["grid"], ph["force"], ph["step"], ph["search"])), ph
     assert bt.force_ms() == ph["force"]
     bt.store()
     for p in plain:

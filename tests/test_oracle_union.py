@@ -81,3 +81,19 @@ def test_union_with_a_far_partner_relaxes_as_the_body_alone():
     alone.relax(3)
     assert np.array_equal(oa.get_particles()[0], alone.get_particles()[0])
     assert np.array_equal(ob.get_particles()[0], far.astype(np.float32).astype(np.float64))
+
+
+def test_union_keep_on_rays_through_mesh_edges():
+    # points straight below the cap's fan edges of a 48-gon cylinder: an
+    # undisplaced +z ray would cross both faces of each edge (even parity)
+    v, t = W.cylinder_mesh(0.2, 0.5, 48, 6)
+    dx, h = 0.01, 0.013
+    cyl = O.Oracle(v, t, dx, h)
+    ang = np.arange(48) * 2 * np.pi / 48
+    r = np.repeat([0.1, 0.3], 48)
+    pts = np.stack([r * np.cos(np.tile(ang, 2)), r * np.sin(np.tile(ang, 2)), np.zeros(96)], 1)
+    bv, bt = W.cube_mesh(0.5)
+    box = O.Oracle(bv, bt, dx, h)
+    box.set_particles(pts.astype(np.float32), np.full(96, W.CLS_S, np.int32))
+    keep = box.union_keep(cyl, volume_stays=False)
+    assert np.array_equal(keep, r > 0.2)
