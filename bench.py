@@ -290,9 +290,17 @@ def main():
         extras["e2e"] = {"value": n * world * G * K / e2e_s, "unit": "particle-iterations/s",
                          "h2d_bytes_per_step": int(n * 16), "d2h_bytes_per_step": int(n * 12)}
 
-        # ---- 64 bodies of uneven size: batched + graph against plain ---------
-        basm = W.batch_workload(seed=3 + 10 * rank)
+        # ---- 64 bodies of uneven size with gear-shaft unions: batched + graph
+        # against plain (single bodies one by one, each union as a 2-body
+        # batch, no graph) ------------------------------------------------------
+        basm = W.batch_union_workload(seed=3 + 10 * rank)
         bbodies = [pkg.Body.from_assembly(a, stream=stream) for a in basm]
+        upairs = [(i, a.meta["union_with"]) for i, a in enumerate(basm) if a.meta.get("union_with", -1) > i]
+        for i, j in upairs:
+            pkg.union(bbodies[i], bbodies[j])
+        in_pair = {k for p in upairs for k in p}
+        singles = [b for k, b in enumerate(bbodies) if k not in in_pair]
+        pair_batches = [pkg.Batch([bbodies[i], bbodies[j]], stream=stream) for i, j in upairs]
         nb = sum(b.n for b in bbodies)
         snap = [b.get_particles() for b in bbodies]
 
@@ -316,11 +324,15 @@ def main():
             torch.cuda.synchronize()
             ms_bb.append(s_.elapsed_time(e_))
             reset_bodies()
+            for pb in pair_batches:
+                pb.load()
             flush.zero_()
             s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s_.record(stream)
-            for b in bbodies:
+            for b in singles:
                 b.relax(G)
+            for pb in pair_batches:
+                pb.relax(G, use_graph=False)
             e_.record(stream)
             torch.cuda.synchronize()
             ms_bp.append(s_.elapsed_time(e_))
@@ -332,14 +344,18 @@ def main():
         bb.relax(G, use_graph=True)
         bphases = bb.phase_ms()
         bb.time_force(False)
-        extras["batch64"] = {"workload": "64 bodies (cubes, cylinders, icospheres, gears; scales 0.1-1), dx=0.008",
+        extras["batch64"] = {"workload": "64 bodies (cubes, cylinders, icospheres, gears; scales 0.1-1), dx=0.008, "
+                                         f"{len(upairs)} gear-shaft Boolean unions",
                              "particles": nb, "iterations_per_step": G, "steps": kb, "warmup": 1,
                              "batched_graph": vb, "plain": vp, "batched_over_plain": vb / vp,
                              "unit": "particle-iterations/s", "autotune": btuned,
                              "phase_ms_per_iteration": bphases,
                              "launches_per_iteration": {"batched": bb.kernels_per_iter,
-                                                        "plain": bb.kernels_per_iter * len(bbodies)}}
+                                                        "plain": bb.kernels_per_iter * (len(singles) +
+                                                                                        len(pair_batches))}}
         bb.close()
+        for pb in pair_batches:
+            pb.close()
 
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
