@@ -148,25 +148,40 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
  * Errors: FPPG_ERR_STATE without particles, FPPG_ERR_ARG for n other than
  * the particle count or an id out of range for the particle's class. */
 int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n);
-/* Boolean union of two bodies (Sec. 3.2.3 and Fig. 10: bodies united
- * through their cell sets, a cell interior to either being interior to the
- * union).  Reading on particles: every particle of a that lies inside b,
- * and every surface, feature or singular particle of b that lies inside a,
- * is dropped (the volume and innermost particles of b stay, so the overlap
- * keeps one copy of its volume particles); "inside" is the ray parity of
- * Fig. 6 against the other mesh (+z ray, FP64, from the particle displaced
- * by (1.234567e-6, 2.345678e-6) dx in x, y so that it meets no edge).  The two bodies become
- * partners: they relax only inside one batch (fppg_batch_create with both),
- * as one assembly — one neighbour grid over both boxes, so their particles
- * repel each other, and one time step — and a surface or feature particle
- * whose projection would lie inside its partner (closest-feature sign of
- * the partner's triangles within the 27 triangle cells) reverts.  The
- * intersection curve gets no feature particles.  *n_a, *n_b (nullable)
- * receive the particle counts left.  Errors: FPPG_ERR_ARG for the same
- * handle twice, different dx / h / feature setting, or a mesh that is not
- * closed and consistently oriented; FPPG_ERR_STATE without particles or
- * when a body is already in a union.  fppg_relax on a partner afterwards
- * returns FPPG_ERR_STATE. */
+/* Boolean operations on two bodies (Sec. 3.2.3 and Fig. 10: bodies combined
+ * through their cell sets, by interval union, difference and intersection).
+ * Reading on particles, with "inside" = the ray parity of Fig. 6 against
+ * the other mesh (+z ray, FP64, from the particle displaced by
+ * (1.234567e-6, 2.345678e-6) dx in x, y so that it meets no edge) and
+ * "volume" = volume or innermost particle:
+ *   FPPG_UNION         a keeps what is outside b; b keeps what is outside a
+ *                      and its volume particles (one copy of the overlap);
+ *   FPPG_DIFFERENCE    a - b: a keeps what is outside b; b keeps its
+ *                      surface, feature and singular particles inside a
+ *                      (the wall of the cavity);
+ *   FPPG_INTERSECTION  a keeps what is inside b; b keeps its surface,
+ *                      feature and singular particles inside a.
+ * The two bodies become partners: they relax only inside one batch
+ * (fppg_batch_create with both) as one assembly — one neighbour grid over
+ * both boxes, so their particles repel each other, and one time step — and
+ * a projected position must keep to the operation's side of the partner
+ * (closest-feature sign of the partner's triangles within the 27 triangle
+ * cells; none in range: the particle is where it started), else the
+ * particle reverts: surface and feature particles of a union stay outside
+ * the partner, of a difference outside b (a's) or inside a (b's, the
+ * cavity wall), of an intersection inside the partner; volume particles of
+ * a difference also stay outside b, of an intersection inside b.  The
+ * curve where the surfaces meet gets no feature particles.  *n_a, *n_b
+ * (nullable) receive the particle counts left.  Errors: FPPG_ERR_ARG for
+ * the same handle twice, an unknown op, different dx / h / feature
+ * setting, or a mesh that is not closed and consistently oriented;
+ * FPPG_ERR_STATE without particles or when a body is already an operand.
+ * fppg_relax on an operand afterwards returns FPPG_ERR_STATE.
+ * fppg_union(a, b, ...) = fppg_boolean(a, b, FPPG_UNION, ...). */
+#define FPPG_UNION 0
+#define FPPG_DIFFERENCE 1
+#define FPPG_INTERSECTION 2
+int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_b);
 int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b);
 /* Positions, classes and constraint ids (triangle for S, feature segment for
  * F, -1 otherwise) into caller buffers of capacity cap (each nullable);

@@ -77,8 +77,8 @@ def lib():
                 "oracle_volume_inside": (None, [vp, P(f32), i64, P(i32)]),
                 "oracle_ray_parity": (None, [vp, P(f64), i64, P(i32)]),
                 "oracle_relax": (C.c_int, [vp, i32]),
-                "oracle_union_keep": (None, [vp, vp, C.c_int, P(i32)]),
-                "oracle_union_relax": (C.c_int, [vp, vp, i32]),
+                "oracle_boolean_keep": (None, [vp, vp, C.c_int, C.c_int, P(i32)]),
+                "oracle_boolean_relax": (C.c_int, [vp, vp, C.c_int, i32]),
                 "oracle_relax_energy": (C.c_int, [vp, i32]),
                 "oracle_last_iteration": (None, [vp, P(f64), P(f64), P(i64)]),
                 "oracle_w0": (None, [vp, P(f64)]),
@@ -289,13 +289,17 @@ class Oracle:
     def relax(self, n_iter):
         lib().oracle_relax(self._c, int(n_iter))
 
-    def union_keep(self, other: "Oracle", volume_stays: bool) -> np.ndarray:
-        """Which of this body's particles stay in its Boolean union with
-        `other` (dropped: inside `other` by ray parity, unless volume_stays
-        and the particle is a volume or innermost one)."""
+    def boolean_keep(self, other: "Oracle", op: int, first: bool) -> np.ndarray:
+        """Which of this body's particles stay in Boolean operation `op`
+        (0 union, 1 difference first - second, 2 intersection) with `other`;
+        `first` says whether this body is the first operand."""
         keep = np.zeros(max(self.n, 1), np.int32)
-        lib().oracle_union_keep(self._c, other._c, int(bool(volume_stays)), _p(keep, C.c_int32))
+        lib().oracle_boolean_keep(self._c, other._c, int(op), int(bool(first)), _p(keep, C.c_int32))
         return keep[:self.n].astype(bool)
+
+    def union_keep(self, other: "Oracle", volume_stays: bool) -> np.ndarray:
+        """boolean_keep for the union: volume_stays marks the second body."""
+        return self.boolean_keep(other, 0, not volume_stays)
 
     def relax_energy(self, n_iter):
         lib().oracle_relax_energy(self._c, int(n_iter))
@@ -336,12 +340,18 @@ class Oracle:
         return dict(zip(STATS_KEYS, out.tolist()))
 
 
+UNION, DIFFERENCE, INTERSECTION = 0, 1, 2
+
+
+def boolean_relax(a: Oracle, b: Oracle, op: int, n_iter: int):
+    """Relax the result of Boolean operation `op` on bodies a (first) and b
+    as one assembly (shared forces and time step, partner rules of `op`)."""
+    if lib().oracle_boolean_relax(a._c, b._c, int(op), int(n_iter)) != 0:
+        raise ValueError("Boolean members need the same dx, h and feature setting")
+
+
 def union_relax(a: Oracle, b: Oracle, n_iter: int):
-    """Relax the Boolean union of bodies a and b as one assembly (shared
-    forces and time step; surface and feature particles kept out of the
-    partner)."""
-    if lib().oracle_union_relax(a._c, b._c, int(n_iter)) != 0:
-        raise ValueError("union members need the same dx, h and feature setting")
+    boolean_relax(a, b, UNION, n_iter)
 
 
 def keep_rows(o: Oracle, keep: np.ndarray):

@@ -1385,16 +1385,28 @@ void oracle_ray_parity(const or_ctx *c, const double *p, int64_t n, int32_t *ins
  * reset); dr = v_{n+1} dt (Eq. 23); tangential part only for surface
  * (triangle normal) and feature (segment direction) particles; then the
  * projection of the trial point, or revert. */
-static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner);
+static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner, int surf_rule,
+                               int vol_rule);
 
-static void apply_step(or_ctx *c, const double *acc, double amax) { apply_step_partner(c, acc, amax, NULL); }
+static void apply_step(or_ctx *c, const double *acc, double amax) { apply_step_partner(c, acc, amax, NULL, 0, 0); }
 
-/* With a union partner (see oracle_union_relax), a surface or feature
- * particle whose projected position lies inside the partner reverts: a
- * partner triangle within the 27 cells and the closest-feature sign inside
- * (no partner triangle near: outside, as the particle started outside the
- * partner and moves less than a cell per iteration). */
-static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner)
+/* With a Boolean partner (see oracle_boolean_relax), a projected position
+ * must also respect the partner: rule 1 = stay outside it, rule 2 = stay
+ * inside it, 0 = no rule; surf_rule for surface and feature particles,
+ * vol_rule for volume particles.  The partner test is the closest-feature
+ * sign of the partner's triangles within the 27 cells; with none near, a
+ * particle is where it started (it moves less than a cell per iteration)
+ * and the rule holds. */
+static int partner_ok(const or_ctx *partner, int rule, const double *x)
+{
+    if (!partner || rule == 0) return 1;
+    float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
+    int t = closest_sign_inside(partner, xf);
+    return rule == 1 ? t != 1 : t != 0;
+}
+
+static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner, int surf_rule,
+                               int vol_rule)
 {
     double dt = amax > 0.0 ? 0.25 * sqrt((double)c->h / amax) : 0.0;
     double *Xn = malloc(sizeof(double) * 3 * (c->n ? c->n : 1));
@@ -1428,10 +1440,8 @@ static void apply_step_partner(or_ctx *c, const double *acc, double amax, const 
         double xn[3];
         int32_t cn;
         int ok = project_point(c, cl, y, cs, xn, &cn);
-        if (ok && partner && (cl == OR_S || cl == OR_F)) {
-            float xf[3] = {(float)xn[0], (float)xn[1], (float)xn[2]};
-            if (closest_sign_inside(partner, xf) == 1) ok = 0;
-        }
+        if (ok && (cl == OR_S || cl == OR_F)) ok = partner_ok(partner, surf_rule, xn);
+        if (ok && cl == OR_V) ok = partner_ok(partner, vol_rule, xn);
         if (ok) {
             memcpy(Xn + 3 * i, xn, sizeof(xn));
             Cn[i] = cn;
@@ -1464,16 +1474,24 @@ int oracle_relax(or_ctx *c, int32_t n_iter)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Boolean union of two bodies (Sec. 3.2.3, Fig. 10)                         */
+/* Boolean operations on two bodies (Sec. 3.2.3, Fig. 10)                    */
 /* ------------------------------------------------------------------------ */
-/* The paper unites two bodies through their cell sets: a cell interior to
- * either is interior to the union.  Reading, on particles: the particles of
- * one body that lie inside the other (ray parity of Fig. 6 against the
- * other's mesh) are dropped, except that the volume and innermost particles
- * of the second body stay, so that the overlap keeps one copy of its
- * volume particles.  keep[i] = 1 for the particles of `self` that stay;
- * volume_stays = 0 for the first body, 1 for the second. */
-void oracle_union_keep(const or_ctx *self, const or_ctx *other, int volume_stays, int32_t *keep)
+/* The paper combines two bodies through their cell sets (interval union,
+ * difference and intersection of C_compact).  Reading, on particles, with
+ * "inside" = ray parity of Fig. 6 against the other mesh and "volume" =
+ * volume or innermost class:
+ *   op 0, union A + B:        A keeps what is outside B; B keeps what is
+ *                             outside A and its volume particles (the
+ *                             overlap keeps one copy of them).
+ *   op 1, difference A - B:   A keeps what is outside B; B keeps its
+ *                             surface, feature and singular particles
+ *                             inside A (the wall of the cavity).
+ *   op 2, intersection A * B: A keeps what is inside B; B keeps its
+ *                             surface, feature and singular particles
+ *                             inside A.
+ * first = 1 for A, 0 for B.  keep[i] = 1 for the particles of self that
+ * stay. */
+void oracle_boolean_keep(const or_ctx *self, const or_ctx *other, int op, int first, int32_t *keep)
 {
     /* the ray starts at the particle displaced by (1.234567e-6, 2.345678e-6) dx
      * in x, y (as in the generation), so that it meets no edge or vertex of
@@ -1489,24 +1507,43 @@ void oracle_union_keep(const or_ctx *self, const or_ctx *other, int volume_stays
     free(q);
     for (int64_t i = 0; i < self->n; i++) {
         int vol = self->cls[i] == OR_V || self->cls[i] == OR_I;
-        keep[i] = !inside[i] || (volume_stays && vol);
+        int in = inside[i];
+        if (op == 0) keep[i] = first ? !in : (!in || vol);
+        else if (op == 1) keep[i] = first ? !in : (in && !vol);
+        else keep[i] = first ? in : (in && !vol);
     }
     free(inside);
 }
 
-/* Relaxation of a union of two bodies (same dx and h) as one assembly: the
- * forces of Eq. 15 over the particles of both (one neighbour grid over both
- * meshes' boxes), one amax and so one dt, then each particle's own
- * projection, a surface or feature particle reverting when it would enter
- * the partner (apply_step_partner). */
-int oracle_union_relax(or_ctx *a, or_ctx *b, int32_t n_iter)
+/* partner rules of each operation for the first (A) and second (B) body:
+ * surface / feature particles, then volume particles (1 outside, 2 inside) */
+static void boolean_rules(int op, int first, int *surf, int *vol)
 {
-    if (a->h != b->h || a->dx != b->dx || a->fixed_features != b->fixed_features) return -1;
+    if (op == 0) {
+        *surf = 1;
+        *vol = 0;
+    } else if (op == 1) {
+        *surf = first ? 1 : 2;
+        *vol = first ? 1 : 0;
+    } else {
+        *surf = 2;
+        *vol = first ? 2 : 0;
+    }
+}
+
+/* Relaxation of the result of a Boolean operation on two bodies (same dx
+ * and h) as one assembly: the forces of Eq. 15 over the particles of both
+ * (one neighbour grid over both meshes' boxes), one amax and so one dt,
+ * then each particle's own projection, subject to the partner rules of the
+ * operation (apply_step_partner). */
+int oracle_boolean_relax(or_ctx *a, or_ctx *b, int op, int32_t n_iter)
+{
+    if (a->h != b->h || a->dx != b->dx || a->fixed_features != b->fixed_features || op < 0 || op > 2) return -1;
     const int64_t n = a->n + b->n;
     double *X = malloc(sizeof(double) * 3 * (n ? n : 1));
     double *acc = malloc(sizeof(double) * 3 * (n ? n : 1));
     int32_t *cls = malloc(sizeof(int32_t) * (n ? n : 1));
-    or_ctx g = *a;   /* a's parameters, the union's neighbour grid and particles */
+    or_ctx g = *a;   /* a's parameters, the pair's neighbour grid and particles */
     float bbmin[3] = {INFINITY, INFINITY, INFINITY}, bbmax[3] = {-INFINITY, -INFINITY, -INFINITY};
     const or_ctx *m[2] = {a, b};
     for (int q = 0; q < 2; q++)
@@ -1516,6 +1553,9 @@ int oracle_union_relax(or_ctx *a, or_ctx *b, int32_t n_iter)
                 bbmax[k] = fmaxf(bbmax[k], m[q]->Vf[3 * i + k]);
             }
     grid_setup(bbmin, bbmax, a->ng_cell, 1.0, 1, g.ng_o, &g.ng_inv, g.ng_n);
+    int sa, va, sb, vb;
+    boolean_rules(op, 1, &sa, &va);
+    boolean_rules(op, 0, &sb, &vb);
     for (int32_t it = 0; it < n_iter; it++) {
         memcpy(X, a->X, sizeof(double) * 3 * a->n);
         memcpy(X + 3 * a->n, b->X, sizeof(double) * 3 * b->n);
@@ -1526,8 +1566,8 @@ int oracle_union_relax(or_ctx *a, or_ctx *b, int32_t n_iter)
         g.n = n;
         double amax = compute_forces(&g, X, acc, NULL);
         a->last_amax = b->last_amax = amax;
-        apply_step_partner(a, acc, amax, b);
-        apply_step_partner(b, acc + 3 * a->n, amax, a);
+        apply_step_partner(a, acc, amax, b, sa, va);
+        apply_step_partner(b, acc + 3 * a->n, amax, a, sb, vb);
     }
     free(X);
     free(acc);

@@ -91,6 +91,7 @@ def lib():
                 "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(f64)],
                 "fppg_batch_configure": [vp, i32, i32, i32],
                 "fppg_union": [vp, vp, P_(i64), P_(i64)],
+                "fppg_boolean": [vp, vp, i32, P_(i64), P_(i64)],
                 "fppg_batch_phase_ms": [vp, P_(f64)],
             }
             for name, args in sig.items():
@@ -310,17 +311,26 @@ class Body:
         self._chk(lib().fppg_copy_positions_dev(self._h, C.c_void_p(ptr)))
 
 
-def union(a: "Body", b: "Body") -> tuple[int, int]:
-    """Boolean union of bodies a and b (fppg_union): drops the particles of
-    a inside b and the surface / feature / singular particles of b inside a;
-    the two then relax together in one Batch.  Returns the counts left."""
+UNION, DIFFERENCE, INTERSECTION = 0, 1, 2
+
+
+def boolean(a: "Body", b: "Body", op: int) -> tuple[int, int]:
+    """Boolean operation `op` (UNION, DIFFERENCE a - b, INTERSECTION) on
+    bodies a and b (fppg_boolean): drops the particles the operation
+    removes; the two then relax together in one Batch.  Returns the counts
+    left."""
     na, nb_ = C.c_int64(), C.c_int64()
-    r = lib().fppg_union(a.handle, b.handle, C.byref(na), C.byref(nb_))
+    r = lib().fppg_boolean(a.handle, b.handle, int(op), C.byref(na), C.byref(nb_))
     if r != OK:
         msg = lib().fppg_last_error(a.handle) or lib().fppg_last_error(None)
         raise FPPGError(r, msg.decode() if isinstance(msg, bytes) else str(msg))
     a.n, b.n = na.value, nb_.value
     return na.value, nb_.value
+
+
+def union(a: "Body", b: "Body") -> tuple[int, int]:
+    """Boolean union of bodies a and b (see boolean)."""
+    return boolean(a, b, UNION)
 
 
 class Batch:

@@ -24,7 +24,9 @@ struct fppg_ctx {
     bool has_particles = false;
     int fixed_features = 0;
     std::vector<int32_t> cls_host;
-    fppg_ctx *partner = nullptr;   // Boolean-union partner (fppg_union)
+    fppg_ctx *partner = nullptr;   // Boolean partner (fppg_boolean)
+    int bool_op = 0;               // FPPG_UNION, FPPG_DIFFERENCE or FPPG_INTERSECTION
+    bool bool_first = false;       // the first operand of the operation
 };
 
 struct fppg_batch {
@@ -251,14 +253,16 @@ int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n) {
     return FPPG_OK;
 }
 
-int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
-    if (!a || !b || a == b) return fail_global(FPPG_ERR_ARG, "fppg_union needs two different bodies");
+int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_b) {
+    if (!a || !b || a == b) return fail_global(FPPG_ERR_ARG, "a Boolean operation needs two different bodies");
+    if (op != FPPG_UNION && op != FPPG_DIFFERENCE && op != FPPG_INTERSECTION)
+        return fail(a->err, FPPG_ERR_ARG, "unknown Boolean operation");
     if (!a->has_particles || !b->has_particles) return fail(a->err, FPPG_ERR_STATE, "no particles set");
-    if (a->partner || b->partner) return fail(a->err, FPPG_ERR_STATE, "a body is already in a union");
+    if (a->partner || b->partner) return fail(a->err, FPPG_ERR_STATE, "a body is already in a Boolean operation");
     if (a->body.dx != b->body.dx || a->body.h != b->body.h || a->fixed_features != b->fixed_features)
-        return fail(a->err, FPPG_ERR_ARG, "union members need the same dx, h and feature setting");
+        return fail(a->err, FPPG_ERR_ARG, "Boolean operands need the same dx, h and feature setting");
     if (!a->body.closed || !b->body.closed)
-        return fail(a->err, FPPG_ERR_ARG, "union members need closed, consistently oriented meshes");
+        return fail(a->err, FPPG_ERR_ARG, "Boolean operands need closed, consistently oriented meshes");
     cudaStream_t s = a->stream;
     CUDA_OR(a->err, cudaStreamSynchronize(b->stream));
     int32_t *in = nullptr;
@@ -271,9 +275,11 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
         CUDA_OR(a->err, cudaMemcpyAsync(inside.data(), in, sizeof(int32_t) * (na + nbp), cudaMemcpyDeviceToHost, s));
     CUDA_OR(a->err, cudaStreamSynchronize(s));
     cudaFree(in);
-    // keep rule: every particle of a inside b goes; of b inside a, the
-    // surface, feature and singular ones go, the volume and innermost ones
-    // stay (the overlap keeps one copy of its volume particles)
+    // keep rules (inside = ray parity against the other body; vol = volume
+    // or innermost): union a keeps !inside, b keeps !inside || vol (the
+    // overlap keeps one copy of its volume particles); difference a - b: a
+    // keeps !inside, b keeps inside && !vol (the cavity wall); intersection:
+    // a keeps inside, b keeps inside && !vol
     fppg_ctx *m[2] = {a, b};
     for (int q = 0; q < 2; q++) {
         fppg_ctx *c = m[q];
@@ -285,8 +291,11 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
         std::vector<float> kx;
         std::vector<int32_t> kc, kk;
         for (int64_t i = 0; i < n; i++) {
-            const bool vol = cls[i] == FPPG_V || cls[i] == FPPG_I;
-            if (inside[base + i] && !(q == 1 && vol)) continue;
+            const bool vol = cls[i] == FPPG_V || cls[i] == FPPG_I, in = inside[base + i] != 0;
+            const bool keep = op == FPPG_UNION ? (q == 0 ? !in : (!in || vol))
+                                               : op == FPPG_DIFFERENCE ? (q == 0 ? !in : (in && !vol))
+                                                                       : (q == 0 ? in : (in && !vol));
+            if (!keep) continue;
             kx.insert(kx.end(), &xyz[3 * i], &xyz[3 * i] + 3);
             kc.push_back(cls[i]);
             kk.push_back(cons[i]);
@@ -297,9 +306,16 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
     }
     a->partner = b;
     b->partner = a;
+    a->bool_op = b->bool_op = op;
+    a->bool_first = true;
+    b->bool_first = false;
     if (n_a) *n_a = a->n;
     if (n_b) *n_b = b->n;
     return FPPG_OK;
+}
+
+int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
+    return fppg_boolean(a, b, FPPG_UNION, n_a, n_b);
 }
 
 int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_t *cons_host, int64_t cap,
@@ -329,7 +345,7 @@ static int relax_impl(fppg_ctx *ctx, int32_t n_iter, bool energy_mode) {
     if (n_iter < 0) return fail(ctx->err, FPPG_ERR_ARG, "n_iter < 0");
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
     if (ctx->partner)
-        return fail(ctx->err, FPPG_ERR_STATE, "a union member relaxes in a batch together with its partner");
+        return fail(ctx->err, FPPG_ERR_STATE, "a Boolean operand relaxes in a batch together with its partner");
     for (int32_t it = 0; it < n_iter; it++) iterate(ctx->group, ctx->stream, energy_mode);
     CUDA_OR(ctx->err, cudaGetLastError());
     return FPPG_OK;
@@ -532,7 +548,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
             if (ctxs[j] == ctxs[i]->partner) partner[i] = j;
         if (partner[i] < 0) {
             delete b;
-            return fail_global(FPPG_ERR_STATE, "a union member needs its partner in the same batch");
+            return fail_global(FPPG_ERR_STATE, "a Boolean operand needs its partner in the same batch");
         }
     }
     int64_t N = 0, cells = 0, nt = 0, nv = 0, hs = 0, nc = 0, np = 0, ns = 0, nl = 0, ow = 0;
@@ -563,7 +579,13 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
             grid_cells = (int64_t)A.ng_n[0] * A.ng_n[1] * A.ng_n[2];
         }
         if (j >= 0) {
+            // partner rules (1 stay outside, 2 stay inside): surface and
+            // feature particles, then volume particles
+            const int op = c->bool_op;
+            const bool first = c->bool_first;
             A.partner = j;
+            A.partner_surf = op == FPPG_UNION ? 1 : op == FPPG_DIFFERENCE ? (first ? 1 : 2) : 2;
+            A.partner_vol = op == FPPG_UNION ? 0 : op == FPPG_DIFFERENCE ? (first ? 1 : 0) : (first ? 2 : 0);
             A.amax_slot = std::min(i, j);
             A.slab_r2 = slab_reach2(A.R2, A.ng_inv);
         }

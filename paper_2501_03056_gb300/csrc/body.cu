@@ -182,6 +182,8 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.edge_tol = b.edge_tol;
     A.closed = b.closed ? 1 : 0;
     A.partner = -1;
+    A.partner_surf = 0;
+    A.partner_vol = 0;
     A.amax_slot = 0;
     A.w0[0] = (float)lattice_w0((double)b.dx, h, 2);
     A.w0[1] = (float)lattice_w0((double)b.dx, h, 3);

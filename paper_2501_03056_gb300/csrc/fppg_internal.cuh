@@ -82,8 +82,10 @@ struct AsmParams {
     float alpha;       // alpha_3
     float edge_tol;    // a foot this close outside a triangle edge still counts as inside
     int closed;        // closed, consistently oriented mesh: inside certificates apply
-    int partner;       // Boolean-union partner (body index in the group) or -1
-    int amax_slot;     // body whose amax / time step this body shares (itself, or its union partner)
+    int partner;       // Boolean partner (body index in the group) or -1
+    int partner_surf;  // rule for surface / feature particles: 0 none, 1 stay outside the partner, 2 inside
+    int partner_vol;   // the same for volume particles
+    int amax_slot;     // body whose amax / time step this body shares (itself, or its Boolean partner)
     int p_begin, p_end;
 };
 

@@ -464,13 +464,11 @@ __device__ inline float block_margin(const AsmParams &A, float3 y) {
     return fmaxf(m, 0.f) / A.tg_inv;
 }
 
-// Volume test (reading: closest point over the 27 triangle cells, sign of
-// the angle-weighted pseudonormal; none in range: `none_inside`, true for a
-// volume particle of the body, false for the test against a union
-// partner).  *clear gets a lower bound of the distance from y to the
-// surface, valid when inside.
-__device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear,
-                                   bool none_inside) {
+// Closest-feature sign (reading: closest point over the 27 triangle cells,
+// sign of the angle-weighted pseudonormal): 1 inside, 0 outside, -1 when no
+// triangle lies in range.  *clear gets a lower bound of the distance from y
+// to the surface, valid when inside.
+__device__ int warp_closest_sign(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear) {
     const int lane = threadIdx.x & 31;
     const CellRange r = lane_cell(M, A, y, lane);
     float best = FLT_MAX;
@@ -496,7 +494,7 @@ __device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3
     warp_argmin(v, t);
     const float blk = block_margin(A, y);
     clear = fmaxf(fminf(t == 0x7fffffff ? FLT_MAX : sqrtf(v), blk) * (1.f - 0x1p-10f) - A.dx * 0x1p-16f, 0.f);
-    if (t == 0x7fffffff) return none_inside;
+    if (t == 0x7fffffff) return -1;
     const uint32_t own = __ballot_sync(0xffffffffu, bt == t && best == v);
     const int src = __ffs(own) - 1;
     int inside = 0;
@@ -505,7 +503,23 @@ __device__ bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3
         const float3 psi = breg == 0 ? f3(M.geo[5 * g + 1]) : f3(M.pn[6 * g + breg - 1]);
         inside = dot3(y - bcp, psi) <= 0.f;
     }
-    return __shfl_sync(0xffffffffu, inside, src) != 0;
+    return __shfl_sync(0xffffffffu, inside, src);
+}
+
+// Volume test of a particle of the body: the closest-feature sign, inside
+// when no triangle is in range (a step is below a cell)
+__device__ inline bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf,
+                                          float &clear) {
+    return warp_closest_sign(M, A, y, buf, clear) != 0;
+}
+
+// Boolean partner rule (1 stay outside, 2 stay inside, 0 none) for point x:
+// with no partner triangle in range the particle is where it started
+__device__ inline bool warp_partner_ok(const MeshView &M, const AsmParams &Q, int rule, float3 x, int32_t *buf) {
+    if (rule == 0) return true;
+    float unused;
+    const int t = warp_closest_sign(M, Q, x, buf, unused);
+    return rule == 1 ? t != 1 : t != 0;
 }
 
 // closest point of the particle's feature line (all lines of the body when
@@ -584,9 +598,9 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             int cn;
             if (project_feature(M, A, y, c, x, cn)) {
                 bool near_partner = false;
-                if (A.partner >= 0) {
+                if (A.partner >= 0 && A.partner_surf != 0) {
                     // the partner's triangles within reach: the search tests
-                    // whether the projection entered the partner
+                    // the partner rule on the projection
                     const AsmParams &Q = P[A.partner];
                     near_partner = test_bit(M.occ, Q.dil_off,
                                             tri_key(Q, cell_coord(x.x, Q.tg_o[0], Q.tg_inv, Q.tg_n[0]),
@@ -607,7 +621,14 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             const int cy = cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]);
             const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
             bool certified = false;
-            if (cls == kClsV && A.closed) {
+            bool near_partner = false;
+            if (cls == kClsV && A.partner >= 0 && A.partner_vol != 0) {
+                const AsmParams &Q = P[A.partner];
+                near_partner = test_bit(M.occ, Q.dil_off,
+                                        tri_key(Q, cell_coord(y.x, Q.tg_o[0], Q.tg_inv, Q.tg_n[0]),
+                                                cell_coord(y.y, Q.tg_o[1], Q.tg_inv, Q.tg_n[1]),
+                                                cell_coord(y.z, Q.tg_o[2], Q.tg_inv, Q.tg_n[2])));
+            } else if (cls == kClsV && A.closed) {
                 // inside a ball that an earlier search found free of surface
                 // and inside the body: the volume test would accept
                 const float4 cc = cert[i];
@@ -617,7 +638,7 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             if (certified) {
                 pos[i] = make_float4(y.x, y.y, y.z, p.w);
                 disp = sqrtf(dot3(dr, dr));
-            } else if (test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
+            } else if (near_partner || test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
                 queue = true;
             } else if (cls == kClsV) {       // nothing near: inside, accept
                 pos[i] = make_float4(y.x, y.y, y.z, p.w);
@@ -679,18 +700,16 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             tri = __shfl_sync(0xffffffffu, cn, 0);
             ok = okf != 0;
         } else {
-            ok = warp_volume_inside(M, A, y, buf, clear, true);
+            ok = warp_volume_inside(M, A, y, buf, clear);
         }
-        // Boolean union: a surface or feature particle does not enter its partner
-        if (ok && A.partner >= 0 && (cls == kClsS || cls == kClsF)) {
-            float unused;
-            ok = !warp_volume_inside(M, P[A.partner], x, buf, unused, false);
-        }
+        // Boolean operations: the partner rule of the particle's class
+        if (ok && A.partner >= 0)
+            ok = warp_partner_ok(M, P[A.partner], cls == kClsV ? A.partner_vol : A.partner_surf, x, buf);
         if (ok && lane == 0) {
             const uint32_t i = id_s[it.x];
             pos[i] = make_float4(x.x, x.y, x.z, p.w);
             if (tri >= 0) cons[i] = tri;
-            if (cls == kClsV && A.closed) cert[i] = make_float4(y.x, y.y, y.z, clear);
+            if (cls == kClsV && A.closed && A.partner_vol == 0) cert[i] = make_float4(y.x, y.y, y.z, clear);
             const float3 w = x - f3(p);
             atomicMax(maxdisp + b, __float_as_uint(sqrtf(dot3(w, w))));
         }
@@ -738,7 +757,7 @@ __global__ void k_project_points(const float *__restrict__ y, const int32_t *__r
         }
     } else if (cl == kClsV) {
         float clear;
-        r = warp_volume_inside(M, A, yy, buf, clear, true);
+        r = warp_volume_inside(M, A, yy, buf, clear);
     } else if (cl == kClsF) {
         r = project_feature(M, A, yy, c, xx, cn);
     }

@@ -149,3 +149,31 @@ def test_config4_gear_shaft_unions_at_full_size():
     for g, o, a in ((ga, oa, asm[i]), (gb, ob, asm[j])):
         err = np.abs(g.get_particles()[0].astype(np.float64) - o.get_particles()[0]).max(axis=1) / a.dx
         assert (err < 1e-4).mean() > 0.999 and err.max() < 1.3 / 16.0, (a.name, err.max())
+
+
+@pytest.mark.parametrize("op", [pkg.DIFFERENCE, pkg.INTERSECTION])
+def test_difference_and_intersection_match_the_oracle(op):
+    a, b, ga, gb, oa, ob = _pair()
+    ka, kb = oa.boolean_keep(ob, op, True), ob.boolean_keep(oa, op, False)
+    O.keep_rows(oa, ka)
+    O.keep_rows(ob, kb)
+    na, nb = pkg.boolean(ga, gb, op)
+    assert (na, nb) == (ka.sum(), kb.sum()) and na > 0 and nb > 0
+    for g, asm, k in ((ga, a, ka), (gb, b, kb)):
+        x, c, _ = g.get_particles()
+        assert np.array_equal(x, asm.xyz[k]) and np.array_equal(c, asm.cls[k])
+    bt = pkg.Batch([ga, gb])
+    bt.set_graph_iters(5)
+    bt.relax(10, use_graph=True)
+    bt.store()
+    O.boolean_relax(oa, ob, op, 10)
+    for g, o, asm in ((ga, oa, a), (gb, ob, b)):
+        err = np.abs(g.get_particles()[0].astype(np.float64) - o.get_particles()[0]).max(axis=1) / asm.dx
+        assert np.quantile(err, 0.999) < 1e-4 and err.max() < 1.3 / 16.0, (asm.name, err.max())
+    c, r_in, r_out = _sphere_frame(b)
+    xa, xb = ga.get_particles()[0], gb.get_particles()[0]
+    assert (np.abs(xb).max(axis=1) <= 0.5 + 1e-6).all()          # b's surface stays inside the cube
+    if op == pkg.DIFFERENCE:
+        assert not (np.linalg.norm(xa - c, axis=1) < r_in - 1e-6).any()
+    else:
+        assert (np.linalg.norm(xa - c, axis=1) <= r_out + 1e-6).all()

@@ -97,3 +97,54 @@ def test_union_keep_on_rays_through_mesh_edges():
     box.set_particles(pts.astype(np.float32), np.full(96, W.CLS_S, np.int32))
     keep = box.union_keep(cyl, volume_stays=False)
     assert np.array_equal(keep, r > 0.2)
+
+
+def _classes(o):
+    x, c, _ = o.get_particles()
+    return x, c, np.isin(c, [W.CLS_S, W.CLS_F]), np.isin(c, [W.CLS_V, W.CLS_I])
+
+
+def test_difference_and_intersection_keep_match_the_closed_forms():
+    a, b, oa, ob = _pair()
+    c, r_in, r_out = _ball_radii(b)
+    xa, ca, _, vola = _classes(oa)
+    xb, cb, surfb, volb = _classes(ob)
+    da = np.linalg.norm(xa - c, axis=1)
+    in_cube_b = np.abs(xb).max(axis=1) < 0.5 - 1e-9
+    out_cube_b = np.abs(xb).max(axis=1) > 0.5 + 1e-9
+    sure_in, sure_out = da < r_in - 1e-9, da > r_out + 1e-9
+    # difference cube - sphere: the cube keeps what is outside the sphere,
+    # the sphere keeps only its surface inside the cube (the cavity wall)
+    ka, kb = oa.boolean_keep(ob, O.DIFFERENCE, True), ob.boolean_keep(oa, O.DIFFERENCE, False)
+    assert not ka[sure_in].any() and ka[sure_out].all()
+    assert not kb[volb].any() and kb[~volb & in_cube_b].all() and not kb[out_cube_b].any()
+    # intersection: the cube keeps what is inside the sphere, the sphere its
+    # surface inside the cube
+    ka, kb = oa.boolean_keep(ob, O.INTERSECTION, True), ob.boolean_keep(oa, O.INTERSECTION, False)
+    assert ka[sure_in].all() and not ka[sure_out].any()
+    assert not kb[volb].any() and kb[~volb & in_cube_b].all() and not kb[out_cube_b].any()
+
+
+def test_difference_relaxation_keeps_the_cavity():
+    a, b, oa, ob = _pair()
+    c, r_in, r_out = _ball_radii(b)
+    O.keep_rows(oa, oa.boolean_keep(ob, O.DIFFERENCE, True))
+    O.keep_rows(ob, ob.boolean_keep(oa, O.DIFFERENCE, False))
+    O.boolean_relax(oa, ob, O.DIFFERENCE, 5)
+    xa, _, _, _ = _classes(oa)
+    xb, _, _, _ = _classes(ob)
+    assert not (np.linalg.norm(xa - c, axis=1) < r_in - 1e-9).any()      # nothing of the cube in the cavity
+    assert (np.abs(xb).max(axis=1) <= 0.5 + 1e-9).all()                    # the wall stays inside the cube
+    assert (np.abs(xa).max(axis=1) <= 0.5 + 1e-9).all()
+
+
+def test_intersection_relaxation_stays_in_both():
+    a, b, oa, ob = _pair()
+    c, r_in, r_out = _ball_radii(b)
+    O.keep_rows(oa, oa.boolean_keep(ob, O.INTERSECTION, True))
+    O.keep_rows(ob, ob.boolean_keep(oa, O.INTERSECTION, False))
+    O.boolean_relax(oa, ob, O.INTERSECTION, 5)
+    for o in (oa, ob):
+        x = o.get_particles()[0]
+        assert (np.abs(x).max(axis=1) <= 0.5 + 1e-9).all()
+        assert (np.linalg.norm(x - c, axis=1) <= r_out + 1e-9).all()
