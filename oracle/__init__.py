@@ -56,6 +56,8 @@ def lib():
                 "oracle_set_threads": (None, [C.c_int]),
                 "oracle_get_threads": (C.c_int, []),
                 "oracle_set_fixed_features": (None, [vp, C.c_int]),
+                "oracle_set_mobile_classes": (None, [vp, C.c_int]),
+                "oracle_set_cascade": (None, [vp, C.c_int]),
                 "oracle_tri_grid": (None, [vp, P(f32), P(f32), P(i32)]),
                 "oracle_nbr_grid": (None, [vp, P(f32), P(f32), P(f32), P(i32), P(f32)]),
                 "oracle_tri_bins": (i64, [vp, P(i64), P(i32), i64]),
@@ -213,6 +215,16 @@ class Oracle:
         xyz, cls, cons = np.zeros((max(m, 1), 3)), np.zeros(max(m, 1), np.int32), np.zeros(max(m, 1), np.int32)
         lib().oracle_map_particles(self._c, *args, _p(xyz, C.c_double), _p(cls, C.c_int32), _p(cons, C.c_int32), m)
         return xyz[:m], cls[:m], cons[:m]
+
+    def set_mobile_classes(self, classes):
+        """Only these classes move (e.g. (S, F) then (V,) for the paper's
+        surface-then-volume schedule)."""
+        lib().oracle_set_mobile_classes(self._c, sum(1 << int(c) for c in classes))
+
+    def set_cascade(self, on: bool):
+        """Surface re-projection by the cascade of Sec. 3.3.3 instead of the
+        closest projectable triangle over the 27 cells."""
+        lib().oracle_set_cascade(self._c, int(bool(on)))
 
     def set_fixed_features(self, fixed: bool):
         lib().oracle_set_fixed_features(self._c, int(bool(fixed)))

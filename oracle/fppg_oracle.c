@@ -115,6 +115,8 @@ typedef struct {
     int32_t *cls;
     int32_t *cons;
     int fixed_features;
+    int mobile_mask;   /* bit c: class c may move (S, V, F; I and P never do) */
+    int cascade;       /* surface re-projection: 0 closest over 27 cells, 1 the cascade of Sec. 3.3.3 */
     double last_maxdisp;
     double last_amax;
     int64_t last_reverts;
@@ -460,6 +462,7 @@ or_ctx *oracle_create(const float *verts, int64_t nv, const int32_t *tris, int64
     c->ng_cell = (float)((double)R * (1.0 + 1.0 / 256.0));
     grid_setup(bbmin, bbmax, c->ng_cell, 1.0, 1, c->ng_o, &c->ng_inv, c->ng_n);
     c->feat_deg = -1.0;
+    c->mobile_mask = (1 << OR_S) | (1 << OR_V) | (1 << OR_F);
     return c;
 }
 
@@ -516,6 +519,16 @@ int oracle_get_threads(void)
 }
 
 void oracle_set_fixed_features(or_ctx *c, int fixed) { c->fixed_features = fixed; }
+
+/* Which classes move (bit c for class c; only S, V and F count): the
+ * paper relaxes surface particles (Algorithm 1) and then the intermediate
+ * volume particles "similarly" (Sec. 3.3.4); mask {S, F} then {V} runs
+ * that schedule, the default {S, V, F} moves all at once. */
+void oracle_set_mobile_classes(or_ctx *c, int mask) { c->mobile_mask = mask & ((1 << OR_S) | (1 << OR_V) | (1 << OR_F)); }
+
+/* Surface re-projection rule: 0 = the closest projectable triangle over the
+ * 27 cells (default), 1 = the cascade of Sec. 3.3.3 (see choose_surface). */
+void oracle_set_cascade(or_ctx *c, int on) { c->cascade = on ? 1 : 0; }
 
 void oracle_tri_grid(const or_ctx *c, float *o, float *inv, int32_t *n)
 {
@@ -826,9 +839,10 @@ void oracle_get_particles(const or_ctx *c, double *xyz, int32_t *cls, int32_t *c
 
 static int is_mobile(const or_ctx *c, int32_t cl)
 {
-    if (cl == OR_S || cl == OR_V) return 1;
-    if (cl == OR_F) return !c->fixed_features;
-    return 0;
+    int m = 0;
+    if (cl == OR_S || cl == OR_V) m = 1;
+    if (cl == OR_F) m = !c->fixed_features;
+    return m && ((c->mobile_mask >> cl) & 1);
 }
 
 /* does a particle of class cj act on one of class ci (interaction rules of
@@ -1144,6 +1158,31 @@ static int64_t choose_surface_triangle(const or_ctx *c, const double *y)
     return bt;
 }
 
+/* The re-projection cascade of Sec. 3.3.3: a particle that is still on its
+ * triangle (foot inside it) stays there; otherwise the closest projectable
+ * triangle of the cell that holds the trial point, as in the mapping of
+ * Sec. 3.2.1; otherwise the closest projectable one over the 27 cells
+ * around it; otherwise none (the particle reverts). */
+static int64_t choose_surface_cascade(const or_ctx *c, const double *y, int32_t cons_in)
+{
+    float yf[3] = {(float)y[0], (float)y[1], (float)y[2]}, d;
+    if (cons_in >= 0 && cons_in < c->nt && surface_candidate(c, cons_in, yf, &d)) return cons_in;
+    int32_t ci[3];
+    tri_cell_of(c, yf, ci);
+    int64_t key = (int64_t)ci[0] + (int64_t)c->tg_n[0] * ((int64_t)ci[1] + (int64_t)c->tg_n[1] * ci[2]);
+    float best = INFINITY;
+    int64_t bt = -1;
+    for (int64_t p = lower_bound_i64(c->pair_key, c->npairs, key); p < c->npairs && c->pair_key[p] == key; p++) {
+        int64_t t = c->pair_tri[p];
+        if (!surface_candidate(c, t, yf, &d)) continue;
+        if (d < best || (d == best && t < bt)) {
+            best = d;
+            bt = t;
+        }
+    }
+    return bt >= 0 ? bt : choose_surface_triangle(c, y);
+}
+
 /* FP32 closest point on triangle t to y; region 0 = face, 1 + k = edge k,
  * 4 + k = vertex k.  Returns the squared distance. */
 static float closest_on_triangle(const or_ctx *c, int64_t t, const float *y, float *cp, int *region)
@@ -1288,7 +1327,7 @@ static int project_point(const or_ctx *c, int32_t cl, const double *y, int32_t c
 {
     *cons_out = cons_in;
     if (cl == OR_S) {
-        int64_t t = choose_surface_triangle(c, y);
+        int64_t t = c->cascade ? choose_surface_cascade(c, y, cons_in) : choose_surface_triangle(c, y);
         if (t < 0) return 0;
         plane_foot(c, t, y, x);
         *cons_out = (int32_t)t;
@@ -1538,7 +1577,9 @@ static void boolean_rules(int op, int first, int *surf, int *vol)
  * operation (apply_step_partner). */
 int oracle_boolean_relax(or_ctx *a, or_ctx *b, int op, int32_t n_iter)
 {
-    if (a->h != b->h || a->dx != b->dx || a->fixed_features != b->fixed_features || op < 0 || op > 2) return -1;
+    if (a->h != b->h || a->dx != b->dx || a->fixed_features != b->fixed_features || a->mobile_mask != b->mobile_mask ||
+        op < 0 || op > 2)
+        return -1;
     const int64_t n = a->n + b->n;
     double *X = malloc(sizeof(double) * 3 * (n ? n : 1));
     double *acc = malloc(sizeof(double) * 3 * (n ? n : 1));
