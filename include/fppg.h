@@ -88,6 +88,24 @@ int fppg_set_stream(fppg_ctx *ctx, void *stream);
 /* Feature particles never move when fixed != 0 (paper-literal boundary
  * role of feature lines, Sec. 2.2); by default they slide along their line. */
 int fppg_set_fixed_features(fppg_ctx *ctx, int32_t fixed);
+/* Classes that move (bit 1 << class of FPPG_S, FPPG_V, FPPG_F; I and P
+ * never move); default all three, relaxed together.  The paper relaxes the
+ * surface particles (Algorithm 1) and then the intermediate volume
+ * particles "similarly" (Sec. 3.3.4): mask (1 << S) | (1 << F) for the
+ * first stage, then (1 << V).  A class that does not move still acts on
+ * the others.  Applies to fppg_relax and to batches created afterwards.
+ * Errors: FPPG_ERR_ARG for bits outside S, V, F. */
+int fppg_set_mobile_classes(fppg_ctx *ctx, int32_t mask);
+/* Surface re-projection rule (A6): FPPG_PROJECT_CLOSEST (default, reading:
+ * the closest projectable triangle over the 27 triangle cells of the trial
+ * point) or FPPG_PROJECT_CASCADE (Sec. 3.3.3's order: a particle still on
+ * its triangle stays there; else the closest projectable triangle of the
+ * trial point's own cell, as in the mapping of Sec. 3.2.1; else over the
+ * 27 cells; else revert).  Applies to fppg_relax, fppg_project_points and
+ * batches created afterwards.  Errors: FPPG_ERR_ARG for another value. */
+#define FPPG_PROJECT_CLOSEST 0
+#define FPPG_PROJECT_CASCADE 1
+int fppg_set_projection_rule(fppg_ctx *ctx, int32_t rule);
 
 /* ---- features (Sec. 3.2.2) -------------------------------------------------
  * fppg_extract_features: edge-face map with v1 < v2 keys; an edge is a
@@ -285,6 +303,9 @@ int fppg_batch_load(fppg_batch *b);
  * measured ms per iteration (0 when taken from the cache). */
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
                         double *ms_per_iter);
+/* fppg_set_mobile_classes for every body of the batch (a captured graph
+ * keeps working: the mask is read from device memory). */
+int fppg_batch_set_mobile_classes(fppg_batch *b, int32_t mask);
 /* The same choice made by hand: force variant 0 or 1, force block 128 or 256,
  * search CTAs per SM 1..64 (FPPG_ERR_ARG otherwise).  Every choice gives the
  * same bits; only the speed differs.  Drops a captured graph. */

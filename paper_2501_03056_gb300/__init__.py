@@ -90,6 +90,9 @@ def lib():
                 "fppg_batch_force_ms": [vp, P_(f64)],
                 "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(f64)],
                 "fppg_batch_configure": [vp, i32, i32, i32],
+                "fppg_set_mobile_classes": [vp, i32],
+                "fppg_set_projection_rule": [vp, i32],
+                "fppg_batch_set_mobile_classes": [vp, i32],
                 "fppg_union": [vp, vp, P_(i64), P_(i64)],
                 "fppg_boolean": [vp, vp, i32, P_(i64), P_(i64)],
                 "fppg_batch_phase_ms": [vp, P_(f64)],
@@ -183,6 +186,16 @@ class Body:
 
     def set_stream(self, stream):
         self._chk(lib().fppg_set_stream(self._h, _stream_ptr(stream)))
+
+    def set_mobile_classes(self, classes):
+        """Only these classes move (e.g. (S, F) then (V,) for the paper's
+        surface-then-volume schedule)."""
+        self._chk(lib().fppg_set_mobile_classes(self._h, sum(1 << int(c) for c in classes)))
+
+    def set_projection_rule(self, cascade: bool):
+        """Surface re-projection by the cascade of Sec. 3.3.3 (own triangle,
+        own cell, 27 cells) instead of the closest over the 27 cells."""
+        self._chk(lib().fppg_set_projection_rule(self._h, 1 if cascade else 0))
 
     def set_fixed_features(self, fixed: bool):
         self._chk(lib().fppg_set_fixed_features(self._h, int(bool(fixed))))
@@ -396,6 +409,10 @@ class Batch:
         self._chk(lib().fppg_batch_autotune(self._h, int(iters), C.byref(v), C.byref(tb), C.byref(sc), C.byref(ms)))
         return {"force_variant": v.value, "force_block": tb.value, "search_ctas_per_sm": sc.value,
                 "ms_per_iter": ms.value}
+
+    def set_mobile_classes(self, classes):
+        """Only these classes move, in every body of the batch."""
+        self._chk(lib().fppg_batch_set_mobile_classes(self._h, sum(1 << int(c) for c in classes)))
 
     def configure(self, force_variant: int = 0, force_block: int = 256, search_ctas_per_sm: int = 16):
         """Set the kernel configuration by hand (the autotuner's choices)."""

@@ -24,6 +24,8 @@ struct fppg_ctx {
     bool has_particles = false;
     int fixed_features = 0;
     std::vector<int32_t> cls_host;
+    int mobile_mask = (1 << FPPG_S) | (1 << FPPG_V) | (1 << FPPG_F);   // classes that move
+    int cascade = 0;               // surface re-projection rule (fppg_set_projection_rule)
     fppg_ctx *partner = nullptr;   // Boolean partner (fppg_boolean)
     int bool_op = 0;               // FPPG_UNION, FPPG_DIFFERENCE or FPPG_INTERSECTION
     bool bool_first = false;       // the first operand of the operation
@@ -99,6 +101,8 @@ int ctx_group(fppg_ctx *c) {
     g.d.B = 1;
     g.d.total_cells = (int64_t)c->body.ng_n[0] * c->body.ng_n[1] * c->body.ng_n[2];
     g.hp.assign(1, make_params(c->body, 0u, 0, (int)c->n, c->fixed_features));
+    g.hp[0].mobile = c->mobile_mask;
+    g.hp[0].cascade = c->cascade;
     g.mesh = view_of(c->body);
     return g.upload_params(c->stream, c->err) ? FPPG_ERR_CUDA : FPPG_OK;
 }
@@ -156,6 +160,22 @@ int fppg_set_stream(fppg_ctx *ctx, void *stream) {
 int fppg_set_fixed_features(fppg_ctx *ctx, int32_t fixed) {
     if (!ctx) return FPPG_ERR_ARG;
     ctx->fixed_features = fixed ? 1 : 0;
+    return ctx_group(ctx);
+}
+
+int fppg_set_mobile_classes(fppg_ctx *ctx, int32_t mask) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (mask & ~((1 << FPPG_S) | (1 << FPPG_V) | (1 << FPPG_F)))
+        return fail(ctx->err, FPPG_ERR_ARG, "only S, V and F can be mobile");
+    ctx->mobile_mask = mask;
+    return ctx_group(ctx);
+}
+
+int fppg_set_projection_rule(fppg_ctx *ctx, int32_t rule) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (rule != FPPG_PROJECT_CLOSEST && rule != FPPG_PROJECT_CASCADE)
+        return fail(ctx->err, FPPG_ERR_ARG, "unknown projection rule");
+    ctx->cascade = rule == FPPG_PROJECT_CASCADE ? 1 : 0;
     return ctx_group(ctx);
 }
 
@@ -557,6 +577,8 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         const Body &bd = c->body;
         AsmParams A = make_params(bd, (uint32_t)cells, (int)N, (int)(N + c->n), c->fixed_features);
         A.amax_slot = i;
+        A.mobile = c->mobile_mask;
+        A.cascade = c->cascade;
         const int j = partner[i];
         int64_t grid_cells = (int64_t)bd.ng_n[0] * bd.ng_n[1] * bd.ng_n[2];
         if (j >= 0 && j < i) {
@@ -896,6 +918,16 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     if (search_ctas) *search_ctas = best.search_ctas;
     if (ms_per_iter) *ms_per_iter = cached ? 0.0 : best_ms;
     return FPPG_OK;
+}
+
+int fppg_batch_set_mobile_classes(fppg_batch *b, int32_t mask) {
+    if (!b) return FPPG_ERR_ARG;
+    if (mask & ~((1 << FPPG_S) | (1 << FPPG_V) | (1 << FPPG_F)))
+        return fail(b->err, FPPG_ERR_ARG, "only S, V and F can be mobile");
+    for (AsmParams &A : b->group.hp) A.mobile = mask;
+    // the kernels read the parameters from device memory: a captured
+    // graph sees the new mask without being captured again
+    return b->group.upload_params(b->stream, b->err) ? FPPG_ERR_CUDA : FPPG_OK;
 }
 
 int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t search_ctas) {

@@ -181,6 +181,8 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.dx = b.dx;
     A.edge_tol = b.edge_tol;
     A.closed = b.closed ? 1 : 0;
+    A.mobile = (1 << kClsS) | (1 << kClsV) | (1 << kClsF);
+    A.cascade = 0;
     A.partner = -1;
     A.partner_surf = 0;
     A.partner_vol = 0;

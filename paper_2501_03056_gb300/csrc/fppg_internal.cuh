@@ -82,6 +82,8 @@ struct AsmParams {
     float alpha;       // alpha_3
     float edge_tol;    // a foot this close outside a triangle edge still counts as inside
     int closed;        // closed, consistently oriented mesh: inside certificates apply
+    int mobile;        // bit c: class c may move (S, V, F; I and P never do)
+    int cascade;       // surface re-projection: 0 closest over 27 cells, 1 the cascade of Sec. 3.3.3
     int partner;       // Boolean partner (body index in the group) or -1
     int partner_surf;  // rule for surface / feature particles: 0 none, 1 stay outside the partner, 2 inside
     int partner_vol;   // the same for volume particles
@@ -296,7 +298,7 @@ __device__ inline float dist2_rn(float dx, float dy, float dz) {
 }
 
 __device__ inline bool is_mobile(int cls, const AsmParams &A) {
-    return cls == kClsS || cls == kClsV || (cls == kClsF && !A.fixed_features);
+    return (cls == kClsS || cls == kClsV || (cls == kClsF && !A.fixed_features)) && ((A.mobile >> cls) & 1);
 }
 
 // ---- host side -------------------------------------------------------------

@@ -10,7 +10,7 @@
 // cudaMalloc / cudaFree may perform.  The paper has no counterpart.
 //
 // The scratch below is a plain __device__ array: every GPU that loads the
-// library holds it (about 6 MB) until the process exits.  In host code its
+// library holds it (about 8 MB) until the process exits.  In host code its
 // name is only a host-side stand-in, not a device address, so the address is
 // looked up with cudaGetSymbolAddress once per device (on the first call
 // made with that device current; make that first call before any stream
@@ -112,6 +112,9 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     A.force_scale = (float)(5.0 * (21.0 / (16.0 * M_PI * hd * hd * hd)) / (hd * hd));
     A.step_h = (float)(hd / 16.0);
     A.fixed_features = fixed_features ? 1 : 0;
+    A.mobile = (1 << kClsS) | (1 << kClsV) | (1 << kClsF);
+    A.partner = -1;
+    A.amax_slot = 0;
     A.p_end = (int)n;
 
     int dev = 0;

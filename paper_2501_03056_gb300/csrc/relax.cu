@@ -414,25 +414,38 @@ __device__ inline void for_candidates(const MeshView &M, const CellRange r, int3
     __syncwarp();
 }
 
-__device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist, int32_t *buf) {
+// Surface candidate test: the foot of y on the plane of triangle t lies
+// inside it (every in-plane edge distance >= -edge_tol: Fig. 8 with a
+// tolerance, so a foot on a shared edge belongs to both triangles); *d gets
+// the signed plane distance
+__device__ inline bool surface_candidate(const MeshView &M, const AsmParams &A, int t, float3 y, float &d) {
+    const float4 *g = M.geo + 5 * (size_t)(A.tri_off + t);
+    const float3 u = y - f3(g[0]);
+    const float tol = -A.edge_tol;
+    const float4 m0 = g[2];
+    if (dot3(u, f3(m0)) < tol) return false;
+    const float4 m1 = g[3];
+    if (dot3(u, f3(m1)) - m1.w < tol) return false;
+    const float4 m2 = g[4];
+    if (dot3(u, f3(m2)) - m2.w < tol) return false;
+    d = dot3(u, f3(g[1]));
+    return true;
+}
+
+// closest projectable triangle (smallest |plane distance|, ties to the lower
+// index) among those binned into the 27 cells around y, or into y's own
+// cell alone (own_cell); -1 when none
+__device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist, int32_t *buf,
+                                    bool own_cell = false) {
     const int lane = threadIdx.x & 31;
-    const CellRange r = lane_cell(M, A, y, lane);
+    CellRange r = lane_cell(M, A, y, lane);
+    if (own_cell && lane != 13) r = CellRange{0u, 0u};   // lane 13 holds the centre cell
     float best = FLT_MAX;
     int bt = 0x7fffffff;
     float bd = 0.f;
     for_candidates(M, r, buf, [&](int t) {
-        const float4 *g = M.geo + 5 * (size_t)(A.tri_off + t);
-        const float3 u = y - f3(g[0]);
-        // inside: every in-plane edge distance >= -edge_tol (Fig. 8 with a
-        // tolerance, so a foot on a shared edge belongs to both triangles)
-        const float tol = -A.edge_tol;
-        const float4 m0 = g[2];
-        if (dot3(u, f3(m0)) < tol) return;
-        const float4 m1 = g[3];
-        if (dot3(u, f3(m1)) - m1.w < tol) return;
-        const float4 m2 = g[4];
-        if (dot3(u, f3(m2)) - m2.w < tol) return;
-        const float d = dot3(u, f3(g[1]));
+        float d;
+        if (!surface_candidate(M, A, t, y, d)) return;
         const float ad = fabsf(d);
         if (ad < best || (ad == best && t < bt)) {
             best = ad;
@@ -447,6 +460,27 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
     const uint32_t own = __ballot_sync(0xffffffffu, bt == t && best == v);
     dist = __shfl_sync(0xffffffffu, bd, own ? __ffs(own) - 1 : 0);
     return t == 0x7fffffff ? -1 : t;
+}
+
+// Surface re-projection of trial point y of a particle on triangle c: the
+// closest projectable triangle over the 27 cells, or with A.cascade the
+// cascade of Sec. 3.3.3 (still on triangle c: stay; else the closest
+// projectable one of y's own cell; else over the 27 cells).  -1: revert.
+__device__ int warp_surface_choice(const MeshView &M, const AsmParams &A, float3 y, int c, float &dist,
+                                   int32_t *buf) {
+    if (A.cascade) {
+        if (c >= 0 && c < A.nt) {
+            float d = 0.f;
+            const bool on = surface_candidate(M, A, c, y, d);   // every lane, same answer
+            if (on) {
+                dist = d;
+                return c;
+            }
+        }
+        const int t = warp_project_surface(M, A, y, dist, buf, true);
+        if (t >= 0) return t;
+    }
+    return warp_project_surface(M, A, y, dist, buf);
 }
 
 // distance from y to the faces of the 3 x 3 x 3 triangle-cell block around
@@ -686,7 +720,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
         bool ok;
         if (cls == kClsS) {
             float d;
-            tri = warp_project_surface(M, A, y, d, buf);
+            tri = warp_surface_choice(M, A, y, A.cascade ? cons[id_s[it.x]] : -1, d, buf);
             ok = tri >= 0;
             if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
         } else if (cls == kClsF) {
@@ -749,7 +783,7 @@ __global__ void k_project_points(const float *__restrict__ y, const int32_t *__r
     const int cl = cls[i];
     if (cl == kClsS) {
         float d;
-        const int t = warp_project_surface(M, A, yy, d, buf);
+        const int t = warp_surface_choice(M, A, yy, c, d, buf);
         r = t >= 0;
         if (r) {
             xx = yy - d * f3(M.geo[5 * (size_t)(A.tri_off + t) + 1]);
