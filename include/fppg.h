@@ -253,6 +253,15 @@ int fppg_project_points(fppg_ctx *ctx, const float *y_host, const int32_t *cls_h
  * Either output may be NULL.  Synchronises. */
 int fppg_debug_search(fppg_ctx *ctx, int64_t *queued, int32_t *closed);
 
+/* Candidate lists of the triangle search: every cell within one cell of a
+ * triangle cell (the dilated occupancy) stores the distinct triangles binned
+ * into its 27 cells (Sec. 3.1.3's C_compact lists, merged once at
+ * fppg_create), so a search reads one list instead of probing 27 cells
+ * through the Eq. 10 hash.  *cells = cells with a list, *entries = total
+ * list entries, *overflow = cells whose list was too long to merge (their
+ * searches probe the cells).  Outputs nullable. */
+int fppg_debug_cell_lists(fppg_ctx *ctx, int64_t *cells, int64_t *entries, int64_t *overflow);
+
 /* Work of one force pass (A4) on the current state, summed over mobile
  * particles: candidates = particles in the 27 neighbour cells around each
  * particle (the search set of the cell grid, Sec. 3.1.3), pairs = masked

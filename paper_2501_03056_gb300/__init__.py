@@ -78,6 +78,7 @@ def lib():
                 "fppg_energy": [vp, vp, vp, P_(f64), vp, vp],
                 "fppg_work_counts": [vp, P_(i64), P_(i64), P_(i64)],
                 "fppg_debug_search": [vp, P_(i64), P_(i32)],
+                "fppg_debug_cell_lists": [vp, P_(i64), P_(i64), P_(i64)],
                 "fppg_batch_load": [vp],
                 "fppg_copy_positions_dev": [vp, vp],
                 "fppg_batch_create": [P_(vp), i32, P_(vp)],
@@ -305,6 +306,13 @@ class Body:
         q, c = C.c_int64(), C.c_int32()
         self._chk(lib().fppg_debug_search(self._h, C.byref(q), C.byref(c)))
         return q.value, bool(c.value)
+
+    def debug_cell_lists(self):
+        """(cells with a candidate list, list entries, cells whose list was
+        too long and that are probed instead)."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._chk(lib().fppg_debug_cell_lists(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
 
     def work_counts(self):
         """(candidates in the 27 cells, pairs within 2h, candidates actually

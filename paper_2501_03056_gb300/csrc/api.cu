@@ -92,7 +92,7 @@ __global__ void k_set_body(float4 *__restrict__ pos, int64_t n, int body) {
 inline unsigned nb(int64_t n) { return (unsigned)std::max<int64_t>((n + 255) / 256, 1); }
 
 MeshView view_of(const Body &b) {
-    return MeshView{b.geo, b.vx, b.pn, b.hrng, b.compact, b.tlist, b.seg, b.lines, b.occ};
+    return MeshView{b.geo, b.vx, b.pn, b.hrng, b.compact, b.tlist, b.seg, b.lines, b.occ, b.drank, b.coff, b.cand};
 }
 
 // (re)build the single-body group of a context
@@ -459,6 +459,21 @@ int fppg_debug_search(fppg_ctx *ctx, int64_t *queued, int32_t *closed) {
     return FPPG_OK;
 }
 
+int fppg_debug_cell_lists(fppg_ctx *ctx, int64_t *cells, int64_t *entries, int64_t *overflow) {
+    if (!ctx) return FPPG_ERR_ARG;
+    const Body &b = ctx->body;
+    int64_t ov = 0;
+    if (overflow && b.n_dil > 0) {
+        std::vector<uint32_t> off((size_t)b.n_dil);
+        CUDA_OR(ctx->err, cudaMemcpy(off.data(), b.coff, sizeof(uint32_t) * off.size(), cudaMemcpyDeviceToHost));
+        for (uint32_t o : off) ov += o >> 31;
+    }
+    if (cells) *cells = b.n_dil;
+    if (entries) *entries = b.n_cand;
+    if (overflow) *overflow = ov;
+    return FPPG_OK;
+}
+
 int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs, int64_t *tested) {
     if (!ctx) return FPPG_ERR_ARG;
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
@@ -572,6 +587,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         }
     }
     int64_t N = 0, cells = 0, nt = 0, nv = 0, hs = 0, nc = 0, np = 0, ns = 0, nl = 0, ow = 0;
+    int64_t dw = 0, dl = 0, dc = 0;   // candidate-list ranks, starts and lists
     for (int32_t i = 0; i < n; i++) {
         const fppg_ctx *c = ctxs[i];
         const Body &bd = c->body;
@@ -620,6 +636,9 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         A.line_off = (int)nl;
         A.occ_off = (uint32_t)ow;
         A.dil_off = (uint32_t)(ow + bd.occ_words);
+        A.drank_off = (uint32_t)dw;
+        A.coff_off = (uint32_t)dl;
+        A.cand_off = (uint32_t)dc;
         g.hp.push_back(A);
         b->off.push_back(N);
         N += c->n;
@@ -632,9 +651,13 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         ns += bd.nseg;
         nl += bd.nlines;
         ow += 2 * bd.occ_words;
+        dw += bd.occ_words;
+        dl += bd.n_dil + 1;
+        dc += bd.n_cand;
     }
     b->off.push_back(N);
-    if (cells >= ((int64_t)1 << 29) || N > ((int64_t)1 << 31) || ow >= 0xffffffffLL) {
+    if (cells >= ((int64_t)1 << 29) || N > ((int64_t)1 << 31) || ow >= 0xffffffffLL || dl >= 0xffffffffLL ||
+        dc >= 0x7fffffffLL) {
         delete b;
         return fail_global(FPPG_ERR_ARG, "batch too large for 32-bit keys");
     }
@@ -646,7 +669,8 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
                A((void **)&d.pn, sizeof(float4) * 6 * nt) || A((void **)&d.hrng, sizeof(uint2) * hs) ||
                A((void **)&d.compact, sizeof(uint4) * nc) || A((void **)&d.tlist, sizeof(int32_t) * np) ||
                A((void **)&d.seg, sizeof(float4) * 3 * ns) || A((void **)&d.lines, sizeof(int2) * nl) ||
-               A((void **)&d.occ, sizeof(uint32_t) * ow)))
+               A((void **)&d.occ, sizeof(uint32_t) * ow) || A((void **)&d.drank, sizeof(uint32_t) * dw) ||
+               A((void **)&d.coff, sizeof(uint32_t) * dl) || A((void **)&d.cand, sizeof(int32_t) * dc)))
         r = FPPG_ERR_OOM;
     cudaStream_t s = b->stream;
     for (int32_t i = 0; i < n && !r; i++) {
@@ -664,12 +688,15 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         if (bd.nseg) cp(d.seg + 3 * (size_t)P.seg_off, bd.seg, sizeof(float4) * 3 * bd.nseg);
         if (bd.nlines) cp(d.lines + P.line_off, bd.lines, sizeof(int2) * bd.nlines);
         cp(d.occ + P.occ_off, bd.occ, sizeof(uint32_t) * 2 * bd.occ_words);
+        cp(d.drank + P.drank_off, bd.drank, sizeof(uint32_t) * bd.occ_words);
+        cp(d.coff + P.coff_off, bd.coff, sizeof(uint32_t) * (bd.n_dil + 1));
+        if (bd.n_cand) cp(d.cand + P.cand_off, bd.cand, sizeof(int32_t) * bd.n_cand);
         const int64_t cn = ctxs[i]->n;
         cp(d.pos + b->off[i], ctxs[i]->group.d.pos, sizeof(float4) * cn);
         cp(d.cons + b->off[i], ctxs[i]->group.d.cons, sizeof(int32_t) * cn);
         if (cn) k_set_body<<<nb(cn), 256, 0, s>>>(d.pos + b->off[i], cn, i);
     }
-    g.mesh = MeshView{d.geo, d.vx, d.pn, d.hrng, d.compact, d.tlist, d.seg, d.lines, d.occ};
+    g.mesh = MeshView{d.geo, d.vx, d.pn, d.hrng, d.compact, d.tlist, d.seg, d.lines, d.occ, d.drank, d.coff, d.cand};
     if (!r) r = g.upload_params(s, err);
     if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = FPPG_ERR_CUDA;
     if (r) {

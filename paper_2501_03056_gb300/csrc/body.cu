@@ -270,7 +270,7 @@ void Group::free_all() {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (owns_mesh) {
-        void *m[] = {g.geo, g.vx, g.pn, g.hrng, g.compact, g.tlist, g.seg, g.lines, g.occ};
+        void *m[] = {g.geo, g.vx, g.pn, g.hrng, g.compact, g.tlist, g.seg, g.lines, g.occ, g.drank, g.coff, g.cand};
         for (void *p : m)
             if (p) cudaFree(p);
     }

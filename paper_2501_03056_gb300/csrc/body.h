@@ -38,6 +38,13 @@ struct Body {
     int64_t npairs = 0;
     uint32_t *occ = nullptr;     // occupancy bitmap, then its 27-cell dilation
     int64_t occ_words = 0;       // words of one bitmap
+    // candidate lists: the distinct triangles of the 27 cells around every
+    // dilated cell; drank[w] = set dilated bits before word w, coff[r] the
+    // list start of the r-th dilated cell (bit 31: list too long, probe
+    // the cells), coff[n_dil] the total
+    uint32_t *drank = nullptr, *coff = nullptr;
+    int32_t *cand = nullptr;
+    int64_t n_dil = 0, n_cand = 0;
     // feature lines (host copies + device segments)
     bool has_features = false;
     std::vector<int32_t> fe;           // [nfe][2] sorted

@@ -61,6 +61,9 @@ struct AsmParams {
     uint32_t tlist_off;    // offset of its triangle list
     uint32_t occ_off;      // word offset of its triangle-cell occupancy bitmap
     uint32_t dil_off;      // word offset of the dilated bitmap (any of 27 cells)
+    uint32_t drank_off;    // offset of its dilated-bit ranks (one per bitmap word)
+    uint32_t coff_off;     // offset of its candidate-list starts (dilated cells + 1)
+    uint32_t cand_off;     // offset of its candidate lists
     int tri_off;           // offset of its triangles (ids are local)
     int nt;
     int vert_off;
@@ -102,6 +105,9 @@ struct MeshView {
     const float4 *seg;
     const int2 *lines;
     const uint32_t *occ;
+    const uint32_t *drank;   // candidate lists of the dilated cells (Body)
+    const uint32_t *coff;
+    const int32_t *cand;
 };
 
 // Device arrays of one group.
@@ -140,6 +146,8 @@ struct DevGroup {
     float4 *seg = nullptr;
     int2 *lines = nullptr;
     uint32_t *occ = nullptr;
+    uint32_t *drank = nullptr, *coff = nullptr;
+    int32_t *cand = nullptr;
     // energy scratch
     float *rho_s = nullptr;
 };

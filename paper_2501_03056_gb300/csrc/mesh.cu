@@ -262,6 +262,103 @@ __global__ void k_closed_check(const uint64_t *__restrict__ key, const uint32_t 
     if (!(a1 == b2 && b1 == a2)) atomicOr(open, 1u);
 }
 
+// ---- candidate lists of the dilated cells ------------------------------------
+// For every cell of the dilated occupancy map (a cell with a triangle among
+// its 27 neighbours) the distinct triangles binned into those 27 cells, so
+// that the search reads one list instead of probing 27 cells through the
+// hash.  The set is the one the 27-cell probe gathers, without repeats.
+
+__global__ void k_word_popc(const uint32_t *__restrict__ words, int64_t n, uint32_t *__restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cnt[i] = __popc(words[i]);
+}
+
+// cell key of every set bit, in key order: dcell[rank] = key
+__global__ void k_bit_cells(const uint32_t *__restrict__ words, int64_t n, const uint32_t *__restrict__ rank,
+                            uint32_t *__restrict__ dcell) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n) return;
+    uint32_t bits = words[w], r = rank[w];
+    while (bits) {
+        const int j = __ffs(bits) - 1;
+        dcell[r++] = (uint32_t)(32 * w + j);
+        bits &= bits - 1u;
+    }
+}
+
+constexpr int kListBuf = 512;   // gathered ids per warp (with repeats); more: the cell keeps the probe
+
+// one warp per dilated cell: gather the 27 cells' triangle ids, keep the
+// first occurrence of each; WRITE = 0 counts (cnt[r], 0 and ovf[r] = 1 on
+// overflow), WRITE = 1 writes the list at off[r]
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_cell_lists(AsmParams A, MeshView M, const uint32_t *__restrict__ dcell,
+                                                    int64_t D, uint32_t *__restrict__ cnt, uint8_t *__restrict__ ovf,
+                                                    const uint32_t *__restrict__ off, int32_t *__restrict__ list) {
+    __shared__ int32_t sbuf[8][kListBuf];
+    int32_t *buf = sbuf[threadIdx.x / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; r < D; r += warps) {
+        const uint32_t c = dcell[r];
+        const int x = (int)(c % (uint32_t)A.tg_n[0]), yz = (int)(c / (uint32_t)A.tg_n[0]);
+        const int y = yz % A.tg_n[1], z = yz / A.tg_n[1];
+        uint32_t beg = 0, len = 0;
+        if (lane < 27) {
+            const int xx = x + lane % 3 - 1, yy = y + (lane / 3) % 3 - 1, zz = z + lane / 9 - 1;
+            if (xx >= 0 && yy >= 0 && zz >= 0 && xx < A.tg_n[0] && yy < A.tg_n[1] && zz < A.tg_n[2] &&
+                test_bit(M.occ, A.occ_off, tri_key(A, xx, yy, zz)))
+                tri_cell(M, A, xx, yy, zz, beg, len);
+        }
+        uint32_t o = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, o, d);
+            if (lane >= d) o += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, o, 31);
+        o -= len;
+        if (total > (uint32_t)kListBuf) {
+            if (!WRITE && lane == 0) {
+                cnt[r] = 0;
+                ovf[r] = 1;
+            }
+            __syncwarp();
+            continue;
+        }
+        for (uint32_t q = 0; q < len; q++) buf[o + q] = M.tlist[beg + q];
+        __syncwarp();
+        uint32_t written = 0;
+        for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            bool first = false;
+            int32_t id = 0;
+            if (q < total) {
+                id = buf[q];
+                first = true;
+                for (uint32_t p = 0; p < q; p++)
+                    if (buf[p] == id) {
+                        first = false;
+                        break;
+                    }
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, first);
+            if (WRITE && first) list[off[r] + written + __popc(m & ((1u << lane) - 1u))] = id;
+            written += __popc(m);
+        }
+        if (!WRITE && lane == 0) {
+            cnt[r] = written;
+            ovf[r] = 0;
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_flag_overflow(uint32_t *__restrict__ off, const uint8_t *__restrict__ ovf, int64_t D) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < D && ovf[r]) off[r] |= 0x80000000u;
+}
+
 __global__ void k_feature_flags(const uint64_t *__restrict__ key, const uint32_t *__restrict__ val, int64_t m,
                                 const double *__restrict__ nu, double cthr, uint32_t *__restrict__ flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,9 +426,13 @@ static cudaError_t dalloc(T **p, int64_t n) {
 }
 
 void Body::free_mesh() {
-    void *ptrs[] = {d_verts, d_tris, geo, vx, pn, hrng, compact, tlist, nu, ekey, eval, seg, lines, occ};
+    void *ptrs[] = {d_verts, d_tris, geo, vx, pn, hrng, compact, tlist, nu, ekey, eval, seg, lines, occ,
+                    drank, coff, cand};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    drank = coff = nullptr;
+    cand = nullptr;
+    n_dil = n_cand = 0;
     d_verts = nullptr;
     d_tris = nullptr;
     geo = vx = pn = nullptr;
@@ -491,8 +592,52 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     CK(dalloc(&occ, 2 * occ_words));
     CK(cudaMemsetAsync(occ, 0, sizeof(uint32_t) * 2 * occ_words, s));
     k_mark_occupancy<<<blocks(ncompact), 256, 0, s>>>(compact, ncompact, g, occ_words, occ);
+
+    // ---- candidate lists of the dilated cells -----------------------------
+    uint32_t *wpop = nullptr, *dcell = nullptr, *lcnt = nullptr, *ltot = nullptr, *lscr = nullptr;
+    uint8_t *lovf = nullptr;
+    CK(dalloc(&drank, occ_words));
+    CK(dalloc(&wpop, occ_words));
+    CK(dalloc(&ltot, 1));
+    int64_t lsc = scan_tmp_elems(occ_words);
+    CK(dalloc(&lscr, lsc));
+    k_word_popc<<<blocks(occ_words), 256, 0, s>>>(occ + occ_words, occ_words, wpop);
+    exclusive_scan_u32(wpop, drank, occ_words, ltot, lscr, lsc, s);
+    uint32_t nd = 0;
+    CK(cudaMemcpyAsync(&nd, ltot, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    n_dil = nd;
+    CK(dalloc(&dcell, n_dil));
+    CK(dalloc(&lcnt, n_dil));
+    CK(dalloc(&lovf, n_dil));
+    CK(dalloc(&coff, n_dil + 1));
+    k_bit_cells<<<blocks(occ_words), 256, 0, s>>>(occ + occ_words, occ_words, drank, dcell);
+    {
+        AsmParams A;
+        memset(&A, 0, sizeof(A));
+        for (int k = 0; k < 3; k++) A.tg_n[k] = tg_n[k];
+        A.hash_mask = (uint32_t)(hash_size - 1);
+        const MeshView M{geo, vx, pn, hrng, compact, tlist, nullptr, nullptr, occ, nullptr, nullptr, nullptr};
+        const unsigned lb = (unsigned)std::min<int64_t>(std::max<int64_t>((n_dil + 7) / 8, 1), 65535);
+        k_cell_lists<false><<<lb, 256, 0, s>>>(A, M, dcell, n_dil, lcnt, lovf, nullptr, nullptr);
+        cudaFree(lscr);
+        lsc = scan_tmp_elems(std::max<int64_t>(n_dil, 1));
+        CK(dalloc(&lscr, lsc));
+        exclusive_scan_u32(lcnt, coff, n_dil, coff + n_dil, lscr, lsc, s);
+        uint32_t nc_ = 0;
+        CK(cudaMemcpyAsync(&nc_, coff + n_dil, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        n_cand = nc_;
+        CK(dalloc(&cand, n_cand));
+        k_cell_lists<true><<<lb, 256, 0, s>>>(A, M, dcell, n_dil, lcnt, lovf, coff, cand);
+        k_flag_overflow<<<blocks(std::max<int64_t>(n_dil, 1)), 256, 0, s>>>(coff, lovf, n_dil);
+    }
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
+    {
+        void *lt[] = {wpop, dcell, lcnt, ltot, lscr, lovf};
+        for (void *p : lt) cudaFree(p);
+    }
     void *tmp[] = {cnt, off, total, scratch, pk[0], pk[1], pt[0], pt[1], flag, pos, cmp_unsorted,
                    hk[0], hk[1], hv[0], hv[1], hist, tot, vpn};
     for (void *p : tmp) cudaFree(p);

@@ -435,15 +435,47 @@ __device__ inline bool surface_candidate(const MeshView &M, const AsmParams &A, 
 // closest projectable triangle (smallest |plane distance|, ties to the lower
 // index) among those binned into the 27 cells around y, or into y's own
 // cell alone (own_cell); -1 when none
+// The candidate triangles of the 27 cells around y's cell from that cell's
+// list (built with the mesh: the distinct triangles of the 27 cells): 1 with
+// [beg, end) into M.cand; 2 when the list was too long to build (probe the
+// cells); 0 when no triangle lies in the 27 cells.  Warp-uniform.
+__device__ inline int cell_candidates(const MeshView &M, const AsmParams &A, float3 y, uint32_t &beg,
+                                      uint32_t &end) {
+    const uint32_t c = tri_key(A, cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]),
+                               cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]),
+                               cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]));
+    const uint32_t w = M.occ[A.dil_off + (c >> 5)];
+    if (!((w >> (c & 31u)) & 1u)) return 0;
+    const uint32_t r = M.drank[A.drank_off + (c >> 5)] + __popc(w & ((1u << (c & 31u)) - 1u));
+    const uint32_t o0 = M.coff[A.coff_off + r], o1 = M.coff[A.coff_off + r + 1];
+    if (o0 >> 31) return 2;
+    beg = A.cand_off + o0;
+    end = A.cand_off + (o1 & 0x7fffffffu);
+    return 1;
+}
+
+// every candidate triangle of the 27 cells around y, spread over the lanes
+template <typename Test>
+__device__ inline void for_27_candidates(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf,
+                                         Test &&test) {
+    const int lane = threadIdx.x & 31;
+    uint32_t beg = 0, end = 0;
+    const int kind = cell_candidates(M, A, y, beg, end);
+    if (kind == 1) {
+        for (uint32_t q = beg + lane; q < end; q += 32) test(M.cand[q]);
+    } else if (kind == 2) {
+        const CellRange r = lane_cell(M, A, y, lane);
+        for_candidates(M, r, buf, test);
+    }
+}
+
 __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist, int32_t *buf,
                                     bool own_cell = false) {
     const int lane = threadIdx.x & 31;
-    CellRange r = lane_cell(M, A, y, lane);
-    if (own_cell && lane != 13) r = CellRange{0u, 0u};   // lane 13 holds the centre cell
     float best = FLT_MAX;
     int bt = 0x7fffffff;
     float bd = 0.f;
-    for_candidates(M, r, buf, [&](int t) {
+    auto test = [&](int t) {
         float d;
         if (!surface_candidate(M, A, t, y, d)) return;
         const float ad = fabsf(d);
@@ -452,7 +484,15 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
             bt = t;
             bd = d;
         }
-    });
+    };
+    if (own_cell) {
+        // the cell that holds y alone: lane 13 probes the centre cell
+        CellRange r = lane_cell(M, A, y, lane);
+        if (lane != 13) r = CellRange{0u, 0u};
+        for_candidates(M, r, buf, test);
+    } else {
+        for_27_candidates(M, A, y, buf, test);
+    }
     float v = best;
     int t = bt;
     warp_argmin(v, t);
@@ -504,11 +544,10 @@ __device__ inline float block_margin(const AsmParams &A, float3 y) {
 // to the surface, valid when inside.
 __device__ int warp_closest_sign(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear) {
     const int lane = threadIdx.x & 31;
-    const CellRange r = lane_cell(M, A, y, lane);
     float best = FLT_MAX;
     int bt = 0x7fffffff, breg = 0;
     float3 bcp = make_float3(0.f, 0.f, 0.f);
-    for_candidates(M, r, buf, [&](int t) {
+    for_27_candidates(M, A, y, buf, [&](int t) {
         const size_t g = (size_t)(A.tri_off + t);
         const float3 n = f3(M.geo[5 * g + 1]);
         if (n.x == 0.f && n.y == 0.f && n.z == 0.f) return;   // degenerate

@@ -146,6 +146,24 @@ def test_surface_projection_matches_oracle(mesh):
         assert np.all(ok[~agree] == ook[~agree])
 
 
+def test_candidate_lists_and_their_overflow_match_the_oracle():
+    # coarse cells on a fine icosphere: the 27-cell unions exceed what the
+    # list build merges, so those cells are probed; both paths must give the
+    # oracle's triangle choices and inside decisions
+    for level, dx, expect_overflow in ((4, 0.03, False), (5, 0.3, True)):
+        v, t = W.icosphere_mesh(level)
+        b, o = pkg.Body(v, t, dx, 1.3 * dx), O.Oracle(v, t, dx, 1.3 * dx)
+        cells, entries, overflow = b.debug_cell_lists()
+        assert cells > 0 and entries >= cells and (overflow > 0) == expect_overflow
+        y = _near_surface_points(v, t, 5000, 0.3 * dx, 11)
+        cls = np.zeros(len(y), np.int32)
+        x, tri, ok = b.project_points(y, cls)
+        ox, otri, ook = o.project_points(y, cls)
+        assert ((tri == otri) & (ok == ook)).mean() > 0.999
+        inside = b.project_points(y, np.full(len(y), W.CLS_V, np.int32))[2]
+        assert (inside == o.volume_inside(y)).mean() > 0.999
+
+
 @pytest.mark.parametrize("mesh", ["ico4", "torus", "cube"])
 def test_volume_inside_matches_oracle(mesh):
     if mesh == "cube":
