@@ -290,6 +290,36 @@ def main():
         extras["e2e"] = {"value": n * world * G * K / e2e_s, "unit": "particle-iterations/s",
                          "h2d_bytes_per_step": int(n * 16), "d2h_bytes_per_step": int(n * 12)}
 
+        # ---- energy (A8): energy-descent relaxation and the backward ------------
+        for b, a in zip(bodies, asm):
+            b.set_particles(a.xyz, a.cls)
+        Ge = 10
+        for b in bodies:
+            b.relax_energy(1)
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es.record(stream)
+        for b in bodies:
+            b.relax_energy(Ge)
+        ee.record(stream)
+        torch.cuda.synchronize()
+        e_relax = n * Ge / (es.elapsed_time(ee) / 1e3)
+        tb, ta = bodies[1], asm[1]                      # the torus: surface particles through the projection
+        y = torch.from_numpy(np.ascontiguousarray(tb.get_particles()[0])).cuda()
+        verts = torch.from_numpy(np.ascontiguousarray(ta.verts)).cuda()
+        gy, gv = torch.empty_like(y), torch.empty_like(verts)
+        tb.energy_ptr(y.data_ptr(), verts.data_ptr(), gy.data_ptr(), gv.data_ptr())
+        reps = 5
+        es.record(stream)
+        for _ in range(reps):
+            tb.energy_ptr(y.data_ptr(), verts.data_ptr(), gy.data_ptr(), gv.data_ptr())
+        ee.record(stream)
+        torch.cuda.synchronize()
+        extras["energy"] = {"relax_energy": {"value": e_relax, "unit": "particle-iterations/s",
+                                             "iterations": Ge, "form": "plain, both bodies"},
+                            "energy_and_backward_ms": es.elapsed_time(ee) / reps,
+                            "backward_workload": f"torus body, {tb.n} particles, {len(ta.verts)} vertices: "
+                                                 "E, dE/dy and dE/dverts through the frozen surface projection"}
+
         # ---- 64 bodies of uneven size with gear-shaft unions: batched + graph
         # against plain (single bodies one by one, each union as a 2-body
         # batch, no graph) ------------------------------------------------------

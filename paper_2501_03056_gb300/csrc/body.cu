@@ -214,7 +214,8 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     const size_t n1 = (size_t)std::max<int64_t>(N, 1);
     g.n_tiles = (int)std::max<int64_t>(radix_tiles(N), 1);
     g.key_bits = fine_key_bits(g.total_cells);
-    g.passes = (g.key_bits + 7) / 8;
+    int digit_bits = 8;
+    g.passes = radix_pass_plan(g.key_bits, &digit_bits);
     CKA(cudaMalloc(&g.pos, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.cons, sizeof(int32_t) * n1));
     for (int k = 0; k < 2; k++) {
@@ -232,8 +233,8 @@ int Group::alloc_particles(int64_t N, std::string &err) {
         CKA(cudaMalloc(&g.work_count, sizeof(uint32_t)));
         CKA(cudaMemset(g.work_count, 0, sizeof(uint32_t)));
     }
-    CKA(cudaMalloc(&g.hist, sizeof(uint32_t) * 256 * (size_t)g.n_tiles));
-    if (!g.totals) CKA(cudaMalloc(&g.totals, sizeof(uint32_t) * 256));
+    CKA(cudaMalloc(&g.hist, sizeof(uint32_t) * kMaxDigits * (size_t)g.n_tiles));
+    if (!g.totals) CKA(cudaMalloc(&g.totals, sizeof(uint32_t) * kMaxDigits));
     if (!g.cells) {
         CKA(cudaMalloc(&g.cells, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));
         CKA(cudaMemset(g.cells, 0, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));

@@ -136,8 +136,8 @@ struct DevGroup {
     uint32_t *maxdisp = nullptr;
     int4 *work = nullptr;          // search queue {key slot, trial point}
     uint32_t *work_count = nullptr;
-    uint32_t *hist = nullptr;  // 256 * n_tiles
-    uint32_t *totals = nullptr; // 256
+    uint32_t *hist = nullptr;  // kMaxDigits * n_tiles
+    uint32_t *totals = nullptr; // kMaxDigits
     // mesh
     float4 *geo = nullptr, *vx = nullptr, *pn = nullptr;
     uint2 *hrng = nullptr;
@@ -322,6 +322,10 @@ int radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t
 int radix_sort_u64(uint64_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                    uint32_t *totals, cudaStream_t s);
 int64_t radix_tiles(int64_t n);
+// radix passes for keys of `bits` bits and their digit width (*digit_bits);
+// the histogram holds kMaxDigits rows of radix_tiles(n)
+int radix_pass_plan(int bits, int *digit_bits);
+constexpr int kMaxDigits = 256;
 // exclusive scan of n uint32 values into out (may alias in); returns the total
 // through *total_dev (device pointer, nullable)
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev, uint32_t *tmp,

@@ -501,8 +501,8 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     CK(dalloc(&cv[1], m));
     CK(dalloc(&vpn, nv));
     int64_t tiles = radix_tiles(m);
-    CK(dalloc(&hist, 256 * std::max<int64_t>(tiles, 1)));
-    CK(dalloc(&tot, 256));
+    CK(dalloc(&hist, kMaxDigits * std::max<int64_t>(tiles, 1)));
+    CK(dalloc(&tot, kMaxDigits));
     k_tri_prep<<<blocks(nt), 256, 0, s>>>(d_verts, d_tris, nt, nv, geo, vx, nu, ek[0], ck[0]);
     int eb = radix_sort_u64(ek, ev, true, m, bits_for((uint64_t)nv * (uint64_t)nv), hist, tot, s);
     k_edge_runs<<<blocks(m), 256, 0, s>>>(ek[eb], ev[eb], m, nu, pn);
@@ -555,7 +555,7 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     k_bin<true><<<blocks(nt, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, nullptr, off, pk[0], pt[0]);
     int64_t pt_tiles = radix_tiles(npairs);
     cudaFree(hist);
-    CK(dalloc(&hist, 256 * std::max<int64_t>(std::max(pt_tiles, tiles), 1)));
+    CK(dalloc(&hist, kMaxDigits * std::max<int64_t>(std::max(pt_tiles, tiles), 1)));
     int pb = radix_sort_u32(pk, pt, false, npairs, bits_for((uint64_t)tg_n[0] * tg_n[1] * tg_n[2]), hist, tot, s);
     CK(dalloc(&tlist, npairs));
     CK(cudaMemcpyAsync(tlist, pt[pb], sizeof(uint32_t) * npairs, cudaMemcpyDeviceToDevice, s));

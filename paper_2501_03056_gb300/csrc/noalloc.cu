@@ -35,8 +35,8 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kOffParams = 0;
 constexpr size_t kOffFlags = kOffParams + align256(sizeof(AsmParams));        // epoch, amax, maxdisp, queue, error
 constexpr size_t kOffTotals = kOffFlags + 256;
-constexpr size_t kOffHist = kOffTotals + align256(256 * 4);
-constexpr size_t kOffPos = kOffHist + align256(256 * 4 * kStaticMaxTiles);
+constexpr size_t kOffHist = kOffTotals + align256(kMaxDigits * 4);
+constexpr size_t kOffPos = kOffHist + align256(kMaxDigits * 4 * kStaticMaxTiles);
 constexpr size_t kOffKey0 = kOffPos + align256(16 * kStaticMaxN);
 constexpr size_t kOffKey1 = kOffKey0 + align256(4 * kStaticMaxN);
 constexpr size_t kOffId0 = kOffKey1 + align256(4 * kStaticMaxN);
@@ -145,7 +145,8 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     d.N = n;
     d.total_cells = cells;
     d.key_bits = fine_key_bits(cells);
-    d.passes = (d.key_bits + 7) / 8;
+    int digit_bits = 8;
+    d.passes = radix_pass_plan(d.key_bits, &digit_bits);
     d.n_tiles = (int)std::max<int64_t>(radix_tiles(n), 1);
     d.params = (AsmParams *)(base + kOffParams);
     d.pos = (float4 *)(base + kOffPos);

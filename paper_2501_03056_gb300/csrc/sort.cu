@@ -54,12 +54,14 @@ __device__ inline uint32_t block_incl_scan(uint32_t v, uint32_t *wsum, uint32_t 
     return r;
 }
 
-template <typename K, int RC>
+// DB-bit digits (ND = 2^DB values; the passes use DB = 8): the upsweep
+// counts them per tile in shared memory
+template <typename K, int RC, int DB>
 __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int64_t n, int shift,
                                                 uint32_t *__restrict__ hist, int n_tiles) {
-    constexpr int TILE = RW * RC * 32;
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
+    constexpr int TILE = RW * RC * 32, ND = 1 << DB;
+    __shared__ uint32_t cnt[ND];
+    for (int d = threadIdx.x; d < ND; d += RT) cnt[d] = 0;
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * TILE + w * (RC * 32) + l;
@@ -67,12 +69,12 @@ __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int6
     for (int c = 0; c < RC; c++) {
         int64_t idx = base + c * 32;
         bool valid = idx < n;
-        uint32_t d = valid ? (uint32_t)((keys[idx] >> shift) & (K)255) : 256u;
+        uint32_t d = valid ? (uint32_t)((keys[idx] >> shift) & (K)(ND - 1)) : (uint32_t)ND;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         if (valid && (uint32_t)(__ffs(peers) - 1) == (uint32_t)l) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
+    for (int d = threadIdx.x; d < ND; d += RT) hist[(int64_t)d * n_tiles + blockIdx.x] = cnt[d];
 }
 
 // one CTA per digit: exclusive scan of its row of per-tile counts
@@ -91,22 +93,22 @@ __global__ void __launch_bounds__(RT) k_digit_scan(uint32_t *__restrict__ hist, 
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-template <typename K, bool IOTA, int RC>
+template <typename K, bool IOTA, int RC, int DB>
 __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                   K *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
                                                   int shift, const uint32_t *__restrict__ hist,
                                                   const uint32_t *__restrict__ totals, int n_tiles) {
-    constexpr int TILE = RW * RC * 32;
+    constexpr int TILE = RW * RC * 32, ND = 1 << DB, KD = ND / RT;
     extern __shared__ __align__(16) unsigned char smem[];
     K *skey = reinterpret_cast<K *>(smem);
     uint32_t *sval = reinterpret_cast<uint32_t *>(smem + sizeof(K) * TILE);
-    uint32_t(*wcnt)[256] = reinterpret_cast<uint32_t(*)[256]>(smem + (sizeof(K) + 4) * TILE);
-    uint32_t *dstart = reinterpret_cast<uint32_t *>(smem + (sizeof(K) + 4) * TILE + RW * 256 * 4);
-    uint32_t *gbase = dstart + 256;
-    uint32_t *wsum = gbase + 256;
+    uint32_t(*wcnt)[ND] = reinterpret_cast<uint32_t(*)[ND]>(smem + (sizeof(K) + 4) * TILE);
+    uint32_t *dstart = reinterpret_cast<uint32_t *>(smem + (sizeof(K) + 4) * TILE + RW * ND * 4);
+    uint32_t *gbase = dstart + ND;
+    uint32_t *wsum = gbase + ND;
 
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < RW * 256; i += RT) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < RW * ND; i += RT) (&wcnt[0][0])[i] = 0;
     __syncthreads();
 
     const int64_t tile0 = (int64_t)blockIdx.x * TILE;
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, con
         bool valid = idx < n;
         k[c] = valid ? kin[idx] : (K)0;
         v[c] = valid ? (IOTA ? (uint32_t)idx : vin[idx]) : 0u;
-        uint32_t d = valid ? (uint32_t)((k[c] >> shift) & (K)255) : 256u;
+        uint32_t d = valid ? (uint32_t)((k[c] >> shift) & (K)(ND - 1)) : (uint32_t)ND;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = valid ? wcnt[w][d] : 0u;
         __syncwarp();
@@ -129,27 +131,41 @@ __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, con
         rank[c] = before + __popc(peers & lt);
     }
     __syncthreads();
-    // thread d: per-warp exclusive offsets and the tile count of digit d
-    const int d = threadIdx.x;
-    uint32_t run = 0;
+    // thread t owns digits t KD .. t KD + KD - 1: per-warp exclusive offsets,
+    // the tile count and the global start of each
+    uint32_t cnt_d[KD], tot_d[KD], s_cnt = 0, s_tot = 0;
 #pragma unroll
-    for (int ww = 0; ww < RW; ww++) {
-        uint32_t t = wcnt[ww][d];
-        wcnt[ww][d] = run;
-        run += t;
+    for (int j = 0; j < KD; j++) {
+        const int d = threadIdx.x * KD + j;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < RW; ww++) {
+            uint32_t t = wcnt[ww][d];
+            wcnt[ww][d] = run;
+            run += t;
+        }
+        cnt_d[j] = run;
+        s_cnt += run;
+        tot_d[j] = totals[d];
+        s_tot += tot_d[j];
     }
     uint32_t tmp;
-    uint32_t local_incl = block_incl_scan(run, wsum, &tmp);
-    uint32_t tot = totals[d];
-    uint32_t digit_incl = block_incl_scan(tot, wsum, &tmp);
-    dstart[d] = local_incl - run;
-    gbase[d] = (digit_incl - tot) + hist[(int64_t)d * n_tiles + blockIdx.x] - (local_incl - run);
+    uint32_t loc = block_incl_scan(s_cnt, wsum, &tmp) - s_cnt;
+    uint32_t dig = block_incl_scan(s_tot, wsum, &tmp) - s_tot;
+#pragma unroll
+    for (int j = 0; j < KD; j++) {
+        const int d = threadIdx.x * KD + j;
+        dstart[d] = loc;
+        gbase[d] = dig + hist[(int64_t)d * n_tiles + blockIdx.x] - loc;
+        loc += cnt_d[j];
+        dig += tot_d[j];
+    }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < RC; c++) {
         int64_t idx = base + c * 32;
         if (idx < n) {
-            uint32_t dd = (uint32_t)((k[c] >> shift) & (K)255);
+            uint32_t dd = (uint32_t)((k[c] >> shift) & (K)(ND - 1));
             uint32_t p = dstart[dd] + wcnt[w][dd] + rank[c];
             skey[p] = k[c];
             sval[p] = v[c];
@@ -159,69 +175,76 @@ __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, con
     const int tile_n = (int)min((int64_t)TILE, n - tile0);
     for (int j = threadIdx.x; j < tile_n; j += RT) {
         K kk = skey[j];
-        uint32_t dd = (uint32_t)((kk >> shift) & (K)255);
+        uint32_t dd = (uint32_t)((kk >> shift) & (K)(ND - 1));
         uint32_t o = gbase[dd] + (uint32_t)j;
         kout[o] = kk;
         vout[o] = sval[j];
     }
 }
 
-template <typename K, int RC>
+template <typename K, int RC, int DB>
 size_t downsweep_smem() {
-    return (sizeof(K) + 4) * (size_t)(RW * RC * 32) + RW * 256 * 4 + 2 * 256 * 4 + RW * 4;
+    return (sizeof(K) + 4) * (size_t)(RW * RC * 32) + RW * (4 << DB) + 2 * (4 << DB) + RW * 4;
 }
 
-template <typename K, int RC>
+template <typename K, int RC, int DB>
 void set_smem_attr() {
-    cudaFuncSetAttribute(k_downsweep<K, true, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)downsweep_smem<K, RC>());
-    cudaFuncSetAttribute(k_downsweep<K, false, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)downsweep_smem<K, RC>());
+    cudaFuncSetAttribute(k_downsweep<K, true, RC, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)downsweep_smem<K, RC, DB>());
+    cudaFuncSetAttribute(k_downsweep<K, false, RC, DB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)downsweep_smem<K, RC, DB>());
 }
 
-template <typename K, int RC>
+template <typename K, int RC, int DB>
 int radix_passes(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int passes, uint32_t *hist,
                  uint32_t *totals, cudaStream_t s) {
     constexpr int TILE = RW * RC * 32;
     const int n_tiles = (int)((n + TILE - 1) / TILE);
     int cur = 0;
     for (int p = 0; p < passes; p++) {
-        const int shift = 8 * p;
-        k_upsweep<K, RC><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles);
-        k_digit_scan<<<256, RT, 0, s>>>(hist, n_tiles, totals);
+        const int shift = DB * p;
+        k_upsweep<K, RC, DB><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles);
+        k_digit_scan<<<1 << DB, RT, 0, s>>>(hist, n_tiles, totals);
         if (p == 0 && iota_vals)
-            k_downsweep<K, true, RC><<<n_tiles, RT, downsweep_smem<K, RC>(), s>>>(
+            k_downsweep<K, true, RC, DB><<<n_tiles, RT, downsweep_smem<K, RC, DB>(), s>>>(
                 keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
         else
-            k_downsweep<K, false, RC><<<n_tiles, RT, downsweep_smem<K, RC>(), s>>>(
+            k_downsweep<K, false, RC, DB><<<n_tiles, RT, downsweep_smem<K, RC, DB>(), s>>>(
                 keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
         cur ^= 1;
     }
     return cur;
 }
 
+template <typename K, int DB>
+int radix_sort_db(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int passes, uint32_t *hist,
+                  uint32_t *totals, cudaStream_t s, int sms) {
+    // the largest tile that still gives every SM four tiles (latency hiding)
+    const int64_t want = 4 * (int64_t)sms;
+    if ((n + 4095) / 4096 >= want) return radix_passes<K, 16, DB>(keys, vals, iota_vals, n, passes, hist, totals, s);
+    if ((n + 2047) / 2048 >= want) return radix_passes<K, 8, DB>(keys, vals, iota_vals, n, passes, hist, totals, s);
+    return radix_passes<K, 4, DB>(keys, vals, iota_vals, n, passes, hist, totals, s);
+}
+
 template <typename K>
 int radix_sort_impl(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                     uint32_t *totals, cudaStream_t s) {
     if (n <= 0) return 0;
-    const int passes = bits <= 0 ? 0 : (bits + 7) / 8;
     static bool attr_done = false;
     static int sms = 0;
     if (!attr_done) {
-        set_smem_attr<K, 4>();
-        set_smem_attr<K, 8>();
-        set_smem_attr<K, 16>();
+        set_smem_attr<K, 4, 8>();
+        set_smem_attr<K, 8, 8>();
+        set_smem_attr<K, 16, 8>();
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
             sms = 152;
         attr_done = true;
     }
-    // the largest tile that still gives every SM four tiles (latency hiding)
-    const int64_t want = 4 * (int64_t)sms;
-    if ((n + 4095) / 4096 >= want) return radix_passes<K, 16>(keys, vals, iota_vals, n, passes, hist, totals, s);
-    if ((n + 2047) / 2048 >= want) return radix_passes<K, 8>(keys, vals, iota_vals, n, passes, hist, totals, s);
-    return radix_passes<K, 4>(keys, vals, iota_vals, n, passes, hist, totals, s);
+    int db = 8;
+    const int passes = radix_pass_plan(bits, &db);
+    return radix_sort_db<K, 8>(keys, vals, iota_vals, n, passes, hist, totals, s, sms);
 }
 
 // ---- exclusive scan (set-up work) -----------------------------------------
@@ -264,6 +287,15 @@ __global__ void k_scan_total(const uint32_t *in, const uint32_t *out, int64_t n,
 
 // tiles of the smallest tile size: room for the histogram of any choice
 int64_t radix_tiles(int64_t n) { return (n + kMinTile - 1) / kMinTile; }
+
+// passes for keys of `bits` bits, in 8-bit digits.  (10-bit digits would
+// save a pass for 17-20 and 25-30 bit keys, but measured slower: with 1024
+// buckets a tile scatters about one key per digit, and the 1024-CTA digit
+// scan costs more than the pass saved.)
+int radix_pass_plan(int bits, int *digit_bits) {
+    *digit_bits = 8;
+    return bits <= 0 ? 0 : (bits + 7) / 8;
+}
 
 int radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                    uint32_t *totals, cudaStream_t s) {
