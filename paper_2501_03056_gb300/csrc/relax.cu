@@ -154,39 +154,63 @@ struct PairAcc {
     int cnt;
 };
 
-template <bool ALL, bool COUNT>
+// One slot pair (2m, 2m + 1).  EDGE: the pair may hold a slot outside the
+// range [s, e) (the first and last pair of a range), which is masked out.
+// When every class acts on the lane (ALL) the weight is clamped at zero,
+// max(1 - r / 2h, 0)^3, instead of testing r^2 < (2h)^2: a pair beyond 2h
+// adds exactly 0, one within rounding of 2h a weight below 1e-18.  The
+// counting form keeps the exact FP32 test.
+template <bool ALL, bool COUNT, bool EDGE>
 __device__ inline void pair_step(const float4 *__restrict__ pos_p, uint32_t m, uint32_t s, uint32_t e,
                                  const float2 npx, const float2 npy, const float2 npz, uint32_t mbits, float R2,
                                  float hih, PairAcc &acc, uint32_t self) {
     const uint32_t j = 2 * m;
-    const bool has0 = j >= s, has1 = j + 1 < e;
+    const bool has0 = !EDGE || j >= s, has1 = !EDGE || j + 1 < e;
     const float4 A = pos_p[2 * (size_t)m], B = pos_p[2 * (size_t)m + 1];
     const float2 dx = __fadd2_rn(make_float2(A.x, A.y), npx);     // q - p
     const float2 dy = __fadd2_rn(make_float2(A.z, A.w), npy);
     const float2 dz = __fadd2_rn(make_float2(B.x, B.y), npz);
     const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
-    bool t0 = has0 && r2.x < R2, t1 = has1 && r2.y < R2;
-    if (!ALL) {
-        t0 = t0 && (mbits & __float_as_uint(B.z)) != 0u;
-        t1 = t1 && (mbits & __float_as_uint(B.w)) != 0u;
-    }
-    if (COUNT) acc.cnt += (int)(t0 && j != self) + (int)(t1 && j + 1 != self);
     const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
-    const float2 t = __ffma2_rn(r, make_float2(-hih, -hih), make_float2(1.f, 1.f));   // 1 - r / 2h
-    float2 w = __fmul2_rn(__fmul2_rn(t, t), t);
-    w.x = t0 ? w.x : 0.f;
-    w.y = t1 ? w.y : 0.f;
+    float2 t = __ffma2_rn(r, make_float2(-hih, -hih), make_float2(1.f, 1.f));   // 1 - r / 2h
+    float2 w;
+    if (ALL && !COUNT) {
+        t = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
+        w = __fmul2_rn(__fmul2_rn(t, t), t);
+        if (EDGE) {
+            w.x = has0 ? w.x : 0.f;
+            w.y = has1 ? w.y : 0.f;
+        }
+    } else {
+        bool t0 = has0 && r2.x < R2, t1 = has1 && r2.y < R2;
+        if (!ALL) {
+            t0 = t0 && (mbits & __float_as_uint(B.z)) != 0u;
+            t1 = t1 && (mbits & __float_as_uint(B.w)) != 0u;
+        }
+        if (COUNT) acc.cnt += (int)(t0 && j != self) + (int)(t1 && j + 1 != self);
+        w = __fmul2_rn(__fmul2_rn(t, t), t);
+        w.x = t0 ? w.x : 0.f;
+        w.y = t1 ? w.y : 0.f;
+    }
     acc.ax = __ffma2_rn(w, dx, acc.ax);
     acc.ay = __ffma2_rn(w, dy, acc.ay);
     acc.az = __ffma2_rn(w, dz, acc.az);
 }
 
+// the slot pairs [s >> 1, (e + 1) >> 1) of range [s, e): the first and last
+// pair masked, the ones between without a range test
 template <bool ALL, bool COUNT>
 __device__ inline void force_range2(const float4 *__restrict__ pos_p, const float2 npx, const float2 npy,
                                     const float2 npz, uint32_t mbits, float R2, float hih, uint32_t s, uint32_t e,
                                     PairAcc &acc, uint32_t self) {
-    for (uint32_t m = s >> 1; 2 * m < e; m++)
-        pair_step<ALL, COUNT>(pos_p, m, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
+    uint32_t m = s >> 1;
+    const uint32_t m1 = (e + 1) >> 1;
+    if (m >= m1) return;
+    pair_step<ALL, COUNT, true>(pos_p, m, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
+    if (m + 1 >= m1) return;
+    for (m = m + 1; m + 1 < m1; m++)
+        pair_step<ALL, COUNT, false>(pos_p, m, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
+    pair_step<ALL, COUNT, true>(pos_p, m1 - 1, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
 }
 
 template <int VARIANT, bool COUNT>
