@@ -156,10 +156,10 @@ struct PairAcc {
 
 // One slot pair (2m, 2m + 1).  EDGE: the pair may hold a slot outside the
 // range [s, e) (the first and last pair of a range), which is masked out.
-// When every class acts on the lane (ALL) the weight is clamped at zero,
-// max(1 - r / 2h, 0)^3, instead of testing r^2 < (2h)^2: a pair beyond 2h
-// adds exactly 0, one within rounding of 2h a weight below 1e-18.  The
-// counting form keeps the exact FP32 test.
+// The weight is clamped at zero, max(1 - r / 2h, 0)^3, instead of testing
+// r^2 < (2h)^2: a pair beyond 2h adds exactly 0, one within rounding of 2h a
+// weight below 1e-18; unless every class acts on the lane (ALL) the class
+// mask selects.  The counting form keeps the exact FP32 test.
 template <bool ALL, bool COUNT, bool EDGE>
 __device__ inline void pair_step(const float4 *__restrict__ pos_p, uint32_t m, uint32_t s, uint32_t e,
                                  const float2 npx, const float2 npy, const float2 npz, uint32_t mbits, float R2,
@@ -174,12 +174,17 @@ __device__ inline void pair_step(const float4 *__restrict__ pos_p, uint32_t m, u
     const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
     float2 t = __ffma2_rn(r, make_float2(-hih, -hih), make_float2(1.f, 1.f));   // 1 - r / 2h
     float2 w;
-    if (ALL && !COUNT) {
+    if (!COUNT) {
         t = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
         w = __fmul2_rn(__fmul2_rn(t, t), t);
-        if (EDGE) {
-            w.x = has0 ? w.x : 0.f;
-            w.y = has1 ? w.y : 0.f;
+        bool k0 = has0, k1 = has1;
+        if (!ALL) {
+            k0 = k0 && (mbits & __float_as_uint(B.z)) != 0u;
+            k1 = k1 && (mbits & __float_as_uint(B.w)) != 0u;
+        }
+        if (EDGE || !ALL) {
+            w.x = k0 ? w.x : 0.f;
+            w.y = k1 ? w.y : 0.f;
         }
     } else {
         bool t0 = has0 && r2.x < R2, t1 = has1 && r2.y < R2;
