@@ -303,8 +303,9 @@ int fppg_batch_store(fppg_batch *b);
 int fppg_batch_load(fppg_batch *b);
 /* Autotuner: times `iters` iterations of the batch for every combination
  * of force-kernel block size (128, 256), force-kernel variant (0 per-lane
- * rows, 1 shared-row union) and
- * persistent search grid (4, 8 or 16 CTAs per SM),
+ * rows, 1 shared-row union) and triangle search (one warp per queued
+ * particle on 4, 8 or 16 CTAs per SM, or — search CTAs 0 — one thread per
+ * queued particle on 16 CTAs per SM),
  * keeps the fastest and restores the particle state afterwards.  The choice
  * is cached per (particle-count bucket, volume-particle share, GPU name) for
  * the life of the process; a cached choice is applied without timing.
@@ -316,7 +317,8 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
  * keeps working: the mask is read from device memory). */
 int fppg_batch_set_mobile_classes(fppg_batch *b, int32_t mask);
 /* The same choice made by hand: force variant 0 or 1, force block 128 or 256,
- * search CTAs per SM 1..64 (FPPG_ERR_ARG otherwise).  Every choice gives the
+ * search CTAs per SM 1..64 for the warp form or 0 for the thread form
+ * (FPPG_ERR_ARG otherwise).  Every choice gives the
  * same bits; only the speed differs.  Drops a captured graph. */
 int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t search_ctas);
 /* Kernel launches of one iteration of the batch (A1-A6, all bodies). */

@@ -878,7 +878,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     int nb = 0;
     while ((int64_t)1 << (nb + 1) <= std::max<int64_t>(d.N, 1)) nb++;
     const TuneKey key{nb, d.N ? (int)(10 * nv / d.N) : 0, prop.name};
-    TuneVal best{g.force_variant, g.force_block, g.search_blocks / std::max(sms, 1)};
+    TuneVal best{g.force_variant, g.force_block, g.search_thread ? 0 : g.search_blocks / std::max(sms, 1)};
     double best_ms = 0.0;
     bool cached = false;
     {
@@ -904,10 +904,11 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
         best_ms = 1e30;
         for (int v = 0; v < 2; v++)
             for (int tb : {128, 256})
-                for (int sc : {4, 8, 16}) {
+                for (int sc : {0, 4, 8, 16}) {   // 0: one thread per queued particle
                     g.force_variant = v;
                     g.force_block = tb;
-                    g.search_blocks = sc * sms;
+                    g.search_thread = sc == 0;
+                    g.search_blocks = (sc == 0 ? 16 : sc) * sms;
                     CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
                     CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
                     iterate(g, s, false);
@@ -935,7 +936,8 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     }
     g.force_variant = best.variant;
     g.force_block = best.block;
-    g.search_blocks = best.search_ctas * sms;
+    g.search_thread = best.search_ctas == 0;
+    g.search_blocks = (best.search_ctas == 0 ? 16 : best.search_ctas) * sms;
     if (g.graph) {
         cudaGraphExecDestroy(g.graph);
         g.graph = nullptr;
@@ -958,7 +960,7 @@ int fppg_batch_set_mobile_classes(fppg_batch *b, int32_t mask) {
 }
 
 int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t search_ctas) {
-    if (!b || variant < 0 || variant > 1 || (block != 128 && block != 256) || search_ctas < 1 || search_ctas > 64)
+    if (!b || variant < 0 || variant > 1 || (block != 128 && block != 256) || search_ctas < 0 || search_ctas > 64)
         return FPPG_ERR_ARG;
     Group &g = b->group;
     int dev = 0;
@@ -967,7 +969,8 @@ int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t 
     CUDA_OR(b->err, cudaGetDeviceProperties(&prop, dev));
     g.force_variant = variant;
     g.force_block = block;
-    g.search_blocks = search_ctas * prop.multiProcessorCount;
+    g.search_thread = search_ctas == 0;
+    g.search_blocks = (search_ctas == 0 ? 16 : search_ctas) * prop.multiProcessorCount;
     if (g.graph) {
         cudaGraphExecDestroy(g.graph);
         g.graph = nullptr;

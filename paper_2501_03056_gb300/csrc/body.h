@@ -80,7 +80,8 @@ struct Group {
     std::vector<cudaEvent_t> ev;
     int ev_used = 0;
     // CUDA graph of graph_iters iterations
-    int search_blocks = 152 * 8;  // persistent grid of the warp-per-particle search
+    int search_blocks = 152 * 8;  // persistent grid of the search
+    bool search_thread = false;   // one thread (not one warp) per queued particle
     int force_block = 256;        // threads per block of the force kernel (multiple of 32, <= 256)
     int force_variant = 0;        // 0 per-lane rows, 1 shared-row union
     cudaGraphExec_t graph = nullptr;

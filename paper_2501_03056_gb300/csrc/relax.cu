@@ -818,6 +818,154 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
     }
 }
 
+// ---- the same search, one thread per queued particle --------------------------
+// Each thread walks its particle's candidate list alone: no lanes idle on a
+// short list, and 32 particles' dependent loads are in flight per warp.
+// The candidate set and the comparisons (smallest distance, ties to the
+// lower index) are those of the warp form, so the choices are identical.
+
+// every candidate triangle of the 27 cells around y, one after another
+template <typename Test>
+__device__ inline void each_27_candidate(const MeshView &M, const AsmParams &A, float3 y, Test &&test) {
+    uint32_t beg = 0, end = 0;
+    const int kind = cell_candidates(M, A, y, beg, end);
+    if (kind == 1) {
+        for (uint32_t q = beg; q < end; q++) test(M.cand[q]);
+    } else if (kind == 2) {
+        for (int c = 0; c < 27; c++) {
+            const CellRange r = lane_cell(M, A, y, c);
+            for (uint32_t e = r.beg; e < r.beg + r.len; e++) test(M.tlist[e]);
+        }
+    }
+}
+
+__device__ int thread_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist,
+                                      bool own_cell = false) {
+    float best = FLT_MAX, bd = 0.f;
+    int bt = 0x7fffffff;
+    auto test = [&](int t) {
+        float d;
+        if (!surface_candidate(M, A, t, y, d)) return;
+        const float ad = fabsf(d);
+        if (ad < best || (ad == best && t < bt)) {
+            best = ad;
+            bt = t;
+            bd = d;
+        }
+    };
+    if (own_cell) {
+        const CellRange r = lane_cell(M, A, y, 13);   // the centre cell
+        for (uint32_t e = r.beg; e < r.beg + r.len; e++) test(M.tlist[e]);
+    } else {
+        each_27_candidate(M, A, y, test);
+    }
+    dist = bd;
+    return bt == 0x7fffffff ? -1 : bt;
+}
+
+__device__ int thread_surface_choice(const MeshView &M, const AsmParams &A, float3 y, int c, float &dist) {
+    if (A.cascade) {
+        if (c >= 0 && c < A.nt) {
+            float d = 0.f;
+            if (surface_candidate(M, A, c, y, d)) {
+                dist = d;
+                return c;
+            }
+        }
+        const int t = thread_project_surface(M, A, y, dist, true);
+        if (t >= 0) return t;
+    }
+    return thread_project_surface(M, A, y, dist);
+}
+
+__device__ int thread_closest_sign(const MeshView &M, const AsmParams &A, float3 y, float &clear) {
+    float best = FLT_MAX;
+    int bt = 0x7fffffff, breg = 0;
+    float3 bcp = make_float3(0.f, 0.f, 0.f);
+    each_27_candidate(M, A, y, [&](int t) {
+        const size_t g = (size_t)(A.tri_off + t);
+        const float3 n = f3(M.geo[5 * g + 1]);
+        if (n.x == 0.f && n.y == 0.f && n.z == 0.f) return;   // degenerate
+        int reg;
+        const float3 cp = closest_on_triangle(y, f3(M.vx[3 * g]), f3(M.vx[3 * g + 1]), f3(M.vx[3 * g + 2]), reg);
+        const float3 w = y - cp;
+        const float dd = dot3(w, w);
+        if (dd < best || (dd == best && t < bt)) {
+            best = dd;
+            bt = t;
+            breg = reg;
+            bcp = cp;
+        }
+    });
+    const float blk = block_margin(A, y);
+    clear = fmaxf(fminf(bt == 0x7fffffff ? FLT_MAX : sqrtf(best), blk) * (1.f - 0x1p-10f) - A.dx * 0x1p-16f, 0.f);
+    if (bt == 0x7fffffff) return -1;
+    const size_t g = (size_t)(A.tri_off + bt);
+    const float3 psi = breg == 0 ? f3(M.geo[5 * g + 1]) : f3(M.pn[6 * g + breg - 1]);
+    return dot3(y - bcp, psi) <= 0.f ? 1 : 0;
+}
+
+__device__ inline bool thread_partner_ok(const MeshView &M, const AsmParams &Q, int rule, float3 x) {
+    if (rule == 0) return true;
+    float unused;
+    const int t = thread_closest_sign(M, Q, x, unused);
+    return rule == 1 ? t != 1 : t != 0;
+}
+
+// k_search_thread: one thread per queued particle; the warps stride over the
+// queue together so that the per-body max move is reduced once per warp
+__global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict__ pos_s,
+                                                       const uint32_t *__restrict__ id_s,
+                                                       const AsmParams *__restrict__ P, float4 *__restrict__ pos,
+                                                       int32_t *__restrict__ cons, MeshView M,
+                                                       uint32_t *__restrict__ maxdisp,
+                                                       const int4 *__restrict__ work,
+                                                       const uint32_t *__restrict__ work_count,
+                                                       float4 *__restrict__ cert) {
+    const uint32_t n = *work_count;
+    const uint32_t stride = gridDim.x * TPB;
+    for (uint32_t e0 = blockIdx.x * TPB + (threadIdx.x & ~31u); e0 < n; e0 += stride) {
+        const uint32_t e = e0 + (threadIdx.x & 31u);
+        int b = 0;
+        float disp = 0.f;
+        if (e < n) {
+            const int4 it = work[e];
+            const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
+            const float4 p = pos_s[it.x];
+            const int cls = cls_of(p.w);
+            b = body_of(p.w);
+            const AsmParams &A = P[b];
+            const uint32_t i = id_s[it.x];
+            float3 x = y;
+            int tri = -2;
+            float clear = 0.f;
+            bool ok;
+            if (cls == kClsS) {
+                float d;
+                tri = thread_surface_choice(M, A, y, A.cascade ? cons[i] : -1, d);
+                ok = tri >= 0;
+                if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
+            } else if (cls == kClsF) {
+                int cn = -1;
+                ok = project_feature(M, A, y, cons[i], x, cn);
+                tri = cn;
+            } else {
+                ok = thread_closest_sign(M, A, y, clear) != 0;
+            }
+            if (ok && A.partner >= 0)
+                ok = thread_partner_ok(M, P[A.partner], cls == kClsV ? A.partner_vol : A.partner_surf, x);
+            if (ok) {
+                pos[i] = make_float4(x.x, x.y, x.z, p.w);
+                if (tri >= 0) cons[i] = tri;
+                if (cls == kClsV && A.closed && A.partner_vol == 0) cert[i] = make_float4(y.x, y.y, y.z, clear);
+                const float3 w = x - f3(p);
+                disp = sqrtf(dot3(w, w));
+            }
+        }
+        labelled_max(maxdisp, b, disp);
+    }
+}
+
 // ---- diagnostics --------------------------------------------------------------
 __global__ void k_unpermute(const float4 *__restrict__ acc_s, const uint32_t *__restrict__ id_s, int64_t N,
                             float *__restrict__ acc, const int32_t *__restrict__ cnt_s, int32_t *__restrict__ cnt) {
@@ -997,8 +1145,12 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
                                          d.maxdisp, d.work, d.work_count, d.cert);
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
-    k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp, d.work,
-                                             d.work_count, d.cert);
+    if (g.search_thread)
+        k_search_thread<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh,
+                                                        d.maxdisp, d.work, d.work_count, d.cert);
+    else
+        k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp,
+                                                 d.work, d.work_count, d.cert);
     if (timed) {
         cudaEventRecordWithFlags(g.ev[g.ev_used + 4], s, flags);
         g.ev_used += kPhaseEvents;

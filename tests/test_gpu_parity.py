@@ -326,15 +326,16 @@ def test_batched_equals_plain_bit_exact():
         assert np.array_equal(x, y) and np.array_equal(c, d)
 
 
-@pytest.mark.parametrize("variant,block", [(0, 128), (1, 256)])
-def test_every_force_variant_gives_the_same_bits(variant, block):
+@pytest.mark.parametrize("variant,block,search", [(0, 128, 4), (1, 256, 4), (0, 128, 0), (1, 256, 0)])
+def test_every_force_variant_gives_the_same_bits(variant, block, search):
     # own ranges and the shared-row union accept the same neighbours into
-    # the same partial sums in the same order
+    # the same partial sums in the same order; the warp and the thread
+    # (search 0) forms of the triangle search make the same choices
     asm = small_sphere_torus(6)
     plain = [pkg.Body.from_assembly(a) for a in asm]
     batched = [pkg.Body.from_assembly(a) for a in asm]
     bt = pkg.Batch(batched)
-    bt.configure(variant, block, 4)
+    bt.configure(variant, block, search)
     bt.relax(4, use_graph=False)
     bt.store()
     for p in plain:
