@@ -83,22 +83,26 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
 __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restrict__ key_s,
                                                        const uint32_t *__restrict__ id_s,
                                                        const float4 *__restrict__ pos, int64_t N,
-                                                       float4 *__restrict__ pos_s, float *__restrict__ pos_p,
+                                                       float4 *__restrict__ pos_s, float4 *__restrict__ pos_p,
                                                        uint32_t *__restrict__ cells, uint8_t *__restrict__ slab,
                                                        const uint32_t *__restrict__ epoch) {
-    int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (k >= N) return;
-    const uint32_t f = key_s[k], c = f >> kSlabBits, sk = f & (kSlabs - 1);
-    const float4 q = pos[id_s[k]];
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const bool valid = k < N;
+    const float4 q = valid ? pos[id_s[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // slot-pair copy {x0, x1, y0, y1}, {z0, z1, w0, w1}: slots 2m and 2m + 1
+    // sit in neighbouring lanes, which swap their points and write one half
+    // each; past the last slot a lane holds a finite point of no class, the
+    // padding of an odd count
+    const float ox = __shfl_xor_sync(0xffffffffu, q.x, 1), oy = __shfl_xor_sync(0xffffffffu, q.y, 1);
+    const float oz = __shfl_xor_sync(0xffffffffu, q.z, 1), ow = __shfl_xor_sync(0xffffffffu, q.w, 1);
+    if ((k & 1) == 0) {
+        if (valid) pos_p[k] = make_float4(q.x, ox, q.y, oy);
+    } else if (k <= N) {
+        pos_p[k] = make_float4(oz, q.z, ow, q.w);
+    }
+    if (!valid) return;
     pos_s[k] = q;
-    // slot-pair copy {x0, x1, y0, y1, z0, z1, w0, w1}; an odd count pads the
-    // last pair with a finite point of no class
-    float *pp = pos_p + 8 * (k >> 1) + (k & 1);
-    pp[0] = q.x;
-    pp[2] = q.y;
-    pp[4] = q.z;
-    pp[6] = q.w;
-    if (k == N - 1 && (k & 1) == 0) pp[1] = pp[3] = pp[5] = pp[7] = 0.f;
+    const uint32_t f = key_s[k], c = f >> kSlabBits, sk = f & (kSlabs - 1);
     const bool first = k == 0 || (key_s[k - 1] >> kSlabBits) != c;
     const bool last = k == N - 1 || (key_s[k + 1] >> kSlabBits) != c;
     uint8_t *b = slab + 8 * (size_t)c;
@@ -1096,7 +1100,7 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
                                                                  d.maxdisp, d.B, d.work_count);
     int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
     k_gather_ranges<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s,
-                                                  reinterpret_cast<float *>(d.pos_p),
+                                                  d.pos_p,
                                                   reinterpret_cast<uint32_t *>(d.cells),
                                                   reinterpret_cast<uint8_t *>(d.slab), d.epoch);
     return buf;
