@@ -207,7 +207,7 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
 int Group::alloc_particles(int64_t N, std::string &err) {
     DevGroup &g = d;
     void *old[] = {g.pos,   g.cons,  g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s,
-                   g.pos_p, g.cert,  g.acc_s,  g.hist,   g.rho_s, g.work};
+                   g.pos_p, g.cert,  g.acc_s,  g.hist,   g.coef_s, g.work};
     for (void *p : old)
         if (p) cudaFree(p);
     g.N = N;
@@ -227,7 +227,7 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     CKA(cudaMalloc(&g.cert, sizeof(float4) * n1));
     CKA(cudaMemset(g.cert, 0, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.acc_s, sizeof(float4) * n1));
-    CKA(cudaMalloc(&g.rho_s, sizeof(float) * n1));
+    CKA(cudaMalloc(&g.coef_s, sizeof(float) * (n1 + 1)));
     CKA(cudaMalloc(&g.work, sizeof(int4) * n1));
     if (!g.work_count) {
         CKA(cudaMalloc(&g.work_count, sizeof(uint32_t)));
@@ -267,7 +267,7 @@ void Group::free_all() {
     ev.clear();
     DevGroup &g = d;
     void *ptrs[] = {g.params, g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
-                    g.acc_s, g.cells, g.slab, g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.rho_s, g.work, g.work_count};
+                    g.acc_s, g.cells, g.slab, g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.coef_s, g.work, g.work_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (owns_mesh) {

@@ -2,7 +2,8 @@
 // hand-written backward, with rho_i = W(0) + sum over masked neighbours of
 // W(r_ij) (the kernel sum that Eq. 15's pressure force equalises).
 //
-//   k_rho        rho in key order (masked, FP32) and E (FP64 atomics)
+//   k_rho        rho in key order (masked, FP32), kept as the coefficient
+//                2 (rho_k - W0_k) of mobile particles, and E (FP64 atomics)
 //   k_grad       dE/dx_k = sum_j dW/dr(r_kj) e_kj * coef, coef =
 //                2 (rho_k - W0_k) [j acts on k, k mobile] +
 //                2 (rho_j - W0_j) [k acts on j, j mobile]
@@ -11,6 +12,7 @@
 // energy_accel() turns -dE/dx into the acceleration of the limited step, so
 // the same step / projection kernel runs an energy-descent relaxation.
 #include <cfloat>
+#include <type_traits>
 
 #include "body.h"
 
@@ -30,54 +32,133 @@ __device__ inline float3 cross(float3 a, float3 b) {
 
 __device__ inline float w0_of(const AsmParams &A, int c) { return c == kClsS ? A.w0[0] : c == kClsV ? A.w0[1] : A.w0[2]; }
 
-// every slot j of the 3 x 3 grid rows around p that the reach cut keeps (a
-// superset of the particles within 2h of p), row by row, slots ascending
+// the classes that feel a particle of class c (its own mask is acts_on_bits)
+__device__ constexpr uint32_t felt_by_bits(int c) {
+    uint32_t m = 0u;
+    for (int t = 0; t <= kClsP; t++)
+        if (acts_on_bits(t) & class_bit(c)) m |= class_bit(t);
+    return m;
+}
+
+// The pair sums walk the same candidates as the force pass: per grid row of
+// the 3 x 3 rows around p, the slots that the reach cut keeps (a superset of
+// the particles within 2h), read two at a time from the slot-pair copy
+// ({x0, x1, y0, y1}, {z0, z1, w0, w1}) into packed FP32x2 operands.  The
+// first and last pair of a range may hold a slot outside it (EDGE), masked
+// out.  Weights use max(1 - r / 2h, 0), so a slot beyond 2h adds exactly 0
+// and one within rounding of 2h a term below 1e-18 of the largest.
 template <typename F>
-__device__ inline void for_rows(const float4 &p, const AsmParams &A, const uint4 *cells, const uint2 *slab,
-                                uint32_t ep, F &&f) {
+__device__ inline void for_row_ranges(const float4 &p, bool on, const AsmParams &A, const uint4 *cells,
+                                      const uint2 *slab, uint32_t ep, F &&f) {
     const int ny = A.ng_n[1], nz = A.ng_n[2];
     const GridPoint g = grid_point(A, p.x, p.y, p.z);
     const int cy = g.c[1], cz = g.c[2];
-    for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++) {
-        const float gz = row_gap(g.t[2], cz, z - cz, g.slack);
-        for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
-            const uint32_t row = A.key_base + (uint32_t)A.ng_n[0] * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-            uint32_t s, e;
-            row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, y - cy, g.slack), gz, row, s, e);
-            for (uint32_t j = s; j < e; j++) f(j);
+    for (int dz = -1; dz <= 1; dz++) {
+        const int z = cz + dz;
+        const float gz = row_gap(g.t[2], cz, dz, g.slack);
+        for (int dy = -1; dy <= 1; dy++) {
+            const int y = cy + dy;
+            uint32_t s = 0xffffffffu, e = 0u;
+            if (on && z >= 0 && z < nz && y >= 0 && y < ny) {
+                const uint32_t row = A.key_base + (uint32_t)A.ng_n[0] * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+                row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
+            }
+            f(s, e);
         }
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, int64_t N,
-                                             const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                             const uint2 *__restrict__ slab, const uint32_t *__restrict__ epoch,
-                                             float *__restrict__ rho_s,
+// the slot pairs [s >> 1, (e + 1) >> 1) of range [s, e): f(edge, m) with
+// edge true for the first and the last
+template <typename F>
+__device__ inline void for_pairs(uint32_t s, uint32_t e, F &&f) {
+    uint32_t m = s >> 1;
+    const uint32_t m1 = (e + 1) >> 1;
+    if (m >= m1) return;
+    f(std::true_type{}, m);
+    if (m + 1 >= m1) return;
+    for (m = m + 1; m + 1 < m1; m++) f(std::false_type{}, m);
+    f(std::true_type{}, m1 - 1);
+}
+
+struct PairGeo {
+    float2 dx, dy, dz, t;   // q - p per axis; max(1 - r / 2h, 0)
+    float2 r;
+    uint32_t w0, w1;        // class bits of the two slots
+};
+
+__device__ inline PairGeo pair_geo(const float4 *__restrict__ pos_p, uint32_t m, float2 npx, float2 npy, float2 npz,
+                                   float hih) {
+    const float4 A = pos_p[2 * (size_t)m], B = pos_p[2 * (size_t)m + 1];
+    PairGeo o;
+    o.dx = __fadd2_rn(make_float2(A.x, A.y), npx);
+    o.dy = __fadd2_rn(make_float2(A.z, A.w), npy);
+    o.dz = __fadd2_rn(make_float2(B.x, B.y), npz);
+    const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(o.dx, o.dx), __fmul2_rn(o.dy, o.dy)), __fmul2_rn(o.dz, o.dz));
+    o.r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
+    const float2 t = __ffma2_rn(o.r, make_float2(-hih, -hih), make_float2(1.f, 1.f));
+    o.t = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
+    o.w0 = __float_as_uint(B.z);
+    o.w1 = __float_as_uint(B.w);
+    return o;
+}
+
+// sum over the masked slots of (1 - q/2)^4 (1 + 2q), q = r / h, the particle
+// itself included (r = 0 gives exactly 1); ALL: every class acts on the lane
+template <bool ALL>
+__device__ inline void rho_range(const float4 *__restrict__ pos_p, uint32_t s, uint32_t e, float2 npx, float2 npy,
+                                 float2 npz, uint32_t mbits, float hih, float2 &acc) {
+    for_pairs(s, e, [&](auto edge, uint32_t m) {
+        constexpr bool EDGE = decltype(edge)::value;
+        const PairGeo g = pair_geo(pos_p, m, npx, npy, npz, hih);
+        const float2 t2 = __fmul2_rn(g.t, g.t);
+        const float2 poly = __ffma2_rn(g.r, make_float2(4.f * hih, 4.f * hih), make_float2(1.f, 1.f));
+        float2 w = __fmul2_rn(__fmul2_rn(t2, t2), poly);
+        bool k0 = !EDGE || 2 * m >= s, k1 = !EDGE || 2 * m + 1 < e;
+        if (!ALL) {
+            k0 = k0 && (mbits & g.w0) != 0u;
+            k1 = k1 && (mbits & g.w1) != 0u;
+        }
+        if (EDGE || !ALL) {
+            w.x = k0 ? w.x : 0.f;
+            w.y = k1 ? w.y : 0.f;
+        }
+        acc = __fadd2_rn(acc, w);
+    });
+}
+
+// k_rho: coef_s[k] = 2 (rho_k - W0_k) for mobile k in key order, else 0 (and
+// 0 in the padding slot N, read by the slot pairs of an odd count); E gets
+// the sum of (rho_k - W0_k)^2 (FP64 atomics)
+__global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
+                                             int64_t N, const AsmParams *__restrict__ P,
+                                             const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
+                                             const uint32_t *__restrict__ epoch, float *__restrict__ coef_s,
                                              double *__restrict__ E) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const bool active = k < N;
+    const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int cls = active ? cls_of(p.w) : kClsI;
+    const AsmParams &A = P[active ? body_of(p.w) : 0];
+    const bool mob = active && is_mobile(cls, A);
+    const uint32_t mbits = mob ? acts_on_bits(cls) : 0u;
+    const float hih = A.half_inv_h;
+    const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y), npz = make_float2(-p.z, -p.z);
+    const bool all_cls = __all_sync(0xffffffffu, mbits == 0u || mbits == 0x1Fu);
+    float2 acc = make_float2(0.f, 0.f);
+    for_row_ranges(p, mob, A, cells, slab, *epoch, [&](uint32_t s, uint32_t e) {
+        if (all_cls) rho_range<true>(pos_p, s, e, npx, npy, npz, mbits, hih, acc);
+        else rho_range<false>(pos_p, s, e, npx, npy, npz, mbits, hih, acc);
+    });
     double e = 0.0;
-    if (k < N) {
-        const float4 p = pos_s[k];
-        const int cls = cls_of(p.w);
-        const AsmParams &A = P[body_of(p.w)];
-        const uint32_t mbits = acts_on_bits(cls);
-        float rho = 0.f;
-        for_rows(p, A, cells, slab, *epoch, [&](uint32_t j) {
-            const float4 q = pos_s[j];
-            const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-            const float r2 = dist2_rn(dx, dy, dz);
-            if (r2 < A.R2 && (int64_t)j != k && (mbits & __float_as_uint(q.w)) != 0u) {
-                const float qh = sqrtf(r2) * A.half_inv_h;
-                const float t = 1.f - qh;
-                rho += t * t * t * t * (4.f * qh + 1.f);
-            }
-        });
-        rho = A.alpha * (rho + 1.f);
-        rho_s[k] = rho;
-        if (is_mobile(cls, A)) {
-            const double d = (double)rho - (double)w0_of(A, cls);
-            e = d * d;
-        }
+    if (mob) {
+        const float rho = A.alpha * (acc.x + acc.y);
+        const float d = rho - w0_of(A, cls);
+        coef_s[k] = 2.f * d;
+        const double dd = (double)rho - (double)w0_of(A, cls);
+        e = dd * dd;
+    } else if (k <= N) {
+        coef_s[k] = 0.f;
     }
     if (E) {
         for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -85,49 +166,67 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, i
     }
 }
 
+// sum over the slots of (1 - q/2)^3 c_kj (q - p), c_kj = ek [j acts on k] +
+// coef_j [k acts on j]; ALLV: the lane is a volume particle (every class acts
+// on it, only volume particles feel it)
+template <bool ALLV>
+__device__ inline void grad_range(const float4 *__restrict__ pos_p, const float2 *__restrict__ coef2, uint32_t s,
+                                  uint32_t e, float2 npx, float2 npy, float2 npz, uint32_t bk, uint32_t fk, float ek,
+                                  float hih, float2 &gx, float2 &gy, float2 &gz) {
+    for_pairs(s, e, [&](auto edge, uint32_t m) {
+        constexpr bool EDGE = decltype(edge)::value;
+        const PairGeo g = pair_geo(pos_p, m, npx, npy, npz, hih);
+        const float2 c = coef2[m];
+        float2 cf;
+        if (ALLV) {
+            cf.x = ek + ((g.w0 & class_bit(kClsV)) ? c.x : 0.f);
+            cf.y = ek + ((g.w1 & class_bit(kClsV)) ? c.y : 0.f);
+        } else {
+            cf.x = ((bk & g.w0) ? ek : 0.f) + ((fk & g.w0) ? c.x : 0.f);
+            cf.y = ((bk & g.w1) ? ek : 0.f) + ((fk & g.w1) ? c.y : 0.f);
+        }
+        if (EDGE) {
+            cf.x = 2 * m >= s ? cf.x : 0.f;
+            cf.y = 2 * m + 1 < e ? cf.y : 0.f;
+        }
+        const float2 w = __fmul2_rn(__fmul2_rn(__fmul2_rn(g.t, g.t), g.t), cf);
+        gx = __ffma2_rn(w, g.dx, gx);
+        gy = __ffma2_rn(w, g.dy, gy);
+        gz = __ffma2_rn(w, g.dz, gz);
+    });
+}
+
 // out_s[k] = sign * dE/dx_k in key order; amax (nullable) gets the largest
-// |out| per body over mobile particles
-__global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, int64_t N,
-                                              const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                              const uint2 *__restrict__ slab, const uint32_t *__restrict__ epoch,
-                                              const float *__restrict__ rho_s,
+// |out| per body over mobile particles (and out is 0 for the others)
+__global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
+                                              int64_t N, const AsmParams *__restrict__ P,
+                                              const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
+                                              const uint32_t *__restrict__ epoch, const float *__restrict__ coef_s,
                                               float sign, float4 *__restrict__ out_s, uint32_t *__restrict__ amax) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int ck = cls_of(p.w);
-    const int b = active ? body_of(p.w) : 0;
-    const AsmParams &A = P[b];
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    if (active) {
-        const bool mk = is_mobile(ck, A);
-        const float ek = mk ? 2.f * (rho_s[k] - w0_of(A, ck)) : 0.f;
-        const uint32_t bk = acts_on_bits(ck);
-        for_rows(p, A, cells, slab, *epoch, [&](uint32_t j) {
-            const float4 q = pos_s[j];
-            const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-            const float r2 = dist2_rn(dx, dy, dz);
-            if (!(r2 < A.R2) || (int64_t)j == k) return;
-            const int cj = cls_of(q.w);
-            float coef = 0.f;
-            if (mk && (bk & class_bit(cj)) != 0u) coef += ek;
-            if (is_mobile(cj, A) && (acts_on_bits(cj) & class_bit(ck)) != 0u) coef += 2.f * (rho_s[j] - w0_of(A, cj));
-            if (coef == 0.f) return;
-            const float t = 1.f - sqrtf(r2) * A.half_inv_h;
-            const float w = -A.force_scale * t * t * t * coef;   // dW/dr / r * coef
-            gx += w * dx;
-            gy += w * dy;
-            gz += w * dz;
-        });
-    }
-    gx *= sign;
-    gy *= sign;
-    gz *= sign;
+    const int ck = active ? cls_of(p.w) : kClsI;
+    const AsmParams &A = P[active ? body_of(p.w) : 0];
+    const bool mk = active && is_mobile(ck, A);
+    const float ek = mk ? coef_s[k] : 0.f;
+    const uint32_t bk = mk ? acts_on_bits(ck) : 0u, fk = felt_by_bits(ck);
+    const float hih = A.half_inv_h;
+    const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y), npz = make_float2(-p.z, -p.z);
+    const float2 *coef2 = reinterpret_cast<const float2 *>(coef_s);
+    const bool allv = __all_sync(0xffffffffu, !active || ck == kClsV);
+    float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+    for_row_ranges(p, active, A, cells, slab, *epoch, [&](uint32_t s, uint32_t e) {
+        if (allv) grad_range<true>(pos_p, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
+        else grad_range<false>(pos_p, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
+    });
+    const float sc = sign * A.force_scale;
+    float fx = (gx.x + gx.y) * sc, fy = (gy.x + gy.y) * sc, fz = (gz.x + gz.y) * sc;
     float mag = 0.f;
-    if (amax && active && !is_mobile(ck, A)) gx = gy = gz = 0.f;
+    if (amax && !mk) fx = fy = fz = 0.f;
     if (active) {
-        mag = sqrtf(gx * gx + gy * gy + gz * gz);
-        out_s[k] = make_float4(gx, gy, gz, mag);
+        mag = sqrtf(fx * fx + fy * fy + fz * fz);
+        out_s[k] = make_float4(fx, fy, fz, mag);
     }
     if (amax) {
         const int slot = A.amax_slot;
@@ -211,9 +310,10 @@ __global__ void k_vjp(const float4 *__restrict__ gx_s, const uint32_t *__restric
 
 void energy_accel(Group &g, cudaStream_t s) {
     DevGroup &d = g.d;
-    k_rho<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, nullptr);
-    k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, -1.f, d.acc_s,
-                                        d.amax);
+    k_rho<<<nblocks(d.N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s,
+                                            nullptr);
+    k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s, -1.f,
+                                        d.acc_s, d.amax);
 }
 
 int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
@@ -234,11 +334,11 @@ int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, 
     d.pos = xs;
     int buf = build_grid(g, s);
     d.pos = saved;
-    k_rho<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, dE);
+    k_rho<<<nblocks(d.N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s, dE);
     if (gy || gV) {
         if (gV) cudaMemsetAsync(gV, 0, sizeof(float) * 3 * (size_t)b.nv, s);
-        k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.slab, d.epoch, d.rho_s, 1.f, d.acc_s,
-                                             nullptr);
+        k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s,
+                                             1.f, d.acc_s, nullptr);
         k_vjp<<<nblocks(d.N), TPB, 0, s>>>(d.acc_s, d.id[buf], d.N, y_dev, d.pos, d.cons, V, b.d_tris, gy, gV);
     }
     cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, s);

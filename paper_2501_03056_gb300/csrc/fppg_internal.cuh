@@ -149,7 +149,7 @@ struct DevGroup {
     uint32_t *drank = nullptr, *coff = nullptr;
     int32_t *cand = nullptr;
     // energy scratch
-    float *rho_s = nullptr;
+    float *coef_s = nullptr;
 };
 
 // ---- small device helpers ------------------------------------------------
@@ -158,6 +158,14 @@ struct DevGroup {
 __device__ inline int cls_of(float w) { return __ffs(__float_as_uint(w) & 0xffu) - 1; }
 
 __host__ __device__ constexpr uint32_t class_bit(int c) { return 1u << c; }
+
+// the approximate square-root instruction: relative error of a few 2^-23,
+// exactly 0 at 0
+__device__ inline float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 __device__ inline int body_of(float w) { return (int)(__float_as_uint(w) >> 8); }
 

@@ -145,13 +145,8 @@ __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restric
 // partial sum, in the same order, in every variant.
 // COUNT adds, per particle, the accepted neighbours (self excluded) and the
 // slots of its own ranges (candidates tested).
-// r = sqrt(r^2) by the approximate square-root instruction (relative error
-// of a few 2^-23; exactly 0 at 0, so the particle itself needs no guard)
-__device__ inline float sqrt_approx(float x) {
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+// r = sqrt(r^2) by sqrt_approx (exactly 0 at 0, so the particle itself
+// needs no guard)
 
 struct PairAcc {
     float2 ax, ay, az;
