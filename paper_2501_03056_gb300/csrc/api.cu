@@ -449,12 +449,12 @@ int fppg_debug_forces(fppg_ctx *ctx, float *acc_host, int32_t *count_host, float
 
 int fppg_debug_search(fppg_ctx *ctx, int64_t *queued, int32_t *closed) {
     if (!ctx) return FPPG_ERR_ARG;
-    uint32_t q = 0;
+    uint32_t q[2] = {0u, 0u};
     if (ctx->group.d.work_count) {
-        CUDA_OR(ctx->err, cudaMemcpyAsync(&q, ctx->group.d.work_count, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_OR(ctx->err, cudaMemcpyAsync(q, ctx->group.d.work_count, sizeof(q), cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
     }
-    if (queued) *queued = q;
+    if (queued) *queued = (int64_t)q[0] + q[1];
     if (closed) *closed = ctx->body.closed ? 1 : 0;
     return FPPG_OK;
 }

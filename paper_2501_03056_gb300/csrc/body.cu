@@ -230,8 +230,8 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     CKA(cudaMalloc(&g.coef_s, sizeof(float) * (n1 + 1)));
     CKA(cudaMalloc(&g.work, sizeof(int4) * n1));
     if (!g.work_count) {
-        CKA(cudaMalloc(&g.work_count, sizeof(uint32_t)));
-        CKA(cudaMemset(g.work_count, 0, sizeof(uint32_t)));
+        CKA(cudaMalloc(&g.work_count, 2 * sizeof(uint32_t)));
+        CKA(cudaMemset(g.work_count, 0, 2 * sizeof(uint32_t)));
     }
     CKA(cudaMalloc(&g.hist, sizeof(uint32_t) * kMaxDigits * (size_t)g.n_tiles));
     if (!g.totals) CKA(cudaMalloc(&g.totals, sizeof(uint32_t) * kMaxDigits));

@@ -33,7 +33,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // byte offsets inside the scratch array
 constexpr size_t kOffParams = 0;
-constexpr size_t kOffFlags = kOffParams + align256(sizeof(AsmParams));        // epoch, amax, maxdisp, queue, error
+constexpr size_t kOffFlags = kOffParams + align256(sizeof(AsmParams));        // epoch, amax, maxdisp, queue (2), error
 constexpr size_t kOffTotals = kOffFlags + 256;
 constexpr size_t kOffHist = kOffTotals + align256(kMaxDigits * 4);
 constexpr size_t kOffPos = kOffHist + align256(kMaxDigits * 4 * kStaticMaxTiles);
@@ -162,10 +162,10 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     d.epoch = flags + 0;
     d.amax = flags + 1;
     d.maxdisp = flags + 2;
-    d.work_count = flags + 3;
+    d.work_count = flags + 3;   // two words: front and back of the search queue
     d.hist = (uint32_t *)(base + kOffHist);
     d.totals = (uint32_t *)(base + kOffTotals);
-    uint32_t *error = flags + 4;
+    uint32_t *error = flags + 5;
     // the error word and amax start at zero on every call; the cell table
     // needs no clearing (entries are valid only for the current epoch)
     if (cudaMemcpyAsync(d.params, &A, sizeof(A), cudaMemcpyHostToDevice, s) != cudaSuccess ||

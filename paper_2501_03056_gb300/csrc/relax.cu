@@ -40,11 +40,12 @@ __device__ inline uint32_t lanemask_lt() {
     return m;
 }
 
-// max of v over the lanes that share `label`, added to dst[label] by one lane
+// max of v (>= 0) over the lanes that share `label`, added to dst[label] by
+// one lane (dst starts every iteration at 0, so a max of 0 needs no atomic)
 __device__ inline void labelled_max(uint32_t *dst, int label, float v) {
     uint32_t peers = __match_any_sync(0xffffffffu, label);
     uint32_t m = __reduce_max_sync(peers, __float_as_uint(v));
-    if ((uint32_t)(__ffs(peers) - 1) == (threadIdx.x & 31u)) atomicMax(dst + label, m);
+    if ((uint32_t)(__ffs(peers) - 1) == (threadIdx.x & 31u) && m) atomicMax(dst + label, m);
 }
 
 // ---- A1 ----------------------------------------------------------------------
@@ -60,7 +61,8 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
     }
     if (i == 0) {
         epoch[0] += 1u;
-        *work_count = 0u;
+        work_count[0] = 0u;
+        work_count[1] = 0u;
     }
     if (i >= N) return;
     float4 p = pos[i];
@@ -747,18 +749,31 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             }                                // S with nothing near: revert
         }
     }
-    // warp-aggregated append to the search queue
-    const uint32_t m = __ballot_sync(0xffffffffu, queue);
-    if (m) {
-        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(work_count, (uint32_t)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (queue)
-            work[base + __popc(m & lanemask_lt())] =
-                make_int4((int)k, __float_as_int(y.x), __float_as_int(y.y), __float_as_int(y.z));
+    // warp-aggregated append to the search queue: surface and feature
+    // particles from the front (count work_count[0]), volume particles from
+    // the back (work_count[1]), so that a warp of the thread-per-particle
+    // search meets one kind of test
+    const bool qv = queue && cls == kClsV, qs = queue && cls != kClsV;
+    const uint32_t ms = __ballot_sync(0xffffffffu, qs), mv = __ballot_sync(0xffffffffu, qv);
+    if (ms | mv) {
+        const int lane = threadIdx.x & 31;
+        const int ls = ms ? __ffs(ms) - 1 : 0, lv = mv ? __ffs(mv) - 1 : 0;
+        uint32_t bs = 0u, bv = 0u;
+        if (ms && lane == ls) bs = atomicAdd(work_count, (uint32_t)__popc(ms));
+        if (mv && lane == lv) bv = atomicAdd(work_count + 1, (uint32_t)__popc(mv));
+        bs = __shfl_sync(0xffffffffu, bs, ls);
+        bv = __shfl_sync(0xffffffffu, bv, lv);
+        const int4 it = make_int4((int)k, __float_as_int(y.x), __float_as_int(y.y), __float_as_int(y.z));
+        if (qs) work[bs + __popc(ms & lanemask_lt())] = it;
+        if (qv) work[N - 1 - (int64_t)(bv + __popc(mv & lanemask_lt()))] = it;
     }
     labelled_max(maxdisp, b, disp);
+}
+
+// entry e of the two-ended search queue: the nf front entries first, then
+// the back ones from slot N - 1 downwards
+__device__ inline int4 queue_entry(const int4 *__restrict__ work, uint32_t nf, int64_t N, uint32_t e) {
+    return e < nf ? work[e] : work[N - 1 - (int64_t)(e - nf)];
 }
 
 // k_search: one warp per queued particle (grid-stride over the queue):
@@ -769,14 +784,19 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
                                                 const AsmParams *__restrict__ P, float4 *__restrict__ pos,
                                                 int32_t *__restrict__ cons, MeshView M,
                                                 uint32_t *__restrict__ maxdisp, const int4 *__restrict__ work,
-                                                const uint32_t *__restrict__ work_count, float4 *__restrict__ cert) {
+                                                const uint32_t *__restrict__ work_count, int64_t N,
+                                                float4 *__restrict__ cert) {
     __shared__ int32_t sbuf[TPB / 32][kSearchBuf];
     int32_t *buf = sbuf[threadIdx.x / 32];
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (TPB / 32);
-    const uint32_t n = *work_count;
+    const uint32_t nf = work_count[0], n = nf + work_count[1];
+    // lane 0's running max move of body run_b, added when the body changes
+    // (the queue is in key order, so a warp meets few bodies)
+    int run_b = -1;
+    uint32_t run = 0u;
     for (uint32_t e = (blockIdx.x * TPB + threadIdx.x) / 32; e < n; e += warps) {
-        const int4 it = work[e];
+        const int4 it = queue_entry(work, nf, N, e);
         const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
         const float4 p = pos_s[it.x];
         const int cls = cls_of(p.w), b = body_of(p.w);
@@ -812,9 +832,15 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             if (tri >= 0) cons[i] = tri;
             if (cls == kClsV && A.closed && A.partner_vol == 0) cert[i] = make_float4(y.x, y.y, y.z, clear);
             const float3 w = x - f3(p);
-            atomicMax(maxdisp + b, __float_as_uint(sqrtf(dot3(w, w))));
+            if (b != run_b) {
+                if (run) atomicMax(maxdisp + run_b, run);
+                run_b = b;
+                run = 0u;
+            }
+            run = max(run, __float_as_uint(sqrtf(dot3(w, w))));
         }
     }
+    if (lane == 0 && run) atomicMax(maxdisp + run_b, run);
 }
 
 // ---- the same search, one thread per queued particle --------------------------
@@ -919,16 +945,16 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
                                                        int32_t *__restrict__ cons, MeshView M,
                                                        uint32_t *__restrict__ maxdisp,
                                                        const int4 *__restrict__ work,
-                                                       const uint32_t *__restrict__ work_count,
+                                                       const uint32_t *__restrict__ work_count, int64_t N,
                                                        float4 *__restrict__ cert) {
-    const uint32_t n = *work_count;
+    const uint32_t nf = work_count[0], n = nf + work_count[1];
     const uint32_t stride = gridDim.x * TPB;
     for (uint32_t e0 = blockIdx.x * TPB + (threadIdx.x & ~31u); e0 < n; e0 += stride) {
         const uint32_t e = e0 + (threadIdx.x & 31u);
         int b = 0;
         float disp = 0.f;
         if (e < n) {
-            const int4 it = work[e];
+            const int4 it = queue_entry(work, nf, N, e);
             const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
             const float4 p = pos_s[it.x];
             const int cls = cls_of(p.w);
@@ -1146,10 +1172,10 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
     if (g.search_thread)
         k_search_thread<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh,
-                                                        d.maxdisp, d.work, d.work_count, d.cert);
+                                                        d.maxdisp, d.work, d.work_count, d.N, d.cert);
     else
         k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp,
-                                                 d.work, d.work_count, d.cert);
+                                                 d.work, d.work_count, d.N, d.cert);
     if (timed) {
         cudaEventRecordWithFlags(g.ev[g.ev_used + 4], s, flags);
         g.ev_used += kPhaseEvents;
