@@ -234,7 +234,7 @@ def main():
         batch.configure(v, tb, sc)
         tuned = {"force_variant": v, "force_block": tb, "search_ctas_per_sm": sc, "fixed": True}
     else:
-        tuned = None if args.no_autotune else batch.autotune(5)
+        tuned = None if args.no_autotune else batch.autotune(G)   # trials as long as a timed step
     batch.set_graph_iters(G)
     clocks = Clocks(local)
     clocks.start()
@@ -302,7 +302,7 @@ def main():
                     b.set_constraints(cons)
 
             cbt = pkg.Batch(cb, stream=stream)
-            ctuned = cbt.autotune(2)
+            ctuned = cbt.autotune(G)
             cbt.set_graph_iters(G)
             t_b, t_p = [], []
             for _ in range(steps + 1):
@@ -408,7 +408,7 @@ def main():
                 b.set_constraints(cons)
 
         bb = pkg.Batch(bbodies, stream=stream)
-        btuned = bb.autotune(3)
+        btuned = bb.autotune(G)
         bb.set_graph_iters(G)
         kb = 3
         ms_bb, ms_bp = [], []
