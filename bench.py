@@ -38,7 +38,7 @@ SMS, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 # (dx = 0.02), from the ncu capture summarised in
 # profiles/k_force_icosphere_torus_dx002.md; None for other workloads and
 # until the current kernel has been captured.
-K_FORCE_DRAM_BYTES = {0.02: 26609920 + 26368}
+K_FORCE_DRAM_BYTES = {0.02: 26610432 + 24832}
 
 
 def parse():
