@@ -172,7 +172,7 @@ def run_reference(args):
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"icosphere_l5+torus_256x64 dx={args.dx}", "bodies": 2, "particles": n,
-                   "iterations_per_step": 1},
+                   "iterations_per_step": 1, "form": "FP64 CPU oracle, one iteration per step (bounded sample)"},
         "cpu_baseline": {"value": value, "unit": "particle-iterations/s", "cores": oracle.get_threads(),
                          "kind": "oracle", "sample": "one FP64 iteration of both bodies per step"},
         "e2e": {"value": value, "unit": "particle-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -464,12 +464,13 @@ def main():
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     useful_gbs = 56.0 * value / world / 1e9
     line = {
-        "metric": "relaxation particle-iterations/s (batched + CUDA graph)",
+        "metric": "relaxation particle-iterations/s",
         "value": value, "unit": "particle-iterations/s", "n_gpus": world, "steps": K, "warmup": Wm,
         "ms_per_step": tot_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"icosphere_l5+torus_256x64 dx={args.dx}", "bodies": len(asm), "particles": n,
-                   "iterations_per_step": G, "l2": "flushed between steps (256 MiB write), working set < L2"},
+                   "iterations_per_step": G, "form": "batched + CUDA graph",
+                   "l2": "flushed between steps (256 MiB write), working set < L2"},
         "roofline": {"bound": "alu", "kernel": "k_force", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": K_FORCE_DRAM_BYTES.get(round(args.dx, 6)),
