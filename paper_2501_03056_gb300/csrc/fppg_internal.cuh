@@ -134,8 +134,8 @@ struct DevGroup {
     uint32_t *epoch = nullptr;
     uint32_t *amax = nullptr;
     uint32_t *maxdisp = nullptr;
-    int4 *work = nullptr;          // search queue {key slot, trial point}
-    uint32_t *work_count = nullptr;
+    int4 *work = nullptr;          // search queue {key slot, trial point}, N entries
+    uint32_t *work_count = nullptr; // [0] entries from the front (S, F), [1] from the back (V)
     uint32_t *hist = nullptr;  // kMaxDigits * n_tiles
     uint32_t *totals = nullptr; // kMaxDigits
     // mesh
