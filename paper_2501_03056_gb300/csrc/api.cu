@@ -29,6 +29,13 @@ struct fppg_ctx {
     fppg_ctx *partner = nullptr;   // Boolean partner (fppg_boolean)
     int bool_op = 0;               // FPPG_UNION, FPPG_DIFFERENCE or FPPG_INTERSECTION
     bool bool_first = false;       // the first operand of the operation
+    // device staging of the host particle arrays of set / get, kept between
+    // calls (both synchronise the stream before they return)
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    ~fppg_ctx() {
+        if (stage) cudaFree(stage);
+    }
 };
 
 struct fppg_batch {
@@ -96,6 +103,22 @@ MeshView view_of(const Body &b) {
 }
 
 // (re)build the single-body group of a context
+// the staging buffer of ctx with at least `bytes` bytes
+int stage_buf(fppg_ctx *ctx, size_t bytes, void **out) {
+    if (bytes > ctx->stage_bytes) {
+        if (ctx->stage) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->stage);
+            ctx->stage = nullptr;
+            ctx->stage_bytes = 0;
+        }
+        CUDA_OR(ctx->err, cudaMalloc(&ctx->stage, bytes));
+        ctx->stage_bytes = bytes;
+    }
+    *out = ctx->stage;
+    return FPPG_OK;
+}
+
 int ctx_group(fppg_ctx *c) {
     Group &g = c->group;
     g.d.B = 1;
@@ -241,18 +264,17 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
     }
     ctx->n = n;
     ctx->cls_host.assign(cls_host, cls_host + n);
-    float *dx = nullptr;
-    int32_t *dc = nullptr;
-    CUDA_OR(ctx->err, cudaMalloc(&dx, sizeof(float) * 3 * (size_t)std::max<int64_t>(n, 1)));
-    CUDA_OR(ctx->err, cudaMalloc(&dc, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
     if (n > 0) {
+        void *st = nullptr;
+        int r = stage_buf(ctx, 16 * (size_t)n, &st);
+        if (r) return r;
+        float *dx = (float *)st;
+        int32_t *dc = (int32_t *)(dx + 3 * n);
         CUDA_OR(ctx->err, cudaMemcpyAsync(dx, xyz_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
         CUDA_OR(ctx->err, cudaMemcpyAsync(dc, cls_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
         k_pack<<<nb(n), 256, 0, ctx->stream>>>(dx, dc, n, 0, g.d.pos, g.d.cons);
     }
     CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
-    cudaFree(dx);
-    cudaFree(dc);
     ctx->has_particles = true;
     return ctx_group(ctx);
 }
@@ -345,12 +367,13 @@ int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_
     const int64_t m = std::min(cap, ctx->n);
     if (m <= 0) return FPPG_OK;
     if (xyz_host) {
-        float *dx = nullptr;
-        CUDA_OR(ctx->err, cudaMalloc(&dx, sizeof(float) * 3 * (size_t)ctx->n));
+        void *st = nullptr;
+        int r = stage_buf(ctx, 12 * (size_t)ctx->n, &st);
+        if (r) return r;
+        float *dx = (float *)st;
         k_unpack<<<nb(ctx->n), 256, 0, ctx->stream>>>(ctx->group.d.pos, ctx->n, dx);
         CUDA_OR(ctx->err, cudaMemcpyAsync(xyz_host, dx, sizeof(float) * 3 * m, cudaMemcpyDeviceToHost, ctx->stream));
         CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
-        cudaFree(dx);
     }
     if (cons_host)
         CUDA_OR(ctx->err, cudaMemcpyAsync(cons_host, ctx->group.d.cons, sizeof(int32_t) * m, cudaMemcpyDeviceToHost,
