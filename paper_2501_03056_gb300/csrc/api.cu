@@ -253,10 +253,17 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
     if (!ctx) return FPPG_ERR_ARG;
     if (n < 0 || n > (int64_t)1 << 31) return fail(ctx->err, FPPG_ERR_ARG, "particle count out of range");
     if (n > 0 && (!xyz_host || !cls_host)) return fail(ctx->err, FPPG_ERR_ARG, "NULL particle buffer");
-    for (int64_t i = 0; i < n; i++)
-        if (cls_host[i] < 0 || cls_host[i] > 4) return fail(ctx->err, FPPG_ERR_ARG, "class outside 0..4");
-    for (int64_t i = 0; i < 3 * n; i++)
-        if (!std::isfinite(xyz_host[i])) return fail(ctx->err, FPPG_ERR_ARG, "non-finite coordinate");
+    // branch-free scans (they vectorise): a class outside 0..4, an exponent
+    // field of all ones (inf or NaN)
+    uint32_t bad_cls = 0u, bad_xyz = 0u;
+    for (int64_t i = 0; i < n; i++) bad_cls |= (uint32_t)((uint32_t)cls_host[i] > 4u);
+    for (int64_t i = 0; i < 3 * n; i++) {
+        uint32_t b;
+        memcpy(&b, xyz_host + i, sizeof(b));
+        bad_xyz |= (uint32_t)((b & 0x7f800000u) == 0x7f800000u);
+    }
+    if (bad_cls) return fail(ctx->err, FPPG_ERR_ARG, "class outside 0..4");
+    if (bad_xyz) return fail(ctx->err, FPPG_ERR_ARG, "non-finite coordinate");
     Group &g = ctx->group;
     if (n != g.d.N || !g.d.pos) {
         int r = g.alloc_particles(n, ctx->err);

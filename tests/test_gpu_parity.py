@@ -400,7 +400,11 @@ def test_edge_cases():
     with pytest.raises(pkg.FPPGError):
         b.set_particles(np.array([[np.nan, 0, 0]], np.float32), np.array([0], np.int32))
     with pytest.raises(pkg.FPPGError):
+        b.set_particles(np.array([[0, -np.inf, 0]], np.float32), np.array([0], np.int32))
+    with pytest.raises(pkg.FPPGError):
         b.set_particles(one, np.array([7], np.int32))
+    with pytest.raises(pkg.FPPGError):
+        b.set_particles(one, np.array([-1], np.int32))
     # far outside the grid: clamped to a boundary cell, keys still exact
     far = np.array([[50, 50, 50], [-50, 0, 0], [0.2, 0.2, 0.2]], np.float32)
     b.set_particles(far, np.full(3, W.CLS_V, np.int32))
