@@ -206,8 +206,8 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
 
 int Group::alloc_particles(int64_t N, std::string &err) {
     DevGroup &g = d;
-    void *old[] = {g.pos,   g.cons,  g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s,
-                   g.pos_p, g.cert,  g.acc_s,  g.hist,   g.coef_s, g.work};
+    void *old[] = {g.pos,   g.cons,  g.cons_s, g.key[0], g.key[1], g.id[0], g.id[1],
+                   g.pos_s, g.pos_p, g.cert,   g.acc_s,  g.hist,   g.coef_s, g.work};
     for (void *p : old)
         if (p) cudaFree(p);
     g.N = N;
@@ -218,6 +218,7 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     g.passes = radix_pass_plan(g.key_bits, &digit_bits);
     CKA(cudaMalloc(&g.pos, sizeof(float4) * n1));
     CKA(cudaMalloc(&g.cons, sizeof(int32_t) * n1));
+    CKA(cudaMalloc(&g.cons_s, sizeof(int32_t) * n1));
     for (int k = 0; k < 2; k++) {
         CKA(cudaMalloc(&g.key[k], sizeof(uint32_t) * n1));
         CKA(cudaMalloc(&g.id[k], sizeof(uint32_t) * n1));
@@ -266,7 +267,7 @@ void Group::free_all() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     ev.clear();
     DevGroup &g = d;
-    void *ptrs[] = {g.params, g.pos, g.cons, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
+    void *ptrs[] = {g.params, g.pos, g.cons, g.cons_s, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
                     g.acc_s, g.cells, g.slab, g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.coef_s, g.work, g.work_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -123,6 +123,7 @@ struct DevGroup {
     // particles
     float4 *pos = nullptr;
     int32_t *cons = nullptr;
+    int32_t *cons_s = nullptr;   // cons in key order, gathered with the positions (null: not gathered)
     uint32_t *key[2] = {nullptr, nullptr};
     uint32_t *id[2] = {nullptr, nullptr};
     float4 *pos_s = nullptr;

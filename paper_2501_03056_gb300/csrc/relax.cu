@@ -87,10 +87,15 @@ __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restric
                                                        const float4 *__restrict__ pos, int64_t N,
                                                        float4 *__restrict__ pos_s, float4 *__restrict__ pos_p,
                                                        uint32_t *__restrict__ cells, uint8_t *__restrict__ slab,
-                                                       const uint32_t *__restrict__ epoch) {
+                                                       const uint32_t *__restrict__ epoch,
+                                                       const int32_t *__restrict__ cons,
+                                                       int32_t *__restrict__ cons_s) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool valid = k < N;
-    const float4 q = valid ? pos[id_s[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t id = valid ? id_s[k] : 0u;
+    const float4 q = valid ? pos[id] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // the constraint ids in key order too, for the step
+    if (valid && cons_s) cons_s[k] = cons[id];
     // slot-pair copy {x0, x1, y0, y1}, {z0, z1, w0, w1}: slots 2m and 2m + 1
     // sit in neighbouring lanes, which swap their points and write one half
     // each; past the last slot a lane holds a finite point of no class, the
@@ -670,7 +675,8 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
                                               const AsmParams *__restrict__ P, const uint32_t *__restrict__ amax,
                                               float4 *__restrict__ pos, int32_t *__restrict__ cons, MeshView M,
                                               uint32_t *__restrict__ maxdisp, int4 *__restrict__ work,
-                                              uint32_t *__restrict__ work_count, const float4 *__restrict__ cert) {
+                                              uint32_t *__restrict__ work_count, const float4 *__restrict__ cert,
+                                              const int32_t *__restrict__ cons_s) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -686,7 +692,7 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
         const float sc = am > 0.f ? A.step_h / am : 0.f;     // dt^2 with dt = 0.25 sqrt(h / amax)
         const float4 a = acc_s[k];
         float3 dr = make_float3(a.x * sc, a.y * sc, a.z * sc);
-        const int c = cons[i];
+        const int c = cons_s[k];
         if (cls == kClsS && c >= 0) {
             const float3 n = f3(M.geo[5 * (size_t)(A.tri_off + c) + 1]);
             dr = dr - dot3(dr, n) * n;
@@ -1123,7 +1129,7 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
     k_gather_ranges<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s,
                                                   d.pos_p,
                                                   reinterpret_cast<uint32_t *>(d.cells),
-                                                  reinterpret_cast<uint8_t *>(d.slab), d.epoch);
+                                                  reinterpret_cast<uint8_t *>(d.slab), d.epoch, d.cons, d.cons_s);
     return buf;
 }
 
@@ -1168,7 +1174,7 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     else forces(g, s, count_dbg);
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 2], s, flags);
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
-                                         d.maxdisp, d.work, d.work_count, d.cert);
+                                         d.maxdisp, d.work, d.work_count, d.cert, d.cons_s);
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
     if (g.search_thread)
         k_search_thread<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh,
