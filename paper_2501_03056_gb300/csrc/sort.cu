@@ -226,22 +226,28 @@ int radix_sort_db(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int 
     return radix_passes<K, 4, DB>(keys, vals, iota_vals, n, passes, hist, totals, s);
 }
 
+// once per key type and process (thread-safe static initialisation): the
+// downsweeps' shared-memory limits on the current device and its SM count
+template <typename K>
+int sort_setup_sms() {
+    static const int sms = [] {
+        set_smem_attr<K, 4, 8>();
+        set_smem_attr<K, 8, 8>();
+        set_smem_attr<K, 16, 8>();
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 152;
+        return v;
+    }();
+    return sms;
+}
+
 template <typename K>
 int radix_sort_impl(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                     uint32_t *totals, cudaStream_t s) {
     if (n <= 0) return 0;
-    static bool attr_done = false;
-    static int sms = 0;
-    if (!attr_done) {
-        set_smem_attr<K, 4, 8>();
-        set_smem_attr<K, 8, 8>();
-        set_smem_attr<K, 16, 8>();
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-        attr_done = true;
-    }
+    const int sms = sort_setup_sms<K>();
     int db = 8;
     const int passes = radix_pass_plan(bits, &db);
     return radix_sort_db<K, 8>(keys, vals, iota_vals, n, passes, hist, totals, s, sms);
