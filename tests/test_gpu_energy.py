@@ -64,7 +64,7 @@ def test_autograd_function():
     E = uniformity_energy(y, v, b)
     (2.0 * E).backward()
     Eo, gyo, gVo = o.energy_projected(x32.astype(np.float64))
-    assert float(E) == pytest.approx(Eo, rel=1e-5)
+    assert float(E.detach()) == pytest.approx(Eo, rel=1e-5)
     g = y.grad.cpu().numpy().astype(np.float64)
     assert np.abs(g - 2.0 * gyo).max() <= 2e-4 * np.abs(gyo).max()
     gv = v.grad.cpu().numpy().astype(np.float64)
