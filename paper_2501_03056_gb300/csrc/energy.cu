@@ -87,9 +87,10 @@ struct PairGeo {
     uint32_t w0, w1;        // class bits of the two slots
 };
 
-__device__ inline PairGeo pair_geo(const float4 *__restrict__ pos_p, uint32_t m, float2 npx, float2 npy, float2 npz,
-                                   float hih) {
-    const float4 A = pos_p[2 * (size_t)m], B = pos_p[2 * (size_t)m + 1];
+// pos_p: the {x, y} halves of the slot pairs, pos_b: the {z, w} halves
+__device__ inline PairGeo pair_geo(const float4 *__restrict__ pos_p, const float4 *__restrict__ pos_b, uint32_t m,
+                                   float2 npx, float2 npy, float2 npz, float hih) {
+    const float4 A = pos_p[m], B = pos_b[m];
     PairGeo o;
     o.dx = __fadd2_rn(make_float2(A.x, A.y), npx);
     o.dy = __fadd2_rn(make_float2(A.z, A.w), npy);
@@ -106,11 +107,12 @@ __device__ inline PairGeo pair_geo(const float4 *__restrict__ pos_p, uint32_t m,
 // sum over the masked slots of (1 - q/2)^4 (1 + 2q), q = r / h, the particle
 // itself included (r = 0 gives exactly 1); ALL: every class acts on the lane
 template <bool ALL>
-__device__ inline void rho_range(const float4 *__restrict__ pos_p, uint32_t s, uint32_t e, float2 npx, float2 npy,
-                                 float2 npz, uint32_t mbits, float hih, float2 &acc) {
+__device__ inline void rho_range(const float4 *__restrict__ pos_p, const float4 *__restrict__ pos_b, uint32_t s,
+                                 uint32_t e, float2 npx, float2 npy, float2 npz, uint32_t mbits, float hih,
+                                 float2 &acc) {
     for_pairs(s, e, [&](auto edge, uint32_t m) {
         constexpr bool EDGE = decltype(edge)::value;
-        const PairGeo g = pair_geo(pos_p, m, npx, npy, npz, hih);
+        const PairGeo g = pair_geo(pos_p, pos_b, m, npx, npy, npz, hih);
         const float2 t2 = __fmul2_rn(g.t, g.t);
         const float2 poly = __ffma2_rn(g.r, make_float2(4.f * hih, 4.f * hih), make_float2(1.f, 1.f));
         float2 w = __fmul2_rn(__fmul2_rn(t2, t2), poly);
@@ -145,10 +147,11 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, c
     const float hih = A.half_inv_h;
     const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y), npz = make_float2(-p.z, -p.z);
     const bool all_cls = __all_sync(0xffffffffu, mbits == 0u || mbits == 0x1Fu);
+    const float4 *pos_b = pos_p + (N + 1) / 2;
     float2 acc = make_float2(0.f, 0.f);
     for_row_ranges(p, mob, A, cells, slab, *epoch, [&](uint32_t s, uint32_t e) {
-        if (all_cls) rho_range<true>(pos_p, s, e, npx, npy, npz, mbits, hih, acc);
-        else rho_range<false>(pos_p, s, e, npx, npy, npz, mbits, hih, acc);
+        if (all_cls) rho_range<true>(pos_p, pos_b, s, e, npx, npy, npz, mbits, hih, acc);
+        else rho_range<false>(pos_p, pos_b, s, e, npx, npy, npz, mbits, hih, acc);
     });
     double e = 0.0;
     if (mob) {
@@ -170,12 +173,13 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, c
 // coef_j [k acts on j]; ALLV: the lane is a volume particle (every class acts
 // on it, only volume particles feel it)
 template <bool ALLV>
-__device__ inline void grad_range(const float4 *__restrict__ pos_p, const float2 *__restrict__ coef2, uint32_t s,
+__device__ inline void grad_range(const float4 *__restrict__ pos_p, const float4 *__restrict__ pos_b,
+                                  const float2 *__restrict__ coef2, uint32_t s,
                                   uint32_t e, float2 npx, float2 npy, float2 npz, uint32_t bk, uint32_t fk, float ek,
                                   float hih, float2 &gx, float2 &gy, float2 &gz) {
     for_pairs(s, e, [&](auto edge, uint32_t m) {
         constexpr bool EDGE = decltype(edge)::value;
-        const PairGeo g = pair_geo(pos_p, m, npx, npy, npz, hih);
+        const PairGeo g = pair_geo(pos_p, pos_b, m, npx, npy, npz, hih);
         const float2 c = coef2[m];
         float2 cf;
         if (ALLV) {
@@ -214,11 +218,12 @@ __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, 
     const float hih = A.half_inv_h;
     const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y), npz = make_float2(-p.z, -p.z);
     const float2 *coef2 = reinterpret_cast<const float2 *>(coef_s);
+    const float4 *pos_b = pos_p + (N + 1) / 2;
     const bool allv = __all_sync(0xffffffffu, !active || ck == kClsV);
     float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
     for_row_ranges(p, active, A, cells, slab, *epoch, [&](uint32_t s, uint32_t e) {
-        if (allv) grad_range<true>(pos_p, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
-        else grad_range<false>(pos_p, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
+        if (allv) grad_range<true>(pos_p, pos_b, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
+        else grad_range<false>(pos_p, pos_b, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
     });
     const float sc = sign * A.force_scale;
     float fx = (gx.x + gx.y) * sc, fy = (gy.x + gy.y) * sc, fz = (gz.x + gz.y) * sc;

@@ -127,7 +127,7 @@ struct DevGroup {
     uint32_t *key[2] = {nullptr, nullptr};
     uint32_t *id[2] = {nullptr, nullptr};
     float4 *pos_s = nullptr;
-    float4 *pos_p = nullptr;   // pos_s as slot pairs: [2m] {x, x', y, y'}, [2m + 1] {z, z', w, w'}
+    float4 *pos_p = nullptr;   // pos_s as slot pairs: [m] {x, x', y, y'}, [(N + 1) / 2 + m] {z, z', w, w'}
     float4 *cert = nullptr;    // id order: inside certificate {centre, radius} of a volume particle
     float4 *acc_s = nullptr;
     uint4 *cells = nullptr;
