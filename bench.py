@@ -37,9 +37,8 @@ SMS, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 # DRAM bytes (read + write) of one k_force launch on the default workload
 # (dx = 0.02), from the ncu capture summarised in
 # profiles/k_force_icosphere_torus_dx002.md; None for other workloads and
-# until the current kernel has been captured (the capture there predates the
-# split slot-pair layout).
-K_FORCE_DRAM_BYTES = {}
+# until the current kernel has been captured.
+K_FORCE_DRAM_BYTES = {0.02: 26615040 + 3072}
 
 
 def parse():
