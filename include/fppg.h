@@ -339,6 +339,13 @@ int fppg_batch_time_force(fppg_batch *b, int32_t enable);
 int fppg_batch_force_ms(fppg_batch *b, double *ms);
 int fppg_batch_phase_ms(fppg_batch *b, double *ms4);
 
+/* Streaming multiprocessors of the current CUDA device
+ * (cudaDevAttrMultiProcessorCount) into *sms: the unit count behind the
+ * ALU roofline of the force pass (SMs x 128 FP32 lanes x clock).  Not part
+ * of the method.  FPPG_ERR_ARG for a null pointer, FPPG_ERR_CUDA when no
+ * device is usable (message in fppg_last_error(NULL)). */
+int fppg_device_sm_count(int32_t *sms);
+
 /* ---- allocation-free force pass ---------------------------------------------
  * fppg_forces_static: the neighbour grid and the force pass (A1-A4) for one
  * body, without a handle and without allocating any memory: for callers
@@ -355,7 +362,8 @@ int fppg_batch_phase_ms(fppg_batch *b, double *ms4);
  * classes); *amax_host (nullable) the largest |a| over moving particles.
  * stream: a cudaStream_t (NULL = legacy default); the call synchronises it.
  *
- * Every temporary lives in one static device array of about 6 MB that each
+ * Every temporary lives in one static device array of about 8.4 MB (8 MiB
+ * plus a few KB of parameters, flags and radix histograms) that each
  * GPU loading the library holds until the process exits.  The first call on
  * a device looks up that array's address (cudaGetSymbolAddress) -- make it
  * before any stream capture.  All calls share the array and it keeps the

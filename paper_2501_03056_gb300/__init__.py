@@ -97,6 +97,7 @@ def lib():
                 "fppg_union": [vp, vp, P_(i64), P_(i64)],
                 "fppg_boolean": [vp, vp, i32, P_(i64), P_(i64)],
                 "fppg_batch_phase_ms": [vp, P_(f64)],
+                "fppg_device_sm_count": [P_(i32)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -330,6 +331,15 @@ class Body:
 
     def copy_positions_dev(self, ptr: int):
         self._chk(lib().fppg_copy_positions_dev(self._h, C.c_void_p(ptr)))
+
+
+def device_sm_count() -> int:
+    """SMs of the current CUDA device, as the library sees it."""
+    v = C.c_int32()
+    r = lib().fppg_device_sm_count(C.byref(v))
+    if r != OK:
+        raise FPPGError(r, lib().fppg_last_error(None).decode())
+    return v.value
 
 
 UNION, DIFFERENCE, INTERSECTION = 0, 1, 2

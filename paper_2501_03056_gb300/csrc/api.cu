@@ -213,6 +213,7 @@ int fppg_extract_features(fppg_ctx *ctx, float dihedral_deg, int64_t *n_edges) {
 
 int fppg_get_feature_edges(fppg_ctx *ctx, int32_t *edges_host, int64_t cap, int64_t *n) {
     if (!ctx) return FPPG_ERR_ARG;
+    if (cap < 0) return fail(ctx->err, FPPG_ERR_ARG, "negative capacity");
     const int64_t m = (int64_t)ctx->body.fe.size() / 2;
     if (n) *n = m;
     if (edges_host) std::copy(ctx->body.fe.begin(), ctx->body.fe.begin() + 2 * std::min(cap, m), edges_host);
@@ -222,6 +223,7 @@ int fppg_get_feature_edges(fppg_ctx *ctx, int32_t *edges_host, int64_t cap, int6
 int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *closed_host, int64_t cap_lines,
                            int32_t *seg_v_host, int64_t cap_seg, int64_t *n_lines, int64_t *n_seg) {
     if (!ctx) return FPPG_ERR_ARG;
+    if (cap_lines < 0 || cap_seg < 0) return fail(ctx->err, FPPG_ERR_ARG, "negative capacity");
     const Body &b = ctx->body;
     if (n_lines) *n_lines = b.nlines;
     if (n_seg) *n_seg = b.nseg;
@@ -643,7 +645,10 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
                 lo[k] = std::min(bd.bbmin[k], pb.bbmin[k]);
                 hi[k] = std::max(bd.bbmax[k], pb.bbmax[k]);
             }
-            grid_setup(lo, hi, bd.ng_cell, 1.0, 1, A.ng_o, &A.ng_inv, A.ng_n);
+            if (!grid_setup(lo, hi, bd.ng_cell, 1.0, 1, A.ng_o, &A.ng_inv, A.ng_n)) {
+                delete b;
+                return fail_global(FPPG_ERR_ARG, "the shared grid of a Boolean pair needs more than 2^20 cells per axis");
+            }
             grid_cells = (int64_t)A.ng_n[0] * A.ng_n[1] * A.ng_n[2];
         }
         if (j >= 0) {
@@ -1005,6 +1010,16 @@ int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t 
         cudaGraphExecDestroy(g.graph);
         g.graph = nullptr;
     }
+    return FPPG_OK;
+}
+
+int fppg_device_sm_count(int32_t *sms) {
+    if (!sms) return fail_global(FPPG_ERR_ARG, "sms is NULL");
+    int dev = 0, v = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail_global(FPPG_ERR_CUDA, cudaGetErrorString(e));
+    *sms = v;
     return FPPG_OK;
 }
 

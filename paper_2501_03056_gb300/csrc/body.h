@@ -6,7 +6,12 @@
 
 namespace fppg {
 
-void grid_setup(const float *bbmin, const float *bbmax, float cell, double shift, int margin, float *o, float *inv,
+// largest cell count of one grid axis (2^20): every grid of the library has
+// its cell keys in 32 bits, which no axis above this can reach anyway
+constexpr int kGridAxisMax = 1 << 20;
+// origin, 1 / cell and cell counts of a grid over [bbmin, bbmax]; false when
+// an axis would need more than kGridAxisMax cells (or cell is not positive)
+bool grid_setup(const float *bbmin, const float *bbmax, float cell, double shift, int margin, float *o, float *inv,
                 int *n);
 
 struct Body {

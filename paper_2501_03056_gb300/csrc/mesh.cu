@@ -402,13 +402,21 @@ int bits_for(uint64_t maxval) {
 // (FP64, rounded), n = ceil((bbmax - origin) / cell) + margin.  The triangle
 // grid uses shift 2.5 with margin 2 (a face on the bounding box passes
 // through cell centres), the neighbour grid shift 1 with margin 1.
-void grid_setup(const float *bbmin, const float *bbmax, float cell, double shift, int margin, float *o, float *inv,
+// The count of every axis is checked in FP64 before it becomes an int:
+// false (n left at 0) when it is not finite or above kGridAxisMax, so that a
+// cell far below the box extent is an argument error, not a wrapped count.
+bool grid_setup(const float *bbmin, const float *bbmax, float cell, double shift, int margin, float *o, float *inv,
                 int *n) {
+    bool ok = std::isfinite(cell) && cell > 0.f;
     for (int a = 0; a < 3; a++) {
         o[a] = (float)((double)bbmin[a] - shift * (double)cell);
-        n[a] = (int)std::ceil(((double)bbmax[a] - (double)o[a]) / (double)cell) + margin;
+        const double c = std::ceil(((double)bbmax[a] - (double)o[a]) / (double)cell) + margin;
+        if (!(c >= 1.0 && c <= (double)kGridAxisMax)) ok = false;
+        n[a] = ok ? (int)c : 0;
     }
+    if (!ok) n[0] = n[1] = n[2] = 0;
     *inv = (float)(1.0 / (double)cell);
+    return ok;
 }
 
 #define CK(x)                                                                          \
@@ -468,12 +476,13 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
         this->bbmin[k] = bbmin[k];
         this->bbmax[k] = bbmax[k];
     }
-    grid_setup(bbmin, bbmax, dx, 2.5, 2, tg_o, &tg_inv, tg_n);
+    const bool tg_ok = grid_setup(bbmin, bbmax, dx, 2.5, 2, tg_o, &tg_inv, tg_n);
     float R = 2.0f * h;
     R2 = (float)((double)R * (double)R);
     ng_cell = (float)((double)R * (1.0 + 1.0 / 256.0));
-    grid_setup(bbmin, bbmax, ng_cell, 1.0, 1, ng_o, &ng_inv, ng_n);
-    if ((double)tg_n[0] * tg_n[1] * tg_n[2] >= 4294967295.0 || (double)ng_n[0] * ng_n[1] * ng_n[2] >= 536870912.0) {
+    const bool ng_ok = grid_setup(bbmin, bbmax, ng_cell, 1.0, 1, ng_o, &ng_inv, ng_n);
+    if (!tg_ok || !ng_ok || (double)tg_n[0] * tg_n[1] * tg_n[2] >= 4294967295.0 ||
+        (double)ng_n[0] * ng_n[1] * ng_n[2] >= 536870912.0) {
         // neighbour keys carry 3 slab bits below the cell index
         err = "grid too large for 32-bit cell keys (dx too small for the mesh extent)";
         return 1;

@@ -98,9 +98,11 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     memset(&A, 0, sizeof(A));
     const float R = 2.0f * h;
     const float cell = (float)((double)R * (1.0 + 1.0 / 256.0));
-    grid_setup(bbmin_host, bbmax_host, cell, 1.0, 1, A.ng_o, &A.ng_inv, A.ng_n);
-    const int64_t cells = (int64_t)A.ng_n[0] * A.ng_n[1] * A.ng_n[2];
-    if (cells > kStaticMaxCells) {
+    // each axis is bounded (2^20) before the product, so the product cannot
+    // wrap; it is then taken in FP64 against the scratch limit
+    const bool axes_ok = grid_setup(bbmin_host, bbmax_host, cell, 1.0, 1, A.ng_o, &A.ng_inv, A.ng_n);
+    const double cells_d = (double)A.ng_n[0] * (double)A.ng_n[1] * (double)A.ng_n[2];
+    if (!axes_ok || !(cells_d <= (double)kStaticMaxCells)) {
         set_global_error("fppg_forces_static: the box needs more than 131072 grid cells of 2h (static scratch limit)");
         return FPPG_ERR_ARG;
     }
@@ -143,6 +145,7 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     DevGroup d;
     d.B = 1;
     d.N = n;
+    const int64_t cells = (int64_t)cells_d;
     d.total_cells = cells;
     d.key_bits = fine_key_bits(cells);
     int digit_bits = 8;
@@ -179,6 +182,16 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
         const int buf = build_grid_dev(d, s);
         forces_dev(d, 256, 0, s);
         unpermute_dev(d, buf, s, acc_dev, nullptr, nullptr);
+        // a launch that failed to start is not reported by the synchronise
+        // below: ask for it here
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            char msg[200];
+            snprintf(msg, sizeof(msg), "fppg_forces_static: launch failed: %s", cudaGetErrorString(le));
+            set_global_error(msg);
+            cudaStreamSynchronize(s);
+            return FPPG_ERR_CUDA;
+        }
     }
     uint32_t err_h = 0, amax_h = 0;
     cudaMemcpyAsync(&err_h, error, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);

@@ -57,3 +57,38 @@ def test_package_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pkg, "_lib", None)
     with pytest.raises(pkg.FPPGError):
         pkg.lib()
+
+
+def test_tiny_cell_sizes_are_rejected_before_any_launch(library):
+    # a cell far below the mesh extent would need more than 2^20 cells per
+    # axis: rejected on the host (no cast to int of an overflowing count)
+    import numpy as np
+    from paper_2501_03056_gb300 import workloads as W
+    L = pkg.lib()
+    v, t = W.cube_mesh()
+    v = np.ascontiguousarray(v, np.float32)
+    t = np.ascontiguousarray(t, np.int32)
+    fp, ip = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)
+    for dx, h in ((0.05, 1e-9), (0.05, 1e-7), (1e-7, 0.065), (1e-30, 1e-30)):
+        out = ctypes.c_void_p()
+        r = L.fppg_create(v.ctypes.data_as(fp), len(v), t.ctypes.data_as(ip), len(t), ctypes.c_float(dx),
+                          ctypes.c_float(h), ctypes.byref(out))
+        assert r == pkg.ERR_ARG and not out.value, (dx, h)
+    # the allocation-free force pass: the per-axis bound comes before the
+    # cell product, so neither a wrapped nor a negative product passes
+    L.fppg_forces_static.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, fp, fp, ctypes.c_float,
+                                     ctypes.c_int32, ctypes.c_void_p, fp, ctypes.c_void_p]
+    lo = np.full(3, -1.0, np.float32)
+    hi = np.full(3, 1.0, np.float32)
+    for h in (1e-7, 1e-20, 0.02):
+        r = L.fppg_forces_static(None, None, 0, lo.ctypes.data_as(fp), hi.ctypes.data_as(fp), ctypes.c_float(h), 0,
+                                 None, None, None)
+        assert r == pkg.ERR_ARG, h
+        assert b"131072" in L.fppg_last_error(None)
+
+
+def test_negative_capacities_are_rejected(library):
+    L = pkg.lib()
+    n = ctypes.c_int64()
+    # no handle: the null check comes first
+    assert L.fppg_get_feature_edges(None, None, -1, ctypes.byref(n)) == pkg.ERR_ARG
