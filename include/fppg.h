@@ -130,7 +130,8 @@ int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *clos
  * Sec. 3.2, built on the triangle grid (cell dx):
  *   features   particles along the feature lines of fppg_extract_features,
  *              n = ceil(L / dx) pieces of length L / n, singular end points
- *              once (class P), the others F (Sec. 3.2.2);
+ *              once (class P), the others F with constraint = the feature
+ *              segment each was placed on (Sec. 3.2.2);
  *   surface    every cell holding triangles maps its centre to the nearest
  *              triangle of that cell whose orthogonal foot is inside (class S,
  *              constraint = that triangle); a centre with none is discarded

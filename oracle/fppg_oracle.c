@@ -746,18 +746,30 @@ static double seg_len(const or_ctx *c, int64_t s)
 /* Feature particles: along each line n = ceil(L / dx) equal pieces of
  * length L / n (slightly below dx); open lines carry both end points, which
  * are singular points (class P, emitted once each); loops carry n points.
- * Writes up to cap points; returns the total count. */
+ * Writes up to cap points; returns the total count.  seg (nullable) gets,
+ * per point, the segment of its own line it was placed on (Sec. 3.2.2
+ * places every feature particle on a known line), -1 for singular points. */
+static int64_t feature_particles_on_segments(const or_ctx *c, double dx, double *xyz, int32_t *cls, int32_t *seg,
+                                             int64_t cap);
+
 int64_t oracle_feature_particles(const or_ctx *c, double dx, double *xyz, int32_t *cls, int64_t cap)
+{
+    return feature_particles_on_segments(c, dx, xyz, cls, NULL, cap);
+}
+
+static int64_t feature_particles_on_segments(const or_ctx *c, double dx, double *xyz, int32_t *cls, int32_t *seg,
+                                             int64_t cap)
 {
     int64_t cnt = 0;
     char *done = calloc((size_t)c->nv, 1);
-#define EMIT(px, py, pz, cl)             \
+#define EMIT(px, py, pz, cl, sg)         \
     do {                                 \
         if (cnt < cap) {                 \
             xyz[3 * cnt] = (px);         \
             xyz[3 * cnt + 1] = (py);     \
             xyz[3 * cnt + 2] = (pz);     \
             cls[cnt] = (cl);             \
+            if (seg) seg[cnt] = (sg);    \
         }                                \
         cnt++;                           \
     } while (0)
@@ -773,11 +785,11 @@ int64_t oracle_feature_particles(const or_ctx *c, double dx, double *xyz, int32_
             int32_t va = c->seg_v[2 * f], vb = c->seg_v[2 * (f + ns - 1) + 1];
             if (!done[va]) {
                 done[va] = 1;
-                EMIT(c->V[3 * va], c->V[3 * va + 1], c->V[3 * va + 2], OR_P);
+                EMIT(c->V[3 * va], c->V[3 * va + 1], c->V[3 * va + 2], OR_P, -1);
             }
             if (!done[vb]) {
                 done[vb] = 1;
-                EMIT(c->V[3 * vb], c->V[3 * vb + 1], c->V[3 * vb + 2], OR_P);
+                EMIT(c->V[3 * vb], c->V[3 * vb + 1], c->V[3 * vb + 2], OR_P, -1);
             }
         }
         int64_t k0 = closed ? 0 : 1, k1 = closed ? npc - 1 : npc - 1;
@@ -791,7 +803,7 @@ int64_t oracle_feature_particles(const or_ctx *c, double dx, double *xyz, int32_
             }
             double len = seg_len(c, s), t = len > 0 ? (target - cum) / len : 0.0;
             const double *a = c->V + 3 * c->seg_v[2 * s], *b = c->V + 3 * c->seg_v[2 * s + 1];
-            EMIT(a[0] + t * (b[0] - a[0]), a[1] + t * (b[1] - a[1]), a[2] + t * (b[2] - a[2]), OR_F);
+            EMIT(a[0] + t * (b[0] - a[0]), a[1] + t * (b[1] - a[1]), a[2] + t * (b[2] - a[2]), OR_F, (int32_t)s);
         }
     }
 #undef EMIT
@@ -1953,7 +1965,8 @@ static void column_inside(const or_ctx *c, int32_t i, int32_t j, unsigned char *
 }
 
 /* Initial particles (Sec. 3.2, Fig. 9):
- *   features: the feature-line particles (F, and P at singular points);
+ *   features: the feature-line particles (F, constraint = the segment it
+ *             lies on; P at singular points, constraint -1);
  *   surface:  every triangle cell holding triangles contributes its centre
  *             mapped to the nearest triangle of that cell whose foot is
  *             inside (smallest |plane distance|, ties to the lower index);
@@ -1971,18 +1984,20 @@ int64_t oracle_map_particles(const or_ctx *c, int surface, int volume, int featu
 {
     int64_t cnt = 0;
     if (features) {
-        int64_t nf = oracle_feature_particles(c, (double)c->dx, NULL, NULL, 0);
+        int64_t nf = feature_particles_on_segments(c, (double)c->dx, NULL, NULL, NULL, 0);
         double *fx = malloc(sizeof(double) * 3 * (nf ? nf : 1));
         int32_t *fc = malloc(sizeof(int32_t) * (nf ? nf : 1));
-        oracle_feature_particles(c, (double)c->dx, fx, fc, nf);
+        int32_t *fs = malloc(sizeof(int32_t) * (nf ? nf : 1));
+        feature_particles_on_segments(c, (double)c->dx, fx, fc, fs, nf);
         for (int64_t i = 0; i < nf; i++, cnt++)
             if (cnt < cap) {
                 memcpy(xyz + 3 * cnt, fx + 3 * i, sizeof(double) * 3);
                 cls[cnt] = fc[i];
-                cons[cnt] = -1;
+                cons[cnt] = fs[i];   /* F: the segment it lies on; P: -1 */
             }
         free(fx);
         free(fc);
+        free(fs);
     }
     const int32_t *n = c->tg_n;
     if (surface) {

@@ -62,7 +62,7 @@ struct Body {
     int2 *lines = nullptr;
     int nseg = 0, nlines = 0;
 
-    void feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls) const;
+    void feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg) const;
     int build_mesh(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,
                    cudaStream_t s, std::string &err);
     int extract_features(float deg, cudaStream_t s, std::string &err);

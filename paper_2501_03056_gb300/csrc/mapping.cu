@@ -227,19 +227,22 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t
 
 // Feature particles of Sec. 3.2.2 on the host from the walked lines: n =
 // ceil(L / dx) pieces of length L / n; open lines add their singular end
-// points once (class P); loops carry n points.
-void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls) const {
+// points once (class P); loops carry n points.  seg gets the segment each
+// feature particle was placed on (-1 for singular points), so its first
+// step already projects onto its own line.
+void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg) const {
     std::vector<char> done(nv, 0);
     auto seglen = [&](int64_t q) {
         const float *a = &verts_host[3 * (size_t)seg_v[2 * q]], *b = &verts_host[3 * (size_t)seg_v[2 * q + 1]];
         const double e0 = (double)b[0] - a[0], e1 = (double)b[1] - a[1], e2 = (double)b[2] - a[2];
         return std::sqrt(e0 * e0 + e1 * e1 + e2 * e2);
     };
-    auto emit = [&](double x, double y, double z, int c) {
+    auto emit = [&](double x, double y, double z, int c, int64_t q) {
         xyz.push_back((float)x);
         xyz.push_back((float)y);
         xyz.push_back((float)z);
         cls.push_back(c);
+        seg.push_back((int32_t)q);
     };
     for (int l = 0; l < nlines; l++) {
         const int64_t f = line_first[l], ns = line_nseg[l];
@@ -253,7 +256,8 @@ void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls)
             for (int32_t v : {seg_v[2 * f], seg_v[2 * (f + ns - 1) + 1]})
                 if (!done[v]) {
                     done[v] = 1;
-                    emit(verts_host[3 * (size_t)v], verts_host[3 * (size_t)v + 1], verts_host[3 * (size_t)v + 2], kClsP);
+                    emit(verts_host[3 * (size_t)v], verts_host[3 * (size_t)v + 1], verts_host[3 * (size_t)v + 2], kClsP,
+                         -1);
                 }
         }
         int64_t q = f;
@@ -267,7 +271,7 @@ void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls)
             const double len = seglen(q), t = len > 0 ? (target - cum) / len : 0.0;
             const float *a = &verts_host[3 * (size_t)seg_v[2 * q]], *b = &verts_host[3 * (size_t)seg_v[2 * q + 1]];
             emit(a[0] + t * ((double)b[0] - a[0]), a[1] + t * ((double)b[1] - a[1]), a[2] + t * ((double)b[2] - a[2]),
-                 kClsF);
+                 kClsF, q);
         }
     }
 }
@@ -297,8 +301,8 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
         return 1;
     }
     std::vector<float> fxyz;
-    std::vector<int32_t> fcls;
-    if (features && b.has_features) b.feature_particles(fxyz, fcls);
+    std::vector<int32_t> fcls, fseg;
+    if (features && b.has_features) b.feature_particles(fxyz, fcls, fseg);
     const int64_t nf = (int64_t)fcls.size();
 
     uint8_t *inside = nullptr, *band = nullptr, *tmp = nullptr, *inner = nullptr;
@@ -375,7 +379,7 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
     }
     if (nf) {
         std::vector<float4> p4(nf);
-        std::vector<int32_t> c4(nf, -1);
+        const std::vector<int32_t> &c4 = fseg;   // constraints: the segment of each feature particle
         for (int64_t i = 0; i < nf; i++) {
             uint32_t bits = class_bit(fcls[i]);
             float w;
