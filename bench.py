@@ -1,20 +1,27 @@
 #!/usr/bin/env python
 """Throughput of the FPPG relaxation path on GB300: particle-iterations/s.
 
-Workload (default): icosphere r = 1 (level 5, 20,480 triangles) plus torus
-R = 1, r = 0.3 (256 x 64 quads) at dx = 0.02, h = 1.3 dx -- two bodies,
-~0.78 M particles, seeded synthetic lattices with +-0.25 dx jitter.  A step
-is one replay of a 50-iteration CUDA graph of the batched form (every phase
-of an iteration is one launch over both bodies); K = 10 steps are the 500
-iterations of the workload.  L2 is flushed (a 256 MiB write) between steps,
-outside the timed events.
+Workload (default, ``--workload vehicle``): the vehicle-like closed shell --
+union of two rounded boxes and four wheel cylinders as a signed-distance
+field, surface nets and two Loop subdivision steps (2,009,344 triangles),
+seeded 1e-3 vertex noise, 30 degree features -- at dx = 0.0068, h = 1.3 dx,
+with its initial particles (19.2 M feature, surface and volume particles)
+generated on the GPU by the method's own generation (Sec. 3.2).  A step is
+one replay of a 50-iteration CUDA graph of the batched form (every phase of
+an iteration is one launch); K = 20 steps are the workload's 1000
+iterations.  The working set (~2.4 GB of particle state) is larger than L2;
+L2 is also flushed (a 256 MiB write) between steps, outside the timed
+events.  ``--workload sphere_torus`` times the icosphere + torus pair at
+dx = 0.02 (777 k particles) instead.
 
-Reported beside it: the plain form (each body relaxed with its own launches,
+Reported beside it: the plain form (the body relaxed with its own launches,
 no graph), the end-to-end number through the C ABI with host buffers (pinned
-host -> device copy of the particles, relaxation, device -> host copy of the
-positions, every step), the force kernel against the FP32 ALU roofline, and
-the FP64 CPU oracle on the host cores.  ``--impl reference`` times the
-oracle alone (the CPU program the GPU path is checked against).
+host -> device copy of the particles and their constraints, relaxation,
+device -> host copy of the positions, every step), the force kernel against
+the FP32 ALU roofline (lane instructions per candidate and per pair against
+SMs x 128 lanes x clock), and the FP64 CPU oracle on the host cores on a
+bounded crop of the same workload.  ``--impl reference`` times the oracle
+alone (the CPU program the GPU path is checked against).
 """
 from __future__ import annotations
 
@@ -33,22 +40,44 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 256 << 20
-SMS, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
-# DRAM bytes (read + write) of one k_force launch on the default workload
-# (dx = 0.02), from the ncu capture summarised in
-# profiles/k_force_icosphere_torus_dx002.md; None for other workloads and
-# until the current kernel has been captured.
-K_FORCE_DRAM_BYTES = {0.02: 26615040 + 3072}
+FP32_LANES = 128                  # FP32 lanes per SM (the SM count is read from the device)
+# FP32 lane instructions of the force pass (Eq. 15): per candidate of the
+# 27-cell search set (difference, squared distance, compare) and per
+# accepted pair (root, Wendland C2 gradient, accumulation)
+INSTR_PER_CANDIDATE, INSTR_PER_PAIR = 7.0, 25.0
+# FP32 flops of the same (FMA = 2): 8 per candidate, 12 per accepted pair
+FLOPS_PER_CANDIDATE, FLOPS_PER_PAIR = 8.0, 12.0
+# DRAM bytes (read + write) of one k_force launch, from one ncu capture per
+# workload of the current kernel (null until captured)
+K_FORCE_DRAM_BYTES = {"sphere_torus": 26615040 + 3072, "vehicle": None}
+# bytes per particle-iteration: state in and out plus the mandated cell-list
+# rebuild (useful), and the compulsory traffic of the whole pipeline
+USEFUL_BYTES, PIPELINE_BYTES = 56.0, 224.0
+
+
+def workload(name, rank=0, dx=0.02):
+    """(assemblies, description) of a named workload; weak scaling gives each
+    rank its own seeded copy."""
+    from paper_2501_03056_gb300 import workloads as W
+    if name == "vehicle":
+        return W.vehicle_workload(), ("vehicle shell (config 5): rounded boxes + 4 wheels, surface nets + 2 Loop "
+                                      "steps, 2,009,344 triangles, 1e-3 noise, 30 deg features, dx=0.0068, "
+                                      "particles generated on the GPU (Sec. 3.2)")
+    if name == "sphere_torus":
+        return (W.sphere_torus_workload(seed=1 + 10 * rank, dx=dx),
+                f"icosphere_l5+torus_256x64 (config 2) dx={dx}")
+    raise ValueError(name)
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="vehicle", choices=["vehicle", "sphere_torus"])
     p.add_argument("--iters-per-step", type=int, default=50)
-    p.add_argument("--dx", type=float, default=0.02)
+    p.add_argument("--dx", type=float, default=0.02, help="dx of the sphere_torus workload")
     p.add_argument("--no-extras", action="store_true", help="skip plain / e2e / CPU legs")
     p.add_argument("--no-autotune", action="store_true", help="keep the default kernel configuration")
     p.add_argument("--config", default=None,
@@ -134,27 +163,32 @@ def max_over_ranks(value: float) -> float:
     return float(t.item())
 
 
-def cpu_oracle(asm, iters=1):
-    """The FP64 oracle on the host cores: `iters` iterations of every body."""
+def oracle_crop(asm, frac):
+    """FP64 oracle bodies on a bounded crop of the workload: every body with
+    its full mesh and features, particles cut to the `frac` of each body
+    with the smallest x (the oracle's own generation where the workload
+    generates its particles).  Returns (bodies, particles, description)."""
     import oracle
-    bodies = [oracle.from_assembly(a) for a in asm]
-    t0 = time.perf_counter()
-    for o in bodies:
-        o.relax(iters)
-    dt = time.perf_counter() - t0
-    n = sum(a.n for a in asm)
-    return n * iters / dt, oracle.get_threads(), dt
+    bodies, n = [], 0
+    for a in asm:
+        o = oracle.from_assembly(a)
+        if frac < 1.0:
+            x, _, _ = o.get_particles()
+            keep = x[:, 0] <= np.quantile(x[:, 0], frac)
+            oracle.keep_rows(o, keep)
+        n += o.n
+        bodies.append(o)
+    return bodies, n, f"the {100 * frac:g} % of particles with the smallest x of each body, full meshes"
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2501_03056_gb300 import workloads as W
     import oracle
-    asm = W.sphere_torus_workload(dx=args.dx)
-    bodies = [oracle.from_assembly(a) for a in asm]
-    n = sum(a.n for a in asm)
+    asm, desc = workload(args.workload, 0, args.dx)
+    frac = 1.0 / 16 if args.workload == "vehicle" else 1.0
+    bodies, n, sample = oracle_crop(asm, frac)
     for _ in range(args.warmup):
         for o in bodies:
             o.relax(1)
@@ -171,13 +205,34 @@ def run_reference(args):
         "unit": "particle-iterations/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"icosphere_l5+torus_256x64 dx={args.dx}", "bodies": 2, "particles": n,
-                   "iterations_per_step": 1, "form": "FP64 CPU oracle, one iteration per step (bounded sample)"},
+        "config": {"workload": desc, "bodies": len(asm), "particles": n, "iterations_per_step": 1,
+                   "form": "FP64 CPU oracle, one iteration per step (bounded sample)", "sample": sample},
         "cpu_baseline": {"value": value, "unit": "particle-iterations/s", "cores": oracle.get_threads(),
-                         "kind": "oracle", "sample": "one FP64 iteration of both bodies per step"},
+                         "kind": "oracle", "sample": f"one FP64 iteration per step of {sample}"},
         "e2e": {"value": value, "unit": "particle-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def force_roofline(cand, pairs, tested, force_ms, sms, sm_mhz, peak_kind, traffic):
+    """ALU roofline of the force pass: FP32 lane instructions per launch
+    (7 per candidate of the 27-cell set + 25 per accepted pair) against
+    SMs x 128 lanes x clock, with the flop form beside it."""
+    lane_peak = sms * FP32_LANES * sm_mhz * 1e6 / 1e12                     # T lane-instr/s
+    instr = INSTR_PER_CANDIDATE * cand + INSTR_PER_PAIR * pairs
+    achieved = instr / (force_ms / 1e3) / 1e12
+    flop_peak = 2.0 * lane_peak
+    flops = FLOPS_PER_CANDIDATE * cand + FLOPS_PER_PAIR * pairs
+    flops_exec = FLOPS_PER_CANDIDATE * tested + FLOPS_PER_PAIR * pairs
+    return {"bound": "alu", "kernel": "k_force", "achieved": achieved, "peak": lane_peak,
+            "unit": "T FP32 lane-instructions/s", "frac": achieved / lane_peak, "traffic": traffic,
+            "peak_kind": f"{sms} SMs (from the device) x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz ({peak_kind} "
+                         "max clock)",
+            "lane_instructions_per_launch": instr, "candidates": cand, "pairs": pairs, "tested": tested,
+            "tested_per_pair": tested / max(pairs, 1), "force_ms": force_ms,
+            "flop_form": {"achieved_TFLOPs": flops / (force_ms / 1e3) / 1e12, "peak_TFLOPs": flop_peak,
+                          "frac": flops / (force_ms / 1e3) / 1e12 / flop_peak,
+                          "executed_frac": flops_exec / (force_ms / 1e3) / 1e12 / flop_peak}}
 
 
 def main():
@@ -195,29 +250,43 @@ def main():
     from paper_2501_03056_gb300 import workloads as W
 
     G, K, Wm = args.iters_per_step, args.steps, args.warmup
-    asm = W.sphere_torus_workload(seed=1 + 10 * rank, dx=args.dx)    # weak scaling: one copy per rank
-    n = sum(a.n for a in asm)
     stream = torch.cuda.current_stream()
-    bodies = [pkg.Body.from_assembly(a, stream=stream) for a in asm]
-    cand = pairs = tested = 0
-    for b in bodies:
-        c, p, t = b.work_counts()
-        cand += c
-        pairs += p
-        tested += t
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    peaks, peak_kind = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sms = pkg.device_sm_count()
 
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
 
-    def timed_steps(step_fn, reset_fn):
+    def make_bodies(asm):
+        """Bodies of the assemblies (generated on the GPU where the workload
+        carries no particles) and a host snapshot of their initial state."""
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bodies = [pkg.Body.from_assembly(a, stream=stream) for a in asm]
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        snap = [b.get_particles() for b in bodies]
+        return bodies, snap, gen_s
+
+    def reset(bodies, snap):
+        for b, (x, c, cons) in zip(bodies, snap):
+            b.set_particles(x, c)
+            b.set_constraints(cons)
+
+    def timed(step_fn, reset_fn, steps, warm):
+        """Device ms of `steps` steps after `warm` warm-up steps, the state
+        reset before each group, L2 flushed before each step (outside the
+        events)."""
         reset_fn()
-        for _ in range(Wm):
+        for _ in range(warm):
             step_fn()
         reset_fn()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         for s, e in ev:
             flush.zero_()
@@ -227,56 +296,106 @@ def main():
         barrier()
         return [s.elapsed_time(e) for s, e in ev]
 
-    # ---- batched form, CUDA graph of G iterations --------------------------
-    batch = pkg.Batch(bodies, stream=stream)
-    if args.config:
-        v, tb, sc = (int(x) for x in args.config.split(","))
-        batch.configure(v, tb, sc)
-        tuned = {"force_variant": v, "force_block": tb, "search_ctas_per_sm": sc, "fixed": True}
-    else:
-        tuned = None if args.no_autotune else batch.autotune(G)   # trials as long as a timed step
-    batch.set_graph_iters(G)
+    def measure(asm, desc, steps, warm, tune=True, config=None, with_plain=False, plain_steps=2, clocks=None):
+        """Batched + graph form of a workload (autotuned), its live phase
+        times, work counts and force roofline; optionally the plain form."""
+        bodies, snap, gen_s = make_bodies(asm)
+        n = sum(b.n for b in bodies)
+        cand = pairs = tested = 0
+        for b in bodies:
+            c, p, t = b.work_counts()
+            cand += c
+            pairs += p
+            tested += t
+        batch = pkg.Batch(bodies, stream=stream)
+        if config:
+            v, tb, sc = (int(x) for x in config.split(","))
+            batch.configure(v, tb, sc)
+            tuned = {"force_variant": v, "force_block": tb, "search_ctas_per_sm": sc, "fixed": True}
+        else:
+            tuned = batch.autotune(G) if tune else None     # trials as long as a timed step
+        batch.set_graph_iters(G)
+        if clocks:
+            clocks.start()
+        ms = timed(lambda: batch.relax(G, use_graph=True), batch.load, steps, warm)
+        clk = clocks.stop() if clocks else None
+        # one more replay, with CUDA event records around the phases of every
+        # iteration captured into the graph: live per-phase device times
+        batch.time_force(True)
+        batch.load()
+        batch.relax(G, use_graph=True)
+        phases = batch.phase_ms()
+        batch.time_force(False)
+        r = {"bodies": bodies, "snap": snap, "batch": batch, "n": n, "ms": ms, "phases": phases, "tuned": tuned,
+             "clocks": clk, "cand": cand, "pairs": pairs, "tested": tested, "gen_s": gen_s,
+             "value": n * G * steps / (sum(ms) / 1e3), "desc": desc}
+        if with_plain:
+            pms = timed(lambda: [b.relax(G) for b in bodies], lambda: reset(bodies, snap), plain_steps, 1)
+            r["plain"] = n * G * plain_steps / (sum(pms) / 1e3)
+            r["plain_ms"] = sum(pms) / plain_steps
+        return r
+
+    # ---- the headline: batched form, CUDA graph of G iterations ----------------
+    asm, desc = workload(args.workload, rank, args.dx)
     clocks = Clocks(local)
-    clocks.start()
-    ms = timed_steps(lambda: batch.relax(G, use_graph=True), batch.load)
-    clk = clocks.stop()
-    # one more replay, with CUDA event records around the phases of every
-    # iteration captured into the graph: live per-phase device times
-    batch.time_force(True)
-    batch.load()
-    batch.relax(G, use_graph=True)
-    phases = batch.phase_ms()
-    force_ms = phases["force"]
-    batch.time_force(False)
-    tot_ms = max_over_ranks(sum(ms))
+    H = measure(asm, desc, K, Wm, tune=not args.no_autotune, config=args.config, clocks=clocks)
+    n, batch, bodies = H["n"], H["batch"], H["bodies"]
+    tot_ms = max_over_ranks(sum(H["ms"]))
     value = n * world * G * K / (tot_ms / 1e3)
     kpi = batch.kernels_per_iter
+    roof = force_roofline(H["cand"], H["pairs"], H["tested"], H["phases"]["force"], sms, sm_max, peak_kind,
+                          K_FORCE_DRAM_BYTES.get(args.workload))
+    it_ms = tot_ms / K / G
+    line = {
+        "metric": "relaxation particle-iterations/s",
+        "value": value, "unit": "particle-iterations/s", "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": tot_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "bodies": len(asm), "particles": n, "iterations_per_step": G,
+                   "iterations": G * K, "form": "batched + CUDA graph",
+                   "l2": "working set larger than L2; L2 also flushed between steps (256 MiB write)"
+                         if args.workload == "vehicle" else
+                         "flushed between steps (256 MiB write), working set < L2"},
+        "roofline": roof,
+        "hbm": {"useful_bytes_per_particle_iteration": USEFUL_BYTES,
+                "useful_GBps": USEFUL_BYTES * value / world / 1e9,
+                "frac_of_measured": USEFUL_BYTES * value / world / 1e9 / hbm,
+                "pipeline_bytes_per_particle_iteration": PIPELINE_BYTES,
+                "pipeline_GBps": PIPELINE_BYTES * value / world / 1e9,
+                "pipeline_frac_of_measured": PIPELINE_BYTES * value / world / 1e9 / hbm,
+                "peak_GBps": hbm, "peak_kind": peak_kind},
+        "phase_ms_per_iteration": {**H["phases"], "whole_iteration": it_ms,
+                                   "note": "one extra replay with event records in the graph"},
+        "gpu_launches": kpi * G * K,
+        "kernels_per_iteration": kpi,
+        "autotune": H["tuned"],
+        "clocks": H["clocks"],
+    }
 
-    extras = {}
     if not args.no_extras:
-        # ---- plain form: each body with its own launches, no graph ---------
-        def plain_reset():
-            for b, a in zip(bodies, asm):
-                b.set_particles(a.xyz, a.cls)
-
-        pms = timed_steps(lambda: [b.relax(G) for b in bodies], plain_reset)
-        plain_value = n * G * K / (sum(pms) / 1e3)
-        extras["plain"] = {"value": plain_value, "unit": "particle-iterations/s", "ms_per_step": sum(pms) / K,
-                           "launches_per_iteration": kpi * len(bodies), "graph": False}
-        extras["batched_over_plain"] = value / world / plain_value
+        # ---- plain form of the headline workload: no graph, own launches ------
+        snap = H["snap"]
+        ps = min(K, 4)
+        pms = timed(lambda: [b.relax(G) for b in bodies], lambda: reset(bodies, snap), ps, 1)
+        plain_value = n * G * ps / (sum(pms) / 1e3)
+        line["plain"] = {"value": plain_value, "unit": "particle-iterations/s", "ms_per_step": sum(pms) / ps,
+                         "steps": ps, "launches_per_iteration": kpi * len(bodies), "graph": False}
+        line["batched_over_plain"] = value / world / plain_value
 
         # ---- end to end through the C ABI with host buffers ------------------
-        pinned = [(torch.from_numpy(np.ascontiguousarray(a.xyz)).pin_memory(),
-                   torch.from_numpy(np.ascontiguousarray(a.cls)).pin_memory(),
-                   torch.empty((a.n, 3), dtype=torch.float32).pin_memory()) for a in asm]
+        pinned = [(torch.from_numpy(np.ascontiguousarray(x)).pin_memory(),
+                   torch.from_numpy(np.ascontiguousarray(c)).pin_memory(),
+                   torch.from_numpy(np.ascontiguousarray(cons)).pin_memory(),
+                   torch.empty((len(x), 3), dtype=torch.float32).pin_memory()) for x, c, cons in snap]
 
         def e2e_step():
-            for b, (x, c, _) in zip(bodies, pinned):
+            for b, (x, c, cons, _) in zip(bodies, pinned):
                 b.set_particles(x.numpy(), c.numpy())
+                b.set_constraints(cons.numpy())
             batch.load()
             batch.relax(G, use_graph=True)
             batch.store()
-            for b, (_, _, out) in zip(bodies, pinned):
+            for b, (_, _, _, out) in zip(bodies, pinned):
                 b.get_positions_into(out.numpy())
 
         for _ in range(Wm):
@@ -287,56 +406,42 @@ def main():
             e2e_step()
         barrier()
         e2e_s = time.perf_counter() - t0
-        extras["e2e"] = {"value": n * world * G * K / e2e_s, "unit": "particle-iterations/s",
-                         "h2d_bytes_per_step": int(n * 16), "d2h_bytes_per_step": int(n * 12)}
+        line["e2e"] = {"value": n * world * G * K / e2e_s, "unit": "particle-iterations/s",
+                       "h2d_bytes_per_step": int(n * 20), "d2h_bytes_per_step": int(n * 12),
+                       "copies": "xyz (12 B) + class (4 B) + constraint (4 B) in, xyz (12 B) out, per particle"}
+        line["generation_headline"] = {"particles": n, "seconds": H["gen_s"],
+                                       "what": "mesh build, feature extraction and fppg_map_particles of the "
+                                               "headline workload (host wall clock around synchronised calls)"}
+        batch.close()
+
+        # ---- config 2 (icosphere + torus) as its own leg ------------------------
+        if args.workload != "sphere_torus":
+            st_asm, st_desc = workload("sphere_torus", rank, 0.02)
+            S2 = measure(st_asm, st_desc, 10, 3, with_plain=True, plain_steps=4)
+            line["sphere_torus"] = {
+                "workload": st_desc, "particles": S2["n"], "iterations_per_step": G, "steps": 10,
+                "batched_graph": S2["value"], "plain": S2["plain"], "batched_over_plain": S2["value"] / S2["plain"],
+                "unit": "particle-iterations/s", "autotune": S2["tuned"], "phase_ms_per_iteration": S2["phases"],
+                "roofline": force_roofline(S2["cand"], S2["pairs"], S2["tested"], S2["phases"]["force"], sms,
+                                           sm_max, peak_kind, K_FORCE_DRAM_BYTES["sphere_torus"])}
+            st_bodies = S2["bodies"]
+            S2["batch"].close()
+        else:
+            st_asm, st_bodies = asm, bodies
 
         # ---- the other configurations at full size: batched + graph and plain ---
         def config_leg(casm, steps=2):
-            cb = [pkg.Body.from_assembly(a, stream=stream) for a in casm]
-            cn = sum(b.n for b in cb)
-            snap_c = [b.get_particles() for b in cb]
-
-            def reset_c():
-                for b, (x, c, cons) in zip(cb, snap_c):
-                    b.set_particles(x, c)
-                    b.set_constraints(cons)
-
-            cbt = pkg.Batch(cb, stream=stream)
-            ctuned = cbt.autotune(G)
-            cbt.set_graph_iters(G)
-            t_b, t_p = [], []
-            for _ in range(steps + 1):
-                cbt.load()
-                flush.zero_()
-                s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s_.record(stream)
-                cbt.relax(G, use_graph=True)
-                e_.record(stream)
-                torch.cuda.synchronize()
-                t_b.append(s_.elapsed_time(e_))
-                reset_c()
-                flush.zero_()
-                s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s_.record(stream)
-                for b in cb:
-                    b.relax(G)
-                e_.record(stream)
-                torch.cuda.synchronize()
-                t_p.append(s_.elapsed_time(e_))
-                reset_c()
-            cbt.close()
-            for b in cb:
+            R = measure(casm, "", steps, 1, with_plain=True, plain_steps=steps)
+            R["batch"].close()
+            for b in R["bodies"]:
                 b.close()
-            vb_ = cn * G * steps / (sum(t_b[1:]) / 1e3)
-            vp_ = cn * G * steps / (sum(t_p[1:]) / 1e3)
-            return {"particles": cn, "iterations_per_step": G, "steps": steps, "warmup": 1,
-                    "batched_graph": vb_, "plain": vp_, "batched_over_plain": vb_ / vp_,
-                    "unit": "particle-iterations/s", "autotune": ctuned}
+            return {"particles": R["n"], "iterations_per_step": G, "steps": steps, "warmup": 1,
+                    "batched_graph": R["value"], "plain": R["plain"], "batched_over_plain": R["value"] / R["plain"],
+                    "unit": "particle-iterations/s", "autotune": R["tuned"], "phase_ms_per_iteration": R["phases"]}
 
-        extras["configs"] = {
+        line["configs"] = {
             "cube (config 1, dx=0.05)": config_leg(W.cube_workload()),
             "spur gear (config 3, dx=0.004, generated)": config_leg(W.gear_workload()),
-            "vehicle shell (config 5, 2.0 M triangles, dx=0.0068, generated)": config_leg(W.vehicle_workload(), 1),
         }
 
         # ---- generation (Sec. 3.2) on the GPU: config 3's gear ------------------
@@ -352,26 +457,27 @@ def main():
         gn = gb.map_particles(**ga.meta["generate"])
         torch.cuda.synchronize()
         t3 = time.perf_counter()
-        extras["generation"] = {"workload": f"spur gear, {len(ga.tris)} triangles, dx={ga.dx:g}, band 2 + inner 1 cells",
-                                "particles": gn, "mesh_build_ms": 1e3 * (t1 - t0),
-                                "features_ms": 1e3 * (t2 - t1), "map_particles_ms": 1e3 * (t3 - t2),
-                                "particles_per_s": gn / (t3 - t2), "timer": "host wall clock around synchronised calls"}
+        line["generation"] = {"workload": f"spur gear, {len(ga.tris)} triangles, dx={ga.dx:g}, band 2 + inner 1 cells",
+                              "particles": gn, "mesh_build_ms": 1e3 * (t1 - t0),
+                              "features_ms": 1e3 * (t2 - t1), "map_particles_ms": 1e3 * (t3 - t2),
+                              "particles_per_s": gn / (t3 - t2), "timer": "host wall clock around synchronised calls"}
         gb.close()
 
         # ---- energy (A8): energy-descent relaxation and the backward ------------
-        for b, a in zip(bodies, asm):
+        for b, a in zip(st_bodies, st_asm):
             b.set_particles(a.xyz, a.cls)
+        st_n = sum(b.n for b in st_bodies)
         Ge = 10
-        for b in bodies:
+        for b in st_bodies:
             b.relax_energy(1)
         es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         es.record(stream)
-        for b in bodies:
+        for b in st_bodies:
             b.relax_energy(Ge)
         ee.record(stream)
         torch.cuda.synchronize()
-        e_relax = n * Ge / (es.elapsed_time(ee) / 1e3)
-        tb, ta = bodies[1], asm[1]                      # the torus: surface particles through the projection
+        e_relax = st_n * Ge / (es.elapsed_time(ee) / 1e3)
+        tb, ta = st_bodies[1], st_asm[1]                # the torus: surface particles through the projection
         y = torch.from_numpy(np.ascontiguousarray(tb.get_particles()[0])).cuda()
         verts = torch.from_numpy(np.ascontiguousarray(ta.verts)).cuda()
         gy, gv = torch.empty_like(y), torch.empty_like(verts)
@@ -382,11 +488,13 @@ def main():
             tb.energy_ptr(y.data_ptr(), verts.data_ptr(), gy.data_ptr(), gv.data_ptr())
         ee.record(stream)
         torch.cuda.synchronize()
-        extras["energy"] = {"relax_energy": {"value": e_relax, "unit": "particle-iterations/s",
-                                             "iterations": Ge, "form": "plain, both bodies"},
-                            "energy_and_backward_ms": es.elapsed_time(ee) / reps,
-                            "backward_workload": f"torus body, {tb.n} particles, {len(ta.verts)} vertices: "
-                                                 "E, dE/dy and dE/dverts through the frozen surface projection"}
+        line["energy"] = {"relax_energy": {"value": e_relax, "unit": "particle-iterations/s",
+                                           "iterations": Ge, "form": "plain, icosphere + torus (config 2)"},
+                          "energy_and_backward_ms": es.elapsed_time(ee) / reps,
+                          "backward_workload": f"torus body, {tb.n} particles, {len(ta.verts)} vertices: "
+                                               "E, dE/dy and dE/dverts through the frozen surface projection"}
+        for b in st_bodies:
+            b.close()
 
         # ---- 64 bodies of uneven size with gear-shaft unions: batched + graph
         # against plain (single bodies one by one, each union as a 2-body
@@ -400,98 +508,62 @@ def main():
         singles = [b for k, b in enumerate(bbodies) if k not in in_pair]
         pair_batches = [pkg.Batch([bbodies[i], bbodies[j]], stream=stream) for i, j in upairs]
         nb = sum(b.n for b in bbodies)
-        snap = [b.get_particles() for b in bbodies]
-
-        def reset_bodies():
-            for b, (x, c, cons) in zip(bbodies, snap):
-                b.set_particles(x, c)
-                b.set_constraints(cons)
-
+        bsnap = [b.get_particles() for b in bbodies]
         bb = pkg.Batch(bbodies, stream=stream)
         btuned = bb.autotune(G)
         bb.set_graph_iters(G)
         kb = 3
-        ms_bb, ms_bp = [], []
-        for _ in range(kb + 1):
-            bb.load()
-            flush.zero_()
-            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s_.record(stream)
-            bb.relax(G, use_graph=True)
-            e_.record(stream)
-            torch.cuda.synchronize()
-            ms_bb.append(s_.elapsed_time(e_))
-            reset_bodies()
+
+        def plain64():
             for pb in pair_batches:
                 pb.load()
-            flush.zero_()
-            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s_.record(stream)
             for b in singles:
                 b.relax(G)
             for pb in pair_batches:
                 pb.relax(G, use_graph=False)
-            e_.record(stream)
-            torch.cuda.synchronize()
-            ms_bp.append(s_.elapsed_time(e_))
-            reset_bodies()
-        vb = nb * G * kb / (sum(ms_bb[1:]) / 1e3)
-        vp = nb * G * kb / (sum(ms_bp[1:]) / 1e3)
+
+        ms_bb = timed(lambda: bb.relax(G, use_graph=True), bb.load, kb, 1)
+        ms_bp = timed(plain64, lambda: reset(bbodies, bsnap), kb, 1)
+        vb = nb * G * kb / (sum(ms_bb) / 1e3)
+        vp = nb * G * kb / (sum(ms_bp) / 1e3)
         bb.time_force(True)
         bb.load()
         bb.relax(G, use_graph=True)
         bphases = bb.phase_ms()
         bb.time_force(False)
-        extras["batch64"] = {"workload": "64 bodies (cubes, cylinders, icospheres, gears; scales 0.1-1), dx=0.008, "
-                                         f"{len(upairs)} gear-shaft Boolean unions",
-                             "particles": nb, "iterations_per_step": G, "steps": kb, "warmup": 1,
-                             "batched_graph": vb, "plain": vp, "batched_over_plain": vb / vp,
-                             "unit": "particle-iterations/s", "autotune": btuned,
-                             "phase_ms_per_iteration": bphases,
-                             "launches_per_iteration": {"batched": bb.kernels_per_iter,
-                                                        "plain": bb.kernels_per_iter * (len(singles) +
-                                                                                        len(pair_batches))}}
+        line["batch64"] = {"workload": "64 bodies (cubes, cylinders, icospheres, gears; scales 0.1-1), dx=0.008, "
+                                       f"{len(upairs)} gear-shaft Boolean unions",
+                           "particles": nb, "iterations_per_step": G, "steps": kb, "warmup": 1,
+                           "batched_graph": vb, "plain": vp, "batched_over_plain": vb / vp,
+                           "unit": "particle-iterations/s", "autotune": btuned,
+                           "phase_ms_per_iteration": bphases,
+                           "launches_per_iteration": {"batched": bb.kernels_per_iter,
+                                                      "plain": bb.kernels_per_iter * (len(singles) +
+                                                                                      len(pair_batches))}}
         bb.close()
         for pb in pair_batches:
             pb.close()
+        for b in bbodies:
+            b.close()
+    else:
+        batch.close()
 
-    peaks, peak_kind = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12     # TFLOP/s, FMA = 2
-    flops = 8.0 * cand + 12.0 * pairs                           # per force launch (all bodies)
-    achieved = flops / (force_ms / 1e3) / 1e12
-    executed = (8.0 * tested + 12.0 * pairs) / (force_ms / 1e3) / 1e12
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    useful_gbs = 56.0 * value / world / 1e9
-    line = {
-        "metric": "relaxation particle-iterations/s",
-        "value": value, "unit": "particle-iterations/s", "n_gpus": world, "steps": K, "warmup": Wm,
-        "ms_per_step": tot_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"icosphere_l5+torus_256x64 dx={args.dx}", "bodies": len(asm), "particles": n,
-                   "iterations_per_step": G, "form": "batched + CUDA graph",
-                   "l2": "flushed between steps (256 MiB write), working set < L2"},
-        "roofline": {"bound": "alu", "kernel": "k_force", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": K_FORCE_DRAM_BYTES.get(round(args.dx, 6)),
-                     "peak_kind": f"FP32 {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz ({peak_kind} clock)",
-                     "flops_per_launch": flops, "candidates": cand, "pairs": pairs, "force_ms": force_ms,
-                     "tested": tested, "executed_TFLOPs": executed, "executed_frac": executed / fp32_peak},
-        "hbm": {"useful_bytes_per_particle_iteration": 56, "useful_GBps": useful_gbs,
-                "frac_of_measured": useful_gbs / hbm},
-        "phase_ms_per_iteration": {**phases, "note": "one extra replay with event records in the graph"},
-        "gpu_launches": kpi * G * K,
-        "autotune": tuned,
-        "clocks": clk,
-    }
-    line.update(extras)
     if not args.no_extras and rank == 0:
-        cpu_v, cores, dt = cpu_oracle(asm, 1)
-        line["cpu_baseline"] = {"value": cpu_v, "unit": "particle-iterations/s", "cores": cores, "kind": "oracle",
-                                "sample": f"one FP64 iteration of both bodies ({dt:.1f} s)"}
+        import oracle
+        frac = 1.0 / 16 if args.workload == "vehicle" else 1.0
+        obodies, on, sample = oracle_crop(asm, frac)
+        iters = 3 if args.workload == "vehicle" else 1
+        t0 = time.perf_counter()
+        for o in obodies:
+            o.relax(iters)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": on * iters / dt, "unit": "particle-iterations/s",
+                                "cores": oracle.get_threads(), "kind": "oracle",
+                                "sample": f"{iters} FP64 iterations of {sample} ({on} particles, {dt:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    batch.close()
+    for b in bodies:
+        b.close()
     if world > 1:
         dist.destroy_process_group()
 
