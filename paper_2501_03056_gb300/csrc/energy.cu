@@ -8,7 +8,11 @@
 //                2 (rho_k - W0_k) [j acts on k, k mobile] +
 //                2 (rho_j - W0_j) [k acts on j, j mobile]
 //   k_vjp        through x = y - ((y - v_a) . n) n (frozen triangle): dE/dy
-//                and the vertex gradients (atomics into gV)
+//                and, per particle, its three vertex contributions
+//   k_vertex_sum dE/dverts: the contributions sorted by vertex (stable radix
+//                sort, so each vertex keeps them in key order) and summed in
+//                that order -- no atomics, the same bits on every run
+// E is summed by a fixed two-level tree (k_sum_fixed), also run to run exact.
 // energy_accel() turns -dE/dx into the acceleration of the limited step, so
 // the same step / projection kernel runs an energy-descent relaxation.
 #include <cfloat>
@@ -130,8 +134,8 @@ __device__ inline void rho_range(const float4 *__restrict__ pos_p, const float4 
 }
 
 // k_rho: coef_s[k] = 2 (rho_k - W0_k) for mobile k in key order, else 0 (and
-// 0 in the padding slot N, read by the slot pairs of an odd count); E gets
-// the sum of (rho_k - W0_k)^2 (FP64 atomics)
+// 0 in the padding slot N, read by the slot pairs of an odd count); E[k]
+// (nullable) gets (rho_k - W0_k)^2 in FP64 (0 for fixed particles)
 __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
                                              int64_t N, const AsmParams *__restrict__ P,
                                              const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
@@ -163,10 +167,28 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, c
     } else if (k <= N) {
         coef_s[k] = 0.f;
     }
-    if (E) {
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-        if ((threadIdx.x & 31) == 0 && e != 0.0) atomicAdd(E, e);
+    if (E && active) E[k] = e;
+}
+
+// Deterministic sum of x[0..n): a fixed grid of kSumBlocks blocks strides
+// over x in a fixed order, each block reduces by a fixed shared-memory
+// tree into part[block], and one block then reduces part[] the same way
+// (out = part when it is the second stage).  No atomics: the bits do not
+// depend on scheduling.
+constexpr int kSumBlocks = 256;
+
+__global__ void __launch_bounds__(TPB) k_sum_fixed(const double *__restrict__ x, int64_t n,
+                                                   double *__restrict__ out) {
+    __shared__ double sh[TPB];
+    double a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < n; i += (int64_t)gridDim.x * TPB) a += x[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = TPB / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
 // sum over the slots of (1 - q/2)^3 c_kj (q - p), c_kj = ek [j acts on k] +
@@ -263,15 +285,19 @@ __global__ void k_project_frozen(const float *__restrict__ y, const float4 *__re
     out[i] = make_float4(yy.x, yy.y, yy.z, p.w);
 }
 
+// vkey[3k + c] / vcon[3k + c]: vertex and contribution of corner c of the
+// frozen triangle of the particle in key slot k (vertex nv = none)
 __global__ void k_vjp(const float4 *__restrict__ gx_s, const uint32_t *__restrict__ id_s, int64_t N,
                       const float *__restrict__ y, const float4 *__restrict__ pos, const int32_t *__restrict__ cons,
-                      const float *__restrict__ V, const int32_t *__restrict__ T, float *__restrict__ gy,
-                      float *__restrict__ gV) {
+                      const float *__restrict__ V, const int32_t *__restrict__ T, int nv, float *__restrict__ gy,
+                      uint32_t *__restrict__ vkey, float4 *__restrict__ vcon) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (k >= N) return;
     const uint32_t i = id_s[k];
     const float3 g = f3(gx_s[k]);
     const int t = cons[i];
+    if (vkey)
+        for (int c = 0; c < 3; c++) vkey[3 * k + c] = (uint32_t)nv;
     if (!(cls_of(pos[i].w) == kClsS && t >= 0)) {
         if (gy) {
             gy[3 * (size_t)i] = g.x;
@@ -294,21 +320,39 @@ __global__ void k_vjp(const float4 *__restrict__ gx_s, const uint32_t *__restric
         gy[3 * (size_t)i + 1] = g.y - gn * n.y;
         gy[3 * (size_t)i + 2] = g.z - gn * n.z;
     }
-    if (!gV) return;
+    if (!vkey) return;
     // dE along dn with u = -(gn (y - a) + s g), dn = (I - n n^T) dm / |m|
     const float3 u = make_float3(-(gn * ya.x + s * g.x), -(gn * ya.y + s * g.y), -(gn * ya.z + s * g.z));
     const float un = dot(u, n);
     const float3 ut = make_float3((u.x - un * n.x) / ml, (u.y - un * n.y) / ml, (u.z - un * n.z) / ml);
     const float3 gb = cross(e2, ut), gc = cross(ut, e1);
-    atomicAdd(gV + 3 * ib, gb.x);
-    atomicAdd(gV + 3 * ib + 1, gb.y);
-    atomicAdd(gV + 3 * ib + 2, gb.z);
-    atomicAdd(gV + 3 * ic, gc.x);
-    atomicAdd(gV + 3 * ic + 1, gc.y);
-    atomicAdd(gV + 3 * ic + 2, gc.z);
-    atomicAdd(gV + 3 * ia, -gb.x - gc.x + gn * n.x);
-    atomicAdd(gV + 3 * ia + 1, -gb.y - gc.y + gn * n.y);
-    atomicAdd(gV + 3 * ia + 2, -gb.z - gc.z + gn * n.z);
+    vkey[3 * k] = (uint32_t)ia;
+    vcon[3 * k] = make_float4(-gb.x - gc.x + gn * n.x, -gb.y - gc.y + gn * n.y, -gb.z - gc.z + gn * n.z, 0.f);
+    vkey[3 * k + 1] = (uint32_t)ib;
+    vcon[3 * k + 1] = make_float4(gb.x, gb.y, gb.z, 0.f);
+    vkey[3 * k + 2] = (uint32_t)ic;
+    vcon[3 * k + 2] = make_float4(gc.x, gc.y, gc.z, 0.f);
+}
+
+// gV[v] = the contributions of vertex v summed in FP64 in sorted order (the
+// stable sort keeps key-slot order within a vertex): the thread at the
+// start of each run of equal vertices walks its run
+__global__ void k_vertex_sum(const uint32_t *__restrict__ vkey_s, const uint32_t *__restrict__ idx_s, int64_t M,
+                             const float4 *__restrict__ vcon, int nv, float *__restrict__ gV) {
+    const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (j >= M) return;
+    const uint32_t v = vkey_s[j];
+    if (v >= (uint32_t)nv || (j > 0 && vkey_s[j - 1] == v)) return;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t q = j; q < M && vkey_s[q] == v; q++) {
+        const float4 c = vcon[idx_s[q]];
+        sx += (double)c.x;
+        sy += (double)c.y;
+        sz += (double)c.z;
+    }
+    gV[3 * (size_t)v] = (float)sx;
+    gV[3 * (size_t)v + 1] = (float)sy;
+    gV[3 * (size_t)v + 2] = (float)sz;
 }
 
 } // namespace
@@ -324,32 +368,56 @@ void energy_accel(Group &g, cudaStream_t s) {
 int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
            cudaStream_t s, std::string &err) {
     DevGroup &d = g.d;
-    float4 *xs = nullptr;
-    double *dE = nullptr;
-    if (cudaMalloc(&xs, sizeof(float4) * (size_t)std::max<int64_t>(d.N, 1)) != cudaSuccess ||
-        cudaMalloc(&dE, sizeof(double)) != cudaSuccess) {
-        cudaFree(xs);
+    const int64_t N = d.N, M = 3 * N;          // M: vertex contributions (three per particle)
+    float4 *xs = nullptr, *vcon = nullptr;
+    double *e_s = nullptr, *part = nullptr;
+    uint32_t *vk[2] = {nullptr, nullptr}, *vi[2] = {nullptr, nullptr}, *hist = nullptr, *tot = nullptr;
+    auto cleanup = [&]() {
+        void *p[] = {xs, vcon, e_s, part, vk[0], vk[1], vi[0], vi[1], hist, tot};
+        for (void *q : p)
+            if (q) cudaFree(q);
+    };
+    const size_t n1 = (size_t)std::max<int64_t>(N, 1), m1 = (size_t)std::max<int64_t>(M, 1);
+    bool fail = cudaMalloc(&xs, sizeof(float4) * n1) != cudaSuccess ||
+                cudaMalloc(&e_s, sizeof(double) * n1) != cudaSuccess ||
+                cudaMalloc(&part, sizeof(double) * (kSumBlocks + 1)) != cudaSuccess;
+    if (!fail && gV)
+        fail = cudaMalloc(&vcon, sizeof(float4) * m1) != cudaSuccess ||
+               cudaMalloc(&vk[0], 4 * m1) != cudaSuccess || cudaMalloc(&vk[1], 4 * m1) != cudaSuccess ||
+               cudaMalloc(&vi[0], 4 * m1) != cudaSuccess || cudaMalloc(&vi[1], 4 * m1) != cudaSuccess ||
+               cudaMalloc(&hist, 4 * (size_t)kMaxDigits * std::max<int64_t>(radix_tiles(M), 1)) != cudaSuccess ||
+               cudaMalloc(&tot, 4 * (size_t)kMaxDigits) != cudaSuccess;
+    if (fail) {
+        cleanup();
         err = "energy: out of device memory";
         return 3;
     }
     const float *V = verts_dev ? verts_dev : b.d_verts;
-    cudaMemsetAsync(dE, 0, sizeof(double), s);
     float4 *saved = d.pos;
-    k_project_frozen<<<nblocks(d.N), TPB, 0, s>>>(y_dev, d.pos, d.cons, d.N, V, b.d_tris, xs);
+    k_project_frozen<<<nblocks(N), TPB, 0, s>>>(y_dev, d.pos, d.cons, N, V, b.d_tris, xs);
     d.pos = xs;
     int buf = build_grid(g, s);
     d.pos = saved;
-    k_rho<<<nblocks(d.N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s, dE);
+    k_rho<<<nblocks(N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.cells, d.slab, d.epoch, d.coef_s, e_s);
+    k_sum_fixed<<<kSumBlocks, TPB, 0, s>>>(e_s, N, part);
+    k_sum_fixed<<<1, TPB, 0, s>>>(part, kSumBlocks, part + kSumBlocks);
     if (gy || gV) {
-        if (gV) cudaMemsetAsync(gV, 0, sizeof(float) * 3 * (size_t)b.nv, s);
-        k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s,
-                                             1.f, d.acc_s, nullptr);
-        k_vjp<<<nblocks(d.N), TPB, 0, s>>>(d.acc_s, d.id[buf], d.N, y_dev, d.pos, d.cons, V, b.d_tris, gy, gV);
+        k_grad<<<nblocks(N), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.cells, d.slab, d.epoch, d.coef_s,
+                                           1.f, d.acc_s, nullptr);
+        k_vjp<<<nblocks(N), TPB, 0, s>>>(d.acc_s, d.id[buf], N, y_dev, d.pos, d.cons, V, b.d_tris, b.nv, gy,
+                                          gV ? vk[0] : nullptr, vcon);
+        if (gV) {
+            cudaMemsetAsync(gV, 0, sizeof(float) * 3 * (size_t)b.nv, s);
+            int bits = 1;
+            while (bits < 32 && ((uint64_t)b.nv >> bits) != 0) bits++;
+            const int vb = radix_sort_u32(vk, vi, true, M, bits, hist, tot, s);
+            k_vertex_sum<<<nblocks(M), TPB, 0, s>>>(vk[vb], vi[vb], M, vcon, b.nv, gV);
+        }
     }
-    cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(E, part + kSumBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    cudaFree(xs);
-    cudaFree(dE);
+    cleanup();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("energy: ") + cudaGetErrorString(e);
         return 4;
