@@ -363,9 +363,11 @@ int fppg_device_sm_count(int32_t *sms);
  * classes); *amax_host (nullable) the largest |a| over moving particles.
  * stream: a cudaStream_t (NULL = legacy default); the call synchronises it.
  *
- * Every temporary lives in one static device array of about 8.4 MB (8 MiB
- * plus a few KB of parameters, flags and radix histograms) that each
- * GPU loading the library holds until the process exits.  The first call on
+ * Every temporary lives in one static device array of about 13 MB (the
+ * per-particle arrays, 5 MiB, the start table of every fine key of the
+ * grid and its counts, 8 MiB, and a few KB of parameters, flags and radix
+ * histograms) that each GPU loading the library holds until the process
+ * exits.  The first call on
  * a device looks up that array's address (cudaGetSymbolAddress) -- make it
  * before any stream capture.  All calls share the array and it keeps the
  * last call's contents, so calls that overlap on the GPU (other streams,

@@ -429,22 +429,22 @@ int fppg_debug_grid(fppg_ctx *ctx, uint32_t *key_host, uint32_t *perm_host, uint
     std::vector<uint32_t> ks(n), perm(n);
     CUDA_OR(ctx->err, cudaMemcpyAsync(ks.data(), g.d.key[buf], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR(ctx->err, cudaMemcpyAsync(perm.data(), g.d.id[buf], 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
-    std::vector<uint4> table((size_t)g.d.total_cells);
-    uint32_t ep = 0;
-    CUDA_OR(ctx->err, cudaMemcpyAsync(table.data(), g.d.cells, sizeof(uint4) * table.size(), cudaMemcpyDeviceToHost,
-                                      ctx->stream));
-    CUDA_OR(ctx->err, cudaMemcpyAsync(&ep, g.d.epoch, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    // the dense start table: cell c holds the slots [fstart[8c], fstart[8c + 8])
+    std::vector<uint32_t> table((size_t)kSlabs * (size_t)g.d.total_cells + 1);
+    CUDA_OR(ctx->err, cudaMemcpyAsync(table.data(), g.d.fstart, sizeof(uint32_t) * table.size(),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
     if (key_host)
         for (int64_t k = 0; k < n; k++) key_host[perm[k]] = ks[k];
     if (perm_host) std::copy(perm.begin(), perm.end(), perm_host);
     int64_t m = 0;
-    for (int64_t c = 0; c < (int64_t)table.size(); c++) {
-        if (table[c].z != ep) continue;
+    for (int64_t c = 0; c < g.d.total_cells; c++) {
+        const uint32_t cs = table[(size_t)kSlabs * c], ce = table[(size_t)kSlabs * (c + 1)];
+        if (ce <= cs) continue;
         if (m < cap_cells) {
             if (cells_host) cells_host[m] = (uint32_t)c;
-            if (start_host) start_host[m] = table[c].x;
-            if (end_host) end_host[m] = table[c].y;
+            if (start_host) start_host[m] = cs;
+            if (end_host) end_host[m] = ce;
         }
         m++;
     }
@@ -1024,8 +1024,8 @@ int fppg_device_sm_count(int32_t *sms) {
 }
 
 int32_t fppg_batch_kernels_per_iter(const fppg_batch *b) {
-    // keys, 3 per radix pass, gather + ranges, force, step, search
-    return b ? 5 + 3 * b->group.d.passes : -1;
+    // keys, 3 per radix pass, gather, the start scan, force, step, search
+    return b ? grid_kernels(b->group.d) + 3 : -1;
 }
 
 int64_t fppg_batch_size(const fppg_batch *b) { return b ? b->group.d.N : -1; }

@@ -236,12 +236,14 @@ int Group::alloc_particles(int64_t N, std::string &err) {
     }
     CKA(cudaMalloc(&g.hist, sizeof(uint32_t) * kMaxDigits * (size_t)g.n_tiles));
     if (!g.totals) CKA(cudaMalloc(&g.totals, sizeof(uint32_t) * kMaxDigits));
-    if (!g.cells) {
-        CKA(cudaMalloc(&g.cells, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));
-        CKA(cudaMemset(g.cells, 0, sizeof(uint4) * (size_t)std::max<int64_t>(g.total_cells, 1)));
-        CKA(cudaMalloc(&g.slab, sizeof(uint2) * (size_t)std::max<int64_t>(g.total_cells, 1)));
-        CKA(cudaMalloc(&g.epoch, sizeof(uint32_t)));
-        CKA(cudaMemset(g.epoch, 0, sizeof(uint32_t)));
+    if (!g.fstart) {
+        // dense start table of every fine key (+1), the counts it is scanned
+        // from (zero between iterations) and the scan's block sums
+        const size_t f1 = (size_t)kSlabs * (size_t)std::max<int64_t>(g.total_cells, 1) + 1;
+        CKA(cudaMalloc(&g.fstart, sizeof(uint32_t) * f1));
+        CKA(cudaMalloc(&g.fcount, sizeof(uint32_t) * f1));
+        CKA(cudaMemset(g.fcount, 0, sizeof(uint32_t) * f1));
+        CKA(cudaMalloc(&g.scan_tmp, sizeof(uint32_t) * (size_t)scan_tmp_elems((int64_t)f1)));
     }
     if (!g.amax) {
         CKA(cudaMalloc(&g.amax, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
@@ -268,7 +270,8 @@ void Group::free_all() {
     ev.clear();
     DevGroup &g = d;
     void *ptrs[] = {g.params, g.pos, g.cons, g.cons_s, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
-                    g.acc_s, g.cells, g.slab, g.epoch, g.amax, g.maxdisp, g.hist, g.totals, g.coef_s, g.work, g.work_count};
+                    g.acc_s, g.fstart, g.fcount, g.scan_tmp, g.amax, g.maxdisp, g.hist, g.totals, g.coef_s, g.work,
+                    g.work_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (owns_mesh) {

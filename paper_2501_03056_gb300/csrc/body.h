@@ -108,6 +108,8 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg = nu
 int build_grid(Group &g, cudaStream_t s);
 // the same on bare device arrays (no Group): A1-A3, A4, back to id order
 int build_grid_dev(DevGroup &d, cudaStream_t s);
+// kernel launches of one grid build (A1-A3)
+int grid_kernels(const DevGroup &d);
 void forces_dev(DevGroup &d, int block, int variant, cudaStream_t s, int32_t *count_s = nullptr,
                 int32_t *tested_s = nullptr);
 void unpermute_dev(DevGroup &d, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s, int32_t *count_out);

@@ -52,8 +52,7 @@ __device__ constexpr uint32_t felt_by_bits(int c) {
 // out.  Weights use max(1 - r / 2h, 0), so a slot beyond 2h adds exactly 0
 // and one within rounding of 2h a term below 1e-18 of the largest.
 template <typename F>
-__device__ inline void for_row_ranges(const float4 &p, bool on, const AsmParams &A, const uint4 *cells,
-                                      const uint2 *slab, uint32_t ep, F &&f) {
+__device__ inline void for_row_ranges(const float4 &p, bool on, const AsmParams &A, const uint32_t *fstart, F &&f) {
     const int ny = A.ng_n[1], nz = A.ng_n[2];
     const GridPoint g = grid_point(A, p.x, p.y, p.z);
     const int cy = g.c[1], cz = g.c[2];
@@ -65,7 +64,7 @@ __device__ inline void for_row_ranges(const float4 &p, bool on, const AsmParams 
             uint32_t s = 0xffffffffu, e = 0u;
             if (on && z >= 0 && z < nz && y >= 0 && y < ny) {
                 const uint32_t row = A.key_base + (uint32_t)A.ng_n[0] * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-                row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
+                row_slots(A, fstart, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
             }
             f(s, e);
         }
@@ -76,9 +75,9 @@ __device__ inline void for_row_ranges(const float4 &p, bool on, const AsmParams 
 // edge true for the first and the last
 template <typename F>
 __device__ inline void for_pairs(uint32_t s, uint32_t e, F &&f) {
+    if (s >= e) return;
     uint32_t m = s >> 1;
     const uint32_t m1 = (e + 1) >> 1;
-    if (m >= m1) return;
     f(std::true_type{}, m);
     if (m + 1 >= m1) return;
     for (m = m + 1; m + 1 < m1; m++) f(std::false_type{}, m);
@@ -138,8 +137,7 @@ __device__ inline void rho_range(const float4 *__restrict__ pos_p, const float4 
 // (nullable) gets (rho_k - W0_k)^2 in FP64 (0 for fixed particles)
 __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
                                              int64_t N, const AsmParams *__restrict__ P,
-                                             const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
-                                             const uint32_t *__restrict__ epoch, float *__restrict__ coef_s,
+                                             const uint32_t *__restrict__ fstart, float *__restrict__ coef_s,
                                              double *__restrict__ E) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
@@ -153,7 +151,7 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, c
     const bool all_cls = __all_sync(0xffffffffu, mbits == 0u || mbits == 0x1Fu);
     const float4 *pos_b = pos_p + (N + 1) / 2;
     float2 acc = make_float2(0.f, 0.f);
-    for_row_ranges(p, mob, A, cells, slab, *epoch, [&](uint32_t s, uint32_t e) {
+    for_row_ranges(p, mob, A, fstart, [&](uint32_t s, uint32_t e) {
         if (all_cls) rho_range<true>(pos_p, pos_b, s, e, npx, npy, npz, mbits, hih, acc);
         else rho_range<false>(pos_p, pos_b, s, e, npx, npy, npz, mbits, hih, acc);
     });
@@ -226,8 +224,7 @@ __device__ inline void grad_range(const float4 *__restrict__ pos_p, const float4
 // |out| per body over mobile particles (and out is 0 for the others)
 __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p,
                                               int64_t N, const AsmParams *__restrict__ P,
-                                              const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
-                                              const uint32_t *__restrict__ epoch, const float *__restrict__ coef_s,
+                                              const uint32_t *__restrict__ fstart, const float *__restrict__ coef_s,
                                               float sign, float4 *__restrict__ out_s, uint32_t *__restrict__ amax) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
@@ -243,7 +240,7 @@ __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, 
     const float4 *pos_b = pos_p + (N + 1) / 2;
     const bool allv = __all_sync(0xffffffffu, !active || ck == kClsV);
     float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
-    for_row_ranges(p, active, A, cells, slab, *epoch, [&](uint32_t s, uint32_t e) {
+    for_row_ranges(p, active, A, fstart, [&](uint32_t s, uint32_t e) {
         if (allv) grad_range<true>(pos_p, pos_b, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
         else grad_range<false>(pos_p, pos_b, coef2, s, e, npx, npy, npz, bk, fk, ek, hih, gx, gy, gz);
     });
@@ -359,9 +356,9 @@ __global__ void k_vertex_sum(const uint32_t *__restrict__ vkey_s, const uint32_t
 
 void energy_accel(Group &g, cudaStream_t s) {
     DevGroup &d = g.d;
-    k_rho<<<nblocks(d.N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s,
+    k_rho<<<nblocks(d.N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.fstart, d.coef_s,
                                             nullptr);
-    k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.coef_s, -1.f,
+    k_grad<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.fstart, d.coef_s, -1.f,
                                         d.acc_s, d.amax);
 }
 
@@ -398,11 +395,11 @@ int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, 
     d.pos = xs;
     int buf = build_grid(g, s);
     d.pos = saved;
-    k_rho<<<nblocks(N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.cells, d.slab, d.epoch, d.coef_s, e_s);
+    k_rho<<<nblocks(N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.fstart, d.coef_s, e_s);
     k_sum_fixed<<<kSumBlocks, TPB, 0, s>>>(e_s, N, part);
     k_sum_fixed<<<1, TPB, 0, s>>>(part, kSumBlocks, part + kSumBlocks);
     if (gy || gV) {
-        k_grad<<<nblocks(N), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.cells, d.slab, d.epoch, d.coef_s,
+        k_grad<<<nblocks(N), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.fstart, d.coef_s,
                                            1.f, d.acc_s, nullptr);
         k_vjp<<<nblocks(N), TPB, 0, s>>>(d.acc_s, d.id[buf], N, y_dev, d.pos, d.cons, V, b.d_tris, b.nv, gy,
                                           gV ? vk[0] : nullptr, vcon);

@@ -6,11 +6,15 @@
 //               key, id  u32[N] x 2 (radix ping-pong), pos_s / acc_s float4[N]
 //               in key order, pos_p float4[N + 1] pos_s as slot pairs;
 //               cert  float4[N]  {x, y, z, r}: a ball of radius r around x
-//               that is free of surface and inside the body (r = 0: none) key = 8 (key_base + cell) + x-slab of the cell
-//   grid        cells uint4[total cells] {start, end, epoch, 0}: dense over
-//               every body's neighbour grid, validated by epoch (never cleared)
-//               slab  uint2[total cells]  low bytes of the first slot of
-//               x-slabs 1..7 of the cell (valid with the cell's epoch)
+//               that is free of surface and inside the body (r = 0: none)
+//               key = 8 (key_base + cell) + x-slab of the cell
+//   grid        fstart u32[F + 1], F = 8 x total cells: the first key slot
+//               whose fine key is >= f, dense over every fine key of every
+//               body's neighbour grid (an exclusive scan of fcount, rebuilt
+//               every iteration), so the slots of fine keys [a, b] are
+//               [fstart[a], fstart[b + 1])
+//               fcount u32[F + 1]: particles per fine key, zero between
+//               iterations (the scan clears it as it reads it)
 //   triangles   geo   float4[5 nt]  v0, n, m0, m1 (w = c1), m2 (w = c2)
 //               vx    float4[3 nt]  v0, v1, v2 (w = vertex id bits)
 //               pn    float4[6 nt]  edge pseudonormals 0..2, vertex ones 0..2
@@ -130,9 +134,9 @@ struct DevGroup {
     float4 *pos_p = nullptr;   // pos_s as slot pairs: [m] {x, x', y, y'}, [(N + 1) / 2 + m] {z, z', w, w'}
     float4 *cert = nullptr;    // id order: inside certificate {centre, radius} of a volume particle
     float4 *acc_s = nullptr;
-    uint4 *cells = nullptr;
-    uint2 *slab = nullptr;
-    uint32_t *epoch = nullptr;
+    uint32_t *fstart = nullptr;   // F + 1 entries (F = kSlabs * total_cells)
+    uint32_t *fcount = nullptr;   // F + 1 entries, zero between iterations
+    uint32_t *scan_tmp = nullptr; // scan_tmp_elems(F + 1) entries
     uint32_t *amax = nullptr;
     uint32_t *maxdisp = nullptr;
     int4 *work = nullptr;          // search queue {key slot, trial point}, N entries
@@ -244,18 +248,19 @@ __device__ inline float row_gap(float t, int c, int d, float slack) {
 
 // Slot range [s, e) of the particles of grid row `row` (index of its x = 0
 // cell) whose fine x lies within reach of the particle, given the row's
-// y / z gaps.  Empty (s = ~0, e = 0) when no point of the row can be within
-// 2h.  The range covers every cell x0..x1 of the 3 x 3 x 3 stencil that the
-// reach touches; in the end cells it starts / stops at a slab boundary
-// unless the cell holds more than 255 particles (then the whole cell).
-__device__ inline void row_slots(const AsmParams &A, const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
-                                 uint32_t ep, const GridPoint &g, float gy, float gz, uint32_t row, uint32_t &s,
-                                 uint32_t &e) {
+// y / z gaps: the fine keys from the slab of t - w to the slab of t + w,
+// cut to the cells x0..x1 of the 3 x 3 x 3 stencil, read from the dense
+// start table (two loads).  Empty (s >= e) when no point of the row can be
+// within 2h.  w carries the slack of the FP32 reach arithmetic, and the
+// approximate root is within a few 2^-23 of the exact one, far inside the
+// 2^-12 relative margin of slab_r2.
+__device__ inline void row_slots(const AsmParams &A, const uint32_t *__restrict__ fstart, const GridPoint &g,
+                                 float gy, float gz, uint32_t row, uint32_t &s, uint32_t &e) {
     s = 0xffffffffu;
     e = 0u;
     const float w2 = A.slab_r2 - gy * gy - gz * gz;
     if (!(w2 > 0.0f)) return;
-    const float w = sqrtf(w2) + g.slack;
+    const float w = sqrt_approx(w2) + g.slack;
     // fine coordinates of t -/+ w under the key's own clamp to [0, 8 n - 1]
     // (monotone, so every point within reach has its fine x in [flo, fhi]),
     // cut to the stencil cells x0..x1; the particle's own slab is inside
@@ -264,22 +269,19 @@ __device__ inline void row_slots(const AsmParams &A, const uint4 *__restrict__ c
                             (float)(kSlabs * x0));
     const float fhi = fminf(fmaxf(floorf((g.t[0] + w) * (float)kSlabs), 0.0f), (float)(kSlabs * x1 + kSlabs - 1));
     if (!(flo <= fhi)) return;   // only for non-finite coordinates
-    const int lo = (int)flo, hi = (int)fhi;
-    const int xl = lo >> kSlabBits, xh = hi >> kSlabBits, sl = lo & (kSlabs - 1), sh = hi & (kSlabs - 1);
-    for (int x = xl; x <= xh; x++) {
-        const uint4 c = cells[row + (uint32_t)x];
-        if (c.z != ep) continue;
-        uint32_t cs = c.x, ce = c.y;
-        const bool cut_lo = x == xl && sl > 0, cut_hi = x == xh && sh < kSlabs - 1;
-        if ((cut_lo || cut_hi) && ce - cs <= 255u) {
-            const uint2 b = slab[row + (uint32_t)x];
-            const uint64_t v = ((uint64_t)b.y << 32) | b.x;
-            if (cut_lo) cs = c.x + (((uint32_t)(v >> (8 * (sl - 1))) - c.x) & 0xffu);
-            if (cut_hi) ce = c.x + (((uint32_t)(v >> (8 * sh)) - c.x) & 0xffu);
-        }
-        s = min(s, cs);
-        e = max(e, ce);
+    const uint32_t f0 = kSlabs * row;
+    const uint32_t a = fstart[f0 + (uint32_t)(int)flo], b = fstart[f0 + (uint32_t)(int)fhi + 1u];
+    if (a < b) {       // empty stays (~0, 0): neutral under a warp min / max
+        s = a;
+        e = b;
     }
+}
+
+// slots [s, e) of the whole cells x0..x1 of grid row `row`
+__device__ inline void cells_slots(const uint32_t *__restrict__ fstart, uint32_t row, int x0, int x1, uint32_t &s,
+                                   uint32_t &e) {
+    s = fstart[kSlabs * (row + (uint32_t)x0)];
+    e = fstart[kSlabs * (row + (uint32_t)x1 + 1u)];
 }
 
 // ---- triangle grid -------------------------------------------------------
@@ -340,5 +342,11 @@ constexpr int kMaxDigits = 256;
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev, uint32_t *tmp,
                         int64_t tmp_elems, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t n);
+// the same scan of counts that are cleared (set to 0) as they are read, so
+// the count array starts the next accumulation at zero
+void exclusive_scan_u32_clear(uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, int64_t tmp_elems,
+                              cudaStream_t s);
+// kernel launches of exclusive_scan_u32 / _clear on n elements (no total)
+int scan_launches(int64_t n);
 
 } // namespace fppg

@@ -10,7 +10,7 @@
 // cudaMalloc / cudaFree may perform.  The paper has no counterpart.
 //
 // The scratch below is a plain __device__ array: every GPU that loads the
-// library holds it (about 8 MB) until the process exits.  In host code its
+// library holds it (about 13 MB) until the process exits.  In host code its
 // name is only a host-side stand-in, not a device address, so the address is
 // looked up with cudaGetSymbolAddress once per device (on the first call
 // made with that device current; make that first call before any stream
@@ -33,7 +33,7 @@ constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // byte offsets inside the scratch array
 constexpr size_t kOffParams = 0;
-constexpr size_t kOffFlags = kOffParams + align256(sizeof(AsmParams));        // epoch, amax, maxdisp, queue (2), error
+constexpr size_t kOffFlags = kOffParams + align256(sizeof(AsmParams));        // (unused), amax, maxdisp, queue (2), error
 constexpr size_t kOffTotals = kOffFlags + 256;
 constexpr size_t kOffHist = kOffTotals + align256(kMaxDigits * 4);
 constexpr size_t kOffPos = kOffHist + align256(kMaxDigits * 4 * kStaticMaxTiles);
@@ -44,9 +44,12 @@ constexpr size_t kOffId1 = kOffId0 + align256(4 * kStaticMaxN);
 constexpr size_t kOffPosS = kOffId1 + align256(4 * kStaticMaxN);
 constexpr size_t kOffPosP = kOffPosS + align256(16 * kStaticMaxN);
 constexpr size_t kOffAccS = kOffPosP + align256(16 * (kStaticMaxN + 1));
-constexpr size_t kOffCells = kOffAccS + align256(16 * kStaticMaxN);
-constexpr size_t kOffSlab = kOffCells + align256(16 * kStaticMaxCells);
-constexpr size_t kScratchBytes = kOffSlab + align256(8 * kStaticMaxCells);
+constexpr int64_t kStaticMaxFine = kSlabs * kStaticMaxCells + 1;   // fine keys + 1
+constexpr int64_t kStaticScanTmp = 2048;                            // block sums of that scan (1030 needed)
+constexpr size_t kOffFstart = kOffAccS + align256(16 * kStaticMaxN);
+constexpr size_t kOffFcount = kOffFstart + align256(4 * kStaticMaxFine);
+constexpr size_t kOffScan = kOffFcount + align256(4 * kStaticMaxFine);
+constexpr size_t kScratchBytes = kOffScan + align256(4 * kStaticScanTmp);
 
 __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
@@ -160,20 +163,27 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     d.pos_s = (float4 *)(base + kOffPosS);
     d.pos_p = (float4 *)(base + kOffPosP);
     d.acc_s = (float4 *)(base + kOffAccS);
-    d.cells = (uint4 *)(base + kOffCells);
-    d.slab = (uint2 *)(base + kOffSlab);
-    d.epoch = flags + 0;
+    d.fstart = (uint32_t *)(base + kOffFstart);
+    d.fcount = (uint32_t *)(base + kOffFcount);
+    d.scan_tmp = (uint32_t *)(base + kOffScan);
     d.amax = flags + 1;
     d.maxdisp = flags + 2;
     d.work_count = flags + 3;   // two words: front and back of the search queue
     d.hist = (uint32_t *)(base + kOffHist);
     d.totals = (uint32_t *)(base + kOffTotals);
     uint32_t *error = flags + 5;
-    // the error word and amax start at zero on every call; the cell table
-    // needs no clearing (entries are valid only for the current epoch)
+    // the error word, amax and the per-fine-key counts start at zero on
+    // every call (the scan clears the counts, but a call that stopped
+    // half-way would leave them set)
+    const int64_t fine1 = kSlabs * cells + 1;
+    if (scan_tmp_elems(fine1) > kStaticScanTmp) {
+        set_global_error("fppg_forces_static: scan scratch too small");
+        return FPPG_ERR_INTERNAL;
+    }
     if (cudaMemcpyAsync(d.params, &A, sizeof(A), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(error, 0, sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMemsetAsync(d.amax, 0, sizeof(uint32_t), s) != cudaSuccess) {
+        cudaMemsetAsync(d.amax, 0, sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(d.fcount, 0, sizeof(uint32_t) * (size_t)fine1, s) != cudaSuccess) {
         set_global_error("fppg_forces_static: could not set up the scratch");
         return FPPG_ERR_CUDA;
     }

@@ -2,11 +2,11 @@
 //
 // Per iteration, all bodies at once:
 //   k_keys          A1  cell key per particle (FP32 rule, no contraction);
-//                       zeroes the per-body amax / max-move and bumps the
-//                       grid epoch
+//                       zeroes the per-body amax / max-move
 //   radix sort      A2  stable (key, id) sort, 8-bit digits
-//   k_gather_ranges A3  positions in key order; start / end / epoch of every
-//                       occupied cell (the cell table is never cleared)
+//   k_gather        A3  positions in key order; particles per fine key
+//   start scan      A3  the dense table of the first slot of every fine key
+//                       (exclusive scan of the counts, which it clears)
 //   k_force         A4  Eq. 15 over the 3 x 3 rows of 3 cells around the
 //                       particle (each row is one contiguous slot range),
 //                       amax per body by a labelled warp max + atomicMax
@@ -48,11 +48,48 @@ __device__ inline void labelled_max(uint32_t *dst, int label, float v) {
     if ((uint32_t)(__ffs(peers) - 1) == (threadIdx.x & 31u) && m) atomicMax(dst + label, m);
 }
 
+// The same over a whole block (every thread must call it): a warp whose
+// lanes share one label leaves (label, max) in shared memory and thread 0
+// adds one atomic per run of equal labels over the warps; a warp that
+// mixes labels uses labelled_max.  On one large body this turns one
+// same-address atomic per warp into one per block.
+template <int WARPS>
+__device__ inline void block_labelled_max(uint32_t *dst, int label, float v, int *s_lab, uint32_t *s_max) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lab0 = __shfl_sync(0xffffffffu, label, 0);
+    if (__all_sync(0xffffffffu, label == lab0)) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+        if (lane == 0) {
+            s_lab[w] = lab0;
+            s_max[w] = m;
+        }
+    } else {
+        labelled_max(dst, label, v);
+        if (lane == 0) {
+            s_lab[w] = -1;
+            s_max[w] = 0u;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run_l = -1;
+        uint32_t run_m = 0u;
+        for (int q = 0; q < WARPS; q++) {
+            if (s_lab[q] != run_l) {
+                if (run_m) atomicMax(dst + run_l, run_m);
+                run_l = s_lab[q];
+                run_m = 0u;
+            }
+            if (run_l >= 0) run_m = max(run_m, s_max[q]);
+        }
+        if (run_m) atomicMax(dst + run_l, run_m);
+    }
+}
+
 // ---- A1 ----------------------------------------------------------------------
 __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, int64_t N,
                                               const AsmParams *__restrict__ P, uint32_t *__restrict__ key,
-                                              uint32_t *__restrict__ epoch, uint32_t *__restrict__ amax,
-                                              uint32_t *__restrict__ maxdisp, int B,
+                                              uint32_t *__restrict__ amax, uint32_t *__restrict__ maxdisp, int B,
                                               uint32_t *__restrict__ work_count) {
     int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (i < B) {
@@ -60,7 +97,6 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
         maxdisp[i] = 0u;
     }
     if (i == 0) {
-        epoch[0] += 1u;
         work_count[0] = 0u;
         work_count[1] = 0u;
     }
@@ -75,21 +111,14 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
 }
 
 // ---- A3 ----------------------------------------------------------------------
-// Positions in key order (also as slot pairs), and per occupied cell its
-// slot range [start, end)
-// with the epoch, plus the first slot of each x-slab 1..7 (low byte, so a
-// reader rebuilds it as start + ((byte - start) & 255) when the cell holds
-// at most 255 particles).  Boundary b of a cell is written by the slot that
-// starts the first fine-key run with slab >= b, or by the cell's last slot
-// (value end) when no slab >= b is present: exactly one writer per byte.
-__global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restrict__ key_s,
-                                                       const uint32_t *__restrict__ id_s,
-                                                       const float4 *__restrict__ pos, int64_t N,
-                                                       float4 *__restrict__ pos_s, float4 *__restrict__ pos_p,
-                                                       uint32_t *__restrict__ cells, uint8_t *__restrict__ slab,
-                                                       const uint32_t *__restrict__ epoch,
-                                                       const int32_t *__restrict__ cons,
-                                                       int32_t *__restrict__ cons_s) {
+// Positions in key order (also as slot pairs) and the number of particles of
+// every fine key: the sorted keys of a warp form runs of equal keys, and the
+// first lane of each run adds the run's length (one atomic per run; the
+// start scan turns the counts into the dense table of first slots).
+__global__ void __launch_bounds__(TPB) k_gather(const uint32_t *__restrict__ key_s, const uint32_t *__restrict__ id_s,
+                                                const float4 *__restrict__ pos, int64_t N, float4 *__restrict__ pos_s,
+                                                float4 *__restrict__ pos_p, uint32_t *__restrict__ fcount,
+                                                const int32_t *__restrict__ cons, int32_t *__restrict__ cons_s) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool valid = k < N;
     const uint32_t id = valid ? id_s[k] : 0u;
@@ -108,23 +137,17 @@ __global__ void __launch_bounds__(TPB) k_gather_ranges(const uint32_t *__restric
     } else if (k <= N) {
         pos_p[(N + 1) / 2 + (k >> 1)] = make_float4(oz, q.z, ow, q.w);
     }
-    if (!valid) return;
-    pos_s[k] = q;
-    const uint32_t f = key_s[k], c = f >> kSlabBits, sk = f & (kSlabs - 1);
-    const bool first = k == 0 || (key_s[k - 1] >> kSlabBits) != c;
-    const bool last = k == N - 1 || (key_s[k + 1] >> kSlabBits) != c;
-    uint8_t *b = slab + 8 * (size_t)c;
-    if (first) {
-        cells[4 * (size_t)c + 0] = (uint32_t)k;
-        cells[4 * (size_t)c + 2] = *epoch;
-        for (uint32_t q = 1; q <= sk; q++) b[q - 1] = (uint8_t)k;
-    } else {
-        const uint32_t sp = key_s[k - 1] & (kSlabs - 1);
-        for (uint32_t q = sp + 1; q <= sk; q++) b[q - 1] = (uint8_t)k;
-    }
-    if (last) {
-        cells[4 * (size_t)c + 1] = (uint32_t)(k + 1);
-        for (uint32_t q = sk + 1; q < (uint32_t)kSlabs; q++) b[q - 1] = (uint8_t)(k + 1);
+    if (valid) pos_s[k] = q;
+    // runs of equal fine keys inside the warp (lanes past N never start one)
+    const int lane = threadIdx.x & 31;
+    const uint32_t f = valid ? key_s[k] : 0xffffffffu;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, f, 1);
+    const uint32_t starts = __ballot_sync(0xffffffffu, valid && (lane == 0 || prev != f));
+    const uint32_t ends = __ballot_sync(0xffffffffu, valid) ;
+    if ((starts >> lane) & 1u) {
+        const uint32_t later = starts & ~((2u << lane) - 1u);          // run starts after this lane
+        const int stop = later ? __ffs(later) - 1 : 32 - __clz(ends);  // first lane of the next run, or past the last valid
+        atomicAdd(fcount + f, (uint32_t)(stop - lane));
     }
 }
 
@@ -225,9 +248,9 @@ template <bool ALL, bool COUNT>
 __device__ inline void force_range2(const float4 *__restrict__ pos_p, const float4 *__restrict__ pos_b,
                                     const float2 npx, const float2 npy, const float2 npz, uint32_t mbits, float R2,
                                     float hih, uint32_t s, uint32_t e, PairAcc &acc, uint32_t self) {
+    if (s >= e) return;
     uint32_t m = s >> 1;
     const uint32_t m1 = (e + 1) >> 1;
-    if (m >= m1) return;
     pair_step<ALL, COUNT, true>(pos_p, pos_b, m, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
     if (m + 1 >= m1) return;
     for (m = m + 1; m + 1 < m1; m++)
@@ -239,9 +262,8 @@ template <int VARIANT, bool COUNT>
 // (at most 48 registers: five 256-thread blocks per SM)
 __global__ void __launch_bounds__(TPB, 5)
     k_force(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p, int64_t N,
-            const AsmParams *__restrict__ P, const uint4 *__restrict__ cells, const uint2 *__restrict__ slab,
-            const uint32_t *__restrict__ epoch, float4 *__restrict__ acc_s, uint32_t *__restrict__ amax,
-            int32_t *__restrict__ count_s, int32_t *__restrict__ tested_s) {
+            const AsmParams *__restrict__ P, const uint32_t *__restrict__ fstart, float4 *__restrict__ acc_s,
+            uint32_t *__restrict__ amax, int32_t *__restrict__ count_s, int32_t *__restrict__ tested_s) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -251,7 +273,6 @@ __global__ void __launch_bounds__(TPB, 5)
     const bool mob = active && is_mobile(cls, A);
     // the counting form also counts the neighbours of fixed particles
     const uint32_t mbits = (mob || (COUNT && active)) ? acts_on_bits(cls) : 0u;
-    const uint32_t ep = *epoch;
     const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
     const GridPoint g = grid_point(A, p.x, p.y, p.z);
     const int cy = g.c[1], cz = g.c[2];
@@ -278,7 +299,7 @@ __global__ void __launch_bounds__(TPB, 5)
             uint32_t s = 0xffffffffu, e = 0u;
             if (mbits && z >= 0 && z < nz && y >= 0 && y < ny) {
                 const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-                row_slots(A, cells, slab, ep, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
+                row_slots(A, fstart, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
             }
             if (COUNT && e > s) tested += (int)(e - s);
             if (VARIANT == 1 && shared_row) {
@@ -311,15 +332,14 @@ __global__ void __launch_bounds__(TPB, 5)
 // particle's own 27 cells (the full stencil, no reach cut), per particle in
 // key order (diagnostics).
 __global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s, int64_t N,
-                                               const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                               const uint32_t *__restrict__ epoch, int32_t *__restrict__ count_s,
-                                               int32_t *__restrict__ cand_s) {
+                                               const AsmParams *__restrict__ P, const uint32_t *__restrict__ fstart,
+                                               int32_t *__restrict__ count_s, int32_t *__restrict__ cand_s) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (k >= N) return;
     const float4 p = pos_s[k];
     const int cls = cls_of(p.w);
     const AsmParams &A = P[body_of(p.w)];
-    const uint32_t mbits = acts_on_bits(cls), ep = *epoch;
+    const uint32_t mbits = acts_on_bits(cls);
     const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
     const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
     const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
@@ -328,14 +348,8 @@ __global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s,
     for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
         for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
             const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-            uint32_t s = 0xffffffffu, e = 0u;
-            for (int x = max(cx - 1, 0); x <= min(cx + 1, nx - 1); x++) {
-                const uint4 c = cells[row + (uint32_t)x];
-                if (c.z == ep) {
-                    s = min(s, c.x);
-                    e = max(e, c.y);
-                }
-            }
+            uint32_t s, e;
+            cells_slots(fstart, row, max(cx - 1, 0), min(cx + 1, nx - 1), s, e);
             if (e > s) cand += (int)(e - s);
             for (uint32_t j = s; j < e; j++) {
                 const float4 q = pos_s[j];
@@ -787,7 +801,9 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
         if (qs) work[bs + __popc(ms & lanemask_lt())] = it;
         if (qv) work[N - 1 - (int64_t)(bv + __popc(mv & lanemask_lt()))] = it;
     }
-    labelled_max(maxdisp, b, disp);
+    __shared__ int s_lab[TPB / 32];
+    __shared__ uint32_t s_max[TPB / 32];
+    block_labelled_max<TPB / 32>(maxdisp, b, disp, s_lab, s_max);
 }
 
 // entry e of the two-ended search queue: the nf front entries first, then
@@ -969,6 +985,10 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
                                                        float4 *__restrict__ cert) {
     const uint32_t nf = work_count[0], n = nf + work_count[1];
     const uint32_t stride = gridDim.x * TPB;
+    // this thread's running max move of body run_b, added when the body
+    // changes and once at the end (the queue is in key order: few changes)
+    int run_b = 0;
+    float run = 0.f;
     for (uint32_t e0 = blockIdx.x * TPB + (threadIdx.x & ~31u); e0 < n; e0 += stride) {
         const uint32_t e = e0 + (threadIdx.x & 31u);
         int b = 0;
@@ -1006,9 +1026,15 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
                 const float3 w = x - f3(p);
                 disp = sqrtf(dot3(w, w));
             }
+            if (b != run_b) {
+                if (run > 0.f) atomicMax(maxdisp + run_b, __float_as_uint(run));
+                run_b = b;
+                run = 0.f;
+            }
+            run = fmaxf(run, disp);
         }
-        labelled_max(maxdisp, b, disp);
     }
+    labelled_max(maxdisp, run_b, run);
 }
 
 // ---- diagnostics --------------------------------------------------------------
@@ -1073,16 +1099,14 @@ __global__ void k_project_points(const float *__restrict__ y, const int32_t *__r
 // kernel sum rho = W(0) + sum of W over masked neighbours; per-class sums in
 // FP64; smallest masked pair distance over mobile particles
 __global__ void __launch_bounds__(TPB) k_density(const float4 *__restrict__ pos_s, int64_t N,
-                                                 const AsmParams *__restrict__ P, const uint4 *__restrict__ cells,
-                                                 const uint32_t *__restrict__ epoch, float *__restrict__ rho_s,
-                                                 uint32_t *__restrict__ minpair) {
+                                                 const AsmParams *__restrict__ P, const uint32_t *__restrict__ fstart,
+                                                 float *__restrict__ rho_s, uint32_t *__restrict__ minpair) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (k >= N) return;
     const float4 p = pos_s[k];
     const int cls = cls_of(p.w);
     const AsmParams &A = P[body_of(p.w)];
     const uint32_t mbits = acts_on_bits(cls);
-    const uint32_t ep = *epoch;
     const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
     const int cx = cell_coord(p.x, A.ng_o[0], A.ng_inv, nx);
     const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, ny);
@@ -1091,14 +1115,8 @@ __global__ void __launch_bounds__(TPB) k_density(const float4 *__restrict__ pos_
     for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
         for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
             const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
-            uint32_t s = 0xffffffffu, e = 0u;
-            for (int x = max(cx - 1, 0); x <= min(cx + 1, nx - 1); x++) {
-                uint4 c = cells[row + (uint32_t)x];
-                if (c.z == ep) {
-                    s = min(s, c.x);
-                    e = max(e, c.y);
-                }
-            }
+            uint32_t s, e;
+            cells_slots(fstart, row, max(cx - 1, 0), min(cx + 1, nx - 1), s, e);
             for (uint32_t j = s; j < e; j++) {
                 const float4 q = pos_s[j];
                 const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
@@ -1137,23 +1155,24 @@ __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__re
 
 // ---- host driver ----------------------------------------------------------------
 int build_grid_dev(DevGroup &d, cudaStream_t s) {
-    k_keys<<<nblocks(std::max<int64_t>(d.N, d.B)), TPB, 0, s>>>(d.pos, d.N, d.params, d.key[0], d.epoch, d.amax,
-                                                                 d.maxdisp, d.B, d.work_count);
+    k_keys<<<nblocks(std::max<int64_t>(d.N, d.B)), TPB, 0, s>>>(d.pos, d.N, d.params, d.key[0], d.amax, d.maxdisp,
+                                                                 d.B, d.work_count);
     int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
-    k_gather_ranges<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s,
-                                                  d.pos_p,
-                                                  reinterpret_cast<uint32_t *>(d.cells),
-                                                  reinterpret_cast<uint8_t *>(d.slab), d.epoch, d.cons, d.cons_s);
+    k_gather<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s, d.pos_p, d.fcount, d.cons,
+                                          d.cons_s);
+    const int64_t F1 = kSlabs * d.total_cells + 1;
+    exclusive_scan_u32_clear(d.fcount, d.fstart, F1, d.scan_tmp, scan_tmp_elems(F1), s);
     return buf;
 }
+
+int grid_kernels(const DevGroup &d) { return 2 + 3 * d.passes + scan_launches(kSlabs * d.total_cells + 1); }
 
 int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
 
 void forces_dev(DevGroup &d, int tb, int variant, cudaStream_t s, int32_t *count_s, int32_t *tested_s) {
     const unsigned nbk = (unsigned)std::max<int64_t>((d.N + tb - 1) / tb, 1);
 #define FPPG_FORCE(V, C)                                                                                       \
-    k_force<V, C><<<nbk, tb, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.cells, d.slab, d.epoch, d.acc_s, d.amax,  \
-                                     count_s, tested_s)
+    k_force<V, C><<<nbk, tb, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.fstart, d.acc_s, d.amax, count_s, tested_s)
     if (count_s) {
         if (variant == 1) FPPG_FORCE(1, true);
         else FPPG_FORCE(0, true);
@@ -1168,7 +1187,7 @@ void forces(Group &g, cudaStream_t s, int32_t *count_s, int32_t *cand_s, int32_t
     DevGroup &d = g.d;
     forces_dev(d, g.force_block, g.force_variant, s, count_s, tested_s);
     if (cand_s)
-        k_count<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, nullptr, cand_s);
+        k_count<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.fstart, nullptr, cand_s);
 }
 
 void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
@@ -1236,7 +1255,7 @@ int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, d
     cudaMemcpyAsync(&md, d.maxdisp, 4, cudaMemcpyDeviceToHost, s);
     if (d.N > 0) {
         build_grid(g, s);
-        k_density<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.cells, d.epoch, rho, mp);
+        k_density<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.N, d.params, d.fstart, rho, mp);
         k_class_sums<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, rho, d.N, nullptr, sums);
     }
     double h[12];

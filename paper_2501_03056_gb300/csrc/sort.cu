@@ -257,7 +257,10 @@ int radix_sort_impl(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, in
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_BLOCK = RT * SCAN_ITEMS;
 
-__global__ void __launch_bounds__(RT) k_scan_block(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+// CLEAR: the input is set to 0 once read (a count array made ready for
+// its next accumulation)
+template <bool CLEAR>
+__global__ void __launch_bounds__(RT) k_scan_block(uint32_t *__restrict__ in, uint32_t *__restrict__ out,
                                                    int64_t n, uint32_t *__restrict__ block_sums) {
     __shared__ uint32_t wsum[RW];
     int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x * SCAN_ITEMS;
@@ -265,6 +268,7 @@ __global__ void __launch_bounds__(RT) k_scan_block(const uint32_t *__restrict__ 
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; i++) {
         v[i] = base + i < n ? in[base + i] : 0u;
+        if (CLEAR && base + i < n) in[base + i] = 0u;
         s += v[i];
     }
     uint32_t tot;
@@ -331,15 +335,36 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
         return;
     }
     int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    uint32_t *in_ = const_cast<uint32_t *>(in);   // not written without CLEAR
     if (nb == 1) {
-        k_scan_block<<<1, RT, 0, s>>>(in, out, n, nullptr);
+        k_scan_block<false><<<1, RT, 0, s>>>(in_, out, n, nullptr);
     } else {
         uint32_t *sums = tmp;
-        k_scan_block<<<(unsigned)nb, RT, 0, s>>>(in, out, n, sums);
+        k_scan_block<false><<<(unsigned)nb, RT, 0, s>>>(in_, out, n, sums);
         exclusive_scan_u32(sums, sums, nb, nullptr, tmp + nb + 1, tmp_elems - nb - 1, s);
         k_scan_add<<<(unsigned)nb, RT, 0, s>>>(out, n, sums);
     }
     if (total_dev) k_scan_total<<<1, 1, 0, s>>>(in, out, n, total_dev);
+}
+
+void exclusive_scan_u32_clear(uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, int64_t tmp_elems,
+                              cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    if (nb == 1) {
+        k_scan_block<true><<<1, RT, 0, s>>>(in, out, n, nullptr);
+    } else {
+        uint32_t *sums = tmp;
+        k_scan_block<true><<<(unsigned)nb, RT, 0, s>>>(in, out, n, sums);
+        exclusive_scan_u32(sums, sums, nb, nullptr, tmp + nb + 1, tmp_elems - nb - 1, s);
+        k_scan_add<<<(unsigned)nb, RT, 0, s>>>(out, n, sums);
+    }
+}
+
+int scan_launches(int64_t n) {
+    if (n <= 0) return 0;
+    const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    return nb == 1 ? 1 : 2 + scan_launches(nb);
 }
 
 } // namespace fppg

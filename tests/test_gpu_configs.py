@@ -77,9 +77,11 @@ def test_gear_energy_backward_on_a_5k_crop(gear):
     assert len(sel) >= 2000
     xc, cc, consc = x[sel], c[sel], cons[sel]
     o = O.Oracle(a.verts, a.tris, a.dx, a.h)
+    o.extract_features(a.dihedral_deg)        # feature particles carry their segment
     o.set_particles(xc, cc)
     o.set_state(xc.astype(np.float64), consc)
     b = pkg.Body(a.verts, a.tris, a.dx, a.h)
+    b.extract_features(a.dihedral_deg)
     b.set_particles(xc, cc)
     b.set_constraints(consc)
     rng = np.random.default_rng(8)
