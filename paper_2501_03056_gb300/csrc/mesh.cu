@@ -149,37 +149,81 @@ struct TriGrid {
     double cell;
 };
 
-template <bool EMIT>
-__global__ void k_bin(const float *__restrict__ verts, const int32_t *__restrict__ tris, int nt, TriGrid g,
-                      uint32_t *__restrict__ count, const uint32_t *__restrict__ offs, uint32_t *__restrict__ pkey,
-                      uint32_t *__restrict__ ptri) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
-    d3 a = vload(verts, tris[3 * t]), b = vload(verts, tris[3 * t + 1]), c = vload(verts, tris[3 * t + 2]);
-    double av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, cv[3] = {c.x, c.y, c.z};
-    int lo[3], hi[3];
-    for (int k = 0; k < 3; k++) {
-        double mn = fmin(av[k], fmin(bv[k], cv[k])), mx = fmax(av[k], fmax(bv[k], cv[k]));
-        lo[k] = (int)floor((mn - (double)g.o[k]) / g.cell) - 1;
-        hi[k] = (int)floor((mx - (double)g.o[k]) / g.cell) + 1;
-        lo[k] = max(lo[k], 0);
-        hi[k] = min(hi[k], g.n[k] - 1);
+// Binning of the triangles into the cells of the triangle grid, one thread
+// per (triangle, candidate cell) so that a large triangle's work is spread
+// over many threads.  The candidates of triangle t are the cells of its
+// bounding box widened by 1e-5 of a cell (the tested box is inflated by
+// 1e-6 of a cell, so no cell outside can pass the overlap test), in the
+// order z, y, x (x fastest); the accepted pairs come out in that order for
+// every triangle in turn.
+
+// per triangle: its candidate box and the number of candidate cells
+// (total64: the 64-bit sum of the counts, so that the host can refuse a
+// mesh whose candidates would not fit 32-bit offsets)
+__global__ void k_bin_boxes(const float *__restrict__ verts, const int32_t *__restrict__ tris, int nt, TriGrid g,
+                            int4 *__restrict__ box_lo, int4 *__restrict__ box_n, uint32_t *__restrict__ ncand,
+                            unsigned long long *__restrict__ total64) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long m = 0;
+    if (t < nt) {
+        d3 a = vload(verts, tris[3 * t]), b = vload(verts, tris[3 * t + 1]), c = vload(verts, tris[3 * t + 2]);
+        double av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, cv[3] = {c.x, c.y, c.z};
+        int lo[3], cnt[3];
+        m = 1;
+        for (int k = 0; k < 3; k++) {
+            double mn = fmin(av[k], fmin(bv[k], cv[k])), mx = fmax(av[k], fmax(bv[k], cv[k]));
+            double lf = floor((mn - (double)g.o[k]) / g.cell - 1e-5), hf = floor((mx - (double)g.o[k]) / g.cell + 1e-5);
+            lf = fmax(lf, 0.0);
+            hf = fmin(hf, (double)(g.n[k] - 1));
+            lo[k] = (int)lf;
+            cnt[k] = hf >= lf ? (int)(hf - lf) + 1 : 0;
+            m *= (unsigned long long)cnt[k];
+        }
+        box_lo[t] = make_int4(lo[0], lo[1], lo[2], 0);
+        box_n[t] = make_int4(cnt[0], cnt[1], cnt[2], 0);
+        ncand[t] = m > 0xffffffffull ? 0xffffffffu : (uint32_t)m;
     }
-    double hs = 0.5 * g.cell + 1e-6 * g.cell;
-    uint32_t m = 0, o = EMIT ? offs[t] : 0u;
-    for (int z = lo[2]; z <= hi[2]; z++)
-        for (int y = lo[1]; y <= hi[1]; y++)
-            for (int x = lo[0]; x <= hi[0]; x++) {
-                d3 ctr = mk((double)g.o[0] + (x + 0.5) * g.cell, (double)g.o[1] + (y + 0.5) * g.cell,
-                            (double)g.o[2] + (z + 0.5) * g.cell);
-                if (!tri_box_overlap(ctr, hs, a, b, c)) continue;
-                if (EMIT) {
-                    pkey[o + m] = (uint32_t)x + (uint32_t)g.n[0] * ((uint32_t)y + (uint32_t)g.n[1] * (uint32_t)z);
-                    ptri[o + m] = (uint32_t)t;
-                }
-                m++;
-            }
-    if (!EMIT) count[t] = m;
+    for (int o = 16; o > 0; o >>= 1) m += __shfl_down_sync(0xffffffffu, m, o);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(total64, m);
+}
+
+// per candidate q: its triangle (the last t with coff[t] <= q) and cell;
+// flag[q] = the triangle-box overlap test, key[q] the cell key
+__global__ void k_bin_test(const float *__restrict__ verts, const int32_t *__restrict__ tris, int nt, TriGrid g,
+                           const int4 *__restrict__ box_lo, const int4 *__restrict__ box_n,
+                           const uint32_t *__restrict__ coff, int64_t nc, uint32_t *__restrict__ flag,
+                           uint32_t *__restrict__ key, uint32_t *__restrict__ tri) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc) return;
+    int lo_t = 0, hi_t = nt - 1;                 // coff is ascending: upper bound of q, minus one
+    while (lo_t < hi_t) {
+        const int mid = (lo_t + hi_t + 1) >> 1;
+        if ((int64_t)coff[mid] <= q) lo_t = mid;
+        else hi_t = mid - 1;
+    }
+    const int t = lo_t;
+    const int4 l = box_lo[t], n = box_n[t];
+    const uint32_t r = (uint32_t)(q - (int64_t)coff[t]);
+    const int x = l.x + (int)(r % (uint32_t)n.x);
+    const int y = l.y + (int)((r / (uint32_t)n.x) % (uint32_t)n.y);
+    const int z = l.z + (int)(r / ((uint32_t)n.x * (uint32_t)n.y));
+    d3 a = vload(verts, tris[3 * t]), b = vload(verts, tris[3 * t + 1]), c = vload(verts, tris[3 * t + 2]);
+    const double hs = 0.5 * g.cell + 1e-6 * g.cell;
+    const d3 ctr = mk((double)g.o[0] + (x + 0.5) * g.cell, (double)g.o[1] + (y + 0.5) * g.cell,
+                      (double)g.o[2] + (z + 0.5) * g.cell);
+    flag[q] = tri_box_overlap(ctr, hs, a, b, c) ? 1u : 0u;
+    key[q] = (uint32_t)x + (uint32_t)g.n[0] * ((uint32_t)y + (uint32_t)g.n[1] * (uint32_t)z);
+    tri[q] = (uint32_t)t;
+}
+
+// the accepted candidates, compacted in candidate order
+__global__ void k_bin_emit(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
+                           const uint32_t *__restrict__ key, const uint32_t *__restrict__ tri, int64_t nc,
+                           uint32_t *__restrict__ pkey, uint32_t *__restrict__ ptri) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nc || !flag[q]) return;
+    pkey[pos[q]] = key[q];
+    ptri[pos[q]] = tri[q];
 }
 
 __global__ void k_run_flags(const uint32_t *__restrict__ key, int64_t m, uint32_t *__restrict__ flag) {
@@ -540,20 +584,58 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     }
     g.cell = (double)dx;
     uint32_t *cnt = nullptr, *off = nullptr, *total = nullptr, *scratch = nullptr;
-    int64_t sc = scan_tmp_elems(std::max<int64_t>(nt, 1) * 64);
-    CK(dalloc(&cnt, nt));
-    CK(dalloc(&off, nt));
-    CK(dalloc(&total, 1));
+    int4 *blo = nullptr, *bn = nullptr;
+    int64_t sc = scan_tmp_elems(std::max<int64_t>(nt, 1) + 1);
+    CK(dalloc(&cnt, (int64_t)nt + 1));
+    CK(dalloc(&off, (int64_t)nt + 1));
+    CK(dalloc(&blo, nt));
+    CK(dalloc(&bn, nt));
+    CK(dalloc(&total, 4));
     CK(dalloc(&scratch, sc));
-    k_bin<false><<<blocks(nt, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, cnt, nullptr, nullptr, nullptr);
+    CK(cudaMemsetAsync(total, 0, 16, s));
+    unsigned long long *total64 = reinterpret_cast<unsigned long long *>(total + 2);
+    k_bin_boxes<<<blocks(nt, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, blo, bn, cnt, total64);
     exclusive_scan_u32(cnt, off, nt, total, scratch, sc, s);
-    uint32_t npairs_h = 0, open_h = 1;
-    CK(cudaMemcpyAsync(&npairs_h, total, 4, cudaMemcpyDeviceToHost, s));
+    uint32_t ncand_h = 0, open_h = 1;
+    unsigned long long ncand64 = 0;
+    CK(cudaMemcpyAsync(&ncand_h, total, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&ncand64, total64, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&open_h, open, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    npairs = npairs_h;
     closed = nt > 0 && open_h == 0;
     cudaFree(open);
+    if (ncand64 >= (1ull << 31) || ncand64 != (unsigned long long)ncand_h) {
+        err = "triangle binning: the triangles span more than 2^31 candidate cells (dx too small for them)";
+        cudaFree(cnt);
+        cudaFree(off);
+        cudaFree(blo);
+        cudaFree(bn);
+        cudaFree(total);
+        cudaFree(scratch);
+        return 1;
+    }
+    const int64_t nc = ncand_h;
+    uint32_t *cflag = nullptr, *cpos = nullptr, *ckey = nullptr, *ctri = nullptr;
+    CK(dalloc(&cflag, nc));
+    CK(dalloc(&cpos, nc));
+    CK(dalloc(&ckey, nc));
+    CK(dalloc(&ctri, nc));
+    const int64_t sc_c = scan_tmp_elems(std::max<int64_t>(nc, 1));
+    if (sc_c > sc) {
+        cudaFree(scratch);
+        CK(dalloc(&scratch, sc_c));
+        sc = sc_c;
+    }
+    if (nc > 0) {
+        k_bin_test<<<blocks(nc, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, blo, bn, off, nc, cflag, ckey, ctri);
+        exclusive_scan_u32(cflag, cpos, nc, total + 1, scratch, sc, s);
+    } else {
+        CK(cudaMemsetAsync(total + 1, 0, 4, s));
+    }
+    uint32_t npairs_h = 0;
+    CK(cudaMemcpyAsync(&npairs_h, total + 1, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    npairs = npairs_h;
     uint32_t *pk[2] = {nullptr, nullptr}, *pt[2] = {nullptr, nullptr}, *flag = nullptr, *pos = nullptr;
     CK(dalloc(&pk[0], npairs));
     CK(dalloc(&pk[1], npairs));
@@ -561,7 +643,13 @@ int Body::build_mesh(const float *verts_host, int64_t nv_, const int32_t *tris_h
     CK(dalloc(&pt[1], npairs));
     CK(dalloc(&flag, npairs));
     CK(dalloc(&pos, npairs));
-    k_bin<true><<<blocks(nt, 128), 128, 0, s>>>(d_verts, d_tris, nt, g, nullptr, off, pk[0], pt[0]);
+    if (nc > 0) k_bin_emit<<<blocks(nc, 256), 256, 0, s>>>(cflag, cpos, ckey, ctri, nc, pk[0], pt[0]);
+    cudaFree(cflag);
+    cudaFree(cpos);
+    cudaFree(ckey);
+    cudaFree(ctri);
+    cudaFree(blo);
+    cudaFree(bn);
     int64_t pt_tiles = radix_tiles(npairs);
     cudaFree(hist);
     CK(dalloc(&hist, kMaxDigits * std::max<int64_t>(std::max(pt_tiles, tiles), 1)));

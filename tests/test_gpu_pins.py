@@ -197,8 +197,14 @@ def test_full_size_icosphere_torus_over_100_iterations():
         ox, _, _ = o.get_particles()
         err = np.abs(x.astype(np.float64) - ox).max(axis=1) / a.dx
         cond = _conditioning(a, 100)
-        assert (err < 1e-4).mean() >= 0.998, (a.name, (err >= 1e-4).sum())
-        assert err.max() <= max(1e-4, 2.0 * cond.max()), (a.name, err.max(), cond.max())
+        # the GPU may drift from the oracle as far as the oracle drifts from
+        # itself under FP32-rounding-sized nudges, and no further: at most
+        # twice as many particles beyond 1e-4 dx (and never more than 1 %),
+        # and at most twice the largest drift
+        n_gpu, n_cond = int((err >= 1e-4).sum()), int((cond >= 1e-4).sum())
+        info = (a.name, n_gpu, n_cond, len(err), err.max(), cond.max())
+        assert n_gpu <= max(2 * n_cond, 0.002 * len(err)) and n_gpu <= 0.01 * len(err), info
+        assert err.max() <= max(1e-4, 2.0 * cond.max()), info
         s, so = b.stats(), o.stats()
         for k in ("mean_S", "mean_V", "std_S", "std_V", "min_pair_over_dx"):
             assert s[k] == pytest.approx(so[k], rel=1e-2), (a.name, k, s[k], so[k])

@@ -3,7 +3,8 @@ Eqs. 24-25 and of the inside test's edge tolerance (Fig. 8).
 
 Each case is built so that the statistic or the step has a closed form that
 does not come from the oracle: a single particle's kernel sum is W(0) =
-alpha_3 (Eq. 17, reading 1), three particles give a known population
+alpha_3 (Eq. 17, normalised to a unit integral over the support 2h), three
+particles give a known population
 standard deviation, an exact FP32 lattice has one density and a smallest
 pair of exactly dx, and on a folded surface the step of a surface particle
 that crosses the fold lands where removing the normal part of the
@@ -33,8 +34,8 @@ def stats_of(xyz, cls, **kw):
 
 
 def alpha3(h):
-    # Eq. 17 with reading 1: the normalisation that makes the 3-D kernel
-    # integrate to one over its support 2h
+    # Eq. 17 with the normalisation that makes the 3-D kernel integrate to
+    # one over its support 2h (the printed 21 / (6 pi h^3) integrates to 8/3)
     return 21.0 / (16.0 * math.pi * h ** 3)
 
 
@@ -131,8 +132,9 @@ def folded_sheet(phi_deg, dx):
 def test_surface_step_removes_the_normal_part_of_the_displacement(phi_deg):
     # One surface particle on the flat piece just before the fold, pushed
     # forward and up by a singular point behind it.  It is the only mobile
-    # particle, so its displacement is exactly h / 16 along its force
-    # (reading 3); Eqs. 24-25 (reading 4) drop the part along the flat
+    # particle, so its displacement is exactly h / 16 along its force (dt =
+    # 0.25 sqrt(h / amax) with the velocity reset); Eqs. 24-25, read as acting
+    # on the displacement, drop the part along the flat
     # piece's normal, so the trial point stays in the plane z = 0, crosses
     # the fold by delta, and its only projectable foot is on the tilted
     # piece, delta cos(phi) down the slope.  Keeping the normal part would
