@@ -81,7 +81,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip plain / e2e / CPU legs")
     p.add_argument("--no-autotune", action="store_true", help="keep the default kernel configuration")
     p.add_argument("--config", default=None,
-                   help="force variant,block,search CTAs per SM (e.g. 0,128,4) instead of the autotuner")
+                   help="force variant,block,search CTAs per SM[,incremental order 0/1] (e.g. 0,128,4,1) instead "
+                        "of the autotuner")
     return p.parse_args()
 
 
@@ -309,9 +310,13 @@ def main():
             tested += t
         batch = pkg.Batch(bodies, stream=stream)
         if config:
-            v, tb, sc = (int(x) for x in config.split(","))
+            vals = [int(x) for x in config.split(",")]
+            v, tb, sc = vals[:3]
             batch.configure(v, tb, sc)
             tuned = {"force_variant": v, "force_block": tb, "search_ctas_per_sm": sc, "fixed": True}
+            if len(vals) > 3:
+                batch.set_incremental(bool(vals[3]))
+                tuned["incremental_order"] = vals[3]
         else:
             tuned = batch.autotune(G) if tune else None     # trials as long as a timed step
         batch.set_graph_iters(G)

@@ -175,7 +175,7 @@ def _conditioning(a, iters, seed=0):
     o1, o2 = O.from_assembly(a), O.from_assembly(a)
     x, cls, _ = o2.get_particles()
     pert = np.random.default_rng(seed).normal(size=x.shape) * 3e-8
-    pert[~np.isin(cls, [V])] = 0          # surface particles would leave their triangle plane
+    pert[~np.isin(cls, [S, V, F])] = 0     # fixed particles stay; the next projection puts S and F back
     o2.set_state(x + pert)
     o1.relax(iters)
     o2.relax(iters)
@@ -202,8 +202,10 @@ def test_full_size_icosphere_torus_over_100_iterations():
         # twice as many particles beyond 1e-4 dx (and never more than 1 %),
         # and at most twice the largest drift
         n_gpu, n_cond = int((err >= 1e-4).sum()), int((cond >= 1e-4).sum())
-        info = (a.name, n_gpu, n_cond, len(err), err.max(), cond.max())
+        q_gpu, q_cond = np.quantile(err, 0.999), np.quantile(cond, 0.999)
+        info = (a.name, n_gpu, n_cond, len(err), err.max(), cond.max(), q_gpu, q_cond)
         assert n_gpu <= max(2 * n_cond, 0.002 * len(err)) and n_gpu <= 0.01 * len(err), info
+        assert q_gpu <= max(1e-4, 2.0 * q_cond), info
         assert err.max() <= max(1e-4, 2.0 * cond.max()), info
         s, so = b.stats(), o.stats()
         for k in ("mean_S", "mean_V", "std_S", "std_V", "min_pair_over_dx"):
