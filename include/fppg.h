@@ -307,13 +307,27 @@ int fppg_batch_load(fppg_batch *b);
  * rows, 1 shared-row union) and triangle search (one warp per queued
  * particle on 4, 8 or 16 CTAs per SM, or — search CTAs 0 — one thread per
  * queued particle on 16 CTAs per SM),
- * keeps the fastest and restores the particle state afterwards.  The choice
- * is cached per (particle-count bucket, volume-particle share, GPU name) for
- * the life of the process; a cached choice is applied without timing.
- * Outputs (nullable): chosen variant, block size, search CTAs and the
- * measured ms per iteration (0 when taken from the cache). */
+ * then, with the fastest of those, the two ways of ordering the cell keys
+ * (a full stable sort, or the incremental repair of the previous order,
+ * fppg_batch_set_incremental), keeps the fastest and restores the particle
+ * state afterwards.  The choice is cached per (particle-count bucket,
+ * volume-particle share, GPU name) for the life of the process; a cached
+ * choice is applied without timing.  Outputs (nullable): chosen variant,
+ * block size, search CTAs, ordering (1 incremental) and the measured ms per
+ * iteration (0 when taken from the cache). */
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
-                        double *ms_per_iter);
+                        int32_t *incremental, double *ms_per_iter);
+/* How the cell keys are put in order every iteration (Sec. 3.1.3): 0 a full
+ * stable radix sort of every key; 1 the previous order repaired -- the
+ * particles whose key changed since the last grid build are sorted alone and
+ * merged with the others, which keep their order.  Both give the one order by
+ * (key, particle id), so the results are the same bits; the incremental form
+ * moves less data once few keys change per iteration (large groups start
+ * with it).  Drops a captured graph.  FPPG_ERR_ARG for other values. */
+int fppg_batch_set_incremental(fppg_batch *b, int32_t incremental);
+/* The same for the single body of a handle (its fppg_relax, fppg_stats and
+ * debug calls); a body of at least 2^21 particles starts incremental. */
+int fppg_set_incremental(fppg_ctx *ctx, int32_t incremental);
 /* fppg_set_mobile_classes for every body of the batch (a captured graph
  * keeps working: the mask is read from device memory). */
 int fppg_batch_set_mobile_classes(fppg_batch *b, int32_t mask);
@@ -339,6 +353,13 @@ const char *fppg_batch_last_error(const fppg_batch *b);
 int fppg_batch_time_force(fppg_batch *b, int32_t enable);
 int fppg_batch_force_ms(fppg_batch *b, double *ms);
 int fppg_batch_phase_ms(fppg_batch *b, double *ms4);
+
+/* Test hook for the out-of-memory paths: the k-th device allocation the
+ * library makes from now on (k = 0: the next one) fails as if the device
+ * were out of memory, once; k = -1 cancels.  Not part of the method.  The
+ * call that meets the failure returns FPPG_ERR_OOM and frees what it had
+ * allocated; handles made before stay usable.  FPPG_ERR_ARG for k < -1. */
+int fppg_debug_fail_allocation(int64_t k);
 
 /* Streaming multiprocessors of the current CUDA device
  * (cudaDevAttrMultiProcessorCount) into *sms: the unit count behind the

@@ -89,7 +89,9 @@ def lib():
                 "fppg_batch_store": [vp],
                 "fppg_batch_time_force": [vp, i32],
                 "fppg_batch_force_ms": [vp, P_(f64)],
-                "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(f64)],
+                "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(i32), P_(f64)],
+                "fppg_batch_set_incremental": [vp, i32],
+                "fppg_set_incremental": [vp, i32],
                 "fppg_batch_configure": [vp, i32, i32, i32],
                 "fppg_set_mobile_classes": [vp, i32],
                 "fppg_set_projection_rule": [vp, i32],
@@ -98,6 +100,7 @@ def lib():
                 "fppg_boolean": [vp, vp, i32, P_(i64), P_(i64)],
                 "fppg_batch_phase_ms": [vp, P_(f64)],
                 "fppg_device_sm_count": [P_(i32)],
+                "fppg_debug_fail_allocation": [i64],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -198,6 +201,11 @@ class Body:
         """Surface re-projection by the cascade of Sec. 3.3.3 (own triangle,
         own cell, 27 cells) instead of the closest over the 27 cells."""
         self._chk(lib().fppg_set_projection_rule(self._h, 1 if cascade else 0))
+
+    def set_incremental(self, on: bool):
+        """Order the keys by repairing the previous order (True) or by a full
+        stable sort (False); both give the same bits."""
+        self._chk(lib().fppg_set_incremental(self._h, int(bool(on))))
 
     def set_fixed_features(self, fixed: bool):
         self._chk(lib().fppg_set_fixed_features(self._h, int(bool(fixed))))
@@ -423,10 +431,16 @@ class Batch:
     def autotune(self, iters: int = 5) -> dict:
         """Pick force variant, block size and search grid by timing; the state
         is restored afterwards."""
-        v, tb, sc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
-        self._chk(lib().fppg_batch_autotune(self._h, int(iters), C.byref(v), C.byref(tb), C.byref(sc), C.byref(ms)))
+        v, tb, sc, inc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        self._chk(lib().fppg_batch_autotune(self._h, int(iters), C.byref(v), C.byref(tb), C.byref(sc),
+                                            C.byref(inc), C.byref(ms)))
         return {"force_variant": v.value, "force_block": tb.value, "search_ctas_per_sm": sc.value,
-                "ms_per_iter": ms.value}
+                "incremental_order": inc.value, "ms_per_iter": ms.value}
+
+    def set_incremental(self, on: bool):
+        """Order the keys by repairing the previous order (True) or by a full
+        stable sort (False); both give the same bits."""
+        self._chk(lib().fppg_batch_set_incremental(self._h, int(bool(on))))
 
     def set_mobile_classes(self, classes):
         """Only these classes move, in every body of the batch."""

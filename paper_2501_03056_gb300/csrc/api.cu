@@ -1,5 +1,6 @@
 // extern "C" entry points of the relaxation library (include/fppg.h).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -112,7 +113,7 @@ int stage_buf(fppg_ctx *ctx, size_t bytes, void **out) {
             ctx->stage = nullptr;
             ctx->stage_bytes = 0;
         }
-        CUDA_OR(ctx->err, cudaMalloc(&ctx->stage, bytes));
+        CUDA_OR(ctx->err, dev_malloc(&ctx->stage, bytes));
         ctx->stage_bytes = bytes;
     }
     *out = ctx->stage;
@@ -133,6 +134,25 @@ int ctx_group(fppg_ctx *c) {
 } // namespace
 
 void fppg::set_global_error(const char *msg) { snprintf(g_global_err, sizeof(g_global_err), "%s", msg); }
+
+namespace {
+// allocations to go before one fails (fppg_debug_fail_allocation); -1: none
+std::atomic<int64_t> g_fail_after{-1};
+} // namespace
+
+cudaError_t fppg::dev_malloc_raw(void **p, size_t bytes) {
+    int64_t k = g_fail_after.load();
+    while (k >= 0) {
+        if (g_fail_after.compare_exchange_weak(k, k - 1)) {
+            if (k == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 extern "C" {
 
@@ -206,7 +226,13 @@ int fppg_extract_features(fppg_ctx *ctx, float dihedral_deg, int64_t *n_edges) {
     if (!ctx) return FPPG_ERR_ARG;
     if (!std::isfinite(dihedral_deg)) return fail(ctx->err, FPPG_ERR_ARG, "dihedral_deg must be finite");
     int r = ctx->body.extract_features(dihedral_deg, ctx->stream, ctx->err);
-    if (r) return r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA;
+    if (r) {
+        // the group must not keep a view of feature segments that are gone
+        const std::string msg = ctx->err;
+        ctx_group(ctx);
+        ctx->err = msg;
+        return r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA;
+    }
     if (n_edges) *n_edges = (int64_t)ctx->body.fe.size() / 2;
     return ctx_group(ctx);
 }
@@ -241,6 +267,7 @@ int fppg_map_particles(fppg_ctx *ctx, const fppg_map_opts *opts, int64_t *n_out)
         return fail(ctx->err, FPPG_ERR_ARG, "band_cells or inner_cells outside 0..64");
     int64_t n = 0;
     std::vector<int32_t> cls;
+    ctx->has_particles = false;     // until the new set is complete
     int r = map_particles(ctx->group, ctx->body, opts->surface, opts->volume, opts->features, opts->band_cells,
                           opts->band_cells > 0 ? opts->inner_cells : 0, ctx->stream, &n, cls, ctx->err);
     if (r) return r == 1 ? FPPG_ERR_ARG : (r == 3 ? FPPG_ERR_OOM : (r == 6 ? FPPG_ERR_INTERNAL : FPPG_ERR_CUDA));
@@ -267,6 +294,7 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
     if (bad_cls) return fail(ctx->err, FPPG_ERR_ARG, "class outside 0..4");
     if (bad_xyz) return fail(ctx->err, FPPG_ERR_ARG, "non-finite coordinate");
     Group &g = ctx->group;
+    ctx->has_particles = false;     // until the new set is complete
     if (n != g.d.N || !g.d.pos) {
         int r = g.alloc_particles(n, ctx->err);
         if (r) return r;
@@ -318,7 +346,7 @@ int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_
     CUDA_OR(a->err, cudaStreamSynchronize(b->stream));
     int32_t *in = nullptr;
     const int64_t na = a->n, nbp = b->n;
-    CUDA_OR(a->err, cudaMalloc(&in, sizeof(int32_t) * (size_t)std::max<int64_t>(na + nbp, 1)));
+    CUDA_OR(a->err, dev_malloc(&in, sizeof(int32_t) * (size_t)std::max<int64_t>(na + nbp, 1)));
     ray_parity(b->group, a->group.d.pos, na, in, s);
     ray_parity(a->group, b->group.d.pos, nbp, in + na, s);
     std::vector<int32_t> inside((size_t)(na + nbp));
@@ -460,9 +488,9 @@ int fppg_debug_forces(fppg_ctx *ctx, float *acc_host, int32_t *count_host, float
     if (n == 0) return FPPG_OK;
     float *dacc = nullptr;
     int32_t *dcnt_s = nullptr, *dcnt = nullptr;
-    CUDA_OR(ctx->err, cudaMalloc(&dacc, sizeof(float) * 3 * n));
-    CUDA_OR(ctx->err, cudaMalloc(&dcnt_s, sizeof(int32_t) * n));
-    CUDA_OR(ctx->err, cudaMalloc(&dcnt, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, dev_malloc(&dacc, sizeof(float) * 3 * n));
+    CUDA_OR(ctx->err, dev_malloc(&dcnt_s, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, dev_malloc(&dcnt, sizeof(int32_t) * n));
     int buf = build_grid(g, ctx->stream);
     forces(g, ctx->stream, dcnt_s);
     unpermute(g, buf, ctx->stream, dacc, dcnt_s, dcnt);
@@ -514,9 +542,9 @@ int fppg_work_counts(fppg_ctx *ctx, int64_t *candidates, int64_t *pairs, int64_t
     int64_t c = 0, p = 0, t = 0;
     if (n > 0) {
         int32_t *dcnt = nullptr, *dcand = nullptr, *dtest = nullptr;
-        CUDA_OR(ctx->err, cudaMalloc(&dcnt, sizeof(int32_t) * n));
-        CUDA_OR(ctx->err, cudaMalloc(&dcand, sizeof(int32_t) * n));
-        CUDA_OR(ctx->err, cudaMalloc(&dtest, sizeof(int32_t) * n));
+        CUDA_OR(ctx->err, dev_malloc(&dcnt, sizeof(int32_t) * n));
+        CUDA_OR(ctx->err, dev_malloc(&dcand, sizeof(int32_t) * n));
+        CUDA_OR(ctx->err, dev_malloc(&dtest, sizeof(int32_t) * n));
         build_grid(g, ctx->stream);
         forces(g, ctx->stream, dcnt, dcand, dtest);
         std::vector<int32_t> hc(n), hp(n), ht(n);
@@ -549,12 +577,12 @@ int fppg_project_points(fppg_ctx *ctx, const float *y_host, const int32_t *cls_h
         if (cls_host[i] < 0 || cls_host[i] > 4) return fail(ctx->err, FPPG_ERR_ARG, "class outside 0..4");
     float *dy = nullptr, *dxo = nullptr;
     int32_t *dcls = nullptr, *dcin = nullptr, *dcout = nullptr, *dok = nullptr;
-    CUDA_OR(ctx->err, cudaMalloc(&dy, sizeof(float) * 3 * n));
-    CUDA_OR(ctx->err, cudaMalloc(&dxo, sizeof(float) * 3 * n));
-    CUDA_OR(ctx->err, cudaMalloc(&dcls, sizeof(int32_t) * n));
-    CUDA_OR(ctx->err, cudaMalloc(&dcout, sizeof(int32_t) * n));
-    CUDA_OR(ctx->err, cudaMalloc(&dok, sizeof(int32_t) * n));
-    if (cons_host) CUDA_OR(ctx->err, cudaMalloc(&dcin, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, dev_malloc(&dy, sizeof(float) * 3 * n));
+    CUDA_OR(ctx->err, dev_malloc(&dxo, sizeof(float) * 3 * n));
+    CUDA_OR(ctx->err, dev_malloc(&dcls, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, dev_malloc(&dcout, sizeof(int32_t) * n));
+    CUDA_OR(ctx->err, dev_malloc(&dok, sizeof(int32_t) * n));
+    if (cons_host) CUDA_OR(ctx->err, dev_malloc(&dcin, sizeof(int32_t) * n));
     cudaStream_t s = ctx->stream;
     CUDA_OR(ctx->err, cudaMemcpyAsync(dy, y_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
     CUDA_OR(ctx->err, cudaMemcpyAsync(dcls, cls_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
@@ -699,7 +727,7 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     d.total_cells = cells;
     std::string &err = b->err;
     int r = g.alloc_particles(N, err);
-    auto A = [&](void **p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)); };
+    auto A = [&](void **p, size_t bytes) { return dev_malloc(p, std::max<size_t>(bytes, 16)); };
     if (!r && (A((void **)&d.geo, sizeof(float4) * 5 * nt) || A((void **)&d.vx, sizeof(float4) * 3 * nt) ||
                A((void **)&d.pn, sizeof(float4) * 6 * nt) || A((void **)&d.hrng, sizeof(uint2) * hs) ||
                A((void **)&d.compact, sizeof(uint4) * nc) || A((void **)&d.tlist, sizeof(int32_t) * np) ||
@@ -890,14 +918,21 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int variant, block, search_ctas;
+    int variant, block, search_ctas, incremental;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
 } // namespace
 
+// switch the ordering of the keys; entering the incremental form forgets
+// the previous order (its arrays may be stale after full sorts)
+static void set_ordering(Group &g, bool incremental, cudaStream_t s) {
+    if (incremental && !g.d.incremental) g.invalidate_order(s);
+    g.d.incremental = incremental;
+}
+
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
-                        double *ms_per_iter) {
+                        int32_t *incremental, double *ms_per_iter) {
     if (!b || iters <= 0 || iters > 10000) return FPPG_ERR_ARG;
     Group &g = b->group;
     DevGroup &d = g.d;
@@ -913,7 +948,8 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     int nb = 0;
     while ((int64_t)1 << (nb + 1) <= std::max<int64_t>(d.N, 1)) nb++;
     const TuneKey key{nb, d.N ? (int)(10 * nv / d.N) : 0, prop.name};
-    TuneVal best{g.force_variant, g.force_block, g.search_thread ? 0 : g.search_blocks / std::max(sms, 1)};
+    TuneVal best{g.force_variant, g.force_block, g.search_thread ? 0 : g.search_blocks / std::max(sms, 1),
+                 d.incremental ? 1 : 0};
     double best_ms = 0.0;
     bool cached = false;
     {
@@ -927,8 +963,11 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     if (!cached) {
         float4 *pos0 = nullptr;
         int32_t *cons0 = nullptr;
-        CUDA_OR(b->err, cudaMalloc(&pos0, sizeof(float4) * std::max<int64_t>(d.N, 1)));
-        CUDA_OR(b->err, cudaMalloc(&cons0, sizeof(int32_t) * std::max<int64_t>(d.N, 1)));
+        CUDA_OR(b->err, dev_malloc(&pos0, sizeof(float4) * std::max<int64_t>(d.N, 1)));
+        if (dev_malloc(&cons0, sizeof(int32_t) * std::max<int64_t>(d.N, 1)) != cudaSuccess) {
+            cudaFree(pos0);
+            return fail(b->err, FPPG_ERR_OOM, "autotune: out of device memory");
+        }
         CUDA_OR(b->err, cudaMemcpyAsync(pos0, d.pos, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
         CUDA_OR(b->err, cudaMemcpyAsync(cons0, d.cons, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
         cudaEvent_t e0, e1;
@@ -937,27 +976,44 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
         const bool tf = g.time_force;
         g.time_force = false;
         best_ms = 1e30;
+        // one trial: the state restored, one untimed iteration, `iters` timed
+        auto trial = [&](int v, int tb, int sc, int inc, float *ms) -> int {
+            g.force_variant = v;
+            g.force_block = tb;
+            g.search_thread = sc == 0;
+            g.search_blocks = (sc == 0 ? 16 : sc) * sms;
+            set_ordering(g, inc != 0, s);
+            CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
+            CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
+            iterate(g, s, false);
+            CUDA_OR(b->err, cudaEventRecord(e0, s));
+            for (int it = 0; it < iters; it++) iterate(g, s, false);
+            CUDA_OR(b->err, cudaEventRecord(e1, s));
+            CUDA_OR(b->err, cudaEventSynchronize(e1));
+            CUDA_OR(b->err, cudaEventElapsedTime(ms, e0, e1));
+            return FPPG_OK;
+        };
+        const int inc0 = best.incremental;
         for (int v = 0; v < 2; v++)
             for (int tb : {128, 256})
                 for (int sc : {0, 4, 8, 16}) {   // 0: one thread per queued particle
-                    g.force_variant = v;
-                    g.force_block = tb;
-                    g.search_thread = sc == 0;
-                    g.search_blocks = (sc == 0 ? 16 : sc) * sms;
-                    CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
-                    CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
-                    iterate(g, s, false);
-                    CUDA_OR(b->err, cudaEventRecord(e0, s));
-                    for (int it = 0; it < iters; it++) iterate(g, s, false);
-                    CUDA_OR(b->err, cudaEventRecord(e1, s));
-                    CUDA_OR(b->err, cudaEventSynchronize(e1));
                     float ms = 0.f;
-                    CUDA_OR(b->err, cudaEventElapsedTime(&ms, e0, e1));
+                    const int r = trial(v, tb, sc, inc0, &ms);
+                    if (r) return r;
                     if (ms / iters < best_ms) {
                         best_ms = ms / iters;
-                        best = TuneVal{v, tb, sc};
+                        best = TuneVal{v, tb, sc, inc0};
                     }
                 }
+        {   // the other ordering with the fastest kernels
+            float ms = 0.f;
+            const int r = trial(best.variant, best.block, best.search_ctas, 1 - inc0, &ms);
+            if (r) return r;
+            if (ms / iters < best_ms) {
+                best_ms = ms / iters;
+                best.incremental = 1 - inc0;
+            }
+        }
         g.time_force = tf;
         CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
         CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
@@ -973,6 +1029,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     g.force_block = best.block;
     g.search_thread = best.search_ctas == 0;
     g.search_blocks = (best.search_ctas == 0 ? 16 : best.search_ctas) * sms;
+    set_ordering(g, best.incremental != 0, s);
     if (g.graph) {
         cudaGraphExecDestroy(g.graph);
         g.graph = nullptr;
@@ -980,6 +1037,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     if (variant) *variant = best.variant;
     if (block) *block = best.block;
     if (search_ctas) *search_ctas = best.search_ctas;
+    if (incremental) *incremental = best.incremental;
     if (ms_per_iter) *ms_per_iter = cached ? 0.0 : best_ms;
     return FPPG_OK;
 }
@@ -1013,6 +1071,12 @@ int fppg_batch_configure(fppg_batch *b, int32_t variant, int32_t block, int32_t 
     return FPPG_OK;
 }
 
+int fppg_debug_fail_allocation(int64_t k) {
+    if (k < -1) return fail_global(FPPG_ERR_ARG, "k must be -1 (off) or a count of allocations");
+    g_fail_after.store(k);
+    return FPPG_OK;
+}
+
 int fppg_device_sm_count(int32_t *sms) {
     if (!sms) return fail_global(FPPG_ERR_ARG, "sms is NULL");
     int dev = 0, v = 0;
@@ -1020,6 +1084,25 @@ int fppg_device_sm_count(int32_t *sms) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail_global(FPPG_ERR_CUDA, cudaGetErrorString(e));
     *sms = v;
+    return FPPG_OK;
+}
+
+int fppg_set_incremental(fppg_ctx *ctx, int32_t incremental) {
+    if (!ctx || incremental < 0 || incremental > 1) return FPPG_ERR_ARG;
+    set_ordering(ctx->group, incremental != 0, ctx->stream);
+    CUDA_OR(ctx->err, cudaGetLastError());
+    return FPPG_OK;
+}
+
+int fppg_batch_set_incremental(fppg_batch *b, int32_t incremental) {
+    if (!b || incremental < 0 || incremental > 1) return FPPG_ERR_ARG;
+    Group &g = b->group;
+    set_ordering(g, incremental != 0, b->stream);
+    if (g.graph) {
+        cudaGraphExecDestroy(g.graph);
+        g.graph = nullptr;
+    }
+    CUDA_OR(b->err, cudaGetLastError());
     return FPPG_OK;
 }
 

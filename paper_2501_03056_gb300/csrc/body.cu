@@ -90,6 +90,17 @@ void Body::build_lines() {
     has_features = true;
 }
 
+void Body::drop_features() {
+    has_features = false;
+    fe.clear();
+    sing.clear();
+    line_first.clear();
+    line_nseg.clear();
+    line_closed.clear();
+    seg_v.clear();
+    nseg = nlines = 0;
+}
+
 int Body::upload_lines(cudaStream_t s, std::string &err) {
     if (seg) cudaFree(seg);
     if (lines) cudaFree(lines);
@@ -114,8 +125,14 @@ int Body::upload_lines(cudaStream_t s, std::string &err) {
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    if (cudaMalloc(&seg, sizeof(float4) * hs.size()) != cudaSuccess ||
-        cudaMalloc(&lines, sizeof(int2) * hl.size()) != cudaSuccess) {
+    if (dev_malloc(&seg, sizeof(float4) * hs.size()) != cudaSuccess ||
+        dev_malloc(&lines, sizeof(int2) * hl.size()) != cudaSuccess) {
+        // no half-built feature set: the body is left without features
+        if (seg) cudaFree(seg);
+        if (lines) cudaFree(lines);
+        seg = nullptr;
+        lines = nullptr;
+        drop_features();
         err = "feature lines: out of device memory";
         return 3;
     }
@@ -204,50 +221,134 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
         }                                                                       \
     } while (0)
 
+// Every particle and grid array of the group freed and cleared (N = 0), so
+// that the next allocation starts from scratch.
+void Group::release_particles() {
+    DevGroup &g = d;
+    void *ptrs[] = {g.pos,    g.cons,   g.cons_s,   g.key[0], g.key[1],  g.id[0],   g.id[1],  g.pos_s,
+                    g.pos_p,  g.cert,   g.acc_s,    g.hist,   g.coef_s,  g.work,    g.fstart, g.fcount,
+                    g.scan_tmp, g.amax, g.maxdisp,  g.work_count, g.totals};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    free_order_state();
+    g.pos = g.pos_s = g.pos_p = g.cert = g.acc_s = nullptr;
+    g.cons = g.cons_s = nullptr;
+    g.key[0] = g.key[1] = g.id[0] = g.id[1] = nullptr;
+    g.hist = g.fstart = g.fcount = g.scan_tmp = g.amax = g.maxdisp = g.work_count = g.totals = nullptr;
+    g.coef_s = nullptr;
+    g.work = nullptr;
+    g.N = 0;
+}
+
 int Group::alloc_particles(int64_t N, std::string &err) {
+    const int r = alloc_particles_once(N, err);
+    if (r) release_particles();   // no half-allocated group: the next call starts over
+    return r;
+}
+
+void Group::free_order_state() {
+    DevGroup &g = d;
+    void *ptrs[] = {g.key_id, g.chg, g.cpos, g.keep, g.ck[0], g.ck[1], g.cv[0], g.cv[1], g.uk, g.uv, g.split,
+                    g.counts, g.scan_tmp_n};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    g.key_id = g.chg = g.cpos = g.keep = g.uk = g.uv = g.split = g.counts = g.scan_tmp_n = nullptr;
+    g.ck[0] = g.ck[1] = g.cv[0] = g.cv[1] = nullptr;
+}
+
+__global__ void k_iota_u32(uint32_t *__restrict__ a, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (uint32_t)i;
+}
+
+// The arrays of the incremental ordering: the previous order starts as the
+// identity over ids with no key recorded, so the first grid build sorts
+// every particle.  Allocated with the particles.
+int Group::alloc_order_state(std::string &err) {
+    DevGroup &g = d;
+    free_order_state();
+    const size_t n1 = (size_t)std::max<int64_t>(g.N, 1);
+    const int64_t nblk = (std::max<int64_t>(g.N, 1) + 2047) / 2048;
+    CKA(dev_malloc(&g.key_id, sizeof(uint32_t) * n1));
+    CKA(dev_malloc(&g.chg, sizeof(uint32_t) * n1));
+    CKA(dev_malloc(&g.cpos, sizeof(uint32_t) * n1));
+    CKA(dev_malloc(&g.keep, sizeof(uint32_t) * n1));
+    for (int k = 0; k < 2; k++) {
+        CKA(dev_malloc(&g.ck[k], sizeof(uint32_t) * n1));
+        CKA(dev_malloc(&g.cv[k], sizeof(uint32_t) * n1));
+    }
+    CKA(dev_malloc(&g.uk, sizeof(uint32_t) * n1));
+    CKA(dev_malloc(&g.uv, sizeof(uint32_t) * n1));
+    CKA(dev_malloc(&g.split, sizeof(uint32_t) * (size_t)(nblk + 2)));
+    CKA(dev_malloc(&g.counts, 2 * sizeof(uint32_t)));
+    CKA(dev_malloc(&g.scan_tmp_n, sizeof(uint32_t) * (size_t)scan_tmp_elems(std::max<int64_t>(g.N, 1))));
+    CKA(cudaMemset(g.key_id, 0xff, sizeof(uint32_t) * n1));
+    k_iota_u32<<<(unsigned)((n1 + 255) / 256), 256>>>(g.id[0], (int64_t)n1);
+    CKA(cudaGetLastError());
+    CKA(cudaDeviceSynchronize());
+    return 0;
+}
+
+void Group::invalidate_order(cudaStream_t s) {
+    if (d.key_id && d.N > 0) cudaMemsetAsync(d.key_id, 0xff, sizeof(uint32_t) * (size_t)d.N, s);
+}
+
+int Group::alloc_particles_once(int64_t N, std::string &err) {
     DevGroup &g = d;
     void *old[] = {g.pos,   g.cons,  g.cons_s, g.key[0], g.key[1], g.id[0], g.id[1],
                    g.pos_s, g.pos_p, g.cert,   g.acc_s,  g.hist,   g.coef_s, g.work};
     for (void *p : old)
         if (p) cudaFree(p);
+    g.pos = g.pos_s = g.pos_p = g.cert = g.acc_s = nullptr;
+    g.cons = g.cons_s = nullptr;
+    g.key[0] = g.key[1] = g.id[0] = g.id[1] = nullptr;
+    g.hist = nullptr;
+    g.coef_s = nullptr;
+    g.work = nullptr;
     g.N = N;
     const size_t n1 = (size_t)std::max<int64_t>(N, 1);
     g.n_tiles = (int)std::max<int64_t>(radix_tiles(N), 1);
     g.key_bits = fine_key_bits(g.total_cells);
     int digit_bits = 8;
     g.passes = radix_pass_plan(g.key_bits, &digit_bits);
-    CKA(cudaMalloc(&g.pos, sizeof(float4) * n1));
-    CKA(cudaMalloc(&g.cons, sizeof(int32_t) * n1));
-    CKA(cudaMalloc(&g.cons_s, sizeof(int32_t) * n1));
+    CKA(dev_malloc(&g.pos, sizeof(float4) * n1));
+    CKA(dev_malloc(&g.cons, sizeof(int32_t) * n1));
+    CKA(dev_malloc(&g.cons_s, sizeof(int32_t) * n1));
     for (int k = 0; k < 2; k++) {
-        CKA(cudaMalloc(&g.key[k], sizeof(uint32_t) * n1));
-        CKA(cudaMalloc(&g.id[k], sizeof(uint32_t) * n1));
+        CKA(dev_malloc(&g.key[k], sizeof(uint32_t) * n1));
+        CKA(dev_malloc(&g.id[k], sizeof(uint32_t) * n1));
     }
-    CKA(cudaMalloc(&g.pos_s, sizeof(float4) * n1));
-    CKA(cudaMalloc(&g.pos_p, sizeof(float4) * (n1 + 1)));
-    CKA(cudaMalloc(&g.cert, sizeof(float4) * n1));
+    CKA(dev_malloc(&g.pos_s, sizeof(float4) * n1));
+    CKA(dev_malloc(&g.pos_p, sizeof(float4) * (n1 + 1)));
+    CKA(dev_malloc(&g.cert, sizeof(float4) * n1));
     CKA(cudaMemset(g.cert, 0, sizeof(float4) * n1));
-    CKA(cudaMalloc(&g.acc_s, sizeof(float4) * n1));
-    CKA(cudaMalloc(&g.coef_s, sizeof(float) * (n1 + 1)));
-    CKA(cudaMalloc(&g.work, sizeof(int4) * n1));
+    CKA(dev_malloc(&g.acc_s, sizeof(float4) * n1));
+    CKA(dev_malloc(&g.coef_s, sizeof(float) * (n1 + 1)));
+    CKA(dev_malloc(&g.work, sizeof(int4) * n1));
     if (!g.work_count) {
-        CKA(cudaMalloc(&g.work_count, 2 * sizeof(uint32_t)));
+        CKA(dev_malloc(&g.work_count, 2 * sizeof(uint32_t)));
         CKA(cudaMemset(g.work_count, 0, 2 * sizeof(uint32_t)));
     }
-    CKA(cudaMalloc(&g.hist, sizeof(uint32_t) * kMaxDigits * (size_t)g.n_tiles));
-    if (!g.totals) CKA(cudaMalloc(&g.totals, sizeof(uint32_t) * kMaxDigits));
+    CKA(dev_malloc(&g.hist, sizeof(uint32_t) * kMaxDigits * (size_t)g.n_tiles));
+    if (!g.totals) CKA(dev_malloc(&g.totals, sizeof(uint32_t) * kMaxDigits));
     if (!g.fstart) {
         // dense start table of every fine key (+1), the counts it is scanned
         // from (zero between iterations) and the scan's block sums
         const size_t f1 = (size_t)kSlabs * (size_t)std::max<int64_t>(g.total_cells, 1) + 1;
-        CKA(cudaMalloc(&g.fstart, sizeof(uint32_t) * f1));
-        CKA(cudaMalloc(&g.fcount, sizeof(uint32_t) * f1));
+        CKA(dev_malloc(&g.fstart, sizeof(uint32_t) * f1));
+        CKA(dev_malloc(&g.fcount, sizeof(uint32_t) * f1));
         CKA(cudaMemset(g.fcount, 0, sizeof(uint32_t) * f1));
-        CKA(cudaMalloc(&g.scan_tmp, sizeof(uint32_t) * (size_t)scan_tmp_elems((int64_t)f1)));
+        CKA(dev_malloc(&g.scan_tmp, sizeof(uint32_t) * (size_t)scan_tmp_elems((int64_t)f1)));
+    }
+    // the incremental ordering for large groups (the autotuner may switch)
+    {
+        const int r = alloc_order_state(err);
+        if (r) return r;
+        g.incremental = N >= kIncrementalMinN;
     }
     if (!g.amax) {
-        CKA(cudaMalloc(&g.amax, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
-        CKA(cudaMalloc(&g.maxdisp, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
+        CKA(dev_malloc(&g.amax, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
+        CKA(dev_malloc(&g.maxdisp, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
         CKA(cudaMemset(g.amax, 0, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
         CKA(cudaMemset(g.maxdisp, 0, sizeof(uint32_t) * (size_t)std::max(g.B, 1)));
     }
@@ -255,7 +356,7 @@ int Group::alloc_particles(int64_t N, std::string &err) {
 }
 
 int Group::upload_params(cudaStream_t s, std::string &err) {
-    if (!d.params) CKA(cudaMalloc(&d.params, sizeof(AsmParams) * (size_t)std::max<int>(d.B, 1)));
+    if (!d.params) CKA(dev_malloc(&d.params, sizeof(AsmParams) * (size_t)std::max<int>(d.B, 1)));
     CKA(cudaMemcpyAsync(d.params, hp.data(), sizeof(AsmParams) * hp.size(), cudaMemcpyHostToDevice, s));
     CKA(cudaStreamSynchronize(s));
     return 0;

@@ -68,6 +68,7 @@ struct Body {
     int extract_features(float deg, cudaStream_t s, std::string &err);
     void build_lines();
     int upload_lines(cudaStream_t s, std::string &err);
+    void drop_features();   // forget every feature edge, line and segment
     void free_mesh();
     ~Body() { free_mesh(); }
 };
@@ -93,11 +94,21 @@ struct Group {
     int graph_iters = 0;
     cudaStream_t graph_stream = nullptr;
 
-    int alloc_particles(int64_t N, std::string &err);
+    int alloc_particles(int64_t N, std::string &err);   // on failure: nothing allocated, N = 0
+    int alloc_particles_once(int64_t N, std::string &err);
+    void release_particles();
+    int alloc_order_state(std::string &err);
+    void free_order_state();
+    // forget the previous order (the next grid build sorts every key); used
+    // when the incremental ordering is switched on
+    void invalidate_order(cudaStream_t s);
     int upload_params(cudaStream_t s, std::string &err);
     void free_all();
     ~Group() { free_all(); }
 };
+
+// groups of at least this many particles start with the incremental ordering
+constexpr int64_t kIncrementalMinN = 1 << 21;
 
 // event records per timed iteration: before A1, after A3, A4, A5 and A6
 constexpr int kPhaseEvents = 5;

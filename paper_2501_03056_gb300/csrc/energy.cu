@@ -375,15 +375,15 @@ int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, 
             if (q) cudaFree(q);
     };
     const size_t n1 = (size_t)std::max<int64_t>(N, 1), m1 = (size_t)std::max<int64_t>(M, 1);
-    bool fail = cudaMalloc(&xs, sizeof(float4) * n1) != cudaSuccess ||
-                cudaMalloc(&e_s, sizeof(double) * n1) != cudaSuccess ||
-                cudaMalloc(&part, sizeof(double) * (kSumBlocks + 1)) != cudaSuccess;
+    bool fail = dev_malloc(&xs, sizeof(float4) * n1) != cudaSuccess ||
+                dev_malloc(&e_s, sizeof(double) * n1) != cudaSuccess ||
+                dev_malloc(&part, sizeof(double) * (kSumBlocks + 1)) != cudaSuccess;
     if (!fail && gV)
-        fail = cudaMalloc(&vcon, sizeof(float4) * m1) != cudaSuccess ||
-               cudaMalloc(&vk[0], 4 * m1) != cudaSuccess || cudaMalloc(&vk[1], 4 * m1) != cudaSuccess ||
-               cudaMalloc(&vi[0], 4 * m1) != cudaSuccess || cudaMalloc(&vi[1], 4 * m1) != cudaSuccess ||
-               cudaMalloc(&hist, 4 * (size_t)kMaxDigits * std::max<int64_t>(radix_tiles(M), 1)) != cudaSuccess ||
-               cudaMalloc(&tot, 4 * (size_t)kMaxDigits) != cudaSuccess;
+        fail = dev_malloc(&vcon, sizeof(float4) * m1) != cudaSuccess ||
+               dev_malloc(&vk[0], 4 * m1) != cudaSuccess || dev_malloc(&vk[1], 4 * m1) != cudaSuccess ||
+               dev_malloc(&vi[0], 4 * m1) != cudaSuccess || dev_malloc(&vi[1], 4 * m1) != cudaSuccess ||
+               dev_malloc(&hist, 4 * (size_t)kMaxDigits * std::max<int64_t>(radix_tiles(M), 1)) != cudaSuccess ||
+               dev_malloc(&tot, 4 * (size_t)kMaxDigits) != cudaSuccess;
     if (fail) {
         cleanup();
         err = "energy: out of device memory";

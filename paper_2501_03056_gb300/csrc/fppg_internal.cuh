@@ -137,6 +137,18 @@ struct DevGroup {
     uint32_t *fstart = nullptr;   // F + 1 entries (F = kSlabs * total_cells)
     uint32_t *fcount = nullptr;   // F + 1 entries, zero between iterations
     uint32_t *scan_tmp = nullptr; // scan_tmp_elems(F + 1) entries
+    // incremental ordering (the previous iteration's order repaired, see
+    // order_incremental); null unless incremental is set
+    bool incremental = false;
+    uint32_t *key_id = nullptr;    // by id: fine key at the last grid build (~0: none)
+    uint32_t *chg = nullptr;       // by id: key changed
+    uint32_t *cpos = nullptr;      // scan positions (changed, then kept)
+    uint32_t *keep = nullptr;      // by previous slot: key kept
+    uint32_t *ck[2] = {nullptr, nullptr}, *cv[2] = {nullptr, nullptr};   // changed (key, id), radix ping-pong
+    uint32_t *uk = nullptr, *uv = nullptr;   // kept (key, id) in previous order
+    uint32_t *split = nullptr;     // merge tile splits
+    uint32_t *counts = nullptr;    // [0] changed, [1] kept
+    uint32_t *scan_tmp_n = nullptr; // scan_tmp_elems(N) entries
     uint32_t *amax = nullptr;
     uint32_t *maxdisp = nullptr;
     int4 *work = nullptr;          // search queue {key slot, trial point}, N entries
@@ -321,6 +333,15 @@ __device__ inline bool is_mobile(int cls, const AsmParams &A) {
 }
 
 // ---- host side -------------------------------------------------------------
+// Every device allocation of the library goes through dev_malloc, so that a
+// test can make one chosen allocation fail as if the device were out of
+// memory (fppg_debug_fail_allocation) and check the error path.
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 struct Status {
     int code = 0;
     std::string msg;
@@ -332,6 +353,10 @@ int radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t
                    uint32_t *totals, cudaStream_t s);
 int radix_sort_u64(uint64_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                    uint32_t *totals, cudaStream_t s);
+// the same with the count read from device memory (*n_dev <= n_max; the
+// launches and the histogram are sized for n_max; values given)
+int radix_sort_u32_dev(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max, const uint32_t *n_dev, int bits,
+                       uint32_t *hist, uint32_t *totals, cudaStream_t s);
 int64_t radix_tiles(int64_t n);
 // radix passes for keys of `bits` bits and their digit width (*digit_bits);
 // the histogram holds kMaxDigits rows of radix_tiles(n)

@@ -314,9 +314,9 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
             if (q) cudaFree(q);
     };
     const int64_t sc = scan_tmp_elems(cells);
-    if (cudaMalloc(&inside, cells) || cudaMalloc(&sflag, 4 * cells) || cudaMalloc(&vflag, 4 * cells) ||
-        cudaMalloc(&soff, 4 * cells) || cudaMalloc(&voff, 4 * cells) || cudaMalloc(&tot, 8) ||
-        cudaMalloc(&scr, 4 * sc) || cudaMalloc(&error, 4)) {
+    if (dev_malloc(&inside, cells) || dev_malloc(&sflag, 4 * cells) || dev_malloc(&vflag, 4 * cells) ||
+        dev_malloc(&soff, 4 * cells) || dev_malloc(&voff, 4 * cells) || dev_malloc(&tot, 8) ||
+        dev_malloc(&scr, 4 * sc) || dev_malloc(&error, 4)) {
         cleanup();
         err = "map_particles: out of device memory";
         return 3;
@@ -327,7 +327,7 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
         k_column_parity<<<nblk((int64_t)mg.n[0] * mg.n[1], 8), 256, 0, s>>>(b.d_verts, b.d_tris, b.occ, b.hrng,
                                                                              b.compact, b.tlist, mg, inside, error);
     if (volume && band_cells > 0) {
-        if (cudaMalloc(&band, cells) || cudaMalloc(&tmp, cells)) {
+        if (dev_malloc(&band, cells) || dev_malloc(&tmp, cells)) {
             cleanup();
             err = "map_particles: out of device memory";
             return 3;
@@ -338,7 +338,7 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
             std::swap(band, tmp);
         }
         if (inner_cells > 0) {
-            if (cudaMalloc(&inner, cells)) {
+            if (dev_malloc(&inner, cells)) {
                 cleanup();
                 err = "map_particles: out of device memory";
                 return 3;
@@ -372,7 +372,7 @@ int map_particles(Group &g, Body &b, int surface, int volume, int features, int 
         return r;
     }
     int32_t *dcls = nullptr;
-    if (cudaMalloc(&dcls, 4 * std::max<int64_t>(N, 1))) {
+    if (dev_malloc(&dcls, 4 * std::max<int64_t>(N, 1))) {
         cleanup();
         err = "map_particles: out of device memory";
         return 3;

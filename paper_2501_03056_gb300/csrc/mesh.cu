@@ -474,7 +474,7 @@ bool grid_setup(const float *bbmin, const float *bbmax, float cell, double shift
 
 template <typename T>
 static cudaError_t dalloc(T **p, int64_t n) {
-    return cudaMalloc((void **)p, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+    return dev_malloc((void **)p, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
 }
 
 void Body::free_mesh() {
@@ -748,26 +748,39 @@ int Body::extract_features(float deg, cudaStream_t s, std::string &err) {
     double cthr = std::cos((double)deg * M_PI / 180.0);
     uint32_t *flag = nullptr, *pos = nullptr, *total = nullptr, *scratch = nullptr;
     int32_t *dfe = nullptr;
+    auto release = [&]() {
+        void *p[] = {flag, pos, total, scratch, dfe};
+        for (void *q : p)
+            if (q) cudaFree(q);
+    };
+    // the old features stay as they are until the new edge list is on the host
+#define CKF(x)                                                                         \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) {                                                       \
+            release();                                                                 \
+            err = std::string(#x) + ": " + cudaGetErrorString(e_);                     \
+            return e_ == cudaErrorMemoryAllocation ? 3 : 4;                            \
+        }                                                                              \
+    } while (0)
     int64_t sc = scan_tmp_elems(m);
-    CK(dalloc(&flag, m));
-    CK(dalloc(&pos, m));
-    CK(dalloc(&total, 1));
-    CK(dalloc(&scratch, sc));
+    CKF(dalloc(&flag, m));
+    CKF(dalloc(&pos, m));
+    CKF(dalloc(&total, 1));
+    CKF(dalloc(&scratch, sc));
     k_feature_flags<<<blocks(m), 256, 0, s>>>(ekey, eval, m, nu, cthr, flag);
     exclusive_scan_u32(flag, pos, m, total, scratch, sc, s);
     uint32_t nfe = 0;
-    CK(cudaMemcpyAsync(&nfe, total, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    CK(dalloc(&dfe, 2 * (int64_t)nfe));
+    CKF(cudaMemcpyAsync(&nfe, total, 4, cudaMemcpyDeviceToHost, s));
+    CKF(cudaStreamSynchronize(s));
+    CKF(dalloc(&dfe, 2 * (int64_t)nfe));
     k_feature_emit<<<blocks(m), 256, 0, s>>>(ekey, m, flag, pos, nv, dfe);
-    fe.assign(2 * (size_t)nfe, 0);
-    if (nfe) CK(cudaMemcpyAsync(fe.data(), dfe, sizeof(int32_t) * 2 * nfe, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    cudaFree(flag);
-    cudaFree(pos);
-    cudaFree(total);
-    cudaFree(scratch);
-    cudaFree(dfe);
+    std::vector<int32_t> fe_new(2 * (size_t)nfe, 0);
+    if (nfe) CKF(cudaMemcpyAsync(fe_new.data(), dfe, sizeof(int32_t) * 2 * nfe, cudaMemcpyDeviceToHost, s));
+    CKF(cudaStreamSynchronize(s));
+#undef CKF
+    release();
+    fe.swap(fe_new);
     build_lines();
     return upload_lines(s, err);
 }

@@ -110,6 +110,148 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
              kSlabs * (uint32_t)A.ng_n[0] * ((uint32_t)cy + (uint32_t)A.ng_n[1] * (uint32_t)cz);
 }
 
+// ---- A1-A2, incremental form ---------------------------------------------------
+// A particle moves at most h / 16 per iteration, so from one grid build to
+// the next only a few per cent of the fine keys change (under 1 % once the
+// relaxation settles).  The incremental form keeps the last (key, id) order
+// and repairs it: the particles whose key changed are sorted alone (radix,
+// count on the device), the others keep their relative order, and the two
+// sorted lists are merged by (key, id).  The result is the one order by
+// (key, id), the same permutation as the stable sort of every key; with a
+// stale or foreign previous order every key counts as changed and the
+// repair is a full sort.
+
+// key of particle i (the rule of k_keys), compared with the key it had at
+// the last grid build: chg[i] = changed; key_id[i] updated
+__global__ void __launch_bounds__(TPB) k_keys_inc(const float4 *__restrict__ pos, int64_t N,
+                                                  const AsmParams *__restrict__ P, uint32_t *__restrict__ key_id,
+                                                  uint32_t *__restrict__ chg, uint32_t *__restrict__ amax,
+                                                  uint32_t *__restrict__ maxdisp, int B,
+                                                  uint32_t *__restrict__ work_count) {
+    int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i < B) {
+        amax[i] = 0u;
+        maxdisp[i] = 0u;
+    }
+    if (i == 0) {
+        work_count[0] = 0u;
+        work_count[1] = 0u;
+    }
+    if (i >= N) return;
+    float4 p = pos[i];
+    const AsmParams &A = P[body_of(p.w)];
+    const int fx = fine_coord(p.x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
+    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
+    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
+    const uint32_t k = kSlabs * A.key_base + (uint32_t)fx +
+                       kSlabs * (uint32_t)A.ng_n[0] * ((uint32_t)cy + (uint32_t)A.ng_n[1] * (uint32_t)cz);
+    const uint32_t old = key_id[i];
+    chg[i] = k != old ? 1u : 0u;
+    if (k != old) key_id[i] = k;
+}
+
+// the changed particles, in id order: (key, id) at their scan positions
+__global__ void __launch_bounds__(TPB) k_compact_changed(const uint32_t *__restrict__ chg,
+                                                         const uint32_t *__restrict__ cpos,
+                                                         const uint32_t *__restrict__ key_id, int64_t N,
+                                                         uint32_t *__restrict__ ck, uint32_t *__restrict__ cv) {
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= N || !chg[i]) return;
+    const uint32_t p = cpos[i];
+    ck[p] = key_id[i];
+    cv[p] = (uint32_t)i;
+}
+
+// keep[k] = the particle in slot k of the previous order kept its key
+__global__ void __launch_bounds__(TPB) k_keep_flags(const uint32_t *__restrict__ prev_id,
+                                                    const uint32_t *__restrict__ chg, int64_t N,
+                                                    uint32_t *__restrict__ keep) {
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k < N) keep[k] = chg[prev_id[k]] ? 0u : 1u;
+}
+
+// the kept slots of the previous order, compacted (still sorted)
+__global__ void __launch_bounds__(TPB) k_compact_kept(const uint32_t *__restrict__ keep,
+                                                      const uint32_t *__restrict__ kpos,
+                                                      const uint32_t *__restrict__ prev_key,
+                                                      const uint32_t *__restrict__ prev_id, int64_t N,
+                                                      uint32_t *__restrict__ uk, uint32_t *__restrict__ uv) {
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k >= N || !keep[k]) return;
+    const uint32_t p = kpos[k];
+    uk[p] = prev_key[k];
+    uv[p] = prev_id[k];
+}
+
+// merge of the kept list u (U items) and the sorted changed list c (C
+// items), U + C = N, in (key, id) order; ids are distinct, so the order is
+// strict and the merge unique
+constexpr int kMergeThreads = 256, kMergeItems = 8, kMergeTile = kMergeThreads * kMergeItems;
+
+__device__ inline bool kv_less(uint32_t ka, uint32_t ia, uint32_t kb, uint32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// split[b]: how many u items the first min(b tile, N) outputs take
+__global__ void k_merge_splits(const uint32_t *__restrict__ uk, const uint32_t *__restrict__ uv,
+                               const uint32_t *__restrict__ ck, const uint32_t *__restrict__ cv,
+                               const uint32_t *__restrict__ counts, int64_t N, int nblk,
+                               uint32_t *__restrict__ split) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nblk) return;
+    const int64_t C = counts[0], U = counts[1];
+    const int64_t d = min((int64_t)b * kMergeTile, N);
+    int64_t lo = max((int64_t)0, d - C), hi = min(d, U);
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int64_t j = d - 1 - mid;
+        if (kv_less(uk[mid], uv[mid], ck[j], cv[j])) lo = mid + 1;
+        else hi = mid;
+    }
+    split[b] = (uint32_t)lo;
+}
+
+// one tile of kMergeTile outputs per block: its u and c items staged in
+// shared memory, then kMergeItems outputs per thread
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const uint32_t *__restrict__ uk,
+                                                         const uint32_t *__restrict__ uv,
+                                                         const uint32_t *__restrict__ ck,
+                                                         const uint32_t *__restrict__ cv,
+                                                         const uint32_t *__restrict__ split, int64_t N,
+                                                         uint32_t *__restrict__ out_key,
+                                                         uint32_t *__restrict__ out_id) {
+    __shared__ uint32_t sk[kMergeTile], si[kMergeTile];
+    const int64_t d0 = (int64_t)blockIdx.x * kMergeTile, d1 = min(d0 + kMergeTile, N);
+    const int64_t i0 = split[blockIdx.x], i1 = split[blockIdx.x + 1];
+    const int64_t j0 = d0 - i0, j1 = d1 - i1;
+    const int nu = (int)(i1 - i0), nc = (int)(j1 - j0), n = nu + nc;
+    for (int q = threadIdx.x; q < n; q += kMergeThreads) {
+        if (q < nu) {
+            sk[q] = uk[i0 + q];
+            si[q] = uv[i0 + q];
+        } else {
+            sk[q] = ck[j0 + q - nu];
+            si[q] = cv[j0 + q - nu];
+        }
+    }
+    __syncthreads();
+    const int dt = min((int)threadIdx.x * kMergeItems, n);
+    int lo = max(0, dt - nc), hi = min(dt, nu);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int j = dt - 1 - mid;
+        if (kv_less(sk[mid], si[mid], sk[nu + j], si[nu + j])) lo = mid + 1;
+        else hi = mid;
+    }
+    int i = lo, j = dt - lo;
+    for (int q = 0; q < kMergeItems && dt + q < n; q++) {
+        const bool take_u = j >= nc || (i < nu && kv_less(sk[i], si[i], sk[nu + j], si[nu + j]));
+        const int src = take_u ? i++ : nu + j++;
+        out_key[d0 + dt + q] = sk[src];
+        out_id[d0 + dt + q] = si[src];
+    }
+}
+
 // ---- A3 ----------------------------------------------------------------------
 // Positions in key order (also as slot pairs) and the number of particles of
 // every fine key: the sorted keys of a warp form runs of equal keys, and the
@@ -721,10 +863,10 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
         const float4 a = acc_s[k];
         float3 dr = make_float3(a.x * sc, a.y * sc, a.z * sc);
         const int c = cons_s[k];
-        if (cls == kClsS && c >= 0) {
+        if (cls == kClsS && c >= 0 && c < A.nt) {
             const float3 n = f3(M.geo[5 * (size_t)(A.tri_off + c) + 1]);
             dr = dr - dot3(dr, n) * n;
-        } else if (cls == kClsF && c >= 0) {
+        } else if (cls == kClsF && c >= 0 && c < A.nseg) {
             const float3 tau = f3(M.seg[3 * (size_t)(A.seg_off + c) + 2]);
             dr = dot3(dr, tau) * tau;
         }
@@ -1154,10 +1296,34 @@ __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__re
 } // namespace
 
 // ---- host driver ----------------------------------------------------------------
+// A1-A2 of the incremental form; the order ends in key[0] / id[0], which is
+// also the previous order it starts from
+static void order_incremental(DevGroup &d, cudaStream_t s) {
+    const int64_t N = d.N;
+    k_keys_inc<<<nblocks(std::max<int64_t>(N, d.B)), TPB, 0, s>>>(d.pos, N, d.params, d.key_id, d.chg, d.amax,
+                                                                   d.maxdisp, d.B, d.work_count);
+    if (N == 0) return;
+    exclusive_scan_u32(d.chg, d.cpos, N, d.counts, d.scan_tmp_n, scan_tmp_elems(N), s);
+    k_compact_changed<<<nblocks(N), TPB, 0, s>>>(d.chg, d.cpos, d.key_id, N, d.ck[0], d.cv[0]);
+    const int cb = radix_sort_u32_dev(d.ck, d.cv, N, d.counts, d.key_bits, d.hist, d.totals, s);
+    k_keep_flags<<<nblocks(N), TPB, 0, s>>>(d.id[0], d.chg, N, d.keep);
+    exclusive_scan_u32(d.keep, d.cpos, N, d.counts + 1, d.scan_tmp_n, scan_tmp_elems(N), s);
+    k_compact_kept<<<nblocks(N), TPB, 0, s>>>(d.keep, d.cpos, d.key[0], d.id[0], N, d.uk, d.uv);
+    const int nblk = (int)((N + kMergeTile - 1) / kMergeTile);
+    k_merge_splits<<<(nblk + 1 + 255) / 256, 256, 0, s>>>(d.uk, d.uv, d.ck[cb], d.cv[cb], d.counts, N, nblk,
+                                                          d.split);
+    k_merge<<<nblk, kMergeThreads, 0, s>>>(d.uk, d.uv, d.ck[cb], d.cv[cb], d.split, N, d.key[0], d.id[0]);
+}
+
 int build_grid_dev(DevGroup &d, cudaStream_t s) {
-    k_keys<<<nblocks(std::max<int64_t>(d.N, d.B)), TPB, 0, s>>>(d.pos, d.N, d.params, d.key[0], d.amax, d.maxdisp,
-                                                                 d.B, d.work_count);
-    int buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
+    int buf = 0;
+    if (d.incremental) {
+        order_incremental(d, s);
+    } else {
+        k_keys<<<nblocks(std::max<int64_t>(d.N, d.B)), TPB, 0, s>>>(d.pos, d.N, d.params, d.key[0], d.amax,
+                                                                     d.maxdisp, d.B, d.work_count);
+        buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
+    }
     k_gather<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s, d.pos_p, d.fcount, d.cons,
                                           d.cons_s);
     const int64_t F1 = kSlabs * d.total_cells + 1;
@@ -1165,7 +1331,13 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
     return buf;
 }
 
-int grid_kernels(const DevGroup &d) { return 2 + 3 * d.passes + scan_launches(kSlabs * d.total_cells + 1); }
+int grid_kernels(const DevGroup &d) {
+    const int tail = 1 + scan_launches(kSlabs * d.total_cells + 1);    // gather + start scan
+    if (!d.incremental) return 1 + 3 * d.passes + tail;
+    // keys, 2 scans with totals, 2 compactions, keep flags, the changed
+    // list's radix passes, merge splits and merge
+    return 1 + 2 * (scan_launches(d.N) + 1) + 3 + 3 * d.passes + 2 + tail;
+}
 
 int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
 
@@ -1241,8 +1413,8 @@ int stats(Group &g, cudaStream_t s, double *mean, double *sd, double *minpair, d
     double *sums = nullptr;
     uint32_t *mp = nullptr;
     float *rho = nullptr;
-    if (cudaMalloc(&sums, 12 * sizeof(double)) != cudaSuccess || cudaMalloc(&mp, 8) != cudaSuccess ||
-        cudaMalloc(&rho, sizeof(float) * std::max<int64_t>(d.N, 1)) != cudaSuccess) {
+    if (dev_malloc(&sums, 12 * sizeof(double)) != cudaSuccess || dev_malloc(&mp, 8) != cudaSuccess ||
+        dev_malloc(&rho, sizeof(float) * std::max<int64_t>(d.N, 1)) != cudaSuccess) {
         err = "stats: out of device memory";
         cudaFree(sums);
         cudaFree(mp);

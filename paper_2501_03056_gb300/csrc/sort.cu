@@ -56,11 +56,16 @@ __device__ inline uint32_t block_incl_scan(uint32_t v, uint32_t *wsum, uint32_t 
 
 // DB-bit digits (ND = 2^DB values; the passes use DB = 8): the upsweep
 // counts them per tile in shared memory
+// n_dev (nullable): the item count is read from device memory (at most n),
+// so that a captured graph can sort a list whose length it does not know;
+// tiles past it count nothing and write nothing
 template <typename K, int RC, int DB>
 __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int64_t n, int shift,
-                                                uint32_t *__restrict__ hist, int n_tiles) {
+                                                uint32_t *__restrict__ hist, int n_tiles,
+                                                const uint32_t *__restrict__ n_dev) {
     constexpr int TILE = RW * RC * 32, ND = 1 << DB;
     __shared__ uint32_t cnt[ND];
+    if (n_dev) n = min(n, (int64_t)*n_dev);
     for (int d = threadIdx.x; d < ND; d += RT) cnt[d] = 0;
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -97,8 +102,11 @@ template <typename K, bool IOTA, int RC, int DB>
 __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                   K *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n,
                                                   int shift, const uint32_t *__restrict__ hist,
-                                                  const uint32_t *__restrict__ totals, int n_tiles) {
+                                                  const uint32_t *__restrict__ totals, int n_tiles,
+                                                  const uint32_t *__restrict__ n_dev) {
     constexpr int TILE = RW * RC * 32, ND = 1 << DB, KD = ND / RT;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    if ((int64_t)blockIdx.x * TILE >= n) return;   // the whole block: no barrier is left waiting
     extern __shared__ __align__(16) unsigned char smem[];
     K *skey = reinterpret_cast<K *>(smem);
     uint32_t *sval = reinterpret_cast<uint32_t *>(smem + sizeof(K) * TILE);
@@ -197,20 +205,20 @@ void set_smem_attr() {
 
 template <typename K, int RC, int DB>
 int radix_passes(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int passes, uint32_t *hist,
-                 uint32_t *totals, cudaStream_t s) {
+                 uint32_t *totals, cudaStream_t s, const uint32_t *n_dev) {
     constexpr int TILE = RW * RC * 32;
     const int n_tiles = (int)((n + TILE - 1) / TILE);
     int cur = 0;
     for (int p = 0; p < passes; p++) {
         const int shift = DB * p;
-        k_upsweep<K, RC, DB><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles);
+        k_upsweep<K, RC, DB><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles, n_dev);
         k_digit_scan<<<1 << DB, RT, 0, s>>>(hist, n_tiles, totals);
         if (p == 0 && iota_vals)
             k_downsweep<K, true, RC, DB><<<n_tiles, RT, downsweep_smem<K, RC, DB>(), s>>>(
-                keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
+                keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles, n_dev);
         else
             k_downsweep<K, false, RC, DB><<<n_tiles, RT, downsweep_smem<K, RC, DB>(), s>>>(
-                keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles);
+                keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles, n_dev);
         cur ^= 1;
     }
     return cur;
@@ -218,12 +226,14 @@ int radix_passes(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int p
 
 template <typename K, int DB>
 int radix_sort_db(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int passes, uint32_t *hist,
-                  uint32_t *totals, cudaStream_t s, int sms) {
+                  uint32_t *totals, cudaStream_t s, int sms, const uint32_t *n_dev) {
     // the largest tile that still gives every SM four tiles (latency hiding)
     const int64_t want = 4 * (int64_t)sms;
-    if ((n + 4095) / 4096 >= want) return radix_passes<K, 16, DB>(keys, vals, iota_vals, n, passes, hist, totals, s);
-    if ((n + 2047) / 2048 >= want) return radix_passes<K, 8, DB>(keys, vals, iota_vals, n, passes, hist, totals, s);
-    return radix_passes<K, 4, DB>(keys, vals, iota_vals, n, passes, hist, totals, s);
+    if ((n + 4095) / 4096 >= want)
+        return radix_passes<K, 16, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, n_dev);
+    if ((n + 2047) / 2048 >= want)
+        return radix_passes<K, 8, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, n_dev);
+    return radix_passes<K, 4, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, n_dev);
 }
 
 // once per key type and process (thread-safe static initialisation): the
@@ -250,7 +260,7 @@ int radix_sort_impl(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, in
     const int sms = sort_setup_sms<K>();
     int db = 8;
     const int passes = radix_pass_plan(bits, &db);
-    return radix_sort_db<K, 8>(keys, vals, iota_vals, n, passes, hist, totals, s, sms);
+    return radix_sort_db<K, 8>(keys, vals, iota_vals, n, passes, hist, totals, s, sms, nullptr);
 }
 
 // ---- exclusive scan (set-up work) -----------------------------------------
@@ -310,6 +320,15 @@ int radix_pass_plan(int bits, int *digit_bits) {
 int radix_sort_u32(uint32_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,
                    uint32_t *totals, cudaStream_t s) {
     return radix_sort_impl<uint32_t>(keys, vals, iota_vals, n, bits, hist, totals, s);
+}
+
+int radix_sort_u32_dev(uint32_t *keys[2], uint32_t *vals[2], int64_t n_max, const uint32_t *n_dev, int bits,
+                       uint32_t *hist, uint32_t *totals, cudaStream_t s) {
+    if (n_max <= 0) return 0;
+    const int sms = sort_setup_sms<uint32_t>();
+    int db = 8;
+    const int passes = radix_pass_plan(bits, &db);
+    return radix_sort_db<uint32_t, 8>(keys, vals, false, n_max, passes, hist, totals, s, sms, n_dev);
 }
 
 int radix_sort_u64(uint64_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int bits, uint32_t *hist,

@@ -92,3 +92,17 @@ def test_negative_capacities_are_rejected(library):
     n = ctypes.c_int64()
     # no handle: the null check comes first
     assert L.fppg_get_feature_edges(None, None, -1, ctypes.byref(n)) == pkg.ERR_ARG
+
+
+def test_triangle_cell_hash_uses_the_primes_as_printed():
+    # Eq. 10's primes, from the fixture transcribed from the paper (p1 is
+    # used as printed, 738560931), against the constants the triangle-cell
+    # lookup of the library hashes with
+    gold = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "hash_eq10.txt")):
+        parts = line.split()
+        if len(parts) == 2 and parts[0] in ("p1", "p2", "p3"):
+            gold[parts[0]] = int(parts[1])
+    src = open(os.path.join(ROOT, "paper_2501_03056_gb300", "csrc", "fppg_internal.cuh")).read()
+    m = re.search(r"kHashP1\s*=\s*(\d+)u,\s*kHashP2\s*=\s*(\d+)u,\s*kHashP3\s*=\s*(\d+)u", src)
+    assert m and gold == {"p1": int(m.group(1)), "p2": int(m.group(2)), "p3": int(m.group(3))}

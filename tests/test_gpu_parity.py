@@ -326,16 +326,18 @@ def test_batched_equals_plain_bit_exact():
         assert np.array_equal(x, y) and np.array_equal(c, d)
 
 
-@pytest.mark.parametrize("variant,block,search", [(0, 128, 4), (1, 256, 4), (0, 128, 0), (1, 256, 0)])
-def test_every_force_variant_gives_the_same_bits(variant, block, search):
+@pytest.mark.parametrize("variant,block,search,inc", [(0, 128, 4, 0), (1, 256, 4, 1), (0, 128, 0, 1), (1, 256, 0, 0)])
+def test_every_force_variant_gives_the_same_bits(variant, block, search, inc):
     # own ranges and the shared-row union accept the same neighbours into
     # the same partial sums in the same order; the warp and the thread
-    # (search 0) forms of the triangle search make the same choices
+    # (search 0) forms of the triangle search make the same choices; the
+    # incremental ordering gives the same order as the full sort
     asm = small_sphere_torus(6)
     plain = [pkg.Body.from_assembly(a) for a in asm]
     batched = [pkg.Body.from_assembly(a) for a in asm]
     bt = pkg.Batch(batched)
     bt.configure(variant, block, search)
+    bt.set_incremental(bool(inc))
     bt.relax(4, use_graph=False)
     bt.store()
     for p in plain:
@@ -490,3 +492,51 @@ def test_generation_matches_oracle(mesh):
     # on rims); the edge tolerance of the inside test keeps both sides'
     # choices together there
     assert err.max() < 1e-4, err.max()
+
+
+def test_incremental_ordering_equals_the_full_sort():
+    # the repaired previous order is the one order by (key, id): the same
+    # permutation as the stable sort, every iteration, with graphs, across
+    # a reload of the state (a foreign previous order) and a switch of mode
+    asm = small_sphere_torus(8)
+    full = [pkg.Body.from_assembly(a) for a in asm]
+    inc = [pkg.Body.from_assembly(a) for a in asm]
+    bf, bi = pkg.Batch(full), pkg.Batch(inc)
+    bf.set_incremental(False)
+    bi.set_incremental(True)
+    for bt in (bf, bi):
+        bt.set_graph_iters(5)
+        bt.relax(15, use_graph=True)
+        bt.store()
+    for p, q in zip(full, inc):
+        assert np.array_equal(p.get_particles()[0], q.get_particles()[0])
+    # reload a different state into the incremental batch: its previous
+    # order is now foreign and must repair itself
+    for q, a in zip(inc, asm):
+        q.set_particles(a.xyz, a.cls)
+    bi.load()
+    bi.relax(3, use_graph=False)
+    bi.set_incremental(False)
+    bi.relax(2, use_graph=False)
+    bi.set_incremental(True)
+    bi.relax(3, use_graph=False)
+    bi.store()
+    ref = [pkg.Body.from_assembly(a) for a in asm]
+    for r in ref:
+        r.relax(8)
+    for r, q in zip(ref, inc):
+        assert np.array_equal(r.get_particles()[0], q.get_particles()[0])
+    # keys and the stable permutation of single bodies in the incremental
+    # form against the oracle, on a fresh order and after relaxing
+    for a in asm:
+        b, o = pair(a)
+        b.set_incremental(True)
+        for it in range(3):
+            key, perm, cells, st, en = b.debug_grid()
+            okey, operm = o.keys()
+            assert np.array_equal(key, okey) and np.array_equal(perm, operm), (a.name, it)
+            oc, os_, oe = o.cell_ranges()
+            assert np.array_equal(cells, oc) and np.array_equal(st, os_) and np.array_equal(en, oe)
+            b.relax(2)
+            o.relax(2)
+
