@@ -221,6 +221,25 @@ int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_
  * Enqueued on the stream; does not synchronise.  Errors: FPPG_ERR_STATE
  * without particles; FPPG_ERR_ARG for n_iter < 0. */
 int fppg_relax(fppg_ctx *ctx, int32_t n_iter);
+/* Spatial decomposition over several GPUs (one body split into slabs, one
+ * per process; the exchanges are the caller's).  fppg_set_ghost_count marks
+ * the last n_ghost particles of the set as ghosts: copies of particles a
+ * neighbouring domain owns within 2h of the shared face.  A ghost acts on
+ * its neighbours by its class (Eq. 15 with the class mask) but never moves,
+ * gets no force and is left out of amax and fppg_stats.  fppg_set_particles
+ * clears the count.  FPPG_ERR_ARG outside 0..n, FPPG_ERR_STATE without
+ * particles.
+ * One iteration of Algorithm 1 in two halves, so that the largest force can
+ * be reduced over the domains between them (the time step of Eqs. 22-23 is
+ * shared): fppg_relax_forces builds the grid and sums the forces (A1-A4) and
+ * writes this domain's largest |a| over its moving particles to *amax_host;
+ * fppg_relax_step takes the step with the given amax (every domain passes
+ * the same, the maximum over all) and projects (A5-A6).  Both synchronise
+ * the stream.  fppg_relax_step without a preceding fppg_relax_forces is
+ * FPPG_ERR_STATE; amax must be finite and >= 0. */
+int fppg_set_ghost_count(fppg_ctx *ctx, int64_t n_ghost);
+int fppg_relax_forces(fppg_ctx *ctx, float *amax_host);
+int fppg_relax_step(fppg_ctx *ctx, float amax);
 /* Same iteration with the acceleration a = -dE/dx of the uniformity energy
  * (energy-descent relaxation). */
 int fppg_relax_energy(fppg_ctx *ctx, int32_t n_iter);

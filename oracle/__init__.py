@@ -79,6 +79,9 @@ def lib():
                 "oracle_volume_inside": (None, [vp, P(f32), i64, P(i32)]),
                 "oracle_ray_parity": (None, [vp, P(f64), i64, P(i32)]),
                 "oracle_relax": (C.c_int, [vp, i32]),
+                "oracle_set_ghost_count": (None, [vp, i64]),
+                "oracle_relax_forces": (f64, [vp]),
+                "oracle_relax_step": (C.c_int, [vp, f64]),
                 "oracle_boolean_keep": (None, [vp, vp, C.c_int, C.c_int, P(i32)]),
                 "oracle_boolean_relax": (C.c_int, [vp, vp, C.c_int, i32]),
                 "oracle_relax_energy": (C.c_int, [vp, i32]),
@@ -300,6 +303,19 @@ class Oracle:
 
     def relax(self, n_iter):
         lib().oracle_relax(self._c, int(n_iter))
+
+    def set_ghost_count(self, n_ghost):
+        """The last n_ghost particles are ghosts (act on neighbours, never move)."""
+        lib().oracle_set_ghost_count(self._c, int(n_ghost))
+
+    def relax_forces(self) -> float:
+        """First half of an iteration: forces; returns this body's amax."""
+        return float(lib().oracle_relax_forces(self._c))
+
+    def relax_step(self, amax: float):
+        """Second half: the step with the given amax, then the projections."""
+        if lib().oracle_relax_step(self._c, float(amax)) != 0:
+            raise ValueError("relax_step needs relax_forces first")
 
     def boolean_keep(self, other: "Oracle", op: int, first: bool) -> np.ndarray:
         """Which of this body's particles stay in Boolean operation `op`

@@ -115,6 +115,8 @@ typedef struct {
     int32_t *cls;
     int32_t *cons;
     int fixed_features;
+    int64_t n_ghost;   /* the last n_ghost particles are ghosts: they act, never move */
+    double *split_acc; /* forces of oracle_relax_forces, kept for oracle_relax_step */
     int mobile_mask;   /* bit c: class c may move (S, V, F; I and P never do) */
     int cascade;       /* surface re-projection: 0 closest over 27 cells, 1 the cascade of Sec. 3.3.3 */
     double last_maxdisp;
@@ -483,6 +485,7 @@ static void free_features(or_ctx *c)
 void oracle_destroy(or_ctx *c)
 {
     if (!c) return;
+    free(c->split_acc);
     free(c->V);
     free(c->Vf);
     free(c->T);
@@ -831,6 +834,9 @@ int oracle_set_particles(or_ctx *c, const float *xyz, const int32_t *cls, int64_
         c->cons[i] = -1;
     }
     c->last_maxdisp = 0.0;
+    c->n_ghost = 0;
+    free(c->split_acc);
+    c->split_acc = NULL;
     return 0;
 }
 
@@ -859,6 +865,10 @@ static int is_mobile(const or_ctx *c, int32_t cl)
 
 /* does a particle of class cj act on one of class ci (interaction rules of
  * Sec. 3.3.3 and Sec. 3.3.4) */
+/* particle i moves: a mobile class and not a ghost (a copy of a particle that
+ * another domain of a spatial decomposition owns) */
+static int moves(const or_ctx *c, int64_t i) { return i < c->n - c->n_ghost && is_mobile(c, c->cls[i]); }
+
 static int acts_on(int32_t ci, int32_t cj)
 {
     switch (ci) {
@@ -1044,7 +1054,7 @@ static double compute_forces(const or_ctx *c, const double *X, double *acc, int3
     for (int64_t i = 0; i < c->n; i++) {
         force_acc fa = {c, X, {0, 0, 0}, 0};
         for_neighbours(c, X, c->cls, L, c->n, i, 1, force_pair, &fa);
-        int mob = is_mobile(c, c->cls[i]);
+        int mob = moves(c, i);
         for (int k = 0; k < 3; k++) acc[3 * i + k] = mob ? fa.a[k] : 0.0;
         if (count) count[i] = (int32_t)fa.cnt;
         if (mob) {
@@ -1470,7 +1480,7 @@ static void apply_step_partner(or_ctx *c, const double *acc, double amax, const 
         int32_t cl = c->cls[i];
         Cn[i] = c->cons[i];
         memcpy(Xn + 3 * i, x, sizeof(double) * 3);
-        if (!is_mobile(c, cl)) continue;
+        if (!moves(c, i)) continue;
         double v[3], dr[3], y[3];
         for (int k = 0; k < 3; k++) {
             v[k] = acc[3 * i + k] * dt;   /* Eq. 22 with v_n = 0 */
@@ -1521,6 +1531,34 @@ int oracle_relax(or_ctx *c, int32_t n_iter)
         apply_step(c, acc, amax);
     }
     free(acc);
+    return 0;
+}
+
+/* One iteration in two halves for a spatial decomposition (the domains
+ * share one time step, so the largest force is reduced over them between
+ * the halves): forces of every particle (ghosts act, do not move), returning
+ * this domain's amax; then the step of Eqs. 22-25 with the given amax and
+ * the projections. */
+void oracle_set_ghost_count(or_ctx *c, int64_t n_ghost)
+{
+    c->n_ghost = n_ghost < 0 ? 0 : (n_ghost > c->n ? c->n : n_ghost);
+}
+
+double oracle_relax_forces(or_ctx *c)
+{
+    free(c->split_acc);
+    c->split_acc = malloc(sizeof(double) * 3 * (c->n ? c->n : 1));
+    double amax = compute_forces(c, c->X, c->split_acc, NULL);
+    c->last_amax = amax;
+    return amax;
+}
+
+int oracle_relax_step(or_ctx *c, double amax)
+{
+    if (!c->split_acc) return -1;
+    apply_step(c, c->split_acc, amax);
+    free(c->split_acc);
+    c->split_acc = NULL;
     return 0;
 }
 
@@ -1864,21 +1902,22 @@ void oracle_stats(const or_ctx *c, double *out)
     or_kv *L = build_cells(c, c->X, c->n);
     densities(c, c->X, L, rho);
     double s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0}, cnt[3] = {0, 0, 0}, rmin = INFINITY;
-    for (int64_t i = 0; i < c->n; i++) {
+    const int64_t n_own = c->n - c->n_ghost;   /* ghosts are another domain's */
+    for (int64_t i = 0; i < n_own; i++) {
         int32_t cl = c->cls[i];
         if (cl > OR_F) continue;
         s1[cl] += rho[i];
         cnt[cl] += 1.0;
     }
     for (int k = 0; k < 3; k++) s1[k] = cnt[k] > 0 ? s1[k] / cnt[k] : 0.0;
-    for (int64_t i = 0; i < c->n; i++) {
+    for (int64_t i = 0; i < n_own; i++) {
         int32_t cl = c->cls[i];
         if (cl > OR_F) continue;
         s2[cl] += (rho[i] - s1[cl]) * (rho[i] - s1[cl]);
     }
 #pragma omp parallel for schedule(dynamic, 256) reduction(min : rmin)
     for (int64_t i = 0; i < c->n; i++) {
-        if (!is_mobile(c, c->cls[i])) continue;
+        if (!moves(c, i)) continue;
         min_acc ma = {c->X, INFINITY};
         for_neighbours(c, c->X, c->cls, L, c->n, i, 1, min_pair, &ma);
         if (ma.rmin < rmin) rmin = ma.rmin;

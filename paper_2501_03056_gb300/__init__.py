@@ -92,6 +92,9 @@ def lib():
                 "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(i32), P_(f64)],
                 "fppg_batch_set_incremental": [vp, i32],
                 "fppg_set_incremental": [vp, i32],
+                "fppg_set_ghost_count": [vp, i64],
+                "fppg_relax_forces": [vp, P_(f32)],
+                "fppg_relax_step": [vp, f32],
                 "fppg_batch_configure": [vp, i32, i32, i32],
                 "fppg_set_mobile_classes": [vp, i32],
                 "fppg_set_projection_rule": [vp, i32],
@@ -266,6 +269,22 @@ class Body:
 
     def relax(self, n_iter: int):
         self._chk(lib().fppg_relax(self._h, int(n_iter)))
+
+    def set_ghost_count(self, n_ghost: int):
+        """The last n_ghost particles become ghosts (they act, never move)."""
+        self._chk(lib().fppg_set_ghost_count(self._h, int(n_ghost)))
+
+    def relax_forces(self) -> float:
+        """First half of an iteration (grid and forces); returns this body's
+        largest |a| over its moving particles."""
+        a = C.c_float()
+        self._chk(lib().fppg_relax_forces(self._h, C.byref(a)))
+        return a.value
+
+    def relax_step(self, amax: float):
+        """Second half of the iteration: the step with the given amax, then
+        the projections."""
+        self._chk(lib().fppg_relax_step(self._h, C.c_float(amax)))
 
     def relax_energy(self, n_iter: int):
         self._chk(lib().fppg_relax_energy(self._h, int(n_iter)))

@@ -30,6 +30,8 @@ struct fppg_ctx {
     fppg_ctx *partner = nullptr;   // Boolean partner (fppg_boolean)
     int bool_op = 0;               // FPPG_UNION, FPPG_DIFFERENCE or FPPG_INTERSECTION
     bool bool_first = false;       // the first operand of the operation
+    int64_t n_ghost = 0;           // the last n_ghost particles are ghosts (fppg_set_ghost_count)
+    int split_buf = -1;            // grid buffer of the last fppg_relax_forces, until its step
     // device staging of the host particle arrays of set / get, kept between
     // calls (both synchronise the stream before they return)
     void *stage = nullptr;
@@ -128,7 +130,8 @@ int ctx_group(fppg_ctx *c) {
     g.hp[0].mobile = c->mobile_mask;
     g.hp[0].cascade = c->cascade;
     g.mesh = view_of(c->body);
-    return g.upload_params(c->stream, c->err) ? FPPG_ERR_CUDA : FPPG_OK;
+    const int r = g.upload_params(c->stream, c->err);
+    return r == 0 ? FPPG_OK : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
 }
 
 } // namespace
@@ -295,6 +298,8 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
     if (bad_xyz) return fail(ctx->err, FPPG_ERR_ARG, "non-finite coordinate");
     Group &g = ctx->group;
     ctx->has_particles = false;     // until the new set is complete
+    ctx->split_buf = -1;
+    ctx->n_ghost = 0;
     if (n != g.d.N || !g.d.pos) {
         int r = g.alloc_particles(n, ctx->err);
         if (r) return r;
@@ -432,6 +437,51 @@ static int relax_impl(fppg_ctx *ctx, int32_t n_iter, bool energy_mode) {
 }
 
 int fppg_relax(fppg_ctx *ctx, int32_t n_iter) { return relax_impl(ctx, n_iter, false); }
+
+int fppg_set_ghost_count(fppg_ctx *ctx, int64_t n_ghost) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    if (n_ghost < 0 || n_ghost > ctx->n) return fail(ctx->err, FPPG_ERR_ARG, "ghost count outside 0..n");
+    ctx->n_ghost = n_ghost;
+    tag_ghosts(ctx->group, ctx->n - n_ghost, ctx->stream);
+    CUDA_OR(ctx->err, cudaGetLastError());
+    return FPPG_OK;
+}
+
+int fppg_relax_forces(fppg_ctx *ctx, float *amax_host) {
+    if (!ctx || !amax_host) return FPPG_ERR_ARG;
+    if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
+    if (ctx->partner)
+        return fail(ctx->err, FPPG_ERR_STATE, "a Boolean operand relaxes in a batch together with its partner");
+    uint32_t a = 0u;
+    if (ctx->n > 0) {
+        Group &g = ctx->group;
+        ctx->split_buf = build_grid(g, ctx->stream);
+        forces(g, ctx->stream, nullptr);
+        CUDA_OR(ctx->err, cudaMemcpyAsync(&a, g.d.amax, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    } else {
+        ctx->split_buf = 0;
+    }
+    memcpy(amax_host, &a, sizeof(float));
+    return FPPG_OK;
+}
+
+int fppg_relax_step(fppg_ctx *ctx, float amax) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (ctx->split_buf < 0) return fail(ctx->err, FPPG_ERR_STATE, "fppg_relax_step needs a fppg_relax_forces first");
+    if (!(amax >= 0.f) || !std::isfinite(amax)) return fail(ctx->err, FPPG_ERR_ARG, "amax must be finite, >= 0");
+    const int buf = ctx->split_buf;
+    ctx->split_buf = -1;
+    if (ctx->n == 0) return FPPG_OK;
+    Group &g = ctx->group;
+    uint32_t a;
+    memcpy(&a, &amax, sizeof(a));
+    CUDA_OR(ctx->err, cudaMemcpyAsync(g.d.amax, &a, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    step_and_project(g, ctx->stream, buf);
+    CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
+    return FPPG_OK;
+}
 
 int fppg_relax_energy(fppg_ctx *ctx, int32_t n_iter) { return relax_impl(ctx, n_iter, true); }
 

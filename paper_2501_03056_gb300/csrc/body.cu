@@ -363,6 +363,7 @@ int Group::upload_params(cudaStream_t s, std::string &err) {
 }
 
 void Group::free_all() {
+    escr.release();
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
     if (graph_stream) cudaStreamDestroy(graph_stream);

@@ -76,8 +76,23 @@ struct Body {
 // Host description of one body inside a group.
 AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, int fixed_features);
 
+// scratch of the energy and its backward (energy.cu), kept between calls
+struct EnergyScratch {
+    float4 *xs = nullptr, *vcon = nullptr;
+    double *e_s = nullptr, *part = nullptr;
+    uint32_t *vk[2] = {nullptr, nullptr}, *vi[2] = {nullptr, nullptr}, *hist = nullptr, *tot = nullptr;
+    int64_t n = 0;   // particles it is sized for
+    void release() {
+        void *p[] = {xs, vcon, e_s, part, vk[0], vk[1], vi[0], vi[1], hist, tot};
+        for (void *q : p)
+            if (q) cudaFree(q);
+        *this = EnergyScratch();
+    }
+};
+
 struct Group {
     DevGroup d;
+    EnergyScratch escr;
     std::vector<AsmParams> hp;    // host copy of the per-body parameters
     MeshView mesh{};
     bool owns_mesh = false;       // batches own concatenated copies
@@ -114,6 +129,11 @@ constexpr int64_t kIncrementalMinN = 1 << 21;
 constexpr int kPhaseEvents = 5;
 // one relaxation iteration of every body of the group (A1-A6)
 void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg = nullptr);
+// A5-A6 (step, then the projections) after a grid build that returned buf
+// and a force pass; amax is whatever the device holds
+void step_and_project(Group &g, cudaStream_t s, int buf);
+// particles [first_ghost, N) become ghosts, the others not (the ghost bit of w)
+void tag_ghosts(Group &g, int64_t first_ghost, cudaStream_t s);
 // A1-A3 only (keys, sort, gather + cell ranges); returns the buffer index
 // holding the sorted keys / ids
 int build_grid(Group &g, cudaStream_t s);

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(TPB) k_rho(const float4 *__restrict__ pos_s, c
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int cls = active ? cls_of(p.w) : kClsI;
     const AsmParams &A = P[active ? body_of(p.w) : 0];
-    const bool mob = active && is_mobile(cls, A);
+    const bool mob = active && is_mobile(cls, A) && !is_ghost(p.w);
     const uint32_t mbits = mob ? acts_on_bits(cls) : 0u;
     const float hih = A.half_inv_h;
     const float2 npx = make_float2(-p.x, -p.x), npy = make_float2(-p.y, -p.y), npz = make_float2(-p.z, -p.z);
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(TPB) k_grad(const float4 *__restrict__ pos_s, 
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int ck = active ? cls_of(p.w) : kClsI;
     const AsmParams &A = P[active ? body_of(p.w) : 0];
-    const bool mk = active && is_mobile(ck, A);
+    const bool mk = active && is_mobile(ck, A) && !is_ghost(p.w);
     const float ek = mk ? coef_s[k] : 0.f;
     const uint32_t bk = mk ? acts_on_bits(ck) : 0u, fk = felt_by_bits(ck);
     const float hih = A.half_inv_h;
@@ -362,58 +362,60 @@ void energy_accel(Group &g, cudaStream_t s) {
                                         d.acc_s, d.amax);
 }
 
+// The scratch of energy(): kept in the group between calls (allocated on the
+// first call, grown when the particle count grows), so a repeated energy and
+// backward costs no allocation and no implicit device synchronisation.
+static int energy_scratch(Group &g, int64_t N, std::string &err) {
+    EnergyScratch &e = g.escr;
+    if (e.n >= N && e.xs) return 0;
+    e.release();
+    const int64_t M = 3 * N;
+    const size_t n1 = (size_t)std::max<int64_t>(N, 1), m1 = (size_t)std::max<int64_t>(M, 1);
+    if (dev_malloc(&e.xs, sizeof(float4) * n1) != cudaSuccess ||
+        dev_malloc(&e.e_s, sizeof(double) * n1) != cudaSuccess ||
+        dev_malloc(&e.part, sizeof(double) * (kSumBlocks + 1)) != cudaSuccess ||
+        dev_malloc(&e.vcon, sizeof(float4) * m1) != cudaSuccess ||
+        dev_malloc(&e.vk[0], 4 * m1) != cudaSuccess || dev_malloc(&e.vk[1], 4 * m1) != cudaSuccess ||
+        dev_malloc(&e.vi[0], 4 * m1) != cudaSuccess || dev_malloc(&e.vi[1], 4 * m1) != cudaSuccess ||
+        dev_malloc(&e.hist, 4 * (size_t)kMaxDigits * std::max<int64_t>(radix_tiles(M), 1)) != cudaSuccess ||
+        dev_malloc(&e.tot, 4 * (size_t)kMaxDigits) != cudaSuccess) {
+        e.release();
+        err = "energy: out of device memory";
+        return 3;
+    }
+    e.n = N;
+    return 0;
+}
+
 int energy(Group &g, const Body &b, const float *y_dev, const float *verts_dev, double *E, float *gy, float *gV,
            cudaStream_t s, std::string &err) {
     DevGroup &d = g.d;
     const int64_t N = d.N, M = 3 * N;          // M: vertex contributions (three per particle)
-    float4 *xs = nullptr, *vcon = nullptr;
-    double *e_s = nullptr, *part = nullptr;
-    uint32_t *vk[2] = {nullptr, nullptr}, *vi[2] = {nullptr, nullptr}, *hist = nullptr, *tot = nullptr;
-    auto cleanup = [&]() {
-        void *p[] = {xs, vcon, e_s, part, vk[0], vk[1], vi[0], vi[1], hist, tot};
-        for (void *q : p)
-            if (q) cudaFree(q);
-    };
-    const size_t n1 = (size_t)std::max<int64_t>(N, 1), m1 = (size_t)std::max<int64_t>(M, 1);
-    bool fail = dev_malloc(&xs, sizeof(float4) * n1) != cudaSuccess ||
-                dev_malloc(&e_s, sizeof(double) * n1) != cudaSuccess ||
-                dev_malloc(&part, sizeof(double) * (kSumBlocks + 1)) != cudaSuccess;
-    if (!fail && gV)
-        fail = dev_malloc(&vcon, sizeof(float4) * m1) != cudaSuccess ||
-               dev_malloc(&vk[0], 4 * m1) != cudaSuccess || dev_malloc(&vk[1], 4 * m1) != cudaSuccess ||
-               dev_malloc(&vi[0], 4 * m1) != cudaSuccess || dev_malloc(&vi[1], 4 * m1) != cudaSuccess ||
-               dev_malloc(&hist, 4 * (size_t)kMaxDigits * std::max<int64_t>(radix_tiles(M), 1)) != cudaSuccess ||
-               dev_malloc(&tot, 4 * (size_t)kMaxDigits) != cudaSuccess;
-    if (fail) {
-        cleanup();
-        err = "energy: out of device memory";
-        return 3;
-    }
+    if (const int r = energy_scratch(g, N, err)) return r;
+    EnergyScratch &es = g.escr;
     const float *V = verts_dev ? verts_dev : b.d_verts;
     float4 *saved = d.pos;
-    k_project_frozen<<<nblocks(N), TPB, 0, s>>>(y_dev, d.pos, d.cons, N, V, b.d_tris, xs);
-    d.pos = xs;
+    k_project_frozen<<<nblocks(N), TPB, 0, s>>>(y_dev, d.pos, d.cons, N, V, b.d_tris, es.xs);
+    d.pos = es.xs;
     int buf = build_grid(g, s);
     d.pos = saved;
-    k_rho<<<nblocks(N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.fstart, d.coef_s, e_s);
-    k_sum_fixed<<<kSumBlocks, TPB, 0, s>>>(e_s, N, part);
-    k_sum_fixed<<<1, TPB, 0, s>>>(part, kSumBlocks, part + kSumBlocks);
+    k_rho<<<nblocks(N + 1), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.fstart, d.coef_s, es.e_s);
+    k_sum_fixed<<<kSumBlocks, TPB, 0, s>>>(es.e_s, N, es.part);
+    k_sum_fixed<<<1, TPB, 0, s>>>(es.part, kSumBlocks, es.part + kSumBlocks);
     if (gy || gV) {
-        k_grad<<<nblocks(N), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.fstart, d.coef_s,
-                                           1.f, d.acc_s, nullptr);
+        k_grad<<<nblocks(N), TPB, 0, s>>>(d.pos_s, d.pos_p, N, d.params, d.fstart, d.coef_s, 1.f, d.acc_s, nullptr);
         k_vjp<<<nblocks(N), TPB, 0, s>>>(d.acc_s, d.id[buf], N, y_dev, d.pos, d.cons, V, b.d_tris, b.nv, gy,
-                                          gV ? vk[0] : nullptr, vcon);
+                                          gV ? es.vk[0] : nullptr, es.vcon);
         if (gV) {
             cudaMemsetAsync(gV, 0, sizeof(float) * 3 * (size_t)b.nv, s);
             int bits = 1;
             while (bits < 32 && ((uint64_t)b.nv >> bits) != 0) bits++;
-            const int vb = radix_sort_u32(vk, vi, true, M, bits, hist, tot, s);
-            k_vertex_sum<<<nblocks(M), TPB, 0, s>>>(vk[vb], vi[vb], M, vcon, b.nv, gV);
+            const int vb = radix_sort_u32(es.vk, es.vi, true, M, bits, es.hist, es.tot, s);
+            k_vertex_sum<<<nblocks(M), TPB, 0, s>>>(es.vk[vb], es.vi[vb], M, es.vcon, b.nv, gV);
         }
     }
-    cudaMemcpyAsync(E, part + kSumBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(E, es.part + kSumBlocks, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    cleanup();
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("energy: ") + cudaGetErrorString(e);

@@ -332,6 +332,13 @@ __device__ inline bool is_mobile(int cls, const AsmParams &A) {
     return (cls == kClsS || cls == kClsV || (cls == kClsF && !A.fixed_features)) && ((A.mobile >> cls) & 1);
 }
 
+// Ghost particles (bit 7 of w, above the one-hot class bits): copies of
+// another domain's particles near a shared face (spatial decomposition over
+// several GPUs).  A ghost acts on its neighbours by its class, but it never
+// moves, has no force of its own and is left out of amax and the statistics.
+constexpr uint32_t kGhostBit = 0x80u;
+__device__ inline bool is_ghost(float w) { return (__float_as_uint(w) & kGhostBit) != 0u; }
+
 // ---- host side -------------------------------------------------------------
 // Every device allocation of the library goes through dev_malloc, so that a
 // test can make one chosen allocation fail as if the device were out of
@@ -371,7 +378,8 @@ int64_t scan_tmp_elems(int64_t n);
 // the count array starts the next accumulation at zero
 void exclusive_scan_u32_clear(uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, int64_t tmp_elems,
                               cudaStream_t s);
-// kernel launches of exclusive_scan_u32 / _clear on n elements (no total)
+// kernel launches of exclusive_scan_u32 (no total) / _clear on n elements
 int scan_launches(int64_t n);
+int scan_clear_launches(int64_t n);
 
 } // namespace fppg

@@ -352,12 +352,14 @@ __device__ inline void pair_step(const float4 *__restrict__ pos_p, const float4 
     const float2 dx = __fadd2_rn(make_float2(A.x, A.y), npx);     // q - p
     const float2 dy = __fadd2_rn(make_float2(A.z, A.w), npy);
     const float2 dz = __fadd2_rn(make_float2(B.x, B.y), npz);
-    const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
-    const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
-    float2 t = __ffma2_rn(r, make_float2(-hih, -hih), make_float2(1.f, 1.f));   // 1 - r / 2h
     float2 w;
     if (!COUNT) {
-        t = make_float2(fmaxf(t.x, 0.f), fmaxf(t.y, 0.f));
+        // r^2 with fused multiply-adds and the weight max(1 - r / 2h, 0)^3
+        // from a saturating FMA: no decision is taken on r^2 here (a slot
+        // beyond 2h weighs exactly 0, one within rounding of 2h below 1e-18)
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const float2 t = make_float2(__saturatef(fmaf(sqrt_approx(r2.x), -hih, 1.f)),
+                                     __saturatef(fmaf(sqrt_approx(r2.y), -hih, 1.f)));
         w = __fmul2_rn(__fmul2_rn(t, t), t);
         bool k0 = has0, k1 = has1;
         if (!ALL) {
@@ -369,6 +371,11 @@ __device__ inline void pair_step(const float4 *__restrict__ pos_p, const float4 
             w.y = k1 ? w.y : 0.f;
         }
     } else {
+        // the counting form: the exact FP32 test r^2 = (dx dx + dy dy) + dz dz
+        // < (2h)^2 without contraction decides each neighbour
+        const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+        const float2 r = make_float2(sqrt_approx(r2.x), sqrt_approx(r2.y));
+        const float2 t = __ffma2_rn(r, make_float2(-hih, -hih), make_float2(1.f, 1.f));   // 1 - r / 2h
         bool t0 = has0 && r2.x < R2, t1 = has1 && r2.y < R2;
         if (!ALL) {
             t0 = t0 && (mbits & __float_as_uint(B.z)) != 0u;
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(TPB, 5)
     const int cls = active ? cls_of(p.w) : kClsI;
     const int b = active ? body_of(p.w) : 0;
     const AsmParams &A = P[b];
-    const bool mob = active && is_mobile(cls, A);
+    const bool mob = active && is_mobile(cls, A) && !is_ghost(p.w);
     // the counting form also counts the neighbours of fixed particles
     const uint32_t mbits = (mob || (COUNT && active)) ? acts_on_bits(cls) : 0u;
     const int nx = A.ng_n[0], ny = A.ng_n[1], nz = A.ng_n[2];
@@ -500,7 +507,7 @@ __global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s,
             }
         }
     if (count_s) count_s[k] = cnt;
-    if (cand_s) cand_s[k] = is_mobile(cls, A) ? cand : 0;
+    if (cand_s) cand_s[k] = is_mobile(cls, A) && !is_ghost(p.w) ? cand : 0;
 }
 
 // ---- A6 helpers -------------------------------------------------------------
@@ -856,7 +863,7 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
     float disp = 0.f;
     bool queue = false;
     float3 y = f3(p);
-    if (active && is_mobile(cls, A)) {
+    if (active && is_mobile(cls, A) && !is_ghost(p.w)) {
         const uint32_t i = id_s[k];
         const float am = __uint_as_float(amax[A.amax_slot]);
         const float sc = am > 0.f ? A.step_h / am : 0.f;     // dt^2 with dt = 0.25 sqrt(h / amax)
@@ -1273,7 +1280,7 @@ __global__ void __launch_bounds__(TPB) k_density(const float4 *__restrict__ pos_
             }
         }
     rho_s[k] = A.alpha * (rho + 1.f);
-    if (is_mobile(cls, A) && rmin2 < FLT_MAX) atomicMin(minpair, __float_as_uint(sqrtf(rmin2)));
+    if (is_mobile(cls, A) && !is_ghost(p.w) && rmin2 < FLT_MAX) atomicMin(minpair, __float_as_uint(sqrtf(rmin2)));
 }
 
 __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__restrict__ rho_s, int64_t N,
@@ -1281,8 +1288,9 @@ __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__re
     // sums[0..2] sum rho, [3..5] sum (rho - mean)^2 when mean != null, [6..8] count
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (k >= N) return;
-    int c = cls_of(pos_s[k].w);
-    if (c > kClsF) return;
+    const float w = pos_s[k].w;
+    int c = cls_of(w);
+    if (c > kClsF || is_ghost(w)) return;
     double r = rho_s[k];
     if (mean) {
         double d = r - mean[c];
@@ -1332,7 +1340,7 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
 }
 
 int grid_kernels(const DevGroup &d) {
-    const int tail = 1 + scan_launches(kSlabs * d.total_cells + 1);    // gather + start scan
+    const int tail = 1 + scan_clear_launches(kSlabs * d.total_cells + 1);    // gather + start scan
     if (!d.incremental) return 1 + 3 * d.passes + tail;
     // keys, 2 scans with totals, 2 compactions, keep flags, the changed
     // list's radix passes, merge splits and merge
@@ -1391,6 +1399,32 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
         cudaEventRecordWithFlags(g.ev[g.ev_used + 4], s, flags);
         g.ev_used += kPhaseEvents;
     }
+}
+
+void step_and_project(Group &g, cudaStream_t s, int buf) {
+    DevGroup &d = g.d;
+    if (d.N == 0) return;
+    k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
+                                         d.maxdisp, d.work, d.work_count, d.cert, d.cons_s);
+    if (g.search_thread)
+        k_search_thread<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh,
+                                                        d.maxdisp, d.work, d.work_count, d.N, d.cert);
+    else
+        k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp,
+                                                 d.work, d.work_count, d.N, d.cert);
+}
+
+namespace {
+__global__ void k_tag_ghosts(float4 *__restrict__ pos, int64_t n, int64_t first_ghost) {
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t w = __float_as_uint(pos[i].w);
+    pos[i].w = __uint_as_float(i >= first_ghost ? (w | kGhostBit) : (w & ~kGhostBit));
+}
+} // namespace
+
+void tag_ghosts(Group &g, int64_t first_ghost, cudaStream_t s) {
+    if (g.d.N > 0) k_tag_ghosts<<<nblocks(g.d.N), TPB, 0, s>>>(g.d.pos, g.d.N, first_ghost);
 }
 
 void unpermute_dev(DevGroup &d, int buf, cudaStream_t s, float *acc_out, const int32_t *count_s,

@@ -8,6 +8,7 @@
 //               per-warp counters), staging through shared memory so that
 //               global writes are contiguous runs per digit
 // No CTA waits on another CTA, so nothing here can spin.
+#include <cstdint>
 #include <cstring>
 
 #include "fppg_internal.cuh"
@@ -66,6 +67,10 @@ __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int6
     constexpr int TILE = RW * RC * 32, ND = 1 << DB;
     __shared__ uint32_t cnt[ND];
     if (n_dev) n = min(n, (int64_t)*n_dev);
+    if ((int64_t)blockIdx.x * TILE >= n) {   // a tile past the count: an empty histogram row
+        for (int d = threadIdx.x; d < ND; d += RT) hist[(int64_t)d * n_tiles + blockIdx.x] = 0u;
+        return;
+    }
     for (int d = threadIdx.x; d < ND; d += RT) cnt[d] = 0;
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -264,40 +269,90 @@ int radix_sort_impl(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, in
 }
 
 // ---- exclusive scan (set-up work) -----------------------------------------
-constexpr int SCAN_ITEMS = 4;
+// 16 entries per thread, 4096 per block; entries move as 16-byte vectors
+// when both arrays are 16-byte aligned (VEC), else one by one.  CLEAR: the
+// input is set to 0 once read (a count array made ready for its next
+// accumulation).  in == out is allowed (each thread reads its entries
+// before it writes them).
+constexpr int SCAN_ITEMS = 16;
 constexpr int SCAN_BLOCK = RT * SCAN_ITEMS;
 
-// CLEAR: the input is set to 0 once read (a count array made ready for
-// its next accumulation)
 template <bool CLEAR>
-__global__ void __launch_bounds__(RT) k_scan_block(uint32_t *__restrict__ in, uint32_t *__restrict__ out,
-                                                   int64_t n, uint32_t *__restrict__ block_sums) {
+__global__ void __launch_bounds__(RT) k_scan_block(uint32_t *in, uint32_t *out, int64_t n,
+                                                   uint32_t *__restrict__ block_sums, bool vec) {
     __shared__ uint32_t wsum[RW];
-    int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x * SCAN_ITEMS;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS], s = 0;
+    const bool whole = vec && base + SCAN_ITEMS <= n;
+    if (whole) {
+        uint4 *q = reinterpret_cast<uint4 *>(in + base);
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        v[i] = base + i < n ? in[base + i] : 0u;
-        if (CLEAR && base + i < n) in[base + i] = 0u;
-        s += v[i];
+        for (int c = 0; c < SCAN_ITEMS / 4; c++) {
+            const uint4 a = q[c];
+            v[4 * c] = a.x;
+            v[4 * c + 1] = a.y;
+            v[4 * c + 2] = a.z;
+            v[4 * c + 3] = a.w;
+            if (CLEAR) q[c] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; i++) {
+            v[i] = base + i < n ? in[base + i] : 0u;
+            if (CLEAR && base + i < n) in[base + i] = 0u;
+        }
     }
-    uint32_t tot;
-    uint32_t inc = block_incl_scan(s, wsum, &tot);
-    uint32_t run = inc - s;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        if (base + i < n) out[base + i] = run;
-        run += v[i];
+    for (int i = 0; i < SCAN_ITEMS; i++) s += v[i];
+    uint32_t tot;
+    uint32_t run = block_incl_scan(s, wsum, &tot) - s;
+    if (whole) {
+        uint4 *o = reinterpret_cast<uint4 *>(out + base);
+#pragma unroll
+        for (int c = 0; c < SCAN_ITEMS / 4; c++) {
+            uint4 a;
+            a.x = run;
+            run += v[4 * c];
+            a.y = run;
+            run += v[4 * c + 1];
+            a.z = run;
+            run += v[4 * c + 2];
+            a.w = run;
+            run += v[4 * c + 3];
+            o[c] = a;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; i++) {
+            if (base + i < n) out[base + i] = run;
+            run += v[i];
+        }
     }
     if (threadIdx.x == 0 && block_sums) block_sums[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ offs) {
-    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
-    uint32_t o = offs[blockIdx.x];
-    for (int k = 0; k < SCAN_ITEMS; k++, i += RT)
-        if (i < n) out[i] += o;
+__global__ void __launch_bounds__(RT) k_scan_add(uint32_t *__restrict__ out, int64_t n,
+                                                 const uint32_t *__restrict__ offs, bool vec) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    const uint32_t o = offs[blockIdx.x];
+    if (vec && base + SCAN_ITEMS <= n) {
+        uint4 *q = reinterpret_cast<uint4 *>(out + base);
+#pragma unroll
+        for (int c = 0; c < SCAN_ITEMS / 4; c++) {
+            uint4 a = q[c];
+            a.x += o;
+            a.y += o;
+            a.z += o;
+            a.w += o;
+            q[c] = a;
+        }
+    } else {
+        for (int i = 0; i < SCAN_ITEMS; i++)
+            if (base + i < n) out[base + i] += o;
+    }
 }
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 __global__ void k_scan_total(const uint32_t *in, const uint32_t *out, int64_t n, uint32_t *total) {
     *total = n > 0 ? out[n - 1] + in[n - 1] : 0u;
@@ -336,6 +391,39 @@ int radix_sort_u64(uint64_t *keys[2], uint32_t *vals[2], bool iota_vals, int64_t
     return radix_sort_impl<uint64_t>(keys, vals, iota_vals, n, bits, hist, totals, s);
 }
 
+
+// The last element of `in` is read after the scan to form the total, so
+// `out` must not alias `in` when total_dev is requested.
+template <bool CLEAR>
+static void scan_impl(uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, int64_t tmp_elems, cudaStream_t s) {
+    const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
+    const bool vec = aligned16(in) && aligned16(out);
+    if (nb == 1) {
+        k_scan_block<CLEAR><<<1, RT, 0, s>>>(in, out, n, nullptr, vec);
+    } else {
+        uint32_t *sums = tmp;
+        k_scan_block<CLEAR><<<(unsigned)nb, RT, 0, s>>>(in, out, n, sums, vec);
+        scan_impl<false>(sums, sums, nb, tmp + nb + 1, tmp_elems - nb - 1, s);
+        k_scan_add<<<(unsigned)nb, RT, 0, s>>>(out, n, sums, vec);
+    }
+}
+
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev, uint32_t *tmp,
+                        int64_t tmp_elems, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+        return;
+    }
+    scan_impl<false>(const_cast<uint32_t *>(in), out, n, tmp, tmp_elems, s);   // not written without CLEAR
+    if (total_dev) k_scan_total<<<1, 1, 0, s>>>(in, out, n, total_dev);
+}
+
+void exclusive_scan_u32_clear(uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, int64_t tmp_elems,
+                              cudaStream_t s) {
+    if (n > 0) scan_impl<true>(in, out, n, tmp, tmp_elems, s);
+}
+
+// block sums of every level (with one spare entry each): at most this many
 int64_t scan_tmp_elems(int64_t n) {
     int64_t tot = 0;
     while (n > SCAN_BLOCK) {
@@ -345,45 +433,12 @@ int64_t scan_tmp_elems(int64_t n) {
     return tot + 1;
 }
 
-// The last element of `in` is read after the scan to form the total, so
-// `out` must not alias `in` when total_dev is requested.
-void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total_dev, uint32_t *tmp,
-                        int64_t tmp_elems, cudaStream_t s) {
-    if (n <= 0) {
-        if (total_dev) cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
-        return;
-    }
-    int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    uint32_t *in_ = const_cast<uint32_t *>(in);   // not written without CLEAR
-    if (nb == 1) {
-        k_scan_block<false><<<1, RT, 0, s>>>(in_, out, n, nullptr);
-    } else {
-        uint32_t *sums = tmp;
-        k_scan_block<false><<<(unsigned)nb, RT, 0, s>>>(in_, out, n, sums);
-        exclusive_scan_u32(sums, sums, nb, nullptr, tmp + nb + 1, tmp_elems - nb - 1, s);
-        k_scan_add<<<(unsigned)nb, RT, 0, s>>>(out, n, sums);
-    }
-    if (total_dev) k_scan_total<<<1, 1, 0, s>>>(in, out, n, total_dev);
-}
-
-void exclusive_scan_u32_clear(uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, int64_t tmp_elems,
-                              cudaStream_t s) {
-    if (n <= 0) return;
-    const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
-    if (nb == 1) {
-        k_scan_block<true><<<1, RT, 0, s>>>(in, out, n, nullptr);
-    } else {
-        uint32_t *sums = tmp;
-        k_scan_block<true><<<(unsigned)nb, RT, 0, s>>>(in, out, n, sums);
-        exclusive_scan_u32(sums, sums, nb, nullptr, tmp + nb + 1, tmp_elems - nb - 1, s);
-        k_scan_add<<<(unsigned)nb, RT, 0, s>>>(out, n, sums);
-    }
-}
-
 int scan_launches(int64_t n) {
     if (n <= 0) return 0;
     const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;
     return nb == 1 ? 1 : 2 + scan_launches(nb);
 }
+
+int scan_clear_launches(int64_t n) { return scan_launches(n); }
 
 } // namespace fppg
