@@ -80,6 +80,8 @@ def lib():
                 "oracle_ray_parity": (None, [vp, P(f64), i64, P(i32)]),
                 "oracle_relax": (C.c_int, [vp, i32]),
                 "oracle_set_ghost_count": (None, [vp, i64]),
+                "oracle_boolean_curve": (i64, [vp, vp]),
+                "oracle_curve_points": (i64, [vp, P(f32), i64]),
                 "oracle_relax_forces": (f64, [vp]),
                 "oracle_relax_step": (C.c_int, [vp, f64]),
                 "oracle_boolean_keep": (None, [vp, vp, C.c_int, C.c_int, P(i32)]),
@@ -303,6 +305,20 @@ class Oracle:
 
     def relax(self, n_iter):
         lib().oracle_relax(self._c, int(n_iter))
+
+    def boolean_curve(self, other: "Oracle") -> int:
+        """Feature lines along the curve where this body's surface crosses
+        `other`'s, with their feature particles appended to this body;
+        returns the particles added."""
+        n = int(lib().oracle_boolean_curve(self._c, other._c))
+        self.n += n
+        return n
+
+    def curve_points(self):
+        m = lib().oracle_curve_points(self._c, None, 0)
+        out = np.zeros((max(m, 1), 3), np.float32)
+        lib().oracle_curve_points(self._c, _p(out, C.c_float), m)
+        return out[:m]
 
     def set_ghost_count(self, n_ghost):
         """The last n_ghost particles are ghosts (act on neighbours, never move)."""

@@ -73,6 +73,8 @@ typedef struct {
 typedef struct {
     /* mesh (Sec. 3.1) */
     int64_t nv, nt;
+    int64_t nv_all;     /* nv plus the points of intersection-curve lines (V, Vf hold them all) */
+    int64_t nseg_own;   /* segments of the body's own feature lines; curve segments follow */
     double *V;      /* [nv*3] vertices (FP64 copy of the FP32 input)        */
     float *Vf;      /* [nv*3] vertices as given                             */
     int32_t *T;     /* [nt*3]                                              */
@@ -436,6 +438,7 @@ or_ctx *oracle_create(const float *verts, int64_t nv, const int32_t *tris, int64
         if (tris[i] < 0 || tris[i] >= nv) return NULL;
     or_ctx *c = calloc(1, sizeof(or_ctx));
     c->nv = nv;
+    c->nv_all = nv;
     c->nt = nt;
     c->dx = dx;
     c->h = h;
@@ -480,6 +483,8 @@ static void free_features(or_ctx *c)
     c->fe = c->sing = c->line_closed = c->seg_v = c->seg_line = NULL;
     c->line_first = c->line_nseg = NULL;
     c->nfe = c->nsing = c->nlines = c->nseg = 0;
+    c->nseg_own = 0;
+    c->nv_all = c->nv;   /* the points of intersection-curve lines go with them */
 }
 
 void oracle_destroy(or_ctx *c)
@@ -701,6 +706,7 @@ int64_t oracle_extract_features(or_ctx *c, double dihedral_deg)
     }
 #undef PUSH_SEG
 #undef PUSH_LINE
+    c->nseg_own = c->nseg;
     free(col);
     free(inc);
     free(fill);
@@ -760,11 +766,21 @@ int64_t oracle_feature_particles(const or_ctx *c, double dx, double *xyz, int32_
     return feature_particles_on_segments(c, dx, xyz, cls, NULL, cap);
 }
 
+static int64_t feature_particles_of_lines(const or_ctx *c, double dx, int64_t l0, int64_t l1, double *xyz,
+                                          int32_t *cls, int32_t *seg, int64_t cap);
+
 static int64_t feature_particles_on_segments(const or_ctx *c, double dx, double *xyz, int32_t *cls, int32_t *seg,
                                              int64_t cap)
 {
+    return feature_particles_of_lines(c, dx, 0, c->nlines, xyz, cls, seg, cap);
+}
+
+/* the same for the lines l0 .. l1 - 1 */
+static int64_t feature_particles_of_lines(const or_ctx *c, double dx, int64_t l0, int64_t l1, double *xyz,
+                                          int32_t *cls, int32_t *seg, int64_t cap)
+{
     int64_t cnt = 0;
-    char *done = calloc((size_t)c->nv, 1);
+    char *done = calloc((size_t)(c->nv_all ? c->nv_all : 1), 1);
 #define EMIT(px, py, pz, cl, sg)         \
     do {                                 \
         if (cnt < cap) {                 \
@@ -776,7 +792,7 @@ static int64_t feature_particles_on_segments(const or_ctx *c, double dx, double 
         }                                \
         cnt++;                           \
     } while (0)
-    for (int64_t l = 0; l < c->nlines; l++) {
+    for (int64_t l = l0; l < l1; l++) {
         int64_t f = c->line_first[l], ns = c->line_nseg[l];
         double L = 0.0;
         for (int64_t s = f; s < f + ns; s++) L += seg_len(c, s);
@@ -1501,7 +1517,10 @@ static void apply_step_partner(or_ctx *c, const double *acc, double amax, const 
         double xn[3];
         int32_t cn;
         int ok = project_point(c, cl, y, cs, xn, &cn);
-        if (ok && (cl == OR_S || cl == OR_F)) ok = partner_ok(partner, surf_rule, xn);
+        /* a feature particle on an intersection curve lies on both surfaces:
+         * no side of the partner to keep */
+        int on_curve = cl == OR_F && cn >= c->nseg_own;
+        if (ok && (cl == OR_S || (cl == OR_F && !on_curve))) ok = partner_ok(partner, surf_rule, xn);
         if (ok && cl == OR_V) ok = partner_ok(partner, vol_rule, xn);
         if (ok) {
             memcpy(Xn + 3 * i, xn, sizeof(xn));
@@ -1560,6 +1579,362 @@ int oracle_relax_step(or_ctx *c, double amax)
     free(c->split_acc);
     c->split_acc = NULL;
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* intersection curve of two bodies: feature lines of a Boolean pair         */
+/* ------------------------------------------------------------------------ */
+/* Where the surfaces of two bodies cross, the result of a Boolean operation
+ * (Sec. 3.2.3) has a crease; the paper does not say whether it carries
+ * feature particles.  Reading: it does, like a feature line (Sec. 3.2.2):
+ * the curve is the union of the segments where a triangle of A crosses a
+ * triangle of B, chained into polylines, and feature particles are placed
+ * along them as along feature lines; they belong to A (the first operand).
+ *
+ * One triangle pair (a, b): the signed distances of a's vertices to b's
+ * plane (unnormalised normal, vertex 0 of b as origin; zero counts as
+ * positive) pick the two edges of a that cross b's plane, and the same for
+ * b against a's plane.  The crossing point of an edge (u < v, global vertex
+ * ids) with the other triangle's plane is u + (v - u) du / (du - dv); it is
+ * named by the key (mesh of the edge, u, v, other triangle), so the two
+ * segments that meet there compute it from the same numbers.  Along the
+ * line of the two planes (direction na x nb) the pair's segment is the
+ * overlap of a's two points and b's two points; it is empty unless the
+ * overlap has positive length.  The ends of the overlap are the segment's
+ * ends, with their keys. */
+typedef struct {
+    int32_t side;      /* 0: an edge of A (other triangle of B), 1: an edge of B */
+    int32_t u, v;      /* edge, u < v */
+    int64_t other;     /* the triangle it crosses */
+} or_ckey;
+
+typedef struct {
+    int64_t a, b;      /* the triangle pair */
+    or_ckey k[2];
+    double p[2][3];
+} or_cseg;
+
+static int ckey_cmp(const or_ckey *x, const or_ckey *y)
+{
+    if (x->side != y->side) return x->side < y->side ? -1 : 1;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    if (x->v != y->v) return x->v < y->v ? -1 : 1;
+    if (x->other != y->other) return x->other < y->other ? -1 : 1;
+    return 0;
+}
+
+/* crossing point of edge (u, v) of mesh (V, T) with the plane (n, o) */
+static void edge_plane_point(const double *V, int32_t u, int32_t v, const double *n, const double *o, double *p)
+{
+    double wu[3], wv[3], e[3];
+    sub3(V + 3 * u, o, wu);
+    sub3(V + 3 * v, o, wv);
+    double du = dot3(n, wu), dv = dot3(n, wv);
+    sub3(V + 3 * v, V + 3 * u, e);
+    double t = du / (du - dv);
+    for (int k = 0; k < 3; k++) p[k] = V[3 * u + k] + e[k] * t;
+}
+
+/* the two edges of triangle t (mesh V, T) whose end points lie on opposite
+ * sides of plane (n, o); returns 0 when all three lie on one side */
+static int crossing_edges(const double *V, const int32_t *T, int64_t t, const double *n, const double *o,
+                          int32_t eu[2], int32_t ev[2])
+{
+    int pos[3];
+    for (int i = 0; i < 3; i++) {
+        double w[3];
+        sub3(V + 3 * T[3 * t + i], o, w);
+        pos[i] = dot3(n, w) >= 0.0;
+    }
+    if (pos[0] == pos[1] && pos[1] == pos[2]) return 0;
+    int m = 0;
+    for (int i = 0; i < 3; i++) {
+        int j = (i + 1) % 3;
+        if (pos[i] != pos[j]) {
+            int32_t x = T[3 * t + i], y = T[3 * t + j];
+            eu[m] = x < y ? x : y;
+            ev[m] = x < y ? y : x;
+            m++;
+        }
+    }
+    return m == 2;
+}
+
+static int tri_pair_segment(const or_ctx *A, int64_t a, const or_ctx *B, int64_t b, or_cseg *out)
+{
+    double na[3], nb[3], e1[3], e2[3];
+    const double *a0 = A->V + 3 * A->T[3 * a], *b0 = B->V + 3 * B->T[3 * b];
+    sub3(A->V + 3 * A->T[3 * a + 1], a0, e1);
+    sub3(A->V + 3 * A->T[3 * a + 2], a0, e2);
+    cross3(e1, e2, na);
+    sub3(B->V + 3 * B->T[3 * b + 1], b0, e1);
+    sub3(B->V + 3 * B->T[3 * b + 2], b0, e2);
+    cross3(e1, e2, nb);
+    int32_t au[2], av[2], bu[2], bv[2];
+    if (!crossing_edges(A->V, A->T, a, nb, b0, au, av)) return 0;
+    if (!crossing_edges(B->V, B->T, b, na, a0, bu, bv)) return 0;
+    double dir[3], pts[4][3], t[4];
+    cross3(na, nb, dir);
+    or_ckey keys[4];
+    for (int i = 0; i < 2; i++) {
+        edge_plane_point(A->V, au[i], av[i], nb, b0, pts[i]);
+        keys[i] = (or_ckey){0, au[i], av[i], b};
+        edge_plane_point(B->V, bu[i], bv[i], na, a0, pts[2 + i]);
+        keys[2 + i] = (or_ckey){1, bu[i], bv[i], a};
+    }
+    for (int i = 0; i < 4; i++) t[i] = dot3(dir, pts[i]);
+    int alo = t[0] <= t[1] ? 0 : 1, ahi = 1 - alo, blo = t[2] <= t[3] ? 2 : 3, bhi = 5 - blo;
+    int lo = t[alo] >= t[blo] ? alo : blo;   /* the later start */
+    int hi = t[ahi] <= t[bhi] ? ahi : bhi;   /* the earlier end */
+    if (!(t[lo] < t[hi])) return 0;
+    out->a = a;
+    out->b = b;
+    out->k[0] = keys[lo];
+    out->k[1] = keys[hi];
+    memcpy(out->p[0], pts[lo], sizeof(double) * 3);
+    memcpy(out->p[1], pts[hi], sizeof(double) * 3);
+    return 1;
+}
+
+typedef struct {
+    or_ckey k;
+    int64_t seg;
+    int end;
+} or_cend;
+
+static int cend_cmp(const void *x, const void *y)
+{
+    const or_cend *p = x, *q = y;
+    int c = ckey_cmp(&p->k, &q->k);
+    if (c) return c;
+    if (p->seg != q->seg) return p->seg < q->seg ? -1 : 1;
+    return p->end - q->end;
+}
+
+static void aabb_of(const or_ctx *c, int64_t t, double *lo, double *hi)
+{
+    for (int k = 0; k < 3; k++) {
+        lo[k] = INFINITY;
+        hi[k] = -INFINITY;
+    }
+    for (int i = 0; i < 3; i++)
+        for (int k = 0; k < 3; k++) {
+            double x = c->V[3 * c->T[3 * t + i] + k];
+            if (x < lo[k]) lo[k] = x;
+            if (x > hi[k]) hi[k] = x;
+        }
+}
+
+/* Chaining, in a fixed order: segments sorted by their triangle pair (a, b);
+ * ends matched by key (a key met by other than two ends stops a chain), then
+ * the ends left free matched by position (see below).
+ * Open chains first: from each segment with a free end, in that order, a
+ * walk from the free end; then loops: from the first unvisited segment, a
+ * walk that leaves it by its end of larger key.  A walk appends the point of
+ * every key it passes (a loop its first point once).  The polylines become
+ * feature lines of A with their points appended to A's vertex arrays
+ * (rounded to FP32), and feature particles are placed along them as along
+ * A's own lines (Sec. 3.2.2: n = ceil(L / dx) pieces, open lines with their
+ * end points as singular points).  Returns the particles added. */
+int64_t oracle_boolean_curve(or_ctx *A, const or_ctx *B)
+{
+    /* the triangle pairs whose boxes overlap (brute force) */
+    double *alo = malloc(sizeof(double) * 3 * A->nt), *ahi = malloc(sizeof(double) * 3 * A->nt);
+    for (int64_t a = 0; a < A->nt; a++) aabb_of(A, a, alo + 3 * a, ahi + 3 * a);
+    int64_t cap = 64, ns = 0;
+    or_cseg *S = malloc(sizeof(or_cseg) * cap);
+    for (int64_t b = 0; b < B->nt; b++) {
+        double lo[3], hi[3];
+        aabb_of(B, b, lo, hi);
+        for (int64_t a = 0; a < A->nt; a++) {
+            int apart = 0;
+            for (int k = 0; k < 3; k++)
+                if (alo[3 * a + k] > hi[k] || ahi[3 * a + k] < lo[k]) apart = 1;
+            if (apart) continue;
+            or_cseg g;
+            if (!tri_pair_segment(A, a, B, b, &g)) continue;
+            if (ns == cap) {
+                cap *= 2;
+                S = realloc(S, sizeof(or_cseg) * cap);
+            }
+            S[ns++] = g;
+        }
+    }
+    free(alo);
+    free(ahi);
+    /* sort by (a, b): the loop above runs b outer, a inner */
+    for (int64_t i = 1; i < ns; i++) {
+        or_cseg x = S[i];
+        int64_t j = i - 1;
+        while (j >= 0 && (S[j].a > x.a || (S[j].a == x.a && S[j].b > x.b))) {
+            S[j + 1] = S[j];
+            j--;
+        }
+        S[j + 1] = x;
+    }
+    /* ends sorted by key: partner[2 s + e] = the other end with the same key */
+    or_cend *E = malloc(sizeof(or_cend) * (2 * ns + 1));
+    for (int64_t i = 0; i < ns; i++)
+        for (int e = 0; e < 2; e++) E[2 * i + e] = (or_cend){S[i].k[e], i, e};
+    qsort(E, (size_t)(2 * ns), sizeof(or_cend), cend_cmp);
+    int64_t *partner = malloc(sizeof(int64_t) * (2 * ns + 1));
+    for (int64_t i = 0; i < 2 * ns; i++) partner[i] = -1;
+    for (int64_t i = 0; i < 2 * ns;) {
+        int64_t j = i;
+        while (j < 2 * ns && ckey_cmp(&E[j].k, &E[i].k) == 0) j++;
+        if (j - i == 2) {
+            partner[2 * E[i].seg + E[i].end] = 2 * E[i + 1].seg + E[i + 1].end;
+            partner[2 * E[i + 1].seg + E[i + 1].end] = 2 * E[i].seg + E[i].end;
+        }
+        i = j;
+    }
+    free(E);
+    /* a point where the curve meets an edge of each mesh at once has two keys
+     * (degenerate, e.g. mirror-symmetric meshes): ends still free are joined
+     * to the first free end (in segment order) within 2^-30 of the largest
+     * extent of A */
+    {
+        double ext = 0.0;
+        for (int k = 0; k < 3; k++) {
+            double lo = INFINITY, hi = -INFINITY;
+            for (int64_t v = 0; v < A->nv; v++) {
+                if (A->V[3 * v + k] < lo) lo = A->V[3 * v + k];
+                if (A->V[3 * v + k] > hi) hi = A->V[3 * v + k];
+            }
+            if (hi - lo > ext) ext = hi - lo;
+        }
+        const double tol = ldexp(ext, -30);
+        for (int64_t i = 0; i < 2 * ns; i++) {
+            if (partner[i] >= 0) continue;
+            for (int64_t j = i + 1; j < 2 * ns; j++) {
+                if (partner[j] >= 0 || j / 2 == i / 2) continue;
+                double w[3];
+                sub3(S[i / 2].p[i % 2], S[j / 2].p[j % 2], w);
+                if (sqrt(dot3(w, w)) <= tol) {
+                    partner[i] = j;
+                    partner[j] = i;
+                    break;
+                }
+            }
+        }
+    }
+    /* walks */
+    char *vis = calloc((size_t)(ns ? ns : 1), 1);
+    int64_t pcap = 64, np = 0;
+    double *P = malloc(sizeof(double) * 3 * pcap);
+    int64_t lcap = 8, nl = 0, *lstart = malloc(sizeof(int64_t) * lcap), *lcount = malloc(sizeof(int64_t) * lcap);
+    int32_t *lclosed = malloc(sizeof(int32_t) * lcap);
+#define PUSH_PT(q)                                              \
+    do {                                                        \
+        if (np == pcap) {                                       \
+            pcap *= 2;                                          \
+            P = realloc(P, sizeof(double) * 3 * pcap);          \
+        }                                                       \
+        memcpy(P + 3 * np, (q), sizeof(double) * 3);           \
+        np++;                                                   \
+    } while (0)
+    for (int pass = 0; pass < 2; pass++)
+        for (int64_t s0 = 0; s0 < ns; s0++) {
+            if (vis[s0]) continue;
+            int e_in;
+            if (pass == 0) {
+                if (partner[2 * s0] >= 0 && partner[2 * s0 + 1] >= 0) continue;
+                e_in = partner[2 * s0] < 0 ? 0 : 1;           /* the free end */
+            } else {
+                e_in = ckey_cmp(&S[s0].k[0], &S[s0].k[1]) < 0 ? 0 : 1;   /* leave by the larger key */
+            }
+            if (nl == lcap) {
+                lcap *= 2;
+                lstart = realloc(lstart, sizeof(int64_t) * lcap);
+                lcount = realloc(lcount, sizeof(int64_t) * lcap);
+                lclosed = realloc(lclosed, sizeof(int32_t) * lcap);
+            }
+            int64_t first = np, seg = s0;
+            int closed = 0;
+            PUSH_PT(S[s0].p[e_in]);
+            for (;;) {
+                vis[seg] = 1;
+                int e_out = 1 - e_in;
+                int64_t nx = partner[2 * seg + e_out];
+                if (nx >= 0 && nx / 2 == s0) {
+                    closed = 1;
+                    break;
+                }
+                PUSH_PT(S[seg].p[e_out]);
+                if (nx < 0 || vis[nx / 2]) break;
+                seg = nx / 2;
+                e_in = (int)(nx % 2);
+            }
+            lstart[nl] = first;
+            lcount[nl] = np - first;
+            lclosed[nl] = closed;
+            nl++;
+        }
+#undef PUSH_PT
+    free(vis);
+    free(partner);
+    free(S);
+    /* the points join A's vertex arrays, rounded to FP32; each polyline a line */
+    int64_t v0 = A->nv_all;
+    A->nv_all += np;
+    A->V = realloc(A->V, sizeof(double) * 3 * (A->nv_all ? A->nv_all : 1));
+    A->Vf = realloc(A->Vf, sizeof(float) * 3 * (A->nv_all ? A->nv_all : 1));
+    for (int64_t i = 0; i < np; i++)
+        for (int k = 0; k < 3; k++) {
+            A->Vf[3 * (v0 + i) + k] = (float)P[3 * i + k];
+            A->V[3 * (v0 + i) + k] = (double)A->Vf[3 * (v0 + i) + k];
+        }
+    free(P);
+    int64_t l_first = A->nlines, nseg_new = 0;
+    for (int64_t l = 0; l < nl; l++) nseg_new += lclosed[l] ? lcount[l] : lcount[l] - 1;
+    A->seg_v = realloc(A->seg_v, sizeof(int32_t) * 2 * (A->nseg + nseg_new + 1));
+    A->seg_line = realloc(A->seg_line, sizeof(int32_t) * (A->nseg + nseg_new + 1));
+    A->line_first = realloc(A->line_first, sizeof(int64_t) * (A->nlines + nl + 1));
+    A->line_nseg = realloc(A->line_nseg, sizeof(int64_t) * (A->nlines + nl + 1));
+    A->line_closed = realloc(A->line_closed, sizeof(int32_t) * (A->nlines + nl + 1));
+    for (int64_t l = 0; l < nl; l++) {
+        int64_t m = lcount[l], nseg_l = lclosed[l] ? m : m - 1, first = A->nseg;
+        for (int64_t q = 0; q < nseg_l; q++) {
+            A->seg_v[2 * A->nseg] = (int32_t)(v0 + lstart[l] + q);
+            A->seg_v[2 * A->nseg + 1] = (int32_t)(v0 + lstart[l] + (q + 1) % m);
+            A->seg_line[A->nseg] = (int32_t)A->nlines;
+            A->nseg++;
+        }
+        A->line_first[A->nlines] = first;
+        A->line_nseg[A->nlines] = nseg_l;
+        A->line_closed[A->nlines] = lclosed[l];
+        A->nlines++;
+    }
+    free(lstart);
+    free(lcount);
+    free(lclosed);
+    /* feature particles along the new lines, appended to A's particles */
+    int64_t nf = feature_particles_of_lines(A, (double)A->dx, l_first, A->nlines, NULL, NULL, NULL, 0);
+    double *fx = malloc(sizeof(double) * 3 * (nf ? nf : 1));
+    int32_t *fc = malloc(sizeof(int32_t) * (nf ? nf : 1)), *fs = malloc(sizeof(int32_t) * (nf ? nf : 1));
+    feature_particles_of_lines(A, (double)A->dx, l_first, A->nlines, fx, fc, fs, nf);
+    A->X = realloc(A->X, sizeof(double) * 3 * (A->n + nf + 1));
+    A->cls = realloc(A->cls, sizeof(int32_t) * (A->n + nf + 1));
+    A->cons = realloc(A->cons, sizeof(int32_t) * (A->n + nf + 1));
+    for (int64_t i = 0; i < nf; i++) {
+        for (int k = 0; k < 3; k++) A->X[3 * (A->n + i) + k] = (double)(float)fx[3 * i + k];
+        A->cls[A->n + i] = fc[i];
+        A->cons[A->n + i] = fs[i];
+    }
+    A->n += nf;
+    free(fx);
+    free(fc);
+    free(fs);
+    return nf;
+}
+
+/* vertex coordinates of every intersection-curve point of A (the points
+ * after its mesh vertices), FP32 */
+int64_t oracle_curve_points(const or_ctx *c, float *out, int64_t cap)
+{
+    int64_t m = c->nv_all - c->nv;
+    if (out) memcpy(out, c->Vf + 3 * c->nv, sizeof(float) * 3 * (size_t)(m < cap ? m : cap));
+    return m;
 }
 
 /* ------------------------------------------------------------------------ */
