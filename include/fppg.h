@@ -190,7 +190,8 @@ int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n);
  * the partner, of a difference outside b (a's) or inside a (b's, the
  * cavity wall), of an intersection inside the partner; volume particles of
  * a difference also stay outside b, of an intersection inside b.  The
- * curve where the surfaces meet gets no feature particles.  *n_a, *n_b
+ * curve where the surfaces meet gets feature particles from
+ * fppg_boolean_curve (below).  *n_a, *n_b
  * (nullable) receive the particle counts left.  Errors: FPPG_ERR_ARG for
  * the same handle twice, an unknown op, different dx / h / feature
  * setting, or a mesh that is not closed and consistently oriented;
@@ -202,6 +203,45 @@ int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n);
 #define FPPG_INTERSECTION 2
 int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_b);
 int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b);
+/* The crease of a Boolean result (Sec. 3.2.3) as a feature line (Sec. 3.2.2):
+ * the curve where a's surface crosses b's becomes feature lines of a, with
+ * feature particles along them appended to a's particles, constraint = the
+ * curve segment.  Call after fppg_boolean(a, b, ...) (either order of the
+ * pair; the lines go to the first argument) and before fppg_batch_create.
+ * Set-up on the host, in FP64 with every operation rounded in the written
+ * order:
+ *   - pairs: every (a-triangle, b-triangle) pair whose closed bounding boxes
+ *     overlap; the side of a vertex against the other triangle's plane
+ *     (unnormalised normal (v1 - v0) x (v2 - v0), origin v0) is d >= 0; the
+ *     two edges of each triangle whose ends lie on different sides cross
+ *     the other plane at u + (v - u) du / (du - dv) (u < v vertex ids), a
+ *     point named by the key (mesh, u, v, other triangle); the pair's
+ *     segment is the overlap of the two triangles' crossing intervals along
+ *     na x nb, kept when of positive length;
+ *   - chains: segments in (a, b) order; ends with the same key join when
+ *     exactly two share it; ends still free join the first free end of
+ *     another segment (in segment, end order) within 2^-30 of a's largest
+ *     bounding-box extent; open chains are walked from the free end of the
+ *     first segment that has one, then loops from their first segment,
+ *     leaving by the end of larger key;
+ *   - the points join a's vertex list (rounded to FP32, after the mesh
+ *     vertices; fppg_get_feature_lines gives the segments' vertex ids and
+ *     fppg_get_curve_points their coordinates), each chain one feature line
+ *     after a's own, with n = ceil(L / dx) feature particles placed as on
+ *     a's own lines (open chains add their end points as singular points).
+ * In the relaxation these particles move along their line and are exempt
+ * from the partner rule: they lie on both surfaces.  *n_added (nullable)
+ * receives the particles added.  Errors: FPPG_ERR_ARG for the same handle
+ * twice or more than 2^31 curve points; FPPG_ERR_STATE when b is not a's
+ * Boolean partner, a has no particles, or a has its curve already;
+ * FPPG_ERR_OOM.  On an error a keeps its own lines (after a failed
+ * particle upload, like fppg_set_particles, no particles).  Extracting
+ * features again drops the curve lines. */
+int fppg_boolean_curve(fppg_ctx *a, fppg_ctx *b, int64_t *n_added);
+/* The intersection-curve points of ctx (FP32 xyz, the vertices after the
+ * mesh's own) into xyz_host (capacity cap points, nullable); *n receives
+ * their number. */
+int fppg_get_curve_points(fppg_ctx *ctx, float *xyz_host, int64_t cap, int64_t *n);
 /* Positions, classes and constraint ids (triangle for S, feature segment for
  * F, -1 otherwise) into caller buffers of capacity cap (each nullable);
  * *n_out receives the particle count.  Synchronises the stream. */

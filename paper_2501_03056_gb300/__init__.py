@@ -101,6 +101,8 @@ def lib():
                 "fppg_batch_set_mobile_classes": [vp, i32],
                 "fppg_union": [vp, vp, P_(i64), P_(i64)],
                 "fppg_boolean": [vp, vp, i32, P_(i64), P_(i64)],
+                "fppg_boolean_curve": [vp, vp, P_(i64)],
+                "fppg_get_curve_points": [vp, P_(f32), i64, P_(i64)],
                 "fppg_batch_phase_ms": [vp, P_(f64)],
                 "fppg_device_sm_count": [P_(i32)],
                 "fppg_debug_fail_allocation": [i64],
@@ -234,6 +236,14 @@ class Body:
         self._chk(lib().fppg_get_feature_lines(self._h, _ptr(nseg, C.c_int64), _ptr(closed, C.c_int32), nl.value,
                                                _ptr(segv, C.c_int32), ns.value, C.byref(nl), C.byref(ns)))
         return nseg[:nl.value], closed[:nl.value], segv[:ns.value]
+
+    def curve_points(self) -> np.ndarray:
+        """Intersection-curve points (fppg_get_curve_points), FP32 [m, 3]."""
+        m = C.c_int64()
+        self._chk(lib().fppg_get_curve_points(self._h, None, 0, C.byref(m)))
+        out = np.zeros((max(m.value, 1), 3), np.float32)
+        self._chk(lib().fppg_get_curve_points(self._h, _ptr(out, C.c_float), m.value, C.byref(m)))
+        return out[:m.value]
 
     def map_particles(self, surface=True, volume=True, features=True, band_cells=0, inner_cells=0) -> int:
         """Replace the particles by the initial set of Sec. 3.2 (on the GPU)."""
@@ -384,6 +394,19 @@ def boolean(a: "Body", b: "Body", op: int) -> tuple[int, int]:
         raise FPPGError(r, msg.decode() if isinstance(msg, bytes) else str(msg))
     a.n, b.n = na.value, nb_.value
     return na.value, nb_.value
+
+
+def boolean_curve(a: "Body", b: "Body") -> int:
+    """Feature lines along the curve where a's surface crosses b's Boolean
+    partner b, with their feature particles appended to a
+    (fppg_boolean_curve); returns the particles added."""
+    n = C.c_int64()
+    r = lib().fppg_boolean_curve(a.handle, b.handle, C.byref(n))
+    if r != OK:
+        msg = lib().fppg_last_error(a.handle) or lib().fppg_last_error(None)
+        raise FPPGError(r, msg.decode() if isinstance(msg, bytes) else str(msg))
+    a.n += n.value
+    return n.value
 
 
 def union(a: "Body", b: "Body") -> tuple[int, int]:

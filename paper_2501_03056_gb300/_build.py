@@ -3,7 +3,9 @@
 Each translation unit is compiled by nvcc in parallel and linked into one
 shared library with the CUDA runtime linked statically.  ``mesh.cu`` (the
 FP64 set-up) is compiled without FMA contraction so that its feature and
-normal arithmetic is evaluated exactly in the written order.
+normal arithmetic is evaluated exactly in the written order; the host parts
+of ``mapping.cu`` and ``curve.cu`` (feature particles, intersection curve)
+are compiled without contraction by the host compiler as well.
 """
 from __future__ import annotations
 
@@ -29,8 +31,9 @@ UNITS = {
     "energy.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
-    "mapping.cu": ["-fmad=false"],
+    "mapping.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
     "union.cu": ["-fmad=false"],
+    "curve.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
 }
 
 

@@ -176,6 +176,7 @@ int fppg_create(const float *verts_host, int64_t nv, const int32_t *tris_host, i
     fppg_ctx *c = new (std::nothrow) fppg_ctx();
     if (!c) return fail_global(FPPG_ERR_OOM, "host allocation failed");
     c->body.verts_host.assign(verts_host, verts_host + 3 * nv);
+    c->body.tris_host.assign(tris_host, tris_host + 3 * nt);
     int r = c->body.build_mesh(verts_host, nv, tris_host, nt, dx, h, c->stream, c->err);
     if (r == 0) r = ctx_group(c);
     if (r != 0) {
@@ -400,6 +401,51 @@ int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_
 
 int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
     return fppg_boolean(a, b, FPPG_UNION, n_a, n_b);
+}
+
+int fppg_boolean_curve(fppg_ctx *a, fppg_ctx *b, int64_t *n_added) {
+    if (!a || !b || a == b) return fail_global(FPPG_ERR_ARG, "the intersection curve needs two different bodies");
+    if (a->partner != b) return fail(a->err, FPPG_ERR_STATE, "the intersection curve follows fppg_boolean on the pair");
+    if (!a->has_particles) return fail(a->err, FPPG_ERR_STATE, "no particles set");
+    Body &bd = a->body;
+    if (bd.nseg > bd.nseg_own) return fail(a->err, FPPG_ERR_STATE, "the intersection curve is there already");
+    const int64_t n = a->n;
+    std::vector<float> xyz(3 * (size_t)n);
+    std::vector<int32_t> cls((size_t)n), cons((size_t)n);
+    int r = fppg_get_particles(a, xyz.data(), cls.data(), cons.data(), n, nullptr);
+    if (r) return r;
+    std::vector<float> fx;
+    std::vector<int32_t> fc, fs;
+    r = bd.add_curve(b->body, fx, fc, fs, a->stream, a->err);
+    if (r) return r == 1 ? FPPG_ERR_ARG : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
+    xyz.insert(xyz.end(), fx.begin(), fx.end());
+    cls.insert(cls.end(), fc.begin(), fc.end());
+    cons.insert(cons.end(), fs.begin(), fs.end());
+    r = fppg_set_particles(a, xyz.data(), cls.data(), (int64_t)cls.size());
+    if (!r) r = fppg_set_constraints(a, cons.data(), (int64_t)cons.size());
+    if (r) {
+        // no curve without its particles: the host lines go back to the
+        // body's own (the device copy only holds more segments than used)
+        const std::string msg = a->err;
+        bd.drop_curve();
+        ctx_group(a);
+        a->err = msg;
+        return r;
+    }
+    if (n_added) *n_added = (int64_t)fc.size();
+    return FPPG_OK;
+}
+
+int fppg_get_curve_points(fppg_ctx *ctx, float *xyz_host, int64_t cap, int64_t *n) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (cap < 0) return fail(ctx->err, FPPG_ERR_ARG, "negative capacity");
+    const Body &b = ctx->body;
+    const int64_t m = (int64_t)b.verts_host.size() / 3 - b.nv;
+    if (n) *n = m;
+    if (xyz_host)
+        std::copy(b.verts_host.begin() + 3 * (size_t)b.nv, b.verts_host.begin() + 3 * (size_t)(b.nv + std::min(cap, m)),
+                  xyz_host);
+    return FPPG_OK;
 }
 
 int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_t *cons_host, int64_t cap,

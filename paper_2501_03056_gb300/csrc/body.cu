@@ -13,6 +13,7 @@ namespace fppg {
 // through degree-2 vertices; then closed loops from the lowest uncoloured
 // edge.  Edges are coloured as they are walked.
 void Body::build_lines() {
+    verts_host.resize(3 * (size_t)nv);   // intersection-curve lines are rebuilt by their own call
     const int64_t m = (int64_t)fe.size() / 2;
     std::vector<int32_t> deg(nv, 0);
     for (int64_t e = 0; e < m; e++) {
@@ -86,6 +87,7 @@ void Body::build_lines() {
         line_closed.push_back(closed);
     }
     nseg = (int)(seg_v.size() / 2);
+    nseg_own = nseg;
     nlines = (int)line_first.size();
     has_features = true;
 }
@@ -98,14 +100,11 @@ void Body::drop_features() {
     line_nseg.clear();
     line_closed.clear();
     seg_v.clear();
-    nseg = nlines = 0;
+    nseg = nlines = nseg_own = 0;
+    verts_host.resize(3 * (size_t)nv);   // curve points go with the lines
 }
 
-int Body::upload_lines(cudaStream_t s, std::string &err) {
-    if (seg) cudaFree(seg);
-    if (lines) cudaFree(lines);
-    seg = nullptr;
-    lines = nullptr;
+int Body::upload_lines(cudaStream_t s, std::string &err, bool keep_on_failure) {
     std::vector<float4> hs(3 * (size_t)std::max(nseg, 1));
     std::vector<int2> hl((size_t)std::max(nlines, 1));
     for (int l = 0; l < nlines; l++) {
@@ -125,17 +124,26 @@ int Body::upload_lines(cudaStream_t s, std::string &err) {
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    if (dev_malloc(&seg, sizeof(float4) * hs.size()) != cudaSuccess ||
-        dev_malloc(&lines, sizeof(int2) * hl.size()) != cudaSuccess) {
+    float4 *nseg_d = nullptr;
+    int2 *nlines_d = nullptr;
+    if (dev_malloc(&nseg_d, sizeof(float4) * hs.size()) != cudaSuccess ||
+        dev_malloc(&nlines_d, sizeof(int2) * hl.size()) != cudaSuccess) {
+        if (nseg_d) cudaFree(nseg_d);
+        if (nlines_d) cudaFree(nlines_d);
+        err = "feature lines: out of device memory";
+        if (keep_on_failure) return 3;   // the caller restores the host lines the old buffers hold
         // no half-built feature set: the body is left without features
         if (seg) cudaFree(seg);
         if (lines) cudaFree(lines);
         seg = nullptr;
         lines = nullptr;
         drop_features();
-        err = "feature lines: out of device memory";
         return 3;
     }
+    if (seg) cudaFree(seg);
+    if (lines) cudaFree(lines);
+    seg = nseg_d;
+    lines = nlines_d;
     cudaMemcpyAsync(seg, hs.data(), sizeof(float4) * hs.size(), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(lines, hl.data(), sizeof(int2) * hl.size(), cudaMemcpyHostToDevice, s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -185,6 +193,7 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.nt = b.nt;
     A.nv = b.nv;
     A.nseg = b.nseg;
+    A.curve_seg0 = b.nseg_own;
     A.nlines = b.nlines;
     A.fixed_features = fixed_features;
     const double h = (double)b.h;

@@ -57,17 +57,27 @@ struct Body {
     std::vector<int64_t> line_first, line_nseg;
     std::vector<int32_t> line_closed;
     std::vector<int32_t> seg_v;        // [nseg][2]
-    std::vector<float> verts_host;     // FP32 copy of the mesh vertices
+    std::vector<float> verts_host;     // FP32 mesh vertices, then the intersection-curve points
+    std::vector<int32_t> tris_host;    // the triangles
     float4 *seg = nullptr;
     int2 *lines = nullptr;
     int nseg = 0, nlines = 0;
+    int nseg_own = 0;                  // segments of the body's own lines; intersection-curve ones follow
+    bool own_has_features = false;     // has_features before the intersection curve was added
 
-    void feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg) const;
+    // feature particles of lines l0 .. l1 - 1 (l1 < 0: to the last line)
+    void feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg,
+                           int l0 = 0, int l1 = -1) const;
+    void drop_curve();       // back to the body's own lines (host side)
+    int add_curve(const Body &other, std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg,
+                  cudaStream_t s, std::string &err);
     int build_mesh(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,
                    cudaStream_t s, std::string &err);
     int extract_features(float deg, cudaStream_t s, std::string &err);
     void build_lines();
-    int upload_lines(cudaStream_t s, std::string &err);
+    // upload of the segments and lines; on a failed allocation the body is
+    // left without features, or (keep_on_failure) with its old device copy
+    int upload_lines(cudaStream_t s, std::string &err, bool keep_on_failure = false);
     void drop_features();   // forget every feature edge, line and segment
     void free_mesh();
     ~Body() { free_mesh(); }

@@ -74,6 +74,7 @@ struct AsmParams {
     int nv;
     int seg_off;           // offset of its feature segments (ids are local)
     int nseg;
+    int curve_seg0;        // first intersection-curve segment (on both surfaces: no partner rule)
     int line_off;
     int nlines;
     int fixed_features;

@@ -230,8 +230,10 @@ inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t
 // points once (class P); loops carry n points.  seg gets the segment each
 // feature particle was placed on (-1 for singular points), so its first
 // step already projects onto its own line.
-void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg) const {
-    std::vector<char> done(nv, 0);
+void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg, int l0,
+                             int l1) const {
+    std::vector<char> done(verts_host.size() / 3, 0);
+    if (l1 < 0) l1 = nlines;
     auto seglen = [&](int64_t q) {
         const float *a = &verts_host[3 * (size_t)seg_v[2 * q]], *b = &verts_host[3 * (size_t)seg_v[2 * q + 1]];
         const double e0 = (double)b[0] - a[0], e1 = (double)b[1] - a[1], e2 = (double)b[2] - a[2];
@@ -244,7 +246,7 @@ void Body::feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls,
         cls.push_back(c);
         seg.push_back((int32_t)q);
     };
-    for (int l = 0; l < nlines; l++) {
+    for (int l = l0; l < l1; l++) {
         const int64_t f = line_first[l], ns = line_nseg[l];
         double L = 0.0;
         for (int64_t q = f; q < f + ns; q++) L += seglen(q);

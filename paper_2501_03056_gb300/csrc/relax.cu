@@ -884,7 +884,9 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             int cn;
             if (project_feature(M, A, y, c, x, cn)) {
                 bool near_partner = false;
-                if (A.partner >= 0 && A.partner_surf != 0) {
+                // (a particle on the intersection curve lies on both
+                // surfaces: no partner rule)
+                if (A.partner >= 0 && A.partner_surf != 0 && cn < A.curve_seg0) {
                     // the partner's triangles within reach: the search tests
                     // the partner rule on the projection
                     const AsmParams &Q = P[A.partner];
@@ -1009,7 +1011,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             ok = warp_volume_inside(M, A, y, buf, clear);
         }
         // Boolean operations: the partner rule of the particle's class
-        if (ok && A.partner >= 0)
+        if (ok && A.partner >= 0 && !(cls == kClsF && tri >= A.curve_seg0))
             ok = warp_partner_ok(M, P[A.partner], cls == kClsV ? A.partner_vol : A.partner_surf, x, buf);
         if (ok && lane == 0) {
             const uint32_t i = id_s[it.x];
@@ -1166,7 +1168,7 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
             } else {
                 ok = thread_closest_sign(M, A, y, clear) != 0;
             }
-            if (ok && A.partner >= 0)
+            if (ok && A.partner >= 0 && !(cls == kClsF && tri >= A.curve_seg0))
                 ok = thread_partner_ok(M, P[A.partner], cls == kClsV ? A.partner_vol : A.partner_surf, x);
             if (ok) {
                 pos[i] = make_float4(x.x, x.y, x.z, p.w);
