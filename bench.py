@@ -468,6 +468,36 @@ def main():
                               "particles_per_s": gn / (t3 - t2), "timer": "host wall clock around synchronised calls"}
         gb.close()
 
+        # ---- the paper's sphere at ~1e8 particles: generation and relaxation --
+        sa = W.sphere_1e8_workload()[0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sb = pkg.Body(sa.verts, sa.tris, sa.dx, sa.h, stream=stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sb.extract_features(sa.dihedral_deg)
+        sn = sb.map_particles(**sa.meta["generate"])
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        sbatch = pkg.Batch([sb], stream=stream)
+        tu = H["tuned"] or {}
+        if "force_variant" in tu:       # the headline's tuned configuration (no trials at this size)
+            sbatch.configure(tu["force_variant"], tu["force_block"], tu["search_ctas_per_sm"])
+            sbatch.set_incremental(bool(tu.get("incremental_order", 0)))
+        sbatch.set_graph_iters(G)
+        sms_1e8 = timed(lambda: sbatch.relax(G, use_graph=True), sbatch.load, 2, 1)
+        line["scale_1e8"] = {
+            "workload": f"sphere 1x1x1 (icosphere level 7, {len(sa.tris)} triangles), dx={sa.dx:g}, surface + every "
+                        "interior cell (Sec. 3.2)",
+            "particles": sn, "mesh_build_ms": 1e3 * (t1 - t0), "features_and_map_ms": 1e3 * (t2 - t1),
+            "generated_particles_per_s": sn / (t2 - t1),
+            "relax": {"iterations_per_step": G, "steps": 2, "ms_per_step": sum(sms_1e8) / 2,
+                      "value": sn * G * 2 / (sum(sms_1e8) / 1e3), "unit": "particle-iterations/s",
+                      "configuration": "the headline's autotuned one"},
+            "timer": "generation: host wall clock around synchronised calls; relaxation: CUDA events"}
+        sbatch.close()
+        sb.close()
+
         # ---- energy (A8): energy-descent relaxation and the backward ------------
         for b, a in zip(st_bodies, st_asm):
             b.set_particles(a.xyz, a.cls)

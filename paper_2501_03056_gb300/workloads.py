@@ -702,3 +702,15 @@ def vehicle_workload(dx: float = 0.0068, spacing: float = 0.021) -> list[Assembl
     dxf = float(np.float32(dx))
     return [Assembly("vehicle", v, t, dxf, smoothing_length(dx), None, None, 30.0,
                      {"n_iter": 1000, "generate": {"band_cells": 0, "inner_cells": 0}})]
+
+
+def sphere_1e8_workload(dx: float = 0.00175, level: int = 7) -> list[Assembly]:
+    """The sphere of the paper's scaling table (1 x 1 x 1, Table
+    tab-generate) at about 10^8 particles: an icosphere of level 7 (r = 0.5,
+    327,680 triangles, edges ~2.7 dx) with surface, feature and every
+    interior cell generated by Sec. 3.2 at dx = 0.00175 (about 9.8e7 volume
+    and 1.0e6 surface particles)."""
+    v, t = icosphere_mesh(level, 0.5)
+    dxf = float(np.float32(dx))
+    return [Assembly("sphere_1e8", v, t, dxf, smoothing_length(dx), None, None, 30.0,
+                     {"n_iter": 50, "generate": {"band_cells": 0, "inner_cells": 0}})]

@@ -194,3 +194,27 @@ def test_vehicle_shell_at_full_size():
     o.relax(1)
     err = np.abs(b.get_particles()[0].astype(np.float64) - o.get_particles()[0]).max(axis=1) / a.dx
     assert (err < 1e-4).mean() > 0.9999 and err.max() < 1.3 / 16.0
+
+
+def test_paper_sphere_generated_at_1e8_particles():
+    # the sphere of the paper's scaling table (1 x 1 x 1) at ~1e8 particles:
+    # the whole generation against the oracle's, as on the vehicle shell
+    a = W.sphere_1e8_workload()[0]
+    o = O.Oracle(a.verts, a.tris, a.dx, a.h)
+    o.extract_features(a.dihedral_deg)
+    x, c, _ = o.map_particles()
+    assert 9.5e7 < len(x) < 1.05e8
+    b = pkg.Body(a.verts, a.tris, a.dx, a.h)
+    b.extract_features(a.dihedral_deg)
+    n = b.map_particles(**a.meta["generate"])
+    gx, gc, gcons = b.get_particles()
+    assert n == len(gx)
+    vo, vg = c == W.CLS_V, gc == W.CLS_V
+    assert np.array_equal(gx[vg], x[vo].astype(np.float32))          # ~9.7e7 volume particles, exact
+    so, sg = x[c == W.CLS_S], gx[gc == W.CLS_S].astype(np.float64)
+    assert abs(len(so) - len(sg)) <= 1e-5 * len(so)
+    from scipy.spatial import cKDTree
+    d, _ = cKDTree(so).query(sg)
+    assert (d < 4e-6).mean() > 1 - 1e-5
+    # every surface particle is constrained to a triangle of the mesh
+    assert np.all((gcons[gc == W.CLS_S] >= 0) & (gcons[gc == W.CLS_S] < len(a.tris)))
