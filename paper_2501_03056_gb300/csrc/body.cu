@@ -333,7 +333,7 @@ int Group::alloc_particles_once(int64_t N, std::string &err) {
     CKA(cudaMemset(g.cert, 0, sizeof(float4) * n1));
     CKA(dev_malloc(&g.acc_s, sizeof(float4) * n1));
     CKA(dev_malloc(&g.coef_s, sizeof(float) * (n1 + 1)));
-    CKA(dev_malloc(&g.work, sizeof(int4) * n1));
+    CKA(dev_malloc(&g.work, (sizeof(int4) + sizeof(uint2)) * n1));   // queue entries, then their ranges
     if (!g.work_count) {
         CKA(dev_malloc(&g.work_count, 2 * sizeof(uint32_t)));
         CKA(cudaMemset(g.work_count, 0, 2 * sizeof(uint32_t)));

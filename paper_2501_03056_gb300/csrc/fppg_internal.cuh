@@ -152,7 +152,8 @@ struct DevGroup {
     uint32_t *scan_tmp_n = nullptr; // scan_tmp_elems(N) entries
     uint32_t *amax = nullptr;
     uint32_t *maxdisp = nullptr;
-    int4 *work = nullptr;          // search queue {key slot, trial point}, N entries
+    int4 *work = nullptr;          // search queue {key slot, trial point}, N entries, then N uint2
+                                   // candidate-list ranges (queue_ranges)
     uint32_t *work_count = nullptr; // [0] entries from the front (S, F), [1] from the back (V)
     uint32_t *hist = nullptr;  // kMaxDigits * n_tiles
     uint32_t *totals = nullptr; // kMaxDigits
@@ -169,6 +170,10 @@ struct DevGroup {
     // energy scratch
     float *coef_s = nullptr;
 };
+
+// the candidate-list range of each search-queue entry, stored after the
+// queue's N int4 entries in the same allocation
+inline uint2 *queue_ranges(const DevGroup &d) { return reinterpret_cast<uint2 *>(d.work + d.N); }
 
 // ---- small device helpers ------------------------------------------------
 // the class is stored one-hot in the low byte of w, so "does class c act on

@@ -244,11 +244,28 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint32_t *__restr
         else hi = mid;
     }
     int i = lo, j = dt - lo;
-    for (int q = 0; q < kMergeItems && dt + q < n; q++) {
-        const bool take_u = j >= nc || (i < nu && kv_less(sk[i], si[i], sk[nu + j], si[nu + j]));
-        const int src = take_u ? i++ : nu + j++;
-        out_key[d0 + dt + q] = sk[src];
-        out_id[d0 + dt + q] = si[src];
+    uint32_t rk[kMergeItems], ri[kMergeItems];
+#pragma unroll
+    for (int q = 0; q < kMergeItems; q++) {
+        if (dt + q < n) {
+            const bool take_u = j >= nc || (i < nu && kv_less(sk[i], si[i], sk[nu + j], si[nu + j]));
+            const int src = take_u ? i++ : nu + j++;
+            rk[q] = sk[src];
+            ri[q] = si[src];
+        }
+    }
+    // the tile's outputs back through shared memory, then stored coalesced
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kMergeItems; q++)
+        if (dt + q < n) {
+            sk[dt + q] = rk[q];
+            si[dt + q] = ri[q];
+        }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n; q += kMergeThreads) {
+        out_key[d0 + q] = sk[q];
+        out_id[d0 + q] = si[q];
     }
 }
 
@@ -651,28 +668,44 @@ __device__ inline bool surface_candidate(const MeshView &M, const AsmParams &A, 
 // list (built with the mesh: the distinct triangles of the 27 cells): 1 with
 // [beg, end) into M.cand; 2 when the list was too long to build (probe the
 // cells); 0 when no triangle lies in the 27 cells.  Warp-uniform.
-__device__ inline int cell_candidates(const MeshView &M, const AsmParams &A, float3 y, uint32_t &beg,
-                                      uint32_t &end) {
-    const uint32_t c = tri_key(A, cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]),
-                               cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]),
-                               cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]));
+// The same as a range of triangle cell c: [beg, end) into M.cand, (0, 0)
+// for no triangle, (kProbeCells, kProbeCells) for a list too long to build.
+// The step computes it for every particle it queues, so that the search
+// starts from the list instead of the chain bitmap -> rank -> list start.
+constexpr uint32_t kProbeCells = 0xffffffffu;
+
+__device__ inline uint2 cand_range(const MeshView &M, const AsmParams &A, uint32_t c) {
     const uint32_t w = M.occ[A.dil_off + (c >> 5)];
-    if (!((w >> (c & 31u)) & 1u)) return 0;
+    if (!((w >> (c & 31u)) & 1u)) return make_uint2(0u, 0u);
     const uint32_t r = M.drank[A.drank_off + (c >> 5)] + __popc(w & ((1u << (c & 31u)) - 1u));
     const uint32_t o0 = M.coff[A.coff_off + r], o1 = M.coff[A.coff_off + r + 1];
-    if (o0 >> 31) return 2;
-    beg = A.cand_off + o0;
-    end = A.cand_off + (o1 & 0x7fffffffu);
+    if (o0 >> 31) return make_uint2(kProbeCells, kProbeCells);
+    return make_uint2(A.cand_off + o0, A.cand_off + (o1 & 0x7fffffffu));
+}
+
+__device__ inline uint32_t tri_cell_of(const AsmParams &A, float3 y) {
+    return tri_key(A, cell_coord(y.x, A.tg_o[0], A.tg_inv, A.tg_n[0]), cell_coord(y.y, A.tg_o[1], A.tg_inv, A.tg_n[1]),
+                   cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]));
+}
+
+// pre: the range of y's cell when the caller has it (nullptr: look it up)
+__device__ inline int cell_candidates(const MeshView &M, const AsmParams &A, float3 y, uint32_t &beg, uint32_t &end,
+                                      const uint2 *pre = nullptr) {
+    const uint2 r = pre ? *pre : cand_range(M, A, tri_cell_of(A, y));
+    if (r.x == kProbeCells) return 2;
+    if (r.y <= r.x) return 0;
+    beg = r.x;
+    end = r.y;
     return 1;
 }
 
 // every candidate triangle of the 27 cells around y, spread over the lanes
 template <typename Test>
 __device__ inline void for_27_candidates(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf,
-                                         Test &&test) {
+                                         Test &&test, const uint2 *pre = nullptr) {
     const int lane = threadIdx.x & 31;
     uint32_t beg = 0, end = 0;
-    const int kind = cell_candidates(M, A, y, beg, end);
+    const int kind = cell_candidates(M, A, y, beg, end, pre);
     if (kind == 1) {
         for (uint32_t q = beg + lane; q < end; q += 32) test(M.cand[q]);
     } else if (kind == 2) {
@@ -682,7 +715,7 @@ __device__ inline void for_27_candidates(const MeshView &M, const AsmParams &A, 
 }
 
 __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist, int32_t *buf,
-                                    bool own_cell = false) {
+                                    bool own_cell = false, const uint2 *pre = nullptr) {
     const int lane = threadIdx.x & 31;
     float best = FLT_MAX;
     int bt = 0x7fffffff;
@@ -703,7 +736,7 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
         if (lane != 13) r = CellRange{0u, 0u};
         for_candidates(M, r, buf, test);
     } else {
-        for_27_candidates(M, A, y, buf, test);
+        for_27_candidates(M, A, y, buf, test, pre);
     }
     float v = best;
     int t = bt;
@@ -719,7 +752,7 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
 // cascade of Sec. 3.3.3 (still on triangle c: stay; else the closest
 // projectable one of y's own cell; else over the 27 cells).  -1: revert.
 __device__ int warp_surface_choice(const MeshView &M, const AsmParams &A, float3 y, int c, float &dist,
-                                   int32_t *buf) {
+                                   int32_t *buf, const uint2 *pre = nullptr) {
     if (A.cascade) {
         if (c >= 0 && c < A.nt) {
             float d = 0.f;
@@ -732,7 +765,7 @@ __device__ int warp_surface_choice(const MeshView &M, const AsmParams &A, float3
         const int t = warp_project_surface(M, A, y, dist, buf, true);
         if (t >= 0) return t;
     }
-    return warp_project_surface(M, A, y, dist, buf);
+    return warp_project_surface(M, A, y, dist, buf, false, pre);
 }
 
 // distance from y to the faces of the 3 x 3 x 3 triangle-cell block around
@@ -754,7 +787,8 @@ __device__ inline float block_margin(const AsmParams &A, float3 y) {
 // sign of the angle-weighted pseudonormal): 1 inside, 0 outside, -1 when no
 // triangle lies in range.  *clear gets a lower bound of the distance from y
 // to the surface, valid when inside.
-__device__ int warp_closest_sign(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear) {
+__device__ int warp_closest_sign(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf, float &clear,
+                                 const uint2 *pre = nullptr) {
     const int lane = threadIdx.x & 31;
     float best = FLT_MAX;
     int bt = 0x7fffffff, breg = 0;
@@ -773,7 +807,7 @@ __device__ int warp_closest_sign(const MeshView &M, const AsmParams &A, float3 y
             breg = reg;
             bcp = cp;
         }
-    });
+    }, pre);
     float v = best;
     int t = bt;
     warp_argmin(v, t);
@@ -794,8 +828,8 @@ __device__ int warp_closest_sign(const MeshView &M, const AsmParams &A, float3 y
 // Volume test of a particle of the body: the closest-feature sign, inside
 // when no triangle is in range (a step is below a cell)
 __device__ inline bool warp_volume_inside(const MeshView &M, const AsmParams &A, float3 y, int32_t *buf,
-                                          float &clear) {
-    return warp_closest_sign(M, A, y, buf, clear) != 0;
+                                          float &clear, const uint2 *pre = nullptr) {
+    return warp_closest_sign(M, A, y, buf, clear, pre) != 0;
 }
 
 // Boolean partner rule (1 stay outside, 2 stay inside, 0 none) for point x:
@@ -852,8 +886,8 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
                                               const AsmParams *__restrict__ P, const uint32_t *__restrict__ amax,
                                               float4 *__restrict__ pos, int32_t *__restrict__ cons, MeshView M,
                                               uint32_t *__restrict__ maxdisp, int4 *__restrict__ work,
-                                              uint32_t *__restrict__ work_count, const float4 *__restrict__ cert,
-                                              const int32_t *__restrict__ cons_s) {
+                                              uint2 *__restrict__ work_r, uint32_t *__restrict__ work_count,
+                                              const float4 *__restrict__ cert, const int32_t *__restrict__ cons_s) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -862,6 +896,7 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
     const AsmParams &A = P[b];
     float disp = 0.f;
     bool queue = false;
+    uint2 rng = make_uint2(0u, 0u);   // candidate list of the trial point's triangle cell
     float3 y = f3(p);
     if (active && is_mobile(cls, A) && !is_ghost(p.w)) {
         const uint32_t i = id_s[k];
@@ -928,6 +963,7 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
                 disp = sqrtf(dot3(dr, dr));
             } else if (near_partner || test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
                 queue = true;
+                rng = cand_range(M, A, tri_key(A, cx, cy, cz));
             } else if (cls == kClsV) {       // nothing near: inside, accept
                 pos[i] = make_float4(y.x, y.y, y.z, p.w);
                 disp = sqrtf(dot3(dr, dr));
@@ -949,8 +985,16 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
         bs = __shfl_sync(0xffffffffu, bs, ls);
         bv = __shfl_sync(0xffffffffu, bv, lv);
         const int4 it = make_int4((int)k, __float_as_int(y.x), __float_as_int(y.y), __float_as_int(y.z));
-        if (qs) work[bs + __popc(ms & lanemask_lt())] = it;
-        if (qv) work[N - 1 - (int64_t)(bv + __popc(mv & lanemask_lt()))] = it;
+        if (qs) {
+            const uint32_t q = bs + __popc(ms & lanemask_lt());
+            work[q] = it;
+            work_r[q] = rng;
+        }
+        if (qv) {
+            const int64_t q = N - 1 - (int64_t)(bv + __popc(mv & lanemask_lt()));
+            work[q] = it;
+            work_r[q] = rng;
+        }
     }
     __shared__ int s_lab[TPB / 32];
     __shared__ uint32_t s_max[TPB / 32];
@@ -959,9 +1003,10 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
 
 // entry e of the two-ended search queue: the nf front entries first, then
 // the back ones from slot N - 1 downwards
-__device__ inline int4 queue_entry(const int4 *__restrict__ work, uint32_t nf, int64_t N, uint32_t e) {
-    return e < nf ? work[e] : work[N - 1 - (int64_t)(e - nf)];
+__device__ inline int64_t queue_slot(uint32_t nf, int64_t N, uint32_t e) {
+    return e < nf ? (int64_t)e : N - 1 - (int64_t)(e - nf);
 }
+
 
 // k_search: one warp per queued particle (grid-stride over the queue):
 // surface particles go to the closest projectable triangle or revert,
@@ -971,6 +1016,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
                                                 const AsmParams *__restrict__ P, float4 *__restrict__ pos,
                                                 int32_t *__restrict__ cons, MeshView M,
                                                 uint32_t *__restrict__ maxdisp, const int4 *__restrict__ work,
+                                                const uint2 *__restrict__ work_r,
                                                 const uint32_t *__restrict__ work_count, int64_t N,
                                                 float4 *__restrict__ cert) {
     __shared__ int32_t sbuf[TPB / 32][kSearchBuf];
@@ -983,7 +1029,9 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
     int run_b = -1;
     uint32_t run = 0u;
     for (uint32_t e = (blockIdx.x * TPB + threadIdx.x) / 32; e < n; e += warps) {
-        const int4 it = queue_entry(work, nf, N, e);
+        const int64_t qs = queue_slot(nf, N, e);
+        const int4 it = work[qs];
+        const uint2 rng = work_r[qs];
         const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
         const float4 p = pos_s[it.x];
         const int cls = cls_of(p.w), b = body_of(p.w);
@@ -994,7 +1042,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
         bool ok;
         if (cls == kClsS) {
             float d;
-            tri = warp_surface_choice(M, A, y, A.cascade ? cons[id_s[it.x]] : -1, d, buf);
+            tri = warp_surface_choice(M, A, y, A.cascade ? cons[id_s[it.x]] : -1, d, buf, &rng);
             ok = tri >= 0;
             if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
         } else if (cls == kClsF) {
@@ -1008,7 +1056,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             tri = __shfl_sync(0xffffffffu, cn, 0);
             ok = okf != 0;
         } else {
-            ok = warp_volume_inside(M, A, y, buf, clear);
+            ok = warp_volume_inside(M, A, y, buf, clear, &rng);
         }
         // Boolean operations: the partner rule of the particle's class
         if (ok && A.partner >= 0 && !(cls == kClsF && tri >= A.curve_seg0))
@@ -1038,9 +1086,10 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
 
 // every candidate triangle of the 27 cells around y, one after another
 template <typename Test>
-__device__ inline void each_27_candidate(const MeshView &M, const AsmParams &A, float3 y, Test &&test) {
+__device__ inline void each_27_candidate(const MeshView &M, const AsmParams &A, float3 y, Test &&test,
+                                         const uint2 *pre = nullptr) {
     uint32_t beg = 0, end = 0;
-    const int kind = cell_candidates(M, A, y, beg, end);
+    const int kind = cell_candidates(M, A, y, beg, end, pre);
     if (kind == 1) {
         for (uint32_t q = beg; q < end; q++) test(M.cand[q]);
     } else if (kind == 2) {
@@ -1052,7 +1101,7 @@ __device__ inline void each_27_candidate(const MeshView &M, const AsmParams &A, 
 }
 
 __device__ int thread_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist,
-                                      bool own_cell = false) {
+                                      bool own_cell = false, const uint2 *pre = nullptr) {
     float best = FLT_MAX, bd = 0.f;
     int bt = 0x7fffffff;
     auto test = [&](int t) {
@@ -1069,13 +1118,14 @@ __device__ int thread_project_surface(const MeshView &M, const AsmParams &A, flo
         const CellRange r = lane_cell(M, A, y, 13);   // the centre cell
         for (uint32_t e = r.beg; e < r.beg + r.len; e++) test(M.tlist[e]);
     } else {
-        each_27_candidate(M, A, y, test);
+        each_27_candidate(M, A, y, test, pre);
     }
     dist = bd;
     return bt == 0x7fffffff ? -1 : bt;
 }
 
-__device__ int thread_surface_choice(const MeshView &M, const AsmParams &A, float3 y, int c, float &dist) {
+__device__ int thread_surface_choice(const MeshView &M, const AsmParams &A, float3 y, int c, float &dist,
+                                     const uint2 *pre = nullptr) {
     if (A.cascade) {
         if (c >= 0 && c < A.nt) {
             float d = 0.f;
@@ -1087,10 +1137,11 @@ __device__ int thread_surface_choice(const MeshView &M, const AsmParams &A, floa
         const int t = thread_project_surface(M, A, y, dist, true);
         if (t >= 0) return t;
     }
-    return thread_project_surface(M, A, y, dist);
+    return thread_project_surface(M, A, y, dist, false, pre);
 }
 
-__device__ int thread_closest_sign(const MeshView &M, const AsmParams &A, float3 y, float &clear) {
+__device__ int thread_closest_sign(const MeshView &M, const AsmParams &A, float3 y, float &clear,
+                                   const uint2 *pre = nullptr) {
     float best = FLT_MAX;
     int bt = 0x7fffffff, breg = 0;
     float3 bcp = make_float3(0.f, 0.f, 0.f);
@@ -1108,7 +1159,7 @@ __device__ int thread_closest_sign(const MeshView &M, const AsmParams &A, float3
             breg = reg;
             bcp = cp;
         }
-    });
+    }, pre);
     const float blk = block_margin(A, y);
     clear = fmaxf(fminf(bt == 0x7fffffff ? FLT_MAX : sqrtf(best), blk) * (1.f - 0x1p-10f) - A.dx * 0x1p-16f, 0.f);
     if (bt == 0x7fffffff) return -1;
@@ -1132,6 +1183,7 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
                                                        int32_t *__restrict__ cons, MeshView M,
                                                        uint32_t *__restrict__ maxdisp,
                                                        const int4 *__restrict__ work,
+                                                       const uint2 *__restrict__ work_r,
                                                        const uint32_t *__restrict__ work_count, int64_t N,
                                                        float4 *__restrict__ cert) {
     const uint32_t nf = work_count[0], n = nf + work_count[1];
@@ -1145,7 +1197,9 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
         int b = 0;
         float disp = 0.f;
         if (e < n) {
-            const int4 it = queue_entry(work, nf, N, e);
+            const int64_t qs = queue_slot(nf, N, e);
+            const int4 it = work[qs];
+            const uint2 rng = work_r[qs];
             const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
             const float4 p = pos_s[it.x];
             const int cls = cls_of(p.w);
@@ -1158,7 +1212,7 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
             bool ok;
             if (cls == kClsS) {
                 float d;
-                tri = thread_surface_choice(M, A, y, A.cascade ? cons[i] : -1, d);
+                tri = thread_surface_choice(M, A, y, A.cascade ? cons[i] : -1, d, &rng);
                 ok = tri >= 0;
                 if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
             } else if (cls == kClsF) {
@@ -1166,7 +1220,7 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
                 ok = project_feature(M, A, y, cons[i], x, cn);
                 tri = cn;
             } else {
-                ok = thread_closest_sign(M, A, y, clear) != 0;
+                ok = thread_closest_sign(M, A, y, clear, &rng) != 0;
             }
             if (ok && A.partner >= 0 && !(cls == kClsF && tri >= A.curve_seg0))
                 ok = thread_partner_ok(M, P[A.partner], cls == kClsV ? A.partner_vol : A.partner_surf, x);
@@ -1389,14 +1443,15 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     else forces(g, s, count_dbg);
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 2], s, flags);
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
-                                         d.maxdisp, d.work, d.work_count, d.cert, d.cons_s);
+                                         d.maxdisp, d.work, queue_ranges(d), d.work_count, d.cert, d.cons_s);
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
     if (g.search_thread)
         k_search_thread<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh,
-                                                        d.maxdisp, d.work, d.work_count, d.N, d.cert);
+                                                        d.maxdisp, d.work, queue_ranges(d), d.work_count, d.N,
+                                                        d.cert);
     else
         k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp,
-                                                 d.work, d.work_count, d.N, d.cert);
+                                                 d.work, queue_ranges(d), d.work_count, d.N, d.cert);
     if (timed) {
         cudaEventRecordWithFlags(g.ev[g.ev_used + 4], s, flags);
         g.ev_used += kPhaseEvents;
@@ -1407,13 +1462,14 @@ void step_and_project(Group &g, cudaStream_t s, int buf) {
     DevGroup &d = g.d;
     if (d.N == 0) return;
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
-                                         d.maxdisp, d.work, d.work_count, d.cert, d.cons_s);
+                                         d.maxdisp, d.work, queue_ranges(d), d.work_count, d.cert, d.cons_s);
     if (g.search_thread)
         k_search_thread<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh,
-                                                        d.maxdisp, d.work, d.work_count, d.N, d.cert);
+                                                        d.maxdisp, d.work, queue_ranges(d), d.work_count, d.N,
+                                                        d.cert);
     else
         k_search<<<g.search_blocks, TPB, 0, s>>>(d.pos_s, d.id[buf], d.params, d.pos, d.cons, g.mesh, d.maxdisp,
-                                                 d.work, d.work_count, d.N, d.cert);
+                                                 d.work, queue_ranges(d), d.work_count, d.N, d.cert);
 }
 
 namespace {
