@@ -362,10 +362,10 @@ int fppg_batch_set_graph_iters(fppg_batch *b, int32_t graph_iters);
 int fppg_batch_store(fppg_batch *b);
 int fppg_batch_load(fppg_batch *b);
 /* Autotuner: times `iters` iterations of the batch for every combination
- * of force-kernel block size (128, 256), force-kernel variant (0 per-lane
- * rows, 1 shared-row union) and triangle search (one warp per queued
- * particle on 4, 8 or 16 CTAs per SM, or — search CTAs 0 — one thread per
- * queued particle on 16 CTAs per SM),
+ * of force-kernel block size (128, 256) and force-kernel variant (0 per-lane
+ * rows, 1 shared-row union) with the warp search on 4 CTAs per SM; then,
+ * with the fastest force kernel, the triangle search on 8 or 16 CTAs per SM
+ * or -- search CTAs 0 -- one thread per queued particle on 16 CTAs per SM;
  * then, with the fastest of those, the two ways of ordering the cell keys
  * (a full stable sort, or the incremental repair of the previous order,
  * fppg_batch_set_incremental), keeps the fastest and restores the particle

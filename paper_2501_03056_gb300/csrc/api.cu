@@ -1090,17 +1090,26 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
             return FPPG_OK;
         };
         const int inc0 = best.incremental;
+        auto consider = [&](int v, int tb, int sc, int inc) -> int {
+            float ms = 0.f;
+            const int r = trial(v, tb, sc, inc, &ms);
+            if (r) return r;
+            if (ms / iters < best_ms) {
+                best_ms = ms / iters;
+                best = TuneVal{v, tb, sc, inc};
+            }
+            return FPPG_OK;
+        };
+        // the force kernel (variant, block) with the warp search on 4 CTAs
+        // per SM, then the search grid with the fastest force kernel
         for (int v = 0; v < 2; v++)
             for (int tb : {128, 256})
-                for (int sc : {0, 4, 8, 16}) {   // 0: one thread per queued particle
-                    float ms = 0.f;
-                    const int r = trial(v, tb, sc, inc0, &ms);
-                    if (r) return r;
-                    if (ms / iters < best_ms) {
-                        best_ms = ms / iters;
-                        best = TuneVal{v, tb, sc, inc0};
-                    }
-                }
+                if (const int r = consider(v, tb, 4, inc0)) return r;
+        {
+            const int v = best.variant, tb = best.block;
+            for (int sc : {0, 8, 16})   // 0: one thread per queued particle
+                if (const int r = consider(v, tb, sc, inc0)) return r;
+        }
         {   // the other ordering with the fastest kernels
             float ms = 0.f;
             const int r = trial(best.variant, best.block, best.search_ctas, 1 - inc0, &ms);
