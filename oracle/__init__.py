@@ -86,6 +86,7 @@ def lib():
                 "oracle_relax_step": (C.c_int, [vp, f64]),
                 "oracle_boolean_keep": (None, [vp, vp, C.c_int, C.c_int, P(i32)]),
                 "oracle_boolean_relax": (C.c_int, [vp, vp, C.c_int, i32]),
+                "oracle_boolean_relax_many": (C.c_int, [C.POINTER(vp), i32, P(i32), i32, i32]),
                 "oracle_relax_energy": (C.c_int, [vp, i32]),
                 "oracle_last_iteration": (None, [vp, P(f64), P(f64), P(i64)]),
                 "oracle_w0": (None, [vp, P(f64)]),
@@ -392,6 +393,17 @@ def boolean_relax(a: Oracle, b: Oracle, op: int, n_iter: int):
     as one assembly (shared forces and time step, partner rules of `op`)."""
     if lib().oracle_boolean_relax(a._c, b._c, int(op), int(n_iter)) != 0:
         raise ValueError("Boolean members need the same dx, h and feature setting")
+
+
+def boolean_relax_many(bodies, pairs, n_iter: int):
+    """Relax bodies joined by several Boolean operations as one assembly;
+    pairs = [(first, second, op), ...] indexes `bodies` (a body keeps to the
+    sides of every operation it takes part in)."""
+    arr = (C.c_void_p * len(bodies))(*[b._c for b in bodies])
+    pr = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 3))
+    r = lib().oracle_boolean_relax_many(arr, len(bodies), _p(pr, C.c_int32), pr.shape[0], int(n_iter))
+    if r != 0:
+        raise ValueError("Boolean members need the same dx, h and options, valid pairs, at most 4 operations each")
 
 
 def union_relax(a: Oracle, b: Oracle, n_iter: int):

@@ -65,6 +65,8 @@
 #define OR_I 3
 #define OR_P 4
 
+#define OR_MAX_PARTNERS 4   /* Boolean operations one body takes part in */
+
 typedef struct {
     uint32_t key;
     uint32_t id;
@@ -75,6 +77,11 @@ typedef struct {
     int64_t nv, nt;
     int64_t nv_all;     /* nv plus the points of intersection-curve lines (V, Vf hold them all) */
     int64_t nseg_own;   /* segments of the body's own feature lines; curve segments follow */
+    /* intersection-curve lines: segments [curve_lo[q], curve_hi[q]) lie on
+     * the curve with body curve_with[q] */
+    int32_t ncurves;
+    int64_t curve_lo[OR_MAX_PARTNERS], curve_hi[OR_MAX_PARTNERS];
+    const void *curve_with[OR_MAX_PARTNERS];
     double *V;      /* [nv*3] vertices (FP64 copy of the FP32 input)        */
     float *Vf;      /* [nv*3] vertices as given                             */
     int32_t *T;     /* [nt*3]                                              */
@@ -484,6 +491,7 @@ static void free_features(or_ctx *c)
     c->line_first = c->line_nseg = NULL;
     c->nfe = c->nsing = c->nlines = c->nseg = 0;
     c->nseg_own = 0;
+    c->ncurves = 0;
     c->nv_all = c->nv;   /* the points of intersection-curve lines go with them */
 }
 
@@ -707,6 +715,7 @@ int64_t oracle_extract_features(or_ctx *c, double dihedral_deg)
 #undef PUSH_SEG
 #undef PUSH_LINE
     c->nseg_own = c->nseg;
+    c->ncurves = 0;
     free(col);
     free(inc);
     free(fill);
@@ -1462,18 +1471,23 @@ void oracle_ray_parity(const or_ctx *c, const double *p, int64_t n, int32_t *ins
  * reset); dr = v_{n+1} dt (Eq. 23); tangential part only for surface
  * (triangle normal) and feature (segment direction) particles; then the
  * projection of the trial point, or revert. */
-static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner, int surf_rule,
-                               int vol_rule);
+static void apply_step_partners(or_ctx *c, const double *acc, double amax, const or_ctx *const *partner,
+                                const int *surf_rule, const int *vol_rule, int npart);
 
-static void apply_step(or_ctx *c, const double *acc, double amax) { apply_step_partner(c, acc, amax, NULL, 0, 0); }
+static void apply_step(or_ctx *c, const double *acc, double amax)
+{
+    apply_step_partners(c, acc, amax, NULL, NULL, NULL, 0);
+}
 
-/* With a Boolean partner (see oracle_boolean_relax), a projected position
- * must also respect the partner: rule 1 = stay outside it, rule 2 = stay
- * inside it, 0 = no rule; surf_rule for surface and feature particles,
- * vol_rule for volume particles.  The partner test is the closest-feature
- * sign of the partner's triangles within the 27 cells; with none near, a
- * particle is where it started (it moves less than a cell per iteration)
- * and the rule holds. */
+/* With Boolean partners (see oracle_boolean_relax_many), a projected
+ * position must also respect every partner: rule 1 = stay outside it, rule
+ * 2 = stay inside it, 0 = no rule; surf_rule for surface and feature
+ * particles, vol_rule for volume particles.  The partner test is the
+ * closest-feature sign of the partner's triangles within the 27 cells; with
+ * none near, a particle is where it started (it moves less than a cell per
+ * iteration) and the rule holds.  A feature particle on the intersection
+ * curve with a partner lies on both surfaces: that partner's rule does not
+ * apply to it (the others' do). */
 static int partner_ok(const or_ctx *partner, int rule, const double *x)
 {
     if (!partner || rule == 0) return 1;
@@ -1482,8 +1496,15 @@ static int partner_ok(const or_ctx *partner, int rule, const double *x)
     return rule == 1 ? t != 1 : t != 0;
 }
 
-static void apply_step_partner(or_ctx *c, const double *acc, double amax, const or_ctx *partner, int surf_rule,
-                               int vol_rule)
+static int on_curve_with(const or_ctx *c, int64_t seg, const void *partner)
+{
+    for (int32_t q = 0; q < c->ncurves; q++)
+        if (c->curve_with[q] == partner && seg >= c->curve_lo[q] && seg < c->curve_hi[q]) return 1;
+    return 0;
+}
+
+static void apply_step_partners(or_ctx *c, const double *acc, double amax, const or_ctx *const *partner,
+                                const int *surf_rule, const int *vol_rule, int npart)
 {
     double dt = amax > 0.0 ? 0.25 * sqrt((double)c->h / amax) : 0.0;
     double *Xn = malloc(sizeof(double) * 3 * (c->n ? c->n : 1));
@@ -1517,11 +1538,12 @@ static void apply_step_partner(or_ctx *c, const double *acc, double amax, const 
         double xn[3];
         int32_t cn;
         int ok = project_point(c, cl, y, cs, xn, &cn);
-        /* a feature particle on an intersection curve lies on both surfaces:
-         * no side of the partner to keep */
-        int on_curve = cl == OR_F && cn >= c->nseg_own;
-        if (ok && (cl == OR_S || (cl == OR_F && !on_curve))) ok = partner_ok(partner, surf_rule, xn);
-        if (ok && cl == OR_V) ok = partner_ok(partner, vol_rule, xn);
+        for (int q = 0; q < npart && ok; q++) {
+            if (cl == OR_S || (cl == OR_F && !on_curve_with(c, cn, partner[q])))
+                ok = partner_ok(partner[q], surf_rule[q], xn);
+            else if (cl == OR_V)
+                ok = partner_ok(partner[q], vol_rule[q], xn);
+        }
         if (ok) {
             memcpy(Xn + 3 * i, xn, sizeof(xn));
             Cn[i] = cn;
@@ -1738,6 +1760,7 @@ static void aabb_of(const or_ctx *c, int64_t t, double *lo, double *hi)
  * end points as singular points).  Returns the particles added. */
 int64_t oracle_boolean_curve(or_ctx *A, const or_ctx *B)
 {
+    const int64_t seg_before = A->nseg;
     /* the triangle pairs whose boxes overlap (brute force) */
     double *alo = malloc(sizeof(double) * 3 * A->nt), *ahi = malloc(sizeof(double) * 3 * A->nt);
     for (int64_t a = 0; a < A->nt; a++) aabb_of(A, a, alo + 3 * a, ahi + 3 * a);
@@ -1908,6 +1931,12 @@ int64_t oracle_boolean_curve(or_ctx *A, const or_ctx *B)
     free(lstart);
     free(lcount);
     free(lclosed);
+    if (A->ncurves < OR_MAX_PARTNERS) {
+        A->curve_lo[A->ncurves] = seg_before;
+        A->curve_hi[A->ncurves] = A->nseg;
+        A->curve_with[A->ncurves] = B;
+        A->ncurves++;
+    }
     /* feature particles along the new lines, appended to A's particles */
     int64_t nf = feature_particles_of_lines(A, (double)A->dx, l_first, A->nlines, NULL, NULL, NULL, 0);
     double *fx = malloc(sizeof(double) * 3 * (nf ? nf : 1));
@@ -1995,50 +2024,94 @@ static void boolean_rules(int op, int first, int *surf, int *vol)
     }
 }
 
-/* Relaxation of the result of a Boolean operation on two bodies (same dx
- * and h) as one assembly: the forces of Eq. 15 over the particles of both
- * (one neighbour grid over both meshes' boxes), one amax and so one dt,
- * then each particle's own projection, subject to the partner rules of the
- * operation (apply_step_partner). */
-int oracle_boolean_relax(or_ctx *a, or_ctx *b, int op, int32_t n_iter)
+/* Relaxation of the result of Boolean operations as one assembly: bodies
+ * b[0..nb) (same dx, h and options) and operations pairs[3 q + (0, 1, 2)] =
+ * (first operand, second operand, op).  The forces of Eq. 15 over the
+ * particles of every body (one neighbour grid over all meshes' boxes), one
+ * amax and so one dt, then each particle's own projection, subject to the
+ * rules of every operation its body takes part in (apply_step_partners): a
+ * body in several operations keeps to all of their sides. */
+int oracle_boolean_relax_many(or_ctx *const *b, int32_t nb, const int32_t *pairs, int32_t np, int32_t n_iter)
 {
-    if (a->h != b->h || a->dx != b->dx || a->fixed_features != b->fixed_features || a->mobile_mask != b->mobile_mask ||
-        op < 0 || op > 2)
-        return -1;
-    const int64_t n = a->n + b->n;
+    if (nb < 1) return -1;
+    for (int32_t q = 0; q < np; q++) {
+        const int32_t i = pairs[3 * q], j = pairs[3 * q + 1], op = pairs[3 * q + 2];
+        if (i < 0 || i >= nb || j < 0 || j >= nb || i == j || op < 0 || op > 2) return -1;
+    }
+    int64_t n = 0;
+    for (int32_t i = 0; i < nb; i++) {
+        if (b[i]->h != b[0]->h || b[i]->dx != b[0]->dx || b[i]->fixed_features != b[0]->fixed_features ||
+            b[i]->mobile_mask != b[0]->mobile_mask)
+            return -1;
+        n += b[i]->n;
+    }
+    /* each body's partners and their rules */
+    const or_ctx **part = malloc(sizeof(*part) * OR_MAX_PARTNERS * nb);
+    int *srule = malloc(sizeof(int) * OR_MAX_PARTNERS * nb), *vrule = malloc(sizeof(int) * OR_MAX_PARTNERS * nb);
+    int *npart = calloc((size_t)nb, sizeof(int));
+    for (int32_t q = 0; q < np; q++) {
+        const int32_t ij[2] = {pairs[3 * q], pairs[3 * q + 1]};
+        for (int e = 0; e < 2; e++) {
+            const int32_t me = ij[e], other = ij[1 - e];
+            if (npart[me] == OR_MAX_PARTNERS) {
+                free(part);
+                free(srule);
+                free(vrule);
+                free(npart);
+                return -1;
+            }
+            const int k = OR_MAX_PARTNERS * me + npart[me]++;
+            part[k] = b[other];
+            boolean_rules(pairs[3 * q + 2], e == 0, &srule[k], &vrule[k]);
+        }
+    }
     double *X = malloc(sizeof(double) * 3 * (n ? n : 1));
     double *acc = malloc(sizeof(double) * 3 * (n ? n : 1));
     int32_t *cls = malloc(sizeof(int32_t) * (n ? n : 1));
-    or_ctx g = *a;   /* a's parameters, the pair's neighbour grid and particles */
+    or_ctx g = *b[0];   /* b[0]'s parameters, the assembly's neighbour grid and particles */
     float bbmin[3] = {INFINITY, INFINITY, INFINITY}, bbmax[3] = {-INFINITY, -INFINITY, -INFINITY};
-    const or_ctx *m[2] = {a, b};
-    for (int q = 0; q < 2; q++)
-        for (int64_t i = 0; i < m[q]->nv; i++)
+    for (int32_t q = 0; q < nb; q++)
+        for (int64_t i = 0; i < b[q]->nv; i++)
             for (int k = 0; k < 3; k++) {
-                bbmin[k] = fminf(bbmin[k], m[q]->Vf[3 * i + k]);
-                bbmax[k] = fmaxf(bbmax[k], m[q]->Vf[3 * i + k]);
+                bbmin[k] = fminf(bbmin[k], b[q]->Vf[3 * i + k]);
+                bbmax[k] = fmaxf(bbmax[k], b[q]->Vf[3 * i + k]);
             }
-    grid_setup(bbmin, bbmax, a->ng_cell, 1.0, 1, g.ng_o, &g.ng_inv, g.ng_n);
-    int sa, va, sb, vb;
-    boolean_rules(op, 1, &sa, &va);
-    boolean_rules(op, 0, &sb, &vb);
+    grid_setup(bbmin, bbmax, b[0]->ng_cell, 1.0, 1, g.ng_o, &g.ng_inv, g.ng_n);
     for (int32_t it = 0; it < n_iter; it++) {
-        memcpy(X, a->X, sizeof(double) * 3 * a->n);
-        memcpy(X + 3 * a->n, b->X, sizeof(double) * 3 * b->n);
-        memcpy(cls, a->cls, sizeof(int32_t) * a->n);
-        memcpy(cls + a->n, b->cls, sizeof(int32_t) * b->n);
+        int64_t off = 0;
+        for (int32_t q = 0; q < nb; q++) {
+            memcpy(X + 3 * off, b[q]->X, sizeof(double) * 3 * b[q]->n);
+            memcpy(cls + off, b[q]->cls, sizeof(int32_t) * b[q]->n);
+            off += b[q]->n;
+        }
         g.X = X;
         g.cls = cls;
         g.n = n;
         double amax = compute_forces(&g, X, acc, NULL);
-        a->last_amax = b->last_amax = amax;
-        apply_step_partner(a, acc, amax, b, sa, va);
-        apply_step_partner(b, acc + 3 * a->n, amax, a, sb, vb);
+        off = 0;
+        for (int32_t q = 0; q < nb; q++) {
+            b[q]->last_amax = amax;
+            const int k = OR_MAX_PARTNERS * q;
+            apply_step_partners(b[q], acc + 3 * off, amax, part + k, srule + k, vrule + k, npart[q]);
+            off += b[q]->n;
+        }
     }
     free(X);
     free(acc);
     free(cls);
+    free(part);
+    free(srule);
+    free(vrule);
+    free(npart);
     return 0;
+}
+
+/* The same for the two bodies of one operation. */
+int oracle_boolean_relax(or_ctx *a, or_ctx *b, int op, int32_t n_iter)
+{
+    or_ctx *m[2] = {a, b};
+    const int32_t pair[3] = {0, 1, op};
+    return oracle_boolean_relax_many(m, 2, pair, 1, n_iter);
 }
 
 void oracle_last_iteration(const or_ctx *c, double *amax, double *maxdisp, int64_t *reverts)
