@@ -191,12 +191,21 @@ int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n);
  * cavity wall), of an intersection inside the partner; volume particles of
  * a difference also stay outside b, of an intersection inside b.  The
  * curve where the surfaces meet gets feature particles from
- * fppg_boolean_curve (below).  *n_a, *n_b
+ * fppg_boolean_curve (below).
+ * Chains (Fig. 10 combines several bodies): a body may take part in up to
+ * four operations, each applied to the particles its earlier ones left; it
+ * keeps what every operation keeps and relaxes under the rules of all of
+ * them.  Bodies joined by operations, directly or through others, form one
+ * assembly (one neighbour grid over all their boxes, one time step) and
+ * relax in one batch that holds all of them.  A cavity cut by several
+ * overlapping bodies is their union: unite the cutters as well.  *n_a, *n_b
  * (nullable) receive the particle counts left.  Errors: FPPG_ERR_ARG for
  * the same handle twice, an unknown op, different dx / h / feature
  * setting, or a mesh that is not closed and consistently oriented;
- * FPPG_ERR_STATE without particles or when a body is already an operand.
- * fppg_relax on an operand afterwards returns FPPG_ERR_STATE.
+ * FPPG_ERR_STATE without particles, when the two bodies are already in an
+ * operation together, or when one of them is in four operations already.
+ * fppg_relax on an operand afterwards returns FPPG_ERR_STATE, and so does
+ * fppg_batch_create with an operand but not all of its partners.
  * fppg_union(a, b, ...) = fppg_boolean(a, b, FPPG_UNION, ...). */
 #define FPPG_UNION 0
 #define FPPG_DIFFERENCE 1
@@ -207,7 +216,8 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b);
  * the curve where a's surface crosses b's becomes feature lines of a, with
  * feature particles along them appended to a's particles, constraint = the
  * curve segment.  Call after fppg_boolean(a, b, ...) (either order of the
- * pair; the lines go to the first argument) and before fppg_batch_create.
+ * pair; the lines go to the first argument) and before fppg_batch_create;
+ * in a chain, once per pair whose crease is wanted.
  * Set-up on the host, in FP64 with every operation rounded in the written
  * order:
  *   - pairs: every (a-triangle, b-triangle) pair whose closed bounding boxes
@@ -230,10 +240,11 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b);
  *     after a's own, with n = ceil(L / dx) feature particles placed as on
  *     a's own lines (open chains add their end points as singular points).
  * In the relaxation these particles move along their line and are exempt
- * from the partner rule: they lie on both surfaces.  *n_added (nullable)
- * receives the particles added.  Errors: FPPG_ERR_ARG for the same handle
- * twice or more than 2^31 curve points; FPPG_ERR_STATE when b is not a's
- * Boolean partner, a has no particles, or a has its curve already;
+ * from the pair's partner rule (they lie on both surfaces); the rules of
+ * a's other operations still apply to them.  *n_added (nullable) receives
+ * the particles added.  Errors: FPPG_ERR_ARG for the same handle twice or
+ * more than 2^31 curve points; FPPG_ERR_STATE when b is not a's Boolean
+ * partner, a has no particles, or the pair has its curve already;
  * FPPG_ERR_OOM.  On an error a keeps its own lines (after a failed
  * particle upload, like fppg_set_particles, no particles).  Extracting
  * features again drops the curve lines. */

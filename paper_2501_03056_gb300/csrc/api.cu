@@ -27,9 +27,22 @@ struct fppg_ctx {
     std::vector<int32_t> cls_host;
     int mobile_mask = (1 << FPPG_S) | (1 << FPPG_V) | (1 << FPPG_F);   // classes that move
     int cascade = 0;               // surface re-projection rule (fppg_set_projection_rule)
-    fppg_ctx *partner = nullptr;   // Boolean partner (fppg_boolean)
-    int bool_op = 0;               // FPPG_UNION, FPPG_DIFFERENCE or FPPG_INTERSECTION
-    bool bool_first = false;       // the first operand of the operation
+    // Boolean operations this body takes part in (fppg_boolean), in order:
+    // the other operand, FPPG_UNION / FPPG_DIFFERENCE / FPPG_INTERSECTION,
+    // whether this body is the first operand, and this body's
+    // intersection-curve segments with the other one [curve_lo, curve_hi)
+    struct BoolRel {
+        fppg_ctx *other;
+        int op;
+        bool first;
+        int curve_lo, curve_hi;
+    };
+    std::vector<BoolRel> rels;
+    BoolRel *rel_with(const fppg_ctx *o) {
+        for (BoolRel &r : rels)
+            if (r.other == o) return &r;
+        return nullptr;
+    }
     int64_t n_ghost = 0;           // the last n_ghost particles are ghosts (fppg_set_ghost_count)
     int split_buf = -1;            // grid buffer of the last fppg_relax_forces, until its step
     // device staging of the host particle arrays of set / get, kept between
@@ -191,7 +204,14 @@ int fppg_create(const float *verts_host, int64_t nv, const int32_t *tris_host, i
 int fppg_destroy(fppg_ctx *ctx) {
     if (!ctx) return FPPG_ERR_ARG;
     cudaStreamSynchronize(ctx->stream);
-    if (ctx->partner) ctx->partner->partner = nullptr;
+    for (const fppg_ctx::BoolRel &r : ctx->rels) {
+        auto &o = r.other->rels;
+        for (size_t q = 0; q < o.size(); q++)
+            if (o[q].other == ctx) {
+                o.erase(o.begin() + (long)q);
+                break;
+            }
+    }
     delete ctx;
     return FPPG_OK;
 }
@@ -343,7 +363,9 @@ int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_
     if (op != FPPG_UNION && op != FPPG_DIFFERENCE && op != FPPG_INTERSECTION)
         return fail(a->err, FPPG_ERR_ARG, "unknown Boolean operation");
     if (!a->has_particles || !b->has_particles) return fail(a->err, FPPG_ERR_STATE, "no particles set");
-    if (a->partner || b->partner) return fail(a->err, FPPG_ERR_STATE, "a body is already in a Boolean operation");
+    if (a->rel_with(b)) return fail(a->err, FPPG_ERR_STATE, "the two bodies are already in a Boolean operation");
+    if ((int)a->rels.size() >= kMaxPartners || (int)b->rels.size() >= kMaxPartners)
+        return fail(a->err, FPPG_ERR_STATE, "a body takes part in at most four Boolean operations");
     if (a->body.dx != b->body.dx || a->body.h != b->body.h || a->fixed_features != b->fixed_features)
         return fail(a->err, FPPG_ERR_ARG, "Boolean operands need the same dx, h and feature setting");
     if (!a->body.closed || !b->body.closed)
@@ -389,11 +411,8 @@ int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_
         if (!r) r = fppg_set_constraints(c, kk.data(), (int64_t)kk.size());
         if (r) return r;
     }
-    a->partner = b;
-    b->partner = a;
-    a->bool_op = b->bool_op = op;
-    a->bool_first = true;
-    b->bool_first = false;
+    a->rels.push_back(fppg_ctx::BoolRel{b, op, true, 0, 0});
+    b->rels.push_back(fppg_ctx::BoolRel{a, op, false, 0, 0});
     if (n_a) *n_a = a->n;
     if (n_b) *n_b = b->n;
     return FPPG_OK;
@@ -405,10 +424,15 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
 
 int fppg_boolean_curve(fppg_ctx *a, fppg_ctx *b, int64_t *n_added) {
     if (!a || !b || a == b) return fail_global(FPPG_ERR_ARG, "the intersection curve needs two different bodies");
-    if (a->partner != b) return fail(a->err, FPPG_ERR_STATE, "the intersection curve follows fppg_boolean on the pair");
+    fppg_ctx::BoolRel *rel = a->rel_with(b);
+    if (!rel) return fail(a->err, FPPG_ERR_STATE, "the intersection curve follows fppg_boolean on the pair");
     if (!a->has_particles) return fail(a->err, FPPG_ERR_STATE, "no particles set");
     Body &bd = a->body;
-    if (bd.nseg > bd.nseg_own) return fail(a->err, FPPG_ERR_STATE, "the intersection curve is there already");
+    if (rel->curve_hi > rel->curve_lo || (b->rel_with(a)->curve_hi > b->rel_with(a)->curve_lo))
+        return fail(a->err, FPPG_ERR_STATE, "the intersection curve is there already");
+    const int nseg_before = bd.nseg;
+    const size_t verts_before = bd.verts_host.size();
+    const bool has_before = bd.has_features;
     const int64_t n = a->n;
     std::vector<float> xyz(3 * (size_t)n);
     std::vector<int32_t> cls((size_t)n), cons((size_t)n);
@@ -427,11 +451,13 @@ int fppg_boolean_curve(fppg_ctx *a, fppg_ctx *b, int64_t *n_added) {
         // no curve without its particles: the host lines go back to the
         // body's own (the device copy only holds more segments than used)
         const std::string msg = a->err;
-        bd.drop_curve();
+        bd.drop_lines_after(nseg_before, verts_before, has_before);
         ctx_group(a);
         a->err = msg;
         return r;
     }
+    rel->curve_lo = nseg_before;
+    rel->curve_hi = bd.nseg;
     if (n_added) *n_added = (int64_t)fc.size();
     return FPPG_OK;
 }
@@ -475,8 +501,8 @@ static int relax_impl(fppg_ctx *ctx, int32_t n_iter, bool energy_mode) {
     if (!ctx) return FPPG_ERR_ARG;
     if (n_iter < 0) return fail(ctx->err, FPPG_ERR_ARG, "n_iter < 0");
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
-    if (ctx->partner)
-        return fail(ctx->err, FPPG_ERR_STATE, "a Boolean operand relaxes in a batch together with its partner");
+    if (!ctx->rels.empty())
+        return fail(ctx->err, FPPG_ERR_STATE, "a Boolean operand relaxes in a batch together with its partners");
     for (int32_t it = 0; it < n_iter; it++) iterate(ctx->group, ctx->stream, energy_mode);
     CUDA_OR(ctx->err, cudaGetLastError());
     return FPPG_OK;
@@ -497,8 +523,8 @@ int fppg_set_ghost_count(fppg_ctx *ctx, int64_t n_ghost) {
 int fppg_relax_forces(fppg_ctx *ctx, float *amax_host) {
     if (!ctx || !amax_host) return FPPG_ERR_ARG;
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
-    if (ctx->partner)
-        return fail(ctx->err, FPPG_ERR_STATE, "a Boolean operand relaxes in a batch together with its partner");
+    if (!ctx->rels.empty())
+        return fail(ctx->err, FPPG_ERR_STATE, "a Boolean operand relaxes in a batch together with its partners");
     uint32_t a = 0u;
     if (ctx->n > 0) {
         Group &g = ctx->group;
@@ -730,18 +756,32 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
     g.owns_mesh = true;
     DevGroup &d = g.d;
     d.B = n;
-    // Boolean-union partners share one neighbour grid over both boxes and
-    // one time step
-    std::vector<int> partner(n, -1);
-    for (int32_t i = 0; i < n; i++) {
-        if (!ctxs[i]->partner) continue;
-        for (int32_t j = 0; j < n; j++)
-            if (ctxs[j] == ctxs[i]->partner) partner[i] = j;
-        if (partner[i] < 0) {
-            delete b;
-            return fail_global(FPPG_ERR_STATE, "a Boolean operand needs its partner in the same batch");
+    // Bodies joined by Boolean operations form one assembly: one neighbour
+    // grid over all their boxes (set up at the assembly's first body) and
+    // one time step; root[i] = the assembly's first body
+    auto index_of = [&](const fppg_ctx *c) {
+        for (int32_t q = 0; q < n; q++)
+            if (ctxs[q] == c) return q;
+        return -1;
+    };
+    std::vector<int> root(n);
+    for (int32_t i = 0; i < n; i++) root[i] = i;
+    auto find = [&](int i) {
+        while (root[i] != i) i = root[i] = root[root[i]];
+        return i;
+    };
+    for (int32_t i = 0; i < n; i++)
+        for (const fppg_ctx::BoolRel &r : ctxs[i]->rels) {
+            const int j = index_of(r.other);
+            if (j < 0) {
+                delete b;
+                return fail_global(FPPG_ERR_STATE, "a Boolean operand needs every partner in the same batch");
+            }
+            const int x = find(i), y = find(j);
+            if (x != y) root[std::max(x, y)] = std::min(x, y);
         }
-    }
+    std::vector<int> members(n, 0);
+    for (int32_t i = 0; i < n; i++) members[find(i)]++;
     int64_t N = 0, cells = 0, nt = 0, nv = 0, hs = 0, nc = 0, np = 0, ns = 0, nl = 0, ow = 0;
     int64_t dw = 0, dl = 0, dc = 0;   // candidate-list ranks, starts and lists
     for (int32_t i = 0; i < n; i++) {
@@ -751,10 +791,10 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
         A.amax_slot = i;
         A.mobile = c->mobile_mask;
         A.cascade = c->cascade;
-        const int j = partner[i];
+        const int r0 = find(i);
         int64_t grid_cells = (int64_t)bd.ng_n[0] * bd.ng_n[1] * bd.ng_n[2];
-        if (j >= 0 && j < i) {
-            const AsmParams &Q = g.hp[j];
+        if (r0 < i) {
+            const AsmParams &Q = g.hp[r0];
             for (int k = 0; k < 3; k++) {
                 A.ng_o[k] = Q.ng_o[k];
                 A.ng_n[k] = Q.ng_n[k];
@@ -762,29 +802,40 @@ int fppg_batch_create(fppg_ctx *const *ctxs, int32_t n, fppg_batch **out) {
             A.ng_inv = Q.ng_inv;
             A.key_base = Q.key_base;
             grid_cells = 0;
-        } else if (j > i) {
-            const Body &pb = ctxs[j]->body;
+        } else if (members[i] > 1) {
             float lo[3], hi[3];
             for (int k = 0; k < 3; k++) {
-                lo[k] = std::min(bd.bbmin[k], pb.bbmin[k]);
-                hi[k] = std::max(bd.bbmax[k], pb.bbmax[k]);
+                lo[k] = bd.bbmin[k];
+                hi[k] = bd.bbmax[k];
             }
+            for (int32_t q = i + 1; q < n; q++)
+                if (find(q) == i)
+                    for (int k = 0; k < 3; k++) {
+                        lo[k] = std::min(lo[k], ctxs[q]->body.bbmin[k]);
+                        hi[k] = std::max(hi[k], ctxs[q]->body.bbmax[k]);
+                    }
             if (!grid_setup(lo, hi, bd.ng_cell, 1.0, 1, A.ng_o, &A.ng_inv, A.ng_n)) {
                 delete b;
-                return fail_global(FPPG_ERR_ARG, "the shared grid of a Boolean pair needs more than 2^20 cells per axis");
+                return fail_global(FPPG_ERR_ARG,
+                                   "the shared grid of a Boolean assembly needs more than 2^20 cells per axis");
             }
             grid_cells = (int64_t)A.ng_n[0] * A.ng_n[1] * A.ng_n[2];
         }
-        if (j >= 0) {
-            // partner rules (1 stay outside, 2 stay inside): surface and
-            // feature particles, then volume particles
-            const int op = c->bool_op;
-            const bool first = c->bool_first;
-            A.partner = j;
-            A.partner_surf = op == FPPG_UNION ? 1 : op == FPPG_DIFFERENCE ? (first ? 1 : 2) : 2;
-            A.partner_vol = op == FPPG_UNION ? 0 : op == FPPG_DIFFERENCE ? (first ? 1 : 0) : (first ? 2 : 0);
-            A.amax_slot = std::min(i, j);
+        if (members[r0] > 1) {
+            A.amax_slot = r0;
             A.slab_r2 = slab_reach2(A.R2, A.ng_inv);
+        }
+        // partner rules (1 stay outside, 2 stay inside): surface and feature
+        // particles, then volume particles
+        for (const fppg_ctx::BoolRel &r : c->rels) {
+            const int q = A.npart++;
+            const bool first = r.first;
+            A.partner[q] = index_of(r.other);
+            A.partner_surf[q] = r.op == FPPG_UNION ? 1 : r.op == FPPG_DIFFERENCE ? (first ? 1 : 2) : 2;
+            A.partner_vol[q] = r.op == FPPG_UNION ? 0 : r.op == FPPG_DIFFERENCE ? (first ? 1 : 0) : (first ? 2 : 0);
+            A.curve_lo[q] = r.curve_lo;
+            A.curve_hi[q] = r.curve_hi;
+            if (A.partner_vol[q] != 0) A.vol_rules = 1;
         }
         A.tri_off = (int)nt;
         A.vert_off = (int)nv;

@@ -193,7 +193,6 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.nt = b.nt;
     A.nv = b.nv;
     A.nseg = b.nseg;
-    A.curve_seg0 = b.nseg_own;
     A.nlines = b.nlines;
     A.fixed_features = fixed_features;
     const double h = (double)b.h;
@@ -209,9 +208,8 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     A.closed = b.closed ? 1 : 0;
     A.mobile = (1 << kClsS) | (1 << kClsV) | (1 << kClsF);
     A.cascade = 0;
-    A.partner = -1;
-    A.partner_surf = 0;
-    A.partner_vol = 0;
+    A.npart = 0;
+    A.vol_rules = 0;
     A.amax_slot = 0;
     A.w0[0] = (float)lattice_w0((double)b.dx, h, 2);
     A.w0[1] = (float)lattice_w0((double)b.dx, h, 3);

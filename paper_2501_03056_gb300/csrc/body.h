@@ -63,12 +63,14 @@ struct Body {
     int2 *lines = nullptr;
     int nseg = 0, nlines = 0;
     int nseg_own = 0;                  // segments of the body's own lines; intersection-curve ones follow
-    bool own_has_features = false;     // has_features before the intersection curve was added
 
     // feature particles of lines l0 .. l1 - 1 (l1 < 0: to the last line)
     void feature_particles(std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg,
                            int l0 = 0, int l1 = -1) const;
-    void drop_curve();       // back to the body's own lines (host side)
+    // back to an earlier set of lines: the first nseg_keep segments and the
+    // lines they form, verts_keep vertex coordinates (host side; the device
+    // copy only holds more segments than are used)
+    void drop_lines_after(int nseg_keep, size_t verts_keep, bool has_features_keep);
     int add_curve(const Body &other, std::vector<float> &xyz, std::vector<int32_t> &cls, std::vector<int32_t> &seg,
                   cudaStream_t s, std::string &err);
     int build_mesh(const float *verts_host, int64_t nv, const int32_t *tris_host, int64_t nt, float dx, float h,

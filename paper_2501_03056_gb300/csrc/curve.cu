@@ -363,7 +363,6 @@ int Body::add_curve(const Body &other, std::vector<float> &xyz, std::vector<int3
         nseg += (int)nsl;
         nlines++;
     }
-    own_has_features = has_features;
     has_features = true;
     const int r = upload_lines(s, err, true);
     if (r) {
@@ -381,17 +380,17 @@ int Body::add_curve(const Body &other, std::vector<float> &xyz, std::vector<int3
     return 0;
 }
 
-void Body::drop_curve() {
+void Body::drop_lines_after(int nseg_keep, size_t verts_keep, bool has_features_keep) {
     int keep = 0;
-    while (keep < nlines && line_first[keep] < nseg_own) keep++;
+    while (keep < nlines && line_first[keep] < nseg_keep) keep++;
     line_first.resize(keep);
     line_nseg.resize(keep);
     line_closed.resize(keep);
-    seg_v.resize(2 * (size_t)nseg_own);
-    nseg = nseg_own;
+    seg_v.resize(2 * (size_t)nseg_keep);
+    nseg = nseg_keep;
     nlines = keep;
-    verts_host.resize(3 * (size_t)nv);
-    has_features = own_has_features;
+    verts_host.resize(verts_keep);
+    has_features = has_features_keep;
 }
 
 } // namespace fppg

@@ -48,6 +48,8 @@ __host__ __device__ constexpr uint32_t acts_on_bits(int c) {
 // Eq. 10 primes, exactly as printed.
 constexpr uint32_t kHashP1 = 738560931u, kHashP2 = 19349663u, kHashP3 = 83492791u;
 
+constexpr int kMaxPartners = 4;   // Boolean operations one body takes part in
+
 struct AsmParams {
     // neighbour grid (cell 2h (1 + 2^-8))
     float ng_o[3];
@@ -74,7 +76,6 @@ struct AsmParams {
     int nv;
     int seg_off;           // offset of its feature segments (ids are local)
     int nseg;
-    int curve_seg0;        // first intersection-curve segment (on both surfaces: no partner rule)
     int line_off;
     int nlines;
     int fixed_features;
@@ -92,10 +93,19 @@ struct AsmParams {
     int closed;        // closed, consistently oriented mesh: inside certificates apply
     int mobile;        // bit c: class c may move (S, V, F; I and P never do)
     int cascade;       // surface re-projection: 0 closest over 27 cells, 1 the cascade of Sec. 3.3.3
-    int partner;       // Boolean partner (body index in the group) or -1
-    int partner_surf;  // rule for surface / feature particles: 0 none, 1 stay outside the partner, 2 inside
-    int partner_vol;   // the same for volume particles
-    int amax_slot;     // body whose amax / time step this body shares (itself, or its Boolean partner)
+    // Boolean operations this body takes part in (Sec. 3.2.3), one entry per
+    // partner: its body index in the group, the rule for surface / feature
+    // particles (0 none, 1 stay outside the partner, 2 stay inside), the
+    // rule for volume particles, and this body's intersection-curve
+    // segments with that partner [curve_lo, curve_hi) (on both surfaces:
+    // exempt from that partner's rule)
+    int npart;
+    int partner[kMaxPartners];
+    int partner_surf[kMaxPartners];
+    int partner_vol[kMaxPartners];
+    int curve_lo[kMaxPartners], curve_hi[kMaxPartners];
+    int vol_rules;     // some partner has a volume rule
+    int amax_slot;     // body whose amax / time step this body shares (itself, or its assembly's first body)
     int p_begin, p_end;
 };
 

@@ -118,7 +118,7 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     A.step_h = (float)(hd / 16.0);
     A.fixed_features = fixed_features ? 1 : 0;
     A.mobile = (1 << kClsS) | (1 << kClsV) | (1 << kClsF);
-    A.partner = -1;
+    A.npart = 0;
     A.amax_slot = 0;
     A.p_end = (int)n;
 

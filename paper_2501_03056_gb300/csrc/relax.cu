@@ -875,6 +875,15 @@ __device__ bool project_feature(const MeshView &M, const AsmParams &A, float3 y,
     return bs >= 0;
 }
 
+// some triangle of body Q within the 27 triangle cells of x (its dilated
+// occupancy bit)
+__device__ inline bool near_body(const MeshView &M, const AsmParams &Q, float3 x) {
+    return test_bit(M.occ, Q.dil_off,
+                    tri_key(Q, cell_coord(x.x, Q.tg_o[0], Q.tg_inv, Q.tg_n[0]),
+                            cell_coord(x.y, Q.tg_o[1], Q.tg_inv, Q.tg_n[1]),
+                            cell_coord(x.z, Q.tg_o[2], Q.tg_inv, Q.tg_n[2])));
+}
+
 // ---- A5 + A6 -------------------------------------------------------------------
 // k_step: one thread per particle (key order): the limited step and its
 // tangential part, then the cases that need no triangle search -- feature
@@ -918,18 +927,14 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             float3 x;
             int cn;
             if (project_feature(M, A, y, c, x, cn)) {
+                // a partner's triangles within reach: the search tests that
+                // partner's rule on the projection (a particle on the
+                // intersection curve with a partner lies on both surfaces:
+                // no rule of that partner)
                 bool near_partner = false;
-                // (a particle on the intersection curve lies on both
-                // surfaces: no partner rule)
-                if (A.partner >= 0 && A.partner_surf != 0 && cn < A.curve_seg0) {
-                    // the partner's triangles within reach: the search tests
-                    // the partner rule on the projection
-                    const AsmParams &Q = P[A.partner];
-                    near_partner = test_bit(M.occ, Q.dil_off,
-                                            tri_key(Q, cell_coord(x.x, Q.tg_o[0], Q.tg_inv, Q.tg_n[0]),
-                                                    cell_coord(x.y, Q.tg_o[1], Q.tg_inv, Q.tg_n[1]),
-                                                    cell_coord(x.z, Q.tg_o[2], Q.tg_inv, Q.tg_n[2])));
-                }
+                for (int q = 0; q < A.npart && !near_partner; q++)
+                    if (A.partner_surf[q] != 0 && !(cn >= A.curve_lo[q] && cn < A.curve_hi[q]))
+                        near_partner = near_body(M, P[A.partner[q]], x);
                 if (near_partner) {
                     queue = true;
                 } else {
@@ -945,12 +950,9 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
             const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
             bool certified = false;
             bool near_partner = false;
-            if (cls == kClsV && A.partner >= 0 && A.partner_vol != 0) {
-                const AsmParams &Q = P[A.partner];
-                near_partner = test_bit(M.occ, Q.dil_off,
-                                        tri_key(Q, cell_coord(y.x, Q.tg_o[0], Q.tg_inv, Q.tg_n[0]),
-                                                cell_coord(y.y, Q.tg_o[1], Q.tg_inv, Q.tg_n[1]),
-                                                cell_coord(y.z, Q.tg_o[2], Q.tg_inv, Q.tg_n[2])));
+            if (cls == kClsV && A.vol_rules) {
+                for (int q = 0; q < A.npart && !near_partner; q++)
+                    if (A.partner_vol[q] != 0) near_partner = near_body(M, P[A.partner[q]], y);
             } else if (cls == kClsV && A.closed) {
                 // inside a ball that an earlier search found free of surface
                 // and inside the body: the volume test would accept
@@ -1059,13 +1061,15 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             ok = warp_volume_inside(M, A, y, buf, clear, &rng);
         }
         // Boolean operations: the partner rule of the particle's class
-        if (ok && A.partner >= 0 && !(cls == kClsF && tri >= A.curve_seg0))
-            ok = warp_partner_ok(M, P[A.partner], cls == kClsV ? A.partner_vol : A.partner_surf, x, buf);
+        for (int q = 0; q < A.npart && ok; q++)
+            if (!(cls == kClsF && tri >= A.curve_lo[q] && tri < A.curve_hi[q]))
+                ok = warp_partner_ok(M, P[A.partner[q]], cls == kClsV ? A.partner_vol[q] : A.partner_surf[q], x,
+                                     buf);
         if (ok && lane == 0) {
             const uint32_t i = id_s[it.x];
             pos[i] = make_float4(x.x, x.y, x.z, p.w);
             if (tri >= 0) cons[i] = tri;
-            if (cls == kClsV && A.closed && A.partner_vol == 0) cert[i] = make_float4(y.x, y.y, y.z, clear);
+            if (cls == kClsV && A.closed && !A.vol_rules) cert[i] = make_float4(y.x, y.y, y.z, clear);
             const float3 w = x - f3(p);
             if (b != run_b) {
                 if (run) atomicMax(maxdisp + run_b, run);
@@ -1222,12 +1226,14 @@ __global__ void __launch_bounds__(TPB) k_search_thread(const float4 *__restrict_
             } else {
                 ok = thread_closest_sign(M, A, y, clear, &rng) != 0;
             }
-            if (ok && A.partner >= 0 && !(cls == kClsF && tri >= A.curve_seg0))
-                ok = thread_partner_ok(M, P[A.partner], cls == kClsV ? A.partner_vol : A.partner_surf, x);
+            for (int q = 0; q < A.npart && ok; q++)
+                if (!(cls == kClsF && tri >= A.curve_lo[q] && tri < A.curve_hi[q]))
+                    ok = thread_partner_ok(M, P[A.partner[q]], cls == kClsV ? A.partner_vol[q] : A.partner_surf[q],
+                                           x);
             if (ok) {
                 pos[i] = make_float4(x.x, x.y, x.z, p.w);
                 if (tri >= 0) cons[i] = tri;
-                if (cls == kClsV && A.closed && A.partner_vol == 0) cert[i] = make_float4(y.x, y.y, y.z, clear);
+                if (cls == kClsV && A.closed && !A.vol_rules) cert[i] = make_float4(y.x, y.y, y.z, clear);
                 const float3 w = x - f3(p);
                 disp = sqrtf(dot3(w, w));
             }
