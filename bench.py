@@ -49,7 +49,7 @@ INSTR_PER_CANDIDATE, INSTR_PER_PAIR = 7.0, 25.0
 FLOPS_PER_CANDIDATE, FLOPS_PER_PAIR = 8.0, 12.0
 # DRAM bytes (read + write) of one k_force launch, from one ncu capture per
 # workload of the current kernel (null until captured)
-K_FORCE_DRAM_BYTES = {"sphere_torus": 26981632 + 21248, "vehicle": 653534976 + 285976320}
+K_FORCE_DRAM_BYTES = {"sphere_torus": 26987520 + 6400, "vehicle": 653534976 + 285976320}
 # bytes per particle-iteration: state in and out plus the mandated cell-list
 # rebuild (useful), and the compulsory traffic of the whole pipeline
 USEFUL_BYTES, PIPELINE_BYTES = 56.0, 224.0

@@ -5,6 +5,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <tuple>
 
 #include "../../include/fppg.h"
@@ -113,6 +114,31 @@ __global__ void k_set_body(float4 *__restrict__ pos, int64_t n, int body) {
 }
 
 inline unsigned nb(int64_t n) { return (unsigned)std::max<int64_t>((n + 255) / 256, 1); }
+
+// f(begin, end) over [0, n) in chunks on up to 32 host threads (at least 2^20
+// items each); a thread that cannot be started runs its chunk here
+template <typename F>
+void host_parallel(int64_t n, F &&f) {
+    const int64_t per = (int64_t)1 << 20;
+    const int64_t hw = std::max<int64_t>((int64_t)std::thread::hardware_concurrency(), 1);
+    const int nt = (int)std::min<int64_t>(std::min<int64_t>((n + per - 1) / per, hw), 32);
+    if (nt <= 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)nt);
+    for (int t = 1; t < nt; t++) {
+        const int64_t a = n * t / nt, b = n * (t + 1) / nt;
+        try {
+            th.emplace_back([&f, a, b] { f(a, b); });
+        } catch (...) {
+            f(a, b);
+        }
+    }
+    f((int64_t)0, n / nt);
+    for (std::thread &x : th) x.join();
+}
 
 MeshView view_of(const Body &b) {
     return MeshView{b.geo, b.vx, b.pn, b.hrng, b.compact, b.tlist, b.seg, b.lines, b.occ, b.drank, b.coff, b.cand};
@@ -306,17 +332,37 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
     if (!ctx) return FPPG_ERR_ARG;
     if (n < 0 || n > (int64_t)1 << 31) return fail(ctx->err, FPPG_ERR_ARG, "particle count out of range");
     if (n > 0 && (!xyz_host || !cls_host)) return fail(ctx->err, FPPG_ERR_ARG, "NULL particle buffer");
-    // branch-free scans (they vectorise): a class outside 0..4, an exponent
-    // field of all ones (inf or NaN)
-    uint32_t bad_cls = 0u, bad_xyz = 0u;
-    for (int64_t i = 0; i < n; i++) bad_cls |= (uint32_t)((uint32_t)cls_host[i] > 4u);
-    for (int64_t i = 0; i < 3 * n; i++) {
-        uint32_t b;
-        memcpy(&b, xyz_host + i, sizeof(b));
-        bad_xyz |= (uint32_t)((b & 0x7f800000u) == 0x7f800000u);
+    // the upload into the staging buffer (scratch, not yet the state) runs
+    // while the host checks the input
+    float *dx = nullptr;
+    int32_t *dc = nullptr;
+    if (n > 0) {
+        void *st = nullptr;
+        int r = stage_buf(ctx, 16 * (size_t)n, &st);
+        if (r) return r;
+        dx = (float *)st;
+        dc = (int32_t *)(dx + 3 * n);
+        CUDA_OR(ctx->err, cudaMemcpyAsync(dx, xyz_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CUDA_OR(ctx->err, cudaMemcpyAsync(dc, cls_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
     }
-    if (bad_cls) return fail(ctx->err, FPPG_ERR_ARG, "class outside 0..4");
-    if (bad_xyz) return fail(ctx->err, FPPG_ERR_ARG, "non-finite coordinate");
+    // branch-free scans (they vectorise), on several host threads: a class
+    // outside 0..4, an exponent field of all ones (inf or NaN)
+    std::atomic<uint32_t> bad_cls{0u}, bad_xyz{0u};
+    host_parallel(n, [&](int64_t a, int64_t b) {
+        uint32_t bc = 0u, bx = 0u;
+        for (int64_t i = a; i < b; i++) bc |= (uint32_t)((uint32_t)cls_host[i] > 4u);
+        for (int64_t i = 3 * a; i < 3 * b; i++) {
+            uint32_t w;
+            memcpy(&w, xyz_host + i, sizeof(w));
+            bx |= (uint32_t)((w & 0x7f800000u) == 0x7f800000u);
+        }
+        if (bc) bad_cls.fetch_or(bc);
+        if (bx) bad_xyz.fetch_or(bx);
+    });
+    if (bad_cls.load() || bad_xyz.load()) {
+        cudaStreamSynchronize(ctx->stream);   // the staging copies end before the buffer is reused
+        return fail(ctx->err, FPPG_ERR_ARG, bad_cls.load() ? "class outside 0..4" : "non-finite coordinate");
+    }
     Group &g = ctx->group;
     ctx->has_particles = false;     // until the new set is complete
     ctx->split_buf = -1;
@@ -326,17 +372,10 @@ int fppg_set_particles(fppg_ctx *ctx, const float *xyz_host, const int32_t *cls_
         if (r) return r;
     }
     ctx->n = n;
-    ctx->cls_host.assign(cls_host, cls_host + n);
-    if (n > 0) {
-        void *st = nullptr;
-        int r = stage_buf(ctx, 16 * (size_t)n, &st);
-        if (r) return r;
-        float *dx = (float *)st;
-        int32_t *dc = (int32_t *)(dx + 3 * n);
-        CUDA_OR(ctx->err, cudaMemcpyAsync(dx, xyz_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
-        CUDA_OR(ctx->err, cudaMemcpyAsync(dc, cls_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
-        k_pack<<<nb(n), 256, 0, ctx->stream>>>(dx, dc, n, 0, g.d.pos, g.d.cons);
-    }
+    if ((int64_t)ctx->cls_host.size() != n) ctx->cls_host.resize((size_t)n);
+    int32_t *ch = ctx->cls_host.data();
+    host_parallel(n, [&](int64_t a, int64_t b) { std::copy(cls_host + a, cls_host + b, ch + a); });
+    if (n > 0) k_pack<<<nb(n), 256, 0, ctx->stream>>>(dx, dc, n, 0, g.d.pos, g.d.cons);
     CUDA_OR(ctx->err, cudaStreamSynchronize(ctx->stream));
     ctx->has_particles = true;
     return ctx_group(ctx);
@@ -346,11 +385,18 @@ int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n) {
     if (!ctx) return FPPG_ERR_ARG;
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
     if (n != ctx->n || (n > 0 && !cons_host)) return fail(ctx->err, FPPG_ERR_ARG, "constraint count mismatch");
-    for (int64_t i = 0; i < n; i++) {
-        const int32_t c = cons_host[i], cl = ctx->cls_host[i];
-        const int64_t lim = cl == FPPG_S ? ctx->body.nt : cl == FPPG_F ? ctx->body.nseg : 0;
-        if (c < -1 || c >= lim) return fail(ctx->err, FPPG_ERR_ARG, "constraint id out of range for its class");
-    }
+    std::atomic<uint32_t> bad{0u};
+    const int32_t *cl = ctx->cls_host.data();
+    const int64_t nt = ctx->body.nt, ns = ctx->body.nseg;
+    host_parallel(n, [&](int64_t a, int64_t b) {
+        uint32_t e = 0u;
+        for (int64_t i = a; i < b; i++) {
+            const int64_t lim = cl[i] == FPPG_S ? nt : cl[i] == FPPG_F ? ns : 0;
+            e |= (uint32_t)(cons_host[i] < -1 || cons_host[i] >= lim);
+        }
+        if (e) bad.fetch_or(e);
+    });
+    if (bad.load()) return fail(ctx->err, FPPG_ERR_ARG, "constraint id out of range for its class");
     if (n > 0)
         CUDA_OR(ctx->err, cudaMemcpyAsync(ctx->group.d.cons, cons_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice,
                                           ctx->stream));
