@@ -247,7 +247,8 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b);
  * partner, a has no particles, or the pair has its curve already;
  * FPPG_ERR_OOM.  On an error a keeps its own lines (after a failed
  * particle upload, like fppg_set_particles, no particles).  Extracting
- * features again drops the curve lines. */
+ * features again drops the curve lines (their particles are then left
+ * without a line: extract the features first, then add the curves). */
 int fppg_boolean_curve(fppg_ctx *a, fppg_ctx *b, int64_t *n_added);
 /* The intersection-curve points of ctx (FP32 xyz, the vertices after the
  * mesh's own) into xyz_host (capacity cap points, nullable); *n receives

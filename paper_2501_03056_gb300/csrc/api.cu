@@ -276,6 +276,9 @@ int fppg_extract_features(fppg_ctx *ctx, float dihedral_deg, int64_t *n_edges) {
     if (!ctx) return FPPG_ERR_ARG;
     if (!std::isfinite(dihedral_deg)) return fail(ctx->err, FPPG_ERR_ARG, "dihedral_deg must be finite");
     int r = ctx->body.extract_features(dihedral_deg, ctx->stream, ctx->err);
+    // the lines are rebuilt from the feature edges alone: intersection-curve
+    // lines are gone (fppg_boolean_curve adds them again)
+    for (fppg_ctx::BoolRel &rel : ctx->rels) rel.curve_lo = rel.curve_hi = 0;
     if (r) {
         // the group must not keep a view of feature segments that are gone
         const std::string msg = ctx->err;
