@@ -87,6 +87,7 @@ def lib():
                 "oracle_boolean_keep": (None, [vp, vp, C.c_int, C.c_int, P(i32)]),
                 "oracle_boolean_relax": (C.c_int, [vp, vp, C.c_int, i32]),
                 "oracle_boolean_relax_many": (C.c_int, [C.POINTER(vp), i32, P(i32), i32, i32]),
+                "oracle_set_cell_order": (C.c_int, [vp, i32]),
                 "oracle_relax_energy": (C.c_int, [vp, i32]),
                 "oracle_last_iteration": (None, [vp, P(f64), P(f64), P(i64)]),
                 "oracle_w0": (None, [vp, P(f64)]),
@@ -320,6 +321,12 @@ class Oracle:
         out = np.zeros((max(m, 1), 3), np.float32)
         lib().oracle_curve_points(self._c, _p(out, C.c_float), m)
         return out[:m]
+
+    def set_cell_order(self, order: int):
+        """Order of the grid rows in the cell key: 0 row-major, 1 Morton
+        order of (y, z) (Eq. 9); forces and steps do not depend on it."""
+        if lib().oracle_set_cell_order(self._c, int(order)) != 0:
+            raise ValueError("unknown cell order, or a grid of more than 2^26 rows")
 
     def set_ghost_count(self, n_ghost):
         """The last n_ghost particles are ghosts (act on neighbours, never move)."""

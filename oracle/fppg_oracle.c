@@ -100,6 +100,8 @@ typedef struct {
     int64_t *pair_key; /* sorted (cell key, triangle) pairs = C_compact   */
     int32_t *pair_tri;
     /* neighbour grid, cell = 2h (1 + 2^-8) */
+    int32_t cell_order;   /* 0: rows y + ny z in order; 1: rows in Morton order (row_rank) */
+    uint32_t *row_rank;   /* [ny * nz] place of row y + ny z in the Morton order of (y, z) */
     float ng_o[3];
     float ng_inv;
     float ng_cell;
@@ -498,6 +500,7 @@ static void free_features(or_ctx *c)
 void oracle_destroy(or_ctx *c)
 {
     if (!c) return;
+    free(c->row_rank);
     free(c->split_acc);
     free(c->V);
     free(c->Vf);
@@ -930,9 +933,68 @@ static int32_t fine_coord(float x, float o, float inv, int32_t n)
     return (int32_t)t;
 }
 
+/* Cell index of the key: x + nx * row, where row = y + ny z (row-major) or
+ * its place in the Morton order of Eq. 9 over (y, z) (cell_order 1); x is
+ * the fastest axis inside a row either way. */
 static uint32_t cell_index(const or_ctx *c, const int32_t *ci)
 {
-    return (uint32_t)ci[0] + (uint32_t)c->ng_n[0] * ((uint32_t)ci[1] + (uint32_t)c->ng_n[1] * (uint32_t)ci[2]);
+    uint32_t row = (uint32_t)ci[1] + (uint32_t)c->ng_n[1] * (uint32_t)ci[2];
+    if (c->cell_order) row = c->row_rank[row];
+    return (uint32_t)ci[0] + (uint32_t)c->ng_n[0] * row;
+}
+
+/* Morton code of Eq. 9 over (y, z): bit b of y at position 2b, bit b of z
+ * at position 2b + 1 */
+static uint64_t morton_yz(uint32_t y, uint32_t z)
+{
+    uint64_t m = 0;
+    for (int b = 0; b < 32; b++) {
+        m |= (uint64_t)((y >> b) & 1u) << (2 * b);
+        m |= (uint64_t)((z >> b) & 1u) << (2 * b + 1);
+    }
+    return m;
+}
+
+typedef struct {
+    uint64_t code;
+    uint32_t row;
+} or_rowcode;
+
+static int rowcode_cmp(const void *pa, const void *pb)
+{
+    const or_rowcode *a = pa, *b = pb;
+    return a->code < b->code ? -1 : (a->code > b->code);
+}
+
+/* the rank table of the grid's rows (NULL for more than 2^26 rows) */
+static uint32_t *morton_rank_table(const int32_t *ng_n)
+{
+    const int64_t m = (int64_t)ng_n[1] * ng_n[2];
+    if (m > ((int64_t)1 << 26)) return NULL;
+    or_rowcode *rc = malloc(sizeof(or_rowcode) * (size_t)(m ? m : 1));
+    for (int32_t z = 0; z < ng_n[2]; z++)
+        for (int32_t y = 0; y < ng_n[1]; y++) {
+            const uint32_t r = (uint32_t)y + (uint32_t)ng_n[1] * (uint32_t)z;
+            rc[r].code = morton_yz((uint32_t)y, (uint32_t)z);
+            rc[r].row = r;
+        }
+    qsort(rc, (size_t)m, sizeof(or_rowcode), rowcode_cmp);
+    uint32_t *rank = malloc(sizeof(uint32_t) * (size_t)(m ? m : 1));
+    for (int64_t q = 0; q < m; q++) rank[rc[q].row] = (uint32_t)q;
+    free(rc);
+    return rank;
+}
+
+/* 0 on success, -1 for an unknown order or a grid of more than 2^26 rows */
+int oracle_set_cell_order(or_ctx *c, int32_t order)
+{
+    if (order != 0 && order != 1) return -1;
+    if (order == 1 && !c->row_rank) {
+        c->row_rank = morton_rank_table(c->ng_n);
+        if (!c->row_rank) return -1;
+    }
+    c->cell_order = order;
+    return 0;
 }
 
 static uint32_t key_of(const or_ctx *c, const double *x)
@@ -2077,6 +2139,17 @@ int oracle_boolean_relax_many(or_ctx *const *b, int32_t nb, const int32_t *pairs
                 bbmax[k] = fmaxf(bbmax[k], b[q]->Vf[3 * i + k]);
             }
     grid_setup(bbmin, bbmax, b[0]->ng_cell, 1.0, 1, g.ng_o, &g.ng_inv, g.ng_n);
+    g.row_rank = g.cell_order ? morton_rank_table(g.ng_n) : NULL;   /* the assembly grid's own table */
+    if (g.cell_order && !g.row_rank) {
+        free(X);
+        free(acc);
+        free(cls);
+        free(part);
+        free(srule);
+        free(vrule);
+        free(npart);
+        return -1;
+    }
     for (int32_t it = 0; it < n_iter; it++) {
         int64_t off = 0;
         for (int32_t q = 0; q < nb; q++) {
@@ -2096,6 +2169,7 @@ int oracle_boolean_relax_many(or_ctx *const *b, int32_t nb, const int32_t *pairs
             off += b[q]->n;
         }
     }
+    free(g.row_rank);
     free(X);
     free(acc);
     free(cls);
