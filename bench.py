@@ -81,8 +81,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip plain / e2e / CPU legs")
     p.add_argument("--no-autotune", action="store_true", help="keep the default kernel configuration")
     p.add_argument("--config", default=None,
-                   help="force variant,block,search CTAs per SM[,incremental order 0/1] (e.g. 0,128,4,1) instead "
-                        "of the autotuner")
+                   help="force variant,block,search CTAs per SM[,incremental order 0/1[,row order 0/1]] "
+                        "(e.g. 0,128,4,1) instead of the autotuner")
     return p.parse_args()
 
 
@@ -317,6 +317,9 @@ def main():
             if len(vals) > 3:
                 batch.set_incremental(bool(vals[3]))
                 tuned["incremental_order"] = vals[3]
+            if len(vals) > 4:
+                batch.set_cell_order(vals[4])
+                tuned["cell_order"] = vals[4]
         else:
             tuned = batch.autotune(G) if tune else None     # trials as long as a timed step
         batch.set_graph_iters(G)

@@ -380,14 +380,15 @@ int fppg_batch_load(fppg_batch *b);
  * or -- search CTAs 0 -- one thread per queued particle on 16 CTAs per SM;
  * then, with the fastest of those, the two ways of ordering the cell keys
  * (a full stable sort, or the incremental repair of the previous order,
- * fppg_batch_set_incremental), keeps the fastest and restores the particle
+ * fppg_batch_set_incremental), then the two orders of the grid rows
+ * (fppg_batch_set_cell_order), keeps the fastest and restores the particle
  * state afterwards.  The choice is cached per (particle-count bucket,
  * volume-particle share, GPU name) for the life of the process; a cached
  * choice is applied without timing.  Outputs (nullable): chosen variant,
- * block size, search CTAs, ordering (1 incremental) and the measured ms per
- * iteration (0 when taken from the cache). */
+ * block size, search CTAs, ordering (1 incremental), row order and the
+ * measured ms per iteration (0 when taken from the cache). */
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
-                        int32_t *incremental, double *ms_per_iter);
+                        int32_t *incremental, int32_t *cell_order, double *ms_per_iter);
 /* How the cell keys are put in order every iteration (Sec. 3.1.3): 0 a full
  * stable radix sort of every key; 1 the previous order repaired -- the
  * particles whose key changed since the last grid build are sorted alone and
@@ -399,6 +400,29 @@ int fppg_batch_set_incremental(fppg_batch *b, int32_t incremental);
 /* The same for the single body of a handle (its fppg_relax, fppg_stats and
  * debug calls); a body of at least 2^21 particles starts incremental. */
 int fppg_set_incremental(fppg_ctx *ctx, int32_t incremental);
+/* Order of the neighbour grid's rows in the cell key (Sec. 3.1.3 sorts
+ * particles by cell; Eq. 9 gives the Morton code of a cell):
+ *   FPPG_ORDER_ROWS          key cell = x + nx (y + ny z) (row-major, default)
+ *   FPPG_ORDER_MORTON_ROWS   key cell = x + nx rank(y, z), rank = the place
+ *                            of row (y, z) in the order of its Morton code
+ *                            (Eq. 9 over y and z: the bits interleaved, z's
+ *                            above y's at every level)
+ * x stays the fastest axis inside a row in both, so every grid row is one
+ * range of keys (the force pass cuts each row to the x-slabs in reach); a
+ * full 3-D Morton key would split a row into many ranges.  Both orders give
+ * the same neighbours in the same order (each particle sums its rows in
+ * stencil order and every row in x order), so the forces agree up to the
+ * FP32 rounding of the two partial sums a row's slots are split between
+ * (by the parity of their absolute position); the keys and the permutation
+ * follow the order.  The rank table of every grid is built on first use
+ * (FPPG_ERR_ARG above 2^26 rows).  The previous order of the keys is
+ * forgotten.  fppg_set_cell_order for the body of a handle,
+ * fppg_batch_set_cell_order for a batch (bodies of a batch take the
+ * batch's order). */
+#define FPPG_ORDER_ROWS 0
+#define FPPG_ORDER_MORTON_ROWS 1
+int fppg_set_cell_order(fppg_ctx *ctx, int32_t order);
+int fppg_batch_set_cell_order(fppg_batch *b, int32_t order);
 /* fppg_set_mobile_classes for every body of the batch (a captured graph
  * keeps working: the mask is read from device memory). */
 int fppg_batch_set_mobile_classes(fppg_batch *b, int32_t mask);

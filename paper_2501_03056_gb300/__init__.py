@@ -89,9 +89,11 @@ def lib():
                 "fppg_batch_store": [vp],
                 "fppg_batch_time_force": [vp, i32],
                 "fppg_batch_force_ms": [vp, P_(f64)],
-                "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(i32), P_(f64)],
+                "fppg_batch_autotune": [vp, i32, P_(i32), P_(i32), P_(i32), P_(i32), P_(i32), P_(f64)],
                 "fppg_batch_set_incremental": [vp, i32],
                 "fppg_set_incremental": [vp, i32],
+                "fppg_set_cell_order": [vp, i32],
+                "fppg_batch_set_cell_order": [vp, i32],
                 "fppg_set_ghost_count": [vp, i64],
                 "fppg_relax_forces": [vp, P_(f32)],
                 "fppg_relax_step": [vp, f32],
@@ -211,6 +213,10 @@ class Body:
         """Order the keys by repairing the previous order (True) or by a full
         stable sort (False); both give the same bits."""
         self._chk(lib().fppg_set_incremental(self._h, int(bool(on))))
+
+    def set_cell_order(self, order: int):
+        """Order of the grid rows in the cell key (fppg_set_cell_order)."""
+        self._chk(lib().fppg_set_cell_order(self._h, int(order)))
 
     def set_fixed_features(self, fixed: bool):
         self._chk(lib().fppg_set_fixed_features(self._h, int(bool(fixed))))
@@ -380,6 +386,7 @@ def device_sm_count() -> int:
 
 
 UNION, DIFFERENCE, INTERSECTION = 0, 1, 2
+ORDER_ROWS, ORDER_MORTON_ROWS = 0, 1
 
 
 def boolean(a: "Body", b: "Body", op: int) -> tuple[int, int]:
@@ -473,11 +480,17 @@ class Batch:
     def autotune(self, iters: int = 5) -> dict:
         """Pick force variant, block size and search grid by timing; the state
         is restored afterwards."""
-        v, tb, sc, inc, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        v, tb, sc, inc, co, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
         self._chk(lib().fppg_batch_autotune(self._h, int(iters), C.byref(v), C.byref(tb), C.byref(sc),
-                                            C.byref(inc), C.byref(ms)))
+                                            C.byref(inc), C.byref(co), C.byref(ms)))
         return {"force_variant": v.value, "force_block": tb.value, "search_ctas_per_sm": sc.value,
-                "incremental_order": inc.value, "ms_per_iter": ms.value}
+                "incremental_order": inc.value, "cell_order": co.value, "ms_per_iter": ms.value}
+
+    def set_cell_order(self, order: int):
+        """Order of the grid rows in the cell key: ORDER_ROWS (row-major) or
+        ORDER_MORTON_ROWS (Eq. 9 over y, z); the same neighbours in the same
+        order either way (forces equal up to FP32 rounding)."""
+        self._chk(lib().fppg_batch_set_cell_order(self._h, int(order)))
 
     def set_incremental(self, on: bool):
         """Order the keys by repairing the previous order (True) or by a full

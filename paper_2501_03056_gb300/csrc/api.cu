@@ -168,6 +168,7 @@ int ctx_group(fppg_ctx *c) {
     g.hp.assign(1, make_params(c->body, 0u, 0, (int)c->n, c->fixed_features));
     g.hp[0].mobile = c->mobile_mask;
     g.hp[0].cascade = c->cascade;
+    if (g.cell_order) g.hp[0].row_rank = g.d.row_rank;   // the body's table (fppg_set_cell_order)
     g.mesh = view_of(c->body);
     const int r = g.upload_params(c->stream, c->err);
     return r == 0 ? FPPG_OK : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
@@ -269,6 +270,15 @@ int fppg_set_projection_rule(fppg_ctx *ctx, int32_t rule) {
     if (rule != FPPG_PROJECT_CLOSEST && rule != FPPG_PROJECT_CASCADE)
         return fail(ctx->err, FPPG_ERR_ARG, "unknown projection rule");
     ctx->cascade = rule == FPPG_PROJECT_CASCADE ? 1 : 0;
+    return ctx_group(ctx);
+}
+
+int fppg_set_cell_order(fppg_ctx *ctx, int32_t order) {
+    if (!ctx) return FPPG_ERR_ARG;
+    if (order != FPPG_ORDER_ROWS && order != FPPG_ORDER_MORTON_ROWS)
+        return fail(ctx->err, FPPG_ERR_ARG, "unknown cell order");
+    const int r = ctx->group.set_cell_order(order, ctx->stream, ctx->err);
+    if (r) return r == 1 ? FPPG_ERR_ARG : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
     return ctx_group(ctx);
 }
 
@@ -1114,7 +1124,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int variant, block, search_ctas, incremental;
+    int variant, block, search_ctas, incremental, cell_order;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -1128,7 +1138,7 @@ static void set_ordering(Group &g, bool incremental, cudaStream_t s) {
 }
 
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
-                        int32_t *incremental, double *ms_per_iter) {
+                        int32_t *incremental, int32_t *cell_order, double *ms_per_iter) {
     if (!b || iters <= 0 || iters > 10000) return FPPG_ERR_ARG;
     Group &g = b->group;
     DevGroup &d = g.d;
@@ -1145,7 +1155,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     while ((int64_t)1 << (nb + 1) <= std::max<int64_t>(d.N, 1)) nb++;
     const TuneKey key{nb, d.N ? (int)(10 * nv / d.N) : 0, prop.name};
     TuneVal best{g.force_variant, g.force_block, g.search_thread ? 0 : g.search_blocks / std::max(sms, 1),
-                 d.incremental ? 1 : 0};
+                 d.incremental ? 1 : 0, g.cell_order};
     double best_ms = 0.0;
     bool cached = false;
     {
@@ -1173,12 +1183,16 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
         g.time_force = false;
         best_ms = 1e30;
         // one trial: the state restored, one untimed iteration, `iters` timed
-        auto trial = [&](int v, int tb, int sc, int inc, float *ms) -> int {
+        auto trial = [&](int v, int tb, int sc, int inc, int co, float *ms) -> int {
             g.force_variant = v;
             g.force_block = tb;
             g.search_thread = sc == 0;
             g.search_blocks = (sc == 0 ? 16 : sc) * sms;
             set_ordering(g, inc != 0, s);
+            if (co != g.cell_order) {
+                const int r = g.set_cell_order(co, s, b->err);
+                if (r) return r == 1 ? FPPG_ERR_ARG : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
+            }
             CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
             CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
             iterate(g, s, false);
@@ -1189,14 +1203,14 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
             CUDA_OR(b->err, cudaEventElapsedTime(ms, e0, e1));
             return FPPG_OK;
         };
-        const int inc0 = best.incremental;
-        auto consider = [&](int v, int tb, int sc, int inc) -> int {
+        const int inc0 = best.incremental, co0 = best.cell_order;
+        auto consider = [&](int v, int tb, int sc, int inc, int co) -> int {
             float ms = 0.f;
-            const int r = trial(v, tb, sc, inc, &ms);
+            const int r = trial(v, tb, sc, inc, co, &ms);
             if (r) return r;
             if (ms / iters < best_ms) {
                 best_ms = ms / iters;
-                best = TuneVal{v, tb, sc, inc};
+                best = TuneVal{v, tb, sc, inc, co};
             }
             return FPPG_OK;
         };
@@ -1204,21 +1218,17 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
         // per SM, then the search grid with the fastest force kernel
         for (int v = 0; v < 2; v++)
             for (int tb : {128, 256})
-                if (const int r = consider(v, tb, 4, inc0)) return r;
+                if (const int r = consider(v, tb, 4, inc0, co0)) return r;
         {
             const int v = best.variant, tb = best.block;
             for (int sc : {0, 8, 16})   // 0: one thread per queued particle
-                if (const int r = consider(v, tb, sc, inc0)) return r;
+                if (const int r = consider(v, tb, sc, inc0, co0)) return r;
         }
-        {   // the other ordering with the fastest kernels
-            float ms = 0.f;
-            const int r = trial(best.variant, best.block, best.search_ctas, 1 - inc0, &ms);
-            if (r) return r;
-            if (ms / iters < best_ms) {
-                best_ms = ms / iters;
-                best.incremental = 1 - inc0;
-            }
-        }
+        // the other ordering of the keys, then the other order of the grid
+        // rows, with the fastest kernels
+        if (const int r = consider(best.variant, best.block, best.search_ctas, 1 - inc0, co0)) return r;
+        if (const int r = consider(best.variant, best.block, best.search_ctas, best.incremental, 1 - co0))
+            if (r != FPPG_ERR_ARG) return r;   // a grid too large for the Morton table keeps row-major rows
         g.time_force = tf;
         CUDA_OR(b->err, cudaMemcpyAsync(d.pos, pos0, sizeof(float4) * d.N, cudaMemcpyDeviceToDevice, s));
         CUDA_OR(b->err, cudaMemcpyAsync(d.cons, cons0, sizeof(int32_t) * d.N, cudaMemcpyDeviceToDevice, s));
@@ -1235,6 +1245,10 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     g.search_thread = best.search_ctas == 0;
     g.search_blocks = (best.search_ctas == 0 ? 16 : best.search_ctas) * sms;
     set_ordering(g, best.incremental != 0, s);
+    if (best.cell_order != g.cell_order) {
+        const int r = g.set_cell_order(best.cell_order, s, b->err);
+        if (r) return r == 1 ? FPPG_ERR_ARG : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
+    }
     if (g.graph) {
         cudaGraphExecDestroy(g.graph);
         g.graph = nullptr;
@@ -1243,6 +1257,7 @@ int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t 
     if (block) *block = best.block;
     if (search_ctas) *search_ctas = best.search_ctas;
     if (incremental) *incremental = best.incremental;
+    if (cell_order) *cell_order = best.cell_order;
     if (ms_per_iter) *ms_per_iter = cached ? 0.0 : best_ms;
     return FPPG_OK;
 }
@@ -1308,6 +1323,13 @@ int fppg_batch_set_incremental(fppg_batch *b, int32_t incremental) {
         g.graph = nullptr;
     }
     CUDA_OR(b->err, cudaGetLastError());
+    return FPPG_OK;
+}
+
+int fppg_batch_set_cell_order(fppg_batch *b, int32_t order) {
+    if (!b || (order != FPPG_ORDER_ROWS && order != FPPG_ORDER_MORTON_ROWS)) return FPPG_ERR_ARG;
+    const int r = b->group.set_cell_order(order, b->stream, b->err);
+    if (r) return r == 1 ? FPPG_ERR_ARG : (r == 3 ? FPPG_ERR_OOM : FPPG_ERR_CUDA);
     return FPPG_OK;
 }
 

@@ -219,6 +219,30 @@ AsmParams make_params(const Body &b, uint32_t key_base, int p_begin, int p_end, 
     return A;
 }
 
+// the bits of v moved to the even bit positions
+static uint64_t spread_even(uint32_t v) {
+    uint64_t x = v;
+    x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+    x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+    x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+
+void morton_row_ranks(int ny, int nz, std::vector<uint32_t> &rank) {
+    const int64_t m = (int64_t)ny * nz;
+    std::vector<std::pair<uint64_t, uint32_t>> code((size_t)m);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++) {
+            const uint32_t r = (uint32_t)y + (uint32_t)ny * (uint32_t)z;
+            code[r] = {spread_even((uint32_t)y) | (spread_even((uint32_t)z) << 1), r};
+        }
+    std::sort(code.begin(), code.end());
+    rank.resize((size_t)m);
+    for (int64_t q = 0; q < m; q++) rank[code[(size_t)q].second] = (uint32_t)q;
+}
+
 #define CKA(x)                                                                  \
     do {                                                                        \
         cudaError_t e_ = (x);                                                   \
@@ -369,6 +393,42 @@ int Group::upload_params(cudaStream_t s, std::string &err) {
     return 0;
 }
 
+int Group::set_cell_order(int order, cudaStream_t s, std::string &err) {
+    if (order && !d.row_rank) {
+        // one table per grid: a body shares the grid (and the table) of the
+        // first body with its key base (the members of a Boolean assembly)
+        std::vector<uint32_t> all, t;
+        row_off.assign(hp.size(), 0);
+        for (size_t i = 0; i < hp.size(); i++) {
+            size_t owner = i;
+            for (size_t j = 0; j < i; j++)
+                if (hp[j].key_base == hp[i].key_base) {
+                    owner = j;
+                    break;
+                }
+            if (owner != i) {
+                row_off[i] = row_off[owner];
+                continue;
+            }
+            const int64_t rows = (int64_t)hp[i].ng_n[1] * hp[i].ng_n[2];
+            if (rows > ((int64_t)1 << 26) || (int64_t)all.size() + rows > ((int64_t)1 << 28)) {
+                err = "the Morton row order supports grids of at most 2^26 rows";
+                return 1;
+            }
+            row_off[i] = (int64_t)all.size();
+            morton_row_ranks(hp[i].ng_n[1], hp[i].ng_n[2], t);
+            all.insert(all.end(), t.begin(), t.end());
+        }
+        CKA(dev_malloc(&d.row_rank, sizeof(uint32_t) * std::max<size_t>(all.size(), 1)));
+        CKA(cudaMemcpyAsync(d.row_rank, all.data(), sizeof(uint32_t) * all.size(), cudaMemcpyHostToDevice, s));
+    }
+    cell_order = order;
+    d.morton_rows = order != 0;
+    for (size_t i = 0; i < hp.size(); i++) hp[i].row_rank = order ? d.row_rank + row_off[i] : nullptr;
+    invalidate_order(s);
+    return upload_params(s, err);
+}
+
 void Group::free_all() {
     escr.release();
     if (graph) cudaGraphExecDestroy(graph);
@@ -378,7 +438,7 @@ void Group::free_all() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     ev.clear();
     DevGroup &g = d;
-    void *ptrs[] = {g.params, g.pos, g.cons, g.cons_s, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
+    void *ptrs[] = {g.params, g.row_rank, g.pos, g.cons, g.cons_s, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
                     g.acc_s, g.fstart, g.fcount, g.scan_tmp, g.amax, g.maxdisp, g.hist, g.totals, g.coef_s, g.work,
                     g.work_count};
     for (void *p : ptrs)

@@ -117,6 +117,11 @@ struct Group {
     bool search_thread = false;   // one thread (not one warp) per queued particle
     int force_block = 256;        // threads per block of the force kernel (multiple of 32, <= 256)
     int force_variant = 0;        // 0 per-lane rows, 1 shared-row union
+    // order of the neighbour grid's rows: 0 row-major, 1 Morton (Eq. 9 over
+    // (y, z)); the rank tables of every grid live in d.row_rank, body i's at
+    // row_off[i]
+    int cell_order = 0;
+    std::vector<int64_t> row_off;
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     cudaStream_t graph_stream = nullptr;
@@ -130,9 +135,17 @@ struct Group {
     // when the incremental ordering is switched on
     void invalidate_order(cudaStream_t s);
     int upload_params(cudaStream_t s, std::string &err);
+    // the rank tables of the grids of hp (built once), then every body's
+    // parameters pointed at its table (order 1) or at none (order 0); the
+    // previous order of the keys is forgotten.  Uploads the parameters.
+    int set_cell_order(int order, cudaStream_t s, std::string &err);
     void free_all();
     ~Group() { free_all(); }
 };
+
+// rank[y + ny z] of every grid row in the Morton order of Eq. 9 over (y, z):
+// the bits of y and z interleaved, z's above y's at every level
+void morton_row_ranks(int ny, int nz, std::vector<uint32_t> &rank);
 
 // groups of at least this many particles start with the incremental ordering
 constexpr int64_t kIncrementalMinN = 1 << 21;

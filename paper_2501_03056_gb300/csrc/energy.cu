@@ -63,7 +63,7 @@ __device__ inline void for_row_ranges(const float4 &p, bool on, const AsmParams 
             const int y = cy + dy;
             uint32_t s = 0xffffffffu, e = 0u;
             if (on && z >= 0 && z < nz && y >= 0 && y < ny) {
-                const uint32_t row = A.key_base + (uint32_t)A.ng_n[0] * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+                const uint32_t row = A.key_base + (uint32_t)A.ng_n[0] * grid_row(A, y, z);
                 row_slots(A, fstart, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
             }
             f(s, e);

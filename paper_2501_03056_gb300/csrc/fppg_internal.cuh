@@ -106,6 +106,10 @@ struct AsmParams {
     int curve_lo[kMaxPartners], curve_hi[kMaxPartners];
     int vol_rules;     // some partner has a volume rule
     int amax_slot;     // body whose amax / time step this body shares (itself, or its assembly's first body)
+    // order of the neighbour grid's rows (y, z): null for row-major
+    // (y + ny z), else the rank of each row y + ny z in the Morton order of
+    // Eq. 9 restricted to (y, z); x stays the fastest axis inside a row
+    const uint32_t *row_rank;
     int p_begin, p_end;
 };
 
@@ -135,6 +139,8 @@ struct DevGroup {
     int n_tiles = 0;
     int nt = 0, nv = 0, nseg = 0, nlines = 0;
     AsmParams *params = nullptr;
+    uint32_t *row_rank = nullptr;  // Morton ranks of the grid rows of every grid of the group (null: row-major)
+    bool morton_rows = false;      // the parameters point at row_rank (the order in force)
     // particles
     float4 *pos = nullptr;
     int32_t *cons = nullptr;
@@ -247,6 +253,19 @@ inline float slab_reach2(float R2, float inv) {
 // A particle's place in the grid: unclamped cell coordinates t, clamped
 // cells c and the slack (cell units) that covers the FP32 rounding of t and
 // of the reach arithmetic (relative errors of a few 2^-24 of |t|).
+// index of grid row (y, z) in key order: row-major, or its Morton rank
+__device__ inline uint32_t grid_row(const AsmParams &A, int y, int z) {
+    const uint32_t r = (uint32_t)y + (uint32_t)A.ng_n[1] * (uint32_t)z;
+    return A.row_rank ? A.row_rank[r] : r;
+}
+
+// the same with the order fixed at compile time (the force pass)
+template <bool MORTON>
+__device__ inline uint32_t grid_row_of(const AsmParams &A, int y, int z) {
+    const uint32_t r = (uint32_t)y + (uint32_t)A.ng_n[1] * (uint32_t)z;
+    return MORTON ? A.row_rank[r] : r;
+}
+
 struct GridPoint {
     float t[3];
     int c[3];

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
     const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
     const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
     key[i] = kSlabs * A.key_base + (uint32_t)fx +
-             kSlabs * (uint32_t)A.ng_n[0] * ((uint32_t)cy + (uint32_t)A.ng_n[1] * (uint32_t)cz);
+             kSlabs * (uint32_t)A.ng_n[0] * grid_row(A, cy, cz);
 }
 
 // ---- A1-A2, incremental form ---------------------------------------------------
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(TPB) k_keys_inc(const float4 *__restrict__ pos
     const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
     const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
     const uint32_t k = kSlabs * A.key_base + (uint32_t)fx +
-                       kSlabs * (uint32_t)A.ng_n[0] * ((uint32_t)cy + (uint32_t)A.ng_n[1] * (uint32_t)cz);
+                       kSlabs * (uint32_t)A.ng_n[0] * grid_row(A, cy, cz);
     const uint32_t old = key_id[i];
     chg[i] = k != old ? 1u : 0u;
     if (k != old) key_id[i] = k;
@@ -424,7 +424,7 @@ __device__ inline void force_range2(const float4 *__restrict__ pos_p, const floa
     pair_step<ALL, COUNT, true>(pos_p, pos_b, m1 - 1, s, e, npx, npy, npz, mbits, R2, hih, acc, self);
 }
 
-template <int VARIANT, bool COUNT>
+template <int VARIANT, bool COUNT, bool MORTON>
 // (at most 48 registers: five 256-thread blocks per SM)
 __global__ void __launch_bounds__(TPB, 5)
     k_force(const float4 *__restrict__ pos_s, const float4 *__restrict__ pos_p, int64_t N,
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(TPB, 5)
     if (VARIANT == 1) {
         const uint32_t mover = __ballot_sync(0xffffffffu, mbits != 0u);
         const int leader = mover ? __ffs(mover) - 1 : 0;
-        const uint32_t rowkey = A.key_base + (uint32_t)nx * ((uint32_t)cy + (uint32_t)ny * (uint32_t)cz);
+        const uint32_t rowkey = A.key_base + (uint32_t)nx * grid_row_of<MORTON>(A, cy, cz);
         const uint32_t lead_row = __shfl_sync(0xffffffffu, rowkey, leader);
         shared_row = __all_sync(0xffffffffu, mbits == 0u || rowkey == lead_row);
     }
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(TPB, 5)
             const int y = cy + dy;
             uint32_t s = 0xffffffffu, e = 0u;
             if (mbits && z >= 0 && z < nz && y >= 0 && y < ny) {
-                const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+                const uint32_t row = A.key_base + (uint32_t)nx * grid_row_of<MORTON>(A, y, z);
                 row_slots(A, fstart, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
             }
             if (COUNT && e > s) tested += (int)(e - s);
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(TPB) k_count(const float4 *__restrict__ pos_s,
     int cnt = 0, cand = 0;
     for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
         for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
-            const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+            const uint32_t row = A.key_base + (uint32_t)nx * grid_row(A, y, z);
             uint32_t s, e;
             cells_slots(fstart, row, max(cx - 1, 0), min(cx + 1, nx - 1), s, e);
             if (e > s) cand += (int)(e - s);
@@ -1329,7 +1329,7 @@ __global__ void __launch_bounds__(TPB) k_density(const float4 *__restrict__ pos_
     float rho = 0.f, rmin2 = FLT_MAX;
     for (int z = max(cz - 1, 0); z <= min(cz + 1, nz - 1); z++)
         for (int y = max(cy - 1, 0); y <= min(cy + 1, ny - 1); y++) {
-            const uint32_t row = A.key_base + (uint32_t)nx * ((uint32_t)y + (uint32_t)ny * (uint32_t)z);
+            const uint32_t row = A.key_base + (uint32_t)nx * grid_row(A, y, z);
             uint32_t s, e;
             cells_slots(fstart, row, max(cx - 1, 0), min(cx + 1, nx - 1), s, e);
             for (uint32_t j = s; j < e; j++) {
@@ -1417,14 +1417,23 @@ int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
 
 void forces_dev(DevGroup &d, int tb, int variant, cudaStream_t s, int32_t *count_s, int32_t *tested_s) {
     const unsigned nbk = (unsigned)std::max<int64_t>((d.N + tb - 1) / tb, 1);
-#define FPPG_FORCE(V, C)                                                                                       \
-    k_force<V, C><<<nbk, tb, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.fstart, d.acc_s, d.amax, count_s, tested_s)
-    if (count_s) {
-        if (variant == 1) FPPG_FORCE(1, true);
-        else FPPG_FORCE(0, true);
+#define FPPG_FORCE(V, C, M)                                                                                    \
+    k_force<V, C, M><<<nbk, tb, 0, s>>>(d.pos_s, d.pos_p, d.N, d.params, d.fstart, d.acc_s, d.amax, count_s,        \
+                                        tested_s)
+    if (d.morton_rows) {
+        if (count_s) {
+            if (variant == 1) FPPG_FORCE(1, true, true);
+            else FPPG_FORCE(0, true, true);
+        } else {
+            if (variant == 1) FPPG_FORCE(1, false, true);
+            else FPPG_FORCE(0, false, true);
+        }
+    } else if (count_s) {
+        if (variant == 1) FPPG_FORCE(1, true, false);
+        else FPPG_FORCE(0, true, false);
     } else {
-        if (variant == 1) FPPG_FORCE(1, false);
-        else FPPG_FORCE(0, false);
+        if (variant == 1) FPPG_FORCE(1, false, false);
+        else FPPG_FORCE(0, false, false);
     }
 #undef FPPG_FORCE
 }
