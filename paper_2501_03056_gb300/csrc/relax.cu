@@ -661,6 +661,37 @@ __device__ inline bool surface_candidate(const MeshView &M, const AsmParams &A, 
     return true;
 }
 
+// The same decision, with every edge evaluated: *emin gets the smallest
+// in-plane edge distance of the foot (negative outside), so a triangle that
+// is not projectable at y stays so within -emin - edge_tol of y (the edge
+// distances are 1-Lipschitz in y: unit in-plane edge normals)
+__device__ inline bool surface_candidate_margin(const MeshView &M, const AsmParams &A, int t, float3 y, float &d,
+                                                float &emin) {
+    const float4 *g = M.geo + 5 * (size_t)(A.tri_off + t);
+    const float3 u = y - f3(g[0]);
+    const float tol = -A.edge_tol;
+    const float4 m0 = g[2], m1 = g[3], m2 = g[4];
+    const float e0 = dot3(u, f3(m0));
+    const float e1 = dot3(u, f3(m1)) - m1.w;
+    const float e2 = dot3(u, f3(m2)) - m2.w;
+    emin = fminf(e0, fminf(e1, e2));
+    if (e0 < tol || e1 < tol || e2 < tol) return false;
+    d = dot3(u, f3(g[1]));
+    return true;
+}
+
+// Surface certificate (not in the paper; it changes no decision): when
+// exactly one candidate is projectable at y, every other candidate of y's
+// triangle cell stays non-projectable within the smallest -emin - edge_tol
+// over them, so for a trial point in the same cell and within that radius
+// the choice is the particle's own triangle if it is projectable there, and
+// the step takes it without the search.  Radius shrunk by 2^-10 relative and
+// 2^-12 dx for the FP32 rounding of the edge distances; 0: no certificate.
+__device__ inline float surface_cert_radius(const AsmParams &A, int n_projectable, float r_other) {
+    if (n_projectable != 1 || !(r_other < FLT_MAX)) return 0.f;
+    return fmaxf(r_other * (1.f - 0x1p-10f) - A.dx * 0x1p-12f, 0.f);
+}
+
 // closest projectable triangle (smallest |plane distance|, ties to the lower
 // index) among those binned into the 27 cells around y, or into y's own
 // cell alone (own_cell); -1 when none
@@ -715,14 +746,25 @@ __device__ inline void for_27_candidates(const MeshView &M, const AsmParams &A, 
 }
 
 __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist, int32_t *buf,
-                                    bool own_cell = false, const uint2 *pre = nullptr) {
+                                    bool own_cell = false, const uint2 *pre = nullptr, float *cert_r = nullptr) {
     const int lane = threadIdx.x & 31;
     float best = FLT_MAX;
     int bt = 0x7fffffff;
     float bd = 0.f;
+    int nproj = 0;
+    float rother = FLT_MAX;
     auto test = [&](int t) {
         float d;
-        if (!surface_candidate(M, A, t, y, d)) return;
+        if (cert_r) {
+            float emin;
+            if (!surface_candidate_margin(M, A, t, y, d, emin)) {
+                rother = fminf(rother, -emin - A.edge_tol);
+                return;
+            }
+            nproj++;
+        } else if (!surface_candidate(M, A, t, y, d)) {
+            return;
+        }
         const float ad = fabsf(d);
         if (ad < best || (ad == best && t < bt)) {
             best = ad;
@@ -744,6 +786,13 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
     // the signed distance of the winner, from a lane that holds it
     const uint32_t own = __ballot_sync(0xffffffffu, bt == t && best == v);
     dist = __shfl_sync(0xffffffffu, bd, own ? __ffs(own) - 1 : 0);
+    if (cert_r) {
+        const int total = __reduce_add_sync(0xffffffffu, nproj);
+        float r = rother;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fminf(r, __shfl_xor_sync(0xffffffffu, r, o));
+        *cert_r = surface_cert_radius(A, total, r);
+    }
     return t == 0x7fffffff ? -1 : t;
 }
 
@@ -752,7 +801,7 @@ __device__ int warp_project_surface(const MeshView &M, const AsmParams &A, float
 // cascade of Sec. 3.3.3 (still on triangle c: stay; else the closest
 // projectable one of y's own cell; else over the 27 cells).  -1: revert.
 __device__ int warp_surface_choice(const MeshView &M, const AsmParams &A, float3 y, int c, float &dist,
-                                   int32_t *buf, const uint2 *pre = nullptr) {
+                                   int32_t *buf, const uint2 *pre = nullptr, float *cert_r = nullptr) {
     if (A.cascade) {
         if (c >= 0 && c < A.nt) {
             float d = 0.f;
@@ -765,7 +814,7 @@ __device__ int warp_surface_choice(const MeshView &M, const AsmParams &A, float3
         const int t = warp_project_surface(M, A, y, dist, buf, true);
         if (t >= 0) return t;
     }
-    return warp_project_surface(M, A, y, dist, buf, false, pre);
+    return warp_project_surface(M, A, y, dist, buf, false, pre, A.cascade ? nullptr : cert_r);
 }
 
 // distance from y to the faces of the 3 x 3 x 3 triangle-cell block around
@@ -890,7 +939,7 @@ __device__ inline bool near_body(const MeshView &M, const AsmParams &Q, float3 x
 // particles (their own line), volume particles with no triangle in the 27
 // cells (accepted), surface particles with none (reverted).  Every other
 // particle is queued with its trial point for k_search.
-__global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, const float4 *__restrict__ acc_s,
+__global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_s, const float4 *__restrict__ acc_s,
                                               const uint32_t *__restrict__ id_s, int64_t N,
                                               const AsmParams *__restrict__ P, const uint32_t *__restrict__ amax,
                                               float4 *__restrict__ pos, int32_t *__restrict__ cons, MeshView M,
@@ -960,9 +1009,33 @@ __global__ void __launch_bounds__(TPB) k_step(const float4 *__restrict__ pos_s, 
                 const float3 w = y - f3(cc);
                 certified = cc.w > 0.f && sqrtf(dot3(w, w)) + cc.w * 0x1p-6f + A.dx * 0x1p-10f < cc.w;
             }
+            bool surf_cert = false;
+            float3 xs = y;
+            if (cls == kClsS && c >= 0 && c < A.nt && A.npart == 0 && !A.cascade) {
+                // inside a ball where an earlier search found exactly one
+                // projectable candidate of the same triangle cell: the own
+                // triangle is the choice when it is projectable here, and lies
+                // this close (so it is a candidate of this cell)
+                const float4 cc = cert[i];
+                const float3 w = y - f3(cc);
+                if (cc.w < 0.f && sqrtf(dot3(w, w)) < -cc.w &&
+                    tri_key(A, cell_coord(cc.x, A.tg_o[0], A.tg_inv, A.tg_n[0]),
+                            cell_coord(cc.y, A.tg_o[1], A.tg_inv, A.tg_n[1]),
+                            cell_coord(cc.z, A.tg_o[2], A.tg_inv, A.tg_n[2])) == tri_key(A, cx, cy, cz)) {
+                    float d;
+                    if (surface_candidate(M, A, c, y, d) && fabsf(d) <= A.dx * 0x1p-10f) {
+                        surf_cert = true;
+                        xs = y - d * f3(M.geo[5 * (size_t)(A.tri_off + c) + 1]);
+                    }
+                }
+            }
             if (certified) {
                 pos[i] = make_float4(y.x, y.y, y.z, p.w);
                 disp = sqrtf(dot3(dr, dr));
+            } else if (surf_cert) {
+                pos[i] = make_float4(xs.x, xs.y, xs.z, p.w);
+                const float3 w = xs - p3;
+                disp = sqrtf(dot3(w, w));
             } else if (near_partner || test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
                 queue = true;
                 rng = cand_range(M, A, tri_key(A, cx, cy, cz));
@@ -1044,7 +1117,10 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
         bool ok;
         if (cls == kClsS) {
             float d;
-            tri = warp_surface_choice(M, A, y, A.cascade ? cons[id_s[it.x]] : -1, d, buf, &rng);
+            // (a body in a Boolean operation searches every surface particle:
+            // the partner rule is tested on the projection)
+            tri = warp_surface_choice(M, A, y, A.cascade ? cons[id_s[it.x]] : -1, d, buf, &rng,
+                                      A.npart == 0 ? &clear : nullptr);
             ok = tri >= 0;
             if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
         } else if (cls == kClsF) {
@@ -1070,6 +1146,8 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
             pos[i] = make_float4(x.x, x.y, x.z, p.w);
             if (tri >= 0) cons[i] = tri;
             if (cls == kClsV && A.closed && !A.vol_rules) cert[i] = make_float4(y.x, y.y, y.z, clear);
+            // surface certificates carry a negative radius (never taken for an inside one)
+            if (cls == kClsS && clear > 0.f) cert[i] = make_float4(y.x, y.y, y.z, -clear);
             const float3 w = x - f3(p);
             if (b != run_b) {
                 if (run) atomicMax(maxdisp + run_b, run);
@@ -1105,12 +1183,23 @@ __device__ inline void each_27_candidate(const MeshView &M, const AsmParams &A, 
 }
 
 __device__ int thread_project_surface(const MeshView &M, const AsmParams &A, float3 y, float &dist,
-                                      bool own_cell = false, const uint2 *pre = nullptr) {
+                                      bool own_cell = false, const uint2 *pre = nullptr, float *cert_r = nullptr) {
     float best = FLT_MAX, bd = 0.f;
     int bt = 0x7fffffff;
+    int nproj = 0;
+    float rother = FLT_MAX;
     auto test = [&](int t) {
         float d;
-        if (!surface_candidate(M, A, t, y, d)) return;
+        if (cert_r) {
+            float emin;
+            if (!surface_candidate_margin(M, A, t, y, d, emin)) {
+                rother = fminf(rother, -emin - A.edge_tol);
+                return;
+            }
+            nproj++;
+        } else if (!surface_candidate(M, A, t, y, d)) {
+            return;
+        }
         const float ad = fabsf(d);
         if (ad < best || (ad == best && t < bt)) {
             best = ad;
@@ -1125,11 +1214,12 @@ __device__ int thread_project_surface(const MeshView &M, const AsmParams &A, flo
         each_27_candidate(M, A, y, test, pre);
     }
     dist = bd;
+    if (cert_r) *cert_r = surface_cert_radius(A, nproj, rother);
     return bt == 0x7fffffff ? -1 : bt;
 }
 
 __device__ int thread_surface_choice(const MeshView &M, const AsmParams &A, float3 y, int c, float &dist,
-                                     const uint2 *pre = nullptr) {
+                                     const uint2 *pre = nullptr, float *cert_r = nullptr) {
     if (A.cascade) {
         if (c >= 0 && c < A.nt) {
             float d = 0.f;
@@ -1141,7 +1231,7 @@ __device__ int thread_surface_choice(const MeshView &M, const AsmParams &A, floa
         const int t = thread_project_surface(M, A, y, dist, true);
         if (t >= 0) return t;
     }
-    return thread_project_surface(M, A, y, dist, false, pre);
+    return thread_project_surface(M, A, y, dist, false, pre, A.cascade ? nullptr : cert_r);
 }
 
 __device__ int thread_closest_sign(const MeshView &M, const AsmParams &A, float3 y, float &clear,
@@ -1220,7 +1310,8 @@ __global__ void __launch_bounds__(TPB, 4) k_search_thread(const float4 *__restri
             bool ok;
             if (cls == kClsS) {
                 float d;
-                tri = thread_surface_choice(M, A, y, A.cascade ? cons[i] : -1, d, &rng);
+                tri = thread_surface_choice(M, A, y, A.cascade ? cons[i] : -1, d, &rng,
+                                            A.npart == 0 ? &clear : nullptr);
                 ok = tri >= 0;
                 if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
             } else if (cls == kClsF) {
@@ -1238,6 +1329,8 @@ __global__ void __launch_bounds__(TPB, 4) k_search_thread(const float4 *__restri
                 pos[i] = make_float4(x.x, x.y, x.z, p.w);
                 if (tri >= 0) cons[i] = tri;
                 if (cls == kClsV && A.closed && !A.vol_rules) cert[i] = make_float4(y.x, y.y, y.z, clear);
+                // surface certificates carry a negative radius (never taken for an inside one)
+                if (cls == kClsS && clear > 0.f) cert[i] = make_float4(y.x, y.y, y.z, -clear);
                 const float3 w = x - f3(p);
                 disp = sqrtf(dot3(w, w));
             }
