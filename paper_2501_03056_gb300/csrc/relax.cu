@@ -1011,11 +1011,13 @@ __global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_
             }
             bool surf_cert = false;
             float3 xs = y;
-            if (cls == kClsS && c >= 0 && c < A.nt && A.npart == 0 && !A.cascade) {
+            if (cls == kClsS && c >= 0 && c < A.nt && !A.cascade) {
                 // inside a ball where an earlier search found exactly one
                 // projectable candidate of the same triangle cell: the own
                 // triangle is the choice when it is projectable here, and lies
-                // this close (so it is a candidate of this cell)
+                // this close (so it is a candidate of this cell); with no
+                // Boolean partner's triangle near the foot the partner rules
+                // hold as they would in the search
                 const float4 cc = cert[i];
                 const float3 w = y - f3(cc);
                 if (cc.w < 0.f && sqrtf(dot3(w, w)) < -cc.w &&
@@ -1026,6 +1028,8 @@ __global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_
                     if (surface_candidate(M, A, c, y, d) && fabsf(d) <= A.dx * 0x1p-10f) {
                         surf_cert = true;
                         xs = y - d * f3(M.geo[5 * (size_t)(A.tri_off + c) + 1]);
+                        for (int q = 0; q < A.npart && surf_cert; q++)
+                            if (A.partner_surf[q] != 0 && near_body(M, P[A.partner[q]], xs)) surf_cert = false;
                     }
                 }
             }
@@ -1117,10 +1121,7 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
         bool ok;
         if (cls == kClsS) {
             float d;
-            // (a body in a Boolean operation searches every surface particle:
-            // the partner rule is tested on the projection)
-            tri = warp_surface_choice(M, A, y, A.cascade ? cons[id_s[it.x]] : -1, d, buf, &rng,
-                                      A.npart == 0 ? &clear : nullptr);
+            tri = warp_surface_choice(M, A, y, A.cascade ? cons[id_s[it.x]] : -1, d, buf, &rng, &clear);
             ok = tri >= 0;
             if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
         } else if (cls == kClsF) {
@@ -1310,8 +1311,7 @@ __global__ void __launch_bounds__(TPB, 4) k_search_thread(const float4 *__restri
             bool ok;
             if (cls == kClsS) {
                 float d;
-                tri = thread_surface_choice(M, A, y, A.cascade ? cons[i] : -1, d, &rng,
-                                            A.npart == 0 ? &clear : nullptr);
+                tri = thread_surface_choice(M, A, y, A.cascade ? cons[i] : -1, d, &rng, &clear);
                 ok = tri >= 0;
                 if (ok) x = y - d * f3(M.geo[5 * (size_t)(A.tri_off + tri) + 1]);
             } else if (cls == kClsF) {
