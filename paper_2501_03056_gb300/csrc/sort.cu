@@ -59,7 +59,8 @@ __device__ inline uint32_t block_incl_scan(uint32_t v, uint32_t *wsum, uint32_t 
 // counts them per tile in shared memory
 // n_dev (nullable): the item count is read from device memory (at most n),
 // so that a captured graph can sort a list whose length it does not know;
-// tiles past it count nothing and write nothing
+// tiles past it count nothing and write nothing (the digit scan and the
+// downsweep stop at the last tile that holds items)
 template <typename K, int RC, int DB>
 __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int64_t n, int shift,
                                                 uint32_t *__restrict__ hist, int n_tiles,
@@ -67,10 +68,7 @@ __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int6
     constexpr int TILE = RW * RC * 32, ND = 1 << DB;
     __shared__ uint32_t cnt[ND];
     if (n_dev) n = min(n, (int64_t)*n_dev);
-    if ((int64_t)blockIdx.x * TILE >= n) {   // a tile past the count: an empty histogram row
-        for (int d = threadIdx.x; d < ND; d += RT) hist[(int64_t)d * n_tiles + blockIdx.x] = 0u;
-        return;
-    }
+    if ((int64_t)blockIdx.x * TILE >= n) return;   // a tile past the count
     for (int d = threadIdx.x; d < ND; d += RT) cnt[d] = 0;
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -87,17 +85,21 @@ __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int6
     for (int d = threadIdx.x; d < ND; d += RT) hist[(int64_t)d * n_tiles + blockIdx.x] = cnt[d];
 }
 
-// one CTA per digit: exclusive scan of its row of per-tile counts
+// one CTA per digit: exclusive scan of its row of per-tile counts, over the
+// tiles that hold items (n_dev: the item count on the device, else n)
 __global__ void __launch_bounds__(RT) k_digit_scan(uint32_t *__restrict__ hist, int n_tiles,
-                                                   uint32_t *__restrict__ totals) {
+                                                   uint32_t *__restrict__ totals, int64_t n, int tile,
+                                                   const uint32_t *__restrict__ n_dev) {
     __shared__ uint32_t wsum[RW];
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    const int n_act = (int)min((int64_t)n_tiles, (n + tile - 1) / tile);
     uint32_t *row = hist + (int64_t)blockIdx.x * n_tiles;
     uint32_t carry = 0;
-    for (int start = 0; start < n_tiles; start += RT) {
+    for (int start = 0; start < n_act; start += RT) {
         int idx = start + threadIdx.x;
-        uint32_t v = idx < n_tiles ? row[idx] : 0u, tot;
+        uint32_t v = idx < n_act ? row[idx] : 0u, tot;
         uint32_t inc = block_incl_scan(v, wsum, &tot);
-        if (idx < n_tiles) row[idx] = carry + inc - v;
+        if (idx < n_act) row[idx] = carry + inc - v;
         carry += tot;
     }
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
@@ -217,7 +219,7 @@ int radix_passes(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int p
     for (int p = 0; p < passes; p++) {
         const int shift = DB * p;
         k_upsweep<K, RC, DB><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles, n_dev);
-        k_digit_scan<<<1 << DB, RT, 0, s>>>(hist, n_tiles, totals);
+        k_digit_scan<<<1 << DB, RT, 0, s>>>(hist, n_tiles, totals, n, TILE, n_dev);
         if (p == 0 && iota_vals)
             k_downsweep<K, true, RC, DB><<<n_tiles, RT, downsweep_smem<K, RC, DB>(), s>>>(
                 keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles, n_dev);
