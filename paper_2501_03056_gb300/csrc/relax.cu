@@ -999,10 +999,14 @@ __global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_
             const int cz = cell_coord(y.z, A.tg_o[2], A.tg_inv, A.tg_n[2]);
             bool certified = false;
             bool near_partner = false;
+            // some triangle of the body within the 27 triangle cells of y
+            const bool near_own = test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz));
             if (cls == kClsV && A.vol_rules) {
                 for (int q = 0; q < A.npart && !near_partner; q++)
                     if (A.partner_vol[q] != 0) near_partner = near_body(M, P[A.partner[q]], y);
-            } else if (cls == kClsV && A.closed) {
+            } else if (cls == kClsV && A.closed && near_own) {
+                // (with no triangle near, the volume test accepts anyway: the
+                // certificate is not read)
                 // inside a ball that an earlier search found free of surface
                 // and inside the body: the volume test would accept
                 const float4 cc = cert[i];
@@ -1040,7 +1044,7 @@ __global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_
                 pos[i] = make_float4(xs.x, xs.y, xs.z, p.w);
                 const float3 w = xs - p3;
                 disp = sqrtf(dot3(w, w));
-            } else if (near_partner || test_bit(M.occ, A.dil_off, tri_key(A, cx, cy, cz))) {
+            } else if (near_partner || near_own) {
                 queue = true;
                 rng = cand_range(M, A, tri_key(A, cx, cy, cz));
             } else if (cls == kClsV) {       // nothing near: inside, accept
