@@ -462,6 +462,20 @@ int fppg_debug_fail_allocation(int64_t k);
  * of the method.  FPPG_ERR_ARG for a null pointer, FPPG_ERR_CUDA when no
  * device is usable (message in fppg_last_error(NULL)). */
 int fppg_device_sm_count(int32_t *sms);
+/* Bounds checks.  A library built with -DFPPG_CHECKED (the `checked`
+ * build of paper_2501_03056_gb300._build) checks, in the hot-path kernels,
+ * every index it computes before using it: the sorted ids and fine keys of
+ * the gather, each grid row's slot range of the force pass, the search
+ * queue's slots and entries, the candidate triangles of the searches, the
+ * compaction positions and merge splits of the incremental order.  A
+ * failed check skips the access and ORs its code into a device word:
+ * 1 gather, 2 slot range, 4 queue slot, 8 queue entry, 16 candidate
+ * triangle, 32 merge split, 64 compaction position.  fppg_check_status
+ * returns that word in *word and clears it (0 in the normal build, where
+ * the checks compile away), and *checked (nullable) = 1 for the checked
+ * build.  FPPG_ERR_ARG for word NULL; FPPG_ERR_CUDA when the word cannot be
+ * read. */
+int fppg_check_status(uint32_t *word, int32_t *checked);
 
 /* ---- allocation-free force pass ---------------------------------------------
  * fppg_forces_static: the neighbour grid and the force pass (A1-A4) for one

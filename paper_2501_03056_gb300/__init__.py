@@ -21,7 +21,8 @@ __all__ = ["Body", "Batch", "FPPGError", "lib", "library_path", "workloads", "S"
 S, V, F, I, P = 0, 1, 2, 3, 4
 OK, ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL = range(7)
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIBPATH = os.path.join(_HERE, "_lib", "libfppg.so")
+# FPPG_CHECKED=1 in the environment loads the bounds-checked build instead
+_LIBPATH = os.path.join(_HERE, "_lib", "libfppg_checked.so" if os.environ.get("FPPG_CHECKED") == "1" else "libfppg.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -108,6 +109,7 @@ def lib():
                 "fppg_batch_phase_ms": [vp, P_(f64)],
                 "fppg_device_sm_count": [P_(i32)],
                 "fppg_debug_fail_allocation": [i64],
+                "fppg_check_status": [P_(C.c_uint32), P_(i32)],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -374,6 +376,16 @@ class Body:
 
     def copy_positions_dev(self, ptr: int):
         self._chk(lib().fppg_copy_positions_dev(self._h, C.c_void_p(ptr)))
+
+
+def check_status() -> tuple[int, bool]:
+    """(codes of the failed bounds checks since the last call, whether the
+    loaded library is the checked build); fppg_check_status."""
+    w, c = C.c_uint32(), C.c_int32()
+    r = lib().fppg_check_status(C.byref(w), C.byref(c))
+    if r != OK:
+        raise FPPGError(r, "fppg_check_status")
+    return w.value, bool(c.value)
 
 
 def device_sm_count() -> int:

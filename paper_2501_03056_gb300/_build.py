@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfppg.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libfppg_checked.so")   # the bounds-checked build (-DFPPG_CHECKED)
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -49,15 +50,19 @@ def _sources_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile every unit and link the shared library; returns its path."""
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
+    """Compile every unit and link the shared library; returns its path.
+    checked: the bounds-checked build (every hot-path kernel checks the
+    indices it computes, fppg_check_status reports failures), linked as a
+    library of its own."""
     os.makedirs(LIBDIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
-        return LIB
+    out = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= _sources_mtime():
+        return out
     cc = nvcc()
-    objdir = os.path.join(LIBDIR, "obj")
+    objdir = os.path.join(LIBDIR, "obj_checked" if checked else "obj")
     os.makedirs(objdir, exist_ok=True)
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DFPPG_CHECKED"] if checked else [])
 
     def compile_one(item):
         src, flags = item
@@ -72,13 +77,13 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS.items()))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = out + f".{os.getpid()}.tmp"
     cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs, "-lpthread", "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

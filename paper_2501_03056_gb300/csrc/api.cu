@@ -1297,6 +1297,17 @@ int fppg_debug_fail_allocation(int64_t k) {
     return FPPG_OK;
 }
 
+int fppg_check_status(uint32_t *word, int32_t *checked) {
+    if (!word) return FPPG_ERR_ARG;
+#ifdef FPPG_CHECKED
+    if (checked) *checked = 1;
+#else
+    if (checked) *checked = 0;
+#endif
+    *word = check_word_take();
+    return *word == 0xffffffffu ? FPPG_ERR_CUDA : FPPG_OK;
+}
+
 int fppg_device_sm_count(int32_t *sms) {
     if (!sms) return fail_global(FPPG_ERR_ARG, "sms is NULL");
     int dev = 0, v = 0;

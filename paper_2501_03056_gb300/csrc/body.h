@@ -143,6 +143,10 @@ struct Group {
     ~Group() { free_all(); }
 };
 
+// the codes of the failed bounds checks of a checked build since the last
+// call, cleared (0 in the normal build; 0xffffffff when it cannot be read)
+uint32_t check_word_take();
+
 // rank[y + ny z] of every grid row in the Morton order of Eq. 9 over (y, z):
 // the bits of y and z interleaved, z's above y's at every level
 void morton_row_ranks(int ny, int nz, std::vector<uint32_t> &rank);

@@ -253,6 +253,27 @@ inline float slab_reach2(float R2, float inv) {
 // A particle's place in the grid: unclamped cell coordinates t, clamped
 // cells c and the slack (cell units) that covers the FP32 rounding of t and
 // of the reach arithmetic (relative errors of a few 2^-24 of |t|).
+// Bounds-checked build (compiled with -DFPPG_CHECKED): the hot-path kernels
+// check the indices they compute before using them; a failed check ORs its
+// code into the device word read by fppg_check_status and the access is
+// skipped, so a bad index never reaches memory.  In the normal build every
+// check is the constant true and compiles away.
+enum CheckCode : uint32_t {
+    kChkGather = 1u,     // a sorted id or fine key outside the particle / key count
+    kChkRange = 2u,      // a row's slot range outside [0, N]
+    kChkQueue = 4u,      // a search-queue slot outside [0, N)
+    kChkEntry = 8u,      // a queued key slot outside [0, N)
+    kChkTri = 16u,       // a candidate triangle outside the body's triangles
+    kChkMerge = 32u,     // a merge tile's split outside its lists
+    kChkCompact = 64u,   // a compaction position outside [0, N)
+};
+#ifdef FPPG_CHECKED
+__device__ bool fppg_check_failed(uint32_t code);
+#define FPPG_CHECK(cond, code) ((cond) || fppg_check_failed(code))
+#else
+#define FPPG_CHECK(cond, code) true
+#endif
+
 // index of grid row (y, z) in key order: row-major, or its Morton rank
 __device__ inline uint32_t grid_row(const AsmParams &A, int y, int z) {
     const uint32_t r = (uint32_t)y + (uint32_t)A.ng_n[1] * (uint32_t)z;

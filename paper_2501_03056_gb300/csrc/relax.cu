@@ -22,6 +22,27 @@
 
 namespace fppg {
 
+#ifdef FPPG_CHECKED
+// the codes of the failed bounds checks since the last fppg_check_status
+__device__ uint32_t g_check_word = 0u;
+__device__ bool fppg_check_failed(uint32_t code) {
+    atomicOr(&g_check_word, code);
+    return false;
+}
+#endif
+
+uint32_t check_word_take() {
+#ifdef FPPG_CHECKED
+    uint32_t w = 0u;
+    const uint32_t zero = 0u;
+    if (cudaMemcpyFromSymbol(&w, g_check_word, sizeof(w)) != cudaSuccess) return 0xffffffffu;
+    cudaMemcpyToSymbol(g_check_word, &zero, sizeof(zero));
+    return w;
+#else
+    return 0u;
+#endif
+}
+
 namespace {
 
 constexpr int TPB = 256;
@@ -158,6 +179,7 @@ __global__ void __launch_bounds__(TPB) k_compact_changed(const uint32_t *__restr
     const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (i >= N || !chg[i]) return;
     const uint32_t p = cpos[i];
+    if (!FPPG_CHECK(p < N, kChkCompact)) return;
     ck[p] = key_id[i];
     cv[p] = (uint32_t)i;
 }
@@ -179,6 +201,7 @@ __global__ void __launch_bounds__(TPB) k_compact_kept(const uint32_t *__restrict
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (k >= N || !keep[k]) return;
     const uint32_t p = kpos[k];
+    if (!FPPG_CHECK(p < N, kChkCompact)) return;
     uk[p] = prev_key[k];
     uv[p] = prev_id[k];
 }
@@ -224,6 +247,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint32_t *__restr
     const int64_t d0 = (int64_t)blockIdx.x * kMergeTile, d1 = min(d0 + kMergeTile, N);
     const int64_t i0 = split[blockIdx.x], i1 = split[blockIdx.x + 1];
     const int64_t j0 = d0 - i0, j1 = d1 - i1;
+    // (nu + nc = d1 - d0 <= kMergeTile: the staging fits when both are >= 0)
+    if (!FPPG_CHECK(i0 <= i1 && j0 <= j1 && j0 >= 0, kChkMerge)) return;
     const int nu = (int)(i1 - i0), nc = (int)(j1 - j0), n = nu + nc;
     for (int q = threadIdx.x; q < n; q += kMergeThreads) {
         if (q < nu) {
@@ -277,10 +302,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint32_t *__restr
 __global__ void __launch_bounds__(TPB) k_gather(const uint32_t *__restrict__ key_s, const uint32_t *__restrict__ id_s,
                                                 const float4 *__restrict__ pos, int64_t N, float4 *__restrict__ pos_s,
                                                 float4 *__restrict__ pos_p, uint32_t *__restrict__ fcount,
-                                                const int32_t *__restrict__ cons, int32_t *__restrict__ cons_s) {
+                                                const int32_t *__restrict__ cons, int32_t *__restrict__ cons_s,
+                                                uint32_t n_fine) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool valid = k < N;
-    const uint32_t id = valid ? id_s[k] : 0u;
+    uint32_t id = valid ? id_s[k] : 0u;
+    if (valid && !FPPG_CHECK(id < N, kChkGather)) id = 0u;
     const float4 q = valid ? pos[id] : make_float4(0.f, 0.f, 0.f, 0.f);
     // the constraint ids in key order too, for the step
     if (valid && cons_s) cons_s[k] = cons[id];
@@ -306,7 +333,7 @@ __global__ void __launch_bounds__(TPB) k_gather(const uint32_t *__restrict__ key
     if ((starts >> lane) & 1u) {
         const uint32_t later = starts & ~((2u << lane) - 1u);          // run starts after this lane
         const int stop = later ? __ffs(later) - 1 : 32 - __clz(ends);  // first lane of the next run, or past the last valid
-        atomicAdd(fcount + f, (uint32_t)(stop - lane));
+        if (FPPG_CHECK(f < n_fine, kChkGather)) atomicAdd(fcount + f, (uint32_t)(stop - lane));
     }
 }
 
@@ -466,6 +493,10 @@ __global__ void __launch_bounds__(TPB, 5)
             if (mbits && z >= 0 && z < nz && y >= 0 && y < ny) {
                 const uint32_t row = A.key_base + (uint32_t)nx * grid_row_of<MORTON>(A, y, z);
                 row_slots(A, fstart, g, row_gap(g.t[1], cy, dy, g.slack), gz, row, s, e);
+                if (!FPPG_CHECK(e == 0u || (s <= e && e <= (uint64_t)N), kChkRange)) {
+                    s = 0xffffffffu;
+                    e = 0u;
+                }
             }
             if (COUNT && e > s) tested += (int)(e - s);
             if (VARIANT == 1 && shared_row) {
@@ -737,11 +768,14 @@ __device__ inline void for_27_candidates(const MeshView &M, const AsmParams &A, 
     const int lane = threadIdx.x & 31;
     uint32_t beg = 0, end = 0;
     const int kind = cell_candidates(M, A, y, beg, end, pre);
+    auto checked = [&](int t) {
+        if (FPPG_CHECK(t >= 0 && t < A.nt, kChkTri)) test(t);
+    };
     if (kind == 1) {
-        for (uint32_t q = beg + lane; q < end; q += 32) test(M.cand[q]);
+        for (uint32_t q = beg + lane; q < end; q += 32) checked(M.cand[q]);
     } else if (kind == 2) {
         const CellRange r = lane_cell(M, A, y, lane);
-        for_candidates(M, r, buf, test);
+        for_candidates(M, r, buf, checked);
     }
 }
 
@@ -1070,13 +1104,17 @@ __global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_
         const int4 it = make_int4((int)k, __float_as_int(y.x), __float_as_int(y.y), __float_as_int(y.z));
         if (qs) {
             const uint32_t q = bs + __popc(ms & lanemask_lt());
-            work[q] = it;
-            work_r[q] = rng;
+            if (FPPG_CHECK(q < N, kChkQueue)) {
+                work[q] = it;
+                work_r[q] = rng;
+            }
         }
         if (qv) {
             const int64_t q = N - 1 - (int64_t)(bv + __popc(mv & lanemask_lt()));
-            work[q] = it;
-            work_r[q] = rng;
+            if (FPPG_CHECK(q >= 0 && q < N, kChkQueue)) {
+                work[q] = it;
+                work_r[q] = rng;
+            }
         }
     }
     __shared__ int s_lab[TPB / 32];
@@ -1113,8 +1151,10 @@ __global__ void __launch_bounds__(TPB) k_search(const float4 *__restrict__ pos_s
     uint32_t run = 0u;
     for (uint32_t e = (blockIdx.x * TPB + threadIdx.x) / 32; e < n; e += warps) {
         const int64_t qs = queue_slot(nf, N, e);
+        if (!FPPG_CHECK(qs >= 0 && qs < N, kChkQueue)) continue;
         const int4 it = work[qs];
         const uint2 rng = work_r[qs];
+        if (!FPPG_CHECK(it.x >= 0 && it.x < N, kChkEntry)) continue;
         const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
         const float4 p = pos_s[it.x];
         const int cls = cls_of(p.w), b = body_of(p.w);
@@ -1177,12 +1217,15 @@ __device__ inline void each_27_candidate(const MeshView &M, const AsmParams &A, 
                                          const uint2 *pre = nullptr) {
     uint32_t beg = 0, end = 0;
     const int kind = cell_candidates(M, A, y, beg, end, pre);
+    auto checked = [&](int t) {
+        if (FPPG_CHECK(t >= 0 && t < A.nt, kChkTri)) test(t);
+    };
     if (kind == 1) {
-        for (uint32_t q = beg; q < end; q++) test(M.cand[q]);
+        for (uint32_t q = beg; q < end; q++) checked(M.cand[q]);
     } else if (kind == 2) {
         for (int c = 0; c < 27; c++) {
             const CellRange r = lane_cell(M, A, y, c);
-            for (uint32_t e = r.beg; e < r.beg + r.len; e++) test(M.tlist[e]);
+            for (uint32_t e = r.beg; e < r.beg + r.len; e++) checked(M.tlist[e]);
         }
     }
 }
@@ -1301,6 +1344,9 @@ __global__ void __launch_bounds__(TPB, 4) k_search_thread(const float4 *__restri
         float disp = 0.f;
         if (e < n) {
             const int64_t qs = queue_slot(nf, N, e);
+            const bool entry_ok = FPPG_CHECK(qs >= 0 && qs < N, kChkQueue) &&
+                                  FPPG_CHECK(work[qs].x >= 0 && work[qs].x < N, kChkEntry);
+            if (!entry_ok) continue;
             const int4 it = work[qs];
             const uint2 rng = work_r[qs];
             const float3 y = make_float3(__int_as_float(it.y), __int_as_float(it.z), __int_as_float(it.w));
@@ -1496,7 +1542,7 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
         buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
     }
     k_gather<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s, d.pos_p, d.fcount, d.cons,
-                                          d.cons_s);
+                                          d.cons_s, (uint32_t)(kSlabs * d.total_cells));
     const int64_t F1 = kSlabs * d.total_cells + 1;
     exclusive_scan_u32_clear(d.fcount, d.fstart, F1, d.scan_tmp, scan_tmp_elems(F1), s);
     return buf;
