@@ -78,7 +78,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS.items()))
     tmp = out + f".{os.getpid()}.tmp"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs, "-lpthread", "-o", tmp]
+    cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs, "-lpthread", "-ldl", "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -325,6 +325,7 @@ int fppg_get_feature_lines(fppg_ctx *ctx, int64_t *line_nseg_host, int32_t *clos
 }
 
 int fppg_map_particles(fppg_ctx *ctx, const fppg_map_opts *opts, int64_t *n_out) {
+    NvtxRange nvtx_("fppg_map_particles");
     if (!ctx || !opts) return FPPG_ERR_ARG;
     if (opts->band_cells < 0 || opts->band_cells > 64 || opts->inner_cells < 0 || opts->inner_cells > 64)
         return fail(ctx->err, FPPG_ERR_ARG, "band_cells or inner_cells outside 0..64");
@@ -418,6 +419,7 @@ int fppg_set_constraints(fppg_ctx *ctx, const int32_t *cons_host, int64_t n) {
 }
 
 int fppg_boolean(fppg_ctx *a, fppg_ctx *b, int32_t op, int64_t *n_a, int64_t *n_b) {
+    NvtxRange nvtx_("fppg_boolean");
     if (!a || !b || a == b) return fail_global(FPPG_ERR_ARG, "a Boolean operation needs two different bodies");
     if (op != FPPG_UNION && op != FPPG_DIFFERENCE && op != FPPG_INTERSECTION)
         return fail(a->err, FPPG_ERR_ARG, "unknown Boolean operation");
@@ -482,6 +484,7 @@ int fppg_union(fppg_ctx *a, fppg_ctx *b, int64_t *n_a, int64_t *n_b) {
 }
 
 int fppg_boolean_curve(fppg_ctx *a, fppg_ctx *b, int64_t *n_added) {
+    NvtxRange nvtx_("fppg_boolean_curve");
     if (!a || !b || a == b) return fail_global(FPPG_ERR_ARG, "the intersection curve needs two different bodies");
     fppg_ctx::BoolRel *rel = a->rel_with(b);
     if (!rel) return fail(a->err, FPPG_ERR_STATE, "the intersection curve follows fppg_boolean on the pair");
@@ -557,6 +560,7 @@ int fppg_get_particles(fppg_ctx *ctx, float *xyz_host, int32_t *cls_host, int32_
 }
 
 static int relax_impl(fppg_ctx *ctx, int32_t n_iter, bool energy_mode) {
+    NvtxRange nvtx_("fppg_relax");
     if (!ctx) return FPPG_ERR_ARG;
     if (n_iter < 0) return fail(ctx->err, FPPG_ERR_ARG, "n_iter < 0");
     if (!ctx->has_particles) return fail(ctx->err, FPPG_ERR_STATE, "no particles set");
@@ -1033,6 +1037,7 @@ static int build_graph(fppg_batch *b) {
 }
 
 int fppg_batch_relax(fppg_batch *b, int32_t n_iter, int32_t use_graph) {
+    NvtxRange nvtx_("fppg_batch_relax");
     if (!b) return FPPG_ERR_ARG;
     if (n_iter < 0) return fail(b->err, FPPG_ERR_ARG, "n_iter < 0");
     Group &g = b->group;
@@ -1139,6 +1144,7 @@ static void set_ordering(Group &g, bool incremental, cudaStream_t s) {
 
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
                         int32_t *incremental, int32_t *cell_order, double *ms_per_iter) {
+    NvtxRange nvtx_("fppg_batch_autotune");
     if (!b || iters <= 0 || iters > 10000) return FPPG_ERR_ARG;
     Group &g = b->group;
     DevGroup &d = g.d;

@@ -2,6 +2,7 @@
 // one or many bodies with the same launches.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include "fppg_internal.cuh"
 
 namespace fppg {
@@ -141,6 +142,15 @@ struct Group {
     int set_cell_order(int order, cudaStream_t s, std::string &err);
     void free_all();
     ~Group() { free_all(); }
+};
+
+// an NVTX range for the life of the object (host side; shows the library's
+// calls and phases on a timeline profiler; a few ns with no tool attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // the codes of the failed bounds checks of a checked build since the last

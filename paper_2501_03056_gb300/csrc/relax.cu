@@ -1599,11 +1599,19 @@ void iterate(Group &g, cudaStream_t s, bool energy_mode, int32_t *count_dbg) {
     if (timed) cudaStreamIsCapturing(s, &cap);
     const unsigned flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used], s, flags);
-    int buf = build_grid(g, s);
+    int buf;
+    {
+        NvtxRange r("A1-A3 grid");
+        buf = build_grid(g, s);
+    }
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 1], s, flags);
-    if (energy_mode) energy_accel(g, s);
-    else forces(g, s, count_dbg);
+    {
+        NvtxRange r("A4 force");
+        if (energy_mode) energy_accel(g, s);
+        else forces(g, s, count_dbg);
+    }
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 2], s, flags);
+    NvtxRange r("A5-A6 step and search");
     k_step<<<nblocks(d.N), TPB, 0, s>>>(d.pos_s, d.acc_s, d.id[buf], d.N, d.params, d.amax, d.pos, d.cons, g.mesh,
                                          d.maxdisp, d.work, queue_ranges(d), d.work_count, d.cert, d.cons_s);
     if (timed) cudaEventRecordWithFlags(g.ev[g.ev_used + 3], s, flags);
