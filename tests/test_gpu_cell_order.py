@@ -5,7 +5,8 @@ relaxations equal to the row-major order's up to the FP32 rounding of the
 two partial sums a row's slots are split between (their absolute parity
 moves with the order) in the plain form and a Boolean assembly, the
 batched graph form bit-identical to the plain form in the same order; the
-autotuner choosing between the two orders."""
+energy and its gradients the same in both orders; the autotuner choosing
+between the two orders."""
 import numpy as np
 import pytest
 
@@ -111,3 +112,29 @@ def test_bad_order_is_an_argument_error():
     b = pkg.Body.from_assembly(a)
     assert pkg.lib().fppg_set_cell_order(b.handle, 2) == pkg.ERR_ARG
     assert pkg.lib().fppg_set_cell_order(None, 1) == pkg.ERR_ARG
+
+
+def test_energy_and_backward_in_morton_row_order():
+    import torch
+    a = W.cube_workload(seed=1)[0]
+    b = pkg.Body.from_assembly(a)
+    b.relax(2)
+    x, c, cons = b.get_particles()
+    res = []
+    for order in (pkg.ORDER_ROWS, pkg.ORDER_MORTON_ROWS):
+        g = pkg.Body(a.verts, a.tris, a.dx, a.h)
+        g.extract_features(a.dihedral_deg)
+        g.set_particles(x, c)
+        g.set_constraints(cons)
+        g.set_cell_order(order)
+        y = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        v = torch.from_numpy(np.ascontiguousarray(a.verts)).cuda()
+        gy, gv = torch.empty_like(y), torch.empty_like(v)
+        E = g.energy_ptr(y.data_ptr(), v.data_ptr(), gy.data_ptr(), gv.data_ptr())
+        res.append((E, gy.cpu().numpy(), gv.cpu().numpy()))
+    (E0, gy0, gv0), (E1, gy1, gv1) = res
+    # the same energy and gradients up to the FP32 sums, within the bounds the
+    # energy test holds against the oracle
+    assert E1 == pytest.approx(E0, rel=1e-5)
+    assert np.abs(gy1 - gy0).max() <= 1e-4 * np.abs(gy0).max()
+    assert np.abs(gv1 - gv0).max() <= 1e-4 * np.abs(gv0).max()
