@@ -279,11 +279,12 @@ int Group::alloc_particles(int64_t N, std::string &err) {
 
 void Group::free_order_state() {
     DevGroup &g = d;
-    void *ptrs[] = {g.key_id, g.chg, g.cpos, g.keep, g.ck[0], g.ck[1], g.cv[0], g.cv[1], g.uk, g.uv, g.split,
-                    g.counts, g.scan_tmp_n};
+    void *ptrs[] = {g.key_id, g.chg_bits, g.keep_bits, g.tile_cnt, g.tile_pos, g.ck[0], g.ck[1], g.cv[0],
+                    g.cv[1],  g.uk,       g.uv,        g.split,    g.counts,   g.scan_tmp_n};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    g.key_id = g.chg = g.cpos = g.keep = g.uk = g.uv = g.split = g.counts = g.scan_tmp_n = nullptr;
+    g.key_id = g.chg_bits = g.keep_bits = g.tile_cnt = g.tile_pos = nullptr;
+    g.uk = g.uv = g.split = g.counts = g.scan_tmp_n = nullptr;
     g.ck[0] = g.ck[1] = g.cv[0] = g.cv[1] = nullptr;
 }
 
@@ -301,9 +302,13 @@ int Group::alloc_order_state(std::string &err) {
     const size_t n1 = (size_t)std::max<int64_t>(g.N, 1);
     const int64_t nblk = (std::max<int64_t>(g.N, 1) + 2047) / 2048;
     CKA(dev_malloc(&g.key_id, sizeof(uint32_t) * n1));
-    CKA(dev_malloc(&g.chg, sizeof(uint32_t) * n1));
-    CKA(dev_malloc(&g.cpos, sizeof(uint32_t) * n1));
-    CKA(dev_malloc(&g.keep, sizeof(uint32_t) * n1));
+    // tiles of 256 (the block of the compactions), 32 flags a word
+    const int64_t ntile = (std::max<int64_t>(g.N, 1) + 255) / 256;
+    const size_t nword = (size_t)(ntile * 8);
+    CKA(dev_malloc(&g.chg_bits, sizeof(uint32_t) * nword));
+    CKA(dev_malloc(&g.keep_bits, sizeof(uint32_t) * nword));
+    CKA(dev_malloc(&g.tile_cnt, sizeof(uint32_t) * (size_t)(2 * ntile)));
+    CKA(dev_malloc(&g.tile_pos, sizeof(uint32_t) * (size_t)(2 * ntile)));
     for (int k = 0; k < 2; k++) {
         CKA(dev_malloc(&g.ck[k], sizeof(uint32_t) * n1));
         CKA(dev_malloc(&g.cv[k], sizeof(uint32_t) * n1));
@@ -312,7 +317,7 @@ int Group::alloc_order_state(std::string &err) {
     CKA(dev_malloc(&g.uv, sizeof(uint32_t) * n1));
     CKA(dev_malloc(&g.split, sizeof(uint32_t) * (size_t)(nblk + 2)));
     CKA(dev_malloc(&g.counts, 2 * sizeof(uint32_t)));
-    CKA(dev_malloc(&g.scan_tmp_n, sizeof(uint32_t) * (size_t)scan_tmp_elems(std::max<int64_t>(g.N, 1))));
+    CKA(dev_malloc(&g.scan_tmp_n, sizeof(uint32_t) * (size_t)scan_tmp_elems(2 * ntile)));
     CKA(cudaMemset(g.key_id, 0xff, sizeof(uint32_t) * n1));
     k_iota_u32<<<(unsigned)((n1 + 255) / 256), 256>>>(g.id[0], (int64_t)n1);
     CKA(cudaGetLastError());

@@ -158,14 +158,15 @@ struct DevGroup {
     // order_incremental); null unless incremental is set
     bool incremental = false;
     uint32_t *key_id = nullptr;    // by id: fine key at the last grid build (~0: none)
-    uint32_t *chg = nullptr;       // by id: key changed
-    uint32_t *cpos = nullptr;      // scan positions (changed, then kept)
-    uint32_t *keep = nullptr;      // by previous slot: key kept
+    uint32_t *chg_bits = nullptr;  // by id: key changed, one bit each (bit i & 31 of word i >> 5)
+    uint32_t *keep_bits = nullptr; // by previous slot: key kept, one bit each
+    uint32_t *tile_cnt = nullptr;  // set bits of every tile of 256: the changed tiles, then the kept ones
+    uint32_t *tile_pos = nullptr;  // their exclusive scan
     uint32_t *ck[2] = {nullptr, nullptr}, *cv[2] = {nullptr, nullptr};   // changed (key, id), radix ping-pong
     uint32_t *uk = nullptr, *uv = nullptr;   // kept (key, id) in previous order
     uint32_t *split = nullptr;     // merge tile splits
     uint32_t *counts = nullptr;    // [0] changed, [1] kept
-    uint32_t *scan_tmp_n = nullptr; // scan_tmp_elems(N) entries
+    uint32_t *scan_tmp_n = nullptr; // scan_tmp_elems(2 x tiles) entries
     uint32_t *amax = nullptr;
     uint32_t *maxdisp = nullptr;
     int4 *work = nullptr;          // search queue {key slot, trial point}, N entries, then N uint2

@@ -46,6 +46,7 @@ uint32_t check_word_take() {
 namespace {
 
 constexpr int TPB = 256;
+static_assert(TPB == 256, "the order state (Group::alloc_order_state) has tiles of 256");
 
 inline unsigned nblocks(int64_t n, int t = TPB) { return (unsigned)std::max<int64_t>((n + t - 1) / t, 1); }
 
@@ -142,14 +143,51 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
 // stale or foreign previous order every key counts as changed and the
 // repair is a full sort.
 
+// The flags of both compactions are bits, one 32-bit word per warp (bit
+// i & 31 of word i >> 5: 1/32 of the bytes of a flag array, small enough to
+// stay in L2), and every block of TPB threads counts its set bits.  One
+// exclusive scan of the 2 x tiles counts (the changed tiles by id, then the
+// kept tiles by previous slot) places every tile; inside a tile a bit's rank
+// is the set bits before it, from the warps' counts and the word.
+
+// rank of this lane's bit among the set bits of the block's words (one word
+// per warp, the same in all its lanes); every thread of the block calls it
+__device__ inline uint32_t block_bit_rank(uint32_t word, uint32_t *wcnt) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wcnt[w] = __popc(word);
+    __syncthreads();
+    uint32_t before = 0;
+    for (int q = 0; q < w; q++) before += wcnt[q];
+    return before + __popc(word & ((1u << lane) - 1u));
+}
+
+// the warps' words of a block's flags stored and their set bits counted
+__device__ inline void store_tile_bits(bool flag, int64_t i, int64_t N, uint32_t *__restrict__ bits,
+                                       uint32_t *__restrict__ tile_cnt, uint32_t *wcnt) {
+    const uint32_t word = __ballot_sync(~0u, flag);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        if (i < N) bits[i >> 5] = word;   // i is a multiple of 32 in lane 0
+        wcnt[w] = __popc(word);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x * TPB < N) {
+        uint32_t t = 0;
+        for (int q = 0; q < TPB / 32; q++) t += wcnt[q];
+        tile_cnt[blockIdx.x] = t;
+    }
+}
+
 // key of particle i (the rule of k_keys), compared with the key it had at
-// the last grid build: chg[i] = changed; key_id[i] updated
+// the last grid build: the changed bits by id and their tile counts; key_id[i]
+// updated
 __global__ void __launch_bounds__(TPB) k_keys_inc(const float4 *__restrict__ pos, int64_t N,
                                                   const AsmParams *__restrict__ P, uint32_t *__restrict__ key_id,
-                                                  uint32_t *__restrict__ chg, uint32_t *__restrict__ amax,
-                                                  uint32_t *__restrict__ maxdisp, int B,
+                                                  uint32_t *__restrict__ chg_bits, uint32_t *__restrict__ tile_cnt,
+                                                  uint32_t *__restrict__ amax, uint32_t *__restrict__ maxdisp, int B,
                                                   uint32_t *__restrict__ work_count) {
-    int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    __shared__ uint32_t wcnt[TPB / 32];
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (i < B) {
         amax[i] = 0u;
         maxdisp[i] = 0u;
@@ -158,52 +196,81 @@ __global__ void __launch_bounds__(TPB) k_keys_inc(const float4 *__restrict__ pos
         work_count[0] = 0u;
         work_count[1] = 0u;
     }
-    if (i >= N) return;
-    float4 p = pos[i];
-    const AsmParams &A = P[body_of(p.w)];
-    const int fx = fine_coord(p.x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
-    const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
-    const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
-    const uint32_t k = kSlabs * A.key_base + (uint32_t)fx +
-                       kSlabs * (uint32_t)A.ng_n[0] * grid_row(A, cy, cz);
-    const uint32_t old = key_id[i];
-    chg[i] = k != old ? 1u : 0u;
-    if (k != old) key_id[i] = k;
+    bool changed = false;
+    if (i < N) {
+        const float4 p = pos[i];
+        const AsmParams &A = P[body_of(p.w)];
+        const int fx = fine_coord(p.x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
+        const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
+        const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
+        const uint32_t k = kSlabs * A.key_base + (uint32_t)fx +
+                           kSlabs * (uint32_t)A.ng_n[0] * grid_row(A, cy, cz);
+        changed = k != key_id[i];
+        if (changed) key_id[i] = k;
+    }
+    store_tile_bits(changed, i, N, chg_bits, tile_cnt, wcnt);
 }
 
-// the changed particles, in id order: (key, id) at their scan positions
-__global__ void __launch_bounds__(TPB) k_compact_changed(const uint32_t *__restrict__ chg,
-                                                         const uint32_t *__restrict__ cpos,
+// the kept bits by previous slot (the particle in slot k kept its key) and
+// their tile counts
+__global__ void __launch_bounds__(TPB) k_keep_bits(const uint32_t *__restrict__ prev_id,
+                                                   const uint32_t *__restrict__ chg_bits, int64_t N,
+                                                   uint32_t *__restrict__ keep_bits,
+                                                   uint32_t *__restrict__ tile_cnt) {
+    __shared__ uint32_t wcnt[TPB / 32];
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    bool kept = false;
+    if (k < N) {
+        const uint32_t id = prev_id[k];
+        kept = FPPG_CHECK(id < N, kChkCompact) && !((chg_bits[id >> 5] >> (id & 31)) & 1u);
+    }
+    store_tile_bits(kept, k, N, keep_bits, tile_cnt, wcnt);
+}
+
+// the changed particles, in id order: (key, id) at their positions
+__global__ void __launch_bounds__(TPB) k_compact_changed(const uint32_t *__restrict__ chg_bits,
+                                                         const uint32_t *__restrict__ tile_pos,
                                                          const uint32_t *__restrict__ key_id, int64_t N,
                                                          uint32_t *__restrict__ ck, uint32_t *__restrict__ cv) {
+    __shared__ uint32_t wcnt[TPB / 32];
     const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (i >= N || !chg[i]) return;
-    const uint32_t p = cpos[i];
+    const int64_t i0 = i & ~(int64_t)31;
+    const uint32_t word = i0 < N ? chg_bits[i0 >> 5] : 0u;
+    const uint32_t r = block_bit_rank(word, wcnt);
+    if (!((word >> (threadIdx.x & 31)) & 1u)) return;
+    const uint32_t p = tile_pos[blockIdx.x] + r;
     if (!FPPG_CHECK(p < N, kChkCompact)) return;
     ck[p] = key_id[i];
     cv[p] = (uint32_t)i;
 }
 
-// keep[k] = the particle in slot k of the previous order kept its key
-__global__ void __launch_bounds__(TPB) k_keep_flags(const uint32_t *__restrict__ prev_id,
-                                                    const uint32_t *__restrict__ chg, int64_t N,
-                                                    uint32_t *__restrict__ keep) {
-    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (k < N) keep[k] = chg[prev_id[k]] ? 0u : 1u;
-}
-
-// the kept slots of the previous order, compacted (still sorted)
-__global__ void __launch_bounds__(TPB) k_compact_kept(const uint32_t *__restrict__ keep,
-                                                      const uint32_t *__restrict__ kpos,
+// the kept slots of the previous order, compacted (still sorted); the kept
+// tiles' positions follow the changed tiles' (nb tiles of each), so they
+// start at the number of changed particles, tile_pos[nb]
+__global__ void __launch_bounds__(TPB) k_compact_kept(const uint32_t *__restrict__ keep_bits,
+                                                      const uint32_t *__restrict__ tile_pos, int64_t nb,
                                                       const uint32_t *__restrict__ prev_key,
                                                       const uint32_t *__restrict__ prev_id, int64_t N,
                                                       uint32_t *__restrict__ uk, uint32_t *__restrict__ uv) {
+    __shared__ uint32_t wcnt[TPB / 32];
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (k >= N || !keep[k]) return;
-    const uint32_t p = kpos[k];
+    const int64_t k0 = k & ~(int64_t)31;
+    const uint32_t word = k0 < N ? keep_bits[k0 >> 5] : 0u;
+    const uint32_t r = block_bit_rank(word, wcnt);
+    if (!((word >> (threadIdx.x & 31)) & 1u)) return;
+    const uint32_t p = tile_pos[nb + blockIdx.x] - tile_pos[nb] + r;
     if (!FPPG_CHECK(p < N, kChkCompact)) return;
     uk[p] = prev_key[k];
     uv[p] = prev_id[k];
+}
+
+// counts[0] = changed particles, counts[1] = kept slots, from the scan of
+// the 2 nb tile counts
+__global__ void k_order_counts(const uint32_t *__restrict__ tile_cnt, const uint32_t *__restrict__ tile_pos,
+                               int64_t nb, uint32_t *__restrict__ counts) {
+    const uint32_t c = tile_pos[nb];
+    counts[0] = c;
+    counts[1] = tile_pos[2 * nb - 1] + tile_cnt[2 * nb - 1] - c;
 }
 
 // merge of the kept list u (U items) and the sorted changed list c (C
@@ -1517,15 +1584,17 @@ __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__re
 // also the previous order it starts from
 static void order_incremental(DevGroup &d, cudaStream_t s) {
     const int64_t N = d.N;
-    k_keys_inc<<<nblocks(std::max<int64_t>(N, d.B)), TPB, 0, s>>>(d.pos, N, d.params, d.key_id, d.chg, d.amax,
-                                                                   d.maxdisp, d.B, d.work_count);
+    k_keys_inc<<<nblocks(std::max<int64_t>(N, d.B)), TPB, 0, s>>>(d.pos, N, d.params, d.key_id, d.chg_bits,
+                                                                   d.tile_cnt, d.amax, d.maxdisp, d.B,
+                                                                   d.work_count);
     if (N == 0) return;
-    exclusive_scan_u32(d.chg, d.cpos, N, d.counts, d.scan_tmp_n, scan_tmp_elems(N), s);
-    k_compact_changed<<<nblocks(N), TPB, 0, s>>>(d.chg, d.cpos, d.key_id, N, d.ck[0], d.cv[0]);
+    const int64_t nb = nblocks(N);
+    k_keep_bits<<<nb, TPB, 0, s>>>(d.id[0], d.chg_bits, N, d.keep_bits, d.tile_cnt + nb);
+    exclusive_scan_u32(d.tile_cnt, d.tile_pos, 2 * nb, nullptr, d.scan_tmp_n, scan_tmp_elems(2 * nb), s);
+    k_order_counts<<<1, 1, 0, s>>>(d.tile_cnt, d.tile_pos, nb, d.counts);
+    k_compact_changed<<<nb, TPB, 0, s>>>(d.chg_bits, d.tile_pos, d.key_id, N, d.ck[0], d.cv[0]);
     const int cb = radix_sort_u32_dev(d.ck, d.cv, N, d.counts, d.key_bits, d.hist, d.totals, s);
-    k_keep_flags<<<nblocks(N), TPB, 0, s>>>(d.id[0], d.chg, N, d.keep);
-    exclusive_scan_u32(d.keep, d.cpos, N, d.counts + 1, d.scan_tmp_n, scan_tmp_elems(N), s);
-    k_compact_kept<<<nblocks(N), TPB, 0, s>>>(d.keep, d.cpos, d.key[0], d.id[0], N, d.uk, d.uv);
+    k_compact_kept<<<nb, TPB, 0, s>>>(d.keep_bits, d.tile_pos, nb, d.key[0], d.id[0], N, d.uk, d.uv);
     const int nblk = (int)((N + kMergeTile - 1) / kMergeTile);
     k_merge_splits<<<(nblk + 1 + 255) / 256, 256, 0, s>>>(d.uk, d.uv, d.ck[cb], d.cv[cb], d.counts, N, nblk,
                                                           d.split);
@@ -1551,9 +1620,9 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
 int grid_kernels(const DevGroup &d) {
     const int tail = 1 + scan_clear_launches(kSlabs * d.total_cells + 1);    // gather + start scan
     if (!d.incremental) return 1 + 3 * d.passes + tail;
-    // keys, 2 scans with totals, 2 compactions, keep flags, the changed
-    // list's radix passes, merge splits and merge
-    return 1 + 2 * (scan_launches(d.N) + 1) + 3 + 3 * d.passes + 2 + tail;
+    // keys, keep bits, the scan of the tile counts and the counts, 2
+    // compactions, the changed list's radix passes, merge splits and merge
+    return 2 + scan_launches(2 * (int64_t)nblocks(d.N)) + 1 + 2 + 3 * d.passes + 2 + tail;
 }
 
 int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
