@@ -302,9 +302,9 @@ int Group::alloc_order_state(std::string &err) {
     const size_t n1 = (size_t)std::max<int64_t>(g.N, 1);
     const int64_t nblk = (std::max<int64_t>(g.N, 1) + 2047) / 2048;
     CKA(dev_malloc(&g.key_id, sizeof(uint32_t) * n1));
-    // tiles of 256 (the block of the compactions), 32 flags a word
-    const int64_t ntile = (std::max<int64_t>(g.N, 1) + 255) / 256;
-    const size_t nword = (size_t)(ntile * 8);
+    // tiles of 2048 (those of the compactions), 32 flags a word
+    const int64_t ntile = (std::max<int64_t>(g.N, 1) + 2047) / 2048;
+    const size_t nword = (size_t)(ntile * 64);
     CKA(dev_malloc(&g.chg_bits, sizeof(uint32_t) * nword));
     CKA(dev_malloc(&g.keep_bits, sizeof(uint32_t) * nword));
     CKA(dev_malloc(&g.tile_cnt, sizeof(uint32_t) * (size_t)(2 * ntile)));

@@ -160,7 +160,7 @@ struct DevGroup {
     uint32_t *key_id = nullptr;    // by id: fine key at the last grid build (~0: none)
     uint32_t *chg_bits = nullptr;  // by id: key changed, one bit each (bit i & 31 of word i >> 5)
     uint32_t *keep_bits = nullptr; // by previous slot: key kept, one bit each
-    uint32_t *tile_cnt = nullptr;  // set bits of every tile of 256: the changed tiles, then the kept ones
+    uint32_t *tile_cnt = nullptr;  // set bits of every tile of 2048: the changed tiles, then the kept ones
     uint32_t *tile_pos = nullptr;  // their exclusive scan
     uint32_t *ck[2] = {nullptr, nullptr}, *cv[2] = {nullptr, nullptr};   // changed (key, id), radix ping-pong
     uint32_t *uk = nullptr, *uv = nullptr;   // kept (key, id) in previous order

@@ -46,7 +46,6 @@ uint32_t check_word_take() {
 namespace {
 
 constexpr int TPB = 256;
-static_assert(TPB == 256, "the order state (Group::alloc_order_state) has tiles of 256");
 
 inline unsigned nblocks(int64_t n, int t = TPB) { return (unsigned)std::max<int64_t>((n + t - 1) / t, 1); }
 
@@ -143,72 +142,78 @@ __global__ void __launch_bounds__(TPB) k_keys(const float4 *__restrict__ pos, in
 // stale or foreign previous order every key counts as changed and the
 // repair is a full sort.
 
-// The flags of both compactions are bits, one 32-bit word per warp (bit
-// i & 31 of word i >> 5: 1/32 of the bytes of a flag array, small enough to
-// stay in L2), and every block of TPB threads counts its set bits.  One
-// exclusive scan of the 2 x tiles counts (the changed tiles by id, then the
-// kept tiles by previous slot) places every tile; inside a tile a bit's rank
-// is the set bits before it, from the warps' counts and the word.
+// The flags of both compactions are bits (bit i & 31 of word i >> 5: 1/32 of
+// the bytes of a flag array, small enough to stay in L2).  A block handles a
+// tile of kOrdTile items, kOrdItems per thread at stride TPB (item tile0 +
+// TPB j + thread): fewer, longer blocks than one item per thread, whose
+// launch cost would exceed the work of these light passes.  Word j of warp w
+// holds items tile0 + TPB j + 32 w + (0..31); every tile counts its set
+// bits.  One exclusive scan of the 2 x tiles counts (the changed tiles by
+// id, then the kept tiles by previous slot) places every tile; inside a tile
+// a bit's rank is the set bits of the earlier words and lanes.
+constexpr int kOrdItems = 8, kOrdTile = TPB * kOrdItems, kOrdWords = kOrdItems * (TPB / 32);
+static_assert(kOrdWords == 64, "tile_ranks scans two word counts per lane");
+static_assert(kOrdTile == 2048, "the order state (Group::alloc_order_state) has tiles of 2048");
 
-// rank of this lane's bit among the set bits of the block's words (one word
-// per warp, the same in all its lanes); every thread of the block calls it
-__device__ inline uint32_t block_bit_rank(uint32_t word, uint32_t *wcnt) {
+// the word counts of a tile, summed: its number of set bits
+__device__ inline void store_tile_count(uint32_t cnt, int64_t N, uint32_t *__restrict__ tile_cnt, uint32_t *wcnt) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) wcnt[w] = __popc(word);
+    if (lane == 0) wcnt[w] = cnt;
     __syncthreads();
-    uint32_t before = 0;
-    for (int q = 0; q < w; q++) before += wcnt[q];
-    return before + __popc(word & ((1u << lane) - 1u));
-}
-
-// the warps' words of a block's flags stored and their set bits counted
-__device__ inline void store_tile_bits(bool flag, int64_t i, int64_t N, uint32_t *__restrict__ bits,
-                                       uint32_t *__restrict__ tile_cnt, uint32_t *wcnt) {
-    const uint32_t word = __ballot_sync(~0u, flag);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-        if (i < N) bits[i >> 5] = word;   // i is a multiple of 32 in lane 0
-        wcnt[w] = __popc(word);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && (int64_t)blockIdx.x * TPB < N) {
+    if (threadIdx.x == 0 && (int64_t)blockIdx.x * kOrdTile < N) {
         uint32_t t = 0;
         for (int q = 0; q < TPB / 32; q++) t += wcnt[q];
         tile_cnt[blockIdx.x] = t;
     }
 }
 
-// key of particle i (the rule of k_keys), compared with the key it had at
-// the last grid build: the changed bits by id and their tile counts; key_id[i]
-// updated
+// key of every particle (the rule of k_keys), compared with the key it had
+// at the last grid build: the changed bits by id and their tile counts;
+// key_id updated
 __global__ void __launch_bounds__(TPB) k_keys_inc(const float4 *__restrict__ pos, int64_t N,
                                                   const AsmParams *__restrict__ P, uint32_t *__restrict__ key_id,
                                                   uint32_t *__restrict__ chg_bits, uint32_t *__restrict__ tile_cnt,
                                                   uint32_t *__restrict__ amax, uint32_t *__restrict__ maxdisp, int B,
                                                   uint32_t *__restrict__ work_count) {
     __shared__ uint32_t wcnt[TPB / 32];
-    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (i < B) {
-        amax[i] = 0u;
-        maxdisp[i] = 0u;
+    const int64_t g = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (g < B) {
+        amax[g] = 0u;
+        maxdisp[g] = 0u;
     }
-    if (i == 0) {
+    if (g == 0) {
         work_count[0] = 0u;
         work_count[1] = 0u;
     }
-    bool changed = false;
-    if (i < N) {
-        const float4 p = pos[i];
-        const AsmParams &A = P[body_of(p.w)];
-        const int fx = fine_coord(p.x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
-        const int cy = cell_coord(p.y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
-        const int cz = cell_coord(p.z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
-        const uint32_t k = kSlabs * A.key_base + (uint32_t)fx +
-                           kSlabs * (uint32_t)A.ng_n[0] * grid_row(A, cy, cz);
-        changed = k != key_id[i];
-        if (changed) key_id[i] = k;
+    const int64_t i0 = (int64_t)blockIdx.x * kOrdTile + threadIdx.x;
+    float4 p[kOrdItems];
+    uint32_t old[kOrdItems];
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) {
+        const int64_t i = i0 + (int64_t)j * TPB;
+        p[j] = i < N ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        old[j] = i < N ? key_id[i] : 0u;
     }
-    store_tile_bits(changed, i, N, chg_bits, tile_cnt, wcnt);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) {
+        const int64_t i = i0 + (int64_t)j * TPB;
+        bool changed = false;
+        if (i < N) {
+            const AsmParams &A = P[body_of(p[j].w)];
+            const int fx = fine_coord(p[j].x, A.ng_o[0], A.ng_inv, A.ng_n[0]);
+            const int cy = cell_coord(p[j].y, A.ng_o[1], A.ng_inv, A.ng_n[1]);
+            const int cz = cell_coord(p[j].z, A.ng_o[2], A.ng_inv, A.ng_n[2]);
+            const uint32_t k = kSlabs * A.key_base + (uint32_t)fx +
+                               kSlabs * (uint32_t)A.ng_n[0] * grid_row(A, cy, cz);
+            changed = k != old[j];
+            if (changed) key_id[i] = k;
+        }
+        const uint32_t word = __ballot_sync(~0u, changed);
+        if ((threadIdx.x & 31) == 0 && i < N) chg_bits[i >> 5] = word;   // i is a multiple of 32 in lane 0
+        cnt += __popc(word);
+    }
+    store_tile_count(cnt, N, tile_cnt, wcnt);
 }
 
 // the kept bits by previous slot (the particle in slot k kept its key) and
@@ -218,13 +223,58 @@ __global__ void __launch_bounds__(TPB) k_keep_bits(const uint32_t *__restrict__ 
                                                    uint32_t *__restrict__ keep_bits,
                                                    uint32_t *__restrict__ tile_cnt) {
     __shared__ uint32_t wcnt[TPB / 32];
-    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    bool kept = false;
-    if (k < N) {
-        const uint32_t id = prev_id[k];
-        kept = FPPG_CHECK(id < N, kChkCompact) && !((chg_bits[id >> 5] >> (id & 31)) & 1u);
+    const int64_t k0 = (int64_t)blockIdx.x * kOrdTile + threadIdx.x;
+    uint32_t id[kOrdItems];
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) {
+        const int64_t k = k0 + (int64_t)j * TPB;
+        id[j] = k < N ? prev_id[k] : 0u;
     }
-    store_tile_bits(kept, k, N, keep_bits, tile_cnt, wcnt);
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) {
+        const int64_t k = k0 + (int64_t)j * TPB;
+        const bool kept = k < N && FPPG_CHECK(id[j] < N, kChkCompact) &&
+                          !((chg_bits[id[j] >> 5] >> (id[j] & 31)) & 1u);
+        const uint32_t word = __ballot_sync(~0u, kept);
+        if ((threadIdx.x & 31) == 0 && k < N) keep_bits[k >> 5] = word;
+        cnt += __popc(word);
+    }
+    store_tile_count(cnt, N, tile_cnt, wcnt);
+}
+
+// this thread's words of a tile (word j of its warp) and, for each, the rank
+// of its own bit among the tile's set bits in item order (j, then warp, then
+// lane); sc: kOrdWords shared words
+__device__ inline void tile_ranks(const uint32_t *__restrict__ bits, int64_t tile0, int64_t N,
+                                  uint32_t (&word)[kOrdItems], uint32_t (&rank)[kOrdItems], uint32_t *sc) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) {
+        const int64_t i0 = tile0 + (int64_t)j * TPB + 32 * w;
+        word[j] = i0 < N ? bits[i0 >> 5] : 0u;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < kOrdItems; j++) sc[j * (TPB / 32) + w] = __popc(word[j]);
+    __syncthreads();
+    if (w == 0) {
+        // exclusive scan of the 64 word counts, two per lane
+        const uint32_t a = sc[2 * lane], b = sc[2 * lane + 1];
+        uint32_t v = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(~0u, v, o);
+            if (lane >= o) v += t;
+        }
+        const uint32_t ex = v - a - b;
+        sc[2 * lane] = ex;
+        sc[2 * lane + 1] = ex + a;
+    }
+    __syncthreads();
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) rank[j] = sc[j * (TPB / 32) + w] + __popc(word[j] & lt);
 }
 
 // the changed particles, in id order: (key, id) at their positions
@@ -232,16 +282,21 @@ __global__ void __launch_bounds__(TPB) k_compact_changed(const uint32_t *__restr
                                                          const uint32_t *__restrict__ tile_pos,
                                                          const uint32_t *__restrict__ key_id, int64_t N,
                                                          uint32_t *__restrict__ ck, uint32_t *__restrict__ cv) {
-    __shared__ uint32_t wcnt[TPB / 32];
-    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    const int64_t i0 = i & ~(int64_t)31;
-    const uint32_t word = i0 < N ? chg_bits[i0 >> 5] : 0u;
-    const uint32_t r = block_bit_rank(word, wcnt);
-    if (!((word >> (threadIdx.x & 31)) & 1u)) return;
-    const uint32_t p = tile_pos[blockIdx.x] + r;
-    if (!FPPG_CHECK(p < N, kChkCompact)) return;
-    ck[p] = key_id[i];
-    cv[p] = (uint32_t)i;
+    __shared__ uint32_t sc[kOrdWords];
+    const int64_t tile0 = (int64_t)blockIdx.x * kOrdTile;
+    uint32_t word[kOrdItems], rank[kOrdItems];
+    tile_ranks(chg_bits, tile0, N, word, rank, sc);
+    const uint32_t p0 = tile_pos[blockIdx.x];
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) {
+        if (!((word[j] >> lane) & 1u)) continue;
+        const int64_t i = tile0 + (int64_t)j * TPB + threadIdx.x;
+        const uint32_t p = p0 + rank[j];
+        if (!FPPG_CHECK(p < N, kChkCompact)) continue;
+        ck[p] = key_id[i];
+        cv[p] = (uint32_t)i;
+    }
 }
 
 // the kept slots of the previous order, compacted (still sorted); the kept
@@ -252,16 +307,21 @@ __global__ void __launch_bounds__(TPB) k_compact_kept(const uint32_t *__restrict
                                                       const uint32_t *__restrict__ prev_key,
                                                       const uint32_t *__restrict__ prev_id, int64_t N,
                                                       uint32_t *__restrict__ uk, uint32_t *__restrict__ uv) {
-    __shared__ uint32_t wcnt[TPB / 32];
-    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    const int64_t k0 = k & ~(int64_t)31;
-    const uint32_t word = k0 < N ? keep_bits[k0 >> 5] : 0u;
-    const uint32_t r = block_bit_rank(word, wcnt);
-    if (!((word >> (threadIdx.x & 31)) & 1u)) return;
-    const uint32_t p = tile_pos[nb + blockIdx.x] - tile_pos[nb] + r;
-    if (!FPPG_CHECK(p < N, kChkCompact)) return;
-    uk[p] = prev_key[k];
-    uv[p] = prev_id[k];
+    __shared__ uint32_t sc[kOrdWords];
+    const int64_t tile0 = (int64_t)blockIdx.x * kOrdTile;
+    uint32_t word[kOrdItems], rank[kOrdItems];
+    tile_ranks(keep_bits, tile0, N, word, rank, sc);
+    const uint32_t p0 = tile_pos[nb + blockIdx.x] - tile_pos[nb];
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kOrdItems; j++) {
+        if (!((word[j] >> lane) & 1u)) continue;
+        const int64_t k = tile0 + (int64_t)j * TPB + threadIdx.x;
+        const uint32_t p = p0 + rank[j];
+        if (!FPPG_CHECK(p < N, kChkCompact)) continue;
+        uk[p] = prev_key[k];
+        uv[p] = prev_id[k];
+    }
 }
 
 // counts[0] = changed particles, counts[1] = kept slots, from the scan of
@@ -1584,11 +1644,11 @@ __global__ void k_class_sums(const float4 *__restrict__ pos_s, const float *__re
 // also the previous order it starts from
 static void order_incremental(DevGroup &d, cudaStream_t s) {
     const int64_t N = d.N;
-    k_keys_inc<<<nblocks(std::max<int64_t>(N, d.B)), TPB, 0, s>>>(d.pos, N, d.params, d.key_id, d.chg_bits,
-                                                                   d.tile_cnt, d.amax, d.maxdisp, d.B,
-                                                                   d.work_count);
+    const int64_t nb = nblocks(N, kOrdTile);
+    k_keys_inc<<<std::max<unsigned>(nb, nblocks(d.B)), TPB, 0, s>>>(d.pos, N, d.params, d.key_id, d.chg_bits,
+                                                                     d.tile_cnt, d.amax, d.maxdisp, d.B,
+                                                                     d.work_count);
     if (N == 0) return;
-    const int64_t nb = nblocks(N);
     k_keep_bits<<<nb, TPB, 0, s>>>(d.id[0], d.chg_bits, N, d.keep_bits, d.tile_cnt + nb);
     exclusive_scan_u32(d.tile_cnt, d.tile_pos, 2 * nb, nullptr, d.scan_tmp_n, scan_tmp_elems(2 * nb), s);
     k_order_counts<<<1, 1, 0, s>>>(d.tile_cnt, d.tile_pos, nb, d.counts);
@@ -1622,7 +1682,7 @@ int grid_kernels(const DevGroup &d) {
     if (!d.incremental) return 1 + 3 * d.passes + tail;
     // keys, keep bits, the scan of the tile counts and the counts, 2
     // compactions, the changed list's radix passes, merge splits and merge
-    return 2 + scan_launches(2 * (int64_t)nblocks(d.N)) + 1 + 2 + 3 * d.passes + 2 + tail;
+    return 2 + scan_launches(2 * (int64_t)nblocks(d.N, kOrdTile)) + 1 + 2 + 3 * d.passes + 2 + tail;
 }
 
 int build_grid(Group &g, cudaStream_t s) { return build_grid_dev(g.d, s); }
