@@ -9,6 +9,7 @@
 //               global writes are contiguous runs per digit
 // No CTA waits on another CTA, so nothing here can spin.
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 
 #include "fppg_internal.cuh"
@@ -68,21 +69,24 @@ __global__ void __launch_bounds__(RT) k_upsweep(const K *__restrict__ keys, int6
     constexpr int TILE = RW * RC * 32, ND = 1 << DB;
     __shared__ uint32_t cnt[ND];
     if (n_dev) n = min(n, (int64_t)*n_dev);
-    if ((int64_t)blockIdx.x * TILE >= n) return;   // a tile past the count
-    for (int d = threadIdx.x; d < ND; d += RT) cnt[d] = 0;
-    __syncthreads();
+    const int n_act = (int)min((int64_t)n_tiles, (n + TILE - 1) / TILE);   // tiles past the count: none
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int64_t base = (int64_t)blockIdx.x * TILE + w * (RC * 32) + l;
+    for (int tile = blockIdx.x; tile < n_act; tile += gridDim.x) {
+        for (int d = threadIdx.x; d < ND; d += RT) cnt[d] = 0;
+        __syncthreads();
+        const int64_t base = (int64_t)tile * TILE + w * (RC * 32) + l;
 #pragma unroll 4
-    for (int c = 0; c < RC; c++) {
-        int64_t idx = base + c * 32;
-        bool valid = idx < n;
-        uint32_t d = valid ? (uint32_t)((keys[idx] >> shift) & (K)(ND - 1)) : (uint32_t)ND;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (uint32_t)(__ffs(peers) - 1) == (uint32_t)l) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+        for (int c = 0; c < RC; c++) {
+            int64_t idx = base + c * 32;
+            bool valid = idx < n;
+            uint32_t d = valid ? (uint32_t)((keys[idx] >> shift) & (K)(ND - 1)) : (uint32_t)ND;
+            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && (uint32_t)(__ffs(peers) - 1) == (uint32_t)l) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < ND; d += RT) hist[(int64_t)d * n_tiles + tile] = cnt[d];
+        __syncthreads();   // cnt is zeroed again for the next tile
     }
-    __syncthreads();
-    for (int d = threadIdx.x; d < ND; d += RT) hist[(int64_t)d * n_tiles + blockIdx.x] = cnt[d];
 }
 
 // one CTA per digit: exclusive scan of its row of per-tile counts, over the
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, con
                                                   const uint32_t *__restrict__ n_dev) {
     constexpr int TILE = RW * RC * 32, ND = 1 << DB, KD = ND / RT;
     if (n_dev) n = min(n, (int64_t)*n_dev);
-    if ((int64_t)blockIdx.x * TILE >= n) return;   // the whole block: no barrier is left waiting
+    const int n_act = (int)min((int64_t)n_tiles, (n + TILE - 1) / TILE);   // tiles past the count: none
     extern __shared__ __align__(16) unsigned char smem[];
     K *skey = reinterpret_cast<K *>(smem);
     uint32_t *sval = reinterpret_cast<uint32_t *>(smem + sizeof(K) * TILE);
@@ -123,77 +127,80 @@ __global__ void __launch_bounds__(RT) k_downsweep(const K *__restrict__ kin, con
     uint32_t *wsum = gbase + ND;
 
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < RW * ND; i += RT) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
+    for (int tile = blockIdx.x; tile < n_act; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < RW * ND; i += RT) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
 
-    const int64_t tile0 = (int64_t)blockIdx.x * TILE;
-    const int64_t base = tile0 + w * (RC * 32) + l;
-    K k[RC];
-    uint32_t v[RC], rank[RC];
-    const uint32_t lt = lanemask_lt();
+        const int64_t tile0 = (int64_t)tile * TILE;
+        const int64_t base = tile0 + w * (RC * 32) + l;
+        K k[RC];
+        uint32_t v[RC], rank[RC];
+        const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int c = 0; c < RC; c++) {
-        int64_t idx = base + c * 32;
-        bool valid = idx < n;
-        k[c] = valid ? kin[idx] : (K)0;
-        v[c] = valid ? (IOTA ? (uint32_t)idx : vin[idx]) : 0u;
-        uint32_t d = valid ? (uint32_t)((k[c] >> shift) & (K)(ND - 1)) : (uint32_t)ND;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = valid ? wcnt[w][d] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt) == 0u) wcnt[w][d] = before + __popc(peers);
-        __syncwarp();
-        rank[c] = before + __popc(peers & lt);
-    }
-    __syncthreads();
-    // thread t owns digits t KD .. t KD + KD - 1: per-warp exclusive offsets,
-    // the tile count and the global start of each
-    uint32_t cnt_d[KD], tot_d[KD], s_cnt = 0, s_tot = 0;
-#pragma unroll
-    for (int j = 0; j < KD; j++) {
-        const int d = threadIdx.x * KD + j;
-        uint32_t run = 0;
-#pragma unroll
-        for (int ww = 0; ww < RW; ww++) {
-            uint32_t t = wcnt[ww][d];
-            wcnt[ww][d] = run;
-            run += t;
+        for (int c = 0; c < RC; c++) {
+            int64_t idx = base + c * 32;
+            bool valid = idx < n;
+            k[c] = valid ? kin[idx] : (K)0;
+            v[c] = valid ? (IOTA ? (uint32_t)idx : vin[idx]) : 0u;
+            uint32_t d = valid ? (uint32_t)((k[c] >> shift) & (K)(ND - 1)) : (uint32_t)ND;
+            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            uint32_t before = valid ? wcnt[w][d] : 0u;
+            __syncwarp();
+            if (valid && (peers & lt) == 0u) wcnt[w][d] = before + __popc(peers);
+            __syncwarp();
+            rank[c] = before + __popc(peers & lt);
         }
-        cnt_d[j] = run;
-        s_cnt += run;
-        tot_d[j] = totals[d];
-        s_tot += tot_d[j];
-    }
-    uint32_t tmp;
-    uint32_t loc = block_incl_scan(s_cnt, wsum, &tmp) - s_cnt;
-    uint32_t dig = block_incl_scan(s_tot, wsum, &tmp) - s_tot;
+        __syncthreads();
+        // thread t owns digits t KD .. t KD + KD - 1: per-warp exclusive offsets,
+        // the tile count and the global start of each
+        uint32_t cnt_d[KD], tot_d[KD], s_cnt = 0, s_tot = 0;
 #pragma unroll
-    for (int j = 0; j < KD; j++) {
-        const int d = threadIdx.x * KD + j;
-        dstart[d] = loc;
-        gbase[d] = dig + hist[(int64_t)d * n_tiles + blockIdx.x] - loc;
-        loc += cnt_d[j];
-        dig += tot_d[j];
-    }
-    __syncthreads();
+        for (int j = 0; j < KD; j++) {
+            const int d = threadIdx.x * KD + j;
+            uint32_t run = 0;
 #pragma unroll
-    for (int c = 0; c < RC; c++) {
-        int64_t idx = base + c * 32;
-        if (idx < n) {
-            uint32_t dd = (uint32_t)((k[c] >> shift) & (K)(ND - 1));
-            uint32_t p = dstart[dd] + wcnt[w][dd] + rank[c];
-            skey[p] = k[c];
-            sval[p] = v[c];
+            for (int ww = 0; ww < RW; ww++) {
+                uint32_t t = wcnt[ww][d];
+                wcnt[ww][d] = run;
+                run += t;
+            }
+            cnt_d[j] = run;
+            s_cnt += run;
+            tot_d[j] = totals[d];
+            s_tot += tot_d[j];
         }
-    }
-    __syncthreads();
-    const int tile_n = (int)min((int64_t)TILE, n - tile0);
-    for (int j = threadIdx.x; j < tile_n; j += RT) {
-        K kk = skey[j];
-        uint32_t dd = (uint32_t)((kk >> shift) & (K)(ND - 1));
-        uint32_t o = gbase[dd] + (uint32_t)j;
-        kout[o] = kk;
-        vout[o] = sval[j];
+        uint32_t tmp;
+        uint32_t loc = block_incl_scan(s_cnt, wsum, &tmp) - s_cnt;
+        uint32_t dig = block_incl_scan(s_tot, wsum, &tmp) - s_tot;
+#pragma unroll
+        for (int j = 0; j < KD; j++) {
+            const int d = threadIdx.x * KD + j;
+            dstart[d] = loc;
+            gbase[d] = dig + hist[(int64_t)d * n_tiles + tile] - loc;
+            loc += cnt_d[j];
+            dig += tot_d[j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < RC; c++) {
+            int64_t idx = base + c * 32;
+            if (idx < n) {
+                uint32_t dd = (uint32_t)((k[c] >> shift) & (K)(ND - 1));
+                uint32_t p = dstart[dd] + wcnt[w][dd] + rank[c];
+                skey[p] = k[c];
+                sval[p] = v[c];
+            }
+        }
+        __syncthreads();
+        const int tile_n = (int)min((int64_t)TILE, n - tile0);
+        for (int j = threadIdx.x; j < tile_n; j += RT) {
+            K kk = skey[j];
+            uint32_t dd = (uint32_t)((kk >> shift) & (K)(ND - 1));
+            uint32_t o = gbase[dd] + (uint32_t)j;
+            kout[o] = kk;
+            vout[o] = sval[j];
+        }
+        __syncthreads();   // the staging and the counters are reused by the next tile
     }
 }
 
@@ -210,21 +217,24 @@ void set_smem_attr() {
                          (int)downsweep_smem<K, RC, DB>());
 }
 
+// grid: CTAs of the sweeps (at most the tiles; each CTA takes every grid-th
+// tile)
 template <typename K, int RC, int DB>
 int radix_passes(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int passes, uint32_t *hist,
-                 uint32_t *totals, cudaStream_t s, const uint32_t *n_dev) {
+                 uint32_t *totals, cudaStream_t s, const uint32_t *n_dev, int grid) {
     constexpr int TILE = RW * RC * 32;
     const int n_tiles = (int)((n + TILE - 1) / TILE);
+    const int g = std::max(1, std::min(grid, n_tiles));
     int cur = 0;
     for (int p = 0; p < passes; p++) {
         const int shift = DB * p;
-        k_upsweep<K, RC, DB><<<n_tiles, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles, n_dev);
+        k_upsweep<K, RC, DB><<<g, RT, 0, s>>>(keys[cur], n, shift, hist, n_tiles, n_dev);
         k_digit_scan<<<1 << DB, RT, 0, s>>>(hist, n_tiles, totals, n, TILE, n_dev);
         if (p == 0 && iota_vals)
-            k_downsweep<K, true, RC, DB><<<n_tiles, RT, downsweep_smem<K, RC, DB>(), s>>>(
+            k_downsweep<K, true, RC, DB><<<g, RT, downsweep_smem<K, RC, DB>(), s>>>(
                 keys[cur], nullptr, keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles, n_dev);
         else
-            k_downsweep<K, false, RC, DB><<<n_tiles, RT, downsweep_smem<K, RC, DB>(), s>>>(
+            k_downsweep<K, false, RC, DB><<<g, RT, downsweep_smem<K, RC, DB>(), s>>>(
                 keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist, totals, n_tiles, n_dev);
         cur ^= 1;
     }
@@ -234,13 +244,19 @@ int radix_passes(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int p
 template <typename K, int DB>
 int radix_sort_db(K *keys[2], uint32_t *vals[2], bool iota_vals, int64_t n, int passes, uint32_t *hist,
                   uint32_t *totals, cudaStream_t s, int sms, const uint32_t *n_dev) {
-    // the largest tile that still gives every SM four tiles (latency hiding)
+    // a count on the device (usually far below n): the smallest tiles, taken
+    // by at most 8 CTAs per SM in turn, so that neither the CTAs of the
+    // tiles past the count nor a long walk through a few large tiles set
+    // the time
+    if (n_dev) return radix_passes<K, 4, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, n_dev, 8 * sms);
+    // else the largest tile that still gives every SM four tiles (latency
+    // hiding), one CTA per tile
     const int64_t want = 4 * (int64_t)sms;
     if ((n + 4095) / 4096 >= want)
-        return radix_passes<K, 16, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, n_dev);
+        return radix_passes<K, 16, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, nullptr, INT32_MAX);
     if ((n + 2047) / 2048 >= want)
-        return radix_passes<K, 8, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, n_dev);
-    return radix_passes<K, 4, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, n_dev);
+        return radix_passes<K, 8, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, nullptr, INT32_MAX);
+    return radix_passes<K, 4, DB>(keys, vals, iota_vals, n, passes, hist, totals, s, nullptr, INT32_MAX);
 }
 
 // once per key type and process (thread-safe static initialisation): the
