@@ -1109,7 +1109,12 @@ __global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_
                                               const float4 *__restrict__ cert, const int32_t *__restrict__ cons_s) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool active = k < N;
+    // the particle's streams are read together, before its class is known
+    // (one round trip to memory instead of two)
     const float4 p = active ? pos_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 a = active ? acc_s[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t i = active ? id_s[k] : 0u;
+    const int c = active ? cons_s[k] : -1;
     const int cls = active ? cls_of(p.w) : kClsI;
     const int b = active ? body_of(p.w) : 0;
     const AsmParams &A = P[b];
@@ -1118,12 +1123,9 @@ __global__ void __launch_bounds__(TPB, 5) k_step(const float4 *__restrict__ pos_
     uint2 rng = make_uint2(0u, 0u);   // candidate list of the trial point's triangle cell
     float3 y = f3(p);
     if (active && is_mobile(cls, A) && !is_ghost(p.w)) {
-        const uint32_t i = id_s[k];
         const float am = __uint_as_float(amax[A.amax_slot]);
         const float sc = am > 0.f ? A.step_h / am : 0.f;     // dt^2 with dt = 0.25 sqrt(h / amax)
-        const float4 a = acc_s[k];
         float3 dr = make_float3(a.x * sc, a.y * sc, a.z * sc);
-        const int c = cons_s[k];
         if (cls == kClsS && c >= 0 && c < A.nt) {
             const float3 n = f3(M.geo[5 * (size_t)(A.tri_off + c) + 1]);
             dr = dr - dot3(dr, n) * n;
