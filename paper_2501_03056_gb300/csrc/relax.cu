@@ -377,13 +377,28 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint32_t *__restr
     // (nu + nc = d1 - d0 <= kMergeTile: the staging fits when both are >= 0)
     if (!FPPG_CHECK(i0 <= i1 && j0 <= j1 && j0 >= 0, kChkMerge)) return;
     const int nu = (int)(i1 - i0), nc = (int)(j1 - j0), n = nu + nc;
-    for (int q = threadIdx.x; q < n; q += kMergeThreads) {
-        if (q < nu) {
-            sk[q] = uk[i0 + q];
-            si[q] = uv[i0 + q];
-        } else {
-            sk[q] = ck[j0 + q - nu];
-            si[q] = cv[j0 + q - nu];
+    {
+        // all loads of a thread issued before the first store (one round trip)
+        uint32_t lk[kMergeItems], li[kMergeItems];
+#pragma unroll
+        for (int r = 0; r < kMergeItems; r++) {
+            const int q = (int)threadIdx.x + r * kMergeThreads;
+            lk[r] = li[r] = 0u;
+            if (q < nu) {
+                lk[r] = uk[i0 + q];
+                li[r] = uv[i0 + q];
+            } else if (q < n) {
+                lk[r] = ck[j0 + q - nu];
+                li[r] = cv[j0 + q - nu];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kMergeItems; r++) {
+            const int q = (int)threadIdx.x + r * kMergeThreads;
+            if (q < n) {
+                sk[q] = lk[r];
+                si[q] = li[r];
+            }
         }
     }
     __syncthreads();
