@@ -97,6 +97,10 @@ def lib():
                 "oracle_stats": (None, [vp, P(f64)]),
                 "oracle_map_particles": (i64, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P(f64), P(i32), P(i32),
                                                 i64]),
+                "oracle_lattice_intervals": (i64, [P(f32), i64, P(f32), f32, P(C.c_uint64), P(C.c_uint64), i64]),
+                "oracle_interval_boolean": (i64, [P(C.c_uint64), P(C.c_uint64), i64, P(C.c_uint64), P(C.c_uint64), i64,
+                                                  C.c_int, P(C.c_uint64), P(C.c_uint64), i64]),
+                "oracle_interval_cells": (i64, [P(C.c_uint64), P(C.c_uint64), i64, P(f32), f32, P(f32), i64]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -124,6 +128,50 @@ def lattice_sum(dx, h, dim):
 
 def morton3(x, y, z):
     return int(lib().oracle_morton3(x, y, z))
+
+
+def _u64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint64).reshape(-1))
+
+
+def lattice_intervals(xyz, origin, d):
+    """C_compact (begin, length) of the lattice cells holding the points:
+    Morton codes (Eq. 9) of the cells, ascending, as maximal runs."""
+    x = np.ascontiguousarray(np.asarray(xyz, np.float32).reshape(-1, 3))
+    o = np.ascontiguousarray(np.asarray(origin, np.float32).reshape(3))
+    n = lib().oracle_lattice_intervals(_p(x, C.c_float), len(x), _p(o, C.c_float), float(d), None, None, 0)
+    if n < 0:
+        raise ValueError("a point lies outside the lattice")
+    b, l_ = np.zeros(n, np.uint64), np.zeros(n, np.uint64)
+    lib().oracle_lattice_intervals(_p(x, C.c_float), len(x), _p(o, C.c_float), float(d), _p(b, C.c_uint64),
+                                   _p(l_, C.c_uint64), n)
+    return b, l_
+
+
+def interval_boolean(a, b, op):
+    """op(A, B) of two run lists ((begin, length) pairs of arrays): union 0,
+    difference 1, intersection 2, as maximal runs (Fig. 10)."""
+    ab, al, bb, bl = _u64(a[0]), _u64(a[1]), _u64(b[0]), _u64(b[1])
+    args = (_p(ab, C.c_uint64), _p(al, C.c_uint64), len(ab), _p(bb, C.c_uint64), _p(bl, C.c_uint64), len(bb), int(op))
+    n = lib().oracle_interval_boolean(*args, None, None, 0)
+    if n < 0:
+        raise ValueError("unknown op or a run past 2^63")
+    ob, ol = np.zeros(n, np.uint64), np.zeros(n, np.uint64)
+    lib().oracle_interval_boolean(*args, _p(ob, C.c_uint64), _p(ol, C.c_uint64), n)
+    return ob, ol
+
+
+def interval_cells(runs, origin, d):
+    """The cell centres of a run list, in run order and code order."""
+    b, l_ = _u64(runs[0]), _u64(runs[1])
+    o = np.ascontiguousarray(np.asarray(origin, np.float32).reshape(3))
+    n = lib().oracle_interval_cells(_p(b, C.c_uint64), _p(l_, C.c_uint64), len(b), _p(o, C.c_float), float(d), None, 0)
+    if n < 0:
+        raise ValueError("a run past 2^63")
+    x = np.zeros((n, 3), np.float32)
+    lib().oracle_interval_cells(_p(b, C.c_uint64), _p(l_, C.c_uint64), len(b), _p(o, C.c_float), float(d),
+                                _p(x, C.c_float), n)
+    return x
 
 
 def set_threads(n: int):

@@ -2639,3 +2639,209 @@ int64_t oracle_map_particles(const or_ctx *c, int surface, int volume, int featu
     }
     return cnt;
 }
+
+/* ------------------------------------------------------------------------ */
+/* C_compact interval form of a cell set and its Boolean algebra            */
+/* (Sec. 3.1.3: C_compact begin / length; Sec. 3.2.3 and Fig. 10: union,    */
+/* difference and intersection of two bodies' grid sets as intervals)       */
+/* ------------------------------------------------------------------------ */
+/* A cell set of a lattice (origin o, spacing d; cells (i, j, k) with
+ * 0 <= i, j, k < 2^21) is the ascending list of its Morton codes (Eq. 9),
+ * run-length encoded: C_compact begin = the first code of a run of
+ * consecutive codes, length = the run's size.  Runs are maximal, so the next
+ * begin lies at least one code past the end of a run. */
+
+static int cmp_u64(const void *a, const void *b)
+{
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* the lattice cell holding point x: floor((x - o) / d) per axis in FP32;
+ * -1 when a coordinate lies outside [0, 2^21) */
+static int lattice_cell(const float *x, const float *o, float d, uint32_t *ijk)
+{
+    for (int a = 0; a < 3; a++) {
+        const float t = floorf((x[a] - o[a]) / d);
+        if (!(t >= 0.0f && t < 2097152.0f)) return -1;
+        ijk[a] = (uint32_t)t;
+    }
+    return 0;
+}
+
+/* Morton code (Eq. 9) back to its cell: bit 3b + a of the code is bit b of
+ * axis a */
+static void morton3_decode(uint64_t code, uint32_t *ijk)
+{
+    ijk[0] = ijk[1] = ijk[2] = 0;
+    for (int b = 0; b < 21; b++)
+        for (int a = 0; a < 3; a++) ijk[a] |= (uint32_t)((code >> (3 * b + a)) & 1u) << b;
+}
+
+/* maximal runs of ascending codes (repeats allowed); returns the count and
+ * writes at most cap runs */
+static int64_t runs_of_codes(const uint64_t *code, int64_t n, uint64_t *begin, uint64_t *len, int64_t cap)
+{
+    int64_t r = 0;
+    int64_t i = 0;
+    while (i < n) {
+        const uint64_t b = code[i];
+        uint64_t e = b + 1;
+        i++;
+        while (i < n && code[i] <= e) {   /* a repeat (< e) or the next code (== e) */
+            if (code[i] == e) e++;
+            i++;
+        }
+        if (r < cap) {
+            begin[r] = b;
+            len[r] = e - b;
+        }
+        r++;
+    }
+    return r;
+}
+
+/* C_compact of the cells that hold the n points: the codes of their cells,
+ * sorted, as maximal runs.  Returns the run count (at most cap written), -1
+ * for a point outside the lattice or d not finite and > 0. */
+int64_t oracle_lattice_intervals(const float *xyz, int64_t n, const float *o, float d, uint64_t *begin, uint64_t *len,
+                                 int64_t cap)
+{
+    if (n < 0 || !(d > 0.0f) || !isfinite(d)) return -1;
+    uint64_t *code = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; i++) {
+        uint32_t c[3];
+        if (lattice_cell(xyz + 3 * i, o, d, c)) {
+            free(code);
+            return -1;
+        }
+        code[i] = oracle_morton3(c[0], c[1], c[2]);
+    }
+    qsort(code, (size_t)n, sizeof(uint64_t), cmp_u64);
+    const int64_t r = runs_of_codes(code, n, begin, len, cap);
+    free(code);
+    return r;
+}
+
+typedef struct {
+    uint64_t b, e;   /* [b, e) */
+} or_run;
+
+static int cmp_run(const void *a, const void *b)
+{
+    const or_run *x = a, *y = b;
+    return x->b < y->b ? -1 : (x->b > y->b ? 1 : 0);
+}
+
+/* the same set as maximal runs in ascending order: empty runs dropped,
+ * overlapping and touching runs joined.  Returns the count, -1 when a run's
+ * end passes 2^63. */
+static int64_t canonical_runs(const uint64_t *b, const uint64_t *l, int64_t n, or_run *out)
+{
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (l[i] == 0) continue;
+        if (b[i] >= (1ull << 63) || l[i] > (1ull << 63) - b[i]) return -1;
+        out[m].b = b[i];
+        out[m].e = b[i] + l[i];
+        m++;
+    }
+    qsort(out, (size_t)m, sizeof(or_run), cmp_run);
+    int64_t k = 0;
+    for (int64_t i = 0; i < m; i++) {
+        if (k > 0 && out[i].b <= out[k - 1].e) {
+            if (out[i].e > out[k - 1].e) out[k - 1].e = out[i].e;
+        } else {
+            out[k++] = out[i];
+        }
+    }
+    return k;
+}
+
+/* is code p in the canonical runs r[0..n)?  (binary search for the last run
+ * that begins at or before p) */
+static int in_runs(const or_run *r, int64_t n, uint64_t p)
+{
+    int64_t lo = 0, hi = n;   /* first run with b > p */
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (r[mid].b <= p) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo > 0 && p < r[lo - 1].e;
+}
+
+/* Fig. 10's interval algebra: the cells c with op(c in A, c in B) -- union
+ * (op 0), difference A - B (op 1), intersection (op 2) -- as maximal runs.
+ * The inputs may be in any order, overlap, touch or hold empty runs.  Every
+ * begin or end of an input run cuts the code line into pieces on which
+ * membership in A and in B is constant; a piece is tested at its first code
+ * and joined to the previous one when both are in.  Returns the run count
+ * (at most cap written), -1 for an unknown op or a run past 2^63. */
+int64_t oracle_interval_boolean(const uint64_t *ab, const uint64_t *al, int64_t na, const uint64_t *bb,
+                                const uint64_t *bl, int64_t nb, int op, uint64_t *ob, uint64_t *ol, int64_t cap)
+{
+    if (op < 0 || op > 2 || na < 0 || nb < 0) return -1;
+    or_run *A = malloc(sizeof(or_run) * (size_t)(na > 0 ? na : 1));
+    or_run *B = malloc(sizeof(or_run) * (size_t)(nb > 0 ? nb : 1));
+    const int64_t ma = canonical_runs(ab, al, na, A), mb = canonical_runs(bb, bl, nb, B);
+    if (ma < 0 || mb < 0) {
+        free(A);
+        free(B);
+        return -1;
+    }
+    const int64_t np = 2 * (ma + mb);
+    uint64_t *pt = malloc(sizeof(uint64_t) * (size_t)(np > 0 ? np : 1));
+    int64_t k = 0;
+    for (int64_t i = 0; i < ma; i++) {
+        pt[k++] = A[i].b;
+        pt[k++] = A[i].e;
+    }
+    for (int64_t i = 0; i < mb; i++) {
+        pt[k++] = B[i].b;
+        pt[k++] = B[i].e;
+    }
+    qsort(pt, (size_t)np, sizeof(uint64_t), cmp_u64);
+    int64_t r = 0;
+    int open = 0;   /* the previous piece was in the result */
+    for (int64_t i = 0; i + 1 < np; i++) {
+        if (pt[i] == pt[i + 1]) continue;   /* an empty piece */
+        const int inA = in_runs(A, ma, pt[i]), inB = in_runs(B, mb, pt[i]);
+        const int in = op == 0 ? (inA || inB) : (op == 1 ? (inA && !inB) : (inA && inB));
+        if (in && open) {
+            if (r - 1 < cap) ol[r - 1] = pt[i + 1] - ob[r - 1];
+        } else if (in) {
+            if (r < cap) {
+                ob[r] = pt[i];
+                ol[r] = pt[i + 1] - pt[i];
+            }
+            r++;
+        }
+        open = in;
+    }
+    free(pt);
+    free(A);
+    free(B);
+    return r;
+}
+
+/* the cells of runs (in the given order, codes ascending within a run) as
+ * their centres (float)(o + (i + 0.5) d) per axis, each coordinate evaluated
+ * in FP64 and rounded once -- the generation's cell centres.  Returns the
+ * cell count (at most cap written), -1 for a run past 2^63. */
+int64_t oracle_interval_cells(const uint64_t *b, const uint64_t *l, int64_t n, const float *o, float d, float *xyz,
+                              int64_t cap)
+{
+    int64_t cnt = 0;
+    for (int64_t r = 0; r < n; r++) {
+        if (b[r] >= (1ull << 63) || l[r] > (1ull << 63) - b[r]) return -1;
+        for (uint64_t c = b[r]; c < b[r] + l[r]; c++, cnt++) {
+            if (cnt >= cap) continue;
+            uint32_t ijk[3];
+            morton3_decode(c, ijk);
+            for (int a = 0; a < 3; a++)
+                xyz[3 * cnt + a] = (float)((double)o[a] + ((double)ijk[a] + 0.5) * (double)d);
+        }
+    }
+    return cnt;
+}
