@@ -477,6 +477,57 @@ int fppg_device_sm_count(int32_t *sms);
  * read. */
 int fppg_check_status(uint32_t *word, int32_t *checked);
 
+/* ---- C_compact interval form of grid sets (Sec. 3.1.3, Sec. 3.2.3) --------
+ * Sec. 3.1.3 stores a body's cells as C_compact begin / length, runs of
+ * consecutive Morton codes (Eq. 9); Sec. 3.2.3 and Fig. 10 combine two
+ * bodies' grid sets by union, difference and intersection of those
+ * intervals.  A lattice is an origin o (3 floats, host) and a spacing d;
+ * cell (i, j, k), 0 <= i, j, k < 2^21, has the Morton code with bit b of i,
+ * j, k at bits 3b, 3b + 1, 3b + 2.  A run list is two device arrays of
+ * uint64: begin (first code of a run) and len (its size).  The result of
+ * every call is a set of maximal runs in ascending order (the next begin
+ * lies at least one code past the end of a run).
+ *
+ * Each call enqueues its work on `stream` (a cudaStream_t, NULL = legacy
+ * default), allocates its temporaries, and synchronises the stream to read
+ * the result count into *n_out; it writes the result only when the count
+ * fits cap (else FPPG_ERR_ARG with *n_out set: call again with room).
+ * Errors (message in fppg_last_error(NULL)): FPPG_ERR_ARG for null buffers,
+ * negative sizes, the cases below; FPPG_ERR_OOM; FPPG_ERR_CUDA. */
+
+/* fppg_grid_lattice: the lattice of a body's generation (Sec. 3.2): the
+ * triangle grid's origin (*origin_host, 3 floats) and spacing dx (*d_host).
+ * fppg_map_particles puts one volume particle at the centre of every
+ * interior cell of that lattice.  Bodies whose lattices coincide (the same
+ * dx and origin) have grid sets that combine cell for cell.  FPPG_ERR_ARG
+ * for a NULL argument. */
+int fppg_grid_lattice(const fppg_ctx *ctx, float *origin_host, float *d_host);
+
+/* fppg_lattice_intervals: C_compact of the cells that hold the n points
+ * xyz_dev [n][3] (device): the cell of a point is floor((x - o) / d) per
+ * axis in FP32; repeated cells count once.  n < 2^32.  FPPG_ERR_ARG for d
+ * not finite and > 0 or a point outside the lattice. */
+int fppg_lattice_intervals(const float *xyz_dev, int64_t n, const float *origin_host, float d, uint64_t *begin_dev,
+                           uint64_t *len_dev, int64_t cap, int64_t *n_out, void *stream);
+
+/* fppg_interval_boolean: the runs of the cells c with op(c in A, c in B),
+ * op = FPPG_UNION, FPPG_DIFFERENCE (A - B) or FPPG_INTERSECTION (Fig. 10).
+ * The input runs may come in any order, overlap, touch or be empty;
+ * na + nb < 2^31.  FPPG_ERR_ARG for another op or a run ending past 2^63. */
+int fppg_interval_boolean(const uint64_t *a_begin_dev, const uint64_t *a_len_dev, int64_t na,
+                          const uint64_t *b_begin_dev, const uint64_t *b_len_dev, int64_t nb, int32_t op,
+                          uint64_t *begin_dev, uint64_t *len_dev, int64_t cap, int64_t *n_out, void *stream);
+
+/* fppg_interval_cells: the cells of n runs as their centres xyz_dev
+ * [*n_out][3] (device), runs in the given order and codes ascending within
+ * a run; each coordinate is (float)(o + (i + 0.5) d) evaluated in FP64 --
+ * the generation's cell centres, so the runs of a body's volume particles
+ * give those particles back bit for bit.  n < 2^32, fewer than 2^32 cells.
+ * FPPG_ERR_ARG for d not finite and > 0, a run ending past 2^63 or a run of
+ * 2^32 cells or more. */
+int fppg_interval_cells(const uint64_t *begin_dev, const uint64_t *len_dev, int64_t n, const float *origin_host,
+                        float d, float *xyz_dev, int64_t cap, int64_t *n_out, void *stream);
+
 /* ---- allocation-free force pass ---------------------------------------------
  * fppg_forces_static: the neighbour grid and the force pass (A1-A4) for one
  * body, without a handle and without allocating any memory: for callers

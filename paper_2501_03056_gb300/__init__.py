@@ -110,6 +110,10 @@ def lib():
                 "fppg_device_sm_count": [P_(i32)],
                 "fppg_debug_fail_allocation": [i64],
                 "fppg_check_status": [P_(C.c_uint32), P_(i32)],
+                "fppg_grid_lattice": [vp, P_(f32), P_(f32)],
+                "fppg_lattice_intervals": [vp, i64, P_(f32), f32, vp, vp, i64, P_(i64), vp],
+                "fppg_interval_boolean": [vp, vp, i64, vp, vp, i64, i32, vp, vp, i64, P_(i64), vp],
+                "fppg_interval_cells": [vp, vp, i64, P_(f32), f32, vp, i64, P_(i64), vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -315,6 +319,12 @@ class Body:
                 "min_pair_over_dx": s.min_pair_over_dx, "max_disp_over_dx": s.max_disp_over_dx,
                 "n_S": s.count[0], "n_V": s.count[1], "n_F": s.count[2]}
 
+    def grid_lattice(self):
+        """(origin, dx) of the body's generation lattice (fppg_grid_lattice)."""
+        o, d = np.zeros(3, np.float32), C.c_float()
+        self._chk(lib().fppg_grid_lattice(self._h, _ptr(o, C.c_float), C.byref(d)))
+        return o, float(d.value)
+
     def debug_grid(self):
         n = self.n
         key, perm = np.zeros(max(n, 1), np.uint32), np.zeros(max(n, 1), np.uint32)
@@ -426,6 +436,74 @@ def boolean_curve(a: "Body", b: "Body") -> int:
         raise FPPGError(r, msg.decode() if isinstance(msg, bytes) else str(msg))
     a.n += n.value
     return n.value
+
+
+def _sized_call(fn, out_alloc):
+    """Run an interval call once for its count (capacity 0), allocate the
+    result with out_alloc(count) -> (pointers, tensors) and run it again."""
+    n = C.c_int64()
+    r = fn(None, 0, C.byref(n))
+    if r != OK and not (r == ERR_ARG and n.value > 0):
+        raise FPPGError(r, lib().fppg_last_error(None).decode())
+    ptrs, out = out_alloc(n.value)
+    if n.value > 0:
+        r = fn(ptrs, n.value, C.byref(n))
+        if r != OK:
+            raise FPPGError(r, lib().fppg_last_error(None).decode())
+    return out
+
+
+def _runs_alloc(m):
+    import torch
+    b = torch.empty(max(m, 1), dtype=torch.int64, device="cuda")
+    ln = torch.empty(max(m, 1), dtype=torch.int64, device="cuda")
+    return (b.data_ptr(), ln.data_ptr()), (b[:m], ln[:m])
+
+
+def lattice_intervals(xyz, origin, d, stream=None):
+    """C_compact of the lattice cells holding the points (fppg_lattice_intervals):
+    xyz a CUDA float32 tensor [n, 3]; returns (begin, len) as CUDA int64
+    tensors (Morton codes of Eq. 9, below 2^63)."""
+    x = xyz.contiguous()
+    o = np.ascontiguousarray(np.asarray(origin, np.float32).reshape(3))
+    sp = _stream_ptr(stream)
+
+    def fn(ptrs, cap, n_out):
+        b, ln = ptrs if ptrs else (None, None)
+        return lib().fppg_lattice_intervals(x.data_ptr(), x.shape[0], _ptr(o, C.c_float), float(d), b, ln, cap,
+                                            n_out, sp)
+    return _sized_call(fn, _runs_alloc)
+
+
+def interval_boolean(a, b, op, stream=None):
+    """op(A, B) (UNION, DIFFERENCE A - B, INTERSECTION) of two run lists
+    ((begin, len) CUDA int64 tensors) as maximal runs (fppg_interval_boolean)."""
+    ab, al, bb, bl = (t.contiguous() for t in (a[0], a[1], b[0], b[1]))
+    sp = _stream_ptr(stream)
+
+    def fn(ptrs, cap, n_out):
+        ob, ol = ptrs if ptrs else (None, None)
+        return lib().fppg_interval_boolean(ab.data_ptr(), al.data_ptr(), ab.numel(), bb.data_ptr(), bl.data_ptr(),
+                                           bb.numel(), int(op), ob, ol, cap, n_out, sp)
+    return _sized_call(fn, _runs_alloc)
+
+
+def interval_cells(runs, origin, d, stream=None):
+    """The centres of the cells of a run list (fppg_interval_cells), a CUDA
+    float32 tensor [cells, 3]."""
+    import torch
+    b, ln = (t.contiguous() for t in runs)
+    o = np.ascontiguousarray(np.asarray(origin, np.float32).reshape(3))
+    sp = _stream_ptr(stream)
+
+    def alloc(m):
+        x = torch.empty((max(m, 1), 3), dtype=torch.float32, device="cuda")
+        return x.data_ptr(), x[:m]
+
+    def fn(ptr, cap, n_out):
+        return lib().fppg_interval_cells(b.data_ptr(), ln.data_ptr(), b.numel(), _ptr(o, C.c_float), float(d), ptr,
+                                         cap, n_out, sp)
+    return _sized_call(fn, alloc)
 
 
 def union(a: "Body", b: "Body") -> tuple[int, int]:

@@ -35,6 +35,7 @@ UNITS = {
     "mapping.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
     "union.cu": ["-fmad=false"],
     "curve.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"],
+    "intervals.cu": [],
 }
 
 

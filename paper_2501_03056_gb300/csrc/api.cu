@@ -1314,6 +1314,13 @@ int fppg_check_status(uint32_t *word, int32_t *checked) {
     return *word == 0xffffffffu ? FPPG_ERR_CUDA : FPPG_OK;
 }
 
+int fppg_grid_lattice(const fppg_ctx *ctx, float *origin_host, float *d_host) {
+    if (!ctx || !origin_host || !d_host) return fail_global(FPPG_ERR_ARG, "fppg_grid_lattice: NULL argument");
+    for (int a = 0; a < 3; a++) origin_host[a] = ctx->body.tg_o[a];
+    *d_host = ctx->body.dx;
+    return FPPG_OK;
+}
+
 int fppg_device_sm_count(int32_t *sms) {
     if (!sms) return fail_global(FPPG_ERR_ARG, "sms is NULL");
     int dev = 0, v = 0;
