@@ -86,13 +86,14 @@ def test_interval_errors_and_capacity(torch):
         pkg.interval_cells(past, [0, 0, 0], 1.0)
     with pytest.raises(pkg.FPPGError):
         pkg.lattice_intervals(torch.tensor([[-1.0, 0.5, 0.5]], device="cuda"), [0, 0, 0], 1.0)
-    # a capacity below the count: FPPG_ERR_ARG with the count, nothing written
+    # a capacity below the count: FPPG_ERR_ARG with the count, nothing
+    # written ([0, 2) and [10, 12) with [3, 5): three runs, code 2 between)
     two = (dev(torch, [0, 10]), dev(torch, [2, 2]))
     out_b, out_l = dev(torch, [77]), dev(torch, [77])
     n = C.c_int64()
     r = L.fppg_interval_boolean(two[0].data_ptr(), two[1].data_ptr(), 2, one[0].data_ptr(), one[1].data_ptr(), 1,
                                 pkg.UNION, out_b.data_ptr(), out_l.data_ptr(), 1, C.byref(n), None)
-    assert r == pkg.ERR_ARG and n.value == 2 and int(out_b[0]) == 77 and int(out_l[0]) == 77
+    assert r == pkg.ERR_ARG and n.value == 3 and int(out_b[0]) == 77 and int(out_l[0]) == 77
 
 
 @pytest.mark.parametrize("seed", [0, 1])
