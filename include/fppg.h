@@ -544,10 +544,10 @@ int fppg_interval_cells(const uint64_t *begin_dev, const uint64_t *len_dev, int6
  * classes); *amax_host (nullable) the largest |a| over moving particles.
  * stream: a cudaStream_t (NULL = legacy default); the call synchronises it.
  *
- * Every temporary lives in one static device array of about 13 MB (the
+ * Every temporary lives in one static device array of about 9.5 MB (the
  * per-particle arrays, 5 MiB, the start table of every fine key of the
- * grid and its counts, 8 MiB, and a few KB of parameters, flags and radix
- * histograms) that each GPU loading the library holds until the process
+ * grid, 4 MiB, and a few tens of KB of parameters, flags, radix histograms
+ * and the start table's block starts) that each GPU loading the library holds until the process
  * exits.  The first call on
  * a device looks up that array's address (cudaGetSymbolAddress) -- make it
  * before any stream capture.  All calls share the array and it keeps the

@@ -257,15 +257,15 @@ void morton_row_ranks(int ny, int nz, std::vector<uint32_t> &rank) {
 void Group::release_particles() {
     DevGroup &g = d;
     void *ptrs[] = {g.pos,    g.cons,   g.cons_s,   g.key[0], g.key[1],  g.id[0],   g.id[1],  g.pos_s,
-                    g.pos_p,  g.cert,   g.acc_s,    g.hist,   g.coef_s,  g.work,    g.fstart, g.fcount,
-                    g.scan_tmp, g.amax, g.maxdisp,  g.work_count, g.totals};
+                    g.pos_p,  g.cert,   g.acc_s,    g.hist,   g.coef_s,  g.work,    g.fstart, g.bstart,
+                    g.amax,   g.maxdisp, g.work_count, g.totals};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_order_state();
     g.pos = g.pos_s = g.pos_p = g.cert = g.acc_s = nullptr;
     g.cons = g.cons_s = nullptr;
     g.key[0] = g.key[1] = g.id[0] = g.id[1] = nullptr;
-    g.hist = g.fstart = g.fcount = g.scan_tmp = g.amax = g.maxdisp = g.work_count = g.totals = nullptr;
+    g.hist = g.fstart = g.bstart = g.amax = g.maxdisp = g.work_count = g.totals = nullptr;
     g.coef_s = nullptr;
     g.work = nullptr;
     g.N = 0;
@@ -372,9 +372,7 @@ int Group::alloc_particles_once(int64_t N, std::string &err) {
         // from (zero between iterations) and the scan's block sums
         const size_t f1 = (size_t)kSlabs * (size_t)std::max<int64_t>(g.total_cells, 1) + 1;
         CKA(dev_malloc(&g.fstart, sizeof(uint32_t) * f1));
-        CKA(dev_malloc(&g.fcount, sizeof(uint32_t) * f1));
-        CKA(cudaMemset(g.fcount, 0, sizeof(uint32_t) * f1));
-        CKA(dev_malloc(&g.scan_tmp, sizeof(uint32_t) * (size_t)scan_tmp_elems((int64_t)f1)));
+        CKA(dev_malloc(&g.bstart, sizeof(uint32_t) * (size_t)(start_blocks((int64_t)f1) + 1)));
     }
     // the incremental ordering for large groups (the autotuner may switch)
     {
@@ -444,7 +442,7 @@ void Group::free_all() {
     ev.clear();
     DevGroup &g = d;
     void *ptrs[] = {g.params, g.row_rank, g.pos, g.cons, g.cons_s, g.key[0], g.key[1], g.id[0], g.id[1], g.pos_s, g.pos_p, g.cert,
-                    g.acc_s, g.fstart, g.fcount, g.scan_tmp, g.amax, g.maxdisp, g.hist, g.totals, g.coef_s, g.work,
+                    g.acc_s, g.fstart, g.bstart, g.amax, g.maxdisp, g.hist, g.totals, g.coef_s, g.work,
                     g.work_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);

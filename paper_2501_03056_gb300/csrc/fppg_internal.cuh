@@ -10,11 +10,11 @@
 //               key = 8 (key_base + cell) + x-slab of the cell
 //   grid        fstart u32[F + 1], F = 8 x total cells: the first key slot
 //               whose fine key is >= f, dense over every fine key of every
-//               body's neighbour grid (an exclusive scan of fcount, rebuilt
-//               every iteration), so the slots of fine keys [a, b] are
+//               body's neighbour grid (rebuilt every iteration from the
+//               sorted keys), so the slots of fine keys [a, b] are
 //               [fstart[a], fstart[b + 1])
-//               fcount u32[F + 1]: particles per fine key, zero between
-//               iterations (the scan clears it as it reads it)
+//               bstart u32[F / 256 + 2]: the first slot of every block of
+//               256 fine keys, the step that builds fstart
 //   triangles   geo   float4[5 nt]  v0, n, m0, m1 (w = c1), m2 (w = c2)
 //               vx    float4[3 nt]  v0, v1, v2 (w = vertex id bits)
 //               pn    float4[6 nt]  edge pseudonormals 0..2, vertex ones 0..2
@@ -152,8 +152,7 @@ struct DevGroup {
     float4 *cert = nullptr;    // id order: inside certificate {centre, radius} of a volume particle
     float4 *acc_s = nullptr;
     uint32_t *fstart = nullptr;   // F + 1 entries (F = kSlabs * total_cells)
-    uint32_t *fcount = nullptr;   // F + 1 entries, zero between iterations
-    uint32_t *scan_tmp = nullptr; // scan_tmp_elems(F + 1) entries
+    uint32_t *bstart = nullptr;   // start_blocks(F + 1) + 1 entries
     // incremental ordering (the previous iteration's order repaired, see
     // order_incremental); null unless incremental is set
     bool incremental = false;
@@ -287,6 +286,10 @@ __device__ inline uint32_t grid_row_of(const AsmParams &A, int y, int z) {
     const uint32_t r = (uint32_t)y + (uint32_t)A.ng_n[1] * (uint32_t)z;
     return MORTON ? A.row_rank[r] : r;
 }
+
+// the fine keys in blocks of 256 for building the start table (relax.cu)
+constexpr int kStartBlock = 256;
+constexpr int64_t start_blocks(int64_t f1) { return (f1 + kStartBlock - 1) / kStartBlock; }
 
 struct GridPoint {
     float t[3];

@@ -10,7 +10,7 @@
 // cudaMalloc / cudaFree may perform.  The paper has no counterpart.
 //
 // The scratch below is a plain __device__ array: every GPU that loads the
-// library holds it (about 13 MB) until the process exits.  In host code its
+// library holds it (about 9.5 MB) until the process exits.  In host code its
 // name is only a host-side stand-in, not a device address, so the address is
 // looked up with cudaGetSymbolAddress once per device (on the first call
 // made with that device current; make that first call before any stream
@@ -45,11 +45,9 @@ constexpr size_t kOffPosS = kOffId1 + align256(4 * kStaticMaxN);
 constexpr size_t kOffPosP = kOffPosS + align256(16 * kStaticMaxN);
 constexpr size_t kOffAccS = kOffPosP + align256(16 * (kStaticMaxN + 1));
 constexpr int64_t kStaticMaxFine = kSlabs * kStaticMaxCells + 1;   // fine keys + 1
-constexpr int64_t kStaticScanTmp = 2048;                            // block sums of that scan (1030 needed)
 constexpr size_t kOffFstart = kOffAccS + align256(16 * kStaticMaxN);
-constexpr size_t kOffFcount = kOffFstart + align256(4 * kStaticMaxFine);
-constexpr size_t kOffScan = kOffFcount + align256(4 * kStaticMaxFine);
-constexpr size_t kScratchBytes = kOffScan + align256(4 * kStaticScanTmp);
+constexpr size_t kOffBstart = kOffFstart + align256(4 * kStaticMaxFine);
+constexpr size_t kScratchBytes = kOffBstart + align256(4 * (start_blocks(kStaticMaxFine) + 1));
 
 __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
@@ -164,26 +162,17 @@ extern "C" int fppg_forces_static(const float *xyz_dev, const int32_t *cls_dev, 
     d.pos_p = (float4 *)(base + kOffPosP);
     d.acc_s = (float4 *)(base + kOffAccS);
     d.fstart = (uint32_t *)(base + kOffFstart);
-    d.fcount = (uint32_t *)(base + kOffFcount);
-    d.scan_tmp = (uint32_t *)(base + kOffScan);
+    d.bstart = (uint32_t *)(base + kOffBstart);
     d.amax = flags + 1;
     d.maxdisp = flags + 2;
     d.work_count = flags + 3;   // two words: front and back of the search queue
     d.hist = (uint32_t *)(base + kOffHist);
     d.totals = (uint32_t *)(base + kOffTotals);
     uint32_t *error = flags + 5;
-    // the error word, amax and the per-fine-key counts start at zero on
-    // every call (the scan clears the counts, but a call that stopped
-    // half-way would leave them set)
-    const int64_t fine1 = kSlabs * cells + 1;
-    if (scan_tmp_elems(fine1) > kStaticScanTmp) {
-        set_global_error("fppg_forces_static: scan scratch too small");
-        return FPPG_ERR_INTERNAL;
-    }
+    // the error word and amax start at zero on every call
     if (cudaMemcpyAsync(d.params, &A, sizeof(A), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(error, 0, sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMemsetAsync(d.amax, 0, sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMemsetAsync(d.fcount, 0, sizeof(uint32_t) * (size_t)fine1, s) != cudaSuccess) {
+        cudaMemsetAsync(d.amax, 0, sizeof(uint32_t), s) != cudaSuccess) {
         set_global_error("fppg_forces_static: could not set up the scratch");
         return FPPG_ERR_CUDA;
     }

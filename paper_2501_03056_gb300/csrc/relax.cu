@@ -4,9 +4,10 @@
 //   k_keys          A1  cell key per particle (FP32 rule, no contraction);
 //                       zeroes the per-body amax / max-move
 //   radix sort      A2  stable (key, id) sort, 8-bit digits
-//   k_gather        A3  positions in key order; particles per fine key
-//   start scan      A3  the dense table of the first slot of every fine key
-//                       (exclusive scan of the counts, which it clears)
+//   k_gather        A3  positions and constraint ids in key order
+//   start table     A3  the dense table of the first slot of every fine key,
+//                       from the sorted keys (block starts, then a binary
+//                       search per fine key inside its block's slots)
 //   k_force         A4  Eq. 15 over the 3 x 3 rows of 3 cells around the
 //                       particle (each row is one contiguous slot range),
 //                       amax per body by a labelled warp max + atomicMax
@@ -437,15 +438,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const uint32_t *__restr
 }
 
 // ---- A3 ----------------------------------------------------------------------
-// Positions in key order (also as slot pairs) and the number of particles of
-// every fine key: the sorted keys of a warp form runs of equal keys, and the
-// first lane of each run adds the run's length (one atomic per run; the
-// start scan turns the counts into the dense table of first slots).
-__global__ void __launch_bounds__(TPB) k_gather(const uint32_t *__restrict__ key_s, const uint32_t *__restrict__ id_s,
-                                                const float4 *__restrict__ pos, int64_t N, float4 *__restrict__ pos_s,
-                                                float4 *__restrict__ pos_p, uint32_t *__restrict__ fcount,
-                                                const int32_t *__restrict__ cons, int32_t *__restrict__ cons_s,
-                                                uint32_t n_fine) {
+// Positions in key order (also as slot pairs) and the constraint ids in key
+// order.
+__global__ void __launch_bounds__(TPB) k_gather(const uint32_t *__restrict__ id_s, const float4 *__restrict__ pos,
+                                                int64_t N, float4 *__restrict__ pos_s, float4 *__restrict__ pos_p,
+                                                const int32_t *__restrict__ cons, int32_t *__restrict__ cons_s) {
     const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const bool valid = k < N;
     uint32_t id = valid ? id_s[k] : 0u;
@@ -466,17 +463,57 @@ __global__ void __launch_bounds__(TPB) k_gather(const uint32_t *__restrict__ key
         pos_p[(N + 1) / 2 + (k >> 1)] = make_float4(oz, q.z, ow, q.w);
     }
     if (valid) pos_s[k] = q;
-    // runs of equal fine keys inside the warp (lanes past N never start one)
-    const int lane = threadIdx.x & 31;
-    const uint32_t f = valid ? key_s[k] : 0xffffffffu;
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, f, 1);
-    const uint32_t starts = __ballot_sync(0xffffffffu, valid && (lane == 0 || prev != f));
-    const uint32_t ends = __ballot_sync(0xffffffffu, valid) ;
-    if ((starts >> lane) & 1u) {
-        const uint32_t later = starts & ~((2u << lane) - 1u);          // run starts after this lane
-        const int stop = later ? __ffs(later) - 1 : 32 - __clz(ends);  // first lane of the next run, or past the last valid
-        if (FPPG_CHECK(f < n_fine, kChkGather)) atomicAdd(fcount + f, (uint32_t)(stop - lane));
+}
+
+// The dense start table of the fine keys, from the sorted keys themselves:
+// fstart[f] = the first slot whose fine key is >= f, for f in [0, F] (so
+// fstart[F] = N).  The fine keys are cut into blocks of kStartBlock.
+// k_key_block_starts: slot k starts the blocks (b(k - 1), b(k)] (b = key /
+// kStartBlock; block -1 before the first slot, the block count after the
+// last), so each block's first slot is written once, by the slot whose key
+// step crosses it.  k_fine_starts: one CTA per block; the block's slots
+// [bstart[b], bstart[b + 1]) hold every key of the block, and each thread
+// finds its fine key's lower bound among them by binary search, in shared
+// memory when the slots fit.  Every entry is written once: no counts,
+// atomics or scans.  (Tiles of 4096 fine keys with a 16-key walk per
+// thread measured slower: the table of the largest workload, 63 MB, stays
+// in L2 either way, and the short per-thread search keeps more loads in
+// flight.)
+constexpr int kStartStage = 4096;
+
+__global__ void __launch_bounds__(TPB) k_key_block_starts(const uint32_t *__restrict__ key_s, int64_t N,
+                                                          int64_t nblk, uint32_t *__restrict__ bstart) {
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k > N) return;
+    int64_t b0 = k == 0 ? -1 : (int64_t)(key_s[k - 1] / kStartBlock);
+    int64_t b1 = k == N ? nblk : (int64_t)(key_s[k] / kStartBlock);
+    if (!FPPG_CHECK(b0 < nblk && b1 <= nblk, kChkGather)) {   // a key past the fine-key count
+        b0 = min(b0, nblk - 1);
+        b1 = min(b1, nblk);
     }
+    for (int64_t b = b0 + 1; b <= b1; b++) bstart[b] = (uint32_t)k;
+}
+
+__global__ void __launch_bounds__(kStartBlock) k_fine_starts(const uint32_t *__restrict__ key_s,
+                                                             const uint32_t *__restrict__ bstart, int64_t F1,
+                                                             uint32_t *__restrict__ fstart) {
+    __shared__ uint32_t s_key[kStartStage];
+    const int64_t b = blockIdx.x;
+    const uint32_t lo = bstart[b], hi = bstart[b + 1];
+    const uint32_t len = hi > lo ? hi - lo : 0u;
+    const bool staged = len <= (uint32_t)kStartStage;
+    if (staged)
+        for (uint32_t i = threadIdx.x; i < len; i += kStartBlock) s_key[i] = key_s[lo + i];
+    __syncthreads();
+    const int64_t f = b * kStartBlock + threadIdx.x;
+    if (f >= F1) return;
+    uint32_t a = 0u, c = len;   // first of the block's slots with key >= f
+    while (a < c) {
+        const uint32_t m = (a + c) >> 1;
+        if ((int64_t)(staged ? s_key[m] : key_s[lo + m]) < f) a = m + 1u;
+        else c = m;
+    }
+    fstart[f] = lo + a;
 }
 
 // ---- A4 ----------------------------------------------------------------------
@@ -1687,15 +1724,17 @@ int build_grid_dev(DevGroup &d, cudaStream_t s) {
                                                                      d.maxdisp, d.B, d.work_count);
         buf = radix_sort_u32(d.key, d.id, true, d.N, d.key_bits, d.hist, d.totals, s);
     }
-    k_gather<<<nblocks(d.N), TPB, 0, s>>>(d.key[buf], d.id[buf], d.pos, d.N, d.pos_s, d.pos_p, d.fcount, d.cons,
-                                          d.cons_s, (uint32_t)(kSlabs * d.total_cells));
+    k_gather<<<nblocks(d.N), TPB, 0, s>>>(d.id[buf], d.pos, d.N, d.pos_s, d.pos_p, d.cons, d.cons_s);
+    // the start table from the sorted keys
     const int64_t F1 = kSlabs * d.total_cells + 1;
-    exclusive_scan_u32_clear(d.fcount, d.fstart, F1, d.scan_tmp, scan_tmp_elems(F1), s);
+    const int64_t nblk = start_blocks(F1);
+    k_key_block_starts<<<nblocks(d.N + 1), TPB, 0, s>>>(d.key[buf], d.N, nblk, d.bstart);
+    k_fine_starts<<<(unsigned)nblk, kStartBlock, 0, s>>>(d.key[buf], d.bstart, F1, d.fstart);
     return buf;
 }
 
 int grid_kernels(const DevGroup &d) {
-    const int tail = 1 + scan_clear_launches(kSlabs * d.total_cells + 1);    // gather + start scan
+    const int tail = 3;    // gather, block starts, fine-key starts
     if (!d.incremental) return 1 + 3 * d.passes + tail;
     // keys, keep bits, the scan of the tile counts and the counts, 2
     // compactions, the changed list's radix passes, merge splits and merge
