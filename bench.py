@@ -60,12 +60,12 @@ def workload(name, rank=0, dx=0.02):
     rank its own seeded copy."""
     from paper_2501_03056_gb300 import workloads as W
     if name == "vehicle":
-        return W.vehicle_workload(), ("vehicle shell (config 5): rounded boxes + 4 wheels, surface nets + 2 Loop "
+        return W.vehicle_workload(), ("vehicle shell: rounded boxes + 4 wheels, surface nets + 2 Loop "
                                       "steps, 2,009,344 triangles, 1e-3 noise, 30 deg features, dx=0.0068, "
                                       "particles generated on the GPU (Sec. 3.2)")
     if name == "sphere_torus":
         return (W.sphere_torus_workload(seed=1 + 10 * rank, dx=dx),
-                f"icosphere_l5+torus_256x64 (config 2) dx={dx}")
+                f"icosphere_l5+torus_256x64 dx={dx}")
     raise ValueError(name)
 
 
@@ -422,7 +422,7 @@ def main():
                                                "headline workload (host wall clock around synchronised calls)"}
         batch.close()
 
-        # ---- config 2 (icosphere + torus) as its own leg ------------------------
+        # ---- the icosphere + torus workload as its own leg ------------------------
         if args.workload != "sphere_torus":
             st_asm, st_desc = workload("sphere_torus", rank, 0.02)
             S2 = measure(st_asm, st_desc, 10, 3, with_plain=True, plain_steps=4)
@@ -448,11 +448,11 @@ def main():
                     "unit": "particle-iterations/s", "autotune": R["tuned"], "phase_ms_per_iteration": R["phases"]}
 
         line["configs"] = {
-            "cube (config 1, dx=0.05)": config_leg(W.cube_workload()),
-            "spur gear (config 3, dx=0.004, generated)": config_leg(W.gear_workload()),
+            "unit cube (12 triangles, dx=0.05)": config_leg(W.cube_workload()),
+            "spur gear (51,840 triangles, dx=0.004, generated)": config_leg(W.gear_workload()),
         }
 
-        # ---- generation (Sec. 3.2) on the GPU: config 3's gear ------------------
+        # ---- generation (Sec. 3.2) on the GPU: the spur gear ------------------
         ga = W.gear_workload()[0]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -527,7 +527,7 @@ def main():
         ee.record(stream)
         torch.cuda.synchronize()
         line["energy"] = {"relax_energy": {"value": e_relax, "unit": "particle-iterations/s",
-                                           "iterations": Ge, "form": "plain, icosphere + torus (config 2)"},
+                                           "iterations": Ge, "form": "plain, icosphere + torus"},
                           "energy_and_backward_ms": es.elapsed_time(ee) / reps,
                           "backward_workload": f"torus body, {tb.n} particles, {len(ta.verts)} vertices: "
                                                "E, dE/dy and dE/dverts through the frozen surface projection"}

@@ -509,7 +509,7 @@ def batch_workload(seed: int = 3, bodies: int = 64, dx: float = 0.008) -> list[A
 
 def union_pair_workload(seed: int = 5, dx: float = 0.05) -> list[Assembly]:
     """Two overlapping bodies for the Boolean union (Sec. 3.2.3): the unit
-    cube [-0.5, 0.5]^3 (lattice particles as config 1, 30 degree features)
+    cube [-0.5, 0.5]^3 (lattice particles as the unit cube workload, 30 degree features)
     and an icosphere of level 3, r = 0.35, centred at (0.45, 0.05, -0.03)
     (Fibonacci surface points and a volume lattice), so that the sphere pokes
     out of the cube's +x face.  meta["union_with"] names the partner."""
@@ -526,7 +526,7 @@ def union_pair_workload(seed: int = 5, dx: float = 0.05) -> list[Assembly]:
 
 
 def batch_union_workload(seed: int = 3, bodies: int = 64, dx: float = 0.008) -> list[Assembly]:
-    """Config 4 with its Boolean unions: the 64 bodies of batch_workload,
+    """The 64-body batch with its Boolean unions: the 64 bodies of batch_workload,
     except that the body after each gear becomes a shaft through that gear
     (a cylinder of radius 0.2 and height 0.5 at the gear's scale, through the
     bore of radius 0.15, so it overlaps the hub and sticks out on both

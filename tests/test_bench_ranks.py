@@ -67,7 +67,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    # a bounded crop of the vehicle shell (config 5): 1/16 of its 19.2 M
+    # a bounded crop of the vehicle shell: 1/16 of its 19.2 M
     # generated particles, the same workload as the GPU arm's headline
     assert "vehicle" in d["config"]["workload"] and "smallest x" in d["config"]["sample"]
     assert 1.1e6 < d["config"]["particles"] < 1.3e6

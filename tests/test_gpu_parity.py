@@ -25,7 +25,7 @@ def built():
 
 
 def small_sphere_torus(seed=1):
-    """Config-2 geometry at a coarser spacing (oracle finishes in seconds)."""
+    """The icosphere + torus geometry at a coarser spacing (the oracle finishes in seconds)."""
     return W.sphere_torus_workload(seed=seed, dx=0.06, level=3, torus_nu=64, torus_nv=24)
 
 

@@ -1,7 +1,7 @@
 """Boolean union (Sec. 3.2.3, Fig. 10) on the GPU against the FP64 oracle:
 the particles that stay (bit-exact), the union relaxed as one assembly in
 the batched form, surfaces kept out of the partner, the calls that must
-fail, and config 4's gear-shaft unions at full size."""
+fail, and the 64-body batch's gear-shaft unions at full size."""
 import numpy as np
 import pytest
 
