@@ -106,3 +106,38 @@ def test_triangle_cell_hash_uses_the_primes_as_printed():
     src = open(os.path.join(ROOT, "paper_2501_03056_gb300", "csrc", "fppg_internal.cuh")).read()
     m = re.search(r"kHashP1\s*=\s*(\d+)u,\s*kHashP2\s*=\s*(\d+)u,\s*kHashP3\s*=\s*(\d+)u", src)
     assert m and gold == {"p1": int(m.group(1)), "p2": int(m.group(2)), "p3": int(m.group(3))}
+
+
+def test_interval_calls_reject_bad_arguments_before_any_launch(library):
+    # the C_compact interval calls check their arguments on the host first
+    L = pkg.lib()
+    n = ctypes.c_int64(-5)
+    o = (ctypes.c_float * 3)(0.0, 0.0, 0.0)
+    nan = (ctypes.c_float * 3)(float("nan"), 0.0, 0.0)
+    # unknown op, negative sizes, a missing count pointer
+    assert L.fppg_interval_boolean(None, None, 0, None, None, 0, 3, None, None, 0, ctypes.byref(n), None) == pkg.ERR_ARG
+    assert b"op" in L.fppg_last_error(None)
+    assert L.fppg_interval_boolean(None, None, -1, None, None, 0, pkg.UNION, None, None, 0, ctypes.byref(n),
+                                   None) == pkg.ERR_ARG
+    assert L.fppg_interval_boolean(None, None, 0, None, None, 0, pkg.UNION, None, None, 0, None, None) == pkg.ERR_ARG
+    # runs given without their arrays, a capacity without output arrays
+    assert L.fppg_interval_boolean(None, None, 4, None, None, 0, pkg.UNION, None, None, 0, ctypes.byref(n),
+                                   None) == pkg.ERR_ARG
+    assert L.fppg_interval_cells(None, None, 0, o, ctypes.c_float(1.0), None, 8, ctypes.byref(n), None) == pkg.ERR_ARG
+    # a lattice spacing that is not finite and positive, a non-finite origin
+    for d in (0.0, -1.0, float("inf"), float("nan")):
+        assert L.fppg_lattice_intervals(None, 0, o, ctypes.c_float(d), None, None, 0, ctypes.byref(n),
+                                        None) == pkg.ERR_ARG, d
+        assert L.fppg_interval_cells(None, None, 0, o, ctypes.c_float(d), None, 0, ctypes.byref(n),
+                                     None) == pkg.ERR_ARG, d
+    assert L.fppg_lattice_intervals(None, 0, nan, ctypes.c_float(1.0), None, None, 0, ctypes.byref(n),
+                                    None) == pkg.ERR_ARG
+    # empty inputs need no device: an empty result
+    n.value = -5
+    assert L.fppg_interval_boolean(None, None, 0, None, None, 0, pkg.DIFFERENCE, None, None, 0, ctypes.byref(n),
+                                   None) == pkg.OK and n.value == 0
+    n.value = -5
+    assert L.fppg_lattice_intervals(None, 0, o, ctypes.c_float(0.5), None, None, 0, ctypes.byref(n),
+                                    None) == pkg.OK and n.value == 0
+    d = ctypes.c_float()
+    assert L.fppg_grid_lattice(None, o, ctypes.byref(d)) == pkg.ERR_ARG
