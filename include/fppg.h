@@ -384,7 +384,11 @@ int fppg_batch_load(fppg_batch *b);
  * (fppg_batch_set_cell_order), keeps the fastest and restores the particle
  * state afterwards.  The choice is cached per (particle-count bucket,
  * volume-particle share, GPU name) for the life of the process; a cached
- * choice is applied without timing.  Outputs (nullable): chosen variant,
+ * choice is applied without timing.  Every variant, block size, search
+ * grid and ordering gives the same bits; the Morton row order moves
+ * particles between the force loop's two partial sums, so it agrees with
+ * row-major rows up to FP32 rounding (a plain body set to the same row
+ * order gives the batch's bits).  Outputs (nullable): chosen variant,
  * block size, search CTAs, ordering (1 incremental), row order and the
  * measured ms per iteration (0 when taken from the cache). */
 int fppg_batch_autotune(fppg_batch *b, int32_t iters, int32_t *variant, int32_t *block, int32_t *search_ctas,
