@@ -173,3 +173,50 @@ def test_volume_grid_set_of_a_body_reproduces_its_volume_particles():
     back = oracle.interval_cells(runs, tg_o, a.dx)
     key = lambda p: sorted(map(tuple, p.tolist()))
     assert len(back) == len(vol) and key(back) == key(vol)
+
+
+def _sphere_and_box(dx):
+    """An icosphere and a box with the same lower bounding-box corner, so
+    that their generation lattices (triangle-grid origin and dx) coincide."""
+    v1, t1 = W.icosphere_mesh(3, 0.5)
+    lo = v1.min(axis=0)
+    v2, t2 = W.cube_mesh(0.5)
+    v2 = ((v2 + np.float32(0.5)) * np.float32(0.6) + lo).astype(np.float32)
+    h = W.smoothing_length(dx)
+    gen = {"generate": {"band_cells": 0, "inner_cells": 0}}
+    return [W.Assembly("sphere", v1, t1, dx, h, None, None, 30.0, dict(gen)),
+            W.Assembly("box", v2, t2, dx, h, None, None, 30.0, dict(gen))]
+
+
+def test_interval_algebra_and_the_particle_rule_differ_only_on_the_other_surface():
+    # two readings of the Boolean operation on the volume particles of two
+    # bodies that share a lattice: the interval algebra of their interior
+    # grid sets (Fig. 10) and the particle rule of the relaxed operation
+    # (each particle tested against the other mesh by ray parity).  Cells
+    # without the cutter's triangles are inside it exactly when they are in
+    # its interior set, so the two agree everywhere off the cells that hold
+    # the second body's triangles.
+    dx = float(np.float32(0.04))
+    a, b = _sphere_and_box(dx)
+    oa, ob = oracle.from_assembly(a), oracle.from_assembly(b)
+    (o1, _, _), (o2, _, nb) = oa.tri_grid(), ob.tri_grid()
+    assert np.array_equal(o1, o2)
+
+    def cells(x):
+        return {tuple(t) for t in np.floor((x.astype(np.float32) - o1) / np.float32(dx)).astype(np.int64).tolist()}
+
+    xa, ca, _ = oa.get_particles()
+    xb, cb, _ = ob.get_particles()
+    va, vb = ca == 1, cb == 1                         # volume particles
+    ra = oracle.lattice_intervals(xa[va].astype(np.float32), o1, dx)
+    rb = oracle.lattice_intervals(xb[vb].astype(np.float32), o1, dx)
+    keys, _ = ob.tri_bins()                           # cells that hold the box's triangles
+    k = keys.astype(np.int64)
+    surf_b = set(zip((k % nb[0]).tolist(), ((k // nb[0]) % nb[1]).tolist(), (k // (nb[0] * nb[1])).tolist()))
+    assert cells(xa[va]) & surf_b                     # the box's surface crosses the sphere's interior
+    for op in (UNION, DIFFERENCE, INTERSECTION):
+        ka = oa.boolean_keep(ob, op, True)
+        kb = ob.boolean_keep(oa, op, False)
+        by_particles = cells(xa[va & ka]) | cells(xb[vb & kb])
+        by_intervals = cells(oracle.interval_cells(oracle.interval_boolean(ra, rb, op), o1, dx))
+        assert by_particles - surf_b == by_intervals - surf_b, op
