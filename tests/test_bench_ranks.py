@@ -77,3 +77,15 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_cpu_baseline_leg_times_the_oracle_on_the_cores_and_on_one_thread():
+    import bench
+    import oracle
+    from paper_2501_03056_gb300 import workloads as W
+    before = oracle.get_threads()
+    out = bench.cpu_baseline_leg(W.cube_workload(), "sphere_torus")     # whole bodies, one iteration
+    assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] == before
+    one = out["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["cores_over_one"] > 0
+    assert oracle.get_threads() == before                               # the thread count is restored
